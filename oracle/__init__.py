@@ -1,0 +1,170 @@
+"""FP64 CPU oracle for the GAMER-2 patch-group hydro update (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA path:
+the C sources here are compiled by ``oracle/build.py`` into ``liboracle.so``
+and called through ctypes on numpy arrays in the dense whole-level layout
+``U[var][z][y][x]``.
+
+Every function cites the paper passage it follows (GAMER-2, Schive et al.
+2018): section 2.2 (Hydrodynamics: MUSCL-Hancock, PLM, van Leer-type limiter,
+HLLC; restriction and flux fix-up), section 2.6 (Eq. CFL2), section 2.1 (AMR
+structure, adaptive time-step pseudo-code, refinement and flag buffers).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        _lib = ctypes.CDLL(path)
+        L = _lib
+        L.or_prim.argtypes = [_dp, _dp, ctypes.c_double]
+        L.or_cons.argtypes = [_dp, _dp, ctypes.c_double]
+        L.or_flux.argtypes = [_dp, ctypes.c_int, ctypes.c_double, _dp]
+        L.or_vanleer.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.or_vanleer.restype = ctypes.c_double
+        L.or_hllc.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_double, _dp]
+        L.or_max_speed.argtypes = [_dp, ctypes.c_int64, ctypes.c_double]
+        L.or_max_speed.restype = ctypes.c_double
+        L.or_dt_cfl2.argtypes = [_dp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.or_dt_cfl2.restype = ctypes.c_double
+        L.or_step_periodic.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.or_step_periodic.restype = ctypes.c_int64
+        L.or_conserved_sum.argtypes = [_dp, ctypes.c_int64, ctypes.c_double, _dp]
+        L.or_exact_star.argtypes = [ctypes.c_double] * 7 + [_dp, _dp]
+        L.or_exact_pstar_bisect.argtypes = [ctypes.c_double] * 7
+        L.or_exact_pstar_bisect.restype = ctypes.c_double
+        L.or_exact_sample.argtypes = [ctypes.c_double] * 7 + [_dp, ctypes.c_int, _dp, _dp, _dp]
+        for extra in ("_register_amr", "_register_adjoint"):
+            fn = globals().get(extra)
+            if fn is not None:
+                fn(L)
+    return _lib
+
+
+def _ptr(a):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_dp)
+
+
+def _vec(x):
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+
+
+# ---- pointwise pieces (section 2.2) -----------------------------------------
+
+def prim(U, gamma):
+    """Conserved -> primitive for one state (ideal gas)."""
+    U = _vec(U)
+    W = np.empty(5)
+    lib().or_prim(_ptr(U), _ptr(W), gamma)
+    return W
+
+
+def cons(W, gamma):
+    """Primitive -> conserved for one state."""
+    W = _vec(W)
+    U = np.empty(5)
+    lib().or_cons(_ptr(W), _ptr(U), gamma)
+    return U
+
+
+def flux(U, d, gamma):
+    """Physical Euler flux along direction d of one conserved state."""
+    U = _vec(U)
+    F = np.empty(5)
+    lib().or_flux(_ptr(U), d, gamma, _ptr(F))
+    return F
+
+
+def vanleer(a, b):
+    """van Leer-type limiter, 2ab/(a+b) when ab>0 else 0 (section 2.2)."""
+    return lib().or_vanleer(a, b)
+
+
+def hllc(UL, UR, d, gamma):
+    """HLLC flux through a face normal to d (section 2.2, HLLC solver)."""
+    UL, UR = _vec(UL), _vec(UR)
+    F = np.empty(5)
+    lib().or_hllc(_ptr(UL), _ptr(UR), d, gamma, _ptr(F))
+    return F
+
+
+# ---- whole-level operations ---------------------------------------------------
+
+def max_speed(U, gamma):
+    """max over cells of |vx|+|vy|+|vz|+3c_s (denominator of Eq. CFL2)."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    return lib().or_max_speed(_ptr(U), U[0].size, gamma)
+
+
+def dt_cfl2(U, gamma, cfl, dh):
+    """Eq. CFL2: dt = C_CFL dh / max(|vx|+|vy|+|vz|+3c_s)."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    return lib().or_dt_cfl2(_ptr(U), U[0].size, gamma, cfl, dh)
+
+
+def step_periodic(U, dh, dt, gamma):
+    """One MUSCL-Hancock + PLM + HLLC step on a periodic uniform grid.
+
+    U: [5][nz][ny][nx] float64.  Returns (U_new, n_unphysical)."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    _, nz, ny, nx = U.shape
+    Un = np.empty_like(U)
+    nbad = lib().or_step_periodic(_ptr(U), _ptr(Un), nx, ny, nz, dh, dt, gamma)
+    return Un, nbad
+
+
+def run_periodic(U, dh, gamma, cfl, n_steps):
+    """n_steps steps, each with dt from Eq. CFL2 on the state at the step's start.
+
+    Returns (U, list of dt)."""
+    dts = []
+    for _ in range(n_steps):
+        dt = dt_cfl2(U, gamma, cfl, dh)
+        if not dt > 0:
+            raise FloatingPointError("unphysical state (rho<=0 or P<=0)")
+        U, nbad = step_periodic(U, dh, dt, gamma)
+        if nbad:
+            raise FloatingPointError(f"{nbad} unphysical cells")
+        dts.append(dt)
+    return U, dts
+
+
+def conserved_sum(U, dV):
+    """Sum of U*dV per variable, pairwise in fixed cell order."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    out = np.empty(5)
+    lib().or_conserved_sum(_ptr(U), U[0].size, dV, _ptr(out))
+    return out
+
+
+# ---- exact Riemann solver (validation only) ----------------------------------
+
+def exact_star(rl, ul, pl, rr, ur, pr, gamma):
+    ps, us = ctypes.c_double(), ctypes.c_double()
+    lib().or_exact_star(rl, ul, pl, rr, ur, pr, gamma, ctypes.byref(ps), ctypes.byref(us))
+    return ps.value, us.value
+
+
+def exact_pstar_bisect(rl, ul, pl, rr, ur, pr, gamma):
+    return lib().or_exact_pstar_bisect(rl, ul, pl, rr, ur, pr, gamma)
+
+
+def exact_sample(left, right, gamma, xi):
+    xi = _vec(xi)
+    n = xi.size
+    r, u, p = np.empty(n), np.empty(n), np.empty(n)
+    lib().or_exact_sample(*left, *right, gamma, _ptr(xi), n, _ptr(r), _ptr(u), _ptr(p))
+    return r, u, p

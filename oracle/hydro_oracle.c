@@ -1,0 +1,413 @@
+/*
+ * hydro_oracle.c -- plain FP64 CPU oracle for the GAMER-2 patch-group fluid
+ * update (Schive et al. 2018, "GAMER-2", section 2.2 Hydrodynamics and
+ * section 2.6 Time-step).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call this file:
+ * only the tests, the smoke check and the benchmark's CPU-baseline leg load it.
+ *
+ * It is written as slow, obviously correct per-cell loops over whole-level
+ * dense arrays U[var][z][y][x] (x fastest), never over patch tiles, so that it
+ * shares no structure with the CUDA path.  Conserved variables are
+ * U = (rho, rho vx, rho vy, rho vz, E); primitives W = (rho, vx, vy, vz, P).
+ *
+ * Scheme (section 2.2: MUSCL-Hancock "MHM", PLM on primitive variables,
+ * van Leer-type limiter, HLLC Riemann solver).  The paper defers the scheme's
+ * details to Toro (2009); the readings taken here are:
+ *   - slopes on primitives, per component and per dimension,
+ *     vL(a,b) = 2ab/(a+b) if ab > 0 else 0 (harmonic van Leer form);
+ *   - face states W_{d,-/+} = W -/+ dW_d/2, converted to U;
+ *   - Hancock half step: every face state of a cell gets
+ *     + (dt/2dh) sum_d [F_d(U_{d,-}) - F_d(U_{d,+})];
+ *   - HLLC with Einfeldt/Roe-averaged outer wave speeds, contact speed S*,
+ *     Toro's star states, tie rules S_L>=0 -> F_L, S_R<=0 -> F_R,
+ *     S*>=0 -> F*_L else F*_R;
+ *   - conservative update U^{n+1} = U^n - (dt/dh) sum_d (F_{i+1/2}-F_{i-1/2}).
+ * Time step: Eq. (CFL2), dt = C_CFL dh / max(|vx|+|vy|+|vz|+3 c_s).
+ *
+ * Every per-cell loop is independent, so the OpenMP static split changes no
+ * result: the oracle is bitwise reproducible for any thread count (the
+ * paper's section 2.7.1 property).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NV 5
+
+static inline int64_t cell_index(int x, int y, int z, int nx, int ny) {
+    return ((int64_t)z * ny + y) * nx + x;
+}
+
+static inline int wrap(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+/* ---- equation of state (ideal gas) ------------------------------------ */
+
+/* U -> W.  P = (gamma-1)(E - rho|v|^2/2). */
+void or_prim(const double *U, double *W, double gamma) {
+    double rho = U[0];
+    double vx = U[1] / rho, vy = U[2] / rho, vz = U[3] / rho;
+    double ekin = 0.5 * rho * (vx * vx + vy * vy + vz * vz);
+    W[0] = rho;
+    W[1] = vx;
+    W[2] = vy;
+    W[3] = vz;
+    W[4] = (gamma - 1.0) * (U[4] - ekin);
+}
+
+/* W -> U.  E = P/(gamma-1) + rho|v|^2/2. */
+void or_cons(const double *W, double *U, double gamma) {
+    double rho = W[0];
+    U[0] = rho;
+    U[1] = rho * W[1];
+    U[2] = rho * W[2];
+    U[3] = rho * W[3];
+    U[4] = W[4] / (gamma - 1.0) + 0.5 * rho * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+}
+
+/* Physical Euler flux along direction d (0=x,1=y,2=z) of conserved state U. */
+void or_flux(const double *U, int d, double gamma, double *F) {
+    double W[NV];
+    or_prim(U, W, gamma);
+    double vn = W[1 + d], P = W[4];
+    F[0] = U[0] * vn;
+    F[1] = U[1] * vn;
+    F[2] = U[2] * vn;
+    F[3] = U[3] * vn;
+    F[1 + d] += P;
+    F[4] = (U[4] + P) * vn;
+}
+
+/* Sound speed c_s = sqrt(gamma P / rho). */
+static double sound_speed(const double *W, double gamma) {
+    return sqrt(gamma * W[4] / W[0]);
+}
+
+/* van Leer-type slope limiter (section 2.2), harmonic form. */
+double or_vanleer(double a, double b) {
+    double ab = a * b;
+    return ab > 0.0 ? 2.0 * ab / (a + b) : 0.0;
+}
+
+/* ---- HLLC Riemann solver (section 2.2; Toro 2009 ch. 10 form) ---------- */
+
+/* Flux across a face normal to direction d, left state UL, right state UR. */
+void or_hllc(const double *UL, const double *UR, int d, double gamma, double *F) {
+    double WL[NV], WR[NV], FL[NV], FR[NV];
+    or_prim(UL, WL, gamma);
+    or_prim(UR, WR, gamma);
+    or_flux(UL, d, gamma, FL);
+    or_flux(UR, d, gamma, FR);
+
+    double rl = WL[0], pl = WL[4], ul = WL[1 + d];
+    double rr = WR[0], pr = WR[4], ur = WR[1 + d];
+    double cl = sound_speed(WL, gamma), cr = sound_speed(WR, gamma);
+
+    /* Roe averages (Einfeldt/Batten outer speed estimate). */
+    double sl = sqrt(rl), sr = sqrt(rr);
+    double vt[3];
+    for (int k = 0; k < 3; k++) vt[k] = (sl * WL[1 + k] + sr * WR[1 + k]) / (sl + sr);
+    double hl = (UL[4] + pl) / rl, hr = (UR[4] + pr) / rr;
+    double ht = (sl * hl + sr * hr) / (sl + sr);
+    double ct = sqrt((gamma - 1.0) * (ht - 0.5 * (vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2])));
+
+    double a = ul - cl, b = vt[d] - ct;
+    double SL = (a <= b) ? a : b;
+    a = ur + cr;
+    b = vt[d] + ct;
+    double SR = (a >= b) ? a : b;
+
+    if (SL >= 0.0) {
+        for (int v = 0; v < NV; v++) F[v] = FL[v];
+        return;
+    }
+    if (SR <= 0.0) {
+        for (int v = 0; v < NV; v++) F[v] = FR[v];
+        return;
+    }
+    double Ss = (pr - pl + rl * ul * (SL - ul) - rr * ur * (SR - ur)) /
+                (rl * (SL - ul) - rr * (SR - ur));
+    /* side K = L if S* >= 0 else R */
+    const double *UK = (Ss >= 0.0) ? UL : UR;
+    const double *WK = (Ss >= 0.0) ? WL : WR;
+    const double *FK = (Ss >= 0.0) ? FL : FR;
+    double SK = (Ss >= 0.0) ? SL : SR;
+    double rK = WK[0], uK = WK[1 + d], pK = WK[4];
+    double fac = rK * (SK - uK) / (SK - Ss);
+    double Us[NV];
+    Us[0] = fac;
+    for (int k = 0; k < 3; k++) Us[1 + k] = fac * WK[1 + k];
+    Us[1 + d] = fac * Ss;
+    Us[4] = fac * (UK[4] / rK + (Ss - uK) * (Ss + pK / (rK * (SK - uK))));
+    for (int v = 0; v < NV; v++) F[v] = FK[v] + SK * (Us[v] - UK[v]);
+}
+
+/* ---- time step, Eq. (CFL2) --------------------------------------------- */
+
+/* max over cells of |vx|+|vy|+|vz|+3 c_s.  Returns -1 if a cell has
+ * rho<=0 or P<=0 (unphysical: no floors in the oracle). */
+double or_max_speed(const double *U, int64_t ncell, double gamma) {
+    double smax = 0.0;
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(max : smax) reduction(| : bad)
+    for (int64_t i = 0; i < ncell; i++) {
+        double u[NV], W[NV];
+        for (int v = 0; v < NV; v++) u[v] = U[v * ncell + i];
+        or_prim(u, W, gamma);
+        if (!(W[0] > 0.0) || !(W[4] > 0.0)) {
+            bad = 1;
+            continue;
+        }
+        double s = fabs(W[1]) + fabs(W[2]) + fabs(W[3]) + 3.0 * sound_speed(W, gamma);
+        if (s > smax) smax = s;
+    }
+    return bad ? -1.0 : smax;
+}
+
+double or_dt_cfl2(const double *U, int64_t ncell, double gamma, double cfl, double dh) {
+    double s = or_max_speed(U, ncell, gamma);
+    if (s <= 0.0) return -1.0;
+    return cfl * dh / s;
+}
+
+/* ---- one MUSCL-Hancock step on a uniform periodic grid ----------------- */
+
+/*
+ * U, Unew: [5][nz][ny][nx] FP64.  dh: cell width, dt: time step.
+ * Returns the number of cells of Unew with rho<=0 or P<=0.
+ */
+int64_t or_step_periodic(const double *U, double *Unew, int nx, int ny, int nz,
+                         double dh, double dt, double gamma) {
+    const int64_t n = (int64_t)nx * ny * nz;
+    const int dims[3] = {nx, ny, nz};
+    double *W = malloc(sizeof(double) * NV * n);
+    /* face states after the Hancock half step: FS[face][var][cell],
+     * face = 2*d + s, s=0 the low (-) face, s=1 the high (+) face */
+    double *FS = malloc(sizeof(double) * 6 * NV * n);
+    /* interface fluxes: FX[d][var][cell] is the flux through the high face
+     * of the cell along d (i.e. at i+1/2) */
+    double *FX = malloc(sizeof(double) * 3 * NV * n);
+
+    /* 1. primitives */
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        double u[NV], w[NV];
+        for (int v = 0; v < NV; v++) u[v] = U[v * n + i];
+        or_prim(u, w, gamma);
+        for (int v = 0; v < NV; v++) W[v * n + i] = w[v];
+    }
+
+    /* 2.-3. limited slopes, face states, Hancock half step */
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                int c[3] = {x, y, z};
+                int64_t i = cell_index(x, y, z, nx, ny);
+                double w[NV], Wf[6][NV], Uf[6][NV];
+                for (int v = 0; v < NV; v++) w[v] = W[v * n + i];
+                for (int d = 0; d < 3; d++) {
+                    int cm[3] = {c[0], c[1], c[2]}, cp[3] = {c[0], c[1], c[2]};
+                    cm[d] = wrap(c[d] - 1, dims[d]);
+                    cp[d] = wrap(c[d] + 1, dims[d]);
+                    int64_t im = cell_index(cm[0], cm[1], cm[2], nx, ny);
+                    int64_t ip = cell_index(cp[0], cp[1], cp[2], nx, ny);
+                    for (int v = 0; v < NV; v++) {
+                        double slope = or_vanleer(w[v] - W[v * n + im], W[v * n + ip] - w[v]);
+                        Wf[2 * d][v] = w[v] - 0.5 * slope;
+                        Wf[2 * d + 1][v] = w[v] + 0.5 * slope;
+                    }
+                }
+                for (int f = 0; f < 6; f++) or_cons(Wf[f], Uf[f], gamma);
+                double inc[NV] = {0, 0, 0, 0, 0};
+                for (int d = 0; d < 3; d++) {
+                    double Fm[NV], Fp[NV];
+                    or_flux(Uf[2 * d], d, gamma, Fm);
+                    or_flux(Uf[2 * d + 1], d, gamma, Fp);
+                    for (int v = 0; v < NV; v++) inc[v] += Fm[v] - Fp[v];
+                }
+                for (int f = 0; f < 6; f++)
+                    for (int v = 0; v < NV; v++)
+                        FS[((int64_t)f * NV + v) * n + i] = Uf[f][v] + 0.5 * dt / dh * inc[v];
+            }
+
+    /* 4. HLLC at every face i+1/2: left = high face state of cell i,
+     *    right = low face state of cell i+1 */
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                int c[3] = {x, y, z};
+                int64_t i = cell_index(x, y, z, nx, ny);
+                for (int d = 0; d < 3; d++) {
+                    int cp[3] = {c[0], c[1], c[2]};
+                    cp[d] = wrap(c[d] + 1, dims[d]);
+                    int64_t ip = cell_index(cp[0], cp[1], cp[2], nx, ny);
+                    double UL[NV], UR[NV], F[NV];
+                    for (int v = 0; v < NV; v++) {
+                        UL[v] = FS[((int64_t)(2 * d + 1) * NV + v) * n + i];
+                        UR[v] = FS[((int64_t)(2 * d) * NV + v) * n + ip];
+                    }
+                    or_hllc(UL, UR, d, gamma, F);
+                    for (int v = 0; v < NV; v++) FX[((int64_t)d * NV + v) * n + i] = F[v];
+                }
+            }
+
+    /* 5. conservative update */
+    int64_t nbad = 0;
+#pragma omp parallel for schedule(static) reduction(+ : nbad)
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                int c[3] = {x, y, z};
+                int64_t i = cell_index(x, y, z, nx, ny);
+                double un[NV];
+                for (int v = 0; v < NV; v++) {
+                    double div = 0.0;
+                    for (int d = 0; d < 3; d++) {
+                        int cm[3] = {c[0], c[1], c[2]};
+                        cm[d] = wrap(c[d] - 1, dims[d]);
+                        int64_t im = cell_index(cm[0], cm[1], cm[2], nx, ny);
+                        div += FX[((int64_t)d * NV + v) * n + i] - FX[((int64_t)d * NV + v) * n + im];
+                    }
+                    un[v] = U[v * n + i] - dt / dh * div;
+                    Unew[v * n + i] = un[v];
+                }
+                double w[NV];
+                or_prim(un, w, gamma);
+                if (!(w[0] > 0.0) || !(w[4] > 0.0)) nbad++;
+            }
+
+    free(W);
+    free(FS);
+    free(FX);
+    return nbad;
+}
+
+/* ---- conservation sums (pairwise, fixed order) ------------------------- */
+
+static double pairwise_sum(const double *a, int64_t n) {
+    if (n <= 8) {
+        double s = 0.0;
+        for (int64_t i = 0; i < n; i++) s += a[i];
+        return s;
+    }
+    int64_t h = n / 2;
+    return pairwise_sum(a, h) + pairwise_sum(a + h, n - h);
+}
+
+/* out[v] = sum_cells U[v] * dV, pairwise summation in cell order. */
+void or_conserved_sum(const double *U, int64_t ncell, double dV, double *out) {
+    for (int v = 0; v < NV; v++) out[v] = pairwise_sum(U + v * ncell, ncell) * dV;
+}
+
+/* ---- exact Riemann solver for the 1D Euler equations (Toro 2009 ch. 4) -- */
+/* Used only to validate the scheme on Sod-type problems. */
+
+static void pressure_fn(double p, double rk, double pk, double ck, double gamma,
+                        double *f, double *df) {
+    if (p > pk) { /* shock */
+        double A = 2.0 / ((gamma + 1.0) * rk), B = (gamma - 1.0) / (gamma + 1.0) * pk;
+        double q = sqrt(A / (p + B));
+        *f = (p - pk) * q;
+        *df = q * (1.0 - 0.5 * (p - pk) / (B + p));
+    } else { /* rarefaction */
+        double e = (gamma - 1.0) / (2.0 * gamma);
+        *f = 2.0 * ck / (gamma - 1.0) * (pow(p / pk, e) - 1.0);
+        *df = 1.0 / (rk * ck) * pow(p / pk, -(gamma + 1.0) / (2.0 * gamma));
+    }
+}
+
+/* Star pressure and velocity by Newton iteration on f(p) = fL + fR + du. */
+int or_exact_star(double rl, double ul, double pl, double rr, double ur, double pr,
+                  double gamma, double *pstar, double *ustar) {
+    double cl = sqrt(gamma * pl / rl), cr = sqrt(gamma * pr / rr);
+    double p = 0.5 * (pl + pr); /* arithmetic-mean start, always positive */
+    double fl, dfl, fr, dfr;
+    for (int it = 0; it < 200; it++) {
+        pressure_fn(p, rl, pl, cl, gamma, &fl, &dfl);
+        pressure_fn(p, rr, pr, cr, gamma, &fr, &dfr);
+        double pn = p - (fl + fr + (ur - ul)) / (dfl + dfr);
+        if (pn <= 0.0) pn = 1e-14 * p;
+        double change = 2.0 * fabs(pn - p) / (pn + p);
+        p = pn;
+        if (change < 1e-15) break;
+    }
+    pressure_fn(p, rl, pl, cl, gamma, &fl, &dfl);
+    pressure_fn(p, rr, pr, cr, gamma, &fr, &dfr);
+    *pstar = p;
+    *ustar = 0.5 * (ul + ur) + 0.5 * (fr - fl);
+    return 0;
+}
+
+/* Star pressure by bisection (independent check of the Newton result). */
+double or_exact_pstar_bisect(double rl, double ul, double pl, double rr, double ur,
+                             double pr, double gamma) {
+    double cl = sqrt(gamma * pl / rl), cr = sqrt(gamma * pr / rr);
+    double lo = 1e-12, hi = 100.0 * (pl > pr ? pl : pr);
+    double fl, d, fr;
+    for (int it = 0; it < 400; it++) {
+        double mid = 0.5 * (lo + hi);
+        pressure_fn(mid, rl, pl, cl, gamma, &fl, &d);
+        pressure_fn(mid, rr, pr, cr, gamma, &fr, &d);
+        if (fl + fr + (ur - ul) > 0.0) hi = mid; else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* Sample the exact solution at similarity coordinates xi = x/t. */
+void or_exact_sample(double rl, double ul, double pl, double rr, double ur, double pr,
+                     double gamma, const double *xi, int n, double *rho, double *u,
+                     double *p) {
+    double ps, us;
+    or_exact_star(rl, ul, pl, rr, ur, pr, gamma, &ps, &us);
+    double cl = sqrt(gamma * pl / rl), cr = sqrt(gamma * pr / rr);
+    double g1 = (gamma - 1.0) / (gamma + 1.0);
+    for (int i = 0; i < n; i++) {
+        double s = xi[i], r, v, q;
+        if (s <= us) { /* left of the contact */
+            if (ps > pl) { /* left shock */
+                double SL = ul - cl * sqrt((gamma + 1.0) / (2.0 * gamma) * ps / pl +
+                                           (gamma - 1.0) / (2.0 * gamma));
+                if (s <= SL) { r = rl; v = ul; q = pl; }
+                else { r = rl * (ps / pl + g1) / (g1 * ps / pl + 1.0); v = us; q = ps; }
+            } else { /* left rarefaction */
+                double cs = cl * pow(ps / pl, (gamma - 1.0) / (2.0 * gamma));
+                double head = ul - cl, tail = us - cs;
+                if (s <= head) { r = rl; v = ul; q = pl; }
+                else if (s >= tail) { r = rl * pow(ps / pl, 1.0 / gamma); v = us; q = ps; }
+                else {
+                    double k = 2.0 / (gamma + 1.0) + g1 / cl * (ul - s);
+                    r = rl * pow(k, 2.0 / (gamma - 1.0));
+                    v = 2.0 / (gamma + 1.0) * (cl + (gamma - 1.0) / 2.0 * ul + s);
+                    q = pl * pow(k, 2.0 * gamma / (gamma - 1.0));
+                }
+            }
+        } else { /* right of the contact */
+            if (ps > pr) { /* right shock */
+                double SR = ur + cr * sqrt((gamma + 1.0) / (2.0 * gamma) * ps / pr +
+                                           (gamma - 1.0) / (2.0 * gamma));
+                if (s >= SR) { r = rr; v = ur; q = pr; }
+                else { r = rr * (ps / pr + g1) / (g1 * ps / pr + 1.0); v = us; q = ps; }
+            } else { /* right rarefaction */
+                double cs = cr * pow(ps / pr, (gamma - 1.0) / (2.0 * gamma));
+                double head = ur + cr, tail = us + cs;
+                if (s >= head) { r = rr; v = ur; q = pr; }
+                else if (s <= tail) { r = rr * pow(ps / pr, 1.0 / gamma); v = us; q = ps; }
+                else {
+                    double k = 2.0 / (gamma + 1.0) - g1 / cr * (ur - s);
+                    r = rr * pow(k, 2.0 / (gamma - 1.0));
+                    v = 2.0 / (gamma + 1.0) * (-cr + (gamma - 1.0) / 2.0 * ur + s);
+                    q = pr * pow(k, 2.0 * gamma / (gamma - 1.0));
+                }
+            }
+        }
+        rho[i] = r;
+        u[i] = v;
+        p[i] = q;
+    }
+}
