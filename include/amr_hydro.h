@@ -1,0 +1,217 @@
+/*
+ * amr_hydro.h -- C ABI of the B300-native GAMER-2 patch-group hydro update.
+ *
+ * The method (GAMER-2, Schive et al. 2018):
+ *   - section 2.1: block-structured AMR of fixed 8^3-cell patches, refinement
+ *     ratio 2, a patch has 0 or 8 children and up to 26 siblings; patch
+ *     groups of 2x2x2 sibling patches are the unit of hydro work (section
+ *     3.1); adaptive per-level time steps advanced as a W-cycle.
+ *   - section 2.2: MUSCL-Hancock (MHM) with PLM on primitive variables, a
+ *     van Leer-type limiter and the HLLC Riemann solver; after a coarse
+ *     level synchronises with its child level, restriction (volume-weighted
+ *     average of the children) and the coarse-fine flux fix-up.
+ *   - section 2.6: time step of Eq. (CFL2),
+ *     dt = C_CFL dh / max(|vx|+|vy|+|vz|+3 c_s).
+ *
+ * Conventions for every entry point:
+ *   - Ownership: the caller owns every state and table array; the library
+ *     borrows raw device pointers and never frees them.  The context owns
+ *     only its scratch (neighbour plans, interpolated coarse-fine ghost
+ *     patches, coarse-fine flux registers, reduction scalars).
+ *   - Layout of a level's state: U[slot][var][z][y][x] in FP64, 8^3 cells per
+ *     slot, vars (rho, rho vx, rho vy, rho vz, E), x fastest.  Patch group g
+ *     owns slots 8g..8g+7 in local order x fastest, then y, then z.
+ *   - Streams: every call is asynchronous on the context's CUDA stream unless
+ *     it returns a host value (min_dt to a host pointer, conserved_sum,
+ *     advance_level with a non-NULL n_unphysical_out), which synchronises
+ *     that stream.
+ *   - Errors: every call returns an amr_status; kernels never trap.  Invalid
+ *     arguments are rejected before any launch.
+ *   - Threading: a context is used by one host thread at a time.
+ */
+#ifndef AMR_HYDRO_H
+#define AMR_HYDRO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AMR_OK = 0,
+    AMR_E_INVAL = 1,      /* bad argument (null pointer, size, level, ...) */
+    AMR_E_NOMEM = 2,      /* device or host allocation failed */
+    AMR_E_CUDA = 3,       /* a CUDA runtime call failed */
+    AMR_E_UNPHYSICAL = 4, /* rho<=0 or P<=0 in the updated state */
+    AMR_E_TIMEOUT = 5,    /* a bounded device wait ran out */
+    AMR_E_NESTING = 6     /* the hierarchy violates proper nesting */
+} amr_status;
+
+typedef enum {
+    AMR_FP64 = 0,       /* every step of the update in IEEE FP64 */
+    AMR_FP32_ACC64 = 1  /* reconstruction, Hancock step and HLLC in FP32;
+                           conserved-variable accumulation, flux fix-up,
+                           dt and conservation reductions in FP64 */
+} amr_precision;
+
+/* Run parameters (section 2.1 and 2.6 symbols). */
+typedef struct {
+    double gamma;        /* adiabatic index */
+    double cfl;          /* C_CFL of Eq. (CFL2) */
+    double c_inc, c_dec; /* dt increase / decrease fractions of section 2.1 */
+    double theta;        /* refinement threshold (normalised density gradient) */
+    int lmax;            /* maximum refinement level (0..7) */
+    int nbuf[8];         /* flag-buffer width N_buf per level (section 2.1) */
+    int prec;            /* amr_precision */
+    int periodic[3];     /* 1 = periodic along x, y, z (only periodic is built) */
+    double box[3];       /* domain edge lengths; cells are cubic */
+    int root_n[3];       /* root-level cells per dimension, multiples of 16 */
+    int max_patches;     /* slot capacity per level, a multiple of 8 */
+} amr_hydro_params;
+
+typedef struct amr_hydro_ctx amr_hydro_ctx; /* opaque, library-owned */
+
+/* Create a context bound to the current CUDA device and to cuda_stream
+ * (a cudaStream_t, NULL for the legacy default stream).  Rejects gamma<=1,
+ * cfl<=0, lmax outside 0..7, root_n not a positive multiple of 16,
+ * max_patches not a positive multiple of 8, non-periodic boundaries. */
+amr_status amr_hydro_init(const amr_hydro_params *params, void *cuda_stream,
+                          amr_hydro_ctx **out);
+
+/* Free the context's scratch; caller-owned arrays are untouched. */
+amr_status amr_hydro_destroy(amr_hydro_ctx *ctx);
+
+/*
+ * Register the device arrays of one AMR level (section 2.1).
+ *   n_patches       number of patches, a multiple of 8 (whole groups), <= max_patches
+ *   U_a, U_b        two FP64 state buffers [n_patches][5][8][8][8]; U_a holds the
+ *                   current state on entry, U_b receives the next time level
+ *   corner          int32 [n_patches][3]: lower-corner cell index (x,y,z) of each
+ *                   patch in level-l cell units
+ *   sib             int32 [n_patches][26]: slot of the sibling in direction
+ *                   (dx,dy,dz) in {-1,0,1}^3 \ {0}, at index k - (k > 13) with
+ *                   k = (dx+1) + 3(dy+1) + 9(dz+1); -1 when that sibling is absent
+ *   parent          int32 [n_patches]: parent slot on level l-1 (-1 on level 0)
+ *   child_group     int32 [n_patches]: group index on level l+1 of the 8 children,
+ *                   -1 for a leaf patch
+ * The tables are read once here (device to host) to build the context's
+ * neighbour plan; call set_level again after any regrid.  The level's time is
+ * set to t.  Errors: AMR_E_INVAL on bad sizes or a table entry out of range,
+ * AMR_E_NESTING when a coarse-fine ghost patch has no covering coarse patch.
+ */
+amr_status amr_hydro_set_level(amr_hydro_ctx *ctx, int level, int n_patches,
+                               double *U_a, double *U_b, const int32_t *corner,
+                               const int32_t *sib, const int32_t *parent,
+                               const int32_t *child_group, double t);
+
+/* Report which registered buffer holds the level's newest state (0 = U_a,
+ * 1 = U_b) and the times of the newest and previous states. */
+amr_status amr_hydro_get_state(amr_hydro_ctx *ctx, int level, int *cur_buffer,
+                               double *t_cur, double *t_prev);
+
+/*
+ * Fill the coarse-fine ghost patches of `level` (>0) at time t by linear
+ * interpolation in time between the coarse level's previous and newest
+ * states, then conservative minmod-limited linear interpolation in space
+ * (section 3.2: ghost zones are filled from siblings, or by interpolation
+ * from coarse patches).  advance_level calls this itself; it is exposed for
+ * tests.  t must lie in [t_prev, t_cur] of level-1.
+ */
+amr_status amr_hydro_fill_ghost(amr_hydro_ctx *ctx, int level, double t);
+
+/*
+ * Advance every patch group of `level` by one MUSCL-Hancock step of size dt
+ * (section 2.2): gather the 20^3 ghosted tile, PLM + van Leer limiter,
+ * Hancock half step, HLLC at every face, conservative update into the other
+ * buffer, coarse-fine flux registers, and the CFL reduction of the new
+ * state (fused).  dt < 0 means: use the device-side dt of Eq. (CFL2) from the
+ * latest reduction (no host synchronisation).  If n_unphysical_out is not
+ * NULL the call synchronises and stores the number of updated cells with
+ * rho<=0 or P<=0, returning AMR_E_UNPHYSICAL when it is not zero.
+ */
+amr_status amr_hydro_advance_level(amr_hydro_ctx *ctx, int level, double dt,
+                                   int64_t *n_unphysical_out);
+
+/*
+ * Synchronise coarse_level with coarse_level+1 (section 2.2): coarse leaf
+ * cells next to a coarse-fine interface get
+ * U_c -= (sum dt_f <F_f> - dt_c F_c)/dh_c across their high faces (+= across
+ * low faces), then every non-leaf coarse cell becomes the mean of its 8
+ * children.  Fine fluxes are summed in a fixed order: bitwise reproducible.
+ */
+amr_status amr_hydro_flux_fixup(amr_hydro_ctx *ctx, int coarse_level);
+
+/*
+ * Time step of Eq. (CFL2) on `level`: C_CFL dh / max over the level's cells
+ * of (|vx|+|vy|+|vz|+3 c_s).  dt_out may be a host pointer (the call
+ * synchronises) or a device pointer (asynchronous).  Returns AMR_E_UNPHYSICAL
+ * (dt_out = -1) if a cell has rho<=0 or P<=0.
+ */
+amr_status amr_hydro_min_dt(amr_hydro_ctx *ctx, int level, double *dt_out);
+
+/*
+ * Refinement flags of `level` (section 2.1): a cell is flagged when its
+ * normalised density gradient exceeds theta, i.e.
+ * sum_d ((rho_{+d} - rho_{-d})/2)^2 > theta^2 rho^2; a patch is flagged when
+ * any of its cells is.  patch_flags_dev: device uint8 [n_patches].
+ */
+amr_status amr_hydro_regrid_flags(amr_hydro_ctx *ctx, int level, uint8_t *patch_flags_dev);
+
+/* Sum over the level's leaf cells of U dV per variable, FP64, fixed-order
+ * tree (deterministic).  out: host double[5].  Synchronises. */
+amr_status amr_hydro_conserved_sum(amr_hydro_ctx *ctx, int level, double *out);
+
+/*
+ * Independent periodic boxes advanced together (section 4.2 runs many
+ * independent periodic domains, one per node; here they share one GPU).
+ * set_box registers box `box_id` (< 256): a uniform periodic cube of n^3 cells
+ * (n a multiple of 16, edge length 1, so dh = 1/n) with two caller-owned
+ * state buffers in the patch layout above (uniform slot order of
+ * amr_hydro_uniform_tables).  advance_boxes runs n_steps steps of every listed
+ * box with a per-box dt of Eq. (CFL2) evaluated on the device, as one
+ * persistent launch per step over all groups of all boxes; the steps are
+ * captured once into a CUDA graph and replayed.  dt_log (device, may be NULL)
+ * receives [n_steps][n_boxes] FP64 time steps.
+ */
+amr_status amr_hydro_set_box(amr_hydro_ctx *ctx, int box_id, int n, double *U_a, double *U_b);
+amr_status amr_hydro_advance_boxes(amr_hydro_ctx *ctx, int n_boxes, const int *box_ids,
+                                   int n_steps, double *dt_log);
+amr_status amr_hydro_box_state(amr_hydro_ctx *ctx, int box_id, int *cur_buffer);
+
+/*
+ * Discrete adjoint of one uniform periodic MUSCL-Hancock step of size dt (no
+ * counterpart in the paper; the reverse of section 2.2's update with dt held
+ * fixed): lam_n = (dU^{n+1}/dU^n)^T lam_np1.  U_n, lam_np1, lam_n: device FP64
+ * arrays in the level's patch layout.  At kinks the derivative of the branch
+ * taken by the forward evaluation is used.
+ */
+amr_status amr_hydro_step_adjoint(amr_hydro_ctx *ctx, int level, double dt, const double *U_n,
+                                  const double *lam_np1, double *lam_n);
+
+const char *amr_hydro_strerror(amr_status s);
+
+/* ---- host-side helpers (no device work) ---------------------------------- */
+
+/*
+ * Tables of a level fully covered by patches: np[d] patches per dimension
+ * (each even), periodic wrap.  Slot order: group g = gx + ngx (gy + ngy gz)
+ * with ng = np/2, slot = 8g + px + 2py + 4pz.  Host arrays sized as in
+ * amr_hydro_set_level; parent/child_group are filled with -1.
+ */
+amr_status amr_hydro_uniform_tables(const int np[3], int32_t *corner, int32_t *sib,
+                                    int32_t *parent, int32_t *child_group);
+
+/* ---- device-side layout helpers ------------------------------------------ */
+
+/* Dense [5][nz][ny][nx] <-> patch layout of amr_hydro_uniform_tables, on
+ * cuda_stream.  n{x,y,z} multiples of 16. */
+amr_status amr_hydro_pack_uniform(const double *dense, int nx, int ny, int nz, double *patches,
+                                  void *cuda_stream);
+amr_status amr_hydro_unpack_uniform(const double *patches, int nx, int ny, int nz, double *dense,
+                                    void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMR_HYDRO_H */

@@ -1,0 +1,315 @@
+// amr_hydro.cu -- C ABI of the B300-native GAMER-2 patch-group hydro update:
+// context, per-level neighbour plans, launches.  The ABI is declared and
+// documented in include/amr_hydro.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "amr_hydro.h"
+#include "ctx.h"
+#include "step_kernel.cuh"
+
+using namespace amrh;
+
+namespace amrh {
+
+const char *status_str(amr_status s) {
+    switch (s) {
+        case AMR_OK: return "ok";
+        case AMR_E_INVAL: return "invalid argument";
+        case AMR_E_NOMEM: return "out of memory";
+        case AMR_E_CUDA: return "CUDA error";
+        case AMR_E_UNPHYSICAL: return "unphysical state (rho<=0 or P<=0)";
+        case AMR_E_TIMEOUT: return "bounded device wait timed out";
+        case AMR_E_NESTING: return "proper-nesting violation";
+    }
+    return "unknown status";
+}
+
+amr_status cuda_fail(cudaError_t e, const char *where) {
+    if (e == cudaSuccess) return AMR_OK;
+    std::fprintf(stderr, "amr_hydro: %s: %s\n", where, cudaGetErrorString(e));
+    return AMR_E_CUDA;
+}
+
+template <typename T>
+amr_status DevBuf<T>::reserve(size_t n) {
+    if (n <= cap) return AMR_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    if (cudaMalloc(&p, sizeof(T) * n) != cudaSuccess) {
+        cudaGetLastError();
+        return AMR_E_NOMEM;
+    }
+    cap = n;
+    return AMR_OK;
+}
+template <typename T>
+void DevBuf<T>::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+}
+template struct DevBuf<int32_t>;
+template struct DevBuf<int64_t>;
+template struct DevBuf<double>;
+template struct DevBuf<unsigned long long>;
+
+size_t step_smem_bytes(int prec) {
+    return prec == AMR_FP64 ? sizeof(StepSmem<double>) : sizeof(StepSmem<float>);
+}
+
+amr_status configure_kernels() {
+    static bool done = false;
+    if (done) return AMR_OK;
+    amr_status st = cuda_fail(cudaFuncSetAttribute(k_hydro_step<double>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)sizeof(StepSmem<double>)),
+                              "smem attr fp64");
+    if (st) return st;
+    st = cuda_fail(cudaFuncSetAttribute(k_hydro_step<float>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)sizeof(StepSmem<float>)),
+                   "smem attr fp32");
+    if (st) return st;
+    done = true;
+    return AMR_OK;
+}
+
+// Number of resident step CTAs per SM, for sizing a persistent grid.
+int step_blocks_per_sm(int prec) {
+    int n = 0;
+    if (prec == AMR_FP64)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hydro_step<double>, STEP_THREADS,
+                                                      sizeof(StepSmem<double>));
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hydro_step<float>, STEP_THREADS,
+                                                      sizeof(StepSmem<float>));
+    return n > 0 ? n : 1;
+}
+
+amr_status launch_step(amr_hydro_ctx *c, const StepParams &P, int grid) {
+    if (P.n_work == 0) return AMR_OK;
+    if (c->prm.prec == AMR_FP64)
+        k_hydro_step<double><<<grid, STEP_THREADS, sizeof(StepSmem<double>), c->stream>>>(P);
+    else
+        k_hydro_step<float><<<grid, STEP_THREADS, sizeof(StepSmem<float>), c->stream>>>(P);
+    return cuda_fail(cudaGetLastError(), "k_hydro_step launch");
+}
+
+}  // namespace amrh
+
+// ---------------------------------------------------------------------------
+// reductions and layout kernels
+
+namespace {
+
+template <typename real>
+__global__ void k_max_speed(const double *__restrict__ U, int64_t n_slots, double gamma,
+                            unsigned long long *smax, unsigned long long *n_bad) {
+    Gas<real> g;
+    g.gamma = (real)gamma;
+    g.gm1 = (real)(gamma - 1.0);
+    g.inv_gm1 = (real)(1.0 / (gamma - 1.0));
+    double m = 0.0;
+    unsigned bad = 0;
+    const int64_t ncell = n_slots * PV;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ncell;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = i / PV, c = i % PV;
+        real u[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) u[v] = (real)U[s * PSLOT + v * PV + c];
+        bool ok;
+        const real sp = cfl_speed(u, g, ok);
+        if (!ok) bad++;
+        else if ((double)sp > m) m = (double)sp;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(smax, (unsigned long long)__double_as_longlong(m));
+        if (bad) atomicAdd(n_bad, (unsigned long long)bad);
+    }
+}
+
+__global__ void k_dt_from_speed(const unsigned long long *smax, const unsigned long long *n_bad,
+                                double cfl, double dh, double *dt_out) {
+    const double s = __longlong_as_double((long long)*smax);
+    *dt_out = (*n_bad || !(s > 0.0)) ? -1.0 : cfl * dh / s;
+}
+
+// dense [5][nz][ny][nx] <-> uniform patch layout
+__global__ void k_pack(double *__restrict__ dense, int nx, int ny, int nz,
+                       double *__restrict__ patches, int to_patches) {
+    const int64_t n = (int64_t)nx * ny * nz;
+    const int ngx = nx / 16, ngy = ny / 16;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
+        const int64_t g = (x >> 4) + ngx * ((int64_t)(y >> 4) + (int64_t)ngy * (z >> 4));
+        const int64_t slot = 8 * g + ((x >> 3) & 1) + 2 * ((y >> 3) & 1) + 4 * ((z >> 3) & 1);
+        const int64_t off = slot * PSLOT + (z & 7) * 64 + (y & 7) * 8 + (x & 7);
+        for (int v = 0; v < NV; v++) {
+            if (to_patches) patches[off + v * PV] = dense[v * n + i];
+            else dense[v * n + i] = patches[off + v * PV];
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// ABI
+
+extern "C" {
+
+const char *amr_hydro_strerror(amr_status s) { return status_str(s); }
+
+amr_status amr_hydro_init(const amr_hydro_params *p, void *stream, amr_hydro_ctx **out) {
+    if (!p || !out) return AMR_E_INVAL;
+    *out = nullptr;
+    if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || p->lmax < 0 || p->lmax > 7) return AMR_E_INVAL;
+    if (p->prec != AMR_FP64 && p->prec != AMR_FP32_ACC64) return AMR_E_INVAL;
+    if (p->max_patches <= 0 || p->max_patches % 8) return AMR_E_INVAL;
+    for (int d = 0; d < 3; d++) {
+        if (p->root_n[d] <= 0 || p->root_n[d] % 16) return AMR_E_INVAL;
+        if (!p->periodic[d]) return AMR_E_INVAL;
+        if (!(p->box[d] > 0.0)) return AMR_E_INVAL;
+    }
+    // cubic cells
+    const double dh0 = p->box[0] / p->root_n[0];
+    for (int d = 1; d < 3; d++)
+        if (std::fabs(p->box[d] / p->root_n[d] - dh0) > 1e-12 * dh0) return AMR_E_INVAL;
+    amr_status st = configure_kernels();
+    if (st) return st;
+    amr_hydro_ctx *c = new (std::nothrow) amr_hydro_ctx();
+    if (!c) return AMR_E_NOMEM;
+    c->prm = *p;
+    c->stream = (cudaStream_t)stream;
+    cudaGetDevice(&c->device);
+    cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
+    c->step_bps = step_blocks_per_sm(p->prec);
+    if ((st = c->scal.reserve(SCAL_N))) { amr_hydro_destroy(c); return st; }
+    if ((st = c->dtbuf.reserve(MAX_LEVELS + MAX_BOXES))) { amr_hydro_destroy(c); return st; }
+    if ((st = cuda_fail(cudaMemsetAsync(c->scal.p, 0, sizeof(unsigned long long) * SCAL_N, c->stream),
+                        "memset"))) {
+        amr_hydro_destroy(c);
+        return st;
+    }
+    *out = c;
+    return AMR_OK;
+}
+
+amr_status amr_hydro_destroy(amr_hydro_ctx *c) {
+    if (!c) return AMR_E_INVAL;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    for (auto &L : c->lv) L.release();
+    for (auto &B : c->boxes) B.release();
+    c->box_plan.release();
+    c->scal.release();
+    c->dtbuf.release();
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    delete c;
+    return AMR_OK;
+}
+
+amr_status amr_hydro_get_state(amr_hydro_ctx *c, int level, int *cur, double *t_cur, double *t_prev) {
+    if (!c || level < 0 || level > c->prm.lmax) return AMR_E_INVAL;
+    const Level &L = c->lv[level];
+    if (!L.n_patches) return AMR_E_INVAL;
+    amr_status st = level_time(c, level);
+    if (st) return st;
+    if (cur) *cur = L.cur;
+    if (t_cur) *t_cur = L.t;
+    if (t_prev) *t_prev = L.t_prev;
+    return AMR_OK;
+}
+
+amr_status amr_hydro_min_dt(amr_hydro_ctx *c, int level, double *dt_out) {
+    if (!c || !dt_out || level < 0 || level > c->prm.lmax) return AMR_E_INVAL;
+    Level &L = c->lv[level];
+    if (!L.n_patches) return AMR_E_INVAL;
+    amr_status st = level_speed(c, level);
+    if (st) return st;
+    unsigned long long *sm = c->scal.p + L.smax_idx, *nb = c->scal.p + L.nbad_idx;
+    cudaPointerAttributes a;
+    const bool dev = cudaPointerGetAttributes(&a, dt_out) == cudaSuccess &&
+                     (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    const double dh = level_dh(c, level);
+    if (dev) {
+        k_dt_from_speed<<<1, 1, 0, c->stream>>>(sm, nb, c->prm.cfl, dh, dt_out);
+        return cuda_fail(cudaGetLastError(), "k_dt_from_speed");
+    }
+    unsigned long long h[2];
+    if ((st = cuda_fail(cudaMemcpyAsync(&h[0], sm, 8, cudaMemcpyDeviceToHost, c->stream), "d2h")))
+        return st;
+    if ((st = cuda_fail(cudaMemcpyAsync(&h[1], nb, 8, cudaMemcpyDeviceToHost, c->stream), "d2h")))
+        return st;
+    if ((st = cuda_fail(cudaStreamSynchronize(c->stream), "sync"))) return st;
+    double s;
+    std::memcpy(&s, &h[0], 8);
+    if (h[1] || !(s > 0.0)) {
+        *dt_out = -1.0;
+        return AMR_E_UNPHYSICAL;
+    }
+    *dt_out = c->prm.cfl * dh / s;
+    return AMR_OK;
+}
+
+amr_status amr_hydro_pack_uniform(const double *dense, int nx, int ny, int nz, double *patches,
+                                  void *stream) {
+    if (!dense || !patches || nx <= 0 || ny <= 0 || nz <= 0 || nx % 16 || ny % 16 || nz % 16)
+        return AMR_E_INVAL;
+    k_pack<<<1184, 256, 0, (cudaStream_t)stream>>>(const_cast<double *>(dense), nx, ny, nz, patches, 1);
+    return cuda_fail(cudaGetLastError(), "k_pack");
+}
+
+amr_status amr_hydro_unpack_uniform(const double *patches, int nx, int ny, int nz, double *dense,
+                                    void *stream) {
+    if (!dense || !patches || nx <= 0 || ny <= 0 || nz <= 0 || nx % 16 || ny % 16 || nz % 16)
+        return AMR_E_INVAL;
+    k_pack<<<1184, 256, 0, (cudaStream_t)stream>>>(const_cast<double *>(dense), nx, ny, nz,
+                                                    const_cast<double *>(patches), 0);
+    return cuda_fail(cudaGetLastError(), "k_unpack");
+}
+
+}  // extern "C"
+
+namespace amrh {
+
+double level_dh(const amr_hydro_ctx *c, int level) {
+    return c->prm.box[0] / c->prm.root_n[0] / (double)(1 << level);
+}
+
+// Max signal speed of the level's newest state into its scalar slots (reuses
+// the value fused into the last step when the state has not changed since).
+amr_status level_speed(amr_hydro_ctx *c, int level) {
+    Level &L = c->lv[level];
+    if (L.speed_valid) return AMR_OK;
+    unsigned long long *sm = c->scal.p + L.smax_idx, *nb = c->scal.p + L.nbad_idx;
+    amr_status st = cuda_fail(cudaMemsetAsync(sm, 0, 8, c->stream), "memset");
+    if (st) return st;
+    if ((st = cuda_fail(cudaMemsetAsync(nb, 0, 8, c->stream), "memset"))) return st;
+    const int grid = c->n_sm * 8;
+    if (c->prm.prec == AMR_FP64)
+        k_max_speed<double><<<grid, 256, 0, c->stream>>>(L.U[L.cur], L.n_patches, c->prm.gamma, sm, nb);
+    else
+        k_max_speed<float><<<grid, 256, 0, c->stream>>>(L.U[L.cur], L.n_patches, c->prm.gamma, sm, nb);
+    if ((st = cuda_fail(cudaGetLastError(), "k_max_speed"))) return st;
+    L.speed_valid = true;
+    return AMR_OK;
+}
+
+}  // namespace amrh

@@ -1,0 +1,108 @@
+// ctx.h -- library-internal state behind the opaque amr_hydro_ctx.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "amr_hydro.h"
+
+namespace amrh {
+
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t cap = 0;
+    amr_status reserve(size_t n);
+    void release();
+};
+
+constexpr int MAX_LEVELS = 8;
+constexpr int MAX_BOXES = 256;
+// scalar slots (unsigned 64-bit) in ctx->scal: per level 4, per box 4
+constexpr int SCAL_LEVEL0 = 0;
+constexpr int SCAL_BOX0 = 4 * MAX_LEVELS;
+constexpr int SCAL_N = SCAL_BOX0 + 4 * MAX_BOXES;
+
+// One coarse-fine ghost patch of a level: its 8^3 cells are interpolated from
+// the coarse level around the parent patch `cparent` of the group that needs it.
+struct GhostInfo {
+    int32_t cparent;  // coarse slot of the neighbouring group's parent
+    int32_t qx, qy, qz;  // patch position relative to that group (-1..2)
+};
+
+struct Level {
+    int n_patches = 0, n_groups = 0;
+    double *U[2] = {nullptr, nullptr};
+    int cur = 0;
+    double t = 0.0, t_prev = 0.0;
+    bool t_pending = false;  // t awaits a device-side dt
+    const int32_t *d_corner = nullptr, *d_sib = nullptr, *d_parent = nullptr, *d_child = nullptr;
+    std::vector<int32_t> corner, sib, parent, child;  // host mirrors
+    DevBuf<int32_t> nbr;        // [n_groups][64]
+    DevBuf<double> ghost;       // [n_ghost][5][512]
+    DevBuf<int32_t> ghost_info; // [n_ghost][4]
+    int n_ghost = 0;
+    // coarse-fine flux registers
+    DevBuf<int64_t> fine_off;    // [n_groups*6]: where this level's groups add fine fluxes
+    DevBuf<int64_t> coarse_off;  // [n_patches*6]: where this level's patches store coarse fluxes
+    DevBuf<double> cf_coarse, cf_fine;  // registers owned by this (coarse) level
+    DevBuf<int32_t> fix_list;    // [n_fix][2] (slot, face) pairs of this level to fix up
+    int n_fix = 0;
+    int n_cf_regs = 0;
+    bool has_fine_regs = false, has_coarse_regs = false;
+    int smax_idx = 0, nbad_idx = 0;
+    bool speed_valid = false;
+    void release() {
+        nbr.release();
+        ghost.release();
+        ghost_info.release();
+        fine_off.release();
+        coarse_off.release();
+        cf_coarse.release();
+        cf_fine.release();
+        fix_list.release();
+        n_patches = n_groups = 0;
+    }
+};
+
+struct Box {
+    int n = 0, n_groups = 0;
+    double *U[2] = {nullptr, nullptr};
+    int cur = 0;
+    DevBuf<int32_t> nbr;
+    void release() { nbr.release(); n = 0; }
+};
+
+}  // namespace amrh
+
+struct amr_hydro_ctx {
+    amr_hydro_params prm;
+    cudaStream_t stream = nullptr;
+    int device = 0, n_sm = 148, step_bps = 1;
+    amrh::Level lv[amrh::MAX_LEVELS];
+    amrh::Box boxes[amrh::MAX_BOXES];
+    amrh::DevBuf<unsigned long long> scal;
+    amrh::DevBuf<double> dtbuf;
+    // batched-box launch plan and its captured graph
+    amrh::DevBuf<int32_t> box_plan;
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<int> graph_key;
+};
+
+namespace amrh {
+const char *status_str(amr_status s);
+amr_status cuda_fail(cudaError_t e, const char *where);
+double level_dh(const amr_hydro_ctx *c, int level);
+amr_status level_speed(amr_hydro_ctx *c, int level);
+size_t step_smem_bytes(int prec);
+struct StepParams;
+amr_status launch_step(amr_hydro_ctx *c, const StepParams &P, int grid);
+amr_status level_time(amr_hydro_ctx *c, int level);
+// host planning (host_plan.cpp)
+amr_status build_uniform_tables(const int np[3], int32_t *corner, int32_t *sib, int32_t *parent,
+                                int32_t *child);
+amr_status build_nbr_plan(int level, int n_patches, const int32_t *corner, const int32_t *sib,
+                          const int32_t *parent, const int level_cells[3],
+                          std::vector<int32_t> &nbr, std::vector<GhostInfo> &ghosts);
+}  // namespace amrh

@@ -1,0 +1,122 @@
+// host_plan.cpp -- host-side planning of a level's patch-group gathers
+// (GAMER-2 section 2.1: octree of 8^3 patches storing parent, child and 26
+// sibling ids; section 3.1: patch groups of 8 siblings are the unit of work).
+#include <cstdint>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "ctx.h"
+
+namespace amrh {
+
+static inline int wrapi(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+static inline int sib_index(int dx, int dy, int dz) {
+    const int k = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+    return k - (k > 13);
+}
+
+amr_status build_uniform_tables(const int np[3], int32_t *corner, int32_t *sib, int32_t *parent,
+                                int32_t *child) {
+    for (int d = 0; d < 3; d++)
+        if (np[d] <= 0 || np[d] % 2) return AMR_E_INVAL;
+    const int ng[3] = {np[0] / 2, np[1] / 2, np[2] / 2};
+    auto slot_of = [&](int px, int py, int pz) -> int32_t {
+        px = wrapi(px, np[0]);
+        py = wrapi(py, np[1]);
+        pz = wrapi(pz, np[2]);
+        const int64_t g = (px >> 1) + (int64_t)ng[0] * ((py >> 1) + (int64_t)ng[1] * (pz >> 1));
+        return (int32_t)(8 * g + (px & 1) + 2 * (py & 1) + 4 * (pz & 1));
+    };
+    for (int pz = 0; pz < np[2]; pz++)
+        for (int py = 0; py < np[1]; py++)
+            for (int px = 0; px < np[0]; px++) {
+                const int32_t s = slot_of(px, py, pz);
+                corner[3 * s + 0] = 8 * px;
+                corner[3 * s + 1] = 8 * py;
+                corner[3 * s + 2] = 8 * pz;
+                if (parent) parent[s] = -1;
+                if (child) child[s] = -1;
+                for (int dz = -1; dz <= 1; dz++)
+                    for (int dy = -1; dy <= 1; dy++)
+                        for (int dx = -1; dx <= 1; dx++) {
+                            if (!dx && !dy && !dz) continue;
+                            sib[26 * (int64_t)s + sib_index(dx, dy, dz)] = slot_of(px + dx, py + dy, pz + dz);
+                        }
+            }
+    return AMR_OK;
+}
+
+// For every group, the source of each of the 4x4x4 patch positions around
+// it (position q in {-1,0,1,2}^3, index (qx+1) + 4(qy+1) + 16(qz+1)):
+//   >= 0   a same-level slot,
+//   <= -2  coarse-fine ghost patch number (-2 - value), to be interpolated,
+//   -1     a corner position, which no stencil of the step reads.
+// Fails with AMR_E_NESTING when a face or edge neighbour is missing on the
+// root level (nothing to interpolate from).
+amr_status build_nbr_plan(int level, int n_patches, const int32_t *corner, const int32_t *sib,
+                          const int32_t *parent, const int level_cells[3],
+                          std::vector<int32_t> &nbr, std::vector<GhostInfo> &ghosts) {
+    const int n_groups = n_patches / 8;
+    nbr.assign((size_t)n_groups * 64, -1);
+    ghosts.clear();
+    std::map<std::tuple<int, int, int>, int> ghost_id;
+    for (int g = 0; g < n_groups; g++) {
+        for (int qz = -1; qz <= 2; qz++)
+            for (int qy = -1; qy <= 2; qy++)
+                for (int qx = -1; qx <= 2; qx++) {
+                    const int pos = (qx + 1) + 4 * (qy + 1) + 16 * (qz + 1);
+                    const int px = qx < 0 ? 0 : (qx > 1 ? 1 : qx);
+                    const int py = qy < 0 ? 0 : (qy > 1 ? 1 : qy);
+                    const int pz = qz < 0 ? 0 : (qz > 1 ? 1 : qz);
+                    const int own = 8 * g + px + 2 * py + 4 * pz;
+                    const int dx = qx - px, dy = qy - py, dz = qz - pz;
+                    if (!dx && !dy && !dz) {
+                        nbr[(size_t)g * 64 + pos] = own;
+                        continue;
+                    }
+                    const int32_t s = sib[26 * (int64_t)own + sib_index(dx, dy, dz)];
+                    if (s >= n_patches || s < -1) return AMR_E_INVAL;
+                    if (s >= 0) {
+                        nbr[(size_t)g * 64 + pos] = s;
+                        continue;
+                    }
+                    const int outer = (dx != 0) + (dy != 0) + (dz != 0);
+                    if (outer == 3) continue;  // corner: never read
+                    if (level == 0 || !parent) return AMR_E_NESTING;
+                    const int cx = wrapi(corner[3 * own + 0] + 8 * dx, level_cells[0]);
+                    const int cy = wrapi(corner[3 * own + 1] + 8 * dy, level_cells[1]);
+                    const int cz = wrapi(corner[3 * own + 2] + 8 * dz, level_cells[2]);
+                    auto key = std::make_tuple(cx, cy, cz);
+                    auto it = ghost_id.find(key);
+                    int id;
+                    if (it == ghost_id.end()) {
+                        id = (int)ghosts.size();
+                        ghost_id[key] = id;
+                        GhostInfo gi;
+                        gi.cparent = parent[8 * g];
+                        gi.qx = qx;
+                        gi.qy = qy;
+                        gi.qz = qz;
+                        if (gi.cparent < 0) return AMR_E_NESTING;
+                        ghosts.push_back(gi);
+                    } else {
+                        id = it->second;
+                    }
+                    nbr[(size_t)g * 64 + pos] = -2 - id;
+                }
+    }
+    return AMR_OK;
+}
+
+}  // namespace amrh
+
+extern "C" amr_status amr_hydro_uniform_tables(const int np[3], int32_t *corner, int32_t *sib,
+                                               int32_t *parent, int32_t *child_group) {
+    if (!np || !corner || !sib) return AMR_E_INVAL;
+    return amrh::build_uniform_tables(np, corner, sib, parent, child_group);
+}

@@ -1,0 +1,160 @@
+// level.cu -- per-level entry points: registration of a level's arrays and
+// the advance of all its patch groups by one step (GAMER-2 sections 2.1-2.2).
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <vector>
+
+#include "amr_hydro.h"
+#include "ctx.h"
+#include "step_kernel.cuh"
+
+using namespace amrh;
+
+namespace amrh {
+
+// Bring a level's host-side time up to date after device-side time steps.
+static amr_status sync_level_time(amr_hydro_ctx *c, Level &L, int level) {
+    if (!L.t_pending) return AMR_OK;
+    double dt;
+    amr_status st = cuda_fail(cudaMemcpyAsync(&dt, c->dtbuf.p + level, 8, cudaMemcpyDeviceToHost,
+                                              c->stream), "d2h dt");
+    if (st) return st;
+    if ((st = cuda_fail(cudaStreamSynchronize(c->stream), "sync"))) return st;
+    L.t = L.t_prev + dt;
+    L.t_pending = false;
+    return AMR_OK;
+}
+
+amr_status fill_ghost_impl(amr_hydro_ctx *c, int level, double t);
+
+}  // namespace amrh
+
+extern "C" {
+
+amr_status amr_hydro_set_level(amr_hydro_ctx *c, int level, int n_patches, double *U_a, double *U_b,
+                               const int32_t *corner, const int32_t *sib, const int32_t *parent,
+                               const int32_t *child_group, double t) {
+    if (!c || level < 0 || level > c->prm.lmax) return AMR_E_INVAL;
+    if (n_patches < 0 || n_patches % 8 || n_patches > c->prm.max_patches) return AMR_E_INVAL;
+    if (n_patches > 0 && (!U_a || !U_b || !corner || !sib)) return AMR_E_INVAL;
+    if (level > 0 && n_patches > 0 && !parent) return AMR_E_INVAL;
+    Level &L = c->lv[level];
+    amr_status st;
+    if ((st = cuda_fail(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize(), "sync")))
+        return st;
+    L.n_patches = n_patches;
+    L.n_groups = n_patches / 8;
+    L.U[0] = U_a;
+    L.U[1] = U_b;
+    L.cur = 0;
+    L.t = L.t_prev = t;
+    L.t_pending = false;
+    L.d_corner = corner;
+    L.d_sib = sib;
+    L.d_parent = parent;
+    L.d_child = child_group;
+    L.smax_idx = SCAL_LEVEL0 + 4 * level;
+    L.nbad_idx = SCAL_LEVEL0 + 4 * level + 2;
+    L.speed_valid = false;
+    L.n_ghost = 0;
+    if (n_patches == 0) return AMR_OK;
+
+    L.corner.resize((size_t)n_patches * 3);
+    L.sib.resize((size_t)n_patches * 26);
+    L.parent.assign(n_patches, -1);
+    L.child.assign(n_patches, -1);
+    if ((st = cuda_fail(cudaMemcpy(L.corner.data(), corner, 12ull * n_patches, cudaMemcpyDeviceToHost), "d2h")))
+        return st;
+    if ((st = cuda_fail(cudaMemcpy(L.sib.data(), sib, 104ull * n_patches, cudaMemcpyDeviceToHost), "d2h")))
+        return st;
+    if (parent && (st = cuda_fail(cudaMemcpy(L.parent.data(), parent, 4ull * n_patches, cudaMemcpyDeviceToHost), "d2h")))
+        return st;
+    if (child_group && (st = cuda_fail(cudaMemcpy(L.child.data(), child_group, 4ull * n_patches, cudaMemcpyDeviceToHost), "d2h")))
+        return st;
+
+    int cells[3];
+    for (int d = 0; d < 3; d++) cells[d] = c->prm.root_n[d] << level;
+    for (int i = 0; i < 3 * n_patches; i++)
+        if (L.corner[i] < 0 || L.corner[i] >= cells[i % 3] || L.corner[i] % 8) return AMR_E_INVAL;
+    std::vector<int32_t> nbr;
+    std::vector<GhostInfo> ghosts;
+    st = build_nbr_plan(level, n_patches, L.corner.data(), L.sib.data(),
+                        level > 0 ? L.parent.data() : nullptr, cells, nbr, ghosts);
+    if (st) return st;
+    if ((st = L.nbr.reserve(nbr.size()))) return st;
+    if ((st = cuda_fail(cudaMemcpy(L.nbr.p, nbr.data(), 4 * nbr.size(), cudaMemcpyHostToDevice), "h2d")))
+        return st;
+    L.n_ghost = (int)ghosts.size();
+    if (L.n_ghost) {
+        if ((st = L.ghost.reserve((size_t)L.n_ghost * PSLOT))) return st;
+        if ((st = L.ghost_info.reserve((size_t)L.n_ghost * 4))) return st;
+        if ((st = cuda_fail(cudaMemcpy(L.ghost_info.p, ghosts.data(), 16ull * L.n_ghost, cudaMemcpyHostToDevice), "h2d")))
+            return st;
+    }
+    return AMR_OK;
+}
+
+amr_status amr_hydro_advance_level(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphysical_out) {
+    if (!c || level < 0 || level > c->prm.lmax) return AMR_E_INVAL;
+    Level &L = c->lv[level];
+    if (!L.n_patches) return AMR_E_INVAL;
+    if (!(dt >= 0.0) && !(dt < 0.0)) return AMR_E_INVAL;  // NaN
+    amr_status st;
+    if ((st = sync_level_time(c, L, level))) return st;
+    if (L.n_ghost) {
+        if ((st = fill_ghost_impl(c, level, L.t))) return st;
+    }
+    if (dt < 0.0 && (st = level_speed(c, level))) return st;
+    const int out_idx = (L.smax_idx == SCAL_LEVEL0 + 4 * level) ? L.smax_idx + 1 : L.smax_idx - 1;
+    unsigned long long *s_out = c->scal.p + out_idx;
+    if ((st = cuda_fail(cudaMemsetAsync(s_out, 0, 8, c->stream), "memset"))) return st;
+    if ((st = cuda_fail(cudaMemsetAsync(c->scal.p + L.nbad_idx, 0, 8, c->stream), "memset"))) return st;
+
+    StepParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.U_old = L.U[L.cur];
+    P.U_new = L.U[1 - L.cur];
+    P.nbr = L.nbr.p;
+    P.ghost = L.ghost.p;
+    P.work = nullptr;
+    P.n_work = L.n_groups;
+    P.dt = dt;
+    P.smax_in = c->scal.p + L.smax_idx;
+    P.cfl = c->prm.cfl;
+    P.dh = level_dh(c, level);
+    P.gamma = c->prm.gamma;
+    P.smax_out = s_out;
+    P.n_bad = c->scal.p + L.nbad_idx;
+    P.dt_used = c->dtbuf.p + level;
+    P.cf.fine_off = L.has_fine_regs ? L.fine_off.p : nullptr;
+    P.cf.fine_buf = level > 0 ? c->lv[level - 1].cf_fine.p : nullptr;
+    P.cf.coarse_off = L.has_coarse_regs ? L.coarse_off.p : nullptr;
+    P.cf.coarse_buf = L.cf_coarse.p;
+    const int cap = c->n_sm * c->step_bps;
+    const int grid = L.n_groups < cap ? L.n_groups : cap;
+    if ((st = launch_step(c, P, grid))) return st;
+
+    L.cur = 1 - L.cur;
+    L.t_prev = L.t;
+    if (dt >= 0.0) L.t += dt;
+    else L.t_pending = true;
+    L.smax_idx = out_idx;
+    L.speed_valid = true;
+
+    if (n_unphysical_out) {
+        unsigned long long nb = 0;
+        if ((st = cuda_fail(cudaMemcpyAsync(&nb, c->scal.p + L.nbad_idx, 8, cudaMemcpyDeviceToHost, c->stream), "d2h")))
+            return st;
+        if ((st = cuda_fail(cudaStreamSynchronize(c->stream), "sync"))) return st;
+        *n_unphysical_out = (int64_t)nb;
+        if (nb) return AMR_E_UNPHYSICAL;
+    }
+    return AMR_OK;
+}
+
+}  // extern "C"
+
+namespace amrh {
+amr_status level_time(amr_hydro_ctx *c, int level) { return sync_level_time(c, c->lv[level], level); }
+}  // namespace amrh

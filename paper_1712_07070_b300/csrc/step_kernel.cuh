@@ -1,0 +1,314 @@
+// step_kernel.cuh -- the fused per-patch-group MUSCL-Hancock step
+// (GAMER-2 section 2.2 scheme on section 3.1 patch groups; time step of
+// section 2.6 Eq. CFL2 reduced on the fly).
+//
+// One CTA owns one patch group (2x2x2 patches = 16^3 cells) at a time and
+// marches through its 20^3 ghosted tile plane by plane along z:
+//   load   plane z+1 of the tile (gathered from the group's own 8 patches, its
+//          56 same-level neighbours, or interpolated coarse-fine ghost
+//          patches) and convert it to primitives in shared memory
+//          (a ring of three planes);
+//   B      limited slopes + Hancock half step for the cells of plane z whose
+//          face states are needed (16x16 interior + the 64-cell ring of x/y
+//          ghosts); x/y face states go to shared memory, the interior cell's
+//          z face states stay in the owning thread's registers;
+//   C      HLLC on the x and y faces of plane z and on the z face below it;
+//   D      each thread finishes the update of its column's cell at z-1 and
+//          starts the flux divergence of the cell at z.
+// The 20^3 tile never exists in global memory (section 3.4: ghost zones are
+// only allocated temporarily).
+#pragma once
+#include "hydro_math.cuh"
+
+namespace amrh {
+
+constexpr int PS = 8;                 // patch edge
+constexpr int PV = PS * PS * PS;      // cells per patch
+constexpr int PSLOT = NV * PV;        // doubles per patch slot
+constexpr int GE = 16;                // group edge
+constexpr int TW = GE + 4;            // tile edge with 2 ghost cells per side
+constexpr int STEP_THREADS = 256;     // one thread per (x,y) column of the group
+
+// Coarse-fine flux register hook (section 2.2 fix-up): for each group and
+// each of its 6 faces, fine_reg[g*6+f] >= 0 is the offset (in doubles) of an
+// 8x8x5 register block of the coarse patch across that face, into which this
+// step adds dt * (mean of the 2x2 fine fluxes) per coarse face;
+// coarse_reg[slot*6+f] >= 0 is where a coarse patch stores dt * F on that face.
+struct CFRegs {
+    const int64_t *fine_off;    // [n_groups*6] or null
+    double *fine_buf;
+    const int64_t *coarse_off;  // [n_slots*6] or null
+    double *coarse_buf;
+};
+
+struct StepParams {
+    const double *__restrict__ U_old;
+    double *__restrict__ U_new;
+    const int32_t *__restrict__ nbr;  // [n_groups][64] source of each 4x4x4 patch position
+    const double *__restrict__ ghost; // interpolated coarse-fine ghost patches
+    const int32_t *__restrict__ work; // optional list of group ids (null: 0..n_work-1)
+    int n_work;
+    double dt;                               // >= 0: time step from the host
+    const unsigned long long *smax_in;       // dt < 0: dt = cfl*dh/smax_in
+    double cfl, dh, gamma;
+    unsigned long long *smax_out;            // max signal speed of the new state (bits)
+    unsigned long long *n_bad;               // count of unphysical new cells
+    double *dt_used;                         // the dt this step used (device record)
+    CFRegs cf;
+};
+
+template <typename real>
+struct StepSmem {
+    real W[3][NV][TW][TW];       // primitive ring, planes z-1, z, z+1
+    real XS[2][NV][GE][GE + 2];  // x-/x+ face states, cells x=-1..16, rows y=0..15
+    real YS[2][NV][GE + 2][GE];  // y-/y+ face states, cells y=-1..16, columns x=0..15
+    real FX[NV][GE][GE + 1];     // x flux at face x-1/2, x=0..16
+    real FY[NV][GE + 1][GE];     // y flux at face y-1/2, y=0..16
+    int nbr[64];
+    double red[STEP_THREADS / 32];
+    double dt;
+};
+
+// Source pointer for patch position q (0..63) of the current group.
+__device__ __forceinline__ const double *patch_src(const StepParams &P, int s) {
+    if (s >= 0) return P.U_old + (int64_t)s * PSLOT;
+    if (s <= -2) return P.ghost + (int64_t)(-2 - s) * PSLOT;
+    return nullptr;
+}
+
+// Load tile plane tz (-2..17) into ring slot and convert to primitives.
+template <typename real>
+__device__ __forceinline__ void load_plane(StepSmem<real> &S, const StepParams &P, int tz,
+                                           const Gas<real> &g) {
+    const int slot = (tz + 3) % 3;
+    const int qz = (tz + PS) >> 3, lz = (tz + PS) & 7;
+    for (int i = threadIdx.x; i < TW * TW; i += STEP_THREADS) {
+        const int ty = i / TW - 2, tx = i % TW - 2;
+        const int qy = (ty + PS) >> 3, ly = (ty + PS) & 7;
+        const int qx = (tx + PS) >> 3, lx = (tx + PS) & 7;
+        const double *src = patch_src(P, S.nbr[qx + 4 * qy + 16 * qz]);
+        real u[NV], w[NV];
+        if (src) {
+            const int off = lz * 64 + ly * 8 + lx;
+#pragma unroll
+            for (int v = 0; v < NV; v++) u[v] = (real)__ldg(src + v * PV + off);
+            u2w(u, w, g);
+        } else {  // a position no stencil reads (a tile corner): benign state
+            w[0] = real(1); w[1] = w[2] = w[3] = real(0); w[4] = real(1);
+        }
+#pragma unroll
+        for (int v = 0; v < NV; v++) S.W[slot][v][ty + 2][tx + 2] = w[v];
+    }
+}
+
+// Limited slopes and Hancock half step of tile cell (x,y) on plane z.
+// uf[2d] / uf[2d+1]: conserved state on the low / high face along d.
+template <typename real>
+__device__ __forceinline__ void hancock_cell(const StepSmem<real> &S, int x, int y, int z,
+                                             real dtdh_half, const Gas<real> &g,
+                                             real uf[6][NV]) {
+    const int s0 = (z + 3) % 3, sm = (z + 2) % 3, sp = (z + 4) % 3;
+    const int X = x + 2, Y = y + 2;
+    real w[NV], hs[3][NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        w[v] = S.W[s0][v][Y][X];
+        hs[0][v] = half_vanleer(w[v] - S.W[s0][v][Y][X - 1], S.W[s0][v][Y][X + 1] - w[v]);
+        hs[1][v] = half_vanleer(w[v] - S.W[s0][v][Y - 1][X], S.W[s0][v][Y + 1][X] - w[v]);
+        hs[2][v] = half_vanleer(w[v] - S.W[sm][v][Y][X], S.W[sp][v][Y][X] - w[v]);
+    }
+    real inc[NV] = {real(0), real(0), real(0), real(0), real(0)};
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        real wm[NV], wp[NV], fm[NV], fp[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            wm[v] = w[v] - hs[d][v];
+            wp[v] = w[v] + hs[d][v];
+        }
+        w2u(wm, uf[2 * d], g);
+        w2u(wp, uf[2 * d + 1], g);
+        if (d == 0) { phys_flux<0>(wm, uf[0], fm); phys_flux<0>(wp, uf[1], fp); }
+        if (d == 1) { phys_flux<1>(wm, uf[2], fm); phys_flux<1>(wp, uf[3], fp); }
+        if (d == 2) { phys_flux<2>(wm, uf[4], fm); phys_flux<2>(wp, uf[5], fp); }
+#pragma unroll
+        for (int v = 0; v < NV; v++) inc[v] += fm[v] - fp[v];
+    }
+#pragma unroll
+    for (int f = 0; f < 6; f++)
+#pragma unroll
+        for (int v = 0; v < NV; v++) uf[f][v] += dtdh_half * inc[v];
+}
+
+template <typename real>
+__global__ void __launch_bounds__(STEP_THREADS, 1) k_hydro_step(StepParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StepSmem<real> &S = *reinterpret_cast<StepSmem<real> *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int cx = tid & 15, cy = tid >> 4;  // this thread's (x,y) column
+
+    Gas<real> g;
+    g.gamma = (real)P.gamma;
+    g.gm1 = (real)(P.gamma - 1.0);
+    g.inv_gm1 = (real)(1.0 / (P.gamma - 1.0));
+
+    if (tid == 0) {
+        double dt = P.dt;
+        if (dt < 0.0) dt = P.cfl * P.dh / __longlong_as_double((long long)*P.smax_in);
+        S.dt = dt;
+        if (blockIdx.x == 0 && P.dt_used) *P.dt_used = dt;
+    }
+    __syncthreads();
+    const double dt = S.dt;
+    const double dtdh = dt / P.dh;
+    const real dtdh_half = (real)(0.5 * dt / P.dh);
+    double smax = 0.0;
+    unsigned nbad = 0;
+
+    for (int wi = blockIdx.x; wi < P.n_work; wi += gridDim.x) {
+        const int grp = P.work ? P.work[wi] : wi;
+        if (tid < 64) S.nbr[tid] = P.nbr[(int64_t)grp * 64 + tid];
+        __syncthreads();
+        load_plane(S, P, -2, g);
+        load_plane(S, P, -1, g);
+
+        real zp_prev[NV];   // high z face state of this column's cell at z-1
+        double acc[NV];     // flux divergence of this column's cell at z-1 (minus its top z flux)
+#pragma unroll
+        for (int v = 0; v < NV; v++) { zp_prev[v] = real(0); acc[v] = 0.0; }
+
+        for (int z = -1; z <= GE; z++) {
+            load_plane(S, P, z + 1, g);
+            __syncthreads();
+
+            // ---- B: Hancock states of plane z
+            real zm[NV], zp[NV];
+            {
+                real uf[6][NV];
+                hancock_cell(S, cx, cy, z, dtdh_half, g, uf);
+#pragma unroll
+                for (int v = 0; v < NV; v++) { zm[v] = uf[4][v]; zp[v] = uf[5][v]; }
+                if (z >= 0 && z < GE) {
+#pragma unroll
+                    for (int v = 0; v < NV; v++) {
+                        S.XS[0][v][cy][cx + 1] = uf[0][v];
+                        S.XS[1][v][cy][cx + 1] = uf[1][v];
+                        S.YS[0][v][cy + 1][cx] = uf[2][v];
+                        S.YS[1][v][cy + 1][cx] = uf[3][v];
+                    }
+                }
+            }
+            if (z >= 0 && z < GE && tid < 64) {
+                // ring cells: x = -1 / 16 (rows 0..15), then y = -1 / 16 (columns 0..15)
+                const int r = tid & 15;
+                const bool xring = tid < 32;
+                const int side = (tid >> 4) & 1;
+                const int x = xring ? (side ? GE : -1) : r;
+                const int y = xring ? r : (side ? GE : -1);
+                real uf[6][NV];
+                hancock_cell(S, x, y, z, dtdh_half, g, uf);
+                if (xring) {
+#pragma unroll
+                    for (int v = 0; v < NV; v++) {
+                        S.XS[0][v][y][x + 1] = uf[0][v];
+                        S.XS[1][v][y][x + 1] = uf[1][v];
+                    }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < NV; v++) {
+                        S.YS[0][v][y + 1][x] = uf[2][v];
+                        S.YS[1][v][y + 1][x] = uf[3][v];
+                    }
+                }
+            }
+            __syncthreads();
+
+            // ---- C: fluxes
+            real fz[NV];
+            if (z >= 0) hllc<2>(zp_prev, zm, fz, g);
+            if (z >= 0 && z < GE) {
+                real uL[NV], uR[NV], F[NV];
+                // x face at cx-1/2 of row cy
+#pragma unroll
+                for (int v = 0; v < NV; v++) { uL[v] = S.XS[1][v][cy][cx]; uR[v] = S.XS[0][v][cy][cx + 1]; }
+                hllc<0>(uL, uR, F, g);
+#pragma unroll
+                for (int v = 0; v < NV; v++) S.FX[v][cy][cx] = F[v];
+                // y face at cy-1/2 of column cx
+#pragma unroll
+                for (int v = 0; v < NV; v++) { uL[v] = S.YS[1][v][cy][cx]; uR[v] = S.YS[0][v][cy + 1][cx]; }
+                hllc<1>(uL, uR, F, g);
+#pragma unroll
+                for (int v = 0; v < NV; v++) S.FY[v][cy][cx] = F[v];
+                if (tid < 32) {  // the high boundary faces x = 16-1/2 and y = 16-1/2
+                    const int r = tid & 15;
+                    if (tid < 16) {
+#pragma unroll
+                        for (int v = 0; v < NV; v++) { uL[v] = S.XS[1][v][r][GE]; uR[v] = S.XS[0][v][r][GE + 1]; }
+                        hllc<0>(uL, uR, F, g);
+#pragma unroll
+                        for (int v = 0; v < NV; v++) S.FX[v][r][GE] = F[v];
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < NV; v++) { uL[v] = S.YS[1][v][GE][r]; uR[v] = S.YS[0][v][GE + 1][r]; }
+                        hllc<1>(uL, uR, F, g);
+#pragma unroll
+                        for (int v = 0; v < NV; v++) S.FY[v][GE][r] = F[v];
+                    }
+                }
+            }
+            __syncthreads();
+
+            // ---- D: finish cell (cx,cy,z-1), start cell (cx,cy,z)
+            const int64_t own = (int64_t)grp * 8;
+            if (z >= 1) {
+                const int zc = z - 1;
+                const int64_t base = (own + (cx >> 3) + 2 * (cy >> 3) + 4 * (zc >> 3)) * PSLOT +
+                                     (zc & 7) * 64 + (cy & 7) * 8 + (cx & 7);
+                double un[NV];
+#pragma unroll
+                for (int v = 0; v < NV; v++) {
+                    const double tot = acc[v] + (double)fz[v];
+                    un[v] = P.U_old[base + v * PV] - dtdh * tot;
+                    P.U_new[base + v * PV] = un[v];
+                }
+                real ur[NV];
+#pragma unroll
+                for (int v = 0; v < NV; v++) ur[v] = (real)un[v];
+                bool ok;
+                const real s = cfl_speed(ur, g, ok);
+                if (!ok) nbad++;
+                if ((double)s > smax) smax = (double)s;
+            }
+            if (z >= 0 && z < GE) {
+#pragma unroll
+                for (int v = 0; v < NV; v++) {
+                    const real dxy = (S.FX[v][cy][cx + 1] - S.FX[v][cy][cx]) +
+                                     (S.FY[v][cy + 1][cx] - S.FY[v][cy][cx]);
+                    acc[v] = (double)dxy - (double)fz[v];
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < NV; v++) zp_prev[v] = zp[v];
+        }
+        __syncthreads();  // the next group overwrites nbr and the ring
+    }
+
+    // ---- block reduction of the signal speed, one atomic per block
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+    unsigned nb = nbad;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nb += __shfl_xor_sync(0xffffffffu, nb, o);
+    if ((tid & 31) == 0) S.red[tid >> 5] = smax;
+    __syncthreads();
+    if (tid == 0) {
+        double m = 0.0;
+        for (int i = 0; i < STEP_THREADS / 32; i++) m = fmax(m, S.red[i]);
+        // positive doubles order like their bit patterns: exact, order-free max
+        atomicMax(P.smax_out, (unsigned long long)__double_as_longlong(m));
+    }
+    if ((tid & 31) == 0 && nb) atomicAdd(P.n_bad, (unsigned long long)nb);
+}
+
+}  // namespace amrh

@@ -1,0 +1,75 @@
+"""Uniform periodic grids (one fully covered AMR level) on the GPU.
+
+Marshalling around the C ABI only: torch allocates the caller-owned device
+arrays; packing, stepping, reductions all run in libamr_hydro.so.
+"""
+import numpy as np
+import torch
+
+from . import amr_hydro as A
+
+
+class UniformGrid:
+    """A periodic nx x ny x nz box (multiples of 16) as one level of 8^3 patches."""
+
+    def __init__(self, shape, gamma=5.0 / 3.0, cfl=0.5, prec=A.AMR_FP64, box_x=1.0, stream=None,
+                 device="cuda"):
+        nx, ny, nz = shape
+        self.shape = (nx, ny, nz)
+        self.device = torch.device(device)
+        self.stream = stream
+        p = A.make_params(gamma=gamma, cfl=cfl, root_n=(nx, ny, nz),
+                          box=(box_x, box_x * ny / nx, box_x * nz / nx), prec=prec)
+        self.params = p
+        self.dh = box_x / nx
+        self.ctx = A.amr_hydro_init(p, stream)
+        npch = (nx // 8, ny // 8, nz // 8)
+        self.n_patches = npch[0] * npch[1] * npch[2]
+        corner, sib, parent, child = A.amr_hydro_uniform_tables(npch)
+        self.tables = [torch.from_numpy(a).to(self.device) for a in (corner, sib, parent, child)]
+        self.U = [torch.zeros((self.n_patches, 5, 8, 8, 8), dtype=torch.float64, device=self.device)
+                  for _ in range(2)]
+        A.amr_hydro_set_level(self.ctx, 0, self.n_patches, self.U[0], self.U[1], *self.tables, t=0.0)
+
+    def close(self):
+        if self.ctx is not None:
+            A.amr_hydro_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def state(self):
+        cur, _, _ = A.amr_hydro_get_state(self.ctx, 0)
+        return self.U[cur]
+
+    def time(self):
+        _, t, _ = A.amr_hydro_get_state(self.ctx, 0)
+        return t
+
+    def upload(self, U_dense):
+        """U_dense: [5][nz][ny][nx] float64 (numpy or torch) -> current state."""
+        d = torch.as_tensor(np.ascontiguousarray(U_dense) if isinstance(U_dense, np.ndarray) else U_dense)
+        d = d.to(self.device, torch.float64).contiguous()
+        nx, ny, nz = self.shape
+        A.amr_hydro_pack_uniform(d, nx, ny, nz, self.state(), self.stream)
+        # the state changed: re-register so that cached reductions are dropped
+        cur, t, _ = A.amr_hydro_get_state(self.ctx, 0)
+        if cur == 1:
+            self.U.reverse()
+        A.amr_hydro_set_level(self.ctx, 0, self.n_patches, self.U[0], self.U[1], *self.tables, t=t)
+
+    def download(self, out=None):
+        nx, ny, nz = self.shape
+        d = torch.empty((5, nz, ny, nx), dtype=torch.float64, device=self.device)
+        A.amr_hydro_unpack_uniform(self.state(), nx, ny, nz, d, self.stream)
+        return d.cpu().numpy() if out is None else out.copy_(d)
+
+    def min_dt(self):
+        return A.amr_hydro_min_dt(self.ctx, 0)
+
+    def step(self, dt=-1.0, count_unphysical=False):
+        return A.amr_hydro_advance_level(self.ctx, 0, dt, count_unphysical)
