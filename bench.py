@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Throughput of the GAMER-2 patch-group hydro step on B300.
+
+Workload: decaying turbulence on a uniform periodic 512^3 box (32768 patch
+groups of 2x2x2 patches of 8^3 cells), gamma=5/3, C_CFL=0.5; rho=1, P=0.6,
+Gaussian random velocity with k^-4 power on 1<=|k|<=16, rms Mach 1 (seeded,
+synthetic).  One "step" is one pass of the whole per-group hot path over the
+level: ghost gather, PLM + van Leer, Hancock half step, HLLC, conservative
+update, and the Eq. (CFL2) time-step reduction of the new state (the next
+step's dt is computed on the device from it).
+
+`value` is the FP64 step (the plain method); the FP32-compute /
+FP64-accumulate step and the 256^3 box are reported beside it.  Inputs
+(5.4 GB of state) are far larger than the 126 MB L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N>1) each rank runs an independent replica (the uniform
+step has no exchange on one GPU's box): value = all ranks' cell updates /
+max over ranks of the timed region.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+if HERE not in sys.path:
+    sys.path.insert(0, HERE)
+os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+
+METRIC = "cell updates/s per B300 (FP64 & FP32) + % HBM roofline"
+UNIT = "cells/s"
+# Algorithmic FP64 operations per cell update (add/sub, mul, div and sqrt
+# counted as one flop each) of one step plus the Eq. (CFL2) speed, counted by
+# the instrumented oracle build (oracle/flop_count.cpp) on this workload.
+ALG_FLOPS_PER_CELL = 1027.0
+# Algorithmic HBM bytes per cell update: read U^n (5 doubles) + write U^{n+1}.
+ALG_BYTES_PER_CELL = 80.0
+# FP64 peak: 148 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2032 MHz (2 FMA/clk/SM
+# measured: 5.55e11 DFMA/s at 1942 MHz); FP32: 148 x 128 x 2 x 2032 MHz.
+FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# DRAM bytes (read+write) per cell update of one k_hydro_step launch from an
+# ncu capture, keyed by the hash of the kernel sources it was taken on.
+TRAFFIC_BYTES_PER_CELL = {}
+KERNEL_SOURCES = ("paper_1712_07070_b300/csrc/step_kernel.cuh", "paper_1712_07070_b300/csrc/hydro_math.cuh")
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(HERE, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=512, help="box edge (cells), multiple of 16")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    return ap.parse_args()
+
+
+# ---- ranks --------------------------------------------------------------------------
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def dist_init(backend):
+    import torch.distributed as dist
+    rank, world, _ = dist_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend, init_method="env://")
+    return rank, world
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(x, device="cpu"):
+    """Largest value of the float x over all ranks (x itself on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- clocks during the timed region --------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            self.proc.wait()
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        smax = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---- our arm --------------------------------------------------------------------------
+
+def timed_steps(torch, grid, stream, K):
+    """K device-dt steps on `stream`; returns (region ms, mean kernel ms)."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for a, b in evs:
+        a.record(stream)
+        grid.step(-1.0)
+        b.record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1), sum(a.elapsed_time(b) for a, b in evs) / K
+
+
+def e2e_steps(torch, grid, stream, host_in, host_out, K):
+    """K steps through the public API with pinned host buffers: per step the
+    input state goes host->device, one step runs, the new state comes back."""
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(K):
+        grid.upload(host_in)
+        grid.step(-1.0)
+        grid.download(out=host_out)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1)
+
+
+def run_case(torch, A, UniformGrid, U0, n, prec, K, W, stream, want_e2e):
+    g = UniformGrid((n, n, n), prec=prec, stream=stream.cuda_stream)
+    g.upload(torch.from_numpy(U0))
+    torch.cuda.synchronize()
+    for _ in range(W):
+        g.step(-1.0)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    region_ms, kernel_ms = timed_steps(torch, g, stream, K)
+    clocks = clk.stop()
+    torch.cuda.synchronize()
+    barrier()
+    out = {"region_ms": region_ms, "kernel_ms": kernel_ms, "clocks": clocks}
+    if want_e2e:
+        host_in = torch.from_numpy(U0).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        e2e_steps(torch, g, stream, host_in, host_out, 1)
+        barrier()
+        e2e_ms = e2e_steps(torch, g, stream, host_in, host_out, K)
+        barrier()
+        out["e2e_ms"] = e2e_ms
+        out["bytes"] = host_in.numel() * 8
+    g.close()
+    return out
+
+
+def cpu_baseline(n, steps=3, slab=64):
+    """The oracle, as it stands, on a bounded sample of the same workload:
+    `steps` steps of a periodic n x n x slab box cut from the same seeded
+    turbulence field, timed on all host cores."""
+    import oracle
+    from paper_1712_07070_b300 import ics
+    U = ics.turbulence(n, seed=1)[:, :slab].copy()
+    g = 5.0 / 3.0
+    dt = oracle.dt_cfl2(U, g, 0.5, 1.0 / n)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        U, _ = oracle.step_periodic(U, 1.0 / n, dt, g)
+    el = time.perf_counter() - t0
+    cells = n * n * slab * steps
+    return {"value": cells / el, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count())),
+            "kind": "oracle",
+            "sample": f"{steps} FP64 steps of a {n}x{n}x{slab} periodic slab of the same seeded turbulence field "
+                      f"({cells} cell updates, {el:.1f} s)"}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_init("nccl")
+    from paper_1712_07070_b300 import amr_hydro as A
+    from paper_1712_07070_b300 import ics
+    from paper_1712_07070_b300.uniform import UniformGrid
+    A.lib()  # fails loudly when the CUDA library is missing
+    n, K, W = args.n, args.steps, args.warmup
+    stream = torch.cuda.Stream()
+    U0 = ics.turbulence(n, seed=1)
+    cells = n ** 3
+
+    main = run_case(torch, A, UniformGrid, U0, n, A.AMR_FP64, K, W, stream, want_e2e=True)
+    f32 = run_case(torch, A, UniformGrid, U0, n, A.AMR_FP32_ACC64, K, W, stream, want_e2e=True)
+    variants = []
+    if not args.no_variants and n != 256:
+        U1 = ics.turbulence(256, seed=1)
+        for prec, name in ((A.AMR_FP64, "f64"), (A.AMR_FP32_ACC64, "fp32_acc64")):
+            r = run_case(torch, A, UniformGrid, U1, 256, prec, K, W, stream, want_e2e=False)
+            ms = max_over_ranks(r["region_ms"], "cuda") / K
+            variants.append({"workload": "turbulence 256^3", "dtype": name, "ms_per_step": ms,
+                             "value": world * 256 ** 3 / (ms * 1e-3)})
+
+    ms64 = max_over_ranks(main["region_ms"], "cuda") / K
+    ms32 = max_over_ranks(f32["region_ms"], "cuda") / K
+    e64 = max_over_ranks(main["e2e_ms"], "cuda") / K
+    e32 = max_over_ranks(f32["e2e_ms"], "cuda") / K
+    value = world * cells / (ms64 * 1e-3)
+    kh = kernel_hash()
+    tb = TRAFFIC_BYTES_PER_CELL.get(f"f64:{kh}")
+    k64_s = main["kernel_ms"] * 1e-3
+    k32_s = f32["kernel_ms"] * 1e-3
+    ach64 = ALG_FLOPS_PER_CELL * cells / k64_s / 1e12
+    roof = {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach64 / FP64_PEAK_TFLOPS, "traffic": (tb * cells if tb else None),
+            "kernel": "k_hydro_step<double>", "peak_kind": "derived: 148 SM x 2 DFMA/clk x 2 flop x 2032 MHz",
+            "hbm_frac_of_measured": ALG_BYTES_PER_CELL * cells / k64_s / 1e9 / hbm_peak()}
+    tb32 = TRAFFIC_BYTES_PER_CELL.get(f"f32:{kh}")
+    ach32 = ALG_BYTES_PER_CELL * cells / k32_s / 1e9
+    roof32 = {"bound": "hbm", "achieved": ach32, "peak": hbm_peak(), "unit": "GB/s",
+              "frac": ach32 / hbm_peak(), "traffic": (tb32 * cells if tb32 else None),
+              "kernel": "k_hydro_step<float>", "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs)",
+              "alu_fp32_frac": ALG_FLOPS_PER_CELL * cells / k32_s / 1e12 / FP32_PEAK_TFLOPS}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"decaying turbulence {n}^3 periodic, uniform level of 8^3 patches "
+                               f"({cells // 4096} patch groups), MUSCL-Hancock+PLM(van Leer)+HLLC, CFL 0.5",
+                   "cells": cells, "parallelism": f"replicas x{world}",
+                   "l2": "inputs (5.4 GB state at 512^3) larger than L2; no flush"},
+        "roofline": roof,
+        "e2e": {"value": world * cells / (e64 * 1e-3), "unit": UNIT, "h2d_bytes_per_step": main["bytes"],
+                "d2h_bytes_per_step": main["bytes"]},
+        "gpu_launches": K,
+        "clocks": main["clocks"],
+        "fp32_acc64": {"value": world * cells / (ms32 * 1e-3), "ms_per_step": ms32, "dtype": "fp32_acc64",
+                       "roofline": roof32, "clocks": f32["clocks"], "gpu_launches": K,
+                       "e2e": {"value": world * cells / (e32 * 1e-3), "unit": UNIT,
+                               "h2d_bytes_per_step": f32["bytes"], "d2h_bytes_per_step": f32["bytes"]}},
+        "variants": variants,
+        "kernel_hash": kh,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(n)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6400.0  # fallback figure
+
+
+# ---- reference arm: the oracle on the host cores ----------------------------------------
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    n, K, W = args.n, args.steps, args.warmup
+    import oracle
+    from paper_1712_07070_b300 import ics
+    slab = 16
+    U = ics.turbulence(n, seed=1)[:, :slab].copy()
+    g = 5.0 / 3.0
+    for _ in range(W):
+        dt = oracle.dt_cfl2(U, g, 0.5, 1.0 / n)
+        U, _ = oracle.step_periodic(U, 1.0 / n, dt, g)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        dt = oracle.dt_cfl2(U, g, 0.5, 1.0 / n)
+        U, _ = oracle.step_periodic(U, 1.0 / n, dt, g)
+    el = time.perf_counter() - t0
+    cells = n * n * slab
+    value = cells * K / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": el / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": f"decaying turbulence {n}^3 periodic (oracle: bounded sample)", "cells": n ** 3},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: one FP64 step of a {n}x{n}x{slab} periodic slab of the same "
+                                   f"seeded turbulence field ({cells} cell updates)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

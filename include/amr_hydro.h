@@ -110,6 +110,11 @@ amr_status amr_hydro_set_level(amr_hydro_ctx *ctx, int level, int n_patches,
 amr_status amr_hydro_get_state(amr_hydro_ctx *ctx, int level, int *cur_buffer,
                                double *t_cur, double *t_prev);
 
+/* Declare that the caller rewrote the level's newest state buffer (a new
+ * initial condition, a restart, an in-place edit): reductions cached from the
+ * last step are dropped.  Asynchronous; no device work. */
+amr_status amr_hydro_touch_level(amr_hydro_ctx *ctx, int level);
+
 /*
  * Fill the coarse-fine ghost patches of `level` (>0) at time t by linear
  * interpolation in time between the coarse level's previous and newest

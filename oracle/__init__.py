@@ -150,6 +150,23 @@ def conserved_sum(U, dV):
     return out
 
 
+# ---- instrumented operation count ---------------------------------------------
+
+def count_flops(U, gamma):
+    """Per-cell FP64 operation counts of one oracle step and of one Eq. CFL2
+    signal-speed evaluation on state U (flop_count.cpp): a dict with keys
+    add, mul, div, sqrt, cmp for 'step' and 'speed'."""
+    lib()
+    L = ctypes.CDLL(_build.FLOPLIB)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    _, nz, ny, nx = U.shape
+    out = np.zeros(12)
+    L.or_count_flops(U.ctypes.data_as(ctypes.c_void_p), nx, ny, nz, ctypes.c_double(gamma),
+                     out.ctypes.data_as(ctypes.c_void_p))
+    keys = ("add", "mul", "div", "sqrt", "cmp", "other")
+    return {"step": dict(zip(keys, out[:6])), "speed": dict(zip(keys, out[6:]))}
+
+
 # ---- exact Riemann solver (validation only) ----------------------------------
 
 def exact_star(rl, ul, pl, rr, ur, pr, gamma):

@@ -16,14 +16,26 @@ LIB = os.path.join(HERE, "liboracle.so")
 CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-fno-fast-math"]
 
 
+FLOPLIB = os.path.join(HERE, "libflopcount.so")
+
+
+def _stale(lib, srcs):
+    if not os.path.exists(lib):
+        return True
+    m = os.path.getmtime(lib)
+    return any(os.path.getmtime(s) > m for s in srcs)
+
+
 def build(force=False):
     srcs = [os.path.join(HERE, s) for s in SOURCES if os.path.exists(os.path.join(HERE, s))]
-    if not force and os.path.exists(LIB):
-        lib_m = os.path.getmtime(LIB)
-        if all(os.path.getmtime(s) <= lib_m for s in srcs):
-            return LIB
-    cmd = ["gcc", *CFLAGS, "-o", LIB, *srcs, "-lm"]
-    subprocess.run(cmd, check=True)
+    if force or _stale(LIB, srcs):
+        subprocess.run(["gcc", *CFLAGS, "-o", LIB, *srcs, "-lm"], check=True)
+    fsrc = [os.path.join(HERE, "flop_count.cpp"), os.path.join(HERE, "hydro_oracle.c")]
+    if force or _stale(FLOPLIB, fsrc):
+        # the counting build: no OpenMP (its pragmas are ignored), C++ for the
+        # operator-overloaded counting type
+        subprocess.run(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-Wno-unknown-pragmas",
+                        "-o", FLOPLIB, fsrc[0]], check=True)
     return LIB
 
 

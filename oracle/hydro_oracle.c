@@ -184,13 +184,13 @@ int64_t or_step_periodic(const double *U, double *Unew, int nx, int ny, int nz,
                          double dh, double dt, double gamma) {
     const int64_t n = (int64_t)nx * ny * nz;
     const int dims[3] = {nx, ny, nz};
-    double *W = malloc(sizeof(double) * NV * n);
+    double *W = (double *)malloc(sizeof(double) * NV * n);
     /* face states after the Hancock half step: FS[face][var][cell],
      * face = 2*d + s, s=0 the low (-) face, s=1 the high (+) face */
-    double *FS = malloc(sizeof(double) * 6 * NV * n);
+    double *FS = (double *)malloc(sizeof(double) * 6 * NV * n);
     /* interface fluxes: FX[d][var][cell] is the flux through the high face
      * of the cell along d (i.e. at i+1/2) */
-    double *FX = malloc(sizeof(double) * 3 * NV * n);
+    double *FX = (double *)malloc(sizeof(double) * 3 * NV * n);
 
     /* 1. primitives */
 #pragma omp parallel for schedule(static)

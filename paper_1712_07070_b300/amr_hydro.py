@@ -17,6 +17,7 @@ AMR_FP64, AMR_FP32_ACC64 = 0, 1
 # every symbol include/amr_hydro.h declares
 SYMBOLS = (
     "amr_hydro_init", "amr_hydro_destroy", "amr_hydro_set_level", "amr_hydro_get_state",
+    "amr_hydro_touch_level",
     "amr_hydro_fill_ghost", "amr_hydro_advance_level", "amr_hydro_flux_fixup", "amr_hydro_min_dt",
     "amr_hydro_regrid_flags", "amr_hydro_conserved_sum", "amr_hydro_set_box",
     "amr_hydro_advance_boxes", "amr_hydro_box_state", "amr_hydro_step_adjoint",
@@ -58,6 +59,7 @@ def lib():
         "amr_hydro_destroy": [_vp],
         "amr_hydro_set_level": [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_double],
         "amr_hydro_get_state": [_vp, ctypes.c_int, _ip, _dp, _dp],
+        "amr_hydro_touch_level": [_vp, ctypes.c_int],
         "amr_hydro_fill_ghost": [_vp, ctypes.c_int, ctypes.c_double],
         "amr_hydro_advance_level": [_vp, ctypes.c_int, ctypes.c_double, _i64p],
         "amr_hydro_flux_fixup": [_vp, ctypes.c_int],
@@ -123,6 +125,10 @@ def amr_hydro_get_state(ctx, level):
     check(lib().amr_hydro_get_state(ctx, level, ctypes.byref(cur), ctypes.byref(tc), ctypes.byref(tp)),
           "amr_hydro_get_state")
     return cur.value, tc.value, tp.value
+
+
+def amr_hydro_touch_level(ctx, level):
+    check(lib().amr_hydro_touch_level(ctx, level), "amr_hydro_touch_level")
 
 
 def amr_hydro_fill_ghost(ctx, level, t):

@@ -200,7 +200,7 @@ amr_status amr_hydro_init(const amr_hydro_params *p, void *stream, amr_hydro_ctx
     cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
     c->step_bps = step_blocks_per_sm(p->prec);
     if ((st = c->scal.reserve(SCAL_N))) { amr_hydro_destroy(c); return st; }
-    if ((st = c->dtbuf.reserve(MAX_LEVELS + MAX_BOXES))) { amr_hydro_destroy(c); return st; }
+    if ((st = c->dtbuf.reserve(3 * (MAX_LEVELS + MAX_BOXES)))) { amr_hydro_destroy(c); return st; }
     if ((st = cuda_fail(cudaMemsetAsync(c->scal.p, 0, sizeof(unsigned long long) * SCAL_N, c->stream),
                         "memset"))) {
         amr_hydro_destroy(c);
@@ -242,7 +242,7 @@ amr_status amr_hydro_min_dt(amr_hydro_ctx *c, int level, double *dt_out) {
     if (!L.n_patches) return AMR_E_INVAL;
     amr_status st = level_speed(c, level);
     if (st) return st;
-    unsigned long long *sm = c->scal.p + L.smax_idx, *nb = c->scal.p + L.nbad_idx;
+    unsigned long long *sm = c->scal.p + L.scal0 + L.ring, *nb = c->scal.p + L.scal0 + 3 + L.ring;
     cudaPointerAttributes a;
     const bool dev = cudaPointerGetAttributes(&a, dt_out) == cudaSuccess &&
                      (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
@@ -298,7 +298,7 @@ double level_dh(const amr_hydro_ctx *c, int level) {
 amr_status level_speed(amr_hydro_ctx *c, int level) {
     Level &L = c->lv[level];
     if (L.speed_valid) return AMR_OK;
-    unsigned long long *sm = c->scal.p + L.smax_idx, *nb = c->scal.p + L.nbad_idx;
+    unsigned long long *sm = c->scal.p + L.scal0 + L.ring, *nb = c->scal.p + L.scal0 + 3 + L.ring;
     amr_status st = cuda_fail(cudaMemsetAsync(sm, 0, 8, c->stream), "memset");
     if (st) return st;
     if ((st = cuda_fail(cudaMemsetAsync(nb, 0, 8, c->stream), "memset"))) return st;

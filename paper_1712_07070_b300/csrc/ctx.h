@@ -19,10 +19,15 @@ struct DevBuf {
 
 constexpr int MAX_LEVELS = 8;
 constexpr int MAX_BOXES = 256;
-// scalar slots (unsigned 64-bit) in ctx->scal: per level 4, per box 4
+// Scalar slots (unsigned 64-bit) in ctx->scal, 8 per level and 8 per box:
+// a ring of three max-signal-speed slots [0..2] and three unphysical-count
+// slots [3..5].  The state of ring position r has its speed in slot r and its
+// count in slot 3+r; a step reads r, accumulates into (r+1)%3 and zeroes
+// (r+2)%3 for the step after it, so no per-step memset is needed.
+constexpr int SCAL_PER = 8;
 constexpr int SCAL_LEVEL0 = 0;
-constexpr int SCAL_BOX0 = 4 * MAX_LEVELS;
-constexpr int SCAL_N = SCAL_BOX0 + 4 * MAX_BOXES;
+constexpr int SCAL_BOX0 = SCAL_PER * MAX_LEVELS;
+constexpr int SCAL_N = SCAL_BOX0 + SCAL_PER * MAX_BOXES;
 
 // One coarse-fine ghost patch of a level: its 8^3 cells are interpolated from
 // the coarse level around the parent patch `cparent` of the group that needs it.
@@ -51,7 +56,8 @@ struct Level {
     int n_fix = 0;
     int n_cf_regs = 0;
     bool has_fine_regs = false, has_coarse_regs = false;
-    int smax_idx = 0, nbad_idx = 0;
+    int scal0 = 0;  // first of this level's 8 scalar slots
+    int ring = 0;   // ring position of the newest state
     bool speed_valid = false;
     void release() {
         nbr.release();
@@ -70,6 +76,7 @@ struct Box {
     int n = 0, n_groups = 0;
     double *U[2] = {nullptr, nullptr};
     int cur = 0;
+    int ring = 0;
     DevBuf<int32_t> nbr;
     void release() { nbr.release(); n = 0; }
 };

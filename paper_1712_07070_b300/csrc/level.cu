@@ -16,12 +16,13 @@ namespace amrh {
 // Bring a level's host-side time up to date after device-side time steps.
 static amr_status sync_level_time(amr_hydro_ctx *c, Level &L, int level) {
     if (!L.t_pending) return AMR_OK;
-    double dt;
-    amr_status st = cuda_fail(cudaMemcpyAsync(&dt, c->dtbuf.p + level, 8, cudaMemcpyDeviceToHost,
-                                              c->stream), "d2h dt");
+    double rec[3];
+    amr_status st = cuda_fail(cudaMemcpyAsync(rec, c->dtbuf.p + 3 * level, 24, cudaMemcpyDeviceToHost,
+                                              c->stream), "d2h time");
     if (st) return st;
     if ((st = cuda_fail(cudaStreamSynchronize(c->stream), "sync"))) return st;
-    L.t = L.t_prev + dt;
+    L.t = rec[1];
+    L.t_prev = rec[2];
     L.t_pending = false;
     return AMR_OK;
 }
@@ -54,10 +55,16 @@ amr_status amr_hydro_set_level(amr_hydro_ctx *c, int level, int n_patches, doubl
     L.d_sib = sib;
     L.d_parent = parent;
     L.d_child = child_group;
-    L.smax_idx = SCAL_LEVEL0 + 4 * level;
-    L.nbad_idx = SCAL_LEVEL0 + 4 * level + 2;
+    L.scal0 = SCAL_LEVEL0 + SCAL_PER * level;
+    L.ring = 0;
     L.speed_valid = false;
+    if ((st = cuda_fail(cudaMemset(c->scal.p + L.scal0, 0, 8 * SCAL_PER), "memset"))) return st;
     L.n_ghost = 0;
+    {
+        const double rec[3] = {0.0, t, t};
+        if ((st = cuda_fail(cudaMemcpy(c->dtbuf.p + 3 * level, rec, 24, cudaMemcpyHostToDevice), "h2d time")))
+            return st;
+    }
     if (n_patches == 0) return AMR_OK;
 
     L.corner.resize((size_t)n_patches * 3);
@@ -95,21 +102,27 @@ amr_status amr_hydro_set_level(amr_hydro_ctx *c, int level, int n_patches, doubl
     return AMR_OK;
 }
 
+amr_status amr_hydro_touch_level(amr_hydro_ctx *c, int level) {
+    if (!c || level < 0 || level > c->prm.lmax) return AMR_E_INVAL;
+    Level &L = c->lv[level];
+    if (!L.n_patches) return AMR_E_INVAL;
+    L.speed_valid = false;
+    return AMR_OK;
+}
+
 amr_status amr_hydro_advance_level(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphysical_out) {
     if (!c || level < 0 || level > c->prm.lmax) return AMR_E_INVAL;
     Level &L = c->lv[level];
     if (!L.n_patches) return AMR_E_INVAL;
     if (!(dt >= 0.0) && !(dt < 0.0)) return AMR_E_INVAL;  // NaN
     amr_status st;
-    if ((st = sync_level_time(c, L, level))) return st;
-    if (L.n_ghost) {
+    if (L.n_ghost) {  // coarse-fine ghosts need the level's time on the host
+        if ((st = sync_level_time(c, L, level))) return st;
         if ((st = fill_ghost_impl(c, level, L.t))) return st;
     }
     if (dt < 0.0 && (st = level_speed(c, level))) return st;
-    const int out_idx = (L.smax_idx == SCAL_LEVEL0 + 4 * level) ? L.smax_idx + 1 : L.smax_idx - 1;
-    unsigned long long *s_out = c->scal.p + out_idx;
-    if ((st = cuda_fail(cudaMemsetAsync(s_out, 0, 8, c->stream), "memset"))) return st;
-    if ((st = cuda_fail(cudaMemsetAsync(c->scal.p + L.nbad_idx, 0, 8, c->stream), "memset"))) return st;
+    unsigned long long *sc = c->scal.p + L.scal0;
+    const int r_in = L.ring, r_out = (L.ring + 1) % 3, r_clr = (L.ring + 2) % 3;
 
     StepParams P;
     std::memset(&P, 0, sizeof(P));
@@ -120,13 +133,14 @@ amr_status amr_hydro_advance_level(amr_hydro_ctx *c, int level, double dt, int64
     P.work = nullptr;
     P.n_work = L.n_groups;
     P.dt = dt;
-    P.smax_in = c->scal.p + L.smax_idx;
+    P.smax_in = sc + r_in;
     P.cfl = c->prm.cfl;
     P.dh = level_dh(c, level);
     P.gamma = c->prm.gamma;
-    P.smax_out = s_out;
-    P.n_bad = c->scal.p + L.nbad_idx;
-    P.dt_used = c->dtbuf.p + level;
+    P.smax_out = sc + r_out;
+    P.n_bad = sc + 3 + r_out;
+    P.clear2 = sc + r_clr;
+    P.time_rec = c->dtbuf.p + 3 * level;
     P.cf.fine_off = L.has_fine_regs ? L.fine_off.p : nullptr;
     P.cf.fine_buf = level > 0 ? c->lv[level - 1].cf_fine.p : nullptr;
     P.cf.coarse_off = L.has_coarse_regs ? L.coarse_off.p : nullptr;
@@ -136,15 +150,18 @@ amr_status amr_hydro_advance_level(amr_hydro_ctx *c, int level, double dt, int64
     if ((st = launch_step(c, P, grid))) return st;
 
     L.cur = 1 - L.cur;
-    L.t_prev = L.t;
-    if (dt >= 0.0) L.t += dt;
-    else L.t_pending = true;
-    L.smax_idx = out_idx;
+    if (dt >= 0.0 && !L.t_pending) {
+        L.t_prev = L.t;
+        L.t += dt;
+    } else {
+        L.t_pending = true;
+    }
+    L.ring = r_out;
     L.speed_valid = true;
 
     if (n_unphysical_out) {
         unsigned long long nb = 0;
-        if ((st = cuda_fail(cudaMemcpyAsync(&nb, c->scal.p + L.nbad_idx, 8, cudaMemcpyDeviceToHost, c->stream), "d2h")))
+        if ((st = cuda_fail(cudaMemcpyAsync(&nb, sc + 3 + r_out, 8, cudaMemcpyDeviceToHost, c->stream), "d2h")))
             return st;
         if ((st = cuda_fail(cudaStreamSynchronize(c->stream), "sync"))) return st;
         *n_unphysical_out = (int64_t)nb;

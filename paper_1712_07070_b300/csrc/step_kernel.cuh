@@ -53,7 +53,8 @@ struct StepParams {
     double cfl, dh, gamma;
     unsigned long long *smax_out;            // max signal speed of the new state (bits)
     unsigned long long *n_bad;               // count of unphysical new cells
-    double *dt_used;                         // the dt this step used (device record)
+    unsigned long long *clear2;              // two scalars the kernel zeroes for the next step
+    double *time_rec;                        // device record {dt used, t_new, t_old}
     CFRegs cf;
 };
 
@@ -156,7 +157,18 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_hydro_step(StepParams P) {
         double dt = P.dt;
         if (dt < 0.0) dt = P.cfl * P.dh / __longlong_as_double((long long)*P.smax_in);
         S.dt = dt;
-        if (blockIdx.x == 0 && P.dt_used) *P.dt_used = dt;
+        if (blockIdx.x == 0 && P.clear2) {
+            // the slots the following step will accumulate into (its smax_out
+            // and n_bad); nothing reads or writes them during this step
+            P.clear2[0] = 0ull;
+            P.clear2[3] = 0ull;
+        }
+        if (blockIdx.x == 0 && P.time_rec) {
+            const double t = P.time_rec[1];
+            P.time_rec[0] = dt;
+            P.time_rec[2] = t;
+            P.time_rec[1] = t + dt;
+        }
     }
     __syncthreads();
     const double dt = S.dt;

@@ -16,9 +16,22 @@ import numpy as np
 
 
 def conserved(rho, vx, vy, vz, P, gamma):
-    """Stack primitive fields into U = (rho, rho vx, rho vy, rho vz, E)."""
-    E = P / (gamma - 1.0) + 0.5 * rho * (vx * vx + vy * vy + vz * vz)
-    return np.ascontiguousarray(np.stack([rho, rho * vx, rho * vy, rho * vz, E]).astype(np.float64))
+    """Stack primitive fields into U = (rho, rho vx, rho vy, rho vz, E),
+    E = P/(gamma-1) + rho |v|^2 / 2."""
+    shape = np.broadcast(rho, vx, vy, vz, P).shape
+    U = np.empty((5,) + shape, dtype=np.float64)
+    U[0] = rho
+    np.multiply(rho, vx, out=U[1])
+    np.multiply(rho, vy, out=U[2])
+    np.multiply(rho, vz, out=U[3])
+    e = U[4]
+    np.multiply(vx, vx, out=e)
+    e += vy * vy
+    e += vz * vz
+    e *= rho
+    e *= 0.5
+    e += P / (gamma - 1.0)
+    return U
 
 
 def centres(n):
@@ -68,21 +81,31 @@ def sod_noise(n=64, seed=1, gamma=5.0 / 3.0, ny=None, nz=None):
 
 def gaussian_velocity(n, rng, kmin=1.0, kmax=16.0, slope=-4.0, rms=1.0):
     """Gaussian random velocity field: 3D power |v(k)|^2 ~ k^slope on integer
-    kmin<=|k|<=kmax, zero elsewhere; complex normal modes, Hermitian by
-    construction (real inverse FFT); scaled to a 3D rms |v| of ``rms``."""
+    kmin<=|k|<=kmax, zero elsewhere.  For each component, complex normal
+    amplitudes are drawn (in a fixed order) for the modes of the band on the
+    half-spectrum kx >= 0 only, and a real inverse FFT makes the field real
+    (Hermitian by construction); the field is scaled to a 3D rms |v| of ``rms``."""
+    import os
+    import scipy.fft
     k1 = np.fft.fftfreq(n, d=1.0 / n)
     kr = np.fft.rfftfreq(n, d=1.0 / n)
-    KZ, KY, KX = np.meshgrid(k1, k1, kr, indexing="ij")
+    iz = np.nonzero(np.abs(k1) <= kmax)[0]
+    ix = np.nonzero(kr <= kmax)[0]
+    KZ, KY, KX = np.meshgrid(k1[iz], k1[iz], kr[ix], indexing="ij")
     kk = np.sqrt(KX ** 2 + KY ** 2 + KZ ** 2)
-    amp = np.zeros_like(kk)
     band = (kk >= kmin) & (kk <= kmax)
-    amp[band] = kk[band] ** (slope / 2.0)
+    amp = kk[band] ** (slope / 2.0)
+    sel = np.ix_(iz, iz, ix)
     comps = []
     for _ in range(3):
-        c = (rng.normal(size=kk.shape) + 1j * rng.normal(size=kk.shape)) * amp
-        comps.append(np.fft.irfftn(c, s=(n, n, n), axes=(0, 1, 2)))
+        spec = np.zeros((n, n, n // 2 + 1), dtype=np.complex128)
+        blk = np.zeros(kk.shape, dtype=np.complex128)
+        blk[band] = (rng.normal(size=amp.size) + 1j * rng.normal(size=amp.size)) * amp
+        spec[sel] = blk
+        comps.append(scipy.fft.irfftn(spec, s=(n, n, n), axes=(0, 1, 2), workers=os.cpu_count()))
     v = np.stack(comps)
-    v *= rms / np.sqrt((v ** 2).sum(0).mean())
+    ms = sum(float(np.vdot(c, c)) for c in comps) / comps[0].size
+    v *= rms / np.sqrt(ms)
     return v
 
 

@@ -27,6 +27,7 @@ class UniformGrid:
         self.n_patches = npch[0] * npch[1] * npch[2]
         corner, sib, parent, child = A.amr_hydro_uniform_tables(npch)
         self.tables = [torch.from_numpy(a).to(self.device) for a in (corner, sib, parent, child)]
+        self._stage = None
         self.U = [torch.zeros((self.n_patches, 5, 8, 8, 8), dtype=torch.float64, device=self.device)
                   for _ in range(2)]
         A.amr_hydro_set_level(self.ctx, 0, self.n_patches, self.U[0], self.U[1], *self.tables, t=0.0)
@@ -50,23 +51,39 @@ class UniformGrid:
         _, t, _ = A.amr_hydro_get_state(self.ctx, 0)
         return t
 
+    def _staging(self):
+        if self._stage is None:
+            nx, ny, nz = self.shape
+            self._stage = torch.empty((5, nz, ny, nx), dtype=torch.float64, device=self.device)
+        return self._stage
+
+    def _torch_stream(self):
+        if self.stream is None:
+            return torch.cuda.default_stream(self.device)
+        return torch.cuda.ExternalStream(self.stream, device=self.device)
+
     def upload(self, U_dense):
-        """U_dense: [5][nz][ny][nx] float64 (numpy or torch) -> current state."""
-        d = torch.as_tensor(np.ascontiguousarray(U_dense) if isinstance(U_dense, np.ndarray) else U_dense)
-        d = d.to(self.device, torch.float64).contiguous()
-        nx, ny, nz = self.shape
-        A.amr_hydro_pack_uniform(d, nx, ny, nz, self.state(), self.stream)
-        # the state changed: re-register so that cached reductions are dropped
-        cur, t, _ = A.amr_hydro_get_state(self.ctx, 0)
-        if cur == 1:
-            self.U.reverse()
-        A.amr_hydro_set_level(self.ctx, 0, self.n_patches, self.U[0], self.U[1], *self.tables, t=t)
+        """U_dense: [5][nz][ny][nx] float64 (numpy, host or device tensor) ->
+        the current state (copy into a device staging buffer, pack kernel)."""
+        d = torch.from_numpy(np.ascontiguousarray(U_dense)) if isinstance(U_dense, np.ndarray) else U_dense
+        st = self._staging()
+        with torch.cuda.stream(self._torch_stream()):
+            st.copy_(d, non_blocking=d.device.type == "cpu" and d.is_pinned())
+            nx, ny, nz = self.shape
+            A.amr_hydro_pack_uniform(st, nx, ny, nz, self.state(), self.stream)
+        A.amr_hydro_touch_level(self.ctx, 0)
 
     def download(self, out=None):
+        """Current state as [5][nz][ny][nx]: a numpy array, or copied into
+        ``out`` (a host or device tensor; asynchronous for pinned host)."""
         nx, ny, nz = self.shape
-        d = torch.empty((5, nz, ny, nx), dtype=torch.float64, device=self.device)
-        A.amr_hydro_unpack_uniform(self.state(), nx, ny, nz, d, self.stream)
-        return d.cpu().numpy() if out is None else out.copy_(d)
+        st = self._staging()
+        with torch.cuda.stream(self._torch_stream()):
+            A.amr_hydro_unpack_uniform(self.state(), nx, ny, nz, st, self.stream)
+            if out is None:
+                return st.cpu().numpy()
+            out.copy_(st, non_blocking=out.device.type == "cpu" and out.is_pinned())
+            return out
 
     def min_dt(self):
         return A.amr_hydro_min_dt(self.ctx, 0)
