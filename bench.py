@@ -205,7 +205,7 @@ def run_case(torch, A, UniformGrid, U0, n, prec, K, W, stream, want_e2e):
     return out
 
 
-def cpu_baseline(n, steps=3, slab=64):
+def cpu_baseline(n, steps=8, slab=64):
     """The oracle, as it stands, on a bounded sample of the same workload:
     `steps` steps of a periodic n x n x slab box cut from the same seeded
     turbulence field, timed on all host cores."""
