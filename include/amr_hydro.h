@@ -196,6 +196,42 @@ amr_status amr_hydro_step_adjoint(amr_hydro_ctx *ctx, int level, double dt, cons
 
 const char *amr_hydro_strerror(amr_status s);
 
+/*
+ * One step of a uniform periodic grid that allocates no device memory (the
+ * paper has no counterpart: it is a calling convention, not a step of the
+ * method).  For callers that cannot call cudaMalloc -- applications whose
+ * device memory is reserved up front by their own pool allocator, and
+ * latency-critical loops that cannot take the device-wide synchronisation
+ * cudaMalloc/cudaFree may cause -- since a context allocates its scratch.
+ * The step is the one amr_hydro_advance_level runs (same kernel, same
+ * results); its scratch (the per-group neighbour table and the reduction
+ * scalars) lives in a static device array of AMR_NOALLOC_MAX_GROUPS x 64
+ * int32 + 64 bytes (1 MiB) that every GPU loading the library holds until the
+ * process exits.
+ *   U_old, U_new   device FP64 [n_patches][5][8][8][8] in the slot order of
+ *                  amr_hydro_uniform_tables; distinct buffers
+ *   nx, ny, nz     cells per dimension, multiples of 16; at most
+ *                  AMR_NOALLOC_MAX_GROUPS patch groups (nx ny nz / 4096),
+ *                  larger grids are rejected with AMR_E_INVAL and a message
+ *   dh, dt         cell width and time step (dt >= 0, from the host)
+ *   gamma, cfl     adiabatic index and C_CFL; prec an amr_precision
+ *   dt_next_out    device double (may be NULL): Eq. (CFL2) dt of U_new, -1 if
+ *                  a cell is unphysical
+ *   n_unphysical_out  device uint64 (may be NULL): cells of U_new with
+ *                  rho<=0 or P<=0
+ * Asynchronous on cuda_stream.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and configures the kernel;
+ * make that first call before any stream capture.  Every call shares the
+ * array and it keeps the last call's contents (each call rebuilds what it
+ * reads and zeroes what it accumulates into); calls that overlap on the GPU
+ * race on it.
+ */
+#define AMR_NOALLOC_MAX_GROUPS 4096
+amr_status amr_hydro_step_uniform_noalloc(const double *U_old, double *U_new, int nx, int ny, int nz,
+                                          double dh, double dt, double gamma, double cfl, int prec,
+                                          double *dt_next_out, unsigned long long *n_unphysical_out,
+                                          void *cuda_stream);
+
 /* ---- host-side helpers (no device work) ---------------------------------- */
 
 /*

@@ -22,7 +22,7 @@ SYMBOLS = (
     "amr_hydro_regrid_flags", "amr_hydro_conserved_sum", "amr_hydro_set_box",
     "amr_hydro_advance_boxes", "amr_hydro_box_state", "amr_hydro_step_adjoint",
     "amr_hydro_strerror", "amr_hydro_uniform_tables", "amr_hydro_pack_uniform",
-    "amr_hydro_unpack_uniform",
+    "amr_hydro_unpack_uniform", "amr_hydro_step_uniform_noalloc",
 )
 
 
@@ -74,6 +74,9 @@ def lib():
         "amr_hydro_uniform_tables": [_ip, _vp, _vp, _vp, _vp],
         "amr_hydro_pack_uniform": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp],
         "amr_hydro_unpack_uniform": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp],
+        "amr_hydro_step_uniform_noalloc": [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                           _vp, _vp, _vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -215,6 +218,14 @@ def amr_hydro_pack_uniform(dense, nx, ny, nz, patches, stream=None):
 def amr_hydro_unpack_uniform(patches, nx, ny, nz, dense, stream=None):
     check(lib().amr_hydro_unpack_uniform(_p(patches), nx, ny, nz, _p(dense), _p(stream)),
           "amr_hydro_unpack_uniform")
+
+
+def amr_hydro_step_uniform_noalloc(U_old, U_new, nx, ny, nz, dh, dt, gamma, cfl, prec,
+                                   dt_next_out=None, n_unphysical_out=None, stream=None):
+    """One uniform periodic step with no device allocation (static scratch)."""
+    check(lib().amr_hydro_step_uniform_noalloc(_p(U_old), _p(U_new), nx, ny, nz, dh, dt, gamma, cfl, prec,
+                                               _p(dt_next_out), _p(n_unphysical_out), _p(stream)),
+          "amr_hydro_step_uniform_noalloc")
 
 
 def make_params(gamma=5.0 / 3.0, cfl=0.5, root_n=(64, 64, 64), box=None, lmax=0,

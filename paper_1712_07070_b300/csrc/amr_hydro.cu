@@ -103,6 +103,25 @@ amr_status launch_step(amr_hydro_ctx *c, const StepParams &P, int grid) {
     return cuda_fail(cudaGetLastError(), "k_hydro_step launch");
 }
 
+// Launch the step kernel on a stream without a context (grid capped at the
+// resident-CTA count of the current device).  Allocates nothing.
+amr_status launch_step_raw(int prec, const StepParams &P, cudaStream_t stream) {
+    amr_status st = configure_kernels();
+    if (st) return st;
+    if (P.n_work == 0) return AMR_OK;
+    int dev = 0, n_sm = 0;
+    if ((st = cuda_fail(cudaGetDevice(&dev), "cudaGetDevice"))) return st;
+    if ((st = cuda_fail(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev), "sm count")))
+        return st;
+    const int cap = n_sm * step_blocks_per_sm(prec);
+    const int grid = P.n_work < cap ? P.n_work : cap;
+    if (prec == AMR_FP64)
+        k_hydro_step<double><<<grid, STEP_THREADS, sizeof(StepSmem<double>), stream>>>(P);
+    else
+        k_hydro_step<float><<<grid, STEP_THREADS, sizeof(StepSmem<float>), stream>>>(P);
+    return cuda_fail(cudaGetLastError(), "k_hydro_step launch");
+}
+
 }  // namespace amrh
 
 // ---------------------------------------------------------------------------

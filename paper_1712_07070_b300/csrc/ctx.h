@@ -105,6 +105,7 @@ amr_status level_speed(amr_hydro_ctx *c, int level);
 size_t step_smem_bytes(int prec);
 struct StepParams;
 amr_status launch_step(amr_hydro_ctx *c, const StepParams &P, int grid);
+amr_status launch_step_raw(int prec, const StepParams &P, cudaStream_t stream);
 amr_status level_time(amr_hydro_ctx *c, int level);
 // host planning (host_plan.cpp)
 amr_status build_uniform_tables(const int np[3], int32_t *corner, int32_t *sib, int32_t *parent,
