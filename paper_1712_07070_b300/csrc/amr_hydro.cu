@@ -144,7 +144,7 @@ __global__ void k_max_speed(const double *__restrict__ U, int64_t n_slots, doubl
         const int64_t s = i / PV, c = i % PV;
         real u[NV];
 #pragma unroll
-        for (int v = 0; v < NV; v++) u[v] = (real)U[s * PSLOT + v * PV + c];
+        for (int v = 0; v < NV; v++) u[v] = to_real<real>(U[s * PSLOT + v * PV + c]);
         bool ok;
         const real sp = cfl_speed(u, g, ok);
         if (!ok) bad++;

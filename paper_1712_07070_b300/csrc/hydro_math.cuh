@@ -11,14 +11,43 @@ namespace amrh {
 
 constexpr int NV = 5;
 
-// Reciprocal and square root per compute type.  FP64 uses IEEE-rounded
-// division and sqrt; FP32 uses the hardware approximations (about 1 ulp),
-// well inside the FP32 mode's 1e-5 tolerance.
-__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+// ---- reciprocal, reciprocal square root, square root -------------------------
+//
+// FP64: on this GPU the FP64 pipe issues 2 operations per clock per SM, and an
+// IEEE division costs about nine of them.  The reciprocal is instead seeded by
+// the special-function unit's approximate reciprocal (rcp.approx.ftz.f64,
+// which runs on a separate, much wider unit) and refined by two Newton-Raphson
+// steps for f(r) = 1/r - x, r <- r + r (1 - x r): each step squares the
+// relative error, so two steps from the seed reach the FP64 rounding level (a
+// few ulp, well inside the 1e-12 tolerance; checked against IEEE division in
+// the tests).  The reciprocal square root is refined the same way with the
+// Newton step for f(y) = 1/y^2 - x, y <- y (3 - x y^2)/2.
+// FP32: the hardware approximations (about 1 ulp), inside the FP32 mode's
+// 1e-5 tolerance.
+__device__ __forceinline__ double rcp_(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+__device__ __forceinline__ double rsqrt_(double x) {
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double hx = 0.5 * x;
+    y = y * fma(-hx, y * y, 1.5);
+    return y * fma(-hx, y * y, 1.5);
+}
 __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 __device__ __forceinline__ float rcp_(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
 __device__ __forceinline__ float sqrt_(float x) {
@@ -27,20 +56,54 @@ __device__ __forceinline__ float sqrt_(float x) {
     return r;
 }
 
+// ---- FP64 <-> FP32 without the FP64 pipe ---------------------------------------
+//
+// cvt between double and float issues on the FP64 pipe; in the FP32 mode that
+// made conversions the bottleneck, so they are done on the integer units from
+// the IEEE-754 bit layouts (sign | exponent | fraction; biases 1023 and 127).
+// double -> float: round half away from zero on the first dropped fraction
+// bit; magnitudes below 2^-126 flush to zero (the FP32 mode runs with
+// flush-to-zero); finite inputs above the float range are not expected.
+__device__ __forceinline__ float d2f_bits(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    unsigned r = ((hi << 3) | (lo >> 29)) - (896u << 23);
+    r += (lo >> 28) & 1u;
+    r = e > 896u ? r : 0u;
+    return __uint_as_float(r | (hi & 0x80000000u));
+}
+// float -> double: exact (flushed float zeros map to signed zeros).
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned s = b & 0x80000000u, mag = b & 0x7fffffffu;
+    const unsigned hi = mag >= 0x00800000u ? (s | ((mag >> 3) + (896u << 20))) : s;
+    const unsigned lo = mag >= 0x00800000u ? (b << 29) : 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+template <typename real>
+__device__ __forceinline__ real to_real(double x);
+template <>
+__device__ __forceinline__ double to_real<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float to_real<float>(double x) { return d2f_bits(x); }
+
 template <typename real>
 struct Gas {
     real gamma, gm1, inv_gm1;
 };
 
-// U -> W
+// U -> W; also returns 1/rho for reuse.
 template <typename real>
-__device__ __forceinline__ void u2w(const real u[NV], real w[NV], const Gas<real> &g) {
+__device__ __forceinline__ real u2w(const real u[NV], real w[NV], const Gas<real> &g) {
     const real ri = rcp_(u[0]);
     w[0] = u[0];
     w[1] = u[1] * ri;
     w[2] = u[2] * ri;
     w[3] = u[3] * ri;
     w[4] = g.gm1 * (u[4] - real(0.5) * u[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]));
+    return ri;
 }
 
 // W -> U
@@ -74,22 +137,34 @@ __device__ __forceinline__ void phys_flux(const real w[NV], const real u[NV], re
 
 // HLLC flux through a face normal to D (Einfeldt/Roe outer speeds, Toro's
 // star states; ties: S_L>=0 -> F_L, S_R<=0 -> F_R, S*>=0 -> F*_L).
+// Reciprocals are shared: 1/rho from one reciprocal square root per side,
+// which also gives the Roe weight sqrt(rho).
 template <int D, typename real>
 __device__ __forceinline__ void hllc(const real uL[NV], const real uR[NV], real F[NV],
                                      const Gas<real> &g) {
+    const real yl = rsqrt_(uL[0]), yr = rsqrt_(uR[0]);  // 1/sqrt(rho)
+    const real ril = yl * yl, rir = yr * yr;            // 1/rho
+    const real sl = uL[0] * yl, sr = uR[0] * yr;        // sqrt(rho)
     real wL[NV], wR[NV];
-    u2w(uL, wL, g);
-    u2w(uR, wR, g);
+    wL[0] = uL[0];
+    wL[1] = uL[1] * ril;
+    wL[2] = uL[2] * ril;
+    wL[3] = uL[3] * ril;
+    wL[4] = g.gm1 * (uL[4] - real(0.5) * uL[0] * (wL[1] * wL[1] + wL[2] * wL[2] + wL[3] * wL[3]));
+    wR[0] = uR[0];
+    wR[1] = uR[1] * rir;
+    wR[2] = uR[2] * rir;
+    wR[3] = uR[3] * rir;
+    wR[4] = g.gm1 * (uR[4] - real(0.5) * uR[0] * (wR[1] * wR[1] + wR[2] * wR[2] + wR[3] * wR[3]));
     const real rl = wL[0], pl = wL[4], ul = wL[1 + D];
     const real rr = wR[0], pr = wR[4], ur = wR[1 + D];
-    const real cl = sqrt_(g.gamma * pl / rl);
-    const real cr = sqrt_(g.gamma * pr / rr);
-    const real sl = sqrt_(rl), sr = sqrt_(rr);
+    const real cl = sqrt_(g.gamma * pl * ril);
+    const real cr = sqrt_(g.gamma * pr * rir);
     const real iw = rcp_(sl + sr);
     const real vtx = (sl * wL[1] + sr * wR[1]) * iw;
     const real vty = (sl * wL[2] + sr * wR[2]) * iw;
     const real vtz = (sl * wL[3] + sr * wR[3]) * iw;
-    const real hl = (uL[4] + pl) / rl, hr = (uR[4] + pr) / rr;
+    const real hl = (uL[4] + pl) * ril, hr = (uR[4] + pr) * rir;
     const real ht = (sl * hl + sr * hr) * iw;
     const real ct = sqrt_(g.gm1 * (ht - real(0.5) * (vtx * vtx + vty * vty + vtz * vtz)));
     const real vtn = D == 0 ? vtx : (D == 1 ? vty : vtz);
@@ -108,23 +183,25 @@ __device__ __forceinline__ void hllc(const real uL[NV], const real uR[NV], real 
         phys_flux<D>(wR, uR, F);
         return;
     }
-    const real Ss = (pr - pl + rl * ul * (SL - ul) - rr * ur * (SR - ur)) /
-                    (rl * (SL - ul) - rr * (SR - ur));
+    const real ml = rl * (SL - ul), mr = rr * (SR - ur);  // mass fluxes relative to the waves
+    const real Ss = (pr - pl + ml * ul - mr * ur) * rcp_(ml - mr);
     const bool left = Ss >= real(0);
     const real *uK = left ? uL : uR;
     const real *wK = left ? wL : wR;
     const real SK = left ? SL : SR;
-    const real rK = wK[0], uKn = wK[1 + D], pK = wK[4];
+    const real mK = left ? ml : mr;
+    const real riK = left ? ril : rir;
+    const real uKn = wK[1 + D], pK = wK[4];
     real fK[NV];
     phys_flux<D>(wK, uK, fK);
-    const real fac = rK * (SK - uKn) / (SK - Ss);
+    const real fac = mK * rcp_(SK - Ss);
     real us[NV];
     us[0] = fac;
     us[1] = fac * wK[1];
     us[2] = fac * wK[2];
     us[3] = fac * wK[3];
     us[1 + D] = fac * Ss;
-    us[4] = fac * (uK[4] / rK + (Ss - uKn) * (Ss + pK / (rK * (SK - uKn))));
+    us[4] = fac * (uK[4] * riK + (Ss - uKn) * (Ss + pK * rcp_(mK)));
 #pragma unroll
     for (int v = 0; v < NV; v++) F[v] = fK[v] + SK * (us[v] - uK[v]);
 }
@@ -134,9 +211,9 @@ __device__ __forceinline__ void hllc(const real uL[NV], const real uR[NV], real 
 template <typename real>
 __device__ __forceinline__ real cfl_speed(const real u[NV], const Gas<real> &g, bool &ok) {
     real w[NV];
-    u2w(u, w, g);
+    const real ri = u2w(u, w, g);
     ok = (w[0] > real(0)) && (w[4] > real(0));
-    return fabs(w[1]) + fabs(w[2]) + fabs(w[3]) + real(3) * sqrt_(g.gamma * w[4] * rcp_(w[0]));
+    return fabs(w[1]) + fabs(w[2]) + fabs(w[3]) + real(3) * sqrt_(g.gamma * w[4] * ri);
 }
 
 }  // namespace amrh

@@ -92,7 +92,7 @@ __device__ __forceinline__ void load_plane(StepSmem<real> &S, const StepParams &
         if (src) {
             const int off = lz * 64 + ly * 8 + lx;
 #pragma unroll
-            for (int v = 0; v < NV; v++) u[v] = (real)__ldg(src + v * PV + off);
+            for (int v = 0; v < NV; v++) u[v] = to_real<real>(__ldg(src + v * PV + off));
             u2w(u, w, g);
         } else {  // a position no stencil reads (a tile corner): benign state
             w[0] = real(1); w[1] = w[2] = w[3] = real(0); w[4] = real(1);
@@ -173,8 +173,9 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_hydro_step(StepParams P) {
     __syncthreads();
     const double dt = S.dt;
     const double dtdh = dt / P.dh;
+    const real dtdh_r = (real)dtdh;
     const real dtdh_half = (real)(0.5 * dt / P.dh);
-    double smax = 0.0;
+    real smax_r = real(0);
     unsigned nbad = 0;
 
     for (int wi = blockIdx.x; wi < P.n_work; wi += gridDim.x) {
@@ -185,9 +186,9 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_hydro_step(StepParams P) {
         load_plane(S, P, -1, g);
 
         real zp_prev[NV];   // high z face state of this column's cell at z-1
-        double acc[NV];     // flux divergence of this column's cell at z-1 (minus its top z flux)
+        real acc[NV];       // flux divergence of this column's cell at z-1 (minus its top z flux)
 #pragma unroll
-        for (int v = 0; v < NV; v++) { zp_prev[v] = real(0); acc[v] = 0.0; }
+        for (int v = 0; v < NV; v++) { zp_prev[v] = real(0); acc[v] = real(0); }
 
         for (int z = -1; z <= GE; z++) {
             load_plane(S, P, z + 1, g);
@@ -277,27 +278,34 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_hydro_step(StepParams P) {
                 const int zc = z - 1;
                 const int64_t base = (own + (cx >> 3) + 2 * (cy >> 3) + 4 * (zc >> 3)) * PSLOT +
                                      (zc & 7) * 64 + (cy & 7) * 8 + (cx & 7);
-                double un[NV];
+                real ur[NV];  // the new state in the compute type, for its signal speed
 #pragma unroll
                 for (int v = 0; v < NV; v++) {
-                    const double tot = acc[v] + (double)fz[v];
-                    un[v] = P.U_old[base + v * PV] - dtdh * tot;
-                    P.U_new[base + v * PV] = un[v];
+                    const real tot = acc[v] + fz[v];
+                    const double uo = P.U_old[base + v * PV];
+                    double un;
+                    if constexpr (sizeof(real) == sizeof(double)) {
+                        un = uo - dtdh * tot;
+                        ur[v] = un;
+                    } else {
+                        // FP32 increment accumulated into the FP64 state
+                        const real inc = dtdh_r * tot;
+                        un = uo - f2d_bits(inc);
+                        ur[v] = d2f_bits(uo) - inc;
+                    }
+                    P.U_new[base + v * PV] = un;
                 }
-                real ur[NV];
-#pragma unroll
-                for (int v = 0; v < NV; v++) ur[v] = (real)un[v];
                 bool ok;
                 const real s = cfl_speed(ur, g, ok);
                 if (!ok) nbad++;
-                if ((double)s > smax) smax = (double)s;
+                if (s > smax_r) smax_r = s;
             }
             if (z >= 0 && z < GE) {
 #pragma unroll
                 for (int v = 0; v < NV; v++) {
                     const real dxy = (S.FX[v][cy][cx + 1] - S.FX[v][cy][cx]) +
                                      (S.FY[v][cy + 1][cx] - S.FY[v][cy][cx]);
-                    acc[v] = (double)dxy - (double)fz[v];
+                    acc[v] = dxy - fz[v];
                 }
             }
 #pragma unroll
@@ -307,6 +315,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_hydro_step(StepParams P) {
     }
 
     // ---- block reduction of the signal speed, one atomic per block
+    double smax = (double)smax_r;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
     unsigned nb = nbad;
