@@ -180,8 +180,18 @@ double or_dt_cfl2(const double *U, int64_t ncell, double gamma, double cfl, doub
  * U, Unew: [5][nz][ny][nx] FP64.  dh: cell width, dt: time step.
  * Returns the number of cells of Unew with rho<=0 or P<=0.
  */
+int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int nz,
+                            double dh, double dt, double gamma, double *FX_out);
+
 int64_t or_step_periodic(const double *U, double *Unew, int nx, int ny, int nz,
                          double dh, double dt, double gamma) {
+    return or_step_periodic_fx(U, Unew, nx, ny, nz, dh, dt, gamma, NULL);
+}
+
+/* Same step; if FX_out is not NULL it receives the interface fluxes
+ * FX_out[d][var][cell] through the high face (i+1/2 along d) of every cell. */
+int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int nz,
+                            double dh, double dt, double gamma, double *FX_out) {
     const int64_t n = (int64_t)nx * ny * nz;
     const int dims[3] = {nx, ny, nz};
     double *W = (double *)malloc(sizeof(double) * NV * n);
@@ -282,6 +292,7 @@ int64_t or_step_periodic(const double *U, double *Unew, int nx, int ny, int nz,
                 if (!(w[0] > 0.0) || !(w[4] > 0.0)) nbad++;
             }
 
+    if (FX_out) memcpy(FX_out, FX, sizeof(double) * 3 * NV * n);
     free(W);
     free(FS);
     free(FX);
