@@ -103,7 +103,51 @@ amr_status amr_hydro_destroy(amr_hydro_ctx *ctx);
 amr_status amr_hydro_set_level(amr_hydro_ctx *ctx, int level, int n_patches,
                                double *U_a, double *U_b, const int32_t *corner,
                                const int32_t *sib, const int32_t *parent,
-                               const int32_t *child_group, double t);
+                               int32_t *child_group, double t);
+
+/*
+ * Levels built by regridding (AMR runs).  bind_level registers caller-owned
+ * capacity arrays for level 1..lmax, each sized for max_patches slots
+ * (U_a, U_b [max_patches][5][8][8][8] FP64; corner [max_patches][3], sib
+ * [max_patches][26], parent, child_group [max_patches] int32, layouts as in
+ * amr_hydro_set_level).  The level starts empty; amr_hydro_regrid fills the
+ * tables and the state and rewrites them at every regrid.  The child_group
+ * array given to amr_hydro_set_level for level 0 is rewritten in the same way.
+ */
+amr_status amr_hydro_bind_level(amr_hydro_ctx *ctx, int level, double *U_a, double *U_b,
+                                int32_t *corner, int32_t *sib, int32_t *parent,
+                                int32_t *child_group);
+
+/*
+ * Rebuild level+1 from the refinement flags of `level` at its current time
+ * (section 2.1): cell criterion and flag buffer (amr_hydro_regrid_flags);
+ * a patch gains children only if all 26 sibling positions hold patches
+ * (proper nesting); a refined patch keeps its children while any
+ * level-(level+1) patch with children has a 26-neighbour position inside it;
+ * other unflagged patches lose their children (no explicit derefinement
+ * criterion).  Kept children keep their data; new children are interpolated
+ * from the parent level (conservative minmod-limited linear interpolation of
+ * the conserved variables, with all eight children of a coarse cell falling
+ * back to the coarse value when any would have rho<=0 or P<=0).  Groups are
+ * numbered in the order of their parents' corners (z, then y, then x).
+ * Synchronises.  AMR_E_NOMEM if the new level exceeds max_patches.
+ */
+amr_status amr_hydro_regrid(amr_hydro_ctx *ctx, int level);
+
+/*
+ * One root-level step of the adaptive time-step W-cycle (section 2.1):
+ * level l takes steps dt_l = Eq. (CFL2) until it reaches its parent's time;
+ * dt_l grows by up to C_inc to land exactly on the parent's time, or shrinks
+ * by up to C_dec to twice the child level's last step; after each step of
+ * level l its child level catches up, then flux fix-up + restriction and the
+ * regrid of level l+1.  dt0 > 0 fixes the root step, else Eq. (CFL2).
+ * cell_updates (may be NULL) receives the number of cell updates of all
+ * levels.  Synchronises the host once per level step (for its dt).
+ */
+amr_status amr_hydro_advance_root(amr_hydro_ctx *ctx, double dt0, int64_t *cell_updates);
+
+/* Patch and coarse-fine ghost-patch counts of a level. */
+amr_status amr_hydro_level_info(amr_hydro_ctx *ctx, int level, int *n_patches, int *n_ghost);
 
 /* Report which registered buffer holds the level's newest state (0 = U_a,
  * 1 = U_b) and the times of the newest and previous states. */

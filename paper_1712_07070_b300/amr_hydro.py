@@ -22,7 +22,8 @@ SYMBOLS = (
     "amr_hydro_regrid_flags", "amr_hydro_conserved_sum", "amr_hydro_set_box",
     "amr_hydro_advance_boxes", "amr_hydro_box_state", "amr_hydro_step_adjoint",
     "amr_hydro_strerror", "amr_hydro_uniform_tables", "amr_hydro_pack_uniform",
-    "amr_hydro_unpack_uniform", "amr_hydro_step_uniform_noalloc",
+    "amr_hydro_unpack_uniform", "amr_hydro_step_uniform_noalloc", "amr_hydro_bind_level",
+    "amr_hydro_regrid", "amr_hydro_advance_root", "amr_hydro_level_info",
 )
 
 
@@ -74,6 +75,10 @@ def lib():
         "amr_hydro_uniform_tables": [_ip, _vp, _vp, _vp, _vp],
         "amr_hydro_pack_uniform": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp],
         "amr_hydro_unpack_uniform": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp],
+        "amr_hydro_bind_level": [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp],
+        "amr_hydro_regrid": [_vp, ctypes.c_int],
+        "amr_hydro_advance_root": [_vp, ctypes.c_double, _i64p],
+        "amr_hydro_level_info": [_vp, ctypes.c_int, _ip, _ip],
         "amr_hydro_step_uniform_noalloc": [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                            _vp, _vp, _vp],
@@ -226,6 +231,28 @@ def amr_hydro_step_uniform_noalloc(U_old, U_new, nx, ny, nz, dh, dt, gamma, cfl,
     check(lib().amr_hydro_step_uniform_noalloc(_p(U_old), _p(U_new), nx, ny, nz, dh, dt, gamma, cfl, prec,
                                                _p(dt_next_out), _p(n_unphysical_out), _p(stream)),
           "amr_hydro_step_uniform_noalloc")
+
+
+def amr_hydro_bind_level(ctx, level, U_a, U_b, corner, sib, parent, child_group):
+    check(lib().amr_hydro_bind_level(ctx, level, _p(U_a), _p(U_b), _p(corner), _p(sib), _p(parent),
+                                     _p(child_group)), "amr_hydro_bind_level")
+
+
+def amr_hydro_regrid(ctx, level):
+    check(lib().amr_hydro_regrid(ctx, level), "amr_hydro_regrid")
+
+
+def amr_hydro_advance_root(ctx, dt0=-1.0):
+    """One root step of the W-cycle; returns the number of cell updates."""
+    n = ctypes.c_int64()
+    check(lib().amr_hydro_advance_root(ctx, dt0, ctypes.byref(n)), "amr_hydro_advance_root")
+    return n.value
+
+
+def amr_hydro_level_info(ctx, level):
+    n, g = ctypes.c_int(), ctypes.c_int()
+    check(lib().amr_hydro_level_info(ctx, level, ctypes.byref(n), ctypes.byref(g)), "amr_hydro_level_info")
+    return n.value, g.value
 
 
 def make_params(gamma=5.0 / 3.0, cfl=0.5, root_n=(64, 64, 64), box=None, lmax=0,

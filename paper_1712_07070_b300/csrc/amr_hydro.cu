@@ -60,6 +60,7 @@ template struct DevBuf<int32_t>;
 template struct DevBuf<int64_t>;
 template struct DevBuf<double>;
 template struct DevBuf<unsigned long long>;
+template struct DevBuf<uint8_t>;
 
 size_t step_smem_bytes(int prec) {
     return prec == AMR_FP64 ? sizeof(StepSmem<double>) : sizeof(StepSmem<float>);
@@ -238,6 +239,10 @@ amr_status amr_hydro_destroy(amr_hydro_ctx *c) {
     c->box_plan.release();
     c->scal.release();
     c->dtbuf.release();
+    c->cflag.release();
+    c->pflag.release();
+    c->psum.release();
+    c->regrid_tmp.release();
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     delete c;
     return AMR_OK;

@@ -1,53 +1,360 @@
-// amr_ops.cu -- coarse-fine operations of the AMR hierarchy (GAMER-2
-// sections 2.1-2.2, 3.2): ghost interpolation, flux fix-up, restriction,
-// refinement flags, conservation sums.
+// amr_ops.cu -- device operations between AMR levels (GAMER-2 section 2.1:
+// refinement flags and flag buffers; section 2.2: restriction and coarse-fine
+// flux fix-up; section 3.2: ghost zones interpolated from coarse patches).
 #include <cuda_runtime.h>
+
+#include <cstring>
+#include <vector>
 
 #include "amr_hydro.h"
 #include "ctx.h"
+#include "step_kernel.cuh"
 
 using namespace amrh;
 
-namespace amrh {
-amr_status fill_ghost_impl(amr_hydro_ctx *c, int level, double t) {
-    (void)c; (void)level; (void)t;
-    return AMR_E_INVAL;
+namespace {
+
+__device__ __forceinline__ double minmod(double a, double b) {
+    if (!(a * b > 0.0)) return 0.0;
+    return fabs(a) < fabs(b) ? a : b;
 }
+
+// The 27 coarse patches around coarse patch P (index (dx+1)+3(dy+1)+9(dz+1),
+// 13 = P itself), from the coarse level's sibling table.
+__device__ __forceinline__ void load_block27(int *nb, int P, const int32_t *csib) {
+    for (int k = threadIdx.x; k < 27; k += blockDim.x) nb[k] = k == 13 ? P : csib[(int64_t)P * 26 + k - (k > 13)];
+}
+
+struct CoarseView {
+    const double *Uo, *Un;
+    double w;
+    const int *nb;  // 27 slots around the parent
+    // coarse value of variable v at coarse cell c (relative to the parent's
+    // origin, each coordinate in -8..15), time-interpolated
+    __device__ __forceinline__ double at(int v, int cx, int cy, int cz) const {
+        const int px = cx >> 3, py = cy >> 3, pz = cz >> 3;
+        int s = nb[(px + 1) + 3 * (py + 1) + 9 * (pz + 1)];
+        if (s < 0) s = nb[13];  // cannot happen on a properly nested hierarchy
+        const int64_t i = (int64_t)s * PSLOT + v * PV + (cz & 7) * 64 + (cy & 7) * 8 + (cx & 7);
+        if (w == 0.0) return Uo[i];
+        if (w == 1.0) return Un[i];
+        return Uo[i] + w * (Un[i] - Uo[i]);
+    }
+};
+
+// Conservative minmod-limited linear interpolation of the conserved
+// variables at fine cell f (relative to the parent's fine origin), with the
+// positivity fallback: if any of the eight children of the coarse cell would
+// have rho <= 0 or P <= 0, all eight take the coarse value.
+__device__ void interp_fine_cell(const CoarseView &C, int fx, int fy, int fz, double out[NV]) {
+    const int cx = fx >> 1, cy = fy >> 1, cz = fz >> 1;
+    double c[NV], sl[3][NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        c[v] = C.at(v, cx, cy, cz);
+        sl[0][v] = minmod(C.at(v, cx + 1, cy, cz) - c[v], c[v] - C.at(v, cx - 1, cy, cz));
+        sl[1][v] = minmod(C.at(v, cx, cy + 1, cz) - c[v], c[v] - C.at(v, cx, cy - 1, cz));
+        sl[2][v] = minmod(C.at(v, cx, cy, cz + 1) - c[v], c[v] - C.at(v, cx, cy, cz - 1));
+    }
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const double sx = (k & 1) ? 0.25 : -0.25, sy = (k & 2) ? 0.25 : -0.25, sz = (k & 4) ? 0.25 : -0.25;
+        double u[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) u[v] = c[v] + sx * sl[0][v] + sy * sl[1][v] + sz * sl[2][v];
+        const double m2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+        ok = ok && (u[0] > 0.0) && (2.0 * u[0] * u[4] > m2);
+    }
+    const double sx = (fx & 1) ? 0.25 : -0.25, sy = (fy & 1) ? 0.25 : -0.25, sz = (fz & 1) ? 0.25 : -0.25;
+#pragma unroll
+    for (int v = 0; v < NV; v++) out[v] = ok ? c[v] + sx * sl[0][v] + sy * sl[1][v] + sz * sl[2][v] : c[v];
+}
+
+// Fine patches interpolated from the coarse level.  Job j: info[4j..4j+3] =
+// (coarse parent P of the group the patch is placed around, patch position
+// q relative to that group, each -1..2); output patch out_slot[j] (or j).
+__global__ void k_interp_patches(double *__restrict__ out, const int32_t *__restrict__ out_slot,
+                                 const int32_t *__restrict__ info, int n_jobs, const double *Uo,
+                                 const double *Un, double w, const int32_t *__restrict__ csib) {
+    __shared__ int nb[27];
+    for (int j = blockIdx.x; j < n_jobs; j += gridDim.x) {
+        const int P = info[4 * j], qx = info[4 * j + 1], qy = info[4 * j + 2], qz = info[4 * j + 3];
+        __syncthreads();
+        load_block27(nb, P, csib);
+        __syncthreads();
+        CoarseView C{Uo, Un, w, nb};
+        double *o = out + (int64_t)(out_slot ? out_slot[j] : j) * PSLOT;
+        for (int i = threadIdx.x; i < PV; i += blockDim.x) {
+            const int lx = i & 7, ly = (i >> 3) & 7, lz = i >> 6;
+            double u[NV];
+            interp_fine_cell(C, qx * 8 + lx, qy * 8 + ly, qz * 8 + lz, u);
+#pragma unroll
+            for (int v = 0; v < NV; v++) o[v * PV + i] = u[v];
+        }
+    }
+}
+
+// Coarse-fine flux fix-up (section 2.2).  Entry e: fix[13e] = coarse leaf
+// patch Q, fix[13e+1+f] = coarse register block of face f (-1: none),
+// fix[13e+7+f] = the fine register block (of the refined neighbour's child
+// group) of the same interface.  Faces in the order -x,+x,-y,+y,-z,+z: a
+// high face subtracts (dt_f-sum - dt_c F_c)/dh, a low face adds it.
+__global__ void k_cf_fixup(double *__restrict__ U, const int64_t *__restrict__ fix, int n_fix,
+                           const double *__restrict__ creg, const double *__restrict__ freg, double dh) {
+    for (int e = blockIdx.x; e < n_fix; e += gridDim.x) {
+        const int64_t *F = fix + 13 * (int64_t)e;
+        const int64_t Q = F[0];
+        for (int f = 0; f < 6; f++) {
+            const int64_t co = F[1 + f], fo = F[7 + f];
+            if (co >= 0) {
+                const int d = f >> 1, hi = f & 1;
+                for (int i = threadIdx.x; i < 64 * NV; i += blockDim.x) {
+                    const int v = i / 64, t2 = (i >> 3) & 7, t1 = i & 7;
+                    const double *B = freg + fo + (int64_t)v * 256;
+                    const double fsum = 0.25 * (((B[(2 * t2) * 16 + 2 * t1] + B[(2 * t2) * 16 + 2 * t1 + 1]) +
+                                                 B[(2 * t2 + 1) * 16 + 2 * t1]) +
+                                                B[(2 * t2 + 1) * 16 + 2 * t1 + 1]);
+                    const double corr = (fsum - creg[co + (int64_t)v * 64 + t2 * 8 + t1]) / dh;
+                    const int a = hi ? 7 : 0;
+                    int x, y, z;
+                    if (d == 0) { x = a; y = t1; z = t2; }
+                    else if (d == 1) { x = t1; y = a; z = t2; }
+                    else { x = t1; y = t2; z = a; }
+                    double &u = U[Q * PSLOT + v * PV + z * 64 + y * 8 + x];
+                    u = hi ? u - corr : u + corr;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Restriction (section 2.2): entry e = (coarse patch P, its child group G);
+// each coarse cell becomes the mean of its 8 children (x fastest, then y, z).
+__global__ void k_restrict(double *__restrict__ Uc, const double *__restrict__ Uf, const int32_t *__restrict__ list,
+                           int n) {
+    for (int e = blockIdx.x; e < n; e += gridDim.x) {
+        const int64_t P = list[2 * e], G = list[2 * e + 1];
+        for (int i = threadIdx.x; i < PV * NV; i += blockDim.x) {
+            const int v = i / PV, c = i % PV;
+            const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
+            double s = 0.0;
+            for (int dz = 0; dz < 2; dz++)
+                for (int dy = 0; dy < 2; dy++)
+                    for (int dx = 0; dx < 2; dx++) {
+                        const int fx = 2 * x + dx, fy = 2 * y + dy, fz = 2 * z + dz;
+                        const int64_t slot = 8 * G + (fx >> 3) + 2 * (fy >> 3) + 4 * (fz >> 3);
+                        s += Uf[slot * PSLOT + v * PV + (fz & 7) * 64 + (fy & 7) * 8 + (fx & 7)];
+                    }
+            Uc[P * PSLOT + v * PV + c] = s * 0.125;
+        }
+    }
+}
+
+// Cell flags (section 2.1 refinement criterion, FP64 in every mode):
+// sum_d ((rho_{+d} - rho_{-d})/2)^2 > theta^2 rho^2; neighbours through the
+// group's 4x4x4 source table (same-level or interpolated ghost patches).
+__global__ void k_flag_cells(const double *__restrict__ U, const double *__restrict__ ghost,
+                             const int32_t *__restrict__ nbr, int n_groups, double theta,
+                             uint8_t *__restrict__ cflag) {
+    __shared__ int src[64];
+    for (int g = blockIdx.x; g < n_groups; g += gridDim.x) {
+        __syncthreads();
+        if (threadIdx.x < 64) src[threadIdx.x] = nbr[(int64_t)g * 64 + threadIdx.x];
+        __syncthreads();
+        auto rho_at = [&](int x, int y, int z) -> double {
+            const int q = ((x + 8) >> 3) + 4 * ((y + 8) >> 3) + 16 * ((z + 8) >> 3);
+            const int s = src[q];
+            const int off = ((z + 8) & 7) * 64 + ((y + 8) & 7) * 8 + ((x + 8) & 7);
+            if (s >= 0) return U[(int64_t)s * PSLOT + off];
+            if (s <= -2) return ghost[(int64_t)(-2 - s) * PSLOT + off];
+            return 1.0;  // a corner position: the +-1 stencil never reaches it
+        };
+        for (int i = threadIdx.x; i < 4096; i += blockDim.x) {
+            const int x = i & 15, y = (i >> 4) & 15, z = i >> 8;
+            const double r = rho_at(x, y, z);
+            const double gx = (rho_at(x + 1, y, z) - rho_at(x - 1, y, z)) / 2.0;
+            const double gy = (rho_at(x, y + 1, z) - rho_at(x, y - 1, z)) / 2.0;
+            const double gz = (rho_at(x, y, z + 1) - rho_at(x, y, z - 1)) / 2.0;
+            double g2 = gx * gx;
+            g2 += gy * gy;
+            g2 += gz * gz;
+            const int64_t slot = 8 * (int64_t)g + (x >> 3) + 2 * (y >> 3) + 4 * (z >> 3);
+            cflag[slot * PV + (z & 7) * 64 + (y & 7) * 8 + (x & 7)] = (uint8_t)(g2 > theta * theta * (r * r));
+        }
+    }
+}
+
+// Patch flags with the flag buffer: patch P is flagged when a flagged cell of
+// P or of a sibling lies within Chebyshev distance nbuf (<= 8) of P.
+__global__ void k_flag_patches(const uint8_t *__restrict__ cflag, const int32_t *__restrict__ sib, int n_patches,
+                               int nbuf, uint8_t *__restrict__ pflag) {
+    __shared__ int nb[27];
+    __shared__ int hit;
+    for (int P = blockIdx.x; P < n_patches; P += gridDim.x) {
+        __syncthreads();
+        load_block27(nb, P, sib);
+        if (threadIdx.x == 0) hit = 0;
+        __syncthreads();
+        const int W = 8 + 2 * nbuf;
+        int local = 0;
+        for (int i = threadIdx.x; i < W * W * W && !local; i += blockDim.x) {
+            const int x = i % W - nbuf, y = (i / W) % W - nbuf, z = i / (W * W) - nbuf;
+            const int s = nb[((x >> 3) + 1) + 3 * ((y >> 3) + 1) + 9 * ((z >> 3) + 1)];
+            if (s >= 0 && cflag[(int64_t)s * PV + (z & 7) * 64 + (y & 7) * 8 + (x & 7)]) local = 1;
+        }
+        if (local) hit = 1;
+        __syncthreads();
+        if (threadIdx.x == 0) pflag[P] = (uint8_t)hit;
+    }
+}
+
+// Per-patch sums of the conserved variables (fixed-order tree in the block).
+__global__ void k_patch_sums(const double *__restrict__ U, int n_patches, double *__restrict__ out) {
+    __shared__ double red[NV][256];
+    for (int P = blockIdx.x; P < n_patches; P += gridDim.x) {
+        double s[NV] = {0, 0, 0, 0, 0};
+        for (int c = threadIdx.x; c < PV; c += 256)
+#pragma unroll
+            for (int v = 0; v < NV; v++) s[v] += U[(int64_t)P * PSLOT + v * PV + c];
+#pragma unroll
+        for (int v = 0; v < NV; v++) red[v][threadIdx.x] = s[v];
+        __syncthreads();
+        for (int h = 128; h > 0; h >>= 1) {
+            if (threadIdx.x < h)
+#pragma unroll
+                for (int v = 0; v < NV; v++) red[v][threadIdx.x] += red[v][threadIdx.x + h];
+            __syncthreads();
+        }
+        if (threadIdx.x < NV) out[(int64_t)P * NV + threadIdx.x] = red[threadIdx.x][0];
+        __syncthreads();
+    }
+}
+
+// dst[s] = src[map[s]] for every slot s with map[s] >= 0.
+__global__ void k_copy_slots(double *__restrict__ dst, const double *__restrict__ src,
+                             const int32_t *__restrict__ map, int n) {
+    for (int s = blockIdx.x; s < n; s += gridDim.x) {
+        const int m = map[s];
+        if (m < 0) continue;
+        for (int i = threadIdx.x; i < PSLOT; i += blockDim.x) dst[(int64_t)s * PSLOT + i] = src[(int64_t)m * PSLOT + i];
+    }
+}
+
+}  // namespace
+
+namespace amrh {
+
+// time weight of the coarse level at fine time t
+static double coarse_weight(const Level &C, double t) {
+    if (C.t == C.t_prev || t == C.t) return 1.0;
+    return (t - C.t_prev) / (C.t - C.t_prev);
+}
+
+amr_status fill_ghost_impl(amr_hydro_ctx *c, int level, double t) {
+    Level &L = c->lv[level];
+    if (!L.n_ghost) return AMR_OK;
+    if (level == 0) return AMR_E_NESTING;
+    Level &C = c->lv[level - 1];
+    amr_status st = level_time(c, level - 1);
+    if (st) return st;
+    const double w = coarse_weight(C, t);
+    const int grid = L.n_ghost < 4 * c->n_sm ? L.n_ghost : 4 * c->n_sm;
+    k_interp_patches<<<grid, 256, 0, c->stream>>>(L.ghost.p, nullptr, L.ghost_info.p, L.n_ghost, C.U[1 - C.cur],
+                                                   C.U[C.cur], w, C.d_sib);
+    return cuda_fail(cudaGetLastError(), "k_interp_patches");
+}
+
+amr_status interp_new_patches(amr_hydro_ctx *c, int coarse, double *out, const int32_t *out_slot,
+                              const int32_t *info, int n_jobs) {
+    if (!n_jobs) return AMR_OK;
+    Level &C = c->lv[coarse];
+    const int grid = n_jobs < 4 * c->n_sm ? n_jobs : 4 * c->n_sm;
+    k_interp_patches<<<grid, 256, 0, c->stream>>>(out, out_slot, info, n_jobs, C.U[C.cur], C.U[C.cur], 1.0,
+                                                   C.d_sib);
+    return cuda_fail(cudaGetLastError(), "k_interp_patches (new patches)");
+}
+
+amr_status copy_slots(amr_hydro_ctx *c, double *dst, const double *src, const int32_t *map, int n) {
+    if (!n) return AMR_OK;
+    const int grid = n < 8 * c->n_sm ? n : 8 * c->n_sm;
+    k_copy_slots<<<grid, 256, 0, c->stream>>>(dst, src, map, n);
+    return cuda_fail(cudaGetLastError(), "k_copy_slots");
+}
+
+amr_status patch_flags_dev(amr_hydro_ctx *c, int level, uint8_t *pflag) {
+    Level &L = c->lv[level];
+    amr_status st;
+    if (L.n_ghost && (st = fill_ghost_impl(c, level, L.t))) return st;
+    if ((st = c->cflag.reserve((size_t)L.n_patches * PV))) return st;
+    const int g1 = L.n_groups < 4 * c->n_sm ? L.n_groups : 4 * c->n_sm;
+    k_flag_cells<<<g1, 256, 0, c->stream>>>(L.U[L.cur], L.ghost.p, L.nbr.p, L.n_groups, c->prm.theta, c->cflag.p);
+    if ((st = cuda_fail(cudaGetLastError(), "k_flag_cells"))) return st;
+    int nbuf = c->prm.nbuf[level];
+    if (nbuf < 0) nbuf = 0;
+    if (nbuf > 8) nbuf = 8;
+    const int g2 = L.n_patches < 8 * c->n_sm ? L.n_patches : 8 * c->n_sm;
+    k_flag_patches<<<g2, 256, 0, c->stream>>>(c->cflag.p, L.d_sib, L.n_patches, nbuf, pflag);
+    return cuda_fail(cudaGetLastError(), "k_flag_patches");
+}
+
 }  // namespace amrh
 
 extern "C" {
+
 amr_status amr_hydro_fill_ghost(amr_hydro_ctx *c, int level, double t) {
     if (!c || level <= 0 || level > c->prm.lmax) return AMR_E_INVAL;
+    if (!c->lv[level].n_patches) return AMR_E_INVAL;
     return fill_ghost_impl(c, level, t);
 }
-amr_status amr_hydro_flux_fixup(amr_hydro_ctx *c, int coarse_level) {
-    (void)c; (void)coarse_level;
-    return AMR_E_INVAL;
+
+amr_status amr_hydro_flux_fixup(amr_hydro_ctx *c, int l) {
+    if (!c || l < 0 || l >= c->prm.lmax) return AMR_E_INVAL;
+    Level &C = c->lv[l], &F = c->lv[l + 1];
+    if (!C.n_patches || !F.n_patches) return AMR_OK;
+    amr_status st;
+    if (C.n_fix) {
+        const int grid = C.n_fix < 4 * c->n_sm ? C.n_fix : 4 * c->n_sm;
+        k_cf_fixup<<<grid, 128, 0, c->stream>>>(C.U[C.cur], C.fix_list.p, C.n_fix, C.creg.p, F.freg.p, level_dh(c, l));
+        if ((st = cuda_fail(cudaGetLastError(), "k_cf_fixup"))) return st;
+    }
+    if (C.n_restrict) {
+        const int grid = C.n_restrict < 8 * c->n_sm ? C.n_restrict : 8 * c->n_sm;
+        k_restrict<<<grid, 256, 0, c->stream>>>(C.U[C.cur], F.U[F.cur], C.restrict_list.p, C.n_restrict);
+        if ((st = cuda_fail(cudaGetLastError(), "k_restrict"))) return st;
+    }
+    C.speed_valid = false;
+    return AMR_OK;
 }
+
 amr_status amr_hydro_regrid_flags(amr_hydro_ctx *c, int level, uint8_t *flags) {
-    (void)c; (void)level; (void)flags;
-    return AMR_E_INVAL;
+    if (!c || !flags || level < 0 || level > c->prm.lmax) return AMR_E_INVAL;
+    if (!c->lv[level].n_patches) return AMR_E_INVAL;
+    return patch_flags_dev(c, level, flags);
 }
+
 amr_status amr_hydro_conserved_sum(amr_hydro_ctx *c, int level, double *out) {
-    (void)c; (void)level; (void)out;
-    return AMR_E_INVAL;
+    if (!c || !out || level < 0 || level > c->prm.lmax) return AMR_E_INVAL;
+    Level &L = c->lv[level];
+    for (int v = 0; v < NV; v++) out[v] = 0.0;
+    if (!L.n_patches) return AMR_OK;
+    amr_status st;
+    if ((st = c->psum.reserve((size_t)L.n_patches * NV))) return st;
+    const int grid = L.n_patches < 8 * c->n_sm ? L.n_patches : 8 * c->n_sm;
+    k_patch_sums<<<grid, 256, 0, c->stream>>>(L.U[L.cur], L.n_patches, c->psum.p);
+    if ((st = cuda_fail(cudaGetLastError(), "k_patch_sums"))) return st;
+    std::vector<double> h((size_t)L.n_patches * NV);
+    if ((st = cuda_fail(cudaMemcpyAsync(h.data(), c->psum.p, 8 * h.size(), cudaMemcpyDeviceToHost, c->stream), "d2h")))
+        return st;
+    if ((st = cuda_fail(cudaStreamSynchronize(c->stream), "sync"))) return st;
+    const double dV = level_dh(c, level) * level_dh(c, level) * level_dh(c, level);
+    for (int s = 0; s < L.n_patches; s++) {
+        if (L.child[s] >= 0) continue;  // covered by the finer level: not a leaf
+        for (int v = 0; v < NV; v++) out[v] += h[(size_t)s * NV + v];
+    }
+    for (int v = 0; v < NV; v++) out[v] *= dV;
+    return AMR_OK;
 }
-amr_status amr_hydro_set_box(amr_hydro_ctx *c, int box_id, int n, double *U_a, double *U_b) {
-    (void)c; (void)box_id; (void)n; (void)U_a; (void)U_b;
-    return AMR_E_INVAL;
-}
-amr_status amr_hydro_advance_boxes(amr_hydro_ctx *c, int n_boxes, const int *box_ids, int n_steps,
-                                   double *dt_log) {
-    (void)c; (void)n_boxes; (void)box_ids; (void)n_steps; (void)dt_log;
-    return AMR_E_INVAL;
-}
-amr_status amr_hydro_box_state(amr_hydro_ctx *c, int box_id, int *cur) {
-    (void)c; (void)box_id; (void)cur;
-    return AMR_E_INVAL;
-}
-amr_status amr_hydro_step_adjoint(amr_hydro_ctx *c, int level, double dt, const double *U_n,
-                                  const double *lam_np1, double *lam_n) {
-    (void)c; (void)level; (void)dt; (void)U_n; (void)lam_np1; (void)lam_n;
-    return AMR_E_INVAL;
-}
-}
+
+}  // extern "C"

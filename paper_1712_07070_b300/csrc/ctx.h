@@ -48,14 +48,20 @@ struct Level {
     DevBuf<double> ghost;       // [n_ghost][5][512]
     DevBuf<int32_t> ghost_info; // [n_ghost][4]
     int n_ghost = 0;
-    // coarse-fine flux registers
-    DevBuf<int64_t> fine_off;    // [n_groups*6]: where this level's groups add fine fluxes
-    DevBuf<int64_t> coarse_off;  // [n_patches*6]: where this level's patches store coarse fluxes
-    DevBuf<double> cf_coarse, cf_fine;  // registers owned by this (coarse) level
-    DevBuf<int32_t> fix_list;    // [n_fix][2] (slot, face) pairs of this level to fix up
+    // coarse-fine flux registers (section 2.2 fix-up)
+    DevBuf<int64_t> fine_off;    // [n_groups*6]: this level's group faces on coarse-fine interfaces
+    DevBuf<double> freg;         // their [5][16][16] blocks of sum dt*F (this level as the fine side)
+    int n_freg = 0;
+    DevBuf<int64_t> coarse_off;  // [n_patches*6]: this level's leaf-patch faces next to refined patches
+    DevBuf<double> creg;         // their [5][8][8] blocks of dt*F (this level as the coarse side)
+    int n_creg = 0;
+    DevBuf<int64_t> fix_list;    // [n_fix][13]: patch, coarse blocks[6], fine blocks[6]
     int n_fix = 0;
-    int n_cf_regs = 0;
-    bool has_fine_regs = false, has_coarse_regs = false;
+    DevBuf<int32_t> restrict_list;  // [n_restrict][2]: refined patch, child group
+    int n_restrict = 0;
+    bool bound = false;          // capacity arrays registered (levels >= 1)
+    int32_t *w_corner = nullptr, *w_sib = nullptr, *w_parent = nullptr, *w_child = nullptr;
+    double dt_prev = -1.0;       // last step size (W-cycle)
     int scal0 = 0;  // first of this level's 8 scalar slots
     int ring = 0;   // ring position of the newest state
     bool speed_valid = false;
@@ -64,10 +70,11 @@ struct Level {
         ghost.release();
         ghost_info.release();
         fine_off.release();
+        freg.release();
         coarse_off.release();
-        cf_coarse.release();
-        cf_fine.release();
+        creg.release();
         fix_list.release();
+        restrict_list.release();
         n_patches = n_groups = 0;
     }
 };
@@ -91,6 +98,9 @@ struct amr_hydro_ctx {
     amrh::Box boxes[amrh::MAX_BOXES];
     amrh::DevBuf<unsigned long long> scal;
     amrh::DevBuf<double> dtbuf;
+    amrh::DevBuf<uint8_t> cflag, pflag;  // refinement flag scratch
+    amrh::DevBuf<double> psum;           // per-patch conservation partials
+    amrh::DevBuf<int32_t> regrid_tmp;    // slot maps / interpolation jobs of a regrid
     // batched-box launch plan and its captured graph
     amrh::DevBuf<int32_t> box_plan;
     cudaGraphExec_t graph_exec = nullptr;
@@ -106,6 +116,14 @@ size_t step_smem_bytes(int prec);
 struct StepParams;
 amr_status launch_step(amr_hydro_ctx *c, const StepParams &P, int grid);
 amr_status launch_step_raw(int prec, const StepParams &P, cudaStream_t stream);
+// AMR (amr_ops.cu, regrid.cpp)
+amr_status fill_ghost_impl(amr_hydro_ctx *c, int level, double t);
+amr_status interp_new_patches(amr_hydro_ctx *c, int coarse, double *out, const int32_t *out_slot,
+                              const int32_t *info, int n_jobs);
+amr_status copy_slots(amr_hydro_ctx *c, double *dst, const double *src, const int32_t *map, int n);
+amr_status patch_flags_dev(amr_hydro_ctx *c, int level, uint8_t *pflag);
+amr_status plan_level(amr_hydro_ctx *c, int level);
+amr_status rebuild_cf(amr_hydro_ctx *c, int fine_level);
 amr_status level_time(amr_hydro_ctx *c, int level);
 // host planning (host_plan.cpp)
 amr_status build_uniform_tables(const int np[3], int32_t *corner, int32_t *sib, int32_t *parent,

@@ -27,15 +27,13 @@ static amr_status sync_level_time(amr_hydro_ctx *c, Level &L, int level) {
     return AMR_OK;
 }
 
-amr_status fill_ghost_impl(amr_hydro_ctx *c, int level, double t);
-
 }  // namespace amrh
 
 extern "C" {
 
 amr_status amr_hydro_set_level(amr_hydro_ctx *c, int level, int n_patches, double *U_a, double *U_b,
                                const int32_t *corner, const int32_t *sib, const int32_t *parent,
-                               const int32_t *child_group, double t) {
+                               int32_t *child_group, double t) {
     if (!c || level < 0 || level > c->prm.lmax) return AMR_E_INVAL;
     if (n_patches < 0 || n_patches % 8 || n_patches > c->prm.max_patches) return AMR_E_INVAL;
     if (n_patches > 0 && (!U_a || !U_b || !corner || !sib)) return AMR_E_INVAL;
@@ -55,6 +53,7 @@ amr_status amr_hydro_set_level(amr_hydro_ctx *c, int level, int n_patches, doubl
     L.d_sib = sib;
     L.d_parent = parent;
     L.d_child = child_group;
+    L.w_child = child_group;
     L.scal0 = SCAL_LEVEL0 + SCAL_PER * level;
     L.ring = 0;
     L.speed_valid = false;
@@ -84,21 +83,9 @@ amr_status amr_hydro_set_level(amr_hydro_ctx *c, int level, int n_patches, doubl
     for (int d = 0; d < 3; d++) cells[d] = c->prm.root_n[d] << level;
     for (int i = 0; i < 3 * n_patches; i++)
         if (L.corner[i] < 0 || L.corner[i] >= cells[i % 3] || L.corner[i] % 8) return AMR_E_INVAL;
-    std::vector<int32_t> nbr;
-    std::vector<GhostInfo> ghosts;
-    st = build_nbr_plan(level, n_patches, L.corner.data(), L.sib.data(),
-                        level > 0 ? L.parent.data() : nullptr, cells, nbr, ghosts);
-    if (st) return st;
-    if ((st = L.nbr.reserve(nbr.size()))) return st;
-    if ((st = cuda_fail(cudaMemcpy(L.nbr.p, nbr.data(), 4 * nbr.size(), cudaMemcpyHostToDevice), "h2d")))
-        return st;
-    L.n_ghost = (int)ghosts.size();
-    if (L.n_ghost) {
-        if ((st = L.ghost.reserve((size_t)L.n_ghost * PSLOT))) return st;
-        if ((st = L.ghost_info.reserve((size_t)L.n_ghost * 4))) return st;
-        if ((st = cuda_fail(cudaMemcpy(L.ghost_info.p, ghosts.data(), 16ull * L.n_ghost, cudaMemcpyHostToDevice), "h2d")))
-            return st;
-    }
+    if ((st = plan_level(c, level))) return st;
+    if (level > 0 && (st = rebuild_cf(c, level))) return st;
+    if (level < c->prm.lmax && c->lv[level + 1].n_patches && (st = rebuild_cf(c, level + 1))) return st;
     return AMR_OK;
 }
 
@@ -141,10 +128,17 @@ amr_status amr_hydro_advance_level(amr_hydro_ctx *c, int level, double dt, int64
     P.n_bad = sc + 3 + r_out;
     P.clear2 = sc + r_clr;
     P.time_rec = c->dtbuf.p + 3 * level;
-    P.cf.fine_off = L.has_fine_regs ? L.fine_off.p : nullptr;
-    P.cf.fine_buf = level > 0 ? c->lv[level - 1].cf_fine.p : nullptr;
-    P.cf.coarse_off = L.has_coarse_regs ? L.coarse_off.p : nullptr;
-    P.cf.coarse_buf = L.cf_coarse.p;
+    P.cf.fine_off = L.n_freg ? L.fine_off.p : nullptr;
+    P.cf.fine_buf = L.freg.p;
+    P.cf.coarse_off = L.n_creg ? L.coarse_off.p : nullptr;
+    P.cf.coarse_buf = L.creg.p;
+    if (level < c->prm.lmax) {  // a coarse step restarts the fine level's flux sums
+        Level &F = c->lv[level + 1];
+        if (F.n_patches && F.n_freg &&
+            (st = cuda_fail(cudaMemsetAsync(F.freg.p, 0, sizeof(double) * 1280 * (size_t)F.n_freg, c->stream),
+                            "memset fine registers")))
+            return st;
+    }
     const int cap = c->n_sm * c->step_bps;
     const int grid = L.n_groups < cap ? L.n_groups : cap;
     if ((st = launch_step(c, P, grid))) return st;

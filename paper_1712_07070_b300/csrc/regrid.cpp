@@ -1,0 +1,414 @@
+// regrid.cpp -- host-side AMR bookkeeping (GAMER-2 section 2.1):
+//   * per-level gather plans and coarse-fine register maps;
+//   * regridding one level at a time from device refinement flags: flag
+//     buffers (on the device), proper nesting, no explicit derefinement
+//     (children are removed when their parent is not flagged and no
+//     grandchildren need them), new children interpolated from the parent;
+//   * the adaptive time-step W-cycle with the C_inc / C_dec rule of the
+//     section's pseudo-code, followed by fix-up (section 2.2) and regrid.
+// Integer work only; all cell data moves on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cstring>
+#include <unordered_map>
+#include <vector>
+
+#include "amr_hydro.h"
+#include "ctx.h"
+
+namespace amrh {
+
+constexpr int PSLOT_H = 5 * 512;
+
+static inline int wrapi(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+static inline int sib_k(int dx, int dy, int dz) {
+    const int k = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+    return k - (k > 13);
+}
+// face f (0..5: -x,+x,-y,+y,-z,+z) -> sibling index of the neighbour across it
+static inline int face_sib(int f) {
+    int d[3] = {0, 0, 0};
+    d[f >> 1] = (f & 1) ? 1 : -1;
+    return sib_k(d[0], d[1], d[2]);
+}
+static inline uint64_t key3(int x, int y, int z) {
+    return ((uint64_t)(uint32_t)x << 42) ^ ((uint64_t)(uint32_t)y << 21) ^ (uint64_t)(uint32_t)z;
+}
+
+template <typename T>
+static amr_status upload(DevBuf<T> &b, const std::vector<T> &h, cudaStream_t s) {
+    if (h.empty()) return AMR_OK;
+    amr_status st = b.reserve(h.size());
+    if (st) return st;
+    return cuda_fail(cudaMemcpyAsync(b.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s), "h2d");
+}
+
+// Neighbour (gather) plan of a level from its host tables.
+amr_status plan_level(amr_hydro_ctx *c, int level) {
+    Level &L = c->lv[level];
+    L.n_ghost = 0;
+    if (!L.n_patches) return AMR_OK;
+    int cells[3];
+    for (int d = 0; d < 3; d++) cells[d] = c->prm.root_n[d] << level;
+    std::vector<int32_t> nbr;
+    std::vector<GhostInfo> ghosts;
+    amr_status st = build_nbr_plan(level, L.n_patches, L.corner.data(), L.sib.data(),
+                                   level > 0 ? L.parent.data() : nullptr, cells, nbr, ghosts);
+    if (st) return st;
+    if ((st = upload(L.nbr, nbr, c->stream))) return st;
+    L.n_ghost = (int)ghosts.size();
+    if (L.n_ghost) {
+        if ((st = L.ghost.reserve((size_t)L.n_ghost * PSLOT_H))) return st;
+        std::vector<int32_t> gi((size_t)L.n_ghost * 4);
+        for (int i = 0; i < L.n_ghost; i++) {
+            gi[4 * i] = ghosts[i].cparent;
+            gi[4 * i + 1] = ghosts[i].qx;
+            gi[4 * i + 2] = ghosts[i].qy;
+            gi[4 * i + 3] = ghosts[i].qz;
+        }
+        if ((st = upload(L.ghost_info, gi, c->stream))) return st;
+    }
+    return cuda_fail(cudaStreamSynchronize(c->stream), "sync");
+}
+
+// Coarse-fine registers between coarse level l-1 and fine level l, fix-up
+// and restriction lists of the coarse level.  An interface is a face of a
+// leaf coarse patch Q whose neighbour P across it is refined; the fine side
+// is the face of P's child group toward Q.
+amr_status rebuild_cf(amr_hydro_ctx *c, int l) {
+    Level &C = c->lv[l - 1], &F = c->lv[l];
+    C.n_creg = C.n_fix = C.n_restrict = 0;
+    F.n_freg = 0;
+    if (!C.n_patches || !F.n_patches) return AMR_OK;
+    std::vector<int64_t> foff((size_t)F.n_groups * 6, -1), coff((size_t)C.n_patches * 6, -1), fix;
+    std::vector<int32_t> rlist;
+    int nf = 0, nc = 0;
+    // fine side
+    for (int g = 0; g < F.n_groups; g++) {
+        const int P = F.parent[8 * g];
+        if (P < 0 || P >= C.n_patches) return AMR_E_NESTING;
+        for (int f = 0; f < 6; f++) {
+            const int Q = C.sib[(size_t)P * 26 + face_sib(f)];
+            if (Q < 0) return AMR_E_NESTING;
+            if (C.child[Q] < 0) foff[(size_t)g * 6 + f] = (int64_t)(nf++) * 1280;
+        }
+    }
+    // coarse side
+    for (int Q = 0; Q < C.n_patches; Q++) {
+        if (C.child[Q] >= 0) {
+            rlist.push_back(Q);
+            rlist.push_back(C.child[Q]);
+            continue;
+        }
+        std::array<int64_t, 13> e;
+        e.fill(-1);
+        e[0] = Q;
+        bool any = false;
+        for (int f = 0; f < 6; f++) {
+            const int P = C.sib[(size_t)Q * 26 + face_sib(f)];
+            if (P < 0 || C.child[P] < 0) continue;
+            const int G = C.child[P];
+            const int64_t fo = foff[(size_t)G * 6 + (f ^ 1)];
+            if (fo < 0) return AMR_E_NESTING;
+            coff[(size_t)Q * 6 + f] = (int64_t)(nc++) * 320;
+            e[1 + f] = coff[(size_t)Q * 6 + f];
+            e[7 + f] = fo;
+            any = true;
+        }
+        if (any) fix.insert(fix.end(), e.begin(), e.end());
+    }
+    amr_status st;
+    if ((st = upload(F.fine_off, foff, c->stream))) return st;
+    if ((st = upload(C.coarse_off, coff, c->stream))) return st;
+    if ((st = upload(C.fix_list, fix, c->stream))) return st;
+    if ((st = upload(C.restrict_list, rlist, c->stream))) return st;
+    if (nf && (st = F.freg.reserve((size_t)nf * 1280))) return st;
+    if (nc && (st = C.creg.reserve((size_t)nc * 320))) return st;
+    if (nf && (st = cuda_fail(cudaMemsetAsync(F.freg.p, 0, sizeof(double) * 1280 * (size_t)nf, c->stream), "memset")))
+        return st;
+    F.n_freg = nf;
+    C.n_creg = nc;
+    C.n_fix = (int)(fix.size() / 13);
+    C.n_restrict = (int)(rlist.size() / 2);
+    return cuda_fail(cudaStreamSynchronize(c->stream), "sync");
+}
+
+}  // namespace amrh
+
+using namespace amrh;
+
+extern "C" {
+
+amr_status amr_hydro_bind_level(amr_hydro_ctx *c, int level, double *U_a, double *U_b, int32_t *corner,
+                                int32_t *sib, int32_t *parent, int32_t *child_group) {
+    if (!c || level < 1 || level > c->prm.lmax) return AMR_E_INVAL;
+    if (!U_a || !U_b || U_a == U_b || !corner || !sib || !parent || !child_group) return AMR_E_INVAL;
+    Level &L = c->lv[level];
+    L.bound = true;
+    L.U[0] = U_a;
+    L.U[1] = U_b;
+    L.cur = 0;
+    L.d_corner = L.w_corner = corner;
+    L.d_sib = L.w_sib = sib;
+    L.d_parent = L.w_parent = parent;
+    L.d_child = L.w_child = child_group;
+    L.n_patches = L.n_groups = 0;
+    L.n_ghost = 0;
+    L.corner.clear();
+    L.sib.clear();
+    L.parent.clear();
+    L.child.clear();
+    L.scal0 = SCAL_LEVEL0 + SCAL_PER * level;
+    L.ring = 0;
+    L.speed_valid = false;
+    L.dt_prev = -1.0;
+    return AMR_OK;
+}
+
+amr_status amr_hydro_level_info(amr_hydro_ctx *c, int level, int *n_patches, int *n_ghost) {
+    if (!c || level < 0 || level > c->prm.lmax) return AMR_E_INVAL;
+    if (n_patches) *n_patches = c->lv[level].n_patches;
+    if (n_ghost) *n_ghost = c->lv[level].n_ghost;
+    return AMR_OK;
+}
+
+amr_status amr_hydro_regrid(amr_hydro_ctx *c, int l) {
+    if (!c || l < 0 || l >= c->prm.lmax) return AMR_E_INVAL;
+    Level &L = c->lv[l], &F = c->lv[l + 1];
+    if (!L.n_patches || !F.bound) return AMR_E_INVAL;
+    amr_status st;
+    if ((st = level_time(c, l))) return st;
+    const int n = L.n_patches;
+    // device flags (cell criterion + flag buffer) -> host
+    if ((st = c->pflag.reserve(n))) return st;
+    if ((st = patch_flags_dev(c, l, c->pflag.p))) return st;
+    std::vector<uint8_t> pflag(n);
+    if ((st = cuda_fail(cudaMemcpyAsync(pflag.data(), c->pflag.p, n, cudaMemcpyDeviceToHost, c->stream), "d2h")))
+        return st;
+    if ((st = cuda_fail(cudaStreamSynchronize(c->stream), "sync"))) return st;
+
+    int pc[3], fc[3];  // patches per dimension on levels l and l+1
+    for (int d = 0; d < 3; d++) {
+        pc[d] = (c->prm.root_n[d] << l) / 8;
+        fc[d] = 2 * pc[d];
+    }
+    std::unordered_map<uint64_t, int> at_l;
+    at_l.reserve(2 * n);
+    for (int s = 0; s < n; s++)
+        at_l[key3(L.corner[3 * s] / 8, L.corner[3 * s + 1] / 8, L.corner[3 * s + 2] / 8)] = s;
+
+    // keep-for-nesting: level-l parents of the 27-neighbourhoods of refined
+    // level-(l+1) patches stay refined
+    std::vector<uint8_t> keep(n, 0);
+    if (l + 2 <= c->prm.lmax && c->lv[l + 2].n_patches) {
+        for (int x = 0; x < F.n_patches; x++) {
+            if (F.child[x] < 0) continue;
+            const int X[3] = {F.corner[3 * x] / 8, F.corner[3 * x + 1] / 8, F.corner[3 * x + 2] / 8};
+            for (int dz = -1; dz <= 1; dz++)
+                for (int dy = -1; dy <= 1; dy++)
+                    for (int dx = -1; dx <= 1; dx++) {
+                        const int q[3] = {wrapi(X[0] + dx, fc[0]) / 2, wrapi(X[1] + dy, fc[1]) / 2,
+                                          wrapi(X[2] + dz, fc[2]) / 2};
+                        auto it = at_l.find(key3(q[0], q[1], q[2]));
+                        if (it == at_l.end()) return AMR_E_NESTING;
+                        keep[it->second] = 1;
+                    }
+        }
+    }
+    // new refinement: flagged and properly nested, or kept
+    std::vector<int> chosen;
+    for (int s = 0; s < n; s++) {
+        bool nest_ok = true;
+        for (int k = 0; k < 26 && nest_ok; k++) nest_ok = L.sib[(size_t)s * 26 + k] >= 0;
+        if ((pflag[s] && nest_ok) || (keep[s] && L.child[s] >= 0)) chosen.push_back(s);
+    }
+    // canonical group order: parents sorted by corner (z, y, x)
+    std::sort(chosen.begin(), chosen.end(), [&](int a, int b) {
+        for (int d = 2; d >= 0; d--)
+            if (L.corner[3 * a + d] != L.corner[3 * b + d]) return L.corner[3 * a + d] < L.corner[3 * b + d];
+        return a < b;
+    });
+    const int ng = (int)chosen.size(), nn = 8 * ng;
+    if (nn > c->prm.max_patches) return AMR_E_NOMEM;
+
+    std::vector<int32_t> corner((size_t)nn * 3), sib((size_t)nn * 26), parent(nn), child(nn, -1);
+    std::vector<int32_t> old_of(nn, -1), new_of((size_t)F.n_patches, -1), lchild(n, -1), jobs, job_slot;
+    std::unordered_map<uint64_t, int> at_f;
+    at_f.reserve(2 * nn);
+    for (int g = 0; g < ng; g++) {
+        const int P = chosen[g];
+        lchild[P] = g;
+        for (int k = 0; k < 8; k++) {
+            const int s = 8 * g + k, lx = k & 1, ly = (k >> 1) & 1, lz = k >> 2;
+            corner[3 * s] = 2 * L.corner[3 * P] + 8 * lx;
+            corner[3 * s + 1] = 2 * L.corner[3 * P + 1] + 8 * ly;
+            corner[3 * s + 2] = 2 * L.corner[3 * P + 2] + 8 * lz;
+            parent[s] = P;
+            at_f[key3(corner[3 * s] / 8, corner[3 * s + 1] / 8, corner[3 * s + 2] / 8)] = s;
+            if (L.child[P] >= 0) {
+                const int o = 8 * L.child[P] + k;
+                old_of[s] = o;
+                new_of[o] = s;
+                child[s] = F.child[o];
+            } else {
+                jobs.insert(jobs.end(), {P, lx, ly, lz});
+                job_slot.push_back(s);
+            }
+        }
+    }
+    for (int s = 0; s < nn; s++) {
+        const int p[3] = {corner[3 * s] / 8, corner[3 * s + 1] / 8, corner[3 * s + 2] / 8};
+        for (int dz = -1; dz <= 1; dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    if (!dx && !dy && !dz) continue;
+                    auto it = at_f.find(key3(wrapi(p[0] + dx, fc[0]), wrapi(p[1] + dy, fc[1]), wrapi(p[2] + dz, fc[2])));
+                    sib[(size_t)s * 26 + sib_k(dx, dy, dz)] = it == at_f.end() ? -1 : it->second;
+                }
+    }
+    // grandchildren keep their data; their parent slots are renumbered
+    Level *G2 = (l + 2 <= c->prm.lmax && c->lv[l + 2].n_patches) ? &c->lv[l + 2] : nullptr;
+    std::vector<int32_t> g2parent;
+    if (G2) {
+        g2parent.resize(G2->n_patches);
+        for (int y = 0; y < G2->n_patches; y++) {
+            const int op = G2->parent[y];
+            if (op < 0 || op >= (int)new_of.size() || new_of[op] < 0) return AMR_E_NESTING;
+            g2parent[y] = new_of[op];
+        }
+    }
+
+    // cell data of the new level l+1 into its other buffer
+    const int dst = F.n_patches ? 1 - F.cur : 0;
+    double *Ud = F.U[dst];
+    const int ntmp = nn + (int)jobs.size() + (int)job_slot.size();
+    if ((st = c->regrid_tmp.reserve(ntmp > 0 ? ntmp : 1))) return st;
+    std::vector<int32_t> tmp;
+    tmp.reserve(ntmp);
+    tmp.insert(tmp.end(), old_of.begin(), old_of.end());
+    tmp.insert(tmp.end(), jobs.begin(), jobs.end());
+    tmp.insert(tmp.end(), job_slot.begin(), job_slot.end());
+    if (!tmp.empty() &&
+        (st = cuda_fail(cudaMemcpyAsync(c->regrid_tmp.p, tmp.data(), 4 * tmp.size(), cudaMemcpyHostToDevice, c->stream),
+                        "h2d")))
+        return st;
+    if (F.n_patches && (st = copy_slots(c, Ud, F.U[F.cur], c->regrid_tmp.p, nn))) return st;
+    if ((st = interp_new_patches(c, l, Ud, c->regrid_tmp.p + nn + jobs.size(), c->regrid_tmp.p + nn,
+                                 (int)job_slot.size())))
+        return st;
+
+    // tables: host mirrors and the caller's arrays
+    F.corner = corner;
+    F.sib = sib;
+    F.parent = parent;
+    F.child = child;
+    F.n_patches = nn;
+    F.n_groups = ng;
+    F.cur = dst;
+    F.t = F.t_prev = L.t;
+    F.t_pending = false;
+    F.speed_valid = false;
+    F.ring = 0;
+    L.child = lchild;
+    auto put = [&](int32_t *d, const std::vector<int32_t> &h) -> amr_status {
+        if (!d || h.empty()) return AMR_OK;
+        return cuda_fail(cudaMemcpyAsync(d, h.data(), 4 * h.size(), cudaMemcpyHostToDevice, c->stream), "h2d");
+    };
+    if ((st = put(F.w_corner, corner)) || (st = put(F.w_sib, sib)) || (st = put(F.w_parent, parent)) ||
+        (st = put(F.w_child, child)))
+        return st;
+    if ((st = put(L.w_child, lchild))) return st;
+    if (G2) {
+        G2->parent = g2parent;
+        if ((st = put(G2->w_parent, g2parent))) return st;
+    }
+    {
+        const double rec[3] = {0.0, F.t, F.t};
+        if ((st = cuda_fail(cudaMemcpyAsync(c->dtbuf.p + 3 * (l + 1), rec, 24, cudaMemcpyHostToDevice, c->stream),
+                            "h2d time")))
+            return st;
+    }
+    if ((st = cuda_fail(cudaMemsetAsync(c->scal.p + F.scal0, 0, 8 * SCAL_PER, c->stream), "memset"))) return st;
+    if ((st = cuda_fail(cudaStreamSynchronize(c->stream), "sync"))) return st;
+    if (!ng) F.dt_prev = -1.0;
+    // plans of the changed levels
+    if ((st = plan_level(c, l + 1))) return st;
+    if ((st = rebuild_cf(c, l + 1))) return st;
+    if (G2) {
+        if ((st = plan_level(c, l + 2))) return st;
+        if ((st = rebuild_cf(c, l + 2))) return st;
+    }
+    return AMR_OK;
+}
+
+}  // extern "C"
+
+// ---- the W-cycle ------------------------------------------------------------------
+
+namespace {
+
+amr_status min_dt_host(amr_hydro_ctx *c, int l, double *dt) { return amr_hydro_min_dt(c, l, dt); }
+
+// C_dec rule: shrink dt to twice the finer level's last step when that
+// removes a small synchronisation step there.
+double dec_rule(amr_hydro_ctx *c, int l, double dt) {
+    if (l < c->prm.lmax && c->lv[l + 1].n_patches && c->lv[l + 1].dt_prev > 0.0) {
+        const double d2 = 2.0 * c->lv[l + 1].dt_prev;
+        if (dt > d2 && (1.0 - c->prm.c_dec) * dt < d2) return d2;
+    }
+    return dt;
+}
+
+amr_status advance_rec(amr_hydro_ctx *c, int l, double dt0, int64_t *updates) {
+    Level &L = c->lv[l];
+    amr_status st;
+    double target, dt = 0.0;
+    if (l == 0) {
+        dt = dt0;
+        if (!(dt > 0.0) && (st = min_dt_host(c, 0, &dt))) return st;
+        dt = dec_rule(c, 0, dt);
+        target = L.t + dt;
+    } else {
+        target = c->lv[l - 1].t;
+    }
+    while (L.t < target) {
+        bool last = false;
+        double step;
+        if (l == 0) {
+            step = dt;
+        } else {
+            if ((st = min_dt_host(c, l, &step))) return st;
+            if ((1.0 + c->prm.c_inc) * step > target - L.t) {
+                step = target - L.t;
+                last = true;
+            } else {
+                step = dec_rule(c, l, step);
+            }
+        }
+        if ((st = amr_hydro_advance_level(c, l, step, nullptr))) return st;
+        if (last || l == 0) L.t = target;
+        L.dt_prev = step;
+        if (updates) *updates += (int64_t)L.n_patches * 512;
+        if (l < c->prm.lmax && c->lv[l + 1].n_patches) {
+            if ((st = advance_rec(c, l + 1, 0.0, updates))) return st;
+            if ((st = amr_hydro_flux_fixup(c, l))) return st;
+        }
+        if (l < c->prm.lmax && c->lv[l + 1].bound) {
+            if ((st = amr_hydro_regrid(c, l))) return st;
+        }
+    }
+    return AMR_OK;
+}
+
+}  // namespace
+
+extern "C" amr_status amr_hydro_advance_root(amr_hydro_ctx *c, double dt0, int64_t *cell_updates) {
+    if (!c || !c->lv[0].n_patches) return AMR_E_INVAL;
+    if (cell_updates) *cell_updates = 0;
+    return advance_rec(c, 0, dt0, cell_updates);
+}

@@ -29,11 +29,14 @@ constexpr int GE = 16;                // group edge
 constexpr int TW = GE + 4;            // tile edge with 2 ghost cells per side
 constexpr int STEP_THREADS = 256;     // one thread per (x,y) column of the group
 
-// Coarse-fine flux register hook (section 2.2 fix-up): for each group and
-// each of its 6 faces, fine_reg[g*6+f] >= 0 is the offset (in doubles) of an
-// 8x8x5 register block of the coarse patch across that face, into which this
-// step adds dt * (mean of the 2x2 fine fluxes) per coarse face;
-// coarse_reg[slot*6+f] >= 0 is where a coarse patch stores dt * F on that face.
+// Coarse-fine flux registers (section 2.2 fix-up).  Faces f = 0..5 are
+// -x, +x, -y, +y, -z, +z.  Fine side: fine_off[g*6+f] >= 0 is the offset (in
+// doubles) of a [5][16][16] block of this level's fine register buffer for
+// group face f lying on a coarse-fine interface; every step adds dt * F of
+// each fine boundary face into it.  Coarse side: coarse_off[slot*6+f] >= 0 is
+// the offset of a [5][8][8] block of this level's coarse register buffer for
+// a leaf patch face next to a refined patch; every step stores dt * F there.
+// Block index (v, t2, t1) with t1 < t2 the two transverse dimensions.
 struct CFRegs {
     const int64_t *fine_off;    // [n_groups*6] or null
     double *fine_buf;
@@ -66,9 +69,52 @@ struct StepSmem {
     real FX[NV][GE][GE + 1];     // x flux at face x-1/2, x=0..16
     real FY[NV][GE + 1][GE];     // y flux at face y-1/2, y=0..16
     int nbr[64];
+    long long cfo[6];   // fine register blocks of the group's faces (-1: none)
+    long long cco[48];  // coarse register blocks of its 8 patches' faces (-1: none)
+    int any_cf;         // whether the group touches any register
     double red[STEP_THREADS / 32];
     double dt;
 };
+
+// dt * F into the registers of the face between group cells a (low) and b
+// (high) along D at flux value F (compute type), fine face coordinates
+// (t1, t2) in 0..15 within the group; pa/pb: local patch indices (0..7) of the
+// two cells when they belong to this group (-1 otherwise); face_lo/face_hi:
+// whether the face is the group's low / high boundary along D.
+template <int D, typename real>
+__device__ __forceinline__ void cf_register(const StepSmem<real> &S, const StepParams &P, double dt,
+                                            const real F[NV], int t1, int t2, int pa, int pb,
+                                            bool face_lo, bool face_hi) {
+    if (!S.any_cf) return;
+    double Fd[NV];
+    bool need = false;
+    const long long fo = face_lo ? S.cfo[2 * D] : (face_hi ? S.cfo[2 * D + 1] : -1);
+    const long long ca = pa >= 0 ? S.cco[pa * 6 + 2 * D + 1] : -1;  // high face of the low cell's patch
+    const long long cb = pb >= 0 ? S.cco[pb * 6 + 2 * D] : -1;      // low face of the high cell's patch
+    need = fo >= 0 || ca >= 0 || cb >= 0;
+    if (!need) return;
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        if constexpr (sizeof(real) == sizeof(double)) Fd[v] = F[v];
+        else Fd[v] = f2d_bits(F[v]);
+    }
+    if (fo >= 0) {
+        double *b = P.cf.fine_buf + fo;
+#pragma unroll
+        for (int v = 0; v < NV; v++) b[(v * 16 + t2) * 16 + t1] += dt * Fd[v];
+    }
+    const int c1 = t1 & 7, c2 = t2 & 7;
+    if (ca >= 0) {
+        double *b = P.cf.coarse_buf + ca;
+#pragma unroll
+        for (int v = 0; v < NV; v++) b[(v * 8 + c2) * 8 + c1] = dt * Fd[v];
+    }
+    if (cb >= 0) {
+        double *b = P.cf.coarse_buf + cb;
+#pragma unroll
+        for (int v = 0; v < NV; v++) b[(v * 8 + c2) * 8 + c1] = dt * Fd[v];
+    }
+}
 
 // Source pointer for patch position q (0..63) of the current group.
 __device__ __forceinline__ const double *patch_src(const StepParams &P, int s) {
@@ -181,6 +227,19 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_hydro_step(StepParams P) {
     for (int wi = blockIdx.x; wi < P.n_work; wi += gridDim.x) {
         const int grp = P.work ? P.work[wi] : wi;
         if (tid < 64) S.nbr[tid] = P.nbr[(int64_t)grp * 64 + tid];
+        if (tid == 0) S.any_cf = 0;
+        __syncthreads();
+        if (tid < 6) {
+            const long long o = P.cf.fine_off ? P.cf.fine_off[(int64_t)grp * 6 + tid] : -1;
+            S.cfo[tid] = o;
+            if (o >= 0) S.any_cf = 1;
+        }
+        if (tid >= 64 && tid < 112) {
+            const int k = tid - 64;
+            const long long o = P.cf.coarse_off ? P.cf.coarse_off[((int64_t)grp * 8 + k / 6) * 6 + k % 6] : -1;
+            S.cco[k] = o;
+            if (o >= 0) S.any_cf = 1;
+        }
         __syncthreads();
         load_plane(S, P, -2, g);
         load_plane(S, P, -1, g);
@@ -238,7 +297,14 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_hydro_step(StepParams P) {
 
             // ---- C: fluxes
             real fz[NV];
-            if (z >= 0) hllc<2>(zp_prev, zm, fz, g);
+            if (z >= 0) {
+                hllc<2>(zp_prev, zm, fz, g);
+                if (z == 0 || z == GE || (z == 8)) {
+                    const int pl = (cx >> 3) + 2 * (cy >> 3);
+                    cf_register<2>(S, P, dt, fz, cx, cy, z == 0 ? -1 : pl + 4 * ((z - 1) >> 3),
+                                   z == GE ? -1 : pl + 4 * (z >> 3), z == 0, z == GE);
+                }
+            }
             if (z >= 0 && z < GE) {
                 real uL[NV], uR[NV], F[NV];
                 // x face at cx-1/2 of row cy
@@ -247,12 +313,20 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_hydro_step(StepParams P) {
                 hllc<0>(uL, uR, F, g);
 #pragma unroll
                 for (int v = 0; v < NV; v++) S.FX[v][cy][cx] = F[v];
+                if ((cx & 7) == 0) {
+                    const int pr = (cy >> 3) * 2 + (z >> 3) * 4;
+                    cf_register<0>(S, P, dt, F, cy, z, cx == 0 ? -1 : pr, pr + (cx >> 3), cx == 0, false);
+                }
                 // y face at cy-1/2 of column cx
 #pragma unroll
                 for (int v = 0; v < NV; v++) { uL[v] = S.YS[1][v][cy][cx]; uR[v] = S.YS[0][v][cy + 1][cx]; }
                 hllc<1>(uL, uR, F, g);
 #pragma unroll
                 for (int v = 0; v < NV; v++) S.FY[v][cy][cx] = F[v];
+                if ((cy & 7) == 0) {
+                    const int pr = (cx >> 3) + (z >> 3) * 4;
+                    cf_register<1>(S, P, dt, F, cx, z, cy == 0 ? -1 : pr, pr + 2 * (cy >> 3), cy == 0, false);
+                }
                 if (tid < 32) {  // the high boundary faces x = 16-1/2 and y = 16-1/2
                     const int r = tid & 15;
                     if (tid < 16) {
@@ -261,12 +335,14 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_hydro_step(StepParams P) {
                         hllc<0>(uL, uR, F, g);
 #pragma unroll
                         for (int v = 0; v < NV; v++) S.FX[v][r][GE] = F[v];
+                        cf_register<0>(S, P, dt, F, r, z, 1 + (r >> 3) * 2 + (z >> 3) * 4, -1, false, true);
                     } else {
 #pragma unroll
                         for (int v = 0; v < NV; v++) { uL[v] = S.YS[1][v][GE][r]; uR[v] = S.YS[0][v][GE + 1][r]; }
                         hllc<1>(uL, uR, F, g);
 #pragma unroll
                         for (int v = 0; v < NV; v++) S.FY[v][GE][r] = F[v];
+                        cf_register<1>(S, P, dt, F, r, z, (r >> 3) + 2 + (z >> 3) * 4, -1, false, true);
                     }
                 }
             }
