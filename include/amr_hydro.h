@@ -227,6 +227,13 @@ amr_status amr_hydro_set_box(amr_hydro_ctx *ctx, int box_id, int n, double *U_a,
 amr_status amr_hydro_advance_boxes(amr_hydro_ctx *ctx, int n_boxes, const int *box_ids,
                                    int n_steps, double *dt_log);
 amr_status amr_hydro_box_state(amr_hydro_ctx *ctx, int box_id, int *cur_buffer);
+/* Launch shape the autotuner picked for the last box set: persistent grid
+ * size, contiguous (1) or grid-stride (0) work runs per CTA, interleaved (1)
+ * or box-major (0) work order, and its measured time per batch step.
+ * Setting the environment variable AMR_HYDRO_AUTOTUNE=0 skips the timing
+ * and uses the resident grid, grid-stride, box-major shape. */
+amr_status amr_hydro_box_tuning(amr_hydro_ctx *ctx, int *grid, int *chunked, int *interleave,
+                                float *ms_per_step);
 
 /*
  * Discrete adjoint of one uniform periodic MUSCL-Hancock step of size dt (no

@@ -23,7 +23,7 @@ SYMBOLS = (
     "amr_hydro_advance_boxes", "amr_hydro_box_state", "amr_hydro_step_adjoint",
     "amr_hydro_strerror", "amr_hydro_uniform_tables", "amr_hydro_pack_uniform",
     "amr_hydro_unpack_uniform", "amr_hydro_step_uniform_noalloc", "amr_hydro_bind_level",
-    "amr_hydro_regrid", "amr_hydro_advance_root", "amr_hydro_level_info",
+    "amr_hydro_regrid", "amr_hydro_advance_root", "amr_hydro_level_info", "amr_hydro_box_tuning",
 )
 
 
@@ -75,6 +75,7 @@ def lib():
         "amr_hydro_uniform_tables": [_ip, _vp, _vp, _vp, _vp],
         "amr_hydro_pack_uniform": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp],
         "amr_hydro_unpack_uniform": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp],
+        "amr_hydro_box_tuning": [_vp, _ip, _ip, _ip, ctypes.POINTER(ctypes.c_float)],
         "amr_hydro_bind_level": [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp],
         "amr_hydro_regrid": [_vp, ctypes.c_int],
         "amr_hydro_advance_root": [_vp, ctypes.c_double, _i64p],
@@ -193,6 +194,13 @@ def amr_hydro_box_state(ctx, box_id):
     cur = ctypes.c_int()
     check(lib().amr_hydro_box_state(ctx, box_id, ctypes.byref(cur)), "amr_hydro_box_state")
     return cur.value
+
+
+def amr_hydro_box_tuning(ctx):
+    g, c, i, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    check(lib().amr_hydro_box_tuning(ctx, ctypes.byref(g), ctypes.byref(c), ctypes.byref(i), ctypes.byref(ms)),
+          "amr_hydro_box_tuning")
+    return {"grid": g.value, "chunked": c.value, "interleave": i.value, "ms_per_step": ms.value}
 
 
 def amr_hydro_step_adjoint(ctx, level, dt, U_n, lam_np1, lam_n):

@@ -237,6 +237,8 @@ amr_status amr_hydro_destroy(amr_hydro_ctx *c) {
     for (auto &L : c->lv) L.release();
     for (auto &B : c->boxes) B.release();
     c->box_plan.release();
+    c->box_desc.release();
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     c->scal.release();
     c->dtbuf.release();
     c->cflag.release();
@@ -312,6 +314,17 @@ amr_status amr_hydro_unpack_uniform(const double *patches, int nx, int ny, int n
 }  // extern "C"
 
 namespace amrh {
+
+// Max signal speed and unphysical count of n_slots patches into (smax, nbad),
+// which the caller has zeroed.
+amr_status launch_max_speed(int prec, const double *U, int64_t n_slots, double gamma, unsigned long long *smax,
+                            unsigned long long *nbad, int n_sm, cudaStream_t stream) {
+    if (prec == AMR_FP64)
+        k_max_speed<double><<<n_sm * 8, 256, 0, stream>>>(U, n_slots, gamma, smax, nbad);
+    else
+        k_max_speed<float><<<n_sm * 8, 256, 0, stream>>>(U, n_slots, gamma, smax, nbad);
+    return cuda_fail(cudaGetLastError(), "k_max_speed");
+}
 
 double level_dh(const amr_hydro_ctx *c, int level) {
     return c->prm.box[0] / c->prm.root_n[0] / (double)(1 << level);

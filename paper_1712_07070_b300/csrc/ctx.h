@@ -84,8 +84,17 @@ struct Box {
     double *U[2] = {nullptr, nullptr};
     int cur = 0;
     int ring = 0;
+    bool speed_valid = false;
     DevBuf<int32_t> nbr;
     void release() { nbr.release(); n = 0; }
+};
+
+// Launch configuration of the box-batch kernel chosen by the autotuner.
+struct BoxTune {
+    int grid = 0;        // CTAs of the persistent launch
+    int chunked = 0;     // contiguous runs of work items per CTA (1) or grid-stride (0)
+    int interleave = 0;  // work list interleaves the boxes (1) or is box-major (0)
+    float ms = 0.f;      // measured time of one batch step
 };
 
 }  // namespace amrh
@@ -101,10 +110,14 @@ struct amr_hydro_ctx {
     amrh::DevBuf<uint8_t> cflag, pflag;  // refinement flag scratch
     amrh::DevBuf<double> psum;           // per-patch conservation partials
     amrh::DevBuf<int32_t> regrid_tmp;    // slot maps / interpolation jobs of a regrid
-    // batched-box launch plan and its captured graph
-    amrh::DevBuf<int32_t> box_plan;
+    // batched-box launch plan, tuning and its captured graph
+    amrh::DevBuf<int32_t> box_plan;   // (box, group) work items
+    amrh::DevBuf<uint8_t> box_desc;
+    std::vector<int> plan_key, tune_key;
+    amrh::BoxTune tune;
+    cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
-    std::vector<int> graph_key;
+    std::vector<long long> graph_key;
 };
 
 namespace amrh {
@@ -116,6 +129,8 @@ size_t step_smem_bytes(int prec);
 struct StepParams;
 amr_status launch_step(amr_hydro_ctx *c, const StepParams &P, int grid);
 amr_status launch_step_raw(int prec, const StepParams &P, cudaStream_t stream);
+amr_status launch_max_speed(int prec, const double *U, int64_t n_slots, double gamma, unsigned long long *smax,
+                            unsigned long long *nbad, int n_sm, cudaStream_t stream);
 // AMR (amr_ops.cu, regrid.cpp)
 amr_status fill_ghost_impl(amr_hydro_ctx *c, int level, double t);
 amr_status interp_new_patches(amr_hydro_ctx *c, int coarse, double *out, const int32_t *out_slot,

@@ -187,12 +187,186 @@ __device__ __forceinline__ void hancock_cell(const StepSmem<real> &S, int x, int
         for (int v = 0; v < NV; v++) uf[f][v] += dtdh_half * inc[v];
 }
 
+// One patch group: the whole fused step for group `grp` of P's level.  The
+// caller has set S.dt; smax_r / nbad accumulate the new state's largest
+// signal speed and its unphysical cells.
+template <typename real>
+__device__ __forceinline__ void step_group(StepSmem<real> &S, const StepParams &P, int grp, double dt,
+                                           const Gas<real> &g, real &smax_r, unsigned &nbad) {
+    const int tid = threadIdx.x;
+    const int cx = tid & 15, cy = tid >> 4;  // this thread's (x,y) column
+    const double dtdh = dt / P.dh;
+    const real dtdh_r = (real)dtdh;
+    const real dtdh_half = (real)(0.5 * dt / P.dh);
+    if (tid < 64) S.nbr[tid] = P.nbr[(int64_t)grp * 64 + tid];
+    if (tid == 0) S.any_cf = 0;
+    __syncthreads();
+    if (tid < 6) {
+        const long long o = P.cf.fine_off ? P.cf.fine_off[(int64_t)grp * 6 + tid] : -1;
+        S.cfo[tid] = o;
+        if (o >= 0) S.any_cf = 1;
+    }
+    if (tid >= 64 && tid < 112) {
+        const int k = tid - 64;
+        const long long o = P.cf.coarse_off ? P.cf.coarse_off[((int64_t)grp * 8 + k / 6) * 6 + k % 6] : -1;
+        S.cco[k] = o;
+        if (o >= 0) S.any_cf = 1;
+    }
+    __syncthreads();
+    load_plane(S, P, -2, g);
+    load_plane(S, P, -1, g);
+
+    real zp_prev[NV];   // high z face state of this column's cell at z-1
+    real acc[NV];       // flux divergence of this column's cell at z-1 (minus its top z flux)
+#pragma unroll
+    for (int v = 0; v < NV; v++) { zp_prev[v] = real(0); acc[v] = real(0); }
+
+    for (int z = -1; z <= GE; z++) {
+        load_plane(S, P, z + 1, g);
+        __syncthreads();
+
+        // ---- B: Hancock states of plane z
+        real zm[NV], zp[NV];
+        {
+            real uf[6][NV];
+            hancock_cell(S, cx, cy, z, dtdh_half, g, uf);
+#pragma unroll
+            for (int v = 0; v < NV; v++) { zm[v] = uf[4][v]; zp[v] = uf[5][v]; }
+            if (z >= 0 && z < GE) {
+#pragma unroll
+                for (int v = 0; v < NV; v++) {
+                    S.XS[0][v][cy][cx + 1] = uf[0][v];
+                    S.XS[1][v][cy][cx + 1] = uf[1][v];
+                    S.YS[0][v][cy + 1][cx] = uf[2][v];
+                    S.YS[1][v][cy + 1][cx] = uf[3][v];
+                }
+            }
+        }
+        if (z >= 0 && z < GE && tid < 64) {
+            // ring cells: x = -1 / 16 (rows 0..15), then y = -1 / 16 (columns 0..15)
+            const int r = tid & 15;
+            const bool xring = tid < 32;
+            const int side = (tid >> 4) & 1;
+            const int x = xring ? (side ? GE : -1) : r;
+            const int y = xring ? r : (side ? GE : -1);
+            real uf[6][NV];
+            hancock_cell(S, x, y, z, dtdh_half, g, uf);
+            if (xring) {
+#pragma unroll
+                for (int v = 0; v < NV; v++) {
+                    S.XS[0][v][y][x + 1] = uf[0][v];
+                    S.XS[1][v][y][x + 1] = uf[1][v];
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < NV; v++) {
+                    S.YS[0][v][y + 1][x] = uf[2][v];
+                    S.YS[1][v][y + 1][x] = uf[3][v];
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- C: fluxes
+        real fz[NV];
+        if (z >= 0) {
+            hllc<2>(zp_prev, zm, fz, g);
+            if (z == 0 || z == GE || (z == 8)) {
+                const int pl = (cx >> 3) + 2 * (cy >> 3);
+                cf_register<2>(S, P, dt, fz, cx, cy, z == 0 ? -1 : pl + 4 * ((z - 1) >> 3),
+                               z == GE ? -1 : pl + 4 * (z >> 3), z == 0, z == GE);
+            }
+        }
+        if (z >= 0 && z < GE) {
+            real uL[NV], uR[NV], F[NV];
+            // x face at cx-1/2 of row cy
+#pragma unroll
+            for (int v = 0; v < NV; v++) { uL[v] = S.XS[1][v][cy][cx]; uR[v] = S.XS[0][v][cy][cx + 1]; }
+            hllc<0>(uL, uR, F, g);
+#pragma unroll
+            for (int v = 0; v < NV; v++) S.FX[v][cy][cx] = F[v];
+            if ((cx & 7) == 0) {
+                const int pr = (cy >> 3) * 2 + (z >> 3) * 4;
+                cf_register<0>(S, P, dt, F, cy, z, cx == 0 ? -1 : pr, pr + (cx >> 3), cx == 0, false);
+            }
+            // y face at cy-1/2 of column cx
+#pragma unroll
+            for (int v = 0; v < NV; v++) { uL[v] = S.YS[1][v][cy][cx]; uR[v] = S.YS[0][v][cy + 1][cx]; }
+            hllc<1>(uL, uR, F, g);
+#pragma unroll
+            for (int v = 0; v < NV; v++) S.FY[v][cy][cx] = F[v];
+            if ((cy & 7) == 0) {
+                const int pr = (cx >> 3) + (z >> 3) * 4;
+                cf_register<1>(S, P, dt, F, cx, z, cy == 0 ? -1 : pr, pr + 2 * (cy >> 3), cy == 0, false);
+            }
+            if (tid < 32) {  // the high boundary faces x = 16-1/2 and y = 16-1/2
+                const int r = tid & 15;
+                if (tid < 16) {
+#pragma unroll
+                    for (int v = 0; v < NV; v++) { uL[v] = S.XS[1][v][r][GE]; uR[v] = S.XS[0][v][r][GE + 1]; }
+                    hllc<0>(uL, uR, F, g);
+#pragma unroll
+                    for (int v = 0; v < NV; v++) S.FX[v][r][GE] = F[v];
+                    cf_register<0>(S, P, dt, F, r, z, 1 + (r >> 3) * 2 + (z >> 3) * 4, -1, false, true);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < NV; v++) { uL[v] = S.YS[1][v][GE][r]; uR[v] = S.YS[0][v][GE + 1][r]; }
+                    hllc<1>(uL, uR, F, g);
+#pragma unroll
+                    for (int v = 0; v < NV; v++) S.FY[v][GE][r] = F[v];
+                    cf_register<1>(S, P, dt, F, r, z, (r >> 3) + 2 + (z >> 3) * 4, -1, false, true);
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- D: finish cell (cx,cy,z-1), start cell (cx,cy,z)
+        const int64_t own = (int64_t)grp * 8;
+        if (z >= 1) {
+            const int zc = z - 1;
+            const int64_t base = (own + (cx >> 3) + 2 * (cy >> 3) + 4 * (zc >> 3)) * PSLOT +
+                                 (zc & 7) * 64 + (cy & 7) * 8 + (cx & 7);
+            real ur[NV];  // the new state in the compute type, for its signal speed
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+                const real tot = acc[v] + fz[v];
+                const double uo = P.U_old[base + v * PV];
+                double un;
+                if constexpr (sizeof(real) == sizeof(double)) {
+                    un = uo - dtdh * tot;
+                    ur[v] = un;
+                } else {
+                    // FP32 increment accumulated into the FP64 state
+                    const real inc = dtdh_r * tot;
+                    un = uo - f2d_bits(inc);
+                    ur[v] = d2f_bits(uo) - inc;
+                }
+                P.U_new[base + v * PV] = un;
+            }
+            bool ok;
+            const real s = cfl_speed(ur, g, ok);
+            if (!ok) nbad++;
+            if (s > smax_r) smax_r = s;
+        }
+        if (z >= 0 && z < GE) {
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+                const real dxy = (S.FX[v][cy][cx + 1] - S.FX[v][cy][cx]) +
+                                 (S.FY[v][cy + 1][cx] - S.FY[v][cy][cx]);
+                acc[v] = dxy - fz[v];
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; v++) zp_prev[v] = zp[v];
+    }
+    __syncthreads();  // the next group overwrites nbr and the ring
+}
+
 template <typename real>
 __global__ void __launch_bounds__(STEP_THREADS, 1) k_hydro_step(StepParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<real> &S = *reinterpret_cast<StepSmem<real> *>(smem_raw);
     const int tid = threadIdx.x;
-    const int cx = tid & 15, cy = tid >> 4;  // this thread's (x,y) column
 
     Gas<real> g;
     g.gamma = (real)P.gamma;
@@ -218,176 +392,12 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_hydro_step(StepParams P) {
     }
     __syncthreads();
     const double dt = S.dt;
-    const double dtdh = dt / P.dh;
-    const real dtdh_r = (real)dtdh;
-    const real dtdh_half = (real)(0.5 * dt / P.dh);
     real smax_r = real(0);
     unsigned nbad = 0;
 
     for (int wi = blockIdx.x; wi < P.n_work; wi += gridDim.x) {
         const int grp = P.work ? P.work[wi] : wi;
-        if (tid < 64) S.nbr[tid] = P.nbr[(int64_t)grp * 64 + tid];
-        if (tid == 0) S.any_cf = 0;
-        __syncthreads();
-        if (tid < 6) {
-            const long long o = P.cf.fine_off ? P.cf.fine_off[(int64_t)grp * 6 + tid] : -1;
-            S.cfo[tid] = o;
-            if (o >= 0) S.any_cf = 1;
-        }
-        if (tid >= 64 && tid < 112) {
-            const int k = tid - 64;
-            const long long o = P.cf.coarse_off ? P.cf.coarse_off[((int64_t)grp * 8 + k / 6) * 6 + k % 6] : -1;
-            S.cco[k] = o;
-            if (o >= 0) S.any_cf = 1;
-        }
-        __syncthreads();
-        load_plane(S, P, -2, g);
-        load_plane(S, P, -1, g);
-
-        real zp_prev[NV];   // high z face state of this column's cell at z-1
-        real acc[NV];       // flux divergence of this column's cell at z-1 (minus its top z flux)
-#pragma unroll
-        for (int v = 0; v < NV; v++) { zp_prev[v] = real(0); acc[v] = real(0); }
-
-        for (int z = -1; z <= GE; z++) {
-            load_plane(S, P, z + 1, g);
-            __syncthreads();
-
-            // ---- B: Hancock states of plane z
-            real zm[NV], zp[NV];
-            {
-                real uf[6][NV];
-                hancock_cell(S, cx, cy, z, dtdh_half, g, uf);
-#pragma unroll
-                for (int v = 0; v < NV; v++) { zm[v] = uf[4][v]; zp[v] = uf[5][v]; }
-                if (z >= 0 && z < GE) {
-#pragma unroll
-                    for (int v = 0; v < NV; v++) {
-                        S.XS[0][v][cy][cx + 1] = uf[0][v];
-                        S.XS[1][v][cy][cx + 1] = uf[1][v];
-                        S.YS[0][v][cy + 1][cx] = uf[2][v];
-                        S.YS[1][v][cy + 1][cx] = uf[3][v];
-                    }
-                }
-            }
-            if (z >= 0 && z < GE && tid < 64) {
-                // ring cells: x = -1 / 16 (rows 0..15), then y = -1 / 16 (columns 0..15)
-                const int r = tid & 15;
-                const bool xring = tid < 32;
-                const int side = (tid >> 4) & 1;
-                const int x = xring ? (side ? GE : -1) : r;
-                const int y = xring ? r : (side ? GE : -1);
-                real uf[6][NV];
-                hancock_cell(S, x, y, z, dtdh_half, g, uf);
-                if (xring) {
-#pragma unroll
-                    for (int v = 0; v < NV; v++) {
-                        S.XS[0][v][y][x + 1] = uf[0][v];
-                        S.XS[1][v][y][x + 1] = uf[1][v];
-                    }
-                } else {
-#pragma unroll
-                    for (int v = 0; v < NV; v++) {
-                        S.YS[0][v][y + 1][x] = uf[2][v];
-                        S.YS[1][v][y + 1][x] = uf[3][v];
-                    }
-                }
-            }
-            __syncthreads();
-
-            // ---- C: fluxes
-            real fz[NV];
-            if (z >= 0) {
-                hllc<2>(zp_prev, zm, fz, g);
-                if (z == 0 || z == GE || (z == 8)) {
-                    const int pl = (cx >> 3) + 2 * (cy >> 3);
-                    cf_register<2>(S, P, dt, fz, cx, cy, z == 0 ? -1 : pl + 4 * ((z - 1) >> 3),
-                                   z == GE ? -1 : pl + 4 * (z >> 3), z == 0, z == GE);
-                }
-            }
-            if (z >= 0 && z < GE) {
-                real uL[NV], uR[NV], F[NV];
-                // x face at cx-1/2 of row cy
-#pragma unroll
-                for (int v = 0; v < NV; v++) { uL[v] = S.XS[1][v][cy][cx]; uR[v] = S.XS[0][v][cy][cx + 1]; }
-                hllc<0>(uL, uR, F, g);
-#pragma unroll
-                for (int v = 0; v < NV; v++) S.FX[v][cy][cx] = F[v];
-                if ((cx & 7) == 0) {
-                    const int pr = (cy >> 3) * 2 + (z >> 3) * 4;
-                    cf_register<0>(S, P, dt, F, cy, z, cx == 0 ? -1 : pr, pr + (cx >> 3), cx == 0, false);
-                }
-                // y face at cy-1/2 of column cx
-#pragma unroll
-                for (int v = 0; v < NV; v++) { uL[v] = S.YS[1][v][cy][cx]; uR[v] = S.YS[0][v][cy + 1][cx]; }
-                hllc<1>(uL, uR, F, g);
-#pragma unroll
-                for (int v = 0; v < NV; v++) S.FY[v][cy][cx] = F[v];
-                if ((cy & 7) == 0) {
-                    const int pr = (cx >> 3) + (z >> 3) * 4;
-                    cf_register<1>(S, P, dt, F, cx, z, cy == 0 ? -1 : pr, pr + 2 * (cy >> 3), cy == 0, false);
-                }
-                if (tid < 32) {  // the high boundary faces x = 16-1/2 and y = 16-1/2
-                    const int r = tid & 15;
-                    if (tid < 16) {
-#pragma unroll
-                        for (int v = 0; v < NV; v++) { uL[v] = S.XS[1][v][r][GE]; uR[v] = S.XS[0][v][r][GE + 1]; }
-                        hllc<0>(uL, uR, F, g);
-#pragma unroll
-                        for (int v = 0; v < NV; v++) S.FX[v][r][GE] = F[v];
-                        cf_register<0>(S, P, dt, F, r, z, 1 + (r >> 3) * 2 + (z >> 3) * 4, -1, false, true);
-                    } else {
-#pragma unroll
-                        for (int v = 0; v < NV; v++) { uL[v] = S.YS[1][v][GE][r]; uR[v] = S.YS[0][v][GE + 1][r]; }
-                        hllc<1>(uL, uR, F, g);
-#pragma unroll
-                        for (int v = 0; v < NV; v++) S.FY[v][GE][r] = F[v];
-                        cf_register<1>(S, P, dt, F, r, z, (r >> 3) + 2 + (z >> 3) * 4, -1, false, true);
-                    }
-                }
-            }
-            __syncthreads();
-
-            // ---- D: finish cell (cx,cy,z-1), start cell (cx,cy,z)
-            const int64_t own = (int64_t)grp * 8;
-            if (z >= 1) {
-                const int zc = z - 1;
-                const int64_t base = (own + (cx >> 3) + 2 * (cy >> 3) + 4 * (zc >> 3)) * PSLOT +
-                                     (zc & 7) * 64 + (cy & 7) * 8 + (cx & 7);
-                real ur[NV];  // the new state in the compute type, for its signal speed
-#pragma unroll
-                for (int v = 0; v < NV; v++) {
-                    const real tot = acc[v] + fz[v];
-                    const double uo = P.U_old[base + v * PV];
-                    double un;
-                    if constexpr (sizeof(real) == sizeof(double)) {
-                        un = uo - dtdh * tot;
-                        ur[v] = un;
-                    } else {
-                        // FP32 increment accumulated into the FP64 state
-                        const real inc = dtdh_r * tot;
-                        un = uo - f2d_bits(inc);
-                        ur[v] = d2f_bits(uo) - inc;
-                    }
-                    P.U_new[base + v * PV] = un;
-                }
-                bool ok;
-                const real s = cfl_speed(ur, g, ok);
-                if (!ok) nbad++;
-                if (s > smax_r) smax_r = s;
-            }
-            if (z >= 0 && z < GE) {
-#pragma unroll
-                for (int v = 0; v < NV; v++) {
-                    const real dxy = (S.FX[v][cy][cx + 1] - S.FX[v][cy][cx]) +
-                                     (S.FY[v][cy + 1][cx] - S.FY[v][cy][cx]);
-                    acc[v] = dxy - fz[v];
-                }
-            }
-#pragma unroll
-            for (int v = 0; v < NV; v++) zp_prev[v] = zp[v];
-        }
-        __syncthreads();  // the next group overwrites nbr and the ring
+        step_group(S, P, grp, dt, g, smax_r, nbad);
     }
 
     // ---- block reduction of the signal speed, one atomic per block
@@ -406,6 +416,107 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_hydro_step(StepParams P) {
         atomicMax(P.smax_out, (unsigned long long)__double_as_longlong(m));
     }
     if ((tid & 31) == 0 && nb) atomicAdd(P.n_bad, (unsigned long long)nb);
+}
+
+// ---- independent periodic boxes in one persistent launch ------------------------
+
+// A box registered with amr_hydro_set_box: a fully covered periodic level.
+struct BoxDesc {
+    double *U[2];
+    const int32_t *nbr;           // [n_groups][64]
+    unsigned long long *scal;     // the box's 8 scalar slots (ring of speeds, counts)
+    double dh;
+    int n_groups, cur0, ring0, log_index;
+};
+
+struct BoxLaunch {
+    const BoxDesc *desc;
+    const int2 *work;   // (box, group) items
+    int n_work;
+    int step;           // step index within this batch: buffers and ring advance with it
+    int chunked;        // 1: each CTA takes a contiguous run of items; 0: grid-stride
+    double cfl, gamma;
+    double dt_override; // >= 0 (autotuning): fixed dt, no logging
+    double *dt_log;     // [steps][n_boxes] or null
+    int n_boxes;
+};
+
+template <typename real>
+__global__ void __launch_bounds__(STEP_THREADS, 1) k_hydro_step_boxes(BoxLaunch B) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StepSmem<real> &S = *reinterpret_cast<StepSmem<real> *>(smem_raw);
+    const int tid = threadIdx.x;
+    Gas<real> g;
+    g.gamma = (real)B.gamma;
+    g.gm1 = (real)(B.gamma - 1.0);
+    g.inv_gm1 = (real)(1.0 / (B.gamma - 1.0));
+    int first, last, stride;
+    if (B.chunked) {
+        const int per = (B.n_work + gridDim.x - 1) / gridDim.x;
+        first = blockIdx.x * per;
+        last = min(B.n_work, first + per);
+        stride = 1;
+    } else {
+        first = blockIdx.x;
+        last = B.n_work;
+        stride = gridDim.x;
+    }
+    for (int wi = first; wi < last; wi += stride) {
+        const int2 it = B.work[wi];
+        const BoxDesc &d = B.desc[it.x];
+        const int cur = (d.cur0 + B.step) & 1;
+        const int r_in = (d.ring0 + B.step) % 3, r_out = (d.ring0 + B.step + 1) % 3, r_clr = (d.ring0 + B.step + 2) % 3;
+        if (tid == 0) {
+            double dt = B.dt_override;
+            if (dt < 0.0) dt = B.cfl * d.dh / __longlong_as_double((long long)d.scal[r_in]);
+            S.dt = dt;
+            if (it.y == 0 && B.dt_override < 0.0) {
+                d.scal[r_clr] = 0ull;
+                d.scal[3 + r_clr] = 0ull;
+                if (B.dt_log) B.dt_log[(int64_t)B.step * B.n_boxes + d.log_index] = dt;
+            }
+        }
+        __syncthreads();
+        StepParams P;
+        P.U_old = d.U[cur];
+        P.U_new = d.U[1 - cur];
+        P.nbr = d.nbr;
+        P.ghost = nullptr;
+        P.work = nullptr;
+        P.n_work = d.n_groups;
+        P.dt = S.dt;
+        P.smax_in = nullptr;
+        P.cfl = B.cfl;
+        P.dh = d.dh;
+        P.gamma = B.gamma;
+        P.smax_out = d.scal + r_out;
+        P.n_bad = d.scal + 3 + r_out;
+        P.clear2 = nullptr;
+        P.time_rec = nullptr;
+        P.cf.fine_off = nullptr;
+        P.cf.fine_buf = nullptr;
+        P.cf.coarse_off = nullptr;
+        P.cf.coarse_buf = nullptr;
+        real smax_r = real(0);
+        unsigned nbad = 0;
+        step_group(S, P, it.y, S.dt, g, smax_r, nbad);
+        // this group's largest signal speed and unphysical count into its box
+        double smax = (double)smax_r;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+        unsigned nb = nbad;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nb += __shfl_xor_sync(0xffffffffu, nb, o);
+        if ((tid & 31) == 0) S.red[tid >> 5] = smax;
+        __syncthreads();
+        if (tid == 0) {
+            double m = 0.0;
+            for (int i = 0; i < STEP_THREADS / 32; i++) m = fmax(m, S.red[i]);
+            atomicMax(P.smax_out, (unsigned long long)__double_as_longlong(m));
+        }
+        if ((tid & 31) == 0 && nb) atomicAdd(P.n_bad, (unsigned long long)nb);
+        __syncthreads();
+    }
 }
 
 }  // namespace amrh
