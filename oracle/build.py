@@ -9,7 +9,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["hydro_oracle.c", "amr_oracle.c", "adjoint_oracle.c"]
+SOURCES = ["hydro_oracle.c", "amr_oracle.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 # -ffp-contract=off: no fused multiply-adds, so every operation rounds exactly
 # as written; no -march=native: the library must also run on another host.
@@ -17,6 +17,7 @@ CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off"
 
 
 FLOPLIB = os.path.join(HERE, "libflopcount.so")
+ADLIB = os.path.join(HERE, "liboracle_ad.so")
 
 
 def _stale(lib, srcs):
@@ -36,6 +37,11 @@ def build(force=False):
         # operator-overloaded counting type
         subprocess.run(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-Wno-unknown-pragmas",
                         "-o", FLOPLIB, fsrc[0]], check=True)
+    asrc = [os.path.join(HERE, "adjoint_oracle.cpp"), os.path.join(HERE, "hydro_oracle.c")]
+    if force or _stale(ADLIB, asrc):
+        # the taping / dual-number builds: no OpenMP (the tape is sequential)
+        subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off",
+                        "-Wno-unknown-pragmas", "-o", ADLIB, asrc[0]], check=True)
     return LIB
 
 
