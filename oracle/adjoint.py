@@ -18,6 +18,7 @@ def ad_lib():
         vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
         L.or_adj_step.argtypes = [vp, vp, vp, i, i, i, d, d, d]
         L.or_jvp_step.argtypes = [vp, vp, vp, i, i, i, d, d, d]
+        L.or_adj_hllc.argtypes = [vp, vp, i, d, vp, vp, vp]
         _ad = L
     return _ad
 
@@ -42,6 +43,14 @@ def jvp_step(U, V, dh, dt, gamma):
     _, nz, ny, nx = U.shape
     ad_lib().or_jvp_step(U.ctypes.data, V.ctypes.data, out.ctypes.data, nx, ny, nz, dh, dt, gamma)
     return out
+
+
+def adj_hllc(UL, UR, d, gamma, lamF):
+    """(dF/dUL)^T lamF, (dF/dUR)^T lamF of one HLLC face evaluation."""
+    UL, UR, lamF = _c(UL), _c(UR), _c(lamF)
+    a, b = np.empty(5), np.empty(5)
+    ad_lib().or_adj_hllc(UL.ctypes.data, UR.ctypes.data, d, gamma, lamF.ctypes.data, a.ctypes.data, b.ctypes.data)
+    return a, b
 
 
 def run_frozen(U0, dts, dh, gamma):

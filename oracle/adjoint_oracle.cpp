@@ -145,3 +145,29 @@ extern "C" void or_jvp_step(const double *U, const double *V, double *JV, int nx
                              nullptr);
     for (int64_t i = 0; i < n; i++) JV[i] = un[i].d;
 }
+
+// Transposed Jacobian of one HLLC flux evaluation: lamUL, lamUR =
+// (dF/dUL)^T lamF, (dF/dUR)^T lamF, for a face normal to d.
+extern "C" void or_adj_hllc(const double *UL, const double *UR, int d, double gamma, const double *lamF,
+                            double *lamUL, double *lamUR) {
+    std::vector<rev::Node> t;
+    rev::tape = &t;
+    rev::AD uL[5], uR[5], F[5];
+    for (int v = 0; v < 5; v++) uL[v] = rev::leaf(UL[v]);
+    for (int v = 0; v < 5; v++) uR[v] = rev::leaf(UR[v]);
+    rev::or_hllc(uL, uR, d, rev::AD(gamma), F);
+    std::vector<double> adj(t.size(), 0.0);
+    for (int v = 0; v < 5; v++)
+        if (F[v].id >= 0) adj[F[v].id] += lamF[v];
+    for (int64_t k = (int64_t)t.size() - 1; k >= 0; k--) {
+        const double g = adj[k];
+        if (g == 0.0) continue;
+        if (t[k].a >= 0) adj[t[k].a] += t[k].da * g;
+        if (t[k].b >= 0) adj[t[k].b] += t[k].db * g;
+    }
+    for (int v = 0; v < 5; v++) {
+        lamUL[v] = adj[uL[v].id];
+        lamUR[v] = adj[uR[v].id];
+    }
+    rev::tape = nullptr;
+}

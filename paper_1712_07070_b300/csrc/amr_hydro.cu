@@ -245,6 +245,7 @@ amr_status amr_hydro_destroy(amr_hydro_ctx *c) {
     c->pflag.release();
     c->psum.release();
     c->regrid_tmp.release();
+    c->adjbuf.release();
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     delete c;
     return AMR_OK;

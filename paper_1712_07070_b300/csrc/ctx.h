@@ -110,6 +110,7 @@ struct amr_hydro_ctx {
     amrh::DevBuf<uint8_t> cflag, pflag;  // refinement flag scratch
     amrh::DevBuf<double> psum;           // per-patch conservation partials
     amrh::DevBuf<int32_t> regrid_tmp;    // slot maps / interpolation jobs of a regrid
+    amrh::DevBuf<double> adjbuf;         // dense scratch of the adjoint step
     // batched-box launch plan, tuning and its captured graph
     amrh::DevBuf<int32_t> box_plan;   // (box, group) work items
     amrh::DevBuf<uint8_t> box_desc;

@@ -1,0 +1,127 @@
+"""The hand-written discrete-adjoint kernels against the oracle's taped
+reverse mode (one HLLC face; one whole step on 16^3 = one patch group and on
+a non-cubic box), and gradients of the final-density loss through the
+autograd Function with sqrt(N) checkpointing against central finite
+differences (step 1e-6) on seeded smooth directions, at a small size and at
+the adjoint workload's full size (128^3, 40 steps, 32 directions)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import adjoint as OD
+from paper_1712_07070_b300 import amr_hydro as A
+from paper_1712_07070_b300 import ics
+
+pytestmark = pytest.mark.gpu
+G53 = 5.0 / 3.0
+
+
+def spun_up(n, seed, steps=2, **kw):
+    # away from the limiter kinks of the uniform-density initial state
+    U = ics.turbulence(n, seed=seed, **kw)
+    U, _ = oracle.run_periodic(U, 1.0 / n, G53, 0.5, steps)
+    return U
+
+
+def test_hllc_vjp_matches_oracle_tape():
+    import torch
+    rng = np.random.default_rng(3)
+    m = 400
+    WL = np.stack([rng.uniform(0.2, 3, m), rng.normal(0, 1.5, m), rng.normal(0, 1.5, m), rng.normal(0, 1.5, m),
+                   rng.uniform(0.1, 3, m)], 1)
+    WR = np.stack([rng.uniform(0.2, 3, m), rng.normal(0, 1.5, m), rng.normal(0, 1.5, m), rng.normal(0, 1.5, m),
+                   rng.uniform(0.1, 3, m)], 1)
+    UL = np.array([oracle.cons(w, G53) for w in WL])
+    UR = np.array([oracle.cons(w, G53) for w in WR])
+    lF = rng.normal(size=(m, 5))
+    fn = A.lib().amrh_selftest_hllc_vjp
+    fn.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_int, ctypes.c_double] + [ctypes.c_void_p] * 2
+    for d in range(3):
+        t = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (UL, UR, lF)]
+        a = torch.empty((m, 5), dtype=torch.float64, device="cuda")
+        b = torch.empty_like(a)
+        assert fn(t[0].data_ptr(), t[1].data_ptr(), t[2].data_ptr(), m, d, G53, a.data_ptr(), b.data_ptr()) == 0
+        a, b = a.cpu().numpy(), b.cpu().numpy()
+        for i in range(m):
+            ra, rb = OD.adj_hllc(UL[i], UR[i], d, G53, lF[i])
+            scale = np.abs(np.concatenate([ra, rb])).max() + 1e-300
+            assert np.abs(a[i] - ra).max() <= 1e-12 * scale and np.abs(b[i] - rb).max() <= 1e-12 * scale, (d, i)
+
+
+def gpu_adjoint_step(U, lam, dt):
+    import torch
+    from paper_1712_07070_b300.uniform import UniformGrid
+    nz, ny, nx = U.shape[1:]
+    g = UniformGrid((nx, ny, nz))
+    g.upload(U)
+    Ud = g.state().clone()
+    lp = torch.empty_like(Ud)
+    A.amr_hydro_pack_uniform(torch.from_numpy(lam).cuda(), nx, ny, nz, lp)
+    out = torch.empty_like(Ud)
+    A.amr_hydro_step_adjoint(g.ctx, 0, dt, Ud, lp, out)
+    dense = torch.empty((5, nz, ny, nx), dtype=torch.float64, device="cuda")
+    A.amr_hydro_unpack_uniform(out, nx, ny, nz, dense)
+    g.close()
+    return dense.cpu().numpy()
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 16), (32, 16, 48)])
+def test_step_adjoint_matches_oracle(shape):
+    nx, ny, nz = shape
+    U = ics.sod_noise(nx, seed=4, ny=ny, nz=nz)
+    U, _ = oracle.run_periodic(U, 1.0 / nx, G53, 0.5, 2)
+    dt = oracle.dt_cfl2(U, G53, 0.5, 1.0 / nx)
+    lam = np.random.default_rng(1).normal(size=U.shape)
+    ref = OD.adj_step(U, lam, 1.0 / nx, dt, G53)
+    got = gpu_adjoint_step(U, lam, dt)
+    err = np.abs(got - ref).sum() / np.abs(ref).sum()
+    assert err <= 1e-10, err
+
+
+def grad_and_fd(n, n_steps, n_dirs, seed=5, h=1e-6, with_oracle=False):
+    import torch
+    from paper_1712_07070_b300.adjoint import CheckpointedRun, HydroRun, density_loss
+    U0 = spun_up(n, seed)
+    target_np = spun_up(n, seed, density_seed=6)[0]
+    target = torch.from_numpy(target_np).cuda()
+    run = CheckpointedRun((n, n, n))
+    dts = run.record_dts(U0, n_steps)
+    dV = (1.0 / n) ** 3
+    U0t = torch.from_numpy(U0).cuda().requires_grad_(True)
+    L = density_loss(HydroRun.apply(U0t, run, dts), target, dV)
+    L.backward()
+    grad = U0t.grad
+    if with_oracle:
+        ref, _ = OD.gradient(U0, dts, 1.0 / n, G53, target_np)
+        err = np.abs(grad.cpu().numpy() - ref).sum() / np.abs(ref).sum()
+        assert err <= 1e-10, err
+    dirs = ics.smooth_directions(U0.shape, n_dirs, seed=11)
+    out = []
+    for v in dirs:
+        vt = torch.from_numpy(v).cuda()
+        with torch.no_grad():
+            Lp = density_loss(run.forward(U0t.detach() + h * vt, dts), target, dV).item()
+            Lm = density_loss(run.forward(U0t.detach() - h * vt, dts), target, dV).item()
+        out.append(((Lp - Lm) / (2 * h), float((grad * vt).sum().item())))
+    run.close()
+    return out
+
+
+def check_fd(res, tol=1e-4):
+    """Central differences at h = 1e-6 also cross limiter and HLLC branch
+    switches inside +-h (the oracle's own adjoint shows the same 1e-5..4e-4
+    relative gaps on these cases, shrinking in proportion to h), so the
+    check is against the typical size of the directional derivatives."""
+    typical = np.median([abs(g) for _, g in res])
+    bad = [(fd, g) for fd, g in res if not abs(fd - g) <= tol * max(abs(g), typical)]
+    assert not bad, bad
+
+
+def test_gradient_matches_oracle_and_finite_differences_small():
+    check_fd(grad_and_fd(32, 8, 4, with_oracle=True))
+
+
+def test_gradient_full_size_128_40_steps_32_directions():
+    check_fd(grad_and_fd(128, 40, 32))
