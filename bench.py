@@ -290,10 +290,113 @@ def run_ours(args):
         "variants": variants,
         "kernel_hash": kh,
     }
+    if not args.no_variants:
+        line["amr"] = bench_amr(torch, args)
+        line["boxes"] = bench_boxes(torch, args)
+        line["adjoint"] = bench_adjoint(torch, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def bench_amr(torch, args):
+    """3-level AMR: root 128^3 + 2 levels around 3 Gaussian blobs (contrast 100,
+    sigma 0.05) moving at Mach 2, adaptive W-cycle with fix-up and regrid every
+    level step; cell updates of all levels and substeps per second."""
+    from paper_1712_07070_b300 import amr_hydro as A
+    from paper_1712_07070_b300 import ics
+    from paper_1712_07070_b300.amr import AmrHierarchy
+    U0 = ics.blobs(128, seed=3)
+    out = {"workload": "AMR 128^3 root, lmax 2, 3 blobs (contrast 100, sigma 0.05, Mach 2), theta 0.1, "
+                       "N_buf 8/4, adaptive dt W-cycle with fix-up and regrid", "unit": UNIT}
+    for prec, name in ((A.AMR_FP64, "f64"), (A.AMR_FP32_ACC64, "fp32_acc64")):
+        H = AmrHierarchy(U0, lmax=2, theta=0.1, nbuf=(8, 4), prec=prec, max_patches=120000)
+        for _ in range(max(1, args.warmup // 2)):
+            H.advance_root()
+        torch.cuda.synchronize()
+        K = max(2, args.steps // 2)
+        e0, e1 = _events(torch)
+        e0.record()
+        n = 0
+        for _ in range(K):
+            n += H.advance_root()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"value": n / (ms * 1e-3), "ms_per_root_step": ms / K, "cell_updates_per_root_step": n // K,
+                     "patches": [H.n_patches(l) for l in range(3)]}
+        H.close()
+    out["value"] = out["f64"]["value"]
+    return out
+
+
+def bench_boxes(torch, args):
+    """64 periodic Kelvin-Helmholtz boxes of seeded sizes {32..192}^3, one
+    persistent launch per step over all of them, CUDA graph, autotuned."""
+    from paper_1712_07070_b300 import amr_hydro as A
+    from paper_1712_07070_b300 import ics
+    from paper_1712_07070_b300.boxes import BoxBatch
+    sizes = ics.kh_batch_sizes(64, seed=4)
+    cells = sum(n ** 3 for n in sizes)
+    B = BoxBatch(gamma=1.4, prec=A.AMR_FP32_ACC64)
+    for i, n in enumerate(sizes):
+        B.add_box(ics.kh_box(n, seed=100 + i, gamma=1.4))
+    B.advance(args.steps)  # autotune + capture the graph of K steps
+    B.advance(args.steps)
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch)
+    e0.record()
+    B.advance(args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    tune = B.tuning()
+    B.close()
+    return {"workload": f"64 periodic KH boxes, sizes {{32..192}}^3 (seed 4), {cells} cells, gamma 1.4, FP32 "
+                        f"compute / FP64 accumulate, one persistent launch per step, CUDA graph",
+            "value": cells / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "cells": cells, "tuning": tune,
+            "dtype": "fp32_acc64"}
+
+
+def bench_adjoint(torch, args):
+    """Adjoint/forward time ratio: 128^3 turbulence, 40 FP64 steps with a
+    frozen dt sequence, sqrt(N) checkpoints; backward = segment recompute +
+    adjoint kernels."""
+    from paper_1712_07070_b300 import ics
+    from paper_1712_07070_b300.adjoint import CheckpointedRun
+    n, N = 128, 40
+    run = CheckpointedRun((n, n, n))
+    U0 = torch.from_numpy(ics.turbulence(n, seed=5)).cuda()
+    for _ in range(2):  # spin up away from the uniform-density limiter kinks
+        run.grid.upload(U0)
+        run.grid.step(-1.0)
+        U0 = run.grid.download(out=torch.empty_like(U0))
+    dts = run.record_dts(U0, N)
+    lam = torch.zeros_like(U0)
+    lam[0] = 1.0 / n ** 3
+    run.forward(U0, dts)  # warm-up
+    run.backward(lam)
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch)
+    e0.record()
+    run.forward(U0, dts)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd = e0.elapsed_time(e1)
+    e0.record()
+    run.backward(lam)
+    e1.record()
+    torch.cuda.synchronize()
+    bwd = e0.elapsed_time(e1)
+    run.close()
+    return {"workload": "adjoint of 40 FP64 steps of 128^3 turbulence, sqrt(N) checkpoints", "forward_ms": fwd,
+            "backward_ms": bwd, "adjoint_forward_ratio": bwd / fwd,
+            "value": n ** 3 * N / (bwd * 1e-3), "unit": "adjoint cell updates/s"}
 
 
 def hbm_peak():
