@@ -42,55 +42,58 @@ struct CoarseView {
     }
 };
 
-// Conservative minmod-limited linear interpolation of the conserved
-// variables at fine cell f (relative to the parent's fine origin), with the
-// positivity fallback: if any of the eight children of the coarse cell would
-// have rho <= 0 or P <= 0, all eight take the coarse value.
-__device__ void interp_fine_cell(const CoarseView &C, int fx, int fy, int fz, double out[NV]) {
-    const int cx = fx >> 1, cy = fy >> 1, cz = fz >> 1;
-    double c[NV], sl[3][NV];
-#pragma unroll
-    for (int v = 0; v < NV; v++) {
-        c[v] = C.at(v, cx, cy, cz);
-        sl[0][v] = minmod(C.at(v, cx + 1, cy, cz) - c[v], c[v] - C.at(v, cx - 1, cy, cz));
-        sl[1][v] = minmod(C.at(v, cx, cy + 1, cz) - c[v], c[v] - C.at(v, cx, cy - 1, cz));
-        sl[2][v] = minmod(C.at(v, cx, cy, cz + 1) - c[v], c[v] - C.at(v, cx, cy, cz - 1));
-    }
-    bool ok = true;
-#pragma unroll
-    for (int k = 0; k < 8; k++) {
-        const double sx = (k & 1) ? 0.25 : -0.25, sy = (k & 2) ? 0.25 : -0.25, sz = (k & 4) ? 0.25 : -0.25;
-        double u[NV];
-#pragma unroll
-        for (int v = 0; v < NV; v++) u[v] = c[v] + sx * sl[0][v] + sy * sl[1][v] + sz * sl[2][v];
-        const double m2 = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
-        ok = ok && (u[0] > 0.0) && (2.0 * u[0] * u[4] > m2);
-    }
-    const double sx = (fx & 1) ? 0.25 : -0.25, sy = (fy & 1) ? 0.25 : -0.25, sz = (fz & 1) ? 0.25 : -0.25;
-#pragma unroll
-    for (int v = 0; v < NV; v++) out[v] = ok ? c[v] + sx * sl[0][v] + sy * sl[1][v] + sz * sl[2][v] : c[v];
-}
-
-// Fine patches interpolated from the coarse level.  Job j: info[4j..4j+3] =
-// (coarse parent P of the group the patch is placed around, patch position
-// q relative to that group, each -1..2); output patch out_slot[j] (or j).
+// Fine patches interpolated from the coarse level.  Job j (GHOST_INFO ints):
+// coarse parent P of the group the patch is placed around, patch position q
+// relative to that group (each -1..2), and the box of fine cells wanted
+// (even bounds); output patch out_slot[j] (or j).  One thread per coarse
+// cell of the box computes its value, slopes and positivity test once and
+// writes its eight children.
 __global__ void k_interp_patches(double *__restrict__ out, const int32_t *__restrict__ out_slot,
                                  const int32_t *__restrict__ info, int n_jobs, const double *Uo,
                                  const double *Un, double w, const int32_t *__restrict__ csib) {
     __shared__ int nb[27];
     for (int j = blockIdx.x; j < n_jobs; j += gridDim.x) {
-        const int P = info[4 * j], qx = info[4 * j + 1], qy = info[4 * j + 2], qz = info[4 * j + 3];
+        const int32_t *I = info + (int64_t)GHOST_INFO * j;
+        const int P = I[0], qx = I[1], qy = I[2], qz = I[3], box = I[4];
+        const int lo[3] = {box & 15, (box >> 4) & 15, (box >> 8) & 15};
+        const int hi[3] = {(box >> 12) & 15, (box >> 16) & 15, (box >> 20) & 15};
+        const int n[3] = {(hi[0] - lo[0]) >> 1, (hi[1] - lo[1]) >> 1, (hi[2] - lo[2]) >> 1};
         __syncthreads();
         load_block27(nb, P, csib);
         __syncthreads();
         CoarseView C{Uo, Un, w, nb};
         double *o = out + (int64_t)(out_slot ? out_slot[j] : j) * PSLOT;
-        for (int i = threadIdx.x; i < PV; i += blockDim.x) {
-            const int lx = i & 7, ly = (i >> 3) & 7, lz = i >> 6;
-            double u[NV];
-            interp_fine_cell(C, qx * 8 + lx, qy * 8 + ly, qz * 8 + lz, u);
+        const int total = n[0] * n[1] * n[2];
+        for (int i = threadIdx.x; i < total; i += blockDim.x) {
+            // local fine cell of the child (0,0,0) of this coarse cell
+            const int fx = lo[0] + 2 * (i % n[0]), fy = lo[1] + 2 * ((i / n[0]) % n[1]),
+                      fz = lo[2] + 2 * (i / (n[0] * n[1]));
+            // coarse cell relative to the parent's origin
+            const int cx = (qx * 8 + fx) >> 1, cy = (qy * 8 + fy) >> 1, cz = (qz * 8 + fz) >> 1;
+            double c[NV], sl[3][NV];
 #pragma unroll
-            for (int v = 0; v < NV; v++) o[v * PV + i] = u[v];
+            for (int v = 0; v < NV; v++) {
+                c[v] = C.at(v, cx, cy, cz);
+                sl[0][v] = minmod(C.at(v, cx + 1, cy, cz) - c[v], c[v] - C.at(v, cx - 1, cy, cz));
+                sl[1][v] = minmod(C.at(v, cx, cy + 1, cz) - c[v], c[v] - C.at(v, cx, cy - 1, cz));
+                sl[2][v] = minmod(C.at(v, cx, cy, cz + 1) - c[v], c[v] - C.at(v, cx, cy, cz - 1));
+            }
+            double u[8][NV];
+            bool ok = true;
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const double sx = (k & 1) ? 0.25 : -0.25, sy = (k & 2) ? 0.25 : -0.25, sz = (k & 4) ? 0.25 : -0.25;
+#pragma unroll
+                for (int v = 0; v < NV; v++) u[k][v] = c[v] + sx * sl[0][v] + sy * sl[1][v] + sz * sl[2][v];
+                const double m2 = u[k][1] * u[k][1] + u[k][2] * u[k][2] + u[k][3] * u[k][3];
+                ok = ok && (u[k][0] > 0.0) && (2.0 * u[k][0] * u[k][4] > m2);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int off = (fz + (k >> 2)) * 64 + (fy + ((k >> 1) & 1)) * 8 + fx + (k & 1);
+#pragma unroll
+                for (int v = 0; v < NV; v++) o[v * PV + off] = ok ? u[k][v] : c[v];
+            }
         }
     }
 }

@@ -34,7 +34,10 @@ constexpr int SCAL_N = SCAL_BOX0 + SCAL_PER * MAX_BOXES;
 struct GhostInfo {
     int32_t cparent;  // coarse slot of the neighbouring group's parent
     int32_t qx, qy, qz;  // patch position relative to that group (-1..2)
+    int32_t box;      // cells any group reads: 4-bit lo/hi per dim (lo_x | lo_y<<4 | lo_z<<8 |
+                      // hi_x<<12 | hi_y<<16 | hi_z<<20), even bounds in 0..8
 };
+constexpr int GHOST_INFO = 8;  // int32 per ghost-patch job on the device
 
 struct Level {
     int n_patches = 0, n_groups = 0;
@@ -46,7 +49,7 @@ struct Level {
     std::vector<int32_t> corner, sib, parent, child;  // host mirrors
     DevBuf<int32_t> nbr;        // [n_groups][64]
     DevBuf<double> ghost;       // [n_ghost][5][512]
-    DevBuf<int32_t> ghost_info; // [n_ghost][4]
+    DevBuf<int32_t> ghost_info; // [n_ghost][GHOST_INFO]
     int n_ghost = 0;
     // coarse-fine flux registers (section 2.2 fix-up)
     DevBuf<int64_t> fine_off;    // [n_groups*6]: this level's group faces on coarse-fine interfaces

@@ -2,8 +2,6 @@
 // (GAMER-2 section 2.1: octree of 8^3 patches storing parent, child and 26
 // sibling ids; section 3.1: patch groups of 8 siblings are the unit of work).
 #include <cstdint>
-#include <map>
-#include <tuple>
 #include <vector>
 
 #include "ctx.h"
@@ -64,7 +62,10 @@ amr_status build_nbr_plan(int level, int n_patches, const int32_t *corner, const
     const int n_groups = n_patches / 8;
     nbr.assign((size_t)n_groups * 64, -1);
     ghosts.clear();
-    std::map<std::tuple<int, int, int>, int> ghost_id;
+    // ghost patch ids by patch position (dense: the level's patch grid)
+    const int P[3] = {level_cells[0] / 8, level_cells[1] / 8, level_cells[2] / 8};
+    std::vector<int32_t> ghost_id;
+    if (level > 0) ghost_id.assign((size_t)P[0] * P[1] * P[2], -1);
     for (int g = 0; g < n_groups; g++) {
         for (int qz = -1; qz <= 2; qz++)
             for (int qy = -1; qy <= 2; qy++)
@@ -91,21 +92,37 @@ amr_status build_nbr_plan(int level, int n_patches, const int32_t *corner, const
                     const int cx = wrapi(corner[3 * own + 0] + 8 * dx, level_cells[0]);
                     const int cy = wrapi(corner[3 * own + 1] + 8 * dy, level_cells[1]);
                     const int cz = wrapi(corner[3 * own + 2] + 8 * dz, level_cells[2]);
-                    auto key = std::make_tuple(cx, cy, cz);
-                    auto it = ghost_id.find(key);
+                    int32_t &slot_id = ghost_id[((size_t)(cz / 8) * P[1] + cy / 8) * P[0] + cx / 8];
+                    // cells of this position the group's stencils reach: 2 deep
+                    // along an outer direction, all 8 along an inner one
+                    const int q3[3] = {qx, qy, qz};
+                    int lo[3], hi[3];
+                    for (int d = 0; d < 3; d++) {
+                        lo[d] = q3[d] < 0 ? 6 : 0;
+                        hi[d] = q3[d] > 1 ? 2 : 8;
+                    }
                     int id;
-                    if (it == ghost_id.end()) {
+                    if (slot_id < 0) {
                         id = (int)ghosts.size();
-                        ghost_id[key] = id;
+                        slot_id = id;
                         GhostInfo gi;
                         gi.cparent = parent[8 * g];
                         gi.qx = qx;
                         gi.qy = qy;
                         gi.qz = qz;
+                        gi.box = lo[0] | lo[1] << 4 | lo[2] << 8 | hi[0] << 12 | hi[1] << 16 | hi[2] << 20;
                         if (gi.cparent < 0) return AMR_E_NESTING;
                         ghosts.push_back(gi);
                     } else {
-                        id = it->second;
+                        id = slot_id;
+                        GhostInfo &gi = ghosts[id];  // union with what other groups read
+                        int b = gi.box;
+                        for (int d = 0; d < 3; d++) {
+                            const int l0 = (b >> (4 * d)) & 15, h0 = (b >> (12 + 4 * d)) & 15;
+                            const int l1 = lo[d] < l0 ? lo[d] : l0, h1 = hi[d] > h0 ? hi[d] : h0;
+                            b = (b & ~(15 << (4 * d)) & ~(15 << (12 + 4 * d))) | l1 << (4 * d) | h1 << (12 + 4 * d);
+                        }
+                        gi.box = b;
                     }
                     nbr[(size_t)g * 64 + pos] = -2 - id;
                 }

@@ -12,7 +12,6 @@
 #include <algorithm>
 #include <array>
 #include <cstring>
-#include <unordered_map>
 #include <vector>
 
 #include "amr_hydro.h"
@@ -35,9 +34,6 @@ static inline int face_sib(int f) {
     int d[3] = {0, 0, 0};
     d[f >> 1] = (f & 1) ? 1 : -1;
     return sib_k(d[0], d[1], d[2]);
-}
-static inline uint64_t key3(int x, int y, int z) {
-    return ((uint64_t)(uint32_t)x << 42) ^ ((uint64_t)(uint32_t)y << 21) ^ (uint64_t)(uint32_t)z;
 }
 
 template <typename T>
@@ -64,12 +60,13 @@ amr_status plan_level(amr_hydro_ctx *c, int level) {
     L.n_ghost = (int)ghosts.size();
     if (L.n_ghost) {
         if ((st = L.ghost.reserve((size_t)L.n_ghost * PSLOT_H))) return st;
-        std::vector<int32_t> gi((size_t)L.n_ghost * 4);
+        std::vector<int32_t> gi((size_t)L.n_ghost * GHOST_INFO, 0);
         for (int i = 0; i < L.n_ghost; i++) {
-            gi[4 * i] = ghosts[i].cparent;
-            gi[4 * i + 1] = ghosts[i].qx;
-            gi[4 * i + 2] = ghosts[i].qy;
-            gi[4 * i + 3] = ghosts[i].qz;
+            gi[GHOST_INFO * i] = ghosts[i].cparent;
+            gi[GHOST_INFO * i + 1] = ghosts[i].qx;
+            gi[GHOST_INFO * i + 2] = ghosts[i].qy;
+            gi[GHOST_INFO * i + 3] = ghosts[i].qz;
+            gi[GHOST_INFO * i + 4] = ghosts[i].box;
         }
         if ((st = upload(L.ghost_info, gi, c->stream))) return st;
     }
@@ -197,10 +194,11 @@ amr_status amr_hydro_regrid(amr_hydro_ctx *c, int l) {
         pc[d] = (c->prm.root_n[d] << l) / 8;
         fc[d] = 2 * pc[d];
     }
-    std::unordered_map<uint64_t, int> at_l;
-    at_l.reserve(2 * n);
-    for (int s = 0; s < n; s++)
-        at_l[key3(L.corner[3 * s] / 8, L.corner[3 * s + 1] / 8, L.corner[3 * s + 2] / 8)] = s;
+    // patch position -> slot, dense over each level's patch grid
+    std::vector<int32_t> at_l((size_t)pc[0] * pc[1] * pc[2], -1);
+    auto idx_l = [&](int x, int y, int z) { return ((size_t)z * pc[1] + y) * pc[0] + x; };
+    auto idx_f = [&](int x, int y, int z) { return ((size_t)z * fc[1] + y) * fc[0] + x; };
+    for (int s = 0; s < n; s++) at_l[idx_l(L.corner[3 * s] / 8, L.corner[3 * s + 1] / 8, L.corner[3 * s + 2] / 8)] = s;
 
     // keep-for-nesting: level-l parents of the 27-neighbourhoods of refined
     // level-(l+1) patches stay refined
@@ -214,9 +212,9 @@ amr_status amr_hydro_regrid(amr_hydro_ctx *c, int l) {
                     for (int dx = -1; dx <= 1; dx++) {
                         const int q[3] = {wrapi(X[0] + dx, fc[0]) / 2, wrapi(X[1] + dy, fc[1]) / 2,
                                           wrapi(X[2] + dz, fc[2]) / 2};
-                        auto it = at_l.find(key3(q[0], q[1], q[2]));
-                        if (it == at_l.end()) return AMR_E_NESTING;
-                        keep[it->second] = 1;
+                        const int32_t q_slot = at_l[idx_l(q[0], q[1], q[2])];
+                        if (q_slot < 0) return AMR_E_NESTING;
+                        keep[q_slot] = 1;
                     }
         }
     }
@@ -234,12 +232,18 @@ amr_status amr_hydro_regrid(amr_hydro_ctx *c, int l) {
         return a < b;
     });
     const int ng = (int)chosen.size(), nn = 8 * ng;
+    // nothing to do when the refined set is unchanged: the existing groups
+    // are already numbered in the canonical order of their parents
+    if (ng == F.n_groups) {
+        bool same = true;
+        for (int g = 0; g < ng && same; g++) same = L.child[chosen[g]] == g;
+        if (same) return AMR_OK;
+    }
     if (nn > c->prm.max_patches) return AMR_E_NOMEM;
 
     std::vector<int32_t> corner((size_t)nn * 3), sib((size_t)nn * 26), parent(nn), child(nn, -1);
     std::vector<int32_t> old_of(nn, -1), new_of((size_t)F.n_patches, -1), lchild(n, -1), jobs, job_slot;
-    std::unordered_map<uint64_t, int> at_f;
-    at_f.reserve(2 * nn);
+    std::vector<int32_t> at_f((size_t)fc[0] * fc[1] * fc[2], -1);
     for (int g = 0; g < ng; g++) {
         const int P = chosen[g];
         lchild[P] = g;
@@ -249,14 +253,14 @@ amr_status amr_hydro_regrid(amr_hydro_ctx *c, int l) {
             corner[3 * s + 1] = 2 * L.corner[3 * P + 1] + 8 * ly;
             corner[3 * s + 2] = 2 * L.corner[3 * P + 2] + 8 * lz;
             parent[s] = P;
-            at_f[key3(corner[3 * s] / 8, corner[3 * s + 1] / 8, corner[3 * s + 2] / 8)] = s;
+            at_f[idx_f(corner[3 * s] / 8, corner[3 * s + 1] / 8, corner[3 * s + 2] / 8)] = s;
             if (L.child[P] >= 0) {
                 const int o = 8 * L.child[P] + k;
                 old_of[s] = o;
                 new_of[o] = s;
                 child[s] = F.child[o];
             } else {
-                jobs.insert(jobs.end(), {P, lx, ly, lz});
+                jobs.insert(jobs.end(), {P, lx, ly, lz, 8 << 12 | 8 << 16 | 8 << 20, 0, 0, 0});  // whole patch
                 job_slot.push_back(s);
             }
         }
@@ -267,8 +271,8 @@ amr_status amr_hydro_regrid(amr_hydro_ctx *c, int l) {
             for (int dy = -1; dy <= 1; dy++)
                 for (int dx = -1; dx <= 1; dx++) {
                     if (!dx && !dy && !dz) continue;
-                    auto it = at_f.find(key3(wrapi(p[0] + dx, fc[0]), wrapi(p[1] + dy, fc[1]), wrapi(p[2] + dz, fc[2])));
-                    sib[(size_t)s * 26 + sib_k(dx, dy, dz)] = it == at_f.end() ? -1 : it->second;
+                    sib[(size_t)s * 26 + sib_k(dx, dy, dz)] =
+                        at_f[idx_f(wrapi(p[0] + dx, fc[0]), wrapi(p[1] + dy, fc[1]), wrapi(p[2] + dz, fc[2]))];
                 }
     }
     // grandchildren keep their data; their parent slots are renumbered
@@ -299,7 +303,7 @@ amr_status amr_hydro_regrid(amr_hydro_ctx *c, int l) {
         return st;
     if (F.n_patches && (st = copy_slots(c, Ud, F.U[F.cur], c->regrid_tmp.p, nn))) return st;
     if ((st = interp_new_patches(c, l, Ud, c->regrid_tmp.p + nn + jobs.size(), c->regrid_tmp.p + nn,
-                                 (int)job_slot.size())))
+                                 (int)job_slot.size())))  // jobs: GHOST_INFO ints each
         return st;
 
     // tables: host mirrors and the caller's arrays

@@ -68,6 +68,8 @@ struct StepSmem {
     real YS[2][NV][GE + 2][GE];  // y-/y+ face states, cells y=-1..16, columns x=0..15
     real FX[NV][GE][GE + 1];     // x flux at face x-1/2, x=0..16
     real FY[NV][GE + 1][GE];     // y flux at face y-1/2, y=0..16
+    double raw[NV][TW * TW];  // next tile plane in flight (cp.async), cells owned per thread
+    double uo[2][NV][STEP_THREADS];  // each column's U^n one plane ahead of its update (cp.async)
     int nbr[64];
     long long cfo[6];   // fine register blocks of the group's faces (-1: none)
     long long cco[48];  // coarse register blocks of its 8 patches' faces (-1: none)
@@ -148,6 +150,56 @@ __device__ __forceinline__ void load_plane(StepSmem<real> &S, const StepParams &
     }
 }
 
+// Asynchronous copy of tile plane tz into S.raw: each thread copies the
+// cells i = tid, tid + 256 (< 400) that it will also convert, so the copy
+// needs no CTA barrier, only the thread's own cp.async wait.
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename real>
+__device__ __forceinline__ void issue_plane(StepSmem<real> &S, const StepParams &P, int tz) {
+    const int qz = (tz + PS) >> 3, lz = (tz + PS) & 7;
+    for (int i = threadIdx.x; i < TW * TW; i += STEP_THREADS) {
+        const int ty = i / TW - 2, tx = i % TW - 2;
+        const int qy = (ty + PS) >> 3, ly = (ty + PS) & 7;
+        const int qx = (tx + PS) >> 3, lx = (tx + PS) & 7;
+        const double *src = patch_src(P, S.nbr[qx + 4 * qy + 16 * qz]);
+        if (src) {
+            const int off = lz * 64 + ly * 8 + lx;
+#pragma unroll
+            for (int v = 0; v < NV; v++) cp_async8(&S.raw[v][i], src + v * PV + off);
+        }
+    }
+    cp_async_commit();
+}
+
+// Wait for this thread's copies of plane tz and convert them to primitives
+// into the ring (the CTA barrier before stage B publishes them).
+template <typename real>
+__device__ __forceinline__ void finish_plane(StepSmem<real> &S, int tz, const Gas<real> &g) {
+    cp_async_wait_all();
+    const int slot = (tz + 3) % 3;
+    const int qz = (tz + PS) >> 3;
+    for (int i = threadIdx.x; i < TW * TW; i += STEP_THREADS) {
+        const int ty = i / TW - 2, tx = i % TW - 2;
+        const int qy = (ty + PS) >> 3, qx = (tx + PS) >> 3;
+        real u[NV], w[NV];
+        if (S.nbr[qx + 4 * qy + 16 * qz] != -1) {
+#pragma unroll
+            for (int v = 0; v < NV; v++) u[v] = to_real<real>(S.raw[v][i]);
+            u2w(u, w, g);
+        } else {
+            w[0] = real(1); w[1] = w[2] = w[3] = real(0); w[4] = real(1);
+        }
+#pragma unroll
+        for (int v = 0; v < NV; v++) S.W[slot][v][ty + 2][tx + 2] = w[v];
+    }
+}
+
 // Limited slopes and Hancock half step of tile cell (x,y) on plane z.
 // uf[2d] / uf[2d+1]: conserved state on the low / high face along d.
 template <typename real>
@@ -215,14 +267,24 @@ __device__ __forceinline__ void step_group(StepSmem<real> &S, const StepParams &
     __syncthreads();
     load_plane(S, P, -2, g);
     load_plane(S, P, -1, g);
+    issue_plane(S, P, 0);
 
     real zp_prev[NV];   // high z face state of this column's cell at z-1
     real acc[NV];       // flux divergence of this column's cell at z-1 (minus its top z flux)
 #pragma unroll
     for (int v = 0; v < NV; v++) { zp_prev[v] = real(0); acc[v] = real(0); }
 
+    const int64_t own = (int64_t)grp * 8;
     for (int z = -1; z <= GE; z++) {
-        load_plane(S, P, z + 1, g);
+        finish_plane(S, z + 1, g);
+        if (z + 2 <= GE + 1) issue_plane(S, P, z + 2);
+        if (z >= 0 && z < GE) {  // this column's U^n at plane z, for its update next iteration
+            const double *src = P.U_old + (own + (cx >> 3) + 2 * (cy >> 3) + 4 * (z >> 3)) * PSLOT +
+                                (z & 7) * 64 + (cy & 7) * 8 + (cx & 7);
+#pragma unroll
+            for (int v = 0; v < NV; v++) cp_async8(&S.uo[z & 1][v][tid], src + v * PV);
+            cp_async_commit();
+        }
         __syncthreads();
 
         // ---- B: Hancock states of plane z
@@ -321,7 +383,6 @@ __device__ __forceinline__ void step_group(StepSmem<real> &S, const StepParams &
         __syncthreads();
 
         // ---- D: finish cell (cx,cy,z-1), start cell (cx,cy,z)
-        const int64_t own = (int64_t)grp * 8;
         if (z >= 1) {
             const int zc = z - 1;
             const int64_t base = (own + (cx >> 3) + 2 * (cy >> 3) + 4 * (zc >> 3)) * PSLOT +
@@ -330,7 +391,7 @@ __device__ __forceinline__ void step_group(StepSmem<real> &S, const StepParams &
 #pragma unroll
             for (int v = 0; v < NV; v++) {
                 const real tot = acc[v] + fz[v];
-                const double uo = P.U_old[base + v * PV];
+                const double uo = S.uo[zc & 1][v][tid];
                 double un;
                 if constexpr (sizeof(real) == sizeof(double)) {
                     un = uo - dtdh * tot;
