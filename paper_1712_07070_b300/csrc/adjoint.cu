@@ -23,10 +23,12 @@
 
 #include "amr_hydro.h"
 #include "ctx.h"
+#include "hydro_math.cuh"
 
 namespace {
 
 constexpr int NV = 5;
+using amrh::rcp_;  // FP64 reciprocal: special-function seed + two Newton steps
 
 struct Dims {
     int nx, ny, nz;
@@ -40,8 +42,8 @@ struct Dims {
 };
 
 __device__ __forceinline__ void prim(const double U[NV], double W[NV], double gm1) {
-    const double r = U[0];
-    const double vx = U[1] / r, vy = U[2] / r, vz = U[3] / r;
+    const double r = U[0], ri = rcp_(r);
+    const double vx = U[1] * ri, vy = U[2] * ri, vz = U[3] * ri;
     const double ek = 0.5 * r * (vx * vx + vy * vy + vz * vz);
     W[0] = r;
     W[1] = vx;
@@ -52,37 +54,37 @@ __device__ __forceinline__ void prim(const double U[NV], double W[NV], double gm
 
 // lU += (dW/dU)^T lW
 __device__ __forceinline__ void prim_adj(const double U[NV], const double lW[NV], double lU[NV], double gm1) {
-    const double r = U[0];
-    const double v[3] = {U[1] / r, U[2] / r, U[3] / r};
+    const double r = U[0], ri = rcp_(r);
+    const double v[3] = {U[1] * ri, U[2] * ri, U[3] * ri};
     const double lek = -gm1 * lW[4];
     lU[4] += gm1 * lW[4];
     double lr = lW[0] + lek * 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         const double lv = lW[1 + k] + lek * r * v[k];
-        lU[1 + k] += lv / r;
-        lr -= lv * v[k] / r;
+        lU[1 + k] += lv * ri;
+        lr -= lv * v[k] * ri;
     }
     lU[0] += lr;
 }
 
-__device__ __forceinline__ void cons(const double W[NV], double U[NV], double gamma) {
+__device__ __forceinline__ void cons(const double W[NV], double U[NV], double inv_gm1) {
     const double r = W[0];
     U[0] = r;
     U[1] = r * W[1];
     U[2] = r * W[2];
     U[3] = r * W[3];
-    U[4] = W[4] / (gamma - 1.0) + 0.5 * r * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+    U[4] = W[4] * inv_gm1 + 0.5 * r * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
 }
 
 // lW += (dU/dW)^T lU
-__device__ __forceinline__ void cons_adj(const double W[NV], const double lU[NV], double lW[NV], double gamma) {
+__device__ __forceinline__ void cons_adj(const double W[NV], const double lU[NV], double lW[NV], double inv_gm1) {
     const double r = W[0];
     const double k2 = W[1] * W[1] + W[2] * W[2] + W[3] * W[3];
     lW[0] += lU[0] + lU[1] * W[1] + lU[2] * W[2] + lU[3] * W[3] + lU[4] * 0.5 * k2;
 #pragma unroll
     for (int k = 0; k < 3; k++) lW[1 + k] += lU[1 + k] * r + lU[4] * r * W[1 + k];
-    lW[4] += lU[4] / (gamma - 1.0);
+    lW[4] += lU[4] * inv_gm1;
 }
 
 // physical flux along d of conserved U (through its primitives)
@@ -124,16 +126,17 @@ __device__ void hllc_vjp(const double UL[NV], const double UR[NV], int d, double
     prim(UR, WR, gm1);
     const double rl = WL[0], pl = WL[4], ul = WL[1 + d];
     const double rr = WR[0], pr = WR[4], ur = WR[1 + d];
-    const double cl = sqrt(g * pl / rl), cr = sqrt(g * pr / rr);
-    const double sl = sqrt(rl), sr = sqrt(rr), S = sl + sr;
+    const double ril = rcp_(rl), rir = rcp_(rr);
+    const double cl = sqrt(g * pl * ril), cr = sqrt(g * pr * rir);
+    const double sl = sqrt(rl), sr = sqrt(rr), S = sl + sr, iS = rcp_(S);
     double vt[3], Tk[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         Tk[k] = sl * WL[1 + k] + sr * WR[1 + k];
-        vt[k] = Tk[k] / S;
+        vt[k] = Tk[k] * iS;
     }
-    const double hl = (UL[4] + pl) / rl, hr = (UR[4] + pr) / rr;
-    const double T = sl * hl + sr * hr, ht = T / S;
+    const double hl = (UL[4] + pl) * ril, hr = (UR[4] + pr) * rir;
+    const double T = sl * hl + sr * hr, ht = T * iS;
     const double X = gm1 * (ht - 0.5 * (vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]));
     const double ct = sqrt(X);
     const double a = ul - cl, b = vt[d] - ct;
@@ -152,16 +155,18 @@ __device__ void hllc_vjp(const double UL[NV], const double UR[NV], int d, double
     }
     const double num = pr - pl + rl * ul * (SL - ul) - rr * ur * (SR - ur);
     const double den = rl * (SL - ul) - rr * (SR - ur);
-    const double Ss = num / den;
+    const double iden = rcp_(den);
+    const double Ss = num * iden;
     const bool left = Ss >= 0.0;
     const double *UK = left ? UL : UR;
     const double *WK = left ? WL : WR;
     double *lUK = left ? lUL : lUR;
     const double SK = left ? SL : SR;
     const double rK = WK[0], uK = WK[1 + d], pK = WK[4], EK = UK[4];
-    const double D = rK * (SK - uK), M = SK - Ss, fac = D / M;
-    const double R = pK / D;
-    const double Q = EK / rK + (Ss - uK) * (Ss + R);
+    const double riK = left ? ril : rir;
+    const double D = rK * (SK - uK), M = SK - Ss, iM = rcp_(M), fac = D * iM;
+    const double iD = rcp_(D), R = pK * iD;
+    const double Q = EK * riK + (Ss - uK) * (Ss + R);
     double Us[NV];
     Us[0] = fac;
     Us[1] = fac * WK[1];
@@ -190,16 +195,16 @@ __device__ void hllc_vjp(const double UL[NV], const double UR[NV], int d, double
     double lSs = lUs[1 + d] * fac;
     const double lQ = lUs[4] * fac;
     // Q = EK/rK + (Ss - uK)(Ss + R)
-    lUK[4] += lQ / rK;
-    double lrK = -lQ * EK / (rK * rK);
+    lUK[4] += lQ * riK;
+    double lrK = -lQ * EK * riK * riK;
     lSs += lQ * ((Ss + R) + (Ss - uK));
     double luK = -lQ * (Ss + R);
     const double lR = lQ * (Ss - uK);
-    const double lpK = lR / D;
-    double lD = -lR * pK / (D * D);
+    const double lpK = lR * iD;
+    double lD = -lR * R * iD;
     // fac = D / M
-    lD += lfac / M;
-    const double lM = -lfac * D / (M * M);
+    lD += lfac * iM;
+    const double lM = -lfac * fac * iM;
     lSK += lM;
     lSs -= lM;
     // D = rK (SK - uK)
@@ -207,7 +212,7 @@ __device__ void hllc_vjp(const double UL[NV], const double UR[NV], int d, double
     lSK += lD * rK;
     luK -= lD * rK;
     // Ss = num / den
-    const double lnum = lSs / den, lden = -lSs * num / (den * den);
+    const double lnum = lSs * iden, lden = -lSs * Ss * iden;
     double lWL[NV] = {0, 0, 0, 0, 0}, lWR[NV] = {0, 0, 0, 0, 0};
     double lSL = 0.0, lSR = 0.0;
     lWR[4] += lnum;
@@ -250,19 +255,19 @@ __device__ void hllc_vjp(const double UL[NV], const double UR[NV], int d, double
         lct += lSR;
     }
     // ct = sqrt(X), X = gm1 (ht - |vt|^2 / 2)
-    const double lX = lct * 0.5 / ct;
+    const double lX = lct * 0.5 * rcp_(ct);
     const double lht = lX * gm1;
 #pragma unroll
     for (int k = 0; k < 3; k++) lvt[k] -= lX * gm1 * vt[k];
     // ht = T / S, vt_k = Tk / S
-    const double lT = lht / S;
-    double lS = -lht * ht / S;
+    const double lT = lht * iS;
+    double lS = -lht * ht * iS;
     double lsl = lT * hl, lsr = lT * hr;
     const double lhl = lT * sl, lhr = lT * sr;
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        const double lTk = lvt[k] / S;
-        lS -= lvt[k] * vt[k] / S;
+        const double lTk = lvt[k] * iS;
+        lS -= lvt[k] * vt[k] * iS;
         lsl += lTk * WL[1 + k];
         lWL[1 + k] += lTk * sl;
         lsr += lTk * WR[1 + k];
@@ -271,25 +276,25 @@ __device__ void hllc_vjp(const double UL[NV], const double UR[NV], int d, double
     lsl += lS;
     lsr += lS;
     // hl = (E + p)/rho
-    lUL[4] += lhl / rl;
-    lWL[4] += lhl / rl;
-    lWL[0] -= lhl * hl / rl;
-    lUR[4] += lhr / rr;
-    lWR[4] += lhr / rr;
-    lWR[0] -= lhr * hr / rr;
+    lUL[4] += lhl * ril;
+    lWL[4] += lhl * ril;
+    lWL[0] -= lhl * hl * ril;
+    lUR[4] += lhr * rir;
+    lWR[4] += lhr * rir;
+    lWR[0] -= lhr * hr * rir;
     // sqrt(rho)
-    lWL[0] += lsl * 0.5 / sl;
-    lWR[0] += lsr * 0.5 / sr;
+    lWL[0] += lsl * 0.5 * rcp_(sl);
+    lWR[0] += lsr * 0.5 * rcp_(sr);
     // c = sqrt(g p / rho)
     {
-        const double lY = lcl * 0.5 / cl;
-        lWL[4] += lY * g / rl;
-        lWL[0] -= lY * g * pl / (rl * rl);
+        const double lY = lcl * 0.5 * rcp_(cl);
+        lWL[4] += lY * g * ril;
+        lWL[0] -= lY * g * pl * ril * ril;
     }
     {
-        const double lY = lcr * 0.5 / cr;
-        lWR[4] += lY * g / rr;
-        lWR[0] -= lY * g * pr / (rr * rr);
+        const double lY = lcr * 0.5 * rcp_(cr);
+        lWR[4] += lY * g * rir;
+        lWR[0] -= lY * g * pr * rir * rir;
     }
     prim_adj(UL, lWL, lUL, gm1);
     prim_adj(UR, lWR, lUR, gm1);
@@ -330,15 +335,16 @@ __device__ void hancock_fwd(const double *__restrict__ W, const Dims &D, int x, 
             H.a[d][v] = a;
             H.b[d][v] = b;
             const double ab = a * b;
-            const double s = ab > 0.0 ? 2.0 * ab / (a + b) : 0.0;
+            const double s = ab > 0.0 ? 2.0 * ab * rcp_(a + b) : 0.0;
             H.slope[d][v] = s;
             H.Wf[2 * d][v] = H.w[v] - 0.5 * s;
             H.Wf[2 * d + 1][v] = H.w[v] + 0.5 * s;
         }
     double inc[NV] = {0, 0, 0, 0, 0};
     const double gm1 = gamma - 1.0;
+    const double inv_gm1 = rcp_(gm1);
 #pragma unroll
-    for (int f = 0; f < 6; f++) cons(H.Wf[f], H.Uf[f], gamma);
+    for (int f = 0; f < 6; f++) cons(H.Wf[f], H.Uf[f], inv_gm1);
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         double Fm[NV], Fp[NV];
@@ -397,7 +403,7 @@ __global__ void k_adj_hllc(const double *__restrict__ FS, const double *__restri
 __global__ void k_adj_hancock_rev(const double *__restrict__ W, const double *__restrict__ LFS,
                                   double *__restrict__ Lself, double *__restrict__ Lab, Dims D, double gamma,
                                   double c) {
-    const double gm1 = gamma - 1.0;
+    const double gm1 = gamma - 1.0, inv_gm1 = rcp_(gm1);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < D.n; i += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(i % D.nx), y = (int)((i / D.nx) % D.ny), z = (int)(i / ((int64_t)D.nx * D.ny));
         HancockCell H;
@@ -426,8 +432,8 @@ __global__ void k_adj_hancock_rev(const double *__restrict__ W, const double *__
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             double lm[NV] = {0, 0, 0, 0, 0}, lp[NV] = {0, 0, 0, 0, 0};
-            cons_adj(H.Wf[2 * d], lUf[2 * d], lm, gamma);
-            cons_adj(H.Wf[2 * d + 1], lUf[2 * d + 1], lp, gamma);
+            cons_adj(H.Wf[2 * d], lUf[2 * d], lm, inv_gm1);
+            cons_adj(H.Wf[2 * d + 1], lUf[2 * d + 1], lp, inv_gm1);
 #pragma unroll
             for (int v = 0; v < NV; v++) {
                 lw[v] += lm[v] + lp[v];
@@ -435,9 +441,9 @@ __global__ void k_adj_hancock_rev(const double *__restrict__ W, const double *__
                 const double a = H.a[d][v], b = H.b[d][v];
                 double la = 0.0, lb = 0.0;
                 if (a * b > 0.0) {
-                    const double s2 = (a + b) * (a + b);
-                    la = ls * 2.0 * b * b / s2;
-                    lb = ls * 2.0 * a * a / s2;
+                    const double r = rcp_(a + b), r2 = 2.0 * ls * r * r;
+                    la = r2 * b * b;
+                    lb = r2 * a * a;
                 }
                 Lab[((d * NV + v) * 2 + 0) * D.n + i] = la;
                 Lab[((d * NV + v) * 2 + 1) * D.n + i] = lb;
