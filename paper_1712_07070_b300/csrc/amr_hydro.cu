@@ -87,10 +87,10 @@ amr_status configure_kernels() {
 int step_blocks_per_sm(int prec) {
     int n = 0;
     if (prec == AMR_FP64)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hydro_step<double>, STEP_THREADS,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hydro_step<double>, StepCfg<double>::NT,
                                                       sizeof(StepSmem<double>));
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hydro_step<float>, STEP_THREADS,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hydro_step<float>, StepCfg<float>::NT,
                                                       sizeof(StepSmem<float>));
     return n > 0 ? n : 1;
 }
@@ -98,9 +98,9 @@ int step_blocks_per_sm(int prec) {
 amr_status launch_step(amr_hydro_ctx *c, const StepParams &P, int grid) {
     if (P.n_work == 0) return AMR_OK;
     if (c->prm.prec == AMR_FP64)
-        k_hydro_step<double><<<grid, STEP_THREADS, sizeof(StepSmem<double>), c->stream>>>(P);
+        k_hydro_step<double><<<grid, StepCfg<double>::NT, sizeof(StepSmem<double>), c->stream>>>(P);
     else
-        k_hydro_step<float><<<grid, STEP_THREADS, sizeof(StepSmem<float>), c->stream>>>(P);
+        k_hydro_step<float><<<grid, StepCfg<float>::NT, sizeof(StepSmem<float>), c->stream>>>(P);
     return cuda_fail(cudaGetLastError(), "k_hydro_step launch");
 }
 
@@ -117,9 +117,9 @@ amr_status launch_step_raw(int prec, const StepParams &P, cudaStream_t stream) {
     const int cap = n_sm * step_blocks_per_sm(prec);
     const int grid = P.n_work < cap ? P.n_work : cap;
     if (prec == AMR_FP64)
-        k_hydro_step<double><<<grid, STEP_THREADS, sizeof(StepSmem<double>), stream>>>(P);
+        k_hydro_step<double><<<grid, StepCfg<double>::NT, sizeof(StepSmem<double>), stream>>>(P);
     else
-        k_hydro_step<float><<<grid, STEP_THREADS, sizeof(StepSmem<float>), stream>>>(P);
+        k_hydro_step<float><<<grid, StepCfg<float>::NT, sizeof(StepSmem<float>), stream>>>(P);
     return cuda_fail(cudaGetLastError(), "k_hydro_step launch");
 }
 

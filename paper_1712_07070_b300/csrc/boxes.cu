@@ -40,19 +40,19 @@ amr_status configure_box_kernels() {
 int resident_per_sm(int prec) {
     int n = 0;
     if (prec == AMR_FP64)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hydro_step_boxes<double>, STEP_THREADS,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hydro_step_boxes<double>, StepCfg<double>::NT,
                                                       sizeof(StepSmem<double>));
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hydro_step_boxes<float>, STEP_THREADS,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hydro_step_boxes<float>, StepCfg<float>::NT,
                                                       sizeof(StepSmem<float>));
     return n > 0 ? n : 1;
 }
 
 amr_status launch_boxes(amr_hydro_ctx *c, const BoxLaunch &B, int grid, cudaStream_t s) {
     if (c->prm.prec == AMR_FP64)
-        k_hydro_step_boxes<double><<<grid, STEP_THREADS, sizeof(StepSmem<double>), s>>>(B);
+        k_hydro_step_boxes<double><<<grid, StepCfg<double>::NT, sizeof(StepSmem<double>), s>>>(B);
     else
-        k_hydro_step_boxes<float><<<grid, STEP_THREADS, sizeof(StepSmem<float>), s>>>(B);
+        k_hydro_step_boxes<float><<<grid, StepCfg<float>::NT, sizeof(StepSmem<float>), s>>>(B);
     return cuda_fail(cudaGetLastError(), "k_hydro_step_boxes");
 }
 

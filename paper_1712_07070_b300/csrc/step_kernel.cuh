@@ -27,7 +27,17 @@ constexpr int PV = PS * PS * PS;      // cells per patch
 constexpr int PSLOT = NV * PV;        // doubles per patch slot
 constexpr int GE = 16;                // group edge
 constexpr int TW = GE + 4;            // tile edge with 2 ghost cells per side
-constexpr int STEP_THREADS = 256;     // one thread per (x,y) column of the group
+constexpr int COLS = GE * GE;         // (x,y) columns of a group: one owner thread each
+constexpr int MAX_WARPS = 8;
+
+// Threads per CTA: one per (x,y) column of the group.  The FP32 kernel is
+// register-bounded for two resident CTAs per SM, the FP64 kernel for one (its
+// FP64 pipe is the bound, not latency).
+template <typename real>
+struct StepCfg {
+    static constexpr int NT = 256;
+    static constexpr int MINB = sizeof(real) == sizeof(double) ? 1 : 2;  // resident CTAs/SM targeted
+};
 
 // Coarse-fine flux registers (section 2.2 fix-up).  Faces f = 0..5 are
 // -x, +x, -y, +y, -z, +z.  Fine side: fine_off[g*6+f] >= 0 is the offset (in
@@ -69,12 +79,12 @@ struct StepSmem {
     real FX[NV][GE][GE + 1];     // x flux at face x-1/2, x=0..16
     real FY[NV][GE + 1][GE];     // y flux at face y-1/2, y=0..16
     double raw[NV][TW * TW];  // next tile plane in flight (cp.async), cells owned per thread
-    double uo[2][NV][STEP_THREADS];  // each column's U^n one plane ahead of its update (cp.async)
+    double uo[2][NV][COLS];  // each column's U^n one plane ahead of its update (cp.async)
     int nbr[64];
     long long cfo[6];   // fine register blocks of the group's faces (-1: none)
     long long cco[48];  // coarse register blocks of its 8 patches' faces (-1: none)
     int any_cf;         // whether the group touches any register
-    double red[STEP_THREADS / 32];
+    double red[MAX_WARPS];
     double dt;
 };
 
@@ -83,18 +93,16 @@ struct StepSmem {
 // (t1, t2) in 0..15 within the group; pa/pb: local patch indices (0..7) of the
 // two cells when they belong to this group (-1 otherwise); face_lo/face_hi:
 // whether the face is the group's low / high boundary along D.
-template <int D, typename real>
+template <typename real>
 __device__ __forceinline__ void cf_register(const StepSmem<real> &S, const StepParams &P, double dt,
-                                            const real F[NV], int t1, int t2, int pa, int pb,
+                                            const real F[NV], int D, int t1, int t2, int pa, int pb,
                                             bool face_lo, bool face_hi) {
     if (!S.any_cf) return;
     double Fd[NV];
-    bool need = false;
     const long long fo = face_lo ? S.cfo[2 * D] : (face_hi ? S.cfo[2 * D + 1] : -1);
     const long long ca = pa >= 0 ? S.cco[pa * 6 + 2 * D + 1] : -1;  // high face of the low cell's patch
     const long long cb = pb >= 0 ? S.cco[pb * 6 + 2 * D] : -1;      // low face of the high cell's patch
-    need = fo >= 0 || ca >= 0 || cb >= 0;
-    if (!need) return;
+    if (fo < 0 && ca < 0 && cb < 0) return;
 #pragma unroll
     for (int v = 0; v < NV; v++) {
         if constexpr (sizeof(real) == sizeof(double)) Fd[v] = F[v];
@@ -118,6 +126,32 @@ __device__ __forceinline__ void cf_register(const StepSmem<real> &S, const StepP
     }
 }
 
+// HLLC through a face normal to a runtime direction D: the normal momentum is
+// swapped into the x slot, the x-normal solver runs, and the flux is swapped
+// back (register selects only), so lanes of one warp can serve different
+// directions without diverging.
+template <typename real>
+__device__ __forceinline__ void hllc_dir(const real uL[NV], const real uR[NV], int D, real F[NV],
+                                         const Gas<real> &g) {
+    real a[NV], b[NV], f[NV];
+    a[0] = uL[0];
+    a[4] = uL[4];
+    a[1] = D == 1 ? uL[2] : (D == 2 ? uL[3] : uL[1]);
+    a[2] = D == 1 ? uL[1] : uL[2];
+    a[3] = D == 2 ? uL[1] : uL[3];
+    b[0] = uR[0];
+    b[4] = uR[4];
+    b[1] = D == 1 ? uR[2] : (D == 2 ? uR[3] : uR[1]);
+    b[2] = D == 1 ? uR[1] : uR[2];
+    b[3] = D == 2 ? uR[1] : uR[3];
+    hllc<0>(a, b, f, g);
+    F[0] = f[0];
+    F[4] = f[4];
+    F[1] = D == 1 ? f[2] : (D == 2 ? f[3] : f[1]);
+    F[2] = D == 1 ? f[1] : f[2];
+    F[3] = D == 2 ? f[1] : f[3];
+}
+
 // Source pointer for patch position q (0..63) of the current group.
 __device__ __forceinline__ const double *patch_src(const StepParams &P, int s) {
     if (s >= 0) return P.U_old + (int64_t)s * PSLOT;
@@ -131,7 +165,7 @@ __device__ __forceinline__ void load_plane(StepSmem<real> &S, const StepParams &
                                            const Gas<real> &g) {
     const int slot = (tz + 3) % 3;
     const int qz = (tz + PS) >> 3, lz = (tz + PS) & 7;
-    for (int i = threadIdx.x; i < TW * TW; i += STEP_THREADS) {
+    for (int i = threadIdx.x; i < TW * TW; i += StepCfg<real>::NT) {
         const int ty = i / TW - 2, tx = i % TW - 2;
         const int qy = (ty + PS) >> 3, ly = (ty + PS) & 7;
         const int qx = (tx + PS) >> 3, lx = (tx + PS) & 7;
@@ -163,7 +197,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <typename real>
 __device__ __forceinline__ void issue_plane(StepSmem<real> &S, const StepParams &P, int tz) {
     const int qz = (tz + PS) >> 3, lz = (tz + PS) & 7;
-    for (int i = threadIdx.x; i < TW * TW; i += STEP_THREADS) {
+    for (int i = threadIdx.x; i < TW * TW; i += StepCfg<real>::NT) {
         const int ty = i / TW - 2, tx = i % TW - 2;
         const int qy = (ty + PS) >> 3, ly = (ty + PS) & 7;
         const int qx = (tx + PS) >> 3, lx = (tx + PS) & 7;
@@ -184,7 +218,7 @@ __device__ __forceinline__ void finish_plane(StepSmem<real> &S, int tz, const Ga
     cp_async_wait_all();
     const int slot = (tz + 3) % 3;
     const int qz = (tz + PS) >> 3;
-    for (int i = threadIdx.x; i < TW * TW; i += STEP_THREADS) {
+    for (int i = threadIdx.x; i < TW * TW; i += StepCfg<real>::NT) {
         const int ty = i / TW - 2, tx = i % TW - 2;
         const int qy = (ty + PS) >> 3, qx = (tx + PS) >> 3;
         real u[NV], w[NV];
@@ -239,13 +273,71 @@ __device__ __forceinline__ void hancock_cell(const StepSmem<real> &S, int x, int
         for (int v = 0; v < NV; v++) uf[f][v] += dtdh_half * inc[v];
 }
 
+// Stage C face evaluations of plane z.  Thread (cx, cy) takes the x face
+// x = cx - 1/2 of row cy and the y face y = cy - 1/2 of column cx; warp 0
+// also takes the group's high faces, x = 16 - 1/2 of the 16 rows (lanes
+// 0..15) and y = 16 - 1/2 of the 16 columns (lanes 16..31), in one
+// divergence-free pass through hllc_dir.  The FP64 pipe charges a whole warp
+// instruction however few lanes are active, so that pass costs warp 0 one
+// solver evaluation instead of two.
+template <typename real>
+__device__ __forceinline__ void x_face(StepSmem<real> &S, const StepParams &P, double dt, int row, int col, int z,
+                                       const Gas<real> &g) {
+    real uL[NV], uR[NV], F[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) { uL[v] = S.XS[1][v][row][col]; uR[v] = S.XS[0][v][row][col + 1]; }
+    hllc<0>(uL, uR, F, g);
+#pragma unroll
+    for (int v = 0; v < NV; v++) S.FX[v][row][col] = F[v];
+    if ((col & 7) == 0) {  // a patch face: x = 0 (group boundary) or x = 8
+        const int pr = (row >> 3) * 2 + (z >> 3) * 4;
+        cf_register(S, P, dt, F, 0, row, z, col == 0 ? -1 : pr, pr + (col >> 3), col == 0, false);
+    }
+}
+
+template <typename real>
+__device__ __forceinline__ void y_face(StepSmem<real> &S, const StepParams &P, double dt, int r, int col, int z,
+                                       const Gas<real> &g) {
+    real uL[NV], uR[NV], F[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) { uL[v] = S.YS[1][v][r][col]; uR[v] = S.YS[0][v][r + 1][col]; }
+    hllc<1>(uL, uR, F, g);
+#pragma unroll
+    for (int v = 0; v < NV; v++) S.FY[v][r][col] = F[v];
+    if ((r & 7) == 0) {  // a patch face: y = 0 (group boundary) or y = 8
+        const int pr = (col >> 3) + (z >> 3) * 4;
+        cf_register(S, P, dt, F, 1, col, z, r == 0 ? -1 : pr, pr + 2 * (r >> 3), r == 0, false);
+    }
+}
+
+template <typename real>
+__device__ __forceinline__ void high_faces(StepSmem<real> &S, const StepParams &P, double dt, int lane, int z,
+                                           const Gas<real> &g) {
+    const int k = lane & 15, D = lane >> 4;
+    real uL[NV], uR[NV], F[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        uL[v] = D == 0 ? S.XS[1][v][k][GE] : S.YS[1][v][GE][k];
+        uR[v] = D == 0 ? S.XS[0][v][k][GE + 1] : S.YS[0][v][GE + 1][k];
+    }
+    hllc_dir(uL, uR, D, F, g);
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        if (D == 0) S.FX[v][k][GE] = F[v];
+        else S.FY[v][GE][k] = F[v];
+    }
+    const int pa = D == 0 ? 1 + (k >> 3) * 2 + (z >> 3) * 4 : (k >> 3) + 2 + (z >> 3) * 4;
+    cf_register(S, P, dt, F, D, k, z, pa, -1, false, true);
+}
+
 // One patch group: the whole fused step for group `grp` of P's level.  The
 // caller has set S.dt; smax_r / nbad accumulate the new state's largest
 // signal speed and its unphysical cells.
 template <typename real>
 __device__ __forceinline__ void step_group(StepSmem<real> &S, const StepParams &P, int grp, double dt,
                                            const Gas<real> &g, real &smax_r, unsigned &nbad) {
-    const int tid = threadIdx.x;
+    static_assert(StepCfg<real>::NT == COLS, "one thread per (x,y) column");
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cx = tid & 15, cy = tid >> 4;  // this thread's (x,y) column
     const double dtdh = dt / P.dh;
     const real dtdh_r = (real)dtdh;
@@ -329,56 +421,20 @@ __device__ __forceinline__ void step_group(StepSmem<real> &S, const StepParams &
         }
         __syncthreads();
 
-        // ---- C: fluxes
+        // ---- C: the z face below each owned column, then its x and y faces
         real fz[NV];
         if (z >= 0) {
             hllc<2>(zp_prev, zm, fz, g);
-            if (z == 0 || z == GE || (z == 8)) {
+            if (z == 0 || z == GE || z == 8) {
                 const int pl = (cx >> 3) + 2 * (cy >> 3);
-                cf_register<2>(S, P, dt, fz, cx, cy, z == 0 ? -1 : pl + 4 * ((z - 1) >> 3),
-                               z == GE ? -1 : pl + 4 * (z >> 3), z == 0, z == GE);
+                cf_register(S, P, dt, fz, 2, cx, cy, z == 0 ? -1 : pl + 4 * ((z - 1) >> 3),
+                            z == GE ? -1 : pl + 4 * (z >> 3), z == 0, z == GE);
             }
         }
         if (z >= 0 && z < GE) {
-            real uL[NV], uR[NV], F[NV];
-            // x face at cx-1/2 of row cy
-#pragma unroll
-            for (int v = 0; v < NV; v++) { uL[v] = S.XS[1][v][cy][cx]; uR[v] = S.XS[0][v][cy][cx + 1]; }
-            hllc<0>(uL, uR, F, g);
-#pragma unroll
-            for (int v = 0; v < NV; v++) S.FX[v][cy][cx] = F[v];
-            if ((cx & 7) == 0) {
-                const int pr = (cy >> 3) * 2 + (z >> 3) * 4;
-                cf_register<0>(S, P, dt, F, cy, z, cx == 0 ? -1 : pr, pr + (cx >> 3), cx == 0, false);
-            }
-            // y face at cy-1/2 of column cx
-#pragma unroll
-            for (int v = 0; v < NV; v++) { uL[v] = S.YS[1][v][cy][cx]; uR[v] = S.YS[0][v][cy + 1][cx]; }
-            hllc<1>(uL, uR, F, g);
-#pragma unroll
-            for (int v = 0; v < NV; v++) S.FY[v][cy][cx] = F[v];
-            if ((cy & 7) == 0) {
-                const int pr = (cx >> 3) + (z >> 3) * 4;
-                cf_register<1>(S, P, dt, F, cx, z, cy == 0 ? -1 : pr, pr + 2 * (cy >> 3), cy == 0, false);
-            }
-            if (tid < 32) {  // the high boundary faces x = 16-1/2 and y = 16-1/2
-                const int r = tid & 15;
-                if (tid < 16) {
-#pragma unroll
-                    for (int v = 0; v < NV; v++) { uL[v] = S.XS[1][v][r][GE]; uR[v] = S.XS[0][v][r][GE + 1]; }
-                    hllc<0>(uL, uR, F, g);
-#pragma unroll
-                    for (int v = 0; v < NV; v++) S.FX[v][r][GE] = F[v];
-                    cf_register<0>(S, P, dt, F, r, z, 1 + (r >> 3) * 2 + (z >> 3) * 4, -1, false, true);
-                } else {
-#pragma unroll
-                    for (int v = 0; v < NV; v++) { uL[v] = S.YS[1][v][GE][r]; uR[v] = S.YS[0][v][GE + 1][r]; }
-                    hllc<1>(uL, uR, F, g);
-#pragma unroll
-                    for (int v = 0; v < NV; v++) S.FY[v][GE][r] = F[v];
-                    cf_register<1>(S, P, dt, F, r, z, (r >> 3) + 2 + (z >> 3) * 4, -1, false, true);
-                }
-            }
+            x_face(S, P, dt, cy, cx, z, g);
+            y_face(S, P, dt, cy, cx, z, g);
+            if (warp == 0) high_faces(S, P, dt, lane, z, g);
         }
         __syncthreads();
 
@@ -424,7 +480,7 @@ __device__ __forceinline__ void step_group(StepSmem<real> &S, const StepParams &
 }
 
 template <typename real>
-__global__ void __launch_bounds__(STEP_THREADS, 1) k_hydro_step(StepParams P) {
+__global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydro_step(StepParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<real> &S = *reinterpret_cast<StepSmem<real> *>(smem_raw);
     const int tid = threadIdx.x;
@@ -472,7 +528,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_hydro_step(StepParams P) {
     __syncthreads();
     if (tid == 0) {
         double m = 0.0;
-        for (int i = 0; i < STEP_THREADS / 32; i++) m = fmax(m, S.red[i]);
+        for (int i = 0; i < StepCfg<real>::NT / 32; i++) m = fmax(m, S.red[i]);
         // positive doubles order like their bit patterns: exact, order-free max
         atomicMax(P.smax_out, (unsigned long long)__double_as_longlong(m));
     }
@@ -503,7 +559,7 @@ struct BoxLaunch {
 };
 
 template <typename real>
-__global__ void __launch_bounds__(STEP_THREADS, 1) k_hydro_step_boxes(BoxLaunch B) {
+__global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydro_step_boxes(BoxLaunch B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<real> &S = *reinterpret_cast<StepSmem<real> *>(smem_raw);
     const int tid = threadIdx.x;
@@ -572,7 +628,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_hydro_step_boxes(BoxLaunch 
         __syncthreads();
         if (tid == 0) {
             double m = 0.0;
-            for (int i = 0; i < STEP_THREADS / 32; i++) m = fmax(m, S.red[i]);
+            for (int i = 0; i < StepCfg<real>::NT / 32; i++) m = fmax(m, S.red[i]);
             atomicMax(P.smax_out, (unsigned long long)__double_as_longlong(m));
         }
         if ((tid & 31) == 0 && nb) atomicAdd(P.n_bad, (unsigned long long)nb);
