@@ -274,12 +274,12 @@ __device__ __forceinline__ void hancock_cell(const StepSmem<real> &S, int x, int
 }
 
 // Stage C face evaluations of plane z.  Thread (cx, cy) takes the x face
-// x = cx - 1/2 of row cy and the y face y = cy - 1/2 of column cx; warp 0
+// x = cx - 1/2 of row cy and the y face y = cy - 1/2 of column cx; one warp
 // also takes the group's high faces, x = 16 - 1/2 of the 16 rows (lanes
 // 0..15) and y = 16 - 1/2 of the 16 columns (lanes 16..31), in one
 // divergence-free pass through hllc_dir.  The FP64 pipe charges a whole warp
-// instruction however few lanes are active, so that pass costs warp 0 one
-// solver evaluation instead of two.
+// instruction however few lanes are active, so that pass costs one solver
+// evaluation instead of two.
 template <typename real>
 __device__ __forceinline__ void x_face(StepSmem<real> &S, const StepParams &P, double dt, int row, int col, int z,
                                        const Gas<real> &g) {
@@ -328,6 +328,19 @@ __device__ __forceinline__ void high_faces(StepSmem<real> &S, const StepParams &
     }
     const int pa = D == 0 ? 1 + (k >> 3) * 2 + (z >> 3) * 4 : (k >> 3) + 2 + (z >> 3) * 4;
     cf_register(S, P, dt, F, D, k, z, pa, -1, false, true);
+}
+
+// The z face z - 1/2 below column (cx, cy): HLLC of the column's own face
+// states (registers), plus its coarse-fine registers on patch faces.
+template <typename real>
+__device__ __forceinline__ void z_face(const StepSmem<real> &S, const StepParams &P, double dt, const real zp_prev[NV],
+                                       const real zm[NV], int cx, int cy, int z, real fz[NV], const Gas<real> &g) {
+    hllc<2>(zp_prev, zm, fz, g);
+    if (z == 0 || z == GE || z == 8) {
+        const int pl = (cx >> 3) + 2 * (cy >> 3);
+        cf_register(S, P, dt, fz, 2, cx, cy, z == 0 ? -1 : pl + 4 * ((z - 1) >> 3), z == GE ? -1 : pl + 4 * (z >> 3),
+                    z == 0, z == GE);
+    }
 }
 
 // One patch group: the whole fused step for group `grp` of P's level.  The
@@ -380,12 +393,15 @@ __device__ __forceinline__ void step_group(StepSmem<real> &S, const StepParams &
         __syncthreads();
 
         // ---- B: Hancock states of plane z
-        real zm[NV], zp[NV];
+        real zm[NV], zp[NV], fz[NV];
         {
             real uf[6][NV];
             hancock_cell(S, cx, cy, z, dtdh_half, g, uf);
 #pragma unroll
             for (int v = 0; v < NV; v++) { zm[v] = uf[4][v]; zp[v] = uf[5][v]; }
+            // Sub-partitions 2 and 3 (warp & 2) have no ghost-ring cells in this
+            // stage: they take their z face here rather than in stage C.
+            if ((warp & 2) && z >= 0) z_face(S, P, dt, zp_prev, zm, cx, cy, z, fz, g);
             if (z >= 0 && z < GE) {
 #pragma unroll
                 for (int v = 0; v < NV; v++) {
@@ -421,20 +437,15 @@ __device__ __forceinline__ void step_group(StepSmem<real> &S, const StepParams &
         }
         __syncthreads();
 
-        // ---- C: the z face below each owned column, then its x and y faces
-        real fz[NV];
-        if (z >= 0) {
-            hllc<2>(zp_prev, zm, fz, g);
-            if (z == 0 || z == GE || z == 8) {
-                const int pl = (cx >> 3) + 2 * (cy >> 3);
-                cf_register(S, P, dt, fz, 2, cx, cy, z == 0 ? -1 : pl + 4 * ((z - 1) >> 3),
-                            z == GE ? -1 : pl + 4 * (z >> 3), z == 0, z == GE);
-            }
-        }
+        // ---- C: the z face below the column (sub-partitions 0, 1), its x and
+        // y faces, and the group's high faces on warp 2 (sub-partition 2), so
+        // every sub-partition's FP64 share carries 5 or 6 face evaluations
+        // here after 3 or 2 Hancock cells (+2 z faces) in stage B
+        if (!(warp & 2) && z >= 0) z_face(S, P, dt, zp_prev, zm, cx, cy, z, fz, g);
         if (z >= 0 && z < GE) {
             x_face(S, P, dt, cy, cx, z, g);
             y_face(S, P, dt, cy, cx, z, g);
-            if (warp == 0) high_faces(S, P, dt, lane, z, g);
+            if (warp == 2) high_faces(S, P, dt, lane, z, g);
         }
         __syncthreads();
 
