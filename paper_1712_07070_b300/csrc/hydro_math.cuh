@@ -16,30 +16,37 @@ constexpr int NV = 5;
 // FP64: on this GPU the FP64 pipe issues 2 operations per clock per SM, and an
 // IEEE division costs about nine of them.  The reciprocal is instead seeded by
 // the special-function unit's approximate reciprocal (rcp.approx.ftz.f64,
-// which runs on a separate, much wider unit) and refined by two Newton-Raphson
-// steps for f(r) = 1/r - x, r <- r + r (1 - x r): each step squares the
-// relative error, so two steps from the seed reach the FP64 rounding level (a
-// few ulp, well inside the 1e-12 tolerance; checked against IEEE division in
-// the tests).  The reciprocal square root is refined the same way with the
-// Newton step for f(y) = 1/y^2 - x, y <- y (3 - x y^2)/2.
+// which runs on a separate, much wider unit, relative error below 2^-20) and
+// refined by one third-order step of Householder's method for f(r) = 1/r - x:
+// with e = 1 - x r, r <- r (1 + e + e^2) leaves a relative error of e^3
+// (below 2^-60, so the result is at the FP64 rounding level) in 3 fused
+// multiply-adds, one fewer than two Newton-Raphson steps.  The reciprocal
+// square root takes the same route for f(y) = 1/y^2 - x: with e = 1 - x y^2,
+// y <- y (1 + e/2 + 3e^2/8) (the binomial series of (1 - e)^(-1/2) to second
+// order; error 5e^3/16), 5 operations.  The square root of a positive normal
+// x is x * rsqrt_(x) (a few ulp); zeros, subnormals, negative and non-finite
+// inputs take CUDA's sqrt.  All three are checked against IEEE division and
+// square root in the tests.
 // FP32: the hardware approximations (about 1 ulp), inside the FP32 mode's
 // 1e-5 tolerance.
 __device__ __forceinline__ double rcp_(double x) {
     double r;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-    double e = fma(-x, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-x, r, 1.0);
-    return fma(r, e, r);
+    const double e = fma(-x, r, 1.0);
+    return fma(r, fma(e, e, e), r);
 }
 __device__ __forceinline__ double rsqrt_(double x) {
     double y;
     asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-    const double hx = 0.5 * x;
-    y = y * fma(-hx, y * y, 1.5);
-    return y * fma(-hx, y * y, 1.5);
+    const double e = fma(-x, y * y, 1.0);
+    return fma(y * e, fma(e, 0.375, 0.5), y);
 }
-__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+__device__ __forceinline__ double sqrt_(double x) {
+    // positive normal: high word in [0x00100000, 0x7fefffff]
+    const unsigned hi = (unsigned)__double2hiint(x);
+    if (hi - 0x00100000u < 0x7fe00000u) return x * rsqrt_(x);
+    return sqrt(x);
+}
 __device__ __forceinline__ float rcp_(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
