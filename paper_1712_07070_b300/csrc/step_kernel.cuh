@@ -78,8 +78,8 @@ struct StepSmem {
     real YS[2][NV][GE + 2][GE];  // y-/y+ face states, cells y=-1..16, columns x=0..15
     real FX[NV][GE][GE + 1];     // x flux at face x-1/2, x=0..16
     real FY[NV][GE + 1][GE];     // y flux at face y-1/2, y=0..16
-    double raw[NV][TW * TW];  // next tile plane in flight (cp.async), cells owned per thread
-    double uo[2][NV][COLS];  // each column's U^n one plane ahead of its update (cp.async)
+    alignas(16) double raw[NV][TW * TW];  // next tile plane in flight (cp.async), x-pairs owned per thread
+    alignas(16) double uo[2][NV][COLS];   // each column's U^n one plane ahead of its update (cp.async)
     int nbr[64];
     long long cfo[6];   // fine register blocks of the group's faces (-1: none)
     long long cco[48];  // coarse register blocks of its 8 patches' faces (-1: none)
@@ -184,12 +184,15 @@ __device__ __forceinline__ void load_plane(StepSmem<real> &S, const StepParams &
     }
 }
 
-// Asynchronous copy of tile plane tz into S.raw: each thread copies the
-// cells i = tid, tid + 256 (< 400) that it will also convert, so the copy
-// needs no CTA barrier, only the thread's own cp.async wait.
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+// Asynchronous copy of tile plane tz into S.raw in 16-byte pieces: tile
+// columns are taken in x-pairs (tx, tx+1) with tx even, which never straddle a
+// patch and start on a 16-byte boundary in both the patch slot and S.raw.
+// Thread j copies and later converts pair j (< 200), so the copy needs no CTA
+// barrier, only the thread's own cp.async wait.
+constexpr int TPAIRS = TW * TW / 2;
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
@@ -197,15 +200,15 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <typename real>
 __device__ __forceinline__ void issue_plane(StepSmem<real> &S, const StepParams &P, int tz) {
     const int qz = (tz + PS) >> 3, lz = (tz + PS) & 7;
-    for (int i = threadIdx.x; i < TW * TW; i += StepCfg<real>::NT) {
-        const int ty = i / TW - 2, tx = i % TW - 2;
+    for (int j = threadIdx.x; j < TPAIRS; j += StepCfg<real>::NT) {
+        const int ty = j / (TW / 2) - 2, tx = 2 * (j % (TW / 2)) - 2;
         const int qy = (ty + PS) >> 3, ly = (ty + PS) & 7;
         const int qx = (tx + PS) >> 3, lx = (tx + PS) & 7;
         const double *src = patch_src(P, S.nbr[qx + 4 * qy + 16 * qz]);
         if (src) {
             const int off = lz * 64 + ly * 8 + lx;
 #pragma unroll
-            for (int v = 0; v < NV; v++) cp_async8(&S.raw[v][i], src + v * PV + off);
+            for (int v = 0; v < NV; v++) cp_async16(&S.raw[v][2 * j], src + v * PV + off);
         }
     }
     cp_async_commit();
@@ -218,19 +221,29 @@ __device__ __forceinline__ void finish_plane(StepSmem<real> &S, int tz, const Ga
     cp_async_wait_all();
     const int slot = (tz + 3) % 3;
     const int qz = (tz + PS) >> 3;
-    for (int i = threadIdx.x; i < TW * TW; i += StepCfg<real>::NT) {
-        const int ty = i / TW - 2, tx = i % TW - 2;
+    for (int j = threadIdx.x; j < TPAIRS; j += StepCfg<real>::NT) {
+        const int ty = j / (TW / 2) - 2, tx = 2 * (j % (TW / 2)) - 2;
         const int qy = (ty + PS) >> 3, qx = (tx + PS) >> 3;
-        real u[NV], w[NV];
+        real w[2][NV];
         if (S.nbr[qx + 4 * qy + 16 * qz] != -1) {
 #pragma unroll
-            for (int v = 0; v < NV; v++) u[v] = to_real<real>(S.raw[v][i]);
-            u2w(u, w, g);
-        } else {
-            w[0] = real(1); w[1] = w[2] = w[3] = real(0); w[4] = real(1);
+            for (int h = 0; h < 2; h++) {
+                real u[NV];
+#pragma unroll
+                for (int v = 0; v < NV; v++) u[v] = to_real<real>(S.raw[v][2 * j + h]);
+                u2w(u, w[h], g);
+            }
+        } else {  // a position no stencil reads (a tile corner): benign state
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                w[h][0] = real(1); w[h][1] = w[h][2] = w[h][3] = real(0); w[h][4] = real(1);
+            }
         }
 #pragma unroll
-        for (int v = 0; v < NV; v++) S.W[slot][v][ty + 2][tx + 2] = w[v];
+        for (int v = 0; v < NV; v++) {
+            S.W[slot][v][ty + 2][tx + 2] = w[0][v];
+            S.W[slot][v][ty + 2][tx + 3] = w[1][v];
+        }
     }
 }
 
@@ -383,14 +396,19 @@ __device__ __forceinline__ void step_group(StepSmem<real> &S, const StepParams &
     for (int z = -1; z <= GE; z++) {
         finish_plane(S, z + 1, g);
         if (z + 2 <= GE + 1) issue_plane(S, P, z + 2);
-        if (z >= 0 && z < GE) {  // this column's U^n at plane z, for its update next iteration
-            const double *src = P.U_old + (own + (cx >> 3) + 2 * (cy >> 3) + 4 * (z >> 3)) * PSLOT +
-                                (z & 7) * 64 + (cy & 7) * 8 + (cx & 7);
+        __syncthreads();
+        if (z >= 0 && z < GE && tid < COLS / 2) {
+            // U^n of columns 2 tid, 2 tid + 1 at plane z (16-byte copies), for
+            // their update in the next iteration.  Issued after the barrier: the
+            // slot was last read by those columns' threads in the previous
+            // iteration's stage D; the next finish_plane waits for it.
+            const int px = (2 * tid) & 15, py = (2 * tid) >> 4;
+            const double *src = P.U_old + (own + (px >> 3) + 2 * (py >> 3) + 4 * (z >> 3)) * PSLOT +
+                                (z & 7) * 64 + (py & 7) * 8 + (px & 7);
 #pragma unroll
-            for (int v = 0; v < NV; v++) cp_async8(&S.uo[z & 1][v][tid], src + v * PV);
+            for (int v = 0; v < NV; v++) cp_async16(&S.uo[z & 1][v][2 * tid], src + v * PV);
             cp_async_commit();
         }
-        __syncthreads();
 
         // ---- B: Hancock states of plane z
         real zm[NV], zp[NV], fz[NV];
