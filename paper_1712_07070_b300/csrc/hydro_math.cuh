@@ -96,6 +96,35 @@ __device__ __forceinline__ double to_real<double>(double x) { return x; }
 template <>
 __device__ __forceinline__ float to_real<float>(double x) { return d2f_bits(x); }
 
+// ---- sign tests and ordering on the integer units ----------------------------------
+//
+// Every FP64 comparison takes a full issue of the narrow FP64 pipe, which sets
+// the pace of the FP64 step, so in FP64 the limiter's and the Riemann solver's
+// sign tests and min/max read the IEEE-754 bit pattern on the integer units
+// instead.  For a non-NaN double with bits b (a signed 64-bit integer):
+// x > 0 <=> b > 0 (+0 is 0, -0 is negative); x <= 0 <=> b <= 0;
+// x >= 0 <=> b >= 0 or x is -0.  okey(x) flips the magnitude bits of negative
+// values, so it orders like x, except that -0 sorts just below +0 (a min/max
+// of two zeros of opposite sign may return the other zero).  FP32 keeps the
+// ordinary comparisons, which run on the integer/ALU pipe anyway.
+__device__ __forceinline__ long long okey(double x) {
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool gt0(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool le0(double x) { return __double_as_longlong(x) <= 0; }
+__device__ __forceinline__ bool ge0(double x) {
+    const long long b = __double_as_longlong(x);
+    return b >= 0 || b == (long long)0x8000000000000000ULL;
+}
+__device__ __forceinline__ double min_(double a, double b) { return okey(a) <= okey(b) ? a : b; }
+__device__ __forceinline__ double max_(double a, double b) { return okey(a) >= okey(b) ? a : b; }
+__device__ __forceinline__ bool gt0(float x) { return x > 0.0f; }
+__device__ __forceinline__ bool le0(float x) { return x <= 0.0f; }
+__device__ __forceinline__ bool ge0(float x) { return x >= 0.0f; }
+__device__ __forceinline__ float min_(float a, float b) { return (a <= b) ? a : b; }
+__device__ __forceinline__ float max_(float a, float b) { return (a >= b) ? a : b; }
+
 template <typename real>
 struct Gas {
     real gamma, gm1, inv_gm1;
@@ -127,7 +156,7 @@ __device__ __forceinline__ void w2u(const real w[NV], real u[NV], const Gas<real
 template <typename real>
 __device__ __forceinline__ real half_vanleer(real a, real b) {
     const real ab = a * b;
-    return ab > real(0) ? ab * rcp_(a + b) : real(0);
+    return gt0(ab) ? ab * rcp_(a + b) : real(0);
 }
 
 // Physical flux along D of a state known in both forms (w, u).
@@ -176,23 +205,20 @@ __device__ __forceinline__ void hllc(const real uL[NV], const real uR[NV], real 
     const real ct = sqrt_(g.gm1 * (ht - real(0.5) * (vtx * vtx + vty * vty + vtz * vtz)));
     const real vtn = D == 0 ? vtx : (D == 1 ? vty : vtz);
 
-    real a = ul - cl, b = vtn - ct;
-    const real SL = (a <= b) ? a : b;
-    a = ur + cr;
-    b = vtn + ct;
-    const real SR = (a >= b) ? a : b;
+    const real SL = min_(ul - cl, vtn - ct);
+    const real SR = max_(ur + cr, vtn + ct);
 
-    if (SL >= real(0)) {
+    if (ge0(SL)) {
         phys_flux<D>(wL, uL, F);
         return;
     }
-    if (SR <= real(0)) {
+    if (le0(SR)) {
         phys_flux<D>(wR, uR, F);
         return;
     }
     const real ml = rl * (SL - ul), mr = rr * (SR - ur);  // mass fluxes relative to the waves
     const real Ss = (pr - pl + ml * ul - mr * ur) * rcp_(ml - mr);
-    const bool left = Ss >= real(0);
+    const bool left = ge0(Ss);
     const real *uK = left ? uL : uR;
     const real *wK = left ? wL : wR;
     const real SK = left ? SL : SR;
@@ -219,7 +245,7 @@ template <typename real>
 __device__ __forceinline__ real cfl_speed(const real u[NV], const Gas<real> &g, bool &ok) {
     real w[NV];
     const real ri = u2w(u, w, g);
-    ok = (w[0] > real(0)) && (w[4] > real(0));
+    ok = gt0(w[0]) && gt0(w[4]);
     return fabs(w[1]) + fabs(w[2]) + fabs(w[3]) + real(3) * sqrt_(g.gamma * w[4] * ri);
 }
 

@@ -41,3 +41,22 @@ def test_math_helpers_against_ieee():
     fulp = np.spacing(np.abs(o[:, 5]).astype(np.float32)).astype(np.float64)
     assert (np.abs(o[inrange, 4] - o[inrange, 5]) <= fulp[inrange]).all()
     assert np.array_equal(o[inrange, 6], o[inrange, 7])
+
+
+def test_integer_sign_tests_and_minmax():
+    """The FP64 step's integer-unit sign tests and min/max agree with the
+    FP64 comparisons on signed zeros, subnormals, infinities and random
+    values of both signs."""
+    import torch
+    rng = np.random.default_rng(1)
+    special = np.array([0.0, -0.0, 5e-324, -5e-324, 1e-310, -1e-310, 1.0, -1.0, np.inf, -np.inf,
+                        1.7976931348623157e308, -1.7976931348623157e308, 2.2250738585072014e-308])
+    a = np.concatenate([np.repeat(special, len(special)), rng.standard_normal(20000) * 10.0 ** rng.uniform(-5, 5, 20000)])
+    b = np.concatenate([np.tile(special, len(special)), rng.standard_normal(20000) * 10.0 ** rng.uniform(-5, 5, 20000)])
+    b[-5000:] = a[-5000:]  # ties
+    ad, bd = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    out = torch.empty(len(a), dtype=torch.int32, device="cuda")
+    fn = A.lib().amrh_selftest_order
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    assert fn(ad.data_ptr(), bd.data_ptr(), len(a), out.data_ptr()) == 0
+    assert (out.cpu().numpy() == 31).all()
