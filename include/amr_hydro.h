@@ -183,6 +183,31 @@ amr_status amr_hydro_advance_level(amr_hydro_ctx *ctx, int level, double dt,
                                    int64_t *n_unphysical_out);
 
 /*
+ * The step of amr_hydro_advance_level for a uniform periodic root grid held on
+ * the host (section 3.1 overlaps host-device transfers with the GPU solver
+ * through CUDA streams): U_in is copied to the device, advanced one step and
+ * the new state copied back into U_out, in z-slabs of 16 cell planes so that
+ * the copies in both directions overlap the update.  Results are bitwise
+ * those of amr_hydro_advance_level on the same state.
+ *   U_in, U_out  host FP64 [5][nz][ny][nx] (the root grid, x fastest); page-
+ *                locked memory gives the overlap, pageable memory works but
+ *                serialises the copies.  U_out may equal U_in.
+ *   dt           > 0: the step size; <= 0: the Eq. (CFL2) dt of U_in, which
+ *                needs all of U_in on the device before the first slab steps
+ *   dt_next      host double (may be NULL): the Eq. (CFL2) dt of U_out (-1 if
+ *                it has no positive signal speed), to pass as the next dt
+ * Level 0 must be the whole root grid in the order of
+ * amr_hydro_uniform_tables (set with amr_hydro_set_level) and no finer level
+ * may hold patches; otherwise AMR_E_INVAL.  The level's device state becomes
+ * the new state, as after amr_hydro_advance_level.  The call returns when
+ * U_out is complete (it synchronises the context's stream and its two copy
+ * streams).  The device keeps two dense staging copies of the grid
+ * (2 x 40 bytes per cell), allocated on the first call.
+ */
+amr_status amr_hydro_advance_host(amr_hydro_ctx *ctx, const double *U_in, double *U_out, double dt,
+                                  double *dt_next);
+
+/*
  * Synchronise coarse_level with coarse_level+1 (section 2.2): coarse leaf
  * cells next to a coarse-fine interface get
  * U_c -= (sum dt_f <F_f> - dt_c F_c)/dh_c across their high faces (+= across

@@ -8,6 +8,8 @@ there is no CPU fallback.  Device arrays are passed as raw pointers, e.g.
 import ctypes
 import os
 
+import numpy as np
+
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libamr_hydro.so")
 
@@ -24,6 +26,7 @@ SYMBOLS = (
     "amr_hydro_strerror", "amr_hydro_uniform_tables", "amr_hydro_pack_uniform",
     "amr_hydro_unpack_uniform", "amr_hydro_step_uniform_noalloc", "amr_hydro_bind_level",
     "amr_hydro_regrid", "amr_hydro_advance_root", "amr_hydro_level_info", "amr_hydro_box_tuning",
+    "amr_hydro_advance_host",
 )
 
 
@@ -63,6 +66,7 @@ def lib():
         "amr_hydro_touch_level": [_vp, ctypes.c_int],
         "amr_hydro_fill_ghost": [_vp, ctypes.c_int, ctypes.c_double],
         "amr_hydro_advance_level": [_vp, ctypes.c_int, ctypes.c_double, _i64p],
+        "amr_hydro_advance_host": [_vp, _vp, _vp, ctypes.c_double, _dp],
         "amr_hydro_flux_fixup": [_vp, ctypes.c_int],
         "amr_hydro_min_dt": [_vp, ctypes.c_int, _vp],
         "amr_hydro_regrid_flags": [_vp, ctypes.c_int, _vp],
@@ -104,11 +108,13 @@ def check(status, where):
 
 
 def _p(x):
-    """Raw pointer of a torch tensor / int / None."""
+    """Raw pointer of a torch tensor / numpy array / int / None."""
     if x is None:
         return None
     if isinstance(x, int):
         return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
     return x.data_ptr()
 
 
@@ -231,6 +237,15 @@ def amr_hydro_pack_uniform(dense, nx, ny, nz, patches, stream=None):
 def amr_hydro_unpack_uniform(patches, nx, ny, nz, dense, stream=None):
     check(lib().amr_hydro_unpack_uniform(_p(patches), nx, ny, nz, _p(dense), _p(stream)),
           "amr_hydro_unpack_uniform")
+
+
+def amr_hydro_advance_host(ctx, U_in, U_out, dt=-1.0):
+    """One step of the uniform root grid from host state U_in to host state
+    U_out ([5][nz][ny][nx] float64, page-locked for overlapped copies);
+    returns the CFL dt of U_out."""
+    dn = ctypes.c_double()
+    check(lib().amr_hydro_advance_host(ctx, _p(U_in), _p(U_out), dt, ctypes.byref(dn)), "amr_hydro_advance_host")
+    return dn.value
 
 
 def amr_hydro_step_uniform_noalloc(U_old, U_new, nx, ny, nz, dh, dt, gamma, cfl, prec,

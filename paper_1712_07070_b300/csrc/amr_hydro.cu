@@ -247,6 +247,11 @@ amr_status amr_hydro_destroy(amr_hydro_ctx *c) {
     c->regrid_tmp.release();
     c->adjbuf.release();
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    for (cudaStream_t x : c->xfer)
+        if (x) cudaStreamDestroy(x);
+    for (cudaEvent_t e : c->slab_ev) cudaEventDestroy(e);
+    c->hstage[0].release();
+    c->hstage[1].release();
     delete c;
     return AMR_OK;
 }

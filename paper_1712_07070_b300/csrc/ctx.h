@@ -68,6 +68,7 @@ struct Level {
     int scal0 = 0;  // first of this level's 8 scalar slots
     int ring = 0;   // ring position of the newest state
     bool speed_valid = false;
+    bool uniform = false;  // level 0 holding the whole root grid in the order of amr_hydro_uniform_tables
     void release() {
         nbr.release();
         ghost.release();
@@ -122,6 +123,11 @@ struct amr_hydro_ctx {
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<long long> graph_key;
+    // host-streamed steps (amr_hydro_advance_host): copy streams, per-slab
+    // events and the dense device staging of the input and output states
+    cudaStream_t xfer[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> slab_ev;
+    amrh::DevBuf<double> hstage[2];
 };
 
 namespace amrh {

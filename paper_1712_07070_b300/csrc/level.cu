@@ -83,6 +83,20 @@ amr_status amr_hydro_set_level(amr_hydro_ctx *c, int level, int n_patches, doubl
     for (int d = 0; d < 3; d++) cells[d] = c->prm.root_n[d] << level;
     for (int i = 0; i < 3 * n_patches; i++)
         if (L.corner[i] < 0 || L.corner[i] >= cells[i % 3] || L.corner[i] % 8) return AMR_E_INVAL;
+    // the whole root grid in the slot order of amr_hydro_uniform_tables
+    // (groups x-fastest, patches x-fastest within a group)?
+    L.uniform = false;
+    if (level == 0 && (int64_t)n_patches * 512 == (int64_t)cells[0] * cells[1] * cells[2]) {
+        const int ngx = cells[0] / 16, ngy = cells[1] / 16;
+        bool ok = cells[0] % 16 == 0 && cells[1] % 16 == 0 && cells[2] % 16 == 0;
+        for (int s = 0; s < n_patches && ok; s++) {
+            const int g = s / 8, k = s % 8;
+            ok = L.corner[3 * s] == 16 * (g % ngx) + 8 * (k & 1) &&
+                 L.corner[3 * s + 1] == 16 * ((g / ngx) % ngy) + 8 * ((k >> 1) & 1) &&
+                 L.corner[3 * s + 2] == 16 * (g / (ngx * ngy)) + 8 * (k >> 2);
+        }
+        L.uniform = ok;
+    }
     if ((st = plan_level(c, level))) return st;
     if (level > 0 && (st = rebuild_cf(c, level))) return st;
     if (level < c->prm.lmax && c->lv[level + 1].n_patches && (st = rebuild_cf(c, level + 1))) return st;

@@ -59,8 +59,9 @@ struct StepParams {
     double *__restrict__ U_new;
     const int32_t *__restrict__ nbr;  // [n_groups][64] source of each 4x4x4 patch position
     const double *__restrict__ ghost; // interpolated coarse-fine ghost patches
-    const int32_t *__restrict__ work; // optional list of group ids (null: 0..n_work-1)
+    const int32_t *__restrict__ work; // optional list of group ids (null: work0..work0+n_work-1)
     int n_work;
+    int work0;
     double dt;                               // >= 0: time step from the host
     const unsigned long long *smax_in;       // dt < 0: dt = cfl*dh/smax_in
     double cfl, dh, gamma;
@@ -542,7 +543,7 @@ __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydr
     unsigned nbad = 0;
 
     for (int wi = blockIdx.x; wi < P.n_work; wi += gridDim.x) {
-        const int grp = P.work ? P.work[wi] : wi;
+        const int grp = P.work ? P.work[wi] : P.work0 + wi;
         step_group(S, P, grp, dt, g, smax_r, nbad);
     }
 

@@ -90,3 +90,10 @@ class UniformGrid:
 
     def step(self, dt=-1.0, count_unphysical=False):
         return A.amr_hydro_advance_level(self.ctx, 0, dt, count_unphysical)
+
+    def step_host(self, U_in, U_out, dt=-1.0):
+        """One step from host state U_in to host state U_out ([5][nz][ny][nx]
+        float64 tensors or arrays on the host; page-locked memory lets the
+        copies overlap the update).  Returns the CFL dt of U_out, the dt to
+        pass to the next call of a chained run."""
+        return A.amr_hydro_advance_host(self.ctx, U_in, U_out, dt)
