@@ -45,26 +45,30 @@ struct CoarseView {
 // Fine patches interpolated from the coarse level.  Job j (GHOST_INFO ints):
 // coarse parent P of the group the patch is placed around, patch position q
 // relative to that group (each -1..2), and the box of fine cells wanted
-// (even bounds); output patch out_slot[j] (or j).  One thread per coarse
-// cell of the box computes its value, slopes and positivity test once and
-// writes its eight children.
+// (even bounds); output patch out_slot[j] (or j).  One warp per job (a box
+// has at most 4x4x4 coarse cells, a face ghost 16); one lane per coarse cell
+// of the box computes its value, slopes and positivity test once and writes
+// its eight children.
+constexpr int INTERP_WARPS = 8;  // warps (jobs in flight) per 256-thread block
 __global__ void k_interp_patches(double *__restrict__ out, const int32_t *__restrict__ out_slot,
                                  const int32_t *__restrict__ info, int n_jobs, const double *Uo,
                                  const double *Un, double w, const int32_t *__restrict__ csib) {
-    __shared__ int nb[27];
-    for (int j = blockIdx.x; j < n_jobs; j += gridDim.x) {
+    __shared__ int nbs[INTERP_WARPS][27];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *nb = nbs[warp];
+    for (int j = blockIdx.x * INTERP_WARPS + warp; j < n_jobs; j += gridDim.x * INTERP_WARPS) {
         const int32_t *I = info + (int64_t)GHOST_INFO * j;
         const int P = I[0], qx = I[1], qy = I[2], qz = I[3], box = I[4];
         const int lo[3] = {box & 15, (box >> 4) & 15, (box >> 8) & 15};
         const int hi[3] = {(box >> 12) & 15, (box >> 16) & 15, (box >> 20) & 15};
         const int n[3] = {(hi[0] - lo[0]) >> 1, (hi[1] - lo[1]) >> 1, (hi[2] - lo[2]) >> 1};
-        __syncthreads();
-        load_block27(nb, P, csib);
-        __syncthreads();
+        __syncwarp();  // the previous job's reads of nb are done
+        if (lane < 27) nb[lane] = lane == 13 ? P : csib[(int64_t)P * 26 + lane - (lane > 13)];
+        __syncwarp();
         CoarseView C{Uo, Un, w, nb};
         double *o = out + (int64_t)(out_slot ? out_slot[j] : j) * PSLOT;
         const int total = n[0] * n[1] * n[2];
-        for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        for (int i = lane; i < total; i += 32) {
             // local fine cell of the child (0,0,0) of this coarse cell
             const int fx = lo[0] + 2 * (i % n[0]), fy = lo[1] + 2 * ((i / n[0]) % n[1]),
                       fz = lo[2] + 2 * (i / (n[0] * n[1]));
@@ -263,7 +267,8 @@ amr_status fill_ghost_impl(amr_hydro_ctx *c, int level, double t) {
     amr_status st = level_time(c, level - 1);
     if (st) return st;
     const double w = coarse_weight(C, t);
-    const int grid = L.n_ghost < 4 * c->n_sm ? L.n_ghost : 4 * c->n_sm;
+    const int blocks = (L.n_ghost + INTERP_WARPS - 1) / INTERP_WARPS;
+    const int grid = blocks < 8 * c->n_sm ? blocks : 8 * c->n_sm;
     k_interp_patches<<<grid, 256, 0, c->stream>>>(L.ghost.p, nullptr, L.ghost_info.p, L.n_ghost, C.U[1 - C.cur],
                                                    C.U[C.cur], w, C.d_sib);
     return cuda_fail(cudaGetLastError(), "k_interp_patches");
@@ -273,7 +278,8 @@ amr_status interp_new_patches(amr_hydro_ctx *c, int coarse, double *out, const i
                               const int32_t *info, int n_jobs) {
     if (!n_jobs) return AMR_OK;
     Level &C = c->lv[coarse];
-    const int grid = n_jobs < 4 * c->n_sm ? n_jobs : 4 * c->n_sm;
+    const int blocks = (n_jobs + INTERP_WARPS - 1) / INTERP_WARPS;
+    const int grid = blocks < 8 * c->n_sm ? blocks : 8 * c->n_sm;
     k_interp_patches<<<grid, 256, 0, c->stream>>>(out, out_slot, info, n_jobs, C.U[C.cur], C.U[C.cur], 1.0,
                                                    C.d_sib);
     return cuda_fail(cudaGetLastError(), "k_interp_patches (new patches)");
