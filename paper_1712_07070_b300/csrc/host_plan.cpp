@@ -62,70 +62,82 @@ amr_status build_nbr_plan(int level, int n_patches, const int32_t *corner, const
     const int n_groups = n_patches / 8;
     nbr.assign((size_t)n_groups * 64, -1);
     ghosts.clear();
+    // per position (qx+1) + 4(qy+1) + 16(qz+1): the group's own patch it is
+    // reached from, the sibling index of the step to it, its offset in cells,
+    // whether it is a corner (never read) and the box of its cells the
+    // group's stencils reach (2 deep along an outer direction, all 8 along an
+    // inner one)
+    struct PosInfo {
+        int own, sk, off[3], corner, box;
+    };
+    PosInfo pi[64];
+    for (int pos = 0; pos < 64; pos++) {
+        const int q3[3] = {(pos & 3) - 1, ((pos >> 2) & 3) - 1, (pos >> 4) - 1};
+        int p3[3], d3[3], box = 0;
+        for (int d = 0; d < 3; d++) {
+            p3[d] = q3[d] < 0 ? 0 : (q3[d] > 1 ? 1 : q3[d]);
+            d3[d] = q3[d] - p3[d];
+            box |= (q3[d] < 0 ? 6 : 0) << (4 * d) | (q3[d] > 1 ? 2 : 8) << (12 + 4 * d);
+        }
+        PosInfo &e = pi[pos];
+        e.own = p3[0] + 2 * p3[1] + 4 * p3[2];
+        e.sk = (d3[0] || d3[1] || d3[2]) ? sib_index(d3[0], d3[1], d3[2]) : -1;
+        for (int d = 0; d < 3; d++) e.off[d] = 8 * d3[d];
+        e.corner = (d3[0] != 0) + (d3[1] != 0) + (d3[2] != 0) == 3;
+        e.box = box;
+    }
     // ghost patch ids by patch position (dense: the level's patch grid)
     const int P[3] = {level_cells[0] / 8, level_cells[1] / 8, level_cells[2] / 8};
     std::vector<int32_t> ghost_id;
     if (level > 0) ghost_id.assign((size_t)P[0] * P[1] * P[2], -1);
+    auto wrapc = [](int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); };  // |step| <= one patch
     for (int g = 0; g < n_groups; g++) {
-        for (int qz = -1; qz <= 2; qz++)
-            for (int qy = -1; qy <= 2; qy++)
-                for (int qx = -1; qx <= 2; qx++) {
-                    const int pos = (qx + 1) + 4 * (qy + 1) + 16 * (qz + 1);
-                    const int px = qx < 0 ? 0 : (qx > 1 ? 1 : qx);
-                    const int py = qy < 0 ? 0 : (qy > 1 ? 1 : qy);
-                    const int pz = qz < 0 ? 0 : (qz > 1 ? 1 : qz);
-                    const int own = 8 * g + px + 2 * py + 4 * pz;
-                    const int dx = qx - px, dy = qy - py, dz = qz - pz;
-                    if (!dx && !dy && !dz) {
-                        nbr[(size_t)g * 64 + pos] = own;
-                        continue;
-                    }
-                    const int32_t s = sib[26 * (int64_t)own + sib_index(dx, dy, dz)];
-                    if (s >= n_patches || s < -1) return AMR_E_INVAL;
-                    if (s >= 0) {
-                        nbr[(size_t)g * 64 + pos] = s;
-                        continue;
-                    }
-                    const int outer = (dx != 0) + (dy != 0) + (dz != 0);
-                    if (outer == 3) continue;  // corner: never read
-                    if (level == 0 || !parent) return AMR_E_NESTING;
-                    const int cx = wrapi(corner[3 * own + 0] + 8 * dx, level_cells[0]);
-                    const int cy = wrapi(corner[3 * own + 1] + 8 * dy, level_cells[1]);
-                    const int cz = wrapi(corner[3 * own + 2] + 8 * dz, level_cells[2]);
-                    int32_t &slot_id = ghost_id[((size_t)(cz / 8) * P[1] + cy / 8) * P[0] + cx / 8];
-                    // cells of this position the group's stencils reach: 2 deep
-                    // along an outer direction, all 8 along an inner one
-                    const int q3[3] = {qx, qy, qz};
-                    int lo[3], hi[3];
-                    for (int d = 0; d < 3; d++) {
-                        lo[d] = q3[d] < 0 ? 6 : 0;
-                        hi[d] = q3[d] > 1 ? 2 : 8;
-                    }
-                    int id;
-                    if (slot_id < 0) {
-                        id = (int)ghosts.size();
-                        slot_id = id;
-                        GhostInfo gi;
-                        gi.cparent = parent[8 * g];
-                        gi.qx = qx;
-                        gi.qy = qy;
-                        gi.qz = qz;
-                        gi.box = lo[0] | lo[1] << 4 | lo[2] << 8 | hi[0] << 12 | hi[1] << 16 | hi[2] << 20;
-                        if (gi.cparent < 0) return AMR_E_NESTING;
-                        ghosts.push_back(gi);
-                    } else {
-                        id = slot_id;
-                        GhostInfo &gi = ghosts[id];  // union with what other groups read
-                        int b = gi.box;
-                        for (int d = 0; d < 3; d++) {
-                            const int l0 = (b >> (4 * d)) & 15, h0 = (b >> (12 + 4 * d)) & 15;
-                            const int l1 = lo[d] < l0 ? lo[d] : l0, h1 = hi[d] > h0 ? hi[d] : h0;
-                            b = (b & ~(15 << (4 * d)) & ~(15 << (12 + 4 * d))) | l1 << (4 * d) | h1 << (12 + 4 * d);
-                        }
-                        gi.box = b;
-                    }
-                    nbr[(size_t)g * 64 + pos] = -2 - id;
+        int32_t *out = &nbr[(size_t)g * 64];
+        for (int pos = 0; pos < 64; pos++) {
+            const PosInfo &e = pi[pos];
+            const int own = 8 * g + e.own;
+            if (e.sk < 0) {
+                out[pos] = own;
+                continue;
+            }
+            const int32_t s = sib[26 * (int64_t)own + e.sk];
+            if (s >= n_patches || s < -1) return AMR_E_INVAL;
+            if (s >= 0) {
+                out[pos] = s;
+                continue;
+            }
+            if (e.corner) continue;  // never read
+            if (level == 0 || !parent) return AMR_E_NESTING;
+            const int cx = wrapc(corner[3 * own + 0] + e.off[0], level_cells[0]);
+            const int cy = wrapc(corner[3 * own + 1] + e.off[1], level_cells[1]);
+            const int cz = wrapc(corner[3 * own + 2] + e.off[2], level_cells[2]);
+            int32_t &slot_id = ghost_id[((size_t)(cz / 8) * P[1] + cy / 8) * P[0] + cx / 8];
+            int id;
+            if (slot_id < 0) {
+                id = (int)ghosts.size();
+                slot_id = id;
+                GhostInfo gi;
+                gi.cparent = parent[8 * g];
+                gi.qx = (pos & 3) - 1;
+                gi.qy = ((pos >> 2) & 3) - 1;
+                gi.qz = (pos >> 4) - 1;
+                gi.box = e.box;
+                if (gi.cparent < 0) return AMR_E_NESTING;
+                ghosts.push_back(gi);
+            } else {
+                id = slot_id;
+                GhostInfo &gi = ghosts[id];  // union with what other groups read
+                int b = gi.box;
+                for (int d = 0; d < 3; d++) {
+                    const int l0 = (b >> (4 * d)) & 15, h0 = (b >> (12 + 4 * d)) & 15;
+                    const int ln = (e.box >> (4 * d)) & 15, hn = (e.box >> (12 + 4 * d)) & 15;
+                    const int l1 = ln < l0 ? ln : l0, h1 = hn > h0 ? hn : h0;
+                    b = (b & ~(15 << (4 * d)) & ~(15 << (12 + 4 * d))) | l1 << (4 * d) | h1 << (12 + 4 * d);
                 }
+                gi.box = b;
+            }
+            out[pos] = -2 - id;
+        }
     }
     return AMR_OK;
 }

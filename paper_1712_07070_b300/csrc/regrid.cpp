@@ -265,15 +265,30 @@ amr_status amr_hydro_regrid(amr_hydro_ctx *c, int l) {
             }
         }
     }
-    for (int s = 0; s < nn; s++) {
-        const int p[3] = {corner[3 * s] / 8, corner[3 * s + 1] / 8, corner[3 * s + 2] / 8};
-        for (int dz = -1; dz <= 1; dz++)
-            for (int dy = -1; dy <= 1; dy++)
-                for (int dx = -1; dx <= 1; dx++) {
-                    if (!dx && !dy && !dz) continue;
-                    sib[(size_t)s * 26 + sib_k(dx, dy, dz)] =
-                        at_f[idx_f(wrapi(p[0] + dx, fc[0]), wrapi(p[1] + dy, fc[1]), wrapi(p[2] + dz, fc[2]))];
-                }
+    // sibling tables from each new group's 4x4x4 block of patch positions
+    // (64 lookups per group instead of 26 per patch)
+    auto wrapc = [](int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); };  // |step| <= 1 patch
+    for (int g = 0; g < ng; g++) {
+        int q[3][4];
+        for (int d = 0; d < 3; d++) {
+            const int b = corner[3 * (8 * g) + d] / 8;  // the group's low patch position
+            for (int i = 0; i < 4; i++) q[d][i] = wrapc(b - 1 + i, fc[d]);
+        }
+        int32_t blk[64];
+        for (int z = 0; z < 4; z++)
+            for (int y = 0; y < 4; y++) {
+                const size_t row = ((size_t)q[2][z] * fc[1] + q[1][y]) * fc[0];
+                for (int x = 0; x < 4; x++) blk[x + 4 * y + 16 * z] = at_f[row + q[0][x]];
+            }
+        for (int k = 0; k < 8; k++) {
+            const int lx = k & 1, ly = (k >> 1) & 1, lz = k >> 2;
+            int32_t *o = &sib[(size_t)(8 * g + k) * 26];
+            int m = 0;  // sibling index order: dx fastest, the patch itself skipped
+            for (int dz = 0; dz < 3; dz++)
+                for (int dy = 0; dy < 3; dy++)
+                    for (int dx = 0; dx < 3; dx++)
+                        if (dx != 1 || dy != 1 || dz != 1) o[m++] = blk[(lx + dx) + 4 * (ly + dy) + 16 * (lz + dz)];
+        }
     }
     // grandchildren keep their data; their parent slots are renumbered
     Level *G2 = (l + 2 <= c->prm.lmax && c->lv[l + 2].n_patches) ? &c->lv[l + 2] : nullptr;
@@ -307,10 +322,10 @@ amr_status amr_hydro_regrid(amr_hydro_ctx *c, int l) {
         return st;
 
     // tables: host mirrors and the caller's arrays
-    F.corner = corner;
-    F.sib = sib;
-    F.parent = parent;
-    F.child = child;
+    F.corner = std::move(corner);
+    F.sib = std::move(sib);
+    F.parent = std::move(parent);
+    F.child = std::move(child);
     F.n_patches = nn;
     F.n_groups = ng;
     F.cur = dst;
@@ -318,18 +333,18 @@ amr_status amr_hydro_regrid(amr_hydro_ctx *c, int l) {
     F.t_pending = false;
     F.speed_valid = false;
     F.ring = 0;
-    L.child = lchild;
+    L.child = std::move(lchild);
     auto put = [&](int32_t *d, const std::vector<int32_t> &h) -> amr_status {
         if (!d || h.empty()) return AMR_OK;
         return cuda_fail(cudaMemcpyAsync(d, h.data(), 4 * h.size(), cudaMemcpyHostToDevice, c->stream), "h2d");
     };
-    if ((st = put(F.w_corner, corner)) || (st = put(F.w_sib, sib)) || (st = put(F.w_parent, parent)) ||
-        (st = put(F.w_child, child)))
+    if ((st = put(F.w_corner, F.corner)) || (st = put(F.w_sib, F.sib)) || (st = put(F.w_parent, F.parent)) ||
+        (st = put(F.w_child, F.child)))
         return st;
-    if ((st = put(L.w_child, lchild))) return st;
+    if ((st = put(L.w_child, L.child))) return st;
     if (G2) {
-        G2->parent = g2parent;
-        if ((st = put(G2->w_parent, g2parent))) return st;
+        G2->parent = std::move(g2parent);
+        if ((st = put(G2->w_parent, G2->parent))) return st;
     }
     {
         const double rec[3] = {0.0, F.t, F.t};
