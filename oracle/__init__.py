@@ -34,6 +34,14 @@ def lib():
         L.or_vanleer.argtypes = [ctypes.c_double, ctypes.c_double]
         L.or_vanleer.restype = ctypes.c_double
         L.or_hllc.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_double, _dp]
+        L.or_hlle.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_double, _dp]
+        L.or_set_scheme.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double]
+        for name in ("or_gminmod", "or_vl_gminmod"):
+            getattr(L, name).argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            getattr(L, name).restype = ctypes.c_double
+        for name in ("or_albada", "or_slope"):
+            getattr(L, name).argtypes = [ctypes.c_double, ctypes.c_double]
+            getattr(L, name).restype = ctypes.c_double
         L.or_max_speed.argtypes = [_dp, ctypes.c_int64, ctypes.c_double]
         L.or_max_speed.restype = ctypes.c_double
         L.or_dt_cfl2.argtypes = [_dp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double]
@@ -91,6 +99,61 @@ def flux(U, d, gamma):
 def vanleer(a, b):
     """van Leer-type limiter, 2ab/(a+b) when ab>0 else 0 (section 2.2)."""
     return lib().or_vanleer(a, b)
+
+
+# ---- scheme options (section 2.2 lists the limiters and Riemann solvers) -----
+
+LIM_VANLEER, LIM_GMINMOD, LIM_ALBADA, LIM_VL_GMINMOD = 0, 1, 2, 3
+RS_HLLC, RS_HLLE = 0, 1
+
+
+def set_scheme(limiter=LIM_VANLEER, riemann=RS_HLLC, theta=1.5):
+    """Select the slope limiter, the Riemann solver and the generalized
+    minmod coefficient of every later oracle step (process-wide)."""
+    lib().or_set_scheme(limiter, riemann, theta)
+
+
+class scheme:
+    """Context manager: a scheme for the steps inside, the default after."""
+
+    def __init__(self, limiter=LIM_VANLEER, riemann=RS_HLLC, theta=1.5):
+        self.args = (limiter, riemann, theta)
+
+    def __enter__(self):
+        set_scheme(*self.args)
+        return self
+
+    def __exit__(self, *exc):
+        set_scheme()
+        return False
+
+
+def gminmod(a, b, theta):
+    """Generalized minmod slope: sign(a) min(theta|a|, |a+b|/2, theta|b|) if ab>0."""
+    return lib().or_gminmod(a, b, theta)
+
+
+def albada(a, b):
+    """van Albada-type slope: ab(a+b)/(a^2+b^2) if ab>0."""
+    return lib().or_albada(a, b)
+
+
+def vl_gminmod(a, b, theta):
+    """Hybrid slope: the smaller of the van Leer-type and generalized minmod."""
+    return lib().or_vl_gminmod(a, b, theta)
+
+
+def slope(a, b):
+    """The slope of the selected limiter."""
+    return lib().or_slope(a, b)
+
+
+def hlle(UL, UR, d, gamma):
+    """HLLE flux (Einfeldt 1991) through a face normal to d."""
+    UL, UR = _vec(UL), _vec(UR)
+    F = np.empty(5)
+    lib().or_hlle(_ptr(UL), _ptr(UR), d, gamma, _ptr(F))
+    return F
 
 
 def hllc(UL, UR, d, gamma):

@@ -25,6 +25,19 @@
  *   - conservative update U^{n+1} = U^n - (dt/dh) sum_d (F_{i+1/2}-F_{i-1/2}).
  * Time step: Eq. (CFL2), dt = C_CFL dh / max(|vx|+|vy|+|vz|+3 c_s).
  *
+ * Section 2.2 also lists the other slope limiters and Riemann solvers GAMER
+ * offers (generalized minmod, van Albada-type, a hybrid of the generalized
+ * minmod and van Leer-type limiters; HLLE after Einfeldt 1991), again
+ * deferring their definitions to Toro (2009).  With a = W_i - W_{i-1},
+ * b = W_{i+1} - W_i (every limiter gives 0 unless ab > 0):
+ *   - generalized minmod, coefficient theta in [1,2]:
+ *     sign(a) min(theta|a|, |a+b|/2, theta|b|);
+ *   - van Albada-type: ab(a+b)/(a^2+b^2);
+ *   - hybrid: sign(a) min(|vL(a,b)|, |generalized minmod(a,b)|);
+ *   - HLLE: the HLLC outer speeds S_L, S_R above, F_L if S_L>=0, F_R if
+ *     S_R<=0, else (S_R F_L - S_L F_R + S_L S_R (U_R - U_L))/(S_R - S_L).
+ * or_set_scheme selects them; the default is van Leer-type + HLLC.
+ *
  * Every per-cell loop is independent, so the OpenMP static split changes no
  * result: the oracle is bitwise reproducible for any thread count (the
  * paper's section 2.7.1 property).
@@ -93,6 +106,56 @@ double or_vanleer(double a, double b) {
     return ab > 0.0 ? 2.0 * ab / (a + b) : 0.0;
 }
 
+/* ---- scheme selection (section 2.2: limiters and Riemann solvers) ------- */
+
+/* limiter: 0 van Leer-type, 1 generalized minmod, 2 van Albada-type,
+ * 3 hybrid generalized minmod / van Leer-type; riemann: 0 HLLC, 1 HLLE;
+ * theta: the generalized minmod coefficient. */
+static int or_limiter_id = 0, or_riemann_id = 0;
+static double or_theta = 1.5;
+
+void or_set_scheme(int limiter, int riemann, double theta) {
+    or_limiter_id = limiter;
+    or_riemann_id = riemann;
+    or_theta = theta;
+}
+
+/* generalized minmod: sign(a) min(theta|a|, |a+b|/2, theta|b|) if ab > 0 */
+double or_gminmod(double a, double b, double theta) {
+    if (!(a * b > 0.0)) return 0.0;
+    double m = theta * fabs(a);
+    double t = theta * fabs(b);
+    if (t < m) m = t;
+    t = 0.5 * fabs(a + b);
+    if (t < m) m = t;
+    return a > 0.0 ? m : -m;
+}
+
+/* van Albada-type: ab(a+b)/(a^2+b^2) if ab > 0 */
+double or_albada(double a, double b) {
+    double ab = a * b;
+    return ab > 0.0 ? ab * (a + b) / (a * a + b * b) : 0.0;
+}
+
+/* hybrid: the smaller in magnitude of the van Leer-type and generalized
+ * minmod slopes (both carry the sign of a when ab > 0) */
+double or_vl_gminmod(double a, double b, double theta) {
+    if (!(a * b > 0.0)) return 0.0;
+    double v = fabs(or_vanleer(a, b)), m = fabs(or_gminmod(a, b, theta));
+    if (v < m) m = v;
+    return a > 0.0 ? m : -m;
+}
+
+/* the selected limiter */
+double or_slope(double a, double b) {
+    switch (or_limiter_id) {
+        case 1: return or_gminmod(a, b, or_theta);
+        case 2: return or_albada(a, b);
+        case 3: return or_vl_gminmod(a, b, or_theta);
+        default: return or_vanleer(a, b);
+    }
+}
+
 /* ---- HLLC Riemann solver (section 2.2; Toro 2009 ch. 10 form) ---------- */
 
 /* Flux across a face normal to direction d, left state UL, right state UR. */
@@ -144,6 +207,48 @@ void or_hllc(const double *UL, const double *UR, int d, double gamma, double *F)
     Us[1 + d] = fac * Ss;
     Us[4] = fac * (UK[4] / rK + (Ss - uK) * (Ss + pK / (rK * (SK - uK))));
     for (int v = 0; v < NV; v++) F[v] = FK[v] + SK * (Us[v] - UK[v]);
+}
+
+/* ---- HLLE Riemann solver (section 2.2; Einfeldt 1991) ------------------ */
+
+/* Flux across a face normal to d with the HLLC solver's outer wave speeds. */
+void or_hlle(const double *UL, const double *UR, int d, double gamma, double *F) {
+    double WL[NV], WR[NV], FL[NV], FR[NV];
+    or_prim(UL, WL, gamma);
+    or_prim(UR, WR, gamma);
+    or_flux(UL, d, gamma, FL);
+    or_flux(UR, d, gamma, FR);
+    double rl = WL[0], pl = WL[4], ul = WL[1 + d];
+    double rr = WR[0], pr = WR[4], ur = WR[1 + d];
+    double cl = sound_speed(WL, gamma), cr = sound_speed(WR, gamma);
+    double sl = sqrt(rl), sr = sqrt(rr);
+    double vt[3];
+    for (int k = 0; k < 3; k++) vt[k] = (sl * WL[1 + k] + sr * WR[1 + k]) / (sl + sr);
+    double hl = (UL[4] + pl) / rl, hr = (UR[4] + pr) / rr;
+    double ht = (sl * hl + sr * hr) / (sl + sr);
+    double ct = sqrt((gamma - 1.0) * (ht - 0.5 * (vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2])));
+    double a = ul - cl, b = vt[d] - ct;
+    double SL = (a <= b) ? a : b;
+    a = ur + cr;
+    b = vt[d] + ct;
+    double SR = (a >= b) ? a : b;
+    if (SL >= 0.0) {
+        for (int v = 0; v < NV; v++) F[v] = FL[v];
+        return;
+    }
+    if (SR <= 0.0) {
+        for (int v = 0; v < NV; v++) F[v] = FR[v];
+        return;
+    }
+    for (int v = 0; v < NV; v++) F[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (UR[v] - UL[v])) / (SR - SL);
+}
+
+/* the selected Riemann solver */
+void or_riemann(const double *UL, const double *UR, int d, double gamma, double *F) {
+    if (or_riemann_id == 1)
+        or_hlle(UL, UR, d, gamma, F);
+    else
+        or_hllc(UL, UR, d, gamma, F);
 }
 
 /* ---- time step, Eq. (CFL2) --------------------------------------------- */
@@ -227,7 +332,7 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
                     int64_t im = cell_index(cm[0], cm[1], cm[2], nx, ny);
                     int64_t ip = cell_index(cp[0], cp[1], cp[2], nx, ny);
                     for (int v = 0; v < NV; v++) {
-                        double slope = or_vanleer(w[v] - W[v * n + im], W[v * n + ip] - w[v]);
+                        double slope = or_slope(w[v] - W[v * n + im], W[v * n + ip] - w[v]);
                         Wf[2 * d][v] = w[v] - 0.5 * slope;
                         Wf[2 * d + 1][v] = w[v] + 0.5 * slope;
                     }
@@ -245,7 +350,7 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
                         FS[((int64_t)f * NV + v) * n + i] = Uf[f][v] + 0.5 * dt / dh * inc[v];
             }
 
-    /* 4. HLLC at every face i+1/2: left = high face state of cell i,
+    /* 4. Riemann solver (HLLC or HLLE) at every face i+1/2: left = high face state of cell i,
      *    right = low face state of cell i+1 */
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < nz; z++)
@@ -262,7 +367,7 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
                         UL[v] = FS[((int64_t)(2 * d + 1) * NV + v) * n + i];
                         UR[v] = FS[((int64_t)(2 * d) * NV + v) * n + ip];
                     }
-                    or_hllc(UL, UR, d, gamma, F);
+                    or_riemann(UL, UR, d, gamma, F);
                     for (int v = 0; v < NV; v++) FX[((int64_t)d * NV + v) * n + i] = F[v];
                 }
             }

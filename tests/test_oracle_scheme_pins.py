@@ -1,0 +1,203 @@
+"""Pins of the oracle's other slope limiters and of the HLLE solver (section
+2.2 lists them; definitions from Toro 2009 and Einfeldt 1991), against facts
+the mathematics fixes -- never against the oracle itself:
+
+  * limiters: hand-evaluated values, zero at extrema, exact on linear data,
+    symmetry and oddness, Sweby's TVD region 0 <= phi(r) <= min(2r, 2), the
+    generalized minmod at theta = 1 being the classical minmod, and the
+    hybrid equal to the classical minmod at theta = 1 and to the van
+    Leer-type limiter at theta = 2 (the latter never exceeds the MC bound);
+  * HLLE: consistency F(U,U) = F(U), exact upwinding of supersonic states,
+    mirror antisymmetry, and the diffusion of a stationary contact that HLLC
+    resolves exactly;
+  * every scheme: uniform states unchanged to the bit, conservation to
+    round-off, mirror symmetry, Sod converging to the exact solution, second
+    order on a smooth wave, and the diffusion ordering the definitions imply
+    (minmod > generalized minmod 1.5 > MC; HLLE > HLLC on a contact).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1712_07070_b300 import ics
+from test_oracle_pins import G53, random_state, rel_l1, run_to_time, wave_error
+
+LIMS = [oracle.LIM_VANLEER, oracle.LIM_GMINMOD, oracle.LIM_ALBADA, oracle.LIM_VL_GMINMOD]
+
+
+def lim_fn(lim, theta=1.5):
+    return {
+        oracle.LIM_VANLEER: lambda a, b: oracle.vanleer(a, b),
+        oracle.LIM_GMINMOD: lambda a, b: oracle.gminmod(a, b, theta),
+        oracle.LIM_ALBADA: lambda a, b: oracle.albada(a, b),
+        oracle.LIM_VL_GMINMOD: lambda a, b: oracle.vl_gminmod(a, b, theta),
+    }[lim]
+
+
+# ---- limiters ------------------------------------------------------------------
+
+def test_limiter_hand_values():
+    # a = 1, b = 3: vL 2*3/4, minmod family min(theta, 2, 3theta), albada 3*4/10
+    assert oracle.gminmod(1.0, 3.0, 1.0) == 1.0
+    assert oracle.gminmod(1.0, 3.0, 1.5) == 1.5
+    assert oracle.gminmod(1.0, 3.0, 2.0) == 2.0
+    assert oracle.albada(1.0, 3.0) == pytest.approx(1.2, rel=1e-15)
+    assert oracle.vl_gminmod(1.0, 3.0, 1.0) == 1.0   # min(1.5, 1)
+    assert oracle.vl_gminmod(1.0, 3.0, 1.5) == 1.5   # min(1.5, 1.5)
+    # a = 4, b = 1: the central difference 2.5 binds MC, theta|b| binds 1.5
+    assert oracle.gminmod(4.0, 1.0, 2.0) == 2.0
+    assert oracle.gminmod(4.0, 1.0, 1.5) == 1.5
+    # a = -1, b = -10
+    assert oracle.gminmod(-1.0, -10.0, 1.5) == -1.5
+    assert oracle.albada(-1.0, -10.0) == pytest.approx(-110.0 / 101.0, rel=1e-15)
+    assert oracle.vl_gminmod(-1.0, -10.0, 2.0) == pytest.approx(-20.0 / 11.0, rel=1e-15)
+
+
+@pytest.mark.parametrize("lim", LIMS)
+def test_limiter_extrema_linear_symmetry(lim):
+    f = lim_fn(lim)
+    for a, b in [(1.0, -1.0), (0.0, 5.0), (5.0, 0.0), (-1.0, 2.0), (0.0, 0.0)]:
+        assert f(a, b) == 0.0
+    for a in (1.0, -2.0, 0.3, 7e-9):
+        assert f(a, a) == pytest.approx(a, rel=1e-15)
+    rng = np.random.default_rng(4)
+    for _ in range(200):
+        a, b = rng.normal(size=2) * 10.0 ** rng.uniform(-3, 3, 2)
+        assert f(a, b) == f(b, a)
+        assert f(-a, -b) == -f(a, b)
+
+
+@pytest.mark.parametrize("lim", LIMS)
+@pytest.mark.parametrize("theta", [1.0, 1.5, 2.0])
+def test_limiter_in_tvd_region(lim, theta):
+    f = lim_fn(lim, theta)
+    for r in np.concatenate([np.linspace(1e-3, 5.0, 500), [10.0, 50.0, 1e3]]):
+        phi = f(1.0, r)
+        assert 0.0 <= phi <= min(2.0 * r, 2.0) * (1 + 1e-15), (r, phi)
+
+
+def test_minmod_and_hybrid_identities():
+    rng = np.random.default_rng(5)
+    for _ in range(500):
+        a, b = rng.normal(size=2) * 10.0 ** rng.uniform(-3, 3, 2)
+        mm = np.sign(a) * min(abs(a), abs(b)) if a * b > 0 else 0.0
+        assert oracle.gminmod(a, b, 1.0) == mm
+        assert oracle.vl_gminmod(a, b, 1.0) == mm
+        assert oracle.vl_gminmod(a, b, 2.0) == oracle.vanleer(a, b)
+
+
+def test_hybrid_steps_equal_minmod_and_vanleer():
+    # the identities above, through whole steps of the scheme (bitwise)
+    U = ics.sod_noise(16, seed=9, gamma=G53)
+    with oracle.scheme(oracle.LIM_VL_GMINMOD, theta=2.0):
+        A, _ = oracle.run_periodic(U, 1.0 / 16, G53, 0.5, 2)
+    with oracle.scheme(oracle.LIM_VANLEER):
+        B, _ = oracle.run_periodic(U, 1.0 / 16, G53, 0.5, 2)
+    assert np.array_equal(A, B)
+    with oracle.scheme(oracle.LIM_VL_GMINMOD, theta=1.0):
+        A, _ = oracle.run_periodic(U, 1.0 / 16, G53, 0.5, 2)
+    with oracle.scheme(oracle.LIM_GMINMOD, theta=1.0):
+        B, _ = oracle.run_periodic(U, 1.0 / 16, G53, 0.5, 2)
+    assert np.array_equal(A, B)
+
+
+# ---- HLLE ------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_hlle_consistency_and_upwinding(d):
+    rng = np.random.default_rng(30 + d)
+    for _ in range(50):
+        U = random_state(rng, G53)
+        assert np.allclose(oracle.hlle(U, U, d, G53), oracle.flux(U, d, G53), rtol=1e-14, atol=1e-14)
+    for sign in (+1, -1):
+        WL = np.array([1.0, 0.1, -0.2, 0.3, 1.0])
+        WR = np.array([0.5, 0.2, 0.1, -0.1, 0.6])
+        WL[1 + d] = WR[1 + d] = sign * 6.0
+        UL, UR = oracle.cons(WL, G53), oracle.cons(WR, G53)
+        up = UL if sign > 0 else UR
+        assert np.array_equal(oracle.hlle(UL, UR, d, G53), oracle.flux(up, d, G53))
+
+
+def test_hlle_mirror_antisymmetry():
+    rng = np.random.default_rng(6)
+    M = np.array([1, -1, 1, 1, 1.0])
+    for _ in range(50):
+        UL, UR = random_state(rng, G53), random_state(rng, G53)
+        F = oracle.hlle(UL, UR, 0, G53)
+        Fm = oracle.hlle(UR * M, UL * M, 0, G53)
+        assert np.allclose(Fm, -F * M, rtol=1e-13, atol=1e-14)
+
+
+def test_hlle_diffuses_a_stationary_contact():
+    # HLLC resolves it exactly; HLLE's single intermediate state smears it.
+    # At rest with equal pressure F_L = F_R = (0, P, 0, 0, 0) and
+    # E_L = E_R, so the HLLE formula gives mass flux
+    # -S_L S_R (rho_R - rho_L)/(S_R - S_L) > 0 (down the density jump, since
+    # S_L < 0 < S_R), normal-momentum flux P exactly and no energy flux.
+    WL, WR = [1.0, 0.0, 0.0, 0.0, 0.8], [0.1, 0.0, 0.0, 0.0, 0.8]
+    UL, UR = oracle.cons(WL, G53), oracle.cons(WR, G53)
+    Fc = oracle.hllc(UL, UR, 0, G53)
+    Fe = oracle.hlle(UL, UR, 0, G53)
+    assert Fc[0] == 0.0
+    assert Fe[0] > 1e-3
+    assert Fe[1] == pytest.approx(0.8, rel=1e-15) and Fe[4] == 0.0
+
+
+# ---- whole steps of every scheme ----------------------------------------------------
+
+SCHEMES = [(oracle.LIM_VANLEER, oracle.RS_HLLE, 1.5), (oracle.LIM_GMINMOD, oracle.RS_HLLC, 1.5),
+           (oracle.LIM_GMINMOD, oracle.RS_HLLE, 2.0), (oracle.LIM_ALBADA, oracle.RS_HLLC, 1.5),
+           (oracle.LIM_VL_GMINMOD, oracle.RS_HLLC, 1.5)]
+
+
+@pytest.mark.parametrize("lim,rs,theta", SCHEMES)
+def test_scheme_invariants(lim, rs, theta):
+    with oracle.scheme(lim, rs, theta):
+        U = ics.uniform_state(8, gamma=G53)
+        U1, _ = oracle.run_periodic(U, 1.0 / 8, G53, 0.5, 3)
+        assert np.array_equal(U1, U)
+        U = ics.sod_noise(16, seed=2, gamma=G53)
+        s0 = oracle.conserved_sum(U, 1.0 / 16 ** 3)
+        U1, _ = oracle.run_periodic(U, 1.0 / 16, G53, 0.5, 3)
+        s1 = oracle.conserved_sum(U1, 1.0 / 16 ** 3)
+        scale = np.abs(U).sum(axis=(1, 2, 3)) / 16 ** 3
+        assert np.all(np.abs(s1 - s0) <= 1e-14 * 4 * scale)
+        M = np.array([1, -1, 1, 1, 1.0])[:, None, None, None]
+        Um = (U * M)[:, :, :, ::-1].copy()
+        B, _ = oracle.run_periodic(Um, 1.0 / 16, G53, 0.5, 3)
+        Bm = (B * M)[:, :, :, ::-1]
+        for v in range(5):
+            assert rel_l1(Bm[v], U1[v]) <= 1e-14 or np.abs(Bm[v] - U1[v]).max() < 1e-14
+
+
+def sod_error(n, g=G53, t=0.1):
+    L, R = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+    U = ics.riemann_tube(n, L, R, axis=0, gamma=g)
+    U = run_to_time(U, 1.0 / n, g, 0.5, t)
+    x = ics.centres(n)
+    sel = (x > 0.25) & (x < 0.75)
+    r, _, _ = oracle.exact_sample(L, R, g, (x[sel] - 0.5) / t)
+    return np.abs(U[0, 0, 0, sel] - r).mean() * 0.5
+
+
+@pytest.mark.parametrize("lim,rs,theta", SCHEMES)
+def test_scheme_sod_and_smooth_wave(lim, rs, theta):
+    with oracle.scheme(lim, rs, theta):
+        e = [sod_error(n) for n in (64, 128)]
+        assert e[0] > e[1] and e[1] < 7e-3, e
+        w = [wave_error(n, (1, 0, 0), 0.25) for n in (32, 64, 128)]
+    order = np.log2(w[0] / w[2]) / 2
+    assert order >= 1.75, w
+
+
+def test_diffusion_ordering():
+    errs = {}
+    for key, args in {"minmod": (oracle.LIM_GMINMOD, oracle.RS_HLLC, 1.0),
+                      "gmm15": (oracle.LIM_GMINMOD, oracle.RS_HLLC, 1.5),
+                      "mc": (oracle.LIM_GMINMOD, oracle.RS_HLLC, 2.0),
+                      "vl_hllc": (oracle.LIM_VANLEER, oracle.RS_HLLC, 1.5),
+                      "vl_hlle": (oracle.LIM_VANLEER, oracle.RS_HLLE, 1.5)}.items():
+        with oracle.scheme(*args):
+            errs[key] = sod_error(128)
+    assert errs["minmod"] > errs["gmm15"] > errs["mc"], errs
+    assert errs["vl_hlle"] > errs["vl_hllc"], errs
