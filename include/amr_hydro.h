@@ -55,6 +55,23 @@ typedef enum {
                            dt and conservation reductions in FP64 */
 } amr_precision;
 
+/* Slope limiter of the piecewise-linear reconstruction (section 2.2 lists
+ * these; definitions after Toro 2009).  With a = W_i - W_{i-1} and
+ * b = W_{i+1} - W_i per primitive component, every limiter is 0 unless ab > 0. */
+typedef enum {
+    AMR_LIM_VANLEER = 0,    /* van Leer-type 2ab/(a+b) (the default) */
+    AMR_LIM_GMINMOD = 1,    /* generalized minmod sign(a) min(t|a|, |a+b|/2, t|b|), t = minmod_coeff */
+    AMR_LIM_ALBADA = 2,     /* van Albada-type ab(a+b)/(a^2+b^2) */
+    AMR_LIM_VL_GMINMOD = 3  /* hybrid: the smaller in magnitude of the van Leer-type and
+                               generalized minmod slopes */
+} amr_limiter;
+
+/* Riemann solver at every cell face (section 2.2). */
+typedef enum {
+    AMR_RS_HLLC = 0,  /* HLLC, Einfeldt/Roe outer speeds (the default) */
+    AMR_RS_HLLE = 1   /* HLLE (Einfeldt 1991) with the same outer speeds */
+} amr_riemann;
+
 /* Run parameters (section 2.1 and 2.6 symbols). */
 typedef struct {
     double gamma;        /* adiabatic index */
@@ -68,6 +85,9 @@ typedef struct {
     double box[3];       /* domain edge lengths; cells are cubic */
     int root_n[3];       /* root-level cells per dimension, multiples of 16 */
     int max_patches;     /* slot capacity per level, a multiple of 8 */
+    int limiter;         /* amr_limiter (0: van Leer-type) */
+    int riemann;         /* amr_riemann (0: HLLC) */
+    double minmod_coeff; /* generalized minmod coefficient in [1, 2]; 0 means 1.5 */
 } amr_hydro_params;
 
 typedef struct amr_hydro_ctx amr_hydro_ctx; /* opaque, library-owned */

@@ -12,7 +12,7 @@ from . import amr_hydro as A
 
 class AmrHierarchy:
     def __init__(self, U_root, lmax, gamma=5.0 / 3.0, cfl=0.5, theta=0.05, nbuf=(8, 4), prec=A.AMR_FP64,
-                 max_patches=None, c_inc=0.1, c_dec=0.1, stream=None, device="cuda", regrid_at_start=True):
+                 max_patches=None, c_inc=0.1, c_dec=0.1, stream=None, device="cuda", regrid_at_start=True, scheme=None):
         _, nz, ny, nx = U_root.shape
         self.root = (nx, ny, nz)
         self.lmax = lmax
@@ -21,7 +21,7 @@ class AmrHierarchy:
         n0 = (nx // 8) * (ny // 8) * (nz // 8)
         if max_patches is None:
             max_patches = 8 * n0
-        p = A.make_params(gamma=gamma, cfl=cfl, root_n=(nx, ny, nz), lmax=lmax, prec=prec,
+        p = A.make_params(gamma=gamma, cfl=cfl, root_n=(nx, ny, nz), lmax=lmax, prec=prec, **(scheme or {}),
                           max_patches=max(max_patches, n0), theta=theta, c_inc=c_inc, c_dec=c_dec,
                           nbuf=list(nbuf))
         self.ctx = A.amr_hydro_init(p, stream)

@@ -15,6 +15,8 @@ LIB_PATH = os.path.join(_PKG, "libamr_hydro.so")
 
 AMR_OK, AMR_E_INVAL, AMR_E_NOMEM, AMR_E_CUDA, AMR_E_UNPHYSICAL, AMR_E_TIMEOUT, AMR_E_NESTING = range(7)
 AMR_FP64, AMR_FP32_ACC64 = 0, 1
+AMR_LIM_VANLEER, AMR_LIM_GMINMOD, AMR_LIM_ALBADA, AMR_LIM_VL_GMINMOD = 0, 1, 2, 3
+AMR_RS_HLLC, AMR_RS_HLLE = 0, 1
 
 # every symbol include/amr_hydro.h declares
 SYMBOLS = (
@@ -36,6 +38,7 @@ class amr_hydro_params(ctypes.Structure):
         ("c_dec", ctypes.c_double), ("theta", ctypes.c_double), ("lmax", ctypes.c_int),
         ("nbuf", ctypes.c_int * 8), ("prec", ctypes.c_int), ("periodic", ctypes.c_int * 3),
         ("box", ctypes.c_double * 3), ("root_n", ctypes.c_int * 3), ("max_patches", ctypes.c_int),
+        ("limiter", ctypes.c_int), ("riemann", ctypes.c_int), ("minmod_coeff", ctypes.c_double),
     ]
 
 
@@ -279,8 +282,10 @@ def amr_hydro_level_info(ctx, level):
 
 
 def make_params(gamma=5.0 / 3.0, cfl=0.5, root_n=(64, 64, 64), box=None, lmax=0,
-                prec=AMR_FP64, max_patches=None, theta=0.05, c_inc=0.1, c_dec=0.1, nbuf=None):
+                prec=AMR_FP64, max_patches=None, theta=0.05, c_inc=0.1, c_dec=0.1, nbuf=None,
+                limiter=AMR_LIM_VANLEER, riemann=AMR_RS_HLLC, minmod_coeff=1.5):
     p = amr_hydro_params()
+    p.limiter, p.riemann, p.minmod_coeff = limiter, riemann, minmod_coeff
     p.gamma, p.cfl, p.c_inc, p.c_dec, p.theta = gamma, cfl, c_inc, c_dec, theta
     p.lmax = lmax
     nb = nbuf if nbuf is not None else [8] * 8

@@ -7,8 +7,8 @@ from . import amr_hydro as A
 
 
 class BoxBatch:
-    def __init__(self, gamma=1.4, cfl=0.5, prec=A.AMR_FP32_ACC64, stream=None, device="cuda"):
-        p = A.make_params(gamma=gamma, cfl=cfl, root_n=(16, 16, 16), prec=prec)
+    def __init__(self, gamma=1.4, cfl=0.5, prec=A.AMR_FP32_ACC64, stream=None, device="cuda", scheme=None):
+        p = A.make_params(gamma=gamma, cfl=cfl, root_n=(16, 16, 16), prec=prec, **(scheme or {}))
         self.ctx = A.amr_hydro_init(p, stream)
         self.stream = stream
         self.device = torch.device(device)

@@ -66,41 +66,52 @@ size_t step_smem_bytes(int prec) {
     return prec == AMR_FP64 ? sizeof(StepSmem<double>) : sizeof(StepSmem<float>);
 }
 
+template <typename real, bool GEN>
+static amr_status set_step_smem() {
+    return cuda_fail(cudaFuncSetAttribute(k_hydro_step<real, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sizeof(StepSmem<real>)),
+                     "step kernel smem attribute");
+}
+
 amr_status configure_kernels() {
     static bool done = false;
     if (done) return AMR_OK;
-    amr_status st = cuda_fail(cudaFuncSetAttribute(k_hydro_step<double>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)sizeof(StepSmem<double>)),
-                              "smem attr fp64");
-    if (st) return st;
-    st = cuda_fail(cudaFuncSetAttribute(k_hydro_step<float>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)sizeof(StepSmem<float>)),
-                   "smem attr fp32");
-    if (st) return st;
+    amr_status st;
+    if ((st = set_step_smem<double, false>()) || (st = set_step_smem<double, true>()) ||
+        (st = set_step_smem<float, false>()) || (st = set_step_smem<float, true>()))
+        return st;
     done = true;
     return AMR_OK;
 }
 
-// Number of resident step CTAs per SM, for sizing a persistent grid.
-int step_blocks_per_sm(int prec) {
-    int n = 0;
-    if (prec == AMR_FP64)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hydro_step<double>, StepCfg<double>::NT,
-                                                      sizeof(StepSmem<double>));
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hydro_step<float>, StepCfg<float>::NT,
-                                                      sizeof(StepSmem<float>));
+template <typename real>
+static int step_occupancy() {
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_hydro_step<real, false>, StepCfg<real>::NT,
+                                                  sizeof(StepSmem<real>));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_hydro_step<real, true>, StepCfg<real>::NT,
+                                                  sizeof(StepSmem<real>));
+    const int n = a < b ? a : b;
     return n > 0 ? n : 1;
+}
+
+// Number of resident step CTAs per SM, for sizing a persistent grid.
+int step_blocks_per_sm(int prec) { return prec == AMR_FP64 ? step_occupancy<double>() : step_occupancy<float>(); }
+
+template <typename real>
+static void launch_step_k(const StepParams &P, int grid, cudaStream_t s) {
+    if (P.limiter != LIM_VANLEER || P.riemann != RS_HLLC)
+        k_hydro_step<real, true><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(P);
+    else
+        k_hydro_step<real, false><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(P);
 }
 
 amr_status launch_step(amr_hydro_ctx *c, const StepParams &P, int grid) {
     if (P.n_work == 0) return AMR_OK;
     if (c->prm.prec == AMR_FP64)
-        k_hydro_step<double><<<grid, StepCfg<double>::NT, sizeof(StepSmem<double>), c->stream>>>(P);
+        launch_step_k<double>(P, grid, c->stream);
     else
-        k_hydro_step<float><<<grid, StepCfg<float>::NT, sizeof(StepSmem<float>), c->stream>>>(P);
+        launch_step_k<float>(P, grid, c->stream);
     return cuda_fail(cudaGetLastError(), "k_hydro_step launch");
 }
 
@@ -117,9 +128,9 @@ amr_status launch_step_raw(int prec, const StepParams &P, cudaStream_t stream) {
     const int cap = n_sm * step_blocks_per_sm(prec);
     const int grid = P.n_work < cap ? P.n_work : cap;
     if (prec == AMR_FP64)
-        k_hydro_step<double><<<grid, StepCfg<double>::NT, sizeof(StepSmem<double>), stream>>>(P);
+        launch_step_k<double>(P, grid, stream);
     else
-        k_hydro_step<float><<<grid, StepCfg<float>::NT, sizeof(StepSmem<float>), stream>>>(P);
+        launch_step_k<float>(P, grid, stream);
     return cuda_fail(cudaGetLastError(), "k_hydro_step launch");
 }
 
@@ -201,6 +212,9 @@ amr_status amr_hydro_init(const amr_hydro_params *p, void *stream, amr_hydro_ctx
     if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || p->lmax < 0 || p->lmax > 7) return AMR_E_INVAL;
     if (p->prec != AMR_FP64 && p->prec != AMR_FP32_ACC64) return AMR_E_INVAL;
     if (p->max_patches <= 0 || p->max_patches % 8) return AMR_E_INVAL;
+    if (p->limiter < AMR_LIM_VANLEER || p->limiter > AMR_LIM_VL_GMINMOD) return AMR_E_INVAL;
+    if (p->riemann != AMR_RS_HLLC && p->riemann != AMR_RS_HLLE) return AMR_E_INVAL;
+    if (p->minmod_coeff != 0.0 && !(p->minmod_coeff >= 1.0 && p->minmod_coeff <= 2.0)) return AMR_E_INVAL;
     for (int d = 0; d < 3; d++) {
         if (p->root_n[d] <= 0 || p->root_n[d] % 16) return AMR_E_INVAL;
         if (!p->periodic[d]) return AMR_E_INVAL;
@@ -215,6 +229,7 @@ amr_status amr_hydro_init(const amr_hydro_params *p, void *stream, amr_hydro_ctx
     amr_hydro_ctx *c = new (std::nothrow) amr_hydro_ctx();
     if (!c) return AMR_E_NOMEM;
     c->prm = *p;
+    if (c->prm.minmod_coeff == 0.0) c->prm.minmod_coeff = 1.5;
     c->stream = (cudaStream_t)stream;
     cudaGetDevice(&c->device);
     cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);

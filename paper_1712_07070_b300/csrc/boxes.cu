@@ -25,34 +25,49 @@ namespace {
 
 bool configured = false;
 
+template <typename real, bool GEN>
+amr_status set_box_smem() {
+    return cuda_fail(cudaFuncSetAttribute(k_hydro_step_boxes<real, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sizeof(StepSmem<real>)),
+                     "box kernel smem attribute");
+}
+
 amr_status configure_box_kernels() {
     if (configured) return AMR_OK;
-    amr_status st = cuda_fail(cudaFuncSetAttribute(k_hydro_step_boxes<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)sizeof(StepSmem<double>)), "smem attr");
-    if (st) return st;
-    st = cuda_fail(cudaFuncSetAttribute(k_hydro_step_boxes<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)sizeof(StepSmem<float>)), "smem attr");
-    if (st) return st;
+    amr_status st;
+    if ((st = set_box_smem<double, false>()) || (st = set_box_smem<double, true>()) ||
+        (st = set_box_smem<float, false>()) || (st = set_box_smem<float, true>()))
+        return st;
     configured = true;
     return AMR_OK;
 }
 
-int resident_per_sm(int prec) {
-    int n = 0;
-    if (prec == AMR_FP64)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hydro_step_boxes<double>, StepCfg<double>::NT,
-                                                      sizeof(StepSmem<double>));
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hydro_step_boxes<float>, StepCfg<float>::NT,
-                                                      sizeof(StepSmem<float>));
+template <typename real>
+int box_occupancy() {
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_hydro_step_boxes<real, false>, StepCfg<real>::NT,
+                                                  sizeof(StepSmem<real>));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_hydro_step_boxes<real, true>, StepCfg<real>::NT,
+                                                  sizeof(StepSmem<real>));
+    const int n = a < b ? a : b;
     return n > 0 ? n : 1;
+}
+
+int resident_per_sm(int prec) { return prec == AMR_FP64 ? box_occupancy<double>() : box_occupancy<float>(); }
+
+template <typename real>
+void launch_boxes_k(const BoxLaunch &B, int grid, cudaStream_t s) {
+    if (B.limiter != LIM_VANLEER || B.riemann != RS_HLLC)
+        k_hydro_step_boxes<real, true><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(B);
+    else
+        k_hydro_step_boxes<real, false><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(B);
 }
 
 amr_status launch_boxes(amr_hydro_ctx *c, const BoxLaunch &B, int grid, cudaStream_t s) {
     if (c->prm.prec == AMR_FP64)
-        k_hydro_step_boxes<double><<<grid, StepCfg<double>::NT, sizeof(StepSmem<double>), s>>>(B);
+        launch_boxes_k<double>(B, grid, s);
     else
-        k_hydro_step_boxes<float><<<grid, StepCfg<float>::NT, sizeof(StepSmem<float>), s>>>(B);
+        launch_boxes_k<float>(B, grid, s);
     return cuda_fail(cudaGetLastError(), "k_hydro_step_boxes");
 }
 
@@ -193,6 +208,9 @@ amr_status amr_hydro_advance_boxes(amr_hydro_ctx *c, int n_boxes, const int *box
     L.desc = (const BoxDesc *)c->box_desc.p;
     L.cfl = c->prm.cfl;
     L.gamma = c->prm.gamma;
+    L.limiter = c->prm.limiter;
+    L.riemann = c->prm.riemann;
+    L.theta = c->prm.minmod_coeff;
     L.n_boxes = n_boxes;
 
     // autotune the launch shape once per box set

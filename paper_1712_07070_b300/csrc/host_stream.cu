@@ -117,6 +117,9 @@ extern "C" amr_status amr_hydro_advance_host(amr_hydro_ctx *c, const double *U_i
     P.cfl = c->prm.cfl;
     P.dh = level_dh(c, 0);
     P.gamma = c->prm.gamma;
+    P.limiter = c->prm.limiter;
+    P.riemann = c->prm.riemann;
+    P.theta = c->prm.minmod_coeff;
     P.smax_out = sc + r_out;
     P.n_bad = sc + 3 + r_out;
     P.clear2 = sc + r_clr;  // idempotent: every slab launch zeroes the same two slots

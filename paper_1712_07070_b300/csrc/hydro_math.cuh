@@ -125,10 +125,28 @@ __device__ __forceinline__ bool ge0(float x) { return x >= 0.0f; }
 __device__ __forceinline__ float min_(float a, float b) { return (a <= b) ? a : b; }
 __device__ __forceinline__ float max_(float a, float b) { return (a >= b) ? a : b; }
 
+// Scheme options (amr_limiter / amr_riemann of the C ABI).
+constexpr int LIM_VANLEER = 0, LIM_GMINMOD = 1, LIM_ALBADA = 2, LIM_VL_GMINMOD = 3;
+constexpr int RS_HLLC = 0, RS_HLLE = 1;
+
 template <typename real>
 struct Gas {
     real gamma, gm1, inv_gm1;
+    int lim = LIM_VANLEER, rs = RS_HLLC;  // uniform over a launch: the branches on them never diverge
+    real htheta = real(0.75);             // half the generalized minmod coefficient
 };
+
+// |x| and sign transfer on the bit pattern (integer units)
+__device__ __forceinline__ double fabs_(double x) {
+    return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double copysign_(double m, double s) {
+    return __longlong_as_double(__double_as_longlong(m) | (__double_as_longlong(s) & (long long)0x8000000000000000ULL));
+}
+__device__ __forceinline__ float fabs_(float x) { return __int_as_float(__float_as_int(x) & 0x7fffffff); }
+__device__ __forceinline__ float copysign_(float m, float s) {
+    return __int_as_float(__float_as_int(m) | (__float_as_int(s) & (int)0x80000000u));
+}
 
 // U -> W; also returns 1/rho for reuse.
 template <typename real>
@@ -152,11 +170,26 @@ __device__ __forceinline__ void w2u(const real w[NV], real u[NV], const Gas<real
     u[4] = w[4] * g.inv_gm1 + real(0.5) * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
 }
 
-// Half of the van Leer-type limited slope: vL(a,b)/2 = ab/(a+b) if ab>0.
+// Half of the limited slope of the selected limiter, from the one-sided
+// differences a = W_i - W_{i-1}, b = W_{i+1} - W_i (0 unless ab > 0):
+// van Leer-type ab/(a+b); generalized minmod sign(a) min(t|a|, |a+b|/2, t|b|)/2;
+// van Albada-type ab(a+b)/(2(a^2+b^2)); hybrid the smaller in magnitude of
+// the first two.  The selects keep a warp convergent, and the limiter branch
+// is uniform over a launch.
 template <typename real>
-__device__ __forceinline__ real half_vanleer(real a, real b) {
+__device__ __forceinline__ real half_slope(real a, real b, const Gas<real> &g) {
     const real ab = a * b;
-    return gt0(ab) ? ab * rcp_(a + b) : real(0);
+    real h;
+    if (g.lim == LIM_VANLEER) {
+        h = ab * rcp_(a + b);
+    } else if (g.lim == LIM_ALBADA) {
+        h = ab * (a + b) * rcp_(real(2) * (a * a + b * b));
+    } else {
+        real m = min_(min_(g.htheta * fabs_(a), g.htheta * fabs_(b)), real(0.25) * fabs_(a + b));
+        if (g.lim == LIM_VL_GMINMOD) m = min_(m, fabs_(ab * rcp_(a + b)));
+        h = copysign_(m, a);
+    }
+    return gt0(ab) ? h : real(0);
 }
 
 // Physical flux along D of a state known in both forms (w, u).
@@ -171,8 +204,10 @@ __device__ __forceinline__ void phys_flux(const real w[NV], const real u[NV], re
     f[4] = (u[4] + w[4]) * vn;
 }
 
-// HLLC flux through a face normal to D (Einfeldt/Roe outer speeds, Toro's
-// star states; ties: S_L>=0 -> F_L, S_R<=0 -> F_R, S*>=0 -> F*_L).
+// Flux through a face normal to D of the selected Riemann solver: HLLC
+// (Einfeldt/Roe outer speeds, Toro's star states; ties: S_L>=0 -> F_L,
+// S_R<=0 -> F_R, S*>=0 -> F*_L) or HLLE (same outer speeds and ties, one
+// intermediate state).
 // Reciprocals are shared: 1/rho from one reciprocal square root per side,
 // which also gives the Roe weight sqrt(rho).
 template <int D, typename real>
@@ -214,6 +249,15 @@ __device__ __forceinline__ void hllc(const real uL[NV], const real uR[NV], real 
     }
     if (le0(SR)) {
         phys_flux<D>(wR, uR, F);
+        return;
+    }
+    if (g.rs == RS_HLLE) {  // one intermediate state: (S_R F_L - S_L F_R + S_L S_R (U_R - U_L))/(S_R - S_L)
+        real fl[NV], fr[NV];
+        phys_flux<D>(wL, uL, fl);
+        phys_flux<D>(wR, uR, fr);
+        const real ids = rcp_(SR - SL), sls = SL * SR;
+#pragma unroll
+        for (int v = 0; v < NV; v++) F[v] = (SR * fl[v] - SL * fr[v] + sls * (uR[v] - uL[v])) * ids;
         return;
     }
     const real ml = rl * (SL - ul), mr = rr * (SR - ur);  // mass fluxes relative to the waves

@@ -138,6 +138,9 @@ amr_status amr_hydro_advance_level(amr_hydro_ctx *c, int level, double dt, int64
     P.cfl = c->prm.cfl;
     P.dh = level_dh(c, level);
     P.gamma = c->prm.gamma;
+    P.limiter = c->prm.limiter;
+    P.riemann = c->prm.riemann;
+    P.theta = c->prm.minmod_coeff;
     P.smax_out = sc + r_out;
     P.n_bad = sc + 3 + r_out;
     P.clear2 = sc + r_clr;

@@ -65,6 +65,8 @@ struct StepParams {
     double dt;                               // >= 0: time step from the host
     const unsigned long long *smax_in;       // dt < 0: dt = cfl*dh/smax_in
     double cfl, dh, gamma;
+    int limiter, riemann;                    // amr_limiter / amr_riemann
+    double theta;                            // generalized minmod coefficient
     unsigned long long *smax_out;            // max signal speed of the new state (bits)
     unsigned long long *n_bad;               // count of unphysical new cells
     unsigned long long *clear2;              // two scalars the kernel zeroes for the next step
@@ -260,9 +262,9 @@ __device__ __forceinline__ void hancock_cell(const StepSmem<real> &S, int x, int
 #pragma unroll
     for (int v = 0; v < NV; v++) {
         w[v] = S.W[s0][v][Y][X];
-        hs[0][v] = half_vanleer(w[v] - S.W[s0][v][Y][X - 1], S.W[s0][v][Y][X + 1] - w[v]);
-        hs[1][v] = half_vanleer(w[v] - S.W[s0][v][Y - 1][X], S.W[s0][v][Y + 1][X] - w[v]);
-        hs[2][v] = half_vanleer(w[v] - S.W[sm][v][Y][X], S.W[sp][v][Y][X] - w[v]);
+        hs[0][v] = half_slope(w[v] - S.W[s0][v][Y][X - 1], S.W[s0][v][Y][X + 1] - w[v], g);
+        hs[1][v] = half_slope(w[v] - S.W[s0][v][Y - 1][X], S.W[s0][v][Y + 1][X] - w[v], g);
+        hs[2][v] = half_slope(w[v] - S.W[sm][v][Y][X], S.W[sp][v][Y][X] - w[v], g);
     }
     real inc[NV] = {real(0), real(0), real(0), real(0), real(0)};
 #pragma unroll
@@ -509,7 +511,10 @@ __device__ __forceinline__ void step_group(StepSmem<real> &S, const StepParams &
     __syncthreads();  // the next group overwrites nbr and the ring
 }
 
-template <typename real>
+// GEN = false: the default scheme (van Leer-type limiter, HLLC) as
+// compile-time constants, so the scheme branches fold away; GEN = true: the
+// limiter and solver of P (uniform over the launch).
+template <typename real, bool GEN>
 __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydro_step(StepParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<real> &S = *reinterpret_cast<StepSmem<real> *>(smem_raw);
@@ -519,6 +524,11 @@ __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydr
     g.gamma = (real)P.gamma;
     g.gm1 = (real)(P.gamma - 1.0);
     g.inv_gm1 = (real)(1.0 / (P.gamma - 1.0));
+    if constexpr (GEN) {
+        g.lim = P.limiter;
+        g.rs = P.riemann;
+        g.htheta = (real)(0.5 * P.theta);
+    }
 
     if (tid == 0) {
         double dt = P.dt;
@@ -583,12 +593,17 @@ struct BoxLaunch {
     int step;           // step index within this batch: buffers and ring advance with it
     int chunked;        // 1: each CTA takes a contiguous run of items; 0: grid-stride
     double cfl, gamma;
+    int limiter, riemann;  // amr_limiter / amr_riemann
+    double theta;          // generalized minmod coefficient
     double dt_override; // >= 0 (autotuning): fixed dt, no logging
     double *dt_log;     // [steps][n_boxes] or null
     int n_boxes;
 };
 
-template <typename real>
+// GEN = false: the default scheme (van Leer-type limiter, HLLC) as
+// compile-time constants, so the scheme branches fold away; GEN = true: the
+// limiter and solver of B (uniform over the launch).
+template <typename real, bool GEN>
 __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydro_step_boxes(BoxLaunch B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<real> &S = *reinterpret_cast<StepSmem<real> *>(smem_raw);
@@ -597,6 +612,11 @@ __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydr
     g.gamma = (real)B.gamma;
     g.gm1 = (real)(B.gamma - 1.0);
     g.inv_gm1 = (real)(1.0 / (B.gamma - 1.0));
+    if constexpr (GEN) {
+        g.lim = B.limiter;
+        g.rs = B.riemann;
+        g.htheta = (real)(0.5 * B.theta);
+    }
     int first, last, stride;
     if (B.chunked) {
         const int per = (B.n_work + gridDim.x - 1) / gridDim.x;

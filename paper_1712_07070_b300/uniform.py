@@ -13,12 +13,13 @@ class UniformGrid:
     """A periodic nx x ny x nz box (multiples of 16) as one level of 8^3 patches."""
 
     def __init__(self, shape, gamma=5.0 / 3.0, cfl=0.5, prec=A.AMR_FP64, box_x=1.0, stream=None,
-                 device="cuda"):
+                 device="cuda", scheme=None):
+        """scheme: optional dict of make_params' limiter / riemann / minmod_coeff."""
         nx, ny, nz = shape
         self.shape = (nx, ny, nz)
         self.device = torch.device(device)
         self.stream = stream
-        p = A.make_params(gamma=gamma, cfl=cfl, root_n=(nx, ny, nz),
+        p = A.make_params(gamma=gamma, cfl=cfl, root_n=(nx, ny, nz), **(scheme or {}),
                           box=(box_x, box_x * ny / nx, box_x * nz / nx), prec=prec)
         self.params = p
         self.dh = box_x / nx
