@@ -179,8 +179,8 @@ def e2e_steps(torch, grid, stream, host_a, host_b, K, dt):
     return t0.elapsed_time(t1), dt
 
 
-def run_case(torch, A, UniformGrid, U0, n, prec, K, W, stream, want_e2e):
-    g = UniformGrid((n, n, n), prec=prec, stream=stream.cuda_stream)
+def run_case(torch, A, UniformGrid, U0, n, prec, K, W, stream, want_e2e, scheme=None):
+    g = UniformGrid((n, n, n), prec=prec, stream=stream.cuda_stream, scheme=scheme)
     g.upload(torch.from_numpy(U0))
     torch.cuda.synchronize()
     for _ in range(W):
@@ -294,6 +294,7 @@ def run_ours(args):
         "kernel_hash": kh,
     }
     if not args.no_variants:
+        line["schemes"] = bench_schemes(torch, A, UniformGrid, stream, K, W, world)
         line["amr"] = bench_amr(torch, args)
         line["boxes"] = bench_boxes(torch, args)
         line["adjoint"] = bench_adjoint(torch, args)
@@ -305,6 +306,27 @@ def run_ours(args):
 
 def _events(torch):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def bench_schemes(torch, A, UniformGrid, stream, K, W, world):
+    """The other slope limiters and the HLLE solver of section 2.2 on the
+    256^3 turbulence level (the default van Leer-type + HLLC for reference):
+    cells/s per precision."""
+    from paper_1712_07070_b300 import ics
+    U1 = ics.turbulence(256, seed=1)
+    names = {A.AMR_LIM_VANLEER: "van Leer", A.AMR_LIM_GMINMOD: "generalized minmod 1.5",
+             A.AMR_LIM_ALBADA: "van Albada", A.AMR_LIM_VL_GMINMOD: "hybrid van Leer/minmod 1.5"}
+    out = []
+    for lim in names:
+        for rs, rname in ((A.AMR_RS_HLLC, "HLLC"), (A.AMR_RS_HLLE, "HLLE")):
+            sch = {"limiter": lim, "riemann": rs, "minmod_coeff": 1.5}
+            row = {"workload": "turbulence 256^3", "limiter": names[lim], "riemann": rname}
+            for prec, key in ((A.AMR_FP64, "f64"), (A.AMR_FP32_ACC64, "fp32_acc64")):
+                r = run_case(torch, A, UniformGrid, U1, 256, prec, K, W, stream, want_e2e=False, scheme=sch)
+                ms = max_over_ranks(r["region_ms"], "cuda") / K
+                row[key] = world * 256 ** 3 / (ms * 1e-3)
+            out.append(row)
+    return {"unit": UNIT, "rows": out}
 
 
 def bench_amr(torch, args):
