@@ -35,6 +35,8 @@ def lib():
         L.or_vanleer.restype = ctypes.c_double
         L.or_hllc.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_double, _dp]
         L.or_hlle.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_double, _dp]
+        L.or_roe.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_double, _dp]
+        L.or_exact_flux.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_double, _dp]
         L.or_set_scheme.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double]
         for name in ("or_gminmod", "or_vl_gminmod"):
             getattr(L, name).argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
@@ -104,7 +106,7 @@ def vanleer(a, b):
 # ---- scheme options (section 2.2 lists the limiters and Riemann solvers) -----
 
 LIM_VANLEER, LIM_GMINMOD, LIM_ALBADA, LIM_VL_GMINMOD = 0, 1, 2, 3
-RS_HLLC, RS_HLLE = 0, 1
+RS_HLLC, RS_HLLE, RS_ROE, RS_EXACT = 0, 1, 2, 3
 
 
 def set_scheme(limiter=LIM_VANLEER, riemann=RS_HLLC, theta=1.5):
@@ -153,6 +155,22 @@ def hlle(UL, UR, d, gamma):
     UL, UR = _vec(UL), _vec(UR)
     F = np.empty(5)
     lib().or_hlle(_ptr(UL), _ptr(UR), d, gamma, _ptr(F))
+    return F
+
+
+def roe(UL, UR, d, gamma):
+    """Roe flux (with the Harten-Hyman entropy fix) through a face normal to d."""
+    UL, UR = _vec(UL), _vec(UR)
+    F = np.empty(5)
+    lib().or_roe(_ptr(UL), _ptr(UR), d, gamma, _ptr(F))
+    return F
+
+
+def exact_flux(UL, UR, d, gamma):
+    """Godunov flux of the exact Riemann solution through a face normal to d."""
+    UL, UR = _vec(UL), _vec(UR)
+    F = np.empty(5)
+    lib().or_exact_flux(_ptr(UL), _ptr(UR), d, gamma, _ptr(F))
     return F
 
 

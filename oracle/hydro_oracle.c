@@ -36,6 +36,12 @@
  *   - hybrid: sign(a) min(|vL(a,b)|, |generalized minmod(a,b)|);
  *   - HLLE: the HLLC outer speeds S_L, S_R above, F_L if S_L>=0, F_R if
  *     S_R<=0, else (S_R F_L - S_L F_R + S_L S_R (U_R - U_L))/(S_R - S_L).
+ *   - Roe: Roe averages, primitive-jump wave strengths and the averaged
+ *     Jacobian's right eigenvectors (Toro 2009 ch. 11), Harten-Hyman entropy
+ *     fix on the acoustic waves with delta = max(0, lambda~ - lambda(W_L),
+ *     lambda(W_R) - lambda~);
+ *   - exact: the physical flux of the exact solution at x/t = 0 (the exact
+ *     solver below), transverse velocities from the contact's upwind side.
  * or_set_scheme selects them; the default is van Leer-type + HLLC.
  *
  * Every per-cell loop is independent, so the OpenMP static split changes no
@@ -209,6 +215,12 @@ void or_hllc(const double *UL, const double *UR, int d, double gamma, double *F)
     for (int v = 0; v < NV; v++) F[v] = FK[v] + SK * (Us[v] - UK[v]);
 }
 
+int or_exact_star(double rl, double ul, double pl, double rr, double ur, double pr,
+                  double gamma, double *pstar, double *ustar);
+void or_exact_sample(double rl, double ul, double pl, double rr, double ur, double pr,
+                     double gamma, const double *xi, int n, double *rho, double *u,
+                     double *p);
+
 /* ---- HLLE Riemann solver (section 2.2; Einfeldt 1991) ------------------ */
 
 /* Flux across a face normal to d with the HLLC solver's outer wave speeds. */
@@ -243,10 +255,93 @@ void or_hlle(const double *UL, const double *UR, int d, double gamma, double *F)
     for (int v = 0; v < NV; v++) F[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (UR[v] - UL[v])) / (SR - SL);
 }
 
-/* the selected Riemann solver */
+/* ---- Roe's solver (section 2.2; Roe 1981, Toro 2009 ch. 11) ------------- */
+
+/* F = (F_L + F_R)/2 - (1/2) sum_k |lambda_k| alpha_k K_k with Roe averages,
+ * wave strengths of the primitive jumps and right eigenvectors of the
+ * averaged Jacobian; Harten-Hyman entropy fix on the two acoustic waves:
+ * delta = max(0, lambda~ - lambda(W_L), lambda(W_R) - lambda~), and
+ * |lambda~| < delta becomes (lambda~^2 + delta^2)/(2 delta). */
+void or_roe(const double *UL, const double *UR, int d, double gamma, double *F) {
+    double WL[NV], WR[NV], FL[NV], FR[NV];
+    or_prim(UL, WL, gamma);
+    or_prim(UR, WR, gamma);
+    or_flux(UL, d, gamma, FL);
+    or_flux(UR, d, gamma, FR);
+    double sl = sqrt(WL[0]), sr = sqrt(WR[0]);
+    double u[3];
+    for (int k = 0; k < 3; k++) u[k] = (sl * WL[1 + k] + sr * WR[1 + k]) / (sl + sr);
+    double hl = (UL[4] + WL[4]) / WL[0], hr = (UR[4] + WR[4]) / WR[0];
+    double H = (sl * hl + sr * hr) / (sl + sr);
+    double q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    double a = sqrt((gamma - 1.0) * (H - 0.5 * q2));
+    double r = sl * sr; /* Roe-averaged density */
+    double un = u[d];
+    double drho = WR[0] - WL[0], dp = WR[4] - WL[4], dun = WR[1 + d] - WL[1 + d];
+    double a1 = (dp - r * a * dun) / (2.0 * a * a);
+    double a2 = drho - dp / (a * a);
+    double a5 = (dp + r * a * dun) / (2.0 * a * a);
+    double l1 = fabs(un - a), l2 = fabs(un), l5 = fabs(un + a);
+    double cl = sound_speed(WL, gamma), cr = sound_speed(WR, gamma);
+    double del = 0.0, t;
+    t = (un - a) - (WL[1 + d] - cl);
+    if (t > del) del = t;
+    t = (WR[1 + d] - cr) - (un - a);
+    if (t > del) del = t;
+    if (l1 < del) l1 = (l1 * l1 + del * del) / (2.0 * del);
+    del = 0.0;
+    t = (un + a) - (WL[1 + d] + cl);
+    if (t > del) del = t;
+    t = (WR[1 + d] + cr) - (un + a);
+    if (t > del) del = t;
+    if (l5 < del) l5 = (l5 * l5 + del * del) / (2.0 * del);
+    /* D = sum_k |lambda_k| alpha_k K_k:
+     * K_1,5 = (1, u -/+ a n, H -/+ un a), K_2 = (1, u, q2/2),
+     * shear: rho~ dv_t (0, e_t, u_t) for each transverse direction t */
+    double D[NV];
+    D[0] = l1 * a1 + l2 * a2 + l5 * a5;
+    for (int k = 0; k < 3; k++) D[1 + k] = (l1 * a1 + l2 * a2 + l5 * a5) * u[k];
+    D[1 + d] += (l5 * a5 - l1 * a1) * a;
+    D[4] = l1 * a1 * (H - un * a) + l2 * a2 * 0.5 * q2 + l5 * a5 * (H + un * a);
+    for (int k = 0; k < 3; k++) {
+        if (k == d) continue;
+        double sh = l2 * r * (WR[1 + k] - WL[1 + k]);
+        D[1 + k] += sh;
+        D[4] += sh * u[k];
+    }
+    for (int v = 0; v < NV; v++) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * D[v];
+}
+
+/* ---- exact Riemann solver flux (section 2.2; Toro 2009 ch. 4) ----------- */
+
+/* Godunov flux: the physical flux of the exact solution at x/t = 0 (the
+ * normal velocity, density and pressure from or_exact_sample; the
+ * transverse velocities of the side of the contact x/t = 0 lies on,
+ * the left one when the contact does not move). */
+void or_exact_flux(const double *UL, const double *UR, int d, double gamma, double *F) {
+    double WL[NV], WR[NV], W[NV], U[NV];
+    or_prim(UL, WL, gamma);
+    or_prim(UR, WR, gamma);
+    double ps, us, xi = 0.0, r, v, q;
+    or_exact_star(WL[0], WL[1 + d], WL[4], WR[0], WR[1 + d], WR[4], gamma, &ps, &us);
+    or_exact_sample(WL[0], WL[1 + d], WL[4], WR[0], WR[1 + d], WR[4], gamma, &xi, 1, &r, &v, &q);
+    const double *Wt = (us >= 0.0) ? WL : WR;
+    W[0] = r;
+    for (int k = 0; k < 3; k++) W[1 + k] = Wt[1 + k];
+    W[1 + d] = v;
+    W[4] = q;
+    or_cons(W, U, gamma);
+    or_flux(U, d, gamma, F);
+}
+
+/* the selected Riemann solver: 0 HLLC, 1 HLLE, 2 Roe, 3 exact */
 void or_riemann(const double *UL, const double *UR, int d, double gamma, double *F) {
     if (or_riemann_id == 1)
         or_hlle(UL, UR, d, gamma, F);
+    else if (or_riemann_id == 2)
+        or_roe(UL, UR, d, gamma, F);
+    else if (or_riemann_id == 3)
+        or_exact_flux(UL, UR, d, gamma, F);
     else
         or_hllc(UL, UR, d, gamma, F);
 }

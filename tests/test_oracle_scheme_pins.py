@@ -10,6 +10,12 @@ the mathematics fixes -- never against the oracle itself:
   * HLLE: consistency F(U,U) = F(U), exact upwinding of supersonic states,
     mirror antisymmetry, and the diffusion of a stationary contact that HLLC
     resolves exactly;
+  * Roe: consistency, upwinding, mirror antisymmetry, exact resolution of a
+    stationary contact with shear and of a stationary Rankine-Hugoniot shock
+    (Roe's property: any slip in the averages or eigenvectors breaks it),
+    and convergence on a sonic rarefaction (which needs the entropy fix);
+  * exact solver: the Godunov flux of the Sod problem from Toro's published
+    star state (Table 4.2), consistency, upwinding, contact, mirror;
   * every scheme: uniform states unchanged to the bit, conservation to
     round-off, mirror symmetry, Sod converging to the exact solution, second
     order on a smooth wave, and the diffusion ordering the definitions imply
@@ -143,11 +149,90 @@ def test_hlle_diffuses_a_stationary_contact():
     assert Fe[1] == pytest.approx(0.8, rel=1e-15) and Fe[4] == 0.0
 
 
+# ---- Roe and the exact solver --------------------------------------------------
+
+SOLVERS = {"roe": oracle.roe, "exact": oracle.exact_flux}
+
+
+@pytest.mark.parametrize("name", ["roe", "exact"])
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_solver_consistency_upwinding_contact(name, d):
+    f = SOLVERS[name]
+    rng = np.random.default_rng(50 + d)
+    for _ in range(30):
+        U = random_state(rng, G53)
+        assert np.allclose(f(U, U, d, G53), oracle.flux(U, d, G53), rtol=1e-13, atol=1e-13)
+    for sign in (+1, -1):
+        WL = np.array([1.0, 0.1, -0.2, 0.3, 1.0])
+        WR = np.array([0.5, 0.2, 0.1, -0.1, 0.6])
+        WL[1 + d] = WR[1 + d] = sign * 6.0
+        UL, UR = oracle.cons(WL, G53), oracle.cons(WR, G53)
+        up = UL if sign > 0 else UR
+        assert np.allclose(f(UL, UR, d, G53), oracle.flux(up, d, G53), rtol=1e-13, atol=1e-13)
+    vt = np.array([0.3, -0.7, 0.2])
+    vt[d] = 0.0
+    F = f(oracle.cons([1.0, *vt, 0.8], G53), oracle.cons([0.1, *(-vt), 0.8], G53), d, G53)
+    assert abs(F[0]) < 1e-15 and abs(F[4]) < 1e-15 and abs(F[1 + d] - 0.8) < 1e-15
+
+
+@pytest.mark.parametrize("name", ["roe", "exact"])
+def test_solver_mirror_antisymmetry(name):
+    f = SOLVERS[name]
+    rng = np.random.default_rng(7)
+    M = np.array([1, -1, 1, 1, 1.0])
+    for _ in range(30):
+        UL, UR = random_state(rng, G53), random_state(rng, G53)
+        assert np.allclose(f(UR * M, UL * M, 0, G53), -f(UL, UR, 0, G53) * M, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("g", [1.4, G53])
+def test_roe_resolves_a_stationary_shock(g):
+    # Rankine-Hugoniot, upstream Mach 2 moving right into a shock at rest
+    M1, r1, p1 = 2.0, 1.0, 1.0
+    u1 = M1 * np.sqrt(g * p1 / r1)
+    r2 = r1 * (g + 1) * M1 ** 2 / ((g - 1) * M1 ** 2 + 2)
+    p2 = p1 * (1 + 2 * g / (g + 1) * (M1 ** 2 - 1))
+    u2 = u1 * r1 / r2
+    UL, UR = oracle.cons([r1, u1, 0.3, -0.1, p1], g), oracle.cons([r2, u2, 0.3, -0.1, p2], g)
+    FL = oracle.flux(UL, 0, g)
+    assert np.allclose(oracle.flux(UR, 0, g), FL, rtol=1e-13)  # the jump conditions hold
+    assert np.allclose(oracle.roe(UL, UR, 0, g), FL, rtol=1e-12, atol=1e-13)
+
+
+def test_exact_flux_of_sod_from_published_star_state():
+    # Toro (2009) Table 4.2, test 1: p* = 0.30313, u* = 0.92745, rho*_L = 0.42632;
+    # x/t = 0 lies between the left rarefaction's tail and the contact
+    g = 1.4
+    F = oracle.exact_flux(oracle.cons([1.0, 0, 0, 0, 1.0], g), oracle.cons([0.125, 0, 0, 0, 0.1], g), 0, g)
+    r, u, p = 0.42632, 0.92745, 0.30313
+    E = p / (g - 1) + 0.5 * r * u * u
+    assert np.allclose(F, [r * u, r * u * u + p, 0, 0, (E + p) * u], rtol=3e-5, atol=0)
+
+
+def test_roe_entropy_fix_sonic_rarefaction():
+    # Toro's test with a sonic point in the left rarefaction (rho, u, p) =
+    # (1, 0.75, 1) | (0.125, 0, 0.1): without an entropy fix Roe's solver
+    # keeps an expansion shock at x/t ~ 0 and the error stops converging
+    L, R, g, t = (1.0, 0.75, 1.0), (0.125, 0.0, 0.1), 1.4, 0.1
+    errs = []
+    with oracle.scheme(oracle.LIM_VANLEER, oracle.RS_ROE):
+        for n in (64, 128, 256):
+            U = ics.riemann_tube(n, L, R, axis=0, gamma=g)
+            U = run_to_time(U, 1.0 / n, g, 0.5, t)
+            x = ics.centres(n)
+            sel = (x > 0.3) & (x < 0.7)
+            r, _, _ = oracle.exact_sample(L, R, g, (x[sel] - 0.5) / t)
+            errs.append(np.abs(U[0, 0, 0, sel] - r).mean())
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 4e-3, errs
+    assert np.log2(errs[0] / errs[2]) / 2 > 0.6, errs
+
+
 # ---- whole steps of every scheme ----------------------------------------------------
 
 SCHEMES = [(oracle.LIM_VANLEER, oracle.RS_HLLE, 1.5), (oracle.LIM_GMINMOD, oracle.RS_HLLC, 1.5),
            (oracle.LIM_GMINMOD, oracle.RS_HLLE, 2.0), (oracle.LIM_ALBADA, oracle.RS_HLLC, 1.5),
-           (oracle.LIM_VL_GMINMOD, oracle.RS_HLLC, 1.5)]
+           (oracle.LIM_VL_GMINMOD, oracle.RS_HLLC, 1.5), (oracle.LIM_VANLEER, oracle.RS_ROE, 1.5),
+           (oracle.LIM_GMINMOD, oracle.RS_EXACT, 1.5)]
 
 
 @pytest.mark.parametrize("lim,rs,theta", SCHEMES)
