@@ -69,7 +69,9 @@ typedef enum {
 /* Riemann solver at every cell face (section 2.2). */
 typedef enum {
     AMR_RS_HLLC = 0,  /* HLLC, Einfeldt/Roe outer speeds (the default) */
-    AMR_RS_HLLE = 1   /* HLLE (Einfeldt 1991) with the same outer speeds */
+    AMR_RS_HLLE = 1,  /* HLLE (Einfeldt 1991) with the same outer speeds */
+    AMR_RS_ROE = 2,   /* Roe (1981), Harten-Hyman entropy fix on the acoustic waves */
+    AMR_RS_EXACT = 3  /* exact solver (Newton on the star pressure): Godunov flux at x/t = 0 */
 } amr_riemann;
 
 /* Run parameters (section 2.1 and 2.6 symbols). */

@@ -66,9 +66,9 @@ size_t step_smem_bytes(int prec) {
     return prec == AMR_FP64 ? sizeof(StepSmem<double>) : sizeof(StepSmem<float>);
 }
 
-template <typename real, bool GEN>
+template <typename real, int MODE>
 static amr_status set_step_smem() {
-    return cuda_fail(cudaFuncSetAttribute(k_hydro_step<real, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cuda_fail(cudaFuncSetAttribute(k_hydro_step<real, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)sizeof(StepSmem<real>)),
                      "step kernel smem attribute");
 }
@@ -77,8 +77,8 @@ amr_status configure_kernels() {
     static bool done = false;
     if (done) return AMR_OK;
     amr_status st;
-    if ((st = set_step_smem<double, false>()) || (st = set_step_smem<double, true>()) ||
-        (st = set_step_smem<float, false>()) || (st = set_step_smem<float, true>()))
+    if ((st = set_step_smem<double, 0>()) || (st = set_step_smem<double, 1>()) || (st = set_step_smem<double, 2>()) ||
+        (st = set_step_smem<float, 0>()) || (st = set_step_smem<float, 1>()) || (st = set_step_smem<float, 2>()))
         return st;
     done = true;
     return AMR_OK;
@@ -86,12 +86,12 @@ amr_status configure_kernels() {
 
 template <typename real>
 static int step_occupancy() {
-    int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_hydro_step<real, false>, StepCfg<real>::NT,
-                                                  sizeof(StepSmem<real>));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_hydro_step<real, true>, StepCfg<real>::NT,
-                                                  sizeof(StepSmem<real>));
-    const int n = a < b ? a : b;
+    int a = 0, b = 0, c = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_hydro_step<real, 0>, StepCfg<real>::NT, sizeof(StepSmem<real>));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_hydro_step<real, 1>, StepCfg<real>::NT, sizeof(StepSmem<real>));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_hydro_step<real, 2>, StepCfg<real>::NT, sizeof(StepSmem<real>));
+    int n = a < b ? a : b;
+    n = n < c ? n : c;
     return n > 0 ? n : 1;
 }
 
@@ -100,10 +100,11 @@ int step_blocks_per_sm(int prec) { return prec == AMR_FP64 ? step_occupancy<doub
 
 template <typename real>
 static void launch_step_k(const StepParams &P, int grid, cudaStream_t s) {
-    if (P.limiter != LIM_VANLEER || P.riemann != RS_HLLC)
-        k_hydro_step<real, true><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(P);
-    else
-        k_hydro_step<real, false><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(P);
+    switch (scheme_mode(P.limiter, P.riemann)) {
+        case 0: k_hydro_step<real, 0><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(P); break;
+        case 1: k_hydro_step<real, 1><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(P); break;
+        default: k_hydro_step<real, 2><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(P); break;
+    }
 }
 
 amr_status launch_step(amr_hydro_ctx *c, const StepParams &P, int grid) {
@@ -213,7 +214,7 @@ amr_status amr_hydro_init(const amr_hydro_params *p, void *stream, amr_hydro_ctx
     if (p->prec != AMR_FP64 && p->prec != AMR_FP32_ACC64) return AMR_E_INVAL;
     if (p->max_patches <= 0 || p->max_patches % 8) return AMR_E_INVAL;
     if (p->limiter < AMR_LIM_VANLEER || p->limiter > AMR_LIM_VL_GMINMOD) return AMR_E_INVAL;
-    if (p->riemann != AMR_RS_HLLC && p->riemann != AMR_RS_HLLE) return AMR_E_INVAL;
+    if (p->riemann < AMR_RS_HLLC || p->riemann > AMR_RS_EXACT) return AMR_E_INVAL;
     if (p->minmod_coeff != 0.0 && !(p->minmod_coeff >= 1.0 && p->minmod_coeff <= 2.0)) return AMR_E_INVAL;
     for (int d = 0; d < 3; d++) {
         if (p->root_n[d] <= 0 || p->root_n[d] % 16) return AMR_E_INVAL;

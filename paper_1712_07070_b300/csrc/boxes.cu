@@ -25,9 +25,9 @@ namespace {
 
 bool configured = false;
 
-template <typename real, bool GEN>
+template <typename real, int MODE>
 amr_status set_box_smem() {
-    return cuda_fail(cudaFuncSetAttribute(k_hydro_step_boxes<real, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cuda_fail(cudaFuncSetAttribute(k_hydro_step_boxes<real, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)sizeof(StepSmem<real>)),
                      "box kernel smem attribute");
 }
@@ -35,8 +35,8 @@ amr_status set_box_smem() {
 amr_status configure_box_kernels() {
     if (configured) return AMR_OK;
     amr_status st;
-    if ((st = set_box_smem<double, false>()) || (st = set_box_smem<double, true>()) ||
-        (st = set_box_smem<float, false>()) || (st = set_box_smem<float, true>()))
+    if ((st = set_box_smem<double, 0>()) || (st = set_box_smem<double, 1>()) || (st = set_box_smem<double, 2>()) ||
+        (st = set_box_smem<float, 0>()) || (st = set_box_smem<float, 1>()) || (st = set_box_smem<float, 2>()))
         return st;
     configured = true;
     return AMR_OK;
@@ -44,12 +44,12 @@ amr_status configure_box_kernels() {
 
 template <typename real>
 int box_occupancy() {
-    int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_hydro_step_boxes<real, false>, StepCfg<real>::NT,
-                                                  sizeof(StepSmem<real>));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_hydro_step_boxes<real, true>, StepCfg<real>::NT,
-                                                  sizeof(StepSmem<real>));
-    const int n = a < b ? a : b;
+    int a = 0, b = 0, c = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_hydro_step_boxes<real, 0>, StepCfg<real>::NT, sizeof(StepSmem<real>));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_hydro_step_boxes<real, 1>, StepCfg<real>::NT, sizeof(StepSmem<real>));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_hydro_step_boxes<real, 2>, StepCfg<real>::NT, sizeof(StepSmem<real>));
+    int n = a < b ? a : b;
+    n = n < c ? n : c;
     return n > 0 ? n : 1;
 }
 
@@ -57,10 +57,11 @@ int resident_per_sm(int prec) { return prec == AMR_FP64 ? box_occupancy<double>(
 
 template <typename real>
 void launch_boxes_k(const BoxLaunch &B, int grid, cudaStream_t s) {
-    if (B.limiter != LIM_VANLEER || B.riemann != RS_HLLC)
-        k_hydro_step_boxes<real, true><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(B);
-    else
-        k_hydro_step_boxes<real, false><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(B);
+    switch (scheme_mode(B.limiter, B.riemann)) {
+        case 0: k_hydro_step_boxes<real, 0><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(B); break;
+        case 1: k_hydro_step_boxes<real, 1><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(B); break;
+        default: k_hydro_step_boxes<real, 2><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(B); break;
+    }
 }
 
 amr_status launch_boxes(amr_hydro_ctx *c, const BoxLaunch &B, int grid, cudaStream_t s) {

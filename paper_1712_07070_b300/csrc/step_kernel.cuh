@@ -129,7 +129,7 @@ __device__ __forceinline__ void cf_register(const StepSmem<real> &S, const StepP
     }
 }
 
-// HLLC through a face normal to a runtime direction D: the normal momentum is
+// The face solver through a face normal to a runtime direction D: the normal momentum is
 // swapped into the x slot, the x-normal solver runs, and the flux is swapped
 // back (register selects only), so lanes of one warp can serve different
 // directions without diverging.
@@ -147,7 +147,7 @@ __device__ __forceinline__ void hllc_dir(const real uL[NV], const real uR[NV], i
     b[1] = D == 1 ? uR[2] : (D == 2 ? uR[3] : uR[1]);
     b[2] = D == 1 ? uR[1] : uR[2];
     b[3] = D == 2 ? uR[1] : uR[3];
-    hllc<0>(a, b, f, g);
+    face_flux<0>(a, b, f, g);
     F[0] = f[0];
     F[4] = f[4];
     F[1] = D == 1 ? f[2] : (D == 2 ? f[3] : f[1]);
@@ -302,7 +302,7 @@ __device__ __forceinline__ void x_face(StepSmem<real> &S, const StepParams &P, d
     real uL[NV], uR[NV], F[NV];
 #pragma unroll
     for (int v = 0; v < NV; v++) { uL[v] = S.XS[1][v][row][col]; uR[v] = S.XS[0][v][row][col + 1]; }
-    hllc<0>(uL, uR, F, g);
+    face_flux<0>(uL, uR, F, g);
 #pragma unroll
     for (int v = 0; v < NV; v++) S.FX[v][row][col] = F[v];
     if ((col & 7) == 0) {  // a patch face: x = 0 (group boundary) or x = 8
@@ -317,7 +317,7 @@ __device__ __forceinline__ void y_face(StepSmem<real> &S, const StepParams &P, d
     real uL[NV], uR[NV], F[NV];
 #pragma unroll
     for (int v = 0; v < NV; v++) { uL[v] = S.YS[1][v][r][col]; uR[v] = S.YS[0][v][r + 1][col]; }
-    hllc<1>(uL, uR, F, g);
+    face_flux<1>(uL, uR, F, g);
 #pragma unroll
     for (int v = 0; v < NV; v++) S.FY[v][r][col] = F[v];
     if ((r & 7) == 0) {  // a patch face: y = 0 (group boundary) or y = 8
@@ -351,12 +351,18 @@ __device__ __forceinline__ void high_faces(StepSmem<real> &S, const StepParams &
 template <typename real>
 __device__ __forceinline__ void z_face(const StepSmem<real> &S, const StepParams &P, double dt, const real zp_prev[NV],
                                        const real zm[NV], int cx, int cy, int z, real fz[NV], const Gas<real> &g) {
-    hllc<2>(zp_prev, zm, fz, g);
+    face_flux<2>(zp_prev, zm, fz, g);
     if (z == 0 || z == GE || z == 8) {
         const int pl = (cx >> 3) + 2 * (cy >> 3);
         cf_register(S, P, dt, fz, 2, cx, cy, z == 0 ? -1 : pl + 4 * ((z - 1) >> 3), z == GE ? -1 : pl + 4 * (z >> 3),
                     z == 0, z == GE);
     }
+}
+
+// Step-kernel instance (MODE) for a limiter / Riemann solver choice.
+__host__ __device__ inline int scheme_mode(int limiter, int riemann) {
+    if (riemann == RS_EXACT) return 2;
+    return (limiter != LIM_VANLEER || riemann != RS_HLLC) ? 1 : 0;
 }
 
 // One patch group: the whole fused step for group `grp` of P's level.  The
@@ -511,10 +517,11 @@ __device__ __forceinline__ void step_group(StepSmem<real> &S, const StepParams &
     __syncthreads();  // the next group overwrites nbr and the ring
 }
 
-// GEN = false: the default scheme (van Leer-type limiter, HLLC) as
-// compile-time constants, so the scheme branches fold away; GEN = true: the
-// limiter and solver of P (uniform over the launch).
-template <typename real, bool GEN>
+// MODE 0: the default scheme (van Leer-type limiter, HLLC) as compile-time
+// constants, so the scheme branches fold away; MODE 1: the limiter of P
+// and its HLLC, HLLE or Roe solver; MODE 2: the limiter of P and the exact
+// solver (kept out of the other instances: its Newton iteration is a call).
+template <typename real, int MODE>
 __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydro_step(StepParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<real> &S = *reinterpret_cast<StepSmem<real> *>(smem_raw);
@@ -524,11 +531,13 @@ __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydr
     g.gamma = (real)P.gamma;
     g.gm1 = (real)(P.gamma - 1.0);
     g.inv_gm1 = (real)(1.0 / (P.gamma - 1.0));
-    if constexpr (GEN) {
+    if constexpr (MODE != 0) {
         g.lim = P.limiter;
-        g.rs = P.riemann;
         g.htheta = (real)(0.5 * P.theta);
     }
+    if constexpr (MODE == 1)  // a value the compiler can see is never RS_EXACT
+        g.rs = P.riemann == RS_HLLE ? RS_HLLE : (P.riemann == RS_ROE ? RS_ROE : RS_HLLC);
+    if constexpr (MODE == 2) g.rs = RS_EXACT;
 
     if (tid == 0) {
         double dt = P.dt;
@@ -600,10 +609,11 @@ struct BoxLaunch {
     int n_boxes;
 };
 
-// GEN = false: the default scheme (van Leer-type limiter, HLLC) as
-// compile-time constants, so the scheme branches fold away; GEN = true: the
-// limiter and solver of B (uniform over the launch).
-template <typename real, bool GEN>
+// MODE 0: the default scheme (van Leer-type limiter, HLLC) as compile-time
+// constants, so the scheme branches fold away; MODE 1: the limiter of B
+// and its HLLC, HLLE or Roe solver; MODE 2: the limiter of B and the exact
+// solver (kept out of the other instances: its Newton iteration is a call).
+template <typename real, int MODE>
 __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydro_step_boxes(BoxLaunch B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<real> &S = *reinterpret_cast<StepSmem<real> *>(smem_raw);
@@ -612,11 +622,13 @@ __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydr
     g.gamma = (real)B.gamma;
     g.gm1 = (real)(B.gamma - 1.0);
     g.inv_gm1 = (real)(1.0 / (B.gamma - 1.0));
-    if constexpr (GEN) {
+    if constexpr (MODE != 0) {
         g.lim = B.limiter;
-        g.rs = B.riemann;
         g.htheta = (real)(0.5 * B.theta);
     }
+    if constexpr (MODE == 1)  // a value the compiler can see is never RS_EXACT
+        g.rs = B.riemann == RS_HLLE ? RS_HLLE : (B.riemann == RS_ROE ? RS_ROE : RS_HLLC);
+    if constexpr (MODE == 2) g.rs = RS_EXACT;
     int first, last, stride;
     if (B.chunked) {
         const int per = (B.n_work + gridDim.x - 1) / gridDim.x;

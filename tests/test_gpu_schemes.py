@@ -1,4 +1,5 @@
-"""GPU parity of the other slope limiters and the HLLE solver (section 2.2)
+"""GPU parity of the other slope limiters and Riemann solvers (section 2.2:
+HLLE, Roe, the exact solver)
 against the oracle with the same scheme selected: uniform periodic steps in
 FP64 (relative L1 <= 1e-12) and the FP32 mode (1e-5), the AMR W-cycle with
 fix-up and regrid, and the batched-box launch; the adjoint refuses schemes
@@ -25,6 +26,10 @@ SCHEMES = [
     (A.AMR_LIM_ALBADA, A.AMR_RS_HLLE, 1.5),
     (A.AMR_LIM_VL_GMINMOD, A.AMR_RS_HLLC, 1.5),
     (A.AMR_LIM_VL_GMINMOD, A.AMR_RS_HLLE, 1.2),
+    (A.AMR_LIM_VANLEER, A.AMR_RS_ROE, 1.5),
+    (A.AMR_LIM_GMINMOD, A.AMR_RS_ROE, 2.0),
+    (A.AMR_LIM_VANLEER, A.AMR_RS_EXACT, 1.5),
+    (A.AMR_LIM_ALBADA, A.AMR_RS_EXACT, 1.5),
 ]
 
 
@@ -78,9 +83,10 @@ def test_amr_w_cycle_parity(prec, tol, theta, mild):
 
 
 @pytest.mark.parametrize("prec,tol", [(A.AMR_FP64, 1e-12), (A.AMR_FP32_ACC64, 1e-5)])
-def test_boxes_parity(prec, tol):
+@pytest.mark.parametrize("lim,rs", [(A.AMR_LIM_ALBADA, A.AMR_RS_HLLE), (A.AMR_LIM_VANLEER, A.AMR_RS_ROE)])
+def test_boxes_parity(prec, tol, lim, rs):
     from paper_1712_07070_b300.boxes import BoxBatch
-    lim, rs, theta = A.AMR_LIM_ALBADA, A.AMR_RS_HLLE, 1.5
+    theta = 1.5
     g14 = 1.4
     B = BoxBatch(gamma=g14, prec=prec, scheme=sch(lim, rs, theta))
     sizes = [32, 16, 48]
