@@ -28,7 +28,12 @@
 namespace {
 
 constexpr int NV = 5;
-using amrh::rcp_;  // FP64 reciprocal: special-function seed + two Newton steps
+using amrh::rcp_;   // FP64 reciprocal: special-function seed + one third-order refinement
+using amrh::sqrt_;  // FP64 square root: x * refined rsqrt on positive normals
+using amrh::ge0;
+using amrh::le0;
+using amrh::gt0;
+using amrh::okey;
 
 struct Dims {
     int nx, ny, nz;
@@ -127,8 +132,8 @@ __device__ void hllc_vjp(const double UL[NV], const double UR[NV], int d, double
     const double rl = WL[0], pl = WL[4], ul = WL[1 + d];
     const double rr = WR[0], pr = WR[4], ur = WR[1 + d];
     const double ril = rcp_(rl), rir = rcp_(rr);
-    const double cl = sqrt(g * pl * ril), cr = sqrt(g * pr * rir);
-    const double sl = sqrt(rl), sr = sqrt(rr), S = sl + sr, iS = rcp_(S);
+    const double cl = sqrt_(g * pl * ril), cr = sqrt_(g * pr * rir);
+    const double sl = sqrt_(rl), sr = sqrt_(rr), S = sl + sr, iS = rcp_(S);
     double vt[3], Tk[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
@@ -138,18 +143,18 @@ __device__ void hllc_vjp(const double UL[NV], const double UR[NV], int d, double
     const double hl = (UL[4] + pl) * ril, hr = (UR[4] + pr) * rir;
     const double T = sl * hl + sr * hr, ht = T * iS;
     const double X = gm1 * (ht - 0.5 * (vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]));
-    const double ct = sqrt(X);
+    const double ct = sqrt_(X);
     const double a = ul - cl, b = vt[d] - ct;
-    const bool selL = a <= b;
+    const bool selL = okey(a) <= okey(b);  // comparisons on the integer units
     const double SL = selL ? a : b;
     const double a2 = ur + cr, b2 = vt[d] + ct;
-    const bool selR = a2 >= b2;
+    const bool selR = okey(a2) >= okey(b2);
     const double SR = selR ? a2 : b2;
-    if (SL >= 0.0) {
+    if (ge0(SL)) {
         flux_adj(UL, d, lF, lUL, gm1);
         return;
     }
-    if (SR <= 0.0) {
+    if (le0(SR)) {
         flux_adj(UR, d, lF, lUR, gm1);
         return;
     }
@@ -157,7 +162,7 @@ __device__ void hllc_vjp(const double UL[NV], const double UR[NV], int d, double
     const double den = rl * (SL - ul) - rr * (SR - ur);
     const double iden = rcp_(den);
     const double Ss = num * iden;
-    const bool left = Ss >= 0.0;
+    const bool left = ge0(Ss);
     const double *UK = left ? UL : UR;
     const double *WK = left ? WL : WR;
     double *lUK = left ? lUL : lUR;
@@ -335,7 +340,7 @@ __device__ void hancock_fwd(const double *__restrict__ W, const Dims &D, int x, 
             H.a[d][v] = a;
             H.b[d][v] = b;
             const double ab = a * b;
-            const double s = ab > 0.0 ? 2.0 * ab * rcp_(a + b) : 0.0;
+            const double s = gt0(ab) ? 2.0 * ab * rcp_(a + b) : 0.0;
             H.slope[d][v] = s;
             H.Wf[2 * d][v] = H.w[v] - 0.5 * s;
             H.Wf[2 * d + 1][v] = H.w[v] + 0.5 * s;
@@ -440,7 +445,7 @@ __global__ void k_adj_hancock_rev(const double *__restrict__ W, const double *__
                 const double ls = 0.5 * (lp[v] - lm[v]);
                 const double a = H.a[d][v], b = H.b[d][v];
                 double la = 0.0, lb = 0.0;
-                if (a * b > 0.0) {
+                if (gt0(a * b)) {
                     const double r = rcp_(a + b), r2 = 2.0 * ls * r * r;
                     la = r2 * b * b;
                     lb = r2 * a * a;
