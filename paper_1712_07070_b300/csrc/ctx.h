@@ -48,6 +48,8 @@ struct Level {
     const int32_t *d_corner = nullptr, *d_sib = nullptr, *d_parent = nullptr, *d_child = nullptr;
     std::vector<int32_t> corner, sib, parent, child;  // host mirrors
     DevBuf<int32_t> nbr;        // [n_groups][64]
+    DevBuf<int32_t> runs, run_off;  // z-runs of groups (step work items), see build_runs
+    int n_runs = 0;
     DevBuf<double> ghost;       // [n_ghost][5][512]
     DevBuf<int32_t> ghost_info; // [n_ghost][GHOST_INFO]
     int n_ghost = 0;
@@ -71,6 +73,9 @@ struct Level {
     bool uniform = false;  // level 0 holding the whole root grid in the order of amr_hydro_uniform_tables
     void release() {
         nbr.release();
+        runs.release();
+        run_off.release();
+        n_runs = 0;
         ghost.release();
         ghost_info.release();
         fine_off.release();
@@ -156,4 +161,12 @@ amr_status build_uniform_tables(const int np[3], int32_t *corner, int32_t *sib, 
 amr_status build_nbr_plan(int level, int n_patches, const int32_t *corner, const int32_t *sib,
                           const int32_t *parent, const int level_cells[3],
                           std::vector<int32_t> &nbr, std::vector<GhostInfo> &ghosts);
+// z-chains of a level's groups (same-level groups stacked in z), their
+// runs of at most max_len groups, and the run length for a grid (host_plan.cpp).
+void z_chains(int n_groups, const int32_t *nbr, std::vector<int32_t> &chains, std::vector<int32_t> &chain_off);
+void cut_runs(const std::vector<int32_t> &chains, const std::vector<int32_t> &chain_off, int max_len,
+              std::vector<int32_t> &runs, std::vector<int32_t> &run_off);
+void build_runs(int n_groups, const int32_t *nbr, int max_len, std::vector<int32_t> &runs,
+                std::vector<int32_t> &run_off);
+int choose_run_len(const std::vector<int32_t> &chain_off, int grid, double e);
 }  // namespace amrh

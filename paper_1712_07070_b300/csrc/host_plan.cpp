@@ -142,10 +142,119 @@ amr_status build_nbr_plan(int level, int n_patches, const int32_t *corner, const
     return AMR_OK;
 }
 
+// z-chains: group u is g's upper neighbour when position q = (0,0,2) of g
+// (index 53) holds u's first patch and position q = (0,0,-1) of u (index 5)
+// holds g's patch (0,0,1), i.e. both are same-level groups stacked in z.
+// Chains follow the upper neighbours from groups with no lower neighbour (in
+// group order), then the remaining cycles (periodic columns) from their
+// lowest group.
+void z_chains(int n_groups, const int32_t *nbr, std::vector<int32_t> &chains, std::vector<int32_t> &chain_off) {
+    std::vector<int32_t> up(n_groups, -1), down(n_groups, -1);
+    for (int g = 0; g < n_groups; g++) {
+        const int32_t s = nbr[(size_t)g * 64 + 53];
+        if (s < 0 || s % 8) continue;
+        const int u = s / 8;
+        if (u == g || u >= n_groups || nbr[(size_t)u * 64 + 5] != 8 * g + 4) continue;
+        up[g] = u;
+        down[u] = g;
+    }
+    chains.clear();
+    chain_off.assign(1, 0);
+    std::vector<char> seen(n_groups, 0);
+    auto chain = [&](int g) {
+        while (g >= 0 && !seen[g]) {
+            seen[g] = 1;
+            chains.push_back(g);
+            g = up[g];
+        }
+        chain_off.push_back((int32_t)chains.size());
+    };
+    for (int g = 0; g < n_groups; g++)
+        if (!seen[g] && down[g] < 0) chain(g);
+    for (int g = 0; g < n_groups; g++)
+        if (!seen[g]) chain(g);
+}
+
+// Each chain cut into runs of at most max_len groups, in chain order.
+void cut_runs(const std::vector<int32_t> &chains, const std::vector<int32_t> &chain_off, int max_len,
+              std::vector<int32_t> &runs, std::vector<int32_t> &run_off) {
+    runs = chains;
+    run_off.assign(1, 0);
+    for (size_t c = 0; c + 1 < chain_off.size(); c++)
+        for (int a = chain_off[c]; a < chain_off[c + 1]; a += max_len)
+            run_off.push_back(a + max_len < chain_off[c + 1] ? a + max_len : chain_off[c + 1]);
+}
+
+void build_runs(int n_groups, const int32_t *nbr, int max_len, std::vector<int32_t> &runs,
+                std::vector<int32_t> &run_off) {
+    std::vector<int32_t> chains, off;
+    z_chains(n_groups, nbr, chains, off);
+    cut_runs(chains, off, max_len, runs, run_off);
+}
+
+// Run length for `grid` resident CTAs: the CTAs take runs round-robin, so a
+// launch lasts about ceil(n_runs / grid) rounds of (len + e) group-steps,
+// where e is the cost of a run beyond its groups (the two extra Hancock
+// planes and four plane loads of its ends, its prologue; measured about 0.05
+// group-steps in FP64 and 0.13 in the FP32 mode).  The length in 1..32 that
+// minimises that estimate.
+int choose_run_len(const std::vector<int32_t> &chain_off, int grid, double e) {
+    int best_len = 1;
+    double best = 1e300;
+    for (int len = 1; len <= 32; len++) {
+        long long n_runs = 0;
+        int longest = 0;
+        for (size_t c = 0; c + 1 < chain_off.size(); c++) {
+            const int L = chain_off[c + 1] - chain_off[c];
+            n_runs += (L + len - 1) / len;
+            longest = L > longest ? L : longest;
+        }
+        const long long rounds = (n_runs + grid - 1) / grid;
+        const double cost = (double)rounds * ((len < longest ? len : longest) + e);
+        if (cost < best - 1e-9) {
+            best = cost;
+            best_len = len;
+        }
+    }
+    return best_len;
+}
+
 }  // namespace amrh
 
 extern "C" amr_status amr_hydro_uniform_tables(const int np[3], int32_t *corner, int32_t *sib,
                                                int32_t *parent, int32_t *child_group) {
     if (!np || !corner || !sib) return AMR_E_INVAL;
     return amrh::build_uniform_tables(np, corner, sib, parent, child_group);
+}
+
+// Test hook (not part of the C ABI): the z-runs build_runs makes for a
+// neighbour plan; runs_out must hold n_groups entries and run_off_out
+// n_groups + 1.  Returns the number of runs.
+extern "C" int amrh_selftest_runs(int n_groups, const int32_t *nbr, int max_len, int32_t *runs_out,
+                                  int32_t *run_off_out) {
+    std::vector<int32_t> runs, off;
+    amrh::build_runs(n_groups, nbr, max_len, runs, off);
+    for (size_t i = 0; i < runs.size(); i++) runs_out[i] = runs[i];
+    for (size_t i = 0; i < off.size(); i++) run_off_out[i] = off[i];
+    return (int)off.size() - 1;
+}
+
+// Test hook: the neighbour plan of a level from host tables (corner, sib,
+// parent as in amr_hydro_set_level); nbr_out: n_patches / 8 x 64 entries.
+extern "C" int amrh_selftest_nbr_plan(int level, int n_patches, const int32_t *corner, const int32_t *sib,
+                                      const int32_t *parent, const int level_cells[3], int32_t *nbr_out) {
+    std::vector<int32_t> nbr;
+    std::vector<amrh::GhostInfo> ghosts;
+    const amr_status st = amrh::build_nbr_plan(level, n_patches, corner, sib, parent, level_cells, nbr, ghosts);
+    if (st) return -1;
+    for (size_t i = 0; i < nbr.size(); i++) nbr_out[i] = nbr[i];
+    return (int)ghosts.size();
+}
+
+// Test hook: the run length choose_run_len picks for n_chains chains of the
+// given lengths on `grid` resident CTAs with per-run overhead e.
+extern "C" int amrh_selftest_run_len(int n_chains, const int32_t *lengths, int grid, double e) {
+    std::vector<int32_t> off(1, 0);
+    for (int c = 0; c < n_chains; c++) off.push_back(off.back() + lengths[c]);
+    return amrh::choose_run_len(off, grid, e);
 }

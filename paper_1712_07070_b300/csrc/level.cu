@@ -156,8 +156,13 @@ amr_status amr_hydro_advance_level(amr_hydro_ctx *c, int level, double dt, int64
                             "memset fine registers")))
             return st;
     }
+    if (L.n_runs > 0) {  // z-runs of groups as the work items
+        P.runs = L.runs.p;
+        P.run_off = L.run_off.p;
+        P.n_work = L.n_runs;
+    }
     const int cap = c->n_sm * c->step_bps;
-    const int grid = L.n_groups < cap ? L.n_groups : cap;
+    const int grid = P.n_work < cap ? P.n_work : cap;
     if ((st = launch_step(c, P, grid))) return st;
 
     L.cur = 1 - L.cur;

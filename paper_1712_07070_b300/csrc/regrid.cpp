@@ -57,6 +57,19 @@ amr_status plan_level(amr_hydro_ctx *c, int level) {
                                    level > 0 ? L.parent.data() : nullptr, cells, nbr, ghosts);
     if (st) return st;
     if ((st = upload(L.nbr, nbr, c->stream))) return st;
+    {  // z-runs of the length the round-robin cost estimate prefers
+        std::vector<int32_t> chains, coff, runs, off;
+        z_chains(L.n_groups, nbr.data(), chains, coff);
+        const int len = choose_run_len(coff, c->n_sm * c->step_bps, c->prm.prec == AMR_FP64 ? 0.05 : 0.13);
+        // single-group runs: the plain group list (a run list would only add
+        // the lookups of each work item's group ahead of its tables)
+        L.n_runs = 0;
+        if (len > 1) {
+            cut_runs(chains, coff, len, runs, off);
+            L.n_runs = (int)off.size() - 1;
+            if ((st = upload(L.runs, runs, c->stream)) || (st = upload(L.run_off, off, c->stream))) return st;
+        }
+    }
     L.n_ghost = (int)ghosts.size();
     if (L.n_ghost) {
         if ((st = L.ghost.reserve((size_t)L.n_ghost * PSLOT_H))) return st;

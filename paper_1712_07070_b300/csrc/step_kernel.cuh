@@ -62,6 +62,10 @@ struct StepParams {
     const int32_t *__restrict__ work; // optional list of group ids (null: work0..work0+n_work-1)
     int n_work;
     int work0;
+    // optional z-runs: work item i is the groups runs[run_off[i] .. run_off[i+1]),
+    // each the same-level group directly above the previous one
+    const int32_t *__restrict__ runs;
+    const int32_t *__restrict__ run_off;
     double dt;                               // >= 0: time step from the host
     const unsigned long long *smax_in;       // dt < 0: dt = cfl*dh/smax_in
     double cfl, dh, gamma;
@@ -83,28 +87,26 @@ struct StepSmem {
     real FY[NV][GE + 1][GE];     // y flux at face y-1/2, y=0..16
     alignas(16) double raw[NV][TW * TW];  // next tile plane in flight (cp.async), x-pairs owned per thread
     alignas(16) double uo[2][NV][COLS];   // each column's U^n one plane ahead of its update (cp.async)
-    int nbr[64];
-    long long cfo[6];   // fine register blocks of the group's faces (-1: none)
-    long long cco[48];  // coarse register blocks of its 8 patches' faces (-1: none)
-    int any_cf;         // whether the group touches any register
+    // per-group tables, two slots (group k of a run uses slot k & 1)
+    int nbr[2][64];
+    long long cfo[2][6];   // fine register blocks of the group's faces (-1: none)
+    long long cco[2][48];  // coarse register blocks of its 8 patches' faces (-1: none)
     double red[MAX_WARPS];
     double dt;
 };
 
-// dt * F into the registers of the face between group cells a (low) and b
-// (high) along D at flux value F (compute type), fine face coordinates
-// (t1, t2) in 0..15 within the group; pa/pb: local patch indices (0..7) of the
-// two cells when they belong to this group (-1 otherwise); face_lo/face_hi:
-// whether the face is the group's low / high boundary along D.
+// dt * F into the registers of the face between cells a (low) and b (high)
+// along D at flux value F (compute type), fine face coordinates (t1, t2) in
+// 0..15 within the group; pa / pb: local patch indices (0..7) of the two
+// cells in the groups of table slots sa / sb when they belong to the run
+// (-1 otherwise); fo: the fine register block of the face (-1: none).
 template <typename real>
 __device__ __forceinline__ void cf_register(const StepSmem<real> &S, const StepParams &P, double dt,
-                                            const real F[NV], int D, int t1, int t2, int pa, int pb,
-                                            bool face_lo, bool face_hi) {
-    if (!S.any_cf) return;
+                                            const real F[NV], int D, int t1, int t2, int sa, int pa, int sb,
+                                            int pb, long long fo) {
     double Fd[NV];
-    const long long fo = face_lo ? S.cfo[2 * D] : (face_hi ? S.cfo[2 * D + 1] : -1);
-    const long long ca = pa >= 0 ? S.cco[pa * 6 + 2 * D + 1] : -1;  // high face of the low cell's patch
-    const long long cb = pb >= 0 ? S.cco[pb * 6 + 2 * D] : -1;      // low face of the high cell's patch
+    const long long ca = pa >= 0 ? S.cco[sa][pa * 6 + 2 * D + 1] : -1;  // high face of the low cell's patch
+    const long long cb = pb >= 0 ? S.cco[sb][pb * 6 + 2 * D] : -1;      // low face of the high cell's patch
     if (fo < 0 && ca < 0 && cb < 0) return;
 #pragma unroll
     for (int v = 0; v < NV; v++) {
@@ -162,17 +164,18 @@ __device__ __forceinline__ const double *patch_src(const StepParams &P, int s) {
     return nullptr;
 }
 
-// Load tile plane tz (-2..17) into ring slot and convert to primitives.
+// Load tile plane tl (-2..17 within the group of table slot ts) into the
+// ring slot of run plane tr and convert to primitives.
 template <typename real>
-__device__ __forceinline__ void load_plane(StepSmem<real> &S, const StepParams &P, int tz,
+__device__ __forceinline__ void load_plane(StepSmem<real> &S, const StepParams &P, int ts, int tl, int tr,
                                            const Gas<real> &g) {
-    const int slot = (tz + 3) % 3;
-    const int qz = (tz + PS) >> 3, lz = (tz + PS) & 7;
+    const int slot = (tr + 3) % 3;
+    const int qz = (tl + PS) >> 3, lz = (tl + PS) & 7;
     for (int i = threadIdx.x; i < TW * TW; i += StepCfg<real>::NT) {
         const int ty = i / TW - 2, tx = i % TW - 2;
         const int qy = (ty + PS) >> 3, ly = (ty + PS) & 7;
         const int qx = (tx + PS) >> 3, lx = (tx + PS) & 7;
-        const double *src = patch_src(P, S.nbr[qx + 4 * qy + 16 * qz]);
+        const double *src = patch_src(P, S.nbr[ts][qx + 4 * qy + 16 * qz]);
         real u[NV], w[NV];
         if (src) {
             const int off = lz * 64 + ly * 8 + lx;
@@ -201,13 +204,13 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 template <typename real>
-__device__ __forceinline__ void issue_plane(StepSmem<real> &S, const StepParams &P, int tz) {
-    const int qz = (tz + PS) >> 3, lz = (tz + PS) & 7;
+__device__ __forceinline__ void issue_plane(StepSmem<real> &S, const StepParams &P, int ts, int tl) {
+    const int qz = (tl + PS) >> 3, lz = (tl + PS) & 7;
     for (int j = threadIdx.x; j < TPAIRS; j += StepCfg<real>::NT) {
         const int ty = j / (TW / 2) - 2, tx = 2 * (j % (TW / 2)) - 2;
         const int qy = (ty + PS) >> 3, ly = (ty + PS) & 7;
         const int qx = (tx + PS) >> 3, lx = (tx + PS) & 7;
-        const double *src = patch_src(P, S.nbr[qx + 4 * qy + 16 * qz]);
+        const double *src = patch_src(P, S.nbr[ts][qx + 4 * qy + 16 * qz]);
         if (src) {
             const int off = lz * 64 + ly * 8 + lx;
 #pragma unroll
@@ -217,18 +220,19 @@ __device__ __forceinline__ void issue_plane(StepSmem<real> &S, const StepParams 
     cp_async_commit();
 }
 
-// Wait for this thread's copies of plane tz and convert them to primitives
-// into the ring (the CTA barrier before stage B publishes them).
+// Wait for this thread's copies of tile plane tl (group of table slot ts,
+// run plane tr) and convert them to primitives into the ring (the CTA
+// barrier before stage B publishes them).
 template <typename real>
-__device__ __forceinline__ void finish_plane(StepSmem<real> &S, int tz, const Gas<real> &g) {
+__device__ __forceinline__ void finish_plane(StepSmem<real> &S, int ts, int tl, int tr, const Gas<real> &g) {
     cp_async_wait_all();
-    const int slot = (tz + 3) % 3;
-    const int qz = (tz + PS) >> 3;
+    const int slot = (tr + 3) % 3;
+    const int qz = (tl + PS) >> 3;
     for (int j = threadIdx.x; j < TPAIRS; j += StepCfg<real>::NT) {
         const int ty = j / (TW / 2) - 2, tx = 2 * (j % (TW / 2)) - 2;
         const int qy = (ty + PS) >> 3, qx = (tx + PS) >> 3;
         real w[2][NV];
-        if (S.nbr[qx + 4 * qy + 16 * qz] != -1) {
+        if (S.nbr[ts][qx + 4 * qy + 16 * qz] != -1) {
 #pragma unroll
             for (int h = 0; h < 2; h++) {
                 real u[NV];
@@ -289,46 +293,48 @@ __device__ __forceinline__ void hancock_cell(const StepSmem<real> &S, int x, int
         for (int v = 0; v < NV; v++) uf[f][v] += dtdh_half * inc[v];
 }
 
-// Stage C face evaluations of plane z.  Thread (cx, cy) takes the x face
-// x = cx - 1/2 of row cy and the y face y = cy - 1/2 of column cx; one warp
-// also takes the group's high faces, x = 16 - 1/2 of the 16 rows (lanes
-// 0..15) and y = 16 - 1/2 of the 16 columns (lanes 16..31), in one
-// divergence-free pass through hllc_dir.  The FP64 pipe charges a whole warp
-// instruction however few lanes are active, so that pass costs one solver
-// evaluation instead of two.
+// Stage C face evaluations of plane z (local plane zl of the group in table
+// slot ts; cf: whether that group touches a coarse-fine register).  Thread
+// (cx, cy) takes the x face x = cx - 1/2 of row cy and the y face
+// y = cy - 1/2 of column cx; one warp also takes the group's high faces,
+// x = 16 - 1/2 of the 16 rows (lanes 0..15) and y = 16 - 1/2 of the 16
+// columns (lanes 16..31), in one divergence-free pass through hllc_dir.  The
+// FP64 pipe charges a whole warp instruction however few lanes are active,
+// so that pass costs one solver evaluation instead of two.
 template <typename real>
-__device__ __forceinline__ void x_face(StepSmem<real> &S, const StepParams &P, double dt, int row, int col, int z,
-                                       const Gas<real> &g) {
+__device__ __forceinline__ void x_face(StepSmem<real> &S, const StepParams &P, double dt, int row, int col, int zl,
+                                       int ts, bool cf, const Gas<real> &g) {
     real uL[NV], uR[NV], F[NV];
 #pragma unroll
     for (int v = 0; v < NV; v++) { uL[v] = S.XS[1][v][row][col]; uR[v] = S.XS[0][v][row][col + 1]; }
     face_flux<0>(uL, uR, F, g);
 #pragma unroll
     for (int v = 0; v < NV; v++) S.FX[v][row][col] = F[v];
-    if ((col & 7) == 0) {  // a patch face: x = 0 (group boundary) or x = 8
-        const int pr = (row >> 3) * 2 + (z >> 3) * 4;
-        cf_register(S, P, dt, F, 0, row, z, col == 0 ? -1 : pr, pr + (col >> 3), col == 0, false);
+    if (cf && (col & 7) == 0) {  // a patch face: x = 0 (group boundary) or x = 8
+        const int pr = (row >> 3) * 2 + (zl >> 3) * 4;
+        cf_register(S, P, dt, F, 0, row, zl, ts, col == 0 ? -1 : pr, ts, pr + (col >> 3),
+                    col == 0 ? S.cfo[ts][0] : -1LL);
     }
 }
 
 template <typename real>
-__device__ __forceinline__ void y_face(StepSmem<real> &S, const StepParams &P, double dt, int r, int col, int z,
-                                       const Gas<real> &g) {
+__device__ __forceinline__ void y_face(StepSmem<real> &S, const StepParams &P, double dt, int r, int col, int zl,
+                                       int ts, bool cf, const Gas<real> &g) {
     real uL[NV], uR[NV], F[NV];
 #pragma unroll
     for (int v = 0; v < NV; v++) { uL[v] = S.YS[1][v][r][col]; uR[v] = S.YS[0][v][r + 1][col]; }
     face_flux<1>(uL, uR, F, g);
 #pragma unroll
     for (int v = 0; v < NV; v++) S.FY[v][r][col] = F[v];
-    if ((r & 7) == 0) {  // a patch face: y = 0 (group boundary) or y = 8
-        const int pr = (col >> 3) + (z >> 3) * 4;
-        cf_register(S, P, dt, F, 1, col, z, r == 0 ? -1 : pr, pr + 2 * (r >> 3), r == 0, false);
+    if (cf && (r & 7) == 0) {  // a patch face: y = 0 (group boundary) or y = 8
+        const int pr = (col >> 3) + (zl >> 3) * 4;
+        cf_register(S, P, dt, F, 1, col, zl, ts, r == 0 ? -1 : pr, ts, pr + 2 * (r >> 3), r == 0 ? S.cfo[ts][2] : -1LL);
     }
 }
 
 template <typename real>
-__device__ __forceinline__ void high_faces(StepSmem<real> &S, const StepParams &P, double dt, int lane, int z,
-                                           const Gas<real> &g) {
+__device__ __forceinline__ void high_faces(StepSmem<real> &S, const StepParams &P, double dt, int lane, int zl,
+                                           int ts, bool cf, const Gas<real> &g) {
     const int k = lane & 15, D = lane >> 4;
     real uL[NV], uR[NV], F[NV];
 #pragma unroll
@@ -342,20 +348,32 @@ __device__ __forceinline__ void high_faces(StepSmem<real> &S, const StepParams &
         if (D == 0) S.FX[v][k][GE] = F[v];
         else S.FY[v][GE][k] = F[v];
     }
-    const int pa = D == 0 ? 1 + (k >> 3) * 2 + (z >> 3) * 4 : (k >> 3) + 2 + (z >> 3) * 4;
-    cf_register(S, P, dt, F, D, k, z, pa, -1, false, true);
+    if (cf) {
+        const int pa = D == 0 ? 1 + (k >> 3) * 2 + (zl >> 3) * 4 : (k >> 3) + 2 + (zl >> 3) * 4;
+        cf_register(S, P, dt, F, D, k, zl, ts, pa, ts, -1, S.cfo[ts][2 * D + 1]);
+    }
 }
 
-// The z face z - 1/2 below column (cx, cy): HLLC of the column's own face
-// states (registers), plus its coarse-fine registers on patch faces.
+// The z face below column (cx, cy) at run plane z (0..16 len): HLLC of the
+// column's own face states (registers), plus the coarse-fine registers of
+// patch faces.  The cell below is in run group ka, the one above in kb (the
+// same group except at a group boundary, where ka = kb - 1: two same-level
+// groups, so no fine register, but each side's coarse registers);
+// cfm: bit s set when the group in table slot s touches a register.
 template <typename real>
 __device__ __forceinline__ void z_face(const StepSmem<real> &S, const StepParams &P, double dt, const real zp_prev[NV],
-                                       const real zm[NV], int cx, int cy, int z, real fz[NV], const Gas<real> &g) {
+                                       const real zm[NV], int cx, int cy, int z, int len, unsigned cfm, real fz[NV],
+                                       const Gas<real> &g) {
     face_flux<2>(zp_prev, zm, fz, g);
-    if (z == 0 || z == GE || z == 8) {
-        const int pl = (cx >> 3) + 2 * (cy >> 3);
-        cf_register(S, P, dt, fz, 2, cx, cy, z == 0 ? -1 : pl + 4 * ((z - 1) >> 3), z == GE ? -1 : pl + 4 * (z >> 3),
-                    z == 0, z == GE);
+    if ((z & 7) == 0) {
+        const bool bot = z == 0, top = z == GE * len;
+        const int ka = bot ? 0 : (z - 1) >> 4, kb = top ? len - 1 : z >> 4;
+        if ((cfm >> (ka & 1)) & 1u || (cfm >> (kb & 1)) & 1u) {
+            const int pl = (cx >> 3) + 2 * (cy >> 3);
+            const long long fo = bot ? S.cfo[0][4] : (top ? S.cfo[(len - 1) & 1][5] : -1LL);
+            cf_register(S, P, dt, fz, 2, cx, cy, ka & 1, bot ? -1 : pl + 4 * (((z - 1) & 15) >> 3), kb & 1,
+                        top ? -1 : pl + 4 * ((z & 15) >> 3), fo);
+        }
     }
 }
 
@@ -365,58 +383,100 @@ __host__ __device__ inline int scheme_mode(int limiter, int riemann) {
     return (limiter != LIM_VANLEER || riemann != RS_HLLC) ? 1 : 0;
 }
 
-// One patch group: the whole fused step for group `grp` of P's level.  The
-// caller has set S.dt; smax_r / nbad accumulate the new state's largest
-// signal speed and its unphysical cells.
+// The tables of group grp into table slot ts; returns (per thread) whether
+// an entry this thread loaded names a coarse-fine register.
 template <typename real>
-__device__ __forceinline__ void step_group(StepSmem<real> &S, const StepParams &P, int grp, double dt,
-                                           const Gas<real> &g, real &smax_r, unsigned &nbad) {
+__device__ __forceinline__ bool load_tables(StepSmem<real> &S, const StepParams &P, int ts, int grp) {
+    const int tid = threadIdx.x;
+    bool has = false;
+    if (tid < 64) S.nbr[ts][tid] = P.nbr[(int64_t)grp * 64 + tid];
+    if (tid < 6) {
+        const long long o = P.cf.fine_off ? P.cf.fine_off[(int64_t)grp * 6 + tid] : -1;
+        S.cfo[ts][tid] = o;
+        has = o >= 0;
+    }
+    if (tid >= 64 && tid < 112) {
+        const int k = tid - 64;
+        const long long o = P.cf.coarse_off ? P.cf.coarse_off[((int64_t)grp * 8 + k / 6) * 6 + k % 6] : -1;
+        S.cco[ts][k] = o;
+        has = o >= 0;
+    }
+    return has;
+}
+
+// Group k of a run: runs[off + k], or the single group `first`.
+__device__ __forceinline__ int run_group(const int32_t *runs, int off, int first, int k) {
+    return runs ? __ldg(runs + off + k) : first;
+}
+
+// A run of len patch groups stacked in z (each the same-level group directly
+// above the previous one; len = 1: one group): the whole fused step, as one
+// continuous z-march through the run's 16 len planes, so the ghost planes two
+// neighbouring groups share are loaded and advanced by the Hancock step once.
+// Plane z of the run is local plane z - 16k of run group k.  The caller has
+// set S.dt; smax_r / nbad accumulate the new state's largest signal speed and
+// its unphysical cells.
+template <typename real>
+__device__ __forceinline__ void step_run(StepSmem<real> &S, const StepParams &P, const int32_t *runs, int off,
+                                         int first, int len, double dt, const Gas<real> &g, real &smax_r,
+                                         unsigned &nbad) {
     static_assert(StepCfg<real>::NT == COLS, "one thread per (x,y) column");
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cx = tid & 15, cy = tid >> 4;  // this thread's (x,y) column
     const double dtdh = dt / P.dh;
     const real dtdh_r = (real)dtdh;
     const real dtdh_half = (real)(0.5 * dt / P.dh);
-    if (tid < 64) S.nbr[tid] = P.nbr[(int64_t)grp * 64 + tid];
-    if (tid == 0) S.any_cf = 0;
-    __syncthreads();
-    if (tid < 6) {
-        const long long o = P.cf.fine_off ? P.cf.fine_off[(int64_t)grp * 6 + tid] : -1;
-        S.cfo[tid] = o;
-        if (o >= 0) S.any_cf = 1;
-    }
-    if (tid >= 64 && tid < 112) {
-        const int k = tid - 64;
-        const long long o = P.cf.coarse_off ? P.cf.coarse_off[((int64_t)grp * 8 + k / 6) * 6 + k % 6] : -1;
-        S.cco[k] = o;
-        if (o >= 0) S.any_cf = 1;
-    }
-    __syncthreads();
-    load_plane(S, P, -2, g);
-    load_plane(S, P, -1, g);
-    issue_plane(S, P, 0);
+    const int Z = GE * len;
+    // group ids: of the current run plane's group, of the one below it (for
+    // stage D at a group boundary) and of the next one (fetched with its tables)
+    int gcur = run_group(runs, off, first, 0), gprev = gcur, gnext = gcur;
+    unsigned cfm = 0;  // bit s: the group in table slot s touches a coarse-fine register
+    if (__syncthreads_or(load_tables(S, P, 0, gcur))) cfm = 1u;
+    load_plane(S, P, 0, -2, -2, g);
+    load_plane(S, P, 0, -1, -1, g);
+    issue_plane(S, P, 0, 0);
 
     real zp_prev[NV];   // high z face state of this column's cell at z-1
     real acc[NV];       // flux divergence of this column's cell at z-1 (minus its top z flux)
 #pragma unroll
     for (int v = 0; v < NV; v++) { zp_prev[v] = real(0); acc[v] = real(0); }
 
-    const int64_t own = (int64_t)grp * 8;
-    for (int z = -1; z <= GE; z++) {
-        finish_plane(S, z + 1, g);
-        if (z + 2 <= GE + 1) issue_plane(S, P, z + 2);
+    for (int z = -1; z <= Z; z++) {
+        {  // plane z+1 is ready to convert, plane z+2 to stage
+            const int t1 = z + 1, k1 = t1 < 0 ? 0 : min(t1 >> 4, len - 1);
+            finish_plane(S, k1 & 1, t1 - GE * k1, t1, g);
+            const int t2 = z + 2;
+            if (t2 <= Z + 1) {
+                const int k2 = min(t2 >> 4, len - 1);
+                issue_plane(S, P, k2 & 1, t2 - GE * k2);
+            }
+        }
         __syncthreads();
-        if (z >= 0 && z < GE && tid < COLS / 2) {
+        const int kz = z < 0 ? 0 : min(z >> 4, len - 1), zl = z - GE * kz;  // run group and local plane of z
+        if (zl == 0 && z > 0) {  // entering run group kz: its id was fetched with its tables
+            gprev = gcur;
+            gcur = gnext;
+        }
+        if (z >= 0 && z < Z && tid < COLS / 2) {
             // U^n of columns 2 tid, 2 tid + 1 at plane z (16-byte copies), for
             // their update in the next iteration.  Issued after the barrier: the
             // slot was last read by those columns' threads in the previous
             // iteration's stage D; the next finish_plane waits for it.
+            const int64_t own = (int64_t)gcur * 8;
             const int px = (2 * tid) & 15, py = (2 * tid) >> 4;
-            const double *src = P.U_old + (own + (px >> 3) + 2 * (py >> 3) + 4 * (z >> 3)) * PSLOT +
-                                (z & 7) * 64 + (py & 7) * 8 + (px & 7);
+            const double *src = P.U_old + (own + (px >> 3) + 2 * (py >> 3) + 4 * (zl >> 3)) * PSLOT +
+                                (zl & 7) * 64 + (py & 7) * 8 + (px & 7);
 #pragma unroll
             for (int v = 0; v < NV; v++) cp_async16(&S.uo[z & 1][v][2 * tid], src + v * PV);
             cp_async_commit();
+        }
+        // the next run group's tables, into the slot group kz - 1 used last
+        // at run plane 16 kz (its top face); first read at plane 16 kz + 14
+        const bool load_next = zl == 12 && kz + 1 < len;
+        bool has_next = false;
+        if (load_next) {
+            gnext = run_group(runs, off, first, kz + 1);
+            has_next = load_tables(S, P, (kz + 1) & 1, gnext);
         }
 
         // ---- B: Hancock states of plane z
@@ -428,8 +488,8 @@ __device__ __forceinline__ void step_group(StepSmem<real> &S, const StepParams &
             for (int v = 0; v < NV; v++) { zm[v] = uf[4][v]; zp[v] = uf[5][v]; }
             // Sub-partitions 2 and 3 (warp & 2) have no ghost-ring cells in this
             // stage: they take their z face here rather than in stage C.
-            if ((warp & 2) && z >= 0) z_face(S, P, dt, zp_prev, zm, cx, cy, z, fz, g);
-            if (z >= 0 && z < GE) {
+            if ((warp & 2) && z >= 0) z_face(S, P, dt, zp_prev, zm, cx, cy, z, len, cfm, fz, g);
+            if (z >= 0 && z < Z) {
 #pragma unroll
                 for (int v = 0; v < NV; v++) {
                     S.XS[0][v][cy][cx + 1] = uf[0][v];
@@ -439,7 +499,7 @@ __device__ __forceinline__ void step_group(StepSmem<real> &S, const StepParams &
                 }
             }
         }
-        if (z >= 0 && z < GE && tid < 64) {
+        if (z >= 0 && z < Z && tid < 64) {
             // ring cells: x = -1 / 16 (rows 0..15), then y = -1 / 16 (columns 0..15)
             const int r = tid & 15;
             const bool xring = tid < 32;
@@ -462,25 +522,33 @@ __device__ __forceinline__ void step_group(StepSmem<real> &S, const StepParams &
                 }
             }
         }
-        __syncthreads();
+        if (load_next) {  // uniform: every thread takes the same branch
+            const unsigned bit = 1u << ((kz + 1) & 1);
+            cfm = __syncthreads_or(has_next) ? (cfm | bit) : (cfm & ~bit);
+        } else {
+            __syncthreads();
+        }
 
         // ---- C: the z face below the column (sub-partitions 0, 1), its x and
         // y faces, and the group's high faces on warp 2 (sub-partition 2), so
         // every sub-partition's FP64 share carries 5 or 6 face evaluations
         // here after 3 or 2 Hancock cells (+2 z faces) in stage B
-        if (!(warp & 2) && z >= 0) z_face(S, P, dt, zp_prev, zm, cx, cy, z, fz, g);
-        if (z >= 0 && z < GE) {
-            x_face(S, P, dt, cy, cx, z, g);
-            y_face(S, P, dt, cy, cx, z, g);
-            if (warp == 2) high_faces(S, P, dt, lane, z, g);
+        if (!(warp & 2) && z >= 0) z_face(S, P, dt, zp_prev, zm, cx, cy, z, len, cfm, fz, g);
+        if (z >= 0 && z < Z) {
+            const int ts = kz & 1;
+            const bool cf = (cfm >> ts) & 1u;
+            x_face(S, P, dt, cy, cx, zl, ts, cf, g);
+            y_face(S, P, dt, cy, cx, zl, ts, cf, g);
+            if (warp == 2) high_faces(S, P, dt, lane, zl, ts, cf, g);
         }
         __syncthreads();
 
         // ---- D: finish cell (cx,cy,z-1), start cell (cx,cy,z)
         if (z >= 1) {
-            const int zc = z - 1;
-            const int64_t base = (own + (cx >> 3) + 2 * (cy >> 3) + 4 * (zc >> 3)) * PSLOT +
-                                 (zc & 7) * 64 + (cy & 7) * 8 + (cx & 7);
+            const int zc = z - 1, zcl = zc & (GE - 1);  // cell z-1: in the group below at a boundary
+            const int64_t base = ((int64_t)(zl == 0 ? gprev : gcur) * 8 + (cx >> 3) + 2 * (cy >> 3) +
+                                  4 * (zcl >> 3)) * PSLOT +
+                                 (zcl & 7) * 64 + (cy & 7) * 8 + (cx & 7);
             real ur[NV];  // the new state in the compute type, for its signal speed
 #pragma unroll
             for (int v = 0; v < NV; v++) {
@@ -503,7 +571,7 @@ __device__ __forceinline__ void step_group(StepSmem<real> &S, const StepParams &
             if (!ok) nbad++;
             if (s > smax_r) smax_r = s;
         }
-        if (z >= 0 && z < GE) {
+        if (z >= 0 && z < Z) {
 #pragma unroll
             for (int v = 0; v < NV; v++) {
                 const real dxy = (S.FX[v][cy][cx + 1] - S.FX[v][cy][cx]) +
@@ -514,7 +582,7 @@ __device__ __forceinline__ void step_group(StepSmem<real> &S, const StepParams &
 #pragma unroll
         for (int v = 0; v < NV; v++) zp_prev[v] = zp[v];
     }
-    __syncthreads();  // the next group overwrites nbr and the ring
+    __syncthreads();  // the next run overwrites the tables and the ring
 }
 
 // MODE 0: the default scheme (van Leer-type limiter, HLLC) as compile-time
@@ -562,8 +630,12 @@ __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydr
     unsigned nbad = 0;
 
     for (int wi = blockIdx.x; wi < P.n_work; wi += gridDim.x) {
-        const int grp = P.work ? P.work[wi] : P.work0 + wi;
-        step_group(S, P, grp, dt, g, smax_r, nbad);
+        if (P.run_off) {
+            const int o = __ldg(P.run_off + wi);
+            step_run(S, P, P.runs, o, 0, __ldg(P.run_off + wi + 1) - o, dt, g, smax_r, nbad);
+        } else {
+            step_run(S, P, (const int32_t *)nullptr, 0, P.work ? P.work[wi] : P.work0 + wi, 1, dt, g, smax_r, nbad);
+        }
     }
 
     // ---- block reduction of the signal speed, one atomic per block
@@ -678,7 +750,7 @@ __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydr
         P.cf.coarse_buf = nullptr;
         real smax_r = real(0);
         unsigned nbad = 0;
-        step_group(S, P, it.y, S.dt, g, smax_r, nbad);
+        step_run(S, P, (const int32_t *)nullptr, 0, it.y, 1, S.dt, g, smax_r, nbad);
         // this group's largest signal speed and unphysical count into its box
         double smax = (double)smax_r;
 #pragma unroll
