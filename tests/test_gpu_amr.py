@@ -101,3 +101,41 @@ def test_amr_run_to_run_bitwise():
         H.close()
     for a, b in zip(*outs):
         assert np.array_equal(a, b)
+
+
+def test_full_size_amr_root_step():
+    """The benchmark's 3-level AMR workload (128^3 root, blobs of contrast 100
+    at Mach 2, theta 0.1, N_buf 8/4) in its launch configuration: one root
+    step.  The root level's own step is a uniform step of the whole root grid
+    (the cells under refined patches are then overwritten by restriction and
+    the leaf cells next to refined patches get the fix-up), so every root
+    patch whose 27-patch neighbourhood holds no refined patch matches the
+    oracle's uniform 128^3 step with the root dt (1e-12); and the composite
+    conserved sums hold to round-off across the W-cycle, fix-up and regrid."""
+    import oracle
+    from paper_1712_07070_b300.amr import AmrHierarchy
+    U0 = ics.blobs(128, seed=3)
+    H = AmrHierarchy(U0, lmax=2, theta=0.1, nbuf=(8, 4), prec=A.AMR_FP64, max_patches=120000)
+    assert H.n_patches(2) > 0
+    s0 = H.conserved_total()
+    H.advance_root()
+    s1 = H.conserved_total()
+    scale = np.abs(U0).reshape(5, -1).sum(1) / 128 ** 3
+    assert (np.abs(s1 - s0) <= 1e-13 * scale).all(), (s1 - s0) / scale
+    dt0 = H.time(0)
+    ref, nbad = oracle.step_periodic(U0, 1.0 / 128, dt0, G53)
+    assert nbad == 0
+    n0 = H.n_patches(0)
+    corner = H.corners(0)
+    sib = H.tables[0][1][:n0].cpu().numpy()
+    child = H.tables[0][3][:n0].cpu().numpy()
+    U = H.state(0).cpu().numpy()
+    far = (child < 0) & (child[sib] < 0).all(axis=1)
+    assert far.sum() > n0 // 4 and (~far).sum() > 0
+    worst = 0.0
+    for s in np.nonzero(far)[0]:
+        x, y, z = corner[s]
+        r = ref[:, z:z + 8, y:y + 8, x:x + 8]
+        worst = max(worst, (np.abs(U[s] - r).reshape(5, -1).max(1) / scale).max())
+    assert worst <= 1e-12, worst
+    H.close()

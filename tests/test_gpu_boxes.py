@@ -72,3 +72,33 @@ def test_boxes_run_to_run_bitwise():
         B.close()
     for a, b in zip(*res):
         assert np.array_equal(a, b)
+
+
+def test_full_size_batch_in_the_benchmark_launch():
+    """The benchmark's batch (64 KH boxes of seeded sizes {32..192}^3, FP32
+    mode, one persistent autotuned launch per step, CUDA graph): after two
+    steps every box of edge <= 48 matches the oracle (1e-5), and every box
+    conserves mass, momentum and energy to FP32 round-off of its fluxes."""
+    import torch
+    from paper_1712_07070_b300.boxes import BoxBatch
+    sizes = ics.kh_batch_sizes(64, seed=4)
+    B = BoxBatch(gamma=G14, prec=A.AMR_FP32_ACC64)
+    U0 = [ics.kh_box(n, seed=100 + i, gamma=G14) for i, n in enumerate(sizes)]
+    for U in U0:
+        B.add_box(U)
+    B.advance(2)
+    torch.cuda.synchronize()
+    checked = 0
+    for i, n in enumerate(sizes):
+        out = B.download(i)
+        s0 = U0[i].reshape(5, -1).sum(1)
+        s1 = out.reshape(5, -1).sum(1)
+        l1 = np.abs(U0[i]).reshape(5, -1).sum(1)
+        assert (np.abs(s1 - s0) <= 1e-6 * np.maximum(l1, l1[0])).all(), (n, s1 - s0)
+        if n <= 48:
+            ref, _ = oracle.run_periodic(U0[i], 1.0 / n, G14, 0.5, 2)
+            err = rel_l1(out, ref)
+            assert (err <= 1e-5).all(), (n, err)
+            checked += 1
+    assert checked > 0
+    B.close()

@@ -2,10 +2,12 @@
 with the copies overlapped by z-slabs must give bitwise the results of the
 device path (upload, amr_hydro_advance_level, download), for a given dt, for
 the CFL dt of the input, chained through the returned dt, and in place; it
-rejects a level that is not the whole root grid in the uniform order."""
+rejects a level that is not the whole root grid in the uniform order; at the
+benchmark's 512^3 size, sampled cells match the oracle."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1712_07070_b300 import amr_hydro as A
 from paper_1712_07070_b300 import ics
 from paper_1712_07070_b300.uniform import UniformGrid
@@ -99,3 +101,27 @@ def test_rejects_non_uniform_order():
         A.amr_hydro_advance_host(ctx, hin, pinned(np.zeros(hin.shape)), 1e-3)
     assert e.value.status == A.AMR_E_INVAL
     A.amr_hydro_destroy(ctx)
+
+
+def test_full_size_512_host_stream_sampled_cells():
+    """The end-to-end path of the benchmark (512^3 turbulence, host buffers,
+    z-slab overlap) in its launch configuration: 32 sampled cells of the
+    host result recomputed one by one by the oracle on their periodic 9^3
+    neighbourhood (the step's domain of dependence is +-2 cells)."""
+    from test_gpu_uniform import subcube
+    n = 512
+    U0 = ics.turbulence(n, seed=1)
+    dt = oracle.dt_cfl2(U0, 5.0 / 3.0, 0.5, 1.0 / n)
+    g = UniformGrid((n, n, n))
+    a, b = pinned(U0), pinned(np.empty_like(U0))
+    dt_next = g.step_host(a, b, dt)
+    assert dt_next > 0
+    out = b.numpy()
+    rng = np.random.default_rng(3)
+    cells = rng.integers(0, n, size=(32, 3))
+    cells[:4] = [[0, 0, 0], [n - 1, n - 1, n - 1], [5, 9, 15], [100, 200, 16]]  # incl. slab boundaries
+    for c in cells:
+        r, _ = oracle.step_periodic(subcube(U0, c, 4), 1.0 / n, dt, 5.0 / 3.0)
+        scale = np.abs(U0[:, c[2], c[1], c[0]]).max()
+        assert np.abs(out[:, c[2], c[1], c[0]] - r[:, 4, 4, 4]).max() <= 1e-12 * scale, c
+    g.close()
