@@ -38,6 +38,7 @@ def lib():
         L.or_roe.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_double, _dp]
         L.or_exact_flux.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_double, _dp]
         L.or_set_scheme.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double]
+        L.or_set_vl.argtypes = [ctypes.c_int]
         for name in ("or_gminmod", "or_vl_gminmod"):
             getattr(L, name).argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
             getattr(L, name).restype = ctypes.c_double
@@ -109,17 +110,19 @@ LIM_VANLEER, LIM_GMINMOD, LIM_ALBADA, LIM_VL_GMINMOD = 0, 1, 2, 3
 RS_HLLC, RS_HLLE, RS_ROE, RS_EXACT = 0, 1, 2, 3
 
 
-def set_scheme(limiter=LIM_VANLEER, riemann=RS_HLLC, theta=1.5):
-    """Select the slope limiter, the Riemann solver and the generalized
-    minmod coefficient of every later oracle step (process-wide)."""
+def set_scheme(limiter=LIM_VANLEER, riemann=RS_HLLC, theta=1.5, vl=False):
+    """Select the slope limiter, the Riemann solver, the generalized minmod
+    coefficient and the VL half step (else MUSCL-Hancock's) of every later
+    oracle step (process-wide)."""
     lib().or_set_scheme(limiter, riemann, theta)
+    lib().or_set_vl(1 if vl else 0)
 
 
 class scheme:
     """Context manager: a scheme for the steps inside, the default after."""
 
-    def __init__(self, limiter=LIM_VANLEER, riemann=RS_HLLC, theta=1.5):
-        self.args = (limiter, riemann, theta)
+    def __init__(self, limiter=LIM_VANLEER, riemann=RS_HLLC, theta=1.5, vl=False):
+        self.args = (limiter, riemann, theta, vl)
 
     def __enter__(self):
         set_scheme(*self.args)

@@ -44,6 +44,13 @@
  *     solver below), transverse velocities from the contact's upwind side.
  * or_set_scheme selects them; the default is van Leer-type + HLLC.
  *
+ * Scheme (section 2.2 lists the VL variant of MUSCL-Hancock, after Falle 1991
+ * and van Leer 2006); reading: a half step with the Riemann fluxes of the
+ * cell averages, U* = U^n - (dt/2dh) sum_d [F(U_i, U_i+1) - F(U_i-1, U_i)];
+ * the selected limiter's PLM reconstruction of W(U*) to face states
+ * W* -/+ (1/2) dW* (no further evolution); the full step with the Riemann fluxes
+ * of those face states.  or_set_vl(1) selects it for every later step.
+ *
  * Every per-cell loop is independent, so the OpenMP static split changes no
  * result: the oracle is bitwise reproducible for any thread count (the
  * paper's section 2.7.1 property).
@@ -117,8 +124,10 @@ double or_vanleer(double a, double b) {
 /* limiter: 0 van Leer-type, 1 generalized minmod, 2 van Albada-type,
  * 3 hybrid generalized minmod / van Leer-type; riemann: 0 HLLC, 1 HLLE;
  * theta: the generalized minmod coefficient. */
-static int or_limiter_id = 0, or_riemann_id = 0;
+static int or_limiter_id = 0, or_riemann_id = 0, or_vl = 0;
 static double or_theta = 1.5;
+
+void or_set_vl(int on) { or_vl = on; }
 
 void or_set_scheme(int limiter, int riemann, double theta) {
     or_limiter_id = limiter;
@@ -402,11 +411,42 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
      * of the cell along d (i.e. at i+1/2) */
     double *FX = (double *)malloc(sizeof(double) * 3 * NV * n);
 
-    /* 1. primitives */
+    /* 1. primitives (VL: of the half-step state U* from the Riemann fluxes
+     *    of the cell averages) */
+    double *Uh = NULL;
+    if (or_vl) {
+        Uh = (double *)malloc(sizeof(double) * NV * n);
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < nz; z++)
+            for (int y = 0; y < ny; y++)
+                for (int x = 0; x < nx; x++) {
+                    int c[3] = {x, y, z};
+                    int64_t i = cell_index(x, y, z, nx, ny);
+                    double ui[NV], div[NV] = {0, 0, 0, 0, 0};
+                    for (int v = 0; v < NV; v++) ui[v] = U[v * n + i];
+                    for (int d = 0; d < 3; d++) {
+                        int cm[3] = {c[0], c[1], c[2]}, cp[3] = {c[0], c[1], c[2]};
+                        cm[d] = wrap(c[d] - 1, dims[d]);
+                        cp[d] = wrap(c[d] + 1, dims[d]);
+                        int64_t im = cell_index(cm[0], cm[1], cm[2], nx, ny);
+                        int64_t ip = cell_index(cp[0], cp[1], cp[2], nx, ny);
+                        double um[NV], up[NV], Fm[NV], Fp[NV];
+                        for (int v = 0; v < NV; v++) {
+                            um[v] = U[v * n + im];
+                            up[v] = U[v * n + ip];
+                        }
+                        or_riemann(um, ui, d, gamma, Fm);
+                        or_riemann(ui, up, d, gamma, Fp);
+                        for (int v = 0; v < NV; v++) div[v] += Fp[v] - Fm[v];
+                    }
+                    for (int v = 0; v < NV; v++) Uh[v * n + i] = ui[v] - 0.5 * dt / dh * div[v];
+                }
+    }
+    const double *Ur = or_vl ? Uh : U;
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
         double u[NV], w[NV];
-        for (int v = 0; v < NV; v++) u[v] = U[v * n + i];
+        for (int v = 0; v < NV; v++) u[v] = Ur[v * n + i];
         or_prim(u, w, gamma);
         for (int v = 0; v < NV; v++) W[v * n + i] = w[v];
     }
@@ -433,6 +473,11 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
                     }
                 }
                 for (int f = 0; f < 6; f++) or_cons(Wf[f], Uf[f], gamma);
+                if (or_vl) { /* the face states are already at the half step */
+                    for (int f = 0; f < 6; f++)
+                        for (int v = 0; v < NV; v++) FS[((int64_t)f * NV + v) * n + i] = Uf[f][v];
+                    continue;
+                }
                 double inc[NV] = {0, 0, 0, 0, 0};
                 for (int d = 0; d < 3; d++) {
                     double Fm[NV], Fp[NV];
@@ -493,6 +538,7 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
             }
 
     if (FX_out) memcpy(FX_out, FX, sizeof(double) * 3 * NV * n);
+    free(Uh);
     free(W);
     free(FS);
     free(FX);
