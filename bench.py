@@ -311,19 +311,23 @@ def _events(torch):
 def bench_schemes(torch, A, UniformGrid, stream, K, W, world):
     """The other slope limiters and Riemann solvers of section 2.2 (HLLE for
     every limiter; Roe and the exact solver with the van Leer-type limiter)
-    on the 256^3 turbulence level, the default van Leer-type + HLLC for
+    and the VL scheme (van Leer-type with HLLC and with HLLE) on the 256^3
+    turbulence level, the default MUSCL-Hancock van Leer-type + HLLC for
     reference: cells/s per precision."""
     from paper_1712_07070_b300 import ics
     U1 = ics.turbulence(256, seed=1)
     names = {A.AMR_LIM_VANLEER: "van Leer", A.AMR_LIM_GMINMOD: "generalized minmod 1.5",
              A.AMR_LIM_ALBADA: "van Albada", A.AMR_LIM_VL_GMINMOD: "hybrid van Leer/minmod 1.5"}
     out = []
-    combos = [(lim, rs) for lim in names for rs in (A.AMR_RS_HLLC, A.AMR_RS_HLLE)]
-    combos += [(A.AMR_LIM_VANLEER, A.AMR_RS_ROE), (A.AMR_LIM_VANLEER, A.AMR_RS_EXACT)]
+    MH, VL = A.AMR_SCHEME_MH, A.AMR_SCHEME_VL
+    combos = [(lim, rs, MH) for lim in names for rs in (A.AMR_RS_HLLC, A.AMR_RS_HLLE)]
+    combos += [(A.AMR_LIM_VANLEER, A.AMR_RS_ROE, MH), (A.AMR_LIM_VANLEER, A.AMR_RS_EXACT, MH)]
+    combos += [(A.AMR_LIM_VANLEER, A.AMR_RS_HLLC, VL), (A.AMR_LIM_VANLEER, A.AMR_RS_HLLE, VL)]
     rnames = {A.AMR_RS_HLLC: "HLLC", A.AMR_RS_HLLE: "HLLE", A.AMR_RS_ROE: "Roe", A.AMR_RS_EXACT: "exact"}
-    for lim, rs in combos:
-        sch = {"limiter": lim, "riemann": rs, "minmod_coeff": 1.5}
-        row = {"workload": "turbulence 256^3", "limiter": names[lim], "riemann": rnames[rs]}
+    for lim, rs, scheme in combos:
+        sch = {"limiter": lim, "riemann": rs, "minmod_coeff": 1.5, "scheme": scheme}
+        row = {"workload": "turbulence 256^3", "scheme": "VL" if scheme == VL else "MUSCL-Hancock",
+               "limiter": names[lim], "riemann": rnames[rs]}
         for prec, key in ((A.AMR_FP64, "f64"), (A.AMR_FP32_ACC64, "fp32_acc64")):
             r = run_case(torch, A, UniformGrid, U1, 256, prec, K, W, stream, want_e2e=False, scheme=sch)
             ms = max_over_ranks(r["region_ms"], "cuda") / K

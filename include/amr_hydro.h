@@ -74,6 +74,15 @@ typedef enum {
     AMR_RS_EXACT = 3  /* exact solver (Newton on the star pressure): Godunov flux at x/t = 0 */
 } amr_riemann;
 
+/* Integration scheme of the hydro step (section 2.2). */
+typedef enum {
+    AMR_SCHEME_MH = 0, /* MUSCL-Hancock: data-reconstructed half step (the default) */
+    AMR_SCHEME_VL = 1  /* VL: half step U* = U^n - dt/(2 dh) sum_d (F_{d,+} - F_{d,-}) from the
+                          Riemann fluxes of the cell averages, then the Riemann fluxes of the
+                          limited piecewise-linear face states of U* update U^n.  Single-level
+                          grids only: uniform levels (lmax = 0) and the batched boxes. */
+} amr_scheme;
+
 /* Run parameters (section 2.1 and 2.6 symbols). */
 typedef struct {
     double gamma;        /* adiabatic index */
@@ -90,6 +99,7 @@ typedef struct {
     int limiter;         /* amr_limiter (0: van Leer-type) */
     int riemann;         /* amr_riemann (0: HLLC) */
     double minmod_coeff; /* generalized minmod coefficient in [1, 2]; 0 means 1.5 */
+    int scheme;          /* amr_scheme (0: MUSCL-Hancock); AMR_SCHEME_VL needs lmax = 0 */
 } amr_hydro_params;
 
 typedef struct amr_hydro_ctx amr_hydro_ctx; /* opaque, library-owned */
@@ -97,7 +107,9 @@ typedef struct amr_hydro_ctx amr_hydro_ctx; /* opaque, library-owned */
 /* Create a context bound to the current CUDA device and to cuda_stream
  * (a cudaStream_t, NULL for the legacy default stream).  Rejects gamma<=1,
  * cfl<=0, lmax outside 0..7, root_n not a positive multiple of 16,
- * max_patches not a positive multiple of 8, non-periodic boundaries. */
+ * max_patches not a positive multiple of 8, non-periodic boundaries, a
+ * limiter, riemann or scheme value outside its enum, minmod_coeff neither 0
+ * nor in [1, 2], and AMR_SCHEME_VL with lmax > 0. */
 amr_status amr_hydro_init(const amr_hydro_params *params, void *cuda_stream,
                           amr_hydro_ctx **out);
 

@@ -520,8 +520,9 @@ extern "C" amr_status amr_hydro_step_adjoint(amr_hydro_ctx *c, int level, double
                                              const double *lam_np1, double *lam_n) {
     if (!c || level < 0 || level > c->prm.lmax || !U_n || !lam_np1 || !lam_n) return AMR_E_INVAL;
     if (!(dt >= 0.0)) return AMR_E_INVAL;
-    // the hand-written reverse covers the van Leer-type limiter and HLLC
-    if (c->prm.limiter != AMR_LIM_VANLEER || c->prm.riemann != AMR_RS_HLLC) return AMR_E_INVAL;
+    // the hand-written reverse covers MUSCL-Hancock with the van Leer-type limiter and HLLC
+    if (c->prm.limiter != AMR_LIM_VANLEER || c->prm.riemann != AMR_RS_HLLC || c->prm.scheme != AMR_SCHEME_MH)
+        return AMR_E_INVAL;
     Level &L = c->lv[level];
     const int nx = c->prm.root_n[0] << level, ny = c->prm.root_n[1] << level, nz = c->prm.root_n[2] << level;
     const int64_t n = (int64_t)nx * ny * nz;

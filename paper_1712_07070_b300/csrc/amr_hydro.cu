@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <utility>
 #include <vector>
 
 #include "amr_hydro.h"
@@ -66,45 +67,62 @@ size_t step_smem_bytes(int prec) {
     return prec == AMR_FP64 ? sizeof(StepSmem<double>) : sizeof(StepSmem<float>);
 }
 
-template <typename real, int MODE>
+// Kernel instances: key K = MODE + 3 STAGE (scheme_mode of the limiter and
+// solver; ST_MH, ST_VL_PRED or ST_VL_CORR).
+using StepKeys = std::make_integer_sequence<int, 9>;
+
+template <typename real, int K>
 static amr_status set_step_smem() {
-    return cuda_fail(cudaFuncSetAttribute(k_hydro_step<real, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cuda_fail(cudaFuncSetAttribute(k_hydro_step<real, K % 3, K / 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)sizeof(StepSmem<real>)),
                      "step kernel smem attribute");
+}
+template <typename real, int... K>
+static amr_status set_step_smem_all(std::integer_sequence<int, K...>) {
+    amr_status st = AMR_OK;
+    ((st = st ? st : set_step_smem<real, K>()), ...);
+    return st;
 }
 
 amr_status configure_kernels() {
     static bool done = false;
     if (done) return AMR_OK;
     amr_status st;
-    if ((st = set_step_smem<double, 0>()) || (st = set_step_smem<double, 1>()) || (st = set_step_smem<double, 2>()) ||
-        (st = set_step_smem<float, 0>()) || (st = set_step_smem<float, 1>()) || (st = set_step_smem<float, 2>()))
-        return st;
+    if ((st = set_step_smem_all<double>(StepKeys{})) || (st = set_step_smem_all<float>(StepKeys{}))) return st;
     done = true;
     return AMR_OK;
 }
 
-template <typename real>
-static int step_occupancy() {
-    int a = 0, b = 0, c = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_hydro_step<real, 0>, StepCfg<real>::NT, sizeof(StepSmem<real>));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_hydro_step<real, 1>, StepCfg<real>::NT, sizeof(StepSmem<real>));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_hydro_step<real, 2>, StepCfg<real>::NT, sizeof(StepSmem<real>));
-    int n = a < b ? a : b;
-    n = n < c ? n : c;
+template <typename real, int K>
+static int step_occupancy_k() {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hydro_step<real, K % 3, K / 3>, StepCfg<real>::NT,
+                                                  sizeof(StepSmem<real>));
+    return n;
+}
+template <typename real, int... K>
+static int step_occupancy(std::integer_sequence<int, K...>) {
+    int n = 1 << 20;
+    ((n = std::min(n, step_occupancy_k<real, K>())), ...);
     return n > 0 ? n : 1;
 }
 
 // Number of resident step CTAs per SM, for sizing a persistent grid.
-int step_blocks_per_sm(int prec) { return prec == AMR_FP64 ? step_occupancy<double>() : step_occupancy<float>(); }
+int step_blocks_per_sm(int prec) {
+    return prec == AMR_FP64 ? step_occupancy<double>(StepKeys{}) : step_occupancy<float>(StepKeys{});
+}
 
+template <typename real, int K>
+static void launch_step_one(const StepParams &P, int grid, cudaStream_t s) {
+    k_hydro_step<real, K % 3, K / 3><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(P);
+}
+template <typename real, int... K>
+static void launch_step_key(int key, const StepParams &P, int grid, cudaStream_t s, std::integer_sequence<int, K...>) {
+    ((key == K ? launch_step_one<real, K>(P, grid, s) : void()), ...);
+}
 template <typename real>
 static void launch_step_k(const StepParams &P, int grid, cudaStream_t s) {
-    switch (scheme_mode(P.limiter, P.riemann)) {
-        case 0: k_hydro_step<real, 0><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(P); break;
-        case 1: k_hydro_step<real, 1><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(P); break;
-        default: k_hydro_step<real, 2><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(P); break;
-    }
+    launch_step_key<real>(scheme_mode(P.limiter, P.riemann) + 3 * P.stage, P, grid, s, StepKeys{});
 }
 
 amr_status launch_step(amr_hydro_ctx *c, const StepParams &P, int grid) {
@@ -216,6 +234,10 @@ amr_status amr_hydro_init(const amr_hydro_params *p, void *stream, amr_hydro_ctx
     if (p->limiter < AMR_LIM_VANLEER || p->limiter > AMR_LIM_VL_GMINMOD) return AMR_E_INVAL;
     if (p->riemann < AMR_RS_HLLC || p->riemann > AMR_RS_EXACT) return AMR_E_INVAL;
     if (p->minmod_coeff != 0.0 && !(p->minmod_coeff >= 1.0 && p->minmod_coeff <= 2.0)) return AMR_E_INVAL;
+    if (p->scheme != AMR_SCHEME_MH && p->scheme != AMR_SCHEME_VL) return AMR_E_INVAL;
+    // VL on refined levels would need the half-step state in a 3-cell ring of
+    // the coarse-fine ghost patches: single-level grids only
+    if (p->scheme == AMR_SCHEME_VL && p->lmax > 0) return AMR_E_INVAL;
     for (int d = 0; d < 3; d++) {
         if (p->root_n[d] <= 0 || p->root_n[d] % 16) return AMR_E_INVAL;
         if (!p->periodic[d]) return AMR_E_INVAL;

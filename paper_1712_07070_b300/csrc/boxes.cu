@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "amr_hydro.h"
@@ -25,51 +26,71 @@ namespace {
 
 bool configured = false;
 
-template <typename real, int MODE>
+// Kernel instances: key K = MODE + 3 STAGE, as for the level step kernel.
+using BoxKeys = std::make_integer_sequence<int, 9>;
+
+template <typename real, int K>
 amr_status set_box_smem() {
-    return cuda_fail(cudaFuncSetAttribute(k_hydro_step_boxes<real, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)sizeof(StepSmem<real>)),
+    return cuda_fail(cudaFuncSetAttribute(k_hydro_step_boxes<real, K % 3, K / 3>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(StepSmem<real>)),
                      "box kernel smem attribute");
+}
+template <typename real, int... K>
+amr_status set_box_smem_all(std::integer_sequence<int, K...>) {
+    amr_status st = AMR_OK;
+    ((st = st ? st : set_box_smem<real, K>()), ...);
+    return st;
 }
 
 amr_status configure_box_kernels() {
     if (configured) return AMR_OK;
     amr_status st;
-    if ((st = set_box_smem<double, 0>()) || (st = set_box_smem<double, 1>()) || (st = set_box_smem<double, 2>()) ||
-        (st = set_box_smem<float, 0>()) || (st = set_box_smem<float, 1>()) || (st = set_box_smem<float, 2>()))
-        return st;
+    if ((st = set_box_smem_all<double>(BoxKeys{})) || (st = set_box_smem_all<float>(BoxKeys{}))) return st;
     configured = true;
     return AMR_OK;
 }
 
-template <typename real>
-int box_occupancy() {
-    int a = 0, b = 0, c = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_hydro_step_boxes<real, 0>, StepCfg<real>::NT, sizeof(StepSmem<real>));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_hydro_step_boxes<real, 1>, StepCfg<real>::NT, sizeof(StepSmem<real>));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_hydro_step_boxes<real, 2>, StepCfg<real>::NT, sizeof(StepSmem<real>));
-    int n = a < b ? a : b;
-    n = n < c ? n : c;
+template <typename real, int K>
+int box_occupancy_k() {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hydro_step_boxes<real, K % 3, K / 3>, StepCfg<real>::NT,
+                                                  sizeof(StepSmem<real>));
+    return n;
+}
+template <typename real, int... K>
+int box_occupancy(std::integer_sequence<int, K...>) {
+    int n = 1 << 20;
+    ((n = std::min(n, box_occupancy_k<real, K>())), ...);
     return n > 0 ? n : 1;
 }
 
-int resident_per_sm(int prec) { return prec == AMR_FP64 ? box_occupancy<double>() : box_occupancy<float>(); }
-
-template <typename real>
-void launch_boxes_k(const BoxLaunch &B, int grid, cudaStream_t s) {
-    switch (scheme_mode(B.limiter, B.riemann)) {
-        case 0: k_hydro_step_boxes<real, 0><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(B); break;
-        case 1: k_hydro_step_boxes<real, 1><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(B); break;
-        default: k_hydro_step_boxes<real, 2><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(B); break;
-    }
+int resident_per_sm(int prec) {
+    return prec == AMR_FP64 ? box_occupancy<double>(BoxKeys{}) : box_occupancy<float>(BoxKeys{});
 }
 
+template <typename real, int K>
+void launch_boxes_one(const BoxLaunch &B, int grid, cudaStream_t s) {
+    k_hydro_step_boxes<real, K % 3, K / 3><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(B);
+}
+template <typename real, int... K>
+void launch_boxes_key(int key, const BoxLaunch &B, int grid, cudaStream_t s, std::integer_sequence<int, K...>) {
+    ((key == K ? launch_boxes_one<real, K>(B, grid, s) : void()), ...);
+}
+
+// One step of the batch: one launch (MUSCL-Hancock) or the VL predictor and
+// corrector launches.
 amr_status launch_boxes(amr_hydro_ctx *c, const BoxLaunch &B, int grid, cudaStream_t s) {
-    if (c->prm.prec == AMR_FP64)
-        launch_boxes_k<double>(B, grid, s);
-    else
-        launch_boxes_k<float>(B, grid, s);
-    return cuda_fail(cudaGetLastError(), "k_hydro_step_boxes");
+    const int mode = scheme_mode(B.limiter, B.riemann);
+    const bool vl = c->prm.scheme == AMR_SCHEME_VL;
+    for (int stage : vl ? std::vector<int>{ST_VL_PRED, ST_VL_CORR} : std::vector<int>{ST_MH}) {
+        if (c->prm.prec == AMR_FP64)
+            launch_boxes_key<double>(mode + 3 * stage, B, grid, s, BoxKeys{});
+        else
+            launch_boxes_key<float>(mode + 3 * stage, B, grid, s, BoxKeys{});
+        amr_status st = cuda_fail(cudaGetLastError(), "k_hydro_step_boxes");
+        if (st) return st;
+    }
+    return AMR_OK;
 }
 
 __global__ void k_zero_box_out(BoxDesc *desc, int n) {
@@ -127,6 +148,7 @@ amr_status amr_hydro_set_box(amr_hydro_ctx *c, int box_id, int n, double *U_a, d
     const int cells[3] = {n, n, n};
     if ((st = build_nbr_plan(0, (int)npatch, corner.data(), sib.data(), nullptr, cells, nbr, ghosts))) return st;
     if ((st = B.nbr.reserve(nbr.size()))) return st;
+    if (c->prm.scheme == AMR_SCHEME_VL && (st = B.ustar.reserve((size_t)npatch * PSLOT))) return st;
     if ((st = cuda_fail(cudaMemcpy(B.nbr.p, nbr.data(), 4 * nbr.size(), cudaMemcpyHostToDevice), "h2d"))) return st;
     if ((st = cuda_fail(cudaMemset(c->scal.p + SCAL_BOX0 + SCAL_PER * box_id, 0, 8 * SCAL_PER), "memset"))) return st;
     B.n = n;
@@ -191,6 +213,7 @@ amr_status amr_hydro_advance_boxes(amr_hydro_ctx *c, int n_boxes, const int *box
         Box &B = c->boxes[ids[i]];
         desc[i].U[0] = B.U[0];
         desc[i].U[1] = B.U[1];
+        desc[i].ustar = B.ustar.p;
         desc[i].nbr = B.nbr.p;
         desc[i].scal = c->scal.p + SCAL_BOX0 + SCAL_PER * ids[i];
         desc[i].dh = 1.0 / B.n;

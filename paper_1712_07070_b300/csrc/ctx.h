@@ -50,6 +50,7 @@ struct Level {
     DevBuf<int32_t> nbr;        // [n_groups][64]
     DevBuf<int32_t> runs, run_off;  // z-runs of groups (step work items), see build_runs
     int n_runs = 0;
+    DevBuf<double> ustar;       // VL half-step state, [n_patches][5][512]
     DevBuf<double> ghost;       // [n_ghost][5][512]
     DevBuf<int32_t> ghost_info; // [n_ghost][GHOST_INFO]
     int n_ghost = 0;
@@ -73,6 +74,7 @@ struct Level {
     bool uniform = false;  // level 0 holding the whole root grid in the order of amr_hydro_uniform_tables
     void release() {
         nbr.release();
+        ustar.release();
         runs.release();
         run_off.release();
         n_runs = 0;
@@ -95,7 +97,12 @@ struct Box {
     int ring = 0;
     bool speed_valid = false;
     DevBuf<int32_t> nbr;
-    void release() { nbr.release(); n = 0; }
+    DevBuf<double> ustar;  // VL half-step state
+    void release() {
+        nbr.release();
+        ustar.release();
+        n = 0;
+    }
 };
 
 // Launch configuration of the box-batch kernel chosen by the autotuner.

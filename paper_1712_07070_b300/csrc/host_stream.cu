@@ -4,7 +4,10 @@
 // solver through CUDA streams; here the batches are z-slabs of patch groups
 // (16 cell planes each, contiguous in the group order), the state stays on the
 // device between the transfers, and the step of slab k waits only for the
-// slabs it reads (k-1, k, k+1, periodic).
+// slabs it reads (k-1, k, k+1, periodic).  With the VL scheme the predictor
+// of slab k waits for the uploads of k-1..k+1 and the corrector of slab k for
+// the predictors of k-1..k+1; the correctors run in the order 1, ..., ns-1, 0,
+// so the first starts after the first four uploads.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -127,10 +130,36 @@ extern "C" amr_status amr_hydro_advance_host(amr_hydro_ctx *c, const double *U_i
     P.cf.coarse_buf = L.creg.p;
     const int cap = c->n_sm * c->step_bps;
     const int grid = G < cap ? G : cap;
-    for (int k = 0; k < ns; k++) {
-        if ((st = pack((k + ns - 1) % ns)) || (st = pack(k)) || (st = pack((k + 1) % ns))) return st;
+    const bool vl = c->prm.scheme == AMR_SCHEME_VL;
+    std::vector<char> predicted(ns, 0);
+    StepParams H = P;  // the VL predictor: U^n -> U*, no reductions, no time record
+    H.stage = ST_VL_PRED;
+    H.U_new = L.ustar.p;
+    H.smax_out = H.n_bad = H.clear2 = nullptr;
+    H.time_rec = nullptr;
+    H.cf = CFRegs{nullptr, nullptr, nullptr, nullptr};
+    auto predict = [&](int j) -> amr_status {  // VL half step of slab j
+        if (predicted[j]) return AMR_OK;
+        predicted[j] = 1;
+        amr_status s2;
+        if ((s2 = pack((j + ns - 1) % ns)) || (s2 = pack(j)) || (s2 = pack((j + 1) % ns))) return s2;
+        H.work0 = j * G;
+        return launch_step(c, H, grid);
+    };
+    if (vl) {
+        P.stage = ST_VL_CORR;
+        P.U_base = Uold;
+        P.U_old = L.ustar.p;
+    }
+    for (int i = 0; i < ns; i++) {
+        const int k = vl ? (i + 1) % ns : i;
+        if (vl) {
+            if ((st = predict((k + ns - 1) % ns)) || (st = predict(k)) || (st = predict((k + 1) % ns))) return st;
+        } else if ((st = pack((k + ns - 1) % ns)) || (st = pack(k)) || (st = pack((k + 1) % ns))) {
+            return st;
+        }
         P.work0 = k * G;
-        P.time_rec = k == 0 ? c->dtbuf.p : nullptr;  // the level's time advances once
+        P.time_rec = i == 0 ? c->dtbuf.p : nullptr;  // the level's time advances once
         if ((st = launch_step(c, P, grid))) return st;
         k_pack_slab<<<c->n_sm * 4, 256, 0, cs>>>(c->hstage[1].p, nx, ny, nz, k * GE, Unew, 0);
         if ((st = cuda_fail(cudaGetLastError(), "k_unpack_slab"))) return st;

@@ -97,6 +97,7 @@ amr_status amr_hydro_set_level(amr_hydro_ctx *c, int level, int n_patches, doubl
         }
         L.uniform = ok;
     }
+    if (c->prm.scheme == AMR_SCHEME_VL && (st = L.ustar.reserve((size_t)n_patches * PSLOT))) return st;
     if ((st = plan_level(c, level))) return st;
     if (level > 0 && (st = rebuild_cf(c, level))) return st;
     if (level < c->prm.lmax && c->lv[level + 1].n_patches && (st = rebuild_cf(c, level + 1))) return st;
@@ -163,6 +164,18 @@ amr_status amr_hydro_advance_level(amr_hydro_ctx *c, int level, double dt, int64
     }
     const int cap = c->n_sm * c->step_bps;
     const int grid = P.n_work < cap ? P.n_work : cap;
+    if (c->prm.scheme == AMR_SCHEME_VL) {  // predictor into U*, then the corrector
+        StepParams H = P;
+        H.stage = ST_VL_PRED;
+        H.U_new = L.ustar.p;
+        H.smax_out = H.n_bad = H.clear2 = nullptr;
+        H.time_rec = nullptr;
+        H.cf = CFRegs{nullptr, nullptr, nullptr, nullptr};
+        if ((st = launch_step(c, H, grid))) return st;
+        P.stage = ST_VL_CORR;
+        P.U_base = P.U_old;
+        P.U_old = L.ustar.p;
+    }
     if ((st = launch_step(c, P, grid))) return st;
 
     L.cur = 1 - L.cur;

@@ -17,6 +17,13 @@
 //          starts the flux divergence of the cell at z.
 // The 20^3 tile never exists in global memory (section 3.4: ghost zones are
 // only allocated temporarily).
+//
+// The VL scheme (section 2.2) runs as two launches of the same march
+// (STAGE): the predictor (ST_VL_PRED) keeps conserved cell averages in the
+// ring, takes them as the face states of every cell and writes the half
+// step U* = U^n - dt/(2 dh) sum_d (F_{d,+} - F_{d,-}); the corrector
+// (ST_VL_CORR) reconstructs the limited piecewise-linear face states of U*
+// (no Hancock increment) and updates U^n with their Riemann fluxes.
 #pragma once
 #include "hydro_math.cuh"
 
@@ -29,6 +36,11 @@ constexpr int GE = 16;                // group edge
 constexpr int TW = GE + 4;            // tile edge with 2 ghost cells per side
 constexpr int COLS = GE * GE;         // (x,y) columns of a group: one owner thread each
 constexpr int MAX_WARPS = 8;
+
+// Stage of the step a kernel instance computes.
+constexpr int ST_MH = 0;       // MUSCL-Hancock step
+constexpr int ST_VL_PRED = 1;  // VL half step U* from first-order fluxes of U^n
+constexpr int ST_VL_CORR = 2;  // VL update of U^n with the fluxes of the PLM states of U*
 
 // Threads per CTA: one per (x,y) column of the group.  The FP32 kernel is
 // register-bounded for two resident CTAs per SM, the FP64 kernel for one (its
@@ -55,8 +67,10 @@ struct CFRegs {
 };
 
 struct StepParams {
-    const double *__restrict__ U_old;
+    const double *__restrict__ U_old;   // the state reconstructed (U* in the VL corrector)
     double *__restrict__ U_new;
+    const double *__restrict__ U_base;  // VL corrector: U^n, the state the fluxes update
+    int stage;                          // ST_MH, ST_VL_PRED or ST_VL_CORR (selects the instance)
     const int32_t *__restrict__ nbr;  // [n_groups][64] source of each 4x4x4 patch position
     const double *__restrict__ ghost; // interpolated coarse-fine ghost patches
     const int32_t *__restrict__ work; // optional list of group ids (null: work0..work0+n_work-1)
@@ -166,7 +180,7 @@ __device__ __forceinline__ const double *patch_src(const StepParams &P, int s) {
 
 // Load tile plane tl (-2..17 within the group of table slot ts) into the
 // ring slot of run plane tr and convert to primitives.
-template <typename real>
+template <typename real, int STAGE>
 __device__ __forceinline__ void load_plane(StepSmem<real> &S, const StepParams &P, int ts, int tl, int tr,
                                            const Gas<real> &g) {
     const int slot = (tr + 3) % 3;
@@ -181,7 +195,12 @@ __device__ __forceinline__ void load_plane(StepSmem<real> &S, const StepParams &
             const int off = lz * 64 + ly * 8 + lx;
 #pragma unroll
             for (int v = 0; v < NV; v++) u[v] = to_real<real>(__ldg(src + v * PV + off));
-            u2w(u, w, g);
+            if constexpr (STAGE == ST_VL_PRED) {  // the predictor keeps conserved averages
+#pragma unroll
+                for (int v = 0; v < NV; v++) w[v] = u[v];
+            } else {
+                u2w(u, w, g);
+            }
         } else {  // a position no stencil reads (a tile corner): benign state
             w[0] = real(1); w[1] = w[2] = w[3] = real(0); w[4] = real(1);
         }
@@ -222,8 +241,9 @@ __device__ __forceinline__ void issue_plane(StepSmem<real> &S, const StepParams 
 
 // Wait for this thread's copies of tile plane tl (group of table slot ts,
 // run plane tr) and convert them to primitives into the ring (the CTA
-// barrier before stage B publishes them).
-template <typename real>
+// barrier before stage B publishes them); the VL predictor keeps them
+// conserved.
+template <typename real, int STAGE>
 __device__ __forceinline__ void finish_plane(StepSmem<real> &S, int ts, int tl, int tr, const Gas<real> &g) {
     cp_async_wait_all();
     const int slot = (tr + 3) % 3;
@@ -238,7 +258,12 @@ __device__ __forceinline__ void finish_plane(StepSmem<real> &S, int ts, int tl, 
                 real u[NV];
 #pragma unroll
                 for (int v = 0; v < NV; v++) u[v] = to_real<real>(S.raw[v][2 * j + h]);
-                u2w(u, w[h], g);
+                if constexpr (STAGE == ST_VL_PRED) {
+#pragma unroll
+                    for (int v = 0; v < NV; v++) w[h][v] = u[v];
+                } else {
+                    u2w(u, w[h], g);
+                }
             }
         } else {  // a position no stencil reads (a tile corner): benign state
 #pragma unroll
@@ -254,14 +279,23 @@ __device__ __forceinline__ void finish_plane(StepSmem<real> &S, int ts, int tl, 
     }
 }
 
-// Limited slopes and Hancock half step of tile cell (x,y) on plane z.
+// Face states of tile cell (x,y) on plane z: limited slopes and the Hancock
+// half step (ST_MH), the limited slopes alone (ST_VL_CORR), or the cell's
+// conserved average on every face (ST_VL_PRED).
 // uf[2d] / uf[2d+1]: conserved state on the low / high face along d.
-template <typename real>
+template <typename real, int STAGE>
 __device__ __forceinline__ void hancock_cell(const StepSmem<real> &S, int x, int y, int z,
                                              real dtdh_half, const Gas<real> &g,
                                              real uf[6][NV]) {
     const int s0 = (z + 3) % 3, sm = (z + 2) % 3, sp = (z + 4) % 3;
     const int X = x + 2, Y = y + 2;
+    if constexpr (STAGE == ST_VL_PRED) {
+#pragma unroll
+        for (int f = 0; f < 6; f++)
+#pragma unroll
+            for (int v = 0; v < NV; v++) uf[f][v] = S.W[s0][v][Y][X];
+        return;
+    }
     real w[NV], hs[3][NV];
 #pragma unroll
     for (int v = 0; v < NV; v++) {
@@ -281,12 +315,14 @@ __device__ __forceinline__ void hancock_cell(const StepSmem<real> &S, int x, int
         }
         w2u(wm, uf[2 * d], g);
         w2u(wp, uf[2 * d + 1], g);
+        if constexpr (STAGE == ST_VL_CORR) continue;
         if (d == 0) { phys_flux<0>(wm, uf[0], fm); phys_flux<0>(wp, uf[1], fp); }
         if (d == 1) { phys_flux<1>(wm, uf[2], fm); phys_flux<1>(wp, uf[3], fp); }
         if (d == 2) { phys_flux<2>(wm, uf[4], fm); phys_flux<2>(wp, uf[5], fp); }
 #pragma unroll
         for (int v = 0; v < NV; v++) inc[v] += fm[v] - fp[v];
     }
+    if constexpr (STAGE == ST_VL_CORR) return;
 #pragma unroll
     for (int f = 0; f < 6; f++)
 #pragma unroll
@@ -416,15 +452,17 @@ __device__ __forceinline__ int run_group(const int32_t *runs, int off, int first
 // Plane z of the run is local plane z - 16k of run group k.  The caller has
 // set S.dt; smax_r / nbad accumulate the new state's largest signal speed and
 // its unphysical cells.
-template <typename real>
+template <typename real, int STAGE>
 __device__ __forceinline__ void step_run(StepSmem<real> &S, const StepParams &P, const int32_t *runs, int off,
                                          int first, int len, double dt, const Gas<real> &g, real &smax_r,
                                          unsigned &nbad) {
     static_assert(StepCfg<real>::NT == COLS, "one thread per (x,y) column");
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cx = tid & 15, cy = tid >> 4;  // this thread's (x,y) column
-    const double dtdh = dt / P.dh;
+    // the VL predictor advances by half a step
+    const double dtdh = (STAGE == ST_VL_PRED ? 0.5 * dt : dt) / P.dh;
     const real dtdh_r = (real)dtdh;
+    const double *__restrict__ ubase = STAGE == ST_VL_CORR ? P.U_base : P.U_old;
     const real dtdh_half = (real)(0.5 * dt / P.dh);
     const int Z = GE * len;
     // group ids: of the current run plane's group, of the one below it (for
@@ -432,8 +470,8 @@ __device__ __forceinline__ void step_run(StepSmem<real> &S, const StepParams &P,
     int gcur = run_group(runs, off, first, 0), gprev = gcur, gnext = gcur;
     unsigned cfm = 0;  // bit s: the group in table slot s touches a coarse-fine register
     if (__syncthreads_or(load_tables(S, P, 0, gcur))) cfm = 1u;
-    load_plane(S, P, 0, -2, -2, g);
-    load_plane(S, P, 0, -1, -1, g);
+    load_plane<real, STAGE>(S, P, 0, -2, -2, g);
+    load_plane<real, STAGE>(S, P, 0, -1, -1, g);
     issue_plane(S, P, 0, 0);
 
     real zp_prev[NV];   // high z face state of this column's cell at z-1
@@ -444,7 +482,7 @@ __device__ __forceinline__ void step_run(StepSmem<real> &S, const StepParams &P,
     for (int z = -1; z <= Z; z++) {
         {  // plane z+1 is ready to convert, plane z+2 to stage
             const int t1 = z + 1, k1 = t1 < 0 ? 0 : min(t1 >> 4, len - 1);
-            finish_plane(S, k1 & 1, t1 - GE * k1, t1, g);
+            finish_plane<real, STAGE>(S, k1 & 1, t1 - GE * k1, t1, g);
             const int t2 = z + 2;
             if (t2 <= Z + 1) {
                 const int k2 = min(t2 >> 4, len - 1);
@@ -464,7 +502,7 @@ __device__ __forceinline__ void step_run(StepSmem<real> &S, const StepParams &P,
             // iteration's stage D; the next finish_plane waits for it.
             const int64_t own = (int64_t)gcur * 8;
             const int px = (2 * tid) & 15, py = (2 * tid) >> 4;
-            const double *src = P.U_old + (own + (px >> 3) + 2 * (py >> 3) + 4 * (zl >> 3)) * PSLOT +
+            const double *src = ubase + (own + (px >> 3) + 2 * (py >> 3) + 4 * (zl >> 3)) * PSLOT +
                                 (zl & 7) * 64 + (py & 7) * 8 + (px & 7);
 #pragma unroll
             for (int v = 0; v < NV; v++) cp_async16(&S.uo[z & 1][v][2 * tid], src + v * PV);
@@ -483,7 +521,7 @@ __device__ __forceinline__ void step_run(StepSmem<real> &S, const StepParams &P,
         real zm[NV], zp[NV], fz[NV];
         {
             real uf[6][NV];
-            hancock_cell(S, cx, cy, z, dtdh_half, g, uf);
+            hancock_cell<real, STAGE>(S, cx, cy, z, dtdh_half, g, uf);
 #pragma unroll
             for (int v = 0; v < NV; v++) { zm[v] = uf[4][v]; zp[v] = uf[5][v]; }
             // Sub-partitions 2 and 3 (warp & 2) have no ghost-ring cells in this
@@ -507,7 +545,7 @@ __device__ __forceinline__ void step_run(StepSmem<real> &S, const StepParams &P,
             const int x = xring ? (side ? GE : -1) : r;
             const int y = xring ? r : (side ? GE : -1);
             real uf[6][NV];
-            hancock_cell(S, x, y, z, dtdh_half, g, uf);
+            hancock_cell<real, STAGE>(S, x, y, z, dtdh_half, g, uf);
             if (xring) {
 #pragma unroll
                 for (int v = 0; v < NV; v++) {
@@ -566,10 +604,12 @@ __device__ __forceinline__ void step_run(StepSmem<real> &S, const StepParams &P,
                 }
                 P.U_new[base + v * PV] = un;
             }
-            bool ok;
-            const real s = cfl_speed(ur, g, ok);
-            if (!ok) nbad++;
-            if (s > smax_r) smax_r = s;
+            if constexpr (STAGE != ST_VL_PRED) {
+                bool ok;
+                const real s = cfl_speed(ur, g, ok);
+                if (!ok) nbad++;
+                if (s > smax_r) smax_r = s;
+            }
         }
         if (z >= 0 && z < Z) {
 #pragma unroll
@@ -589,7 +629,9 @@ __device__ __forceinline__ void step_run(StepSmem<real> &S, const StepParams &P,
 // constants, so the scheme branches fold away; MODE 1: the limiter of P
 // and its HLLC, HLLE or Roe solver; MODE 2: the limiter of P and the exact
 // solver (kept out of the other instances: its Newton iteration is a call).
-template <typename real, int MODE>
+// STAGE: ST_MH, or one of the two VL launches (the predictor reduces
+// nothing: the corrector reduces the new state's signal speed).
+template <typename real, int MODE, int STAGE>
 __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydro_step(StepParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<real> &S = *reinterpret_cast<StepSmem<real> *>(smem_raw);
@@ -632,11 +674,13 @@ __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydr
     for (int wi = blockIdx.x; wi < P.n_work; wi += gridDim.x) {
         if (P.run_off) {
             const int o = __ldg(P.run_off + wi);
-            step_run(S, P, P.runs, o, 0, __ldg(P.run_off + wi + 1) - o, dt, g, smax_r, nbad);
+            step_run<real, STAGE>(S, P, P.runs, o, 0, __ldg(P.run_off + wi + 1) - o, dt, g, smax_r, nbad);
         } else {
-            step_run(S, P, (const int32_t *)nullptr, 0, P.work ? P.work[wi] : P.work0 + wi, 1, dt, g, smax_r, nbad);
+            step_run<real, STAGE>(S, P, (const int32_t *)nullptr, 0, P.work ? P.work[wi] : P.work0 + wi, 1, dt, g,
+                                  smax_r, nbad);
         }
     }
+    if constexpr (STAGE == ST_VL_PRED) return;
 
     // ---- block reduction of the signal speed, one atomic per block
     double smax = (double)smax_r;
@@ -661,6 +705,7 @@ __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydr
 // A box registered with amr_hydro_set_box: a fully covered periodic level.
 struct BoxDesc {
     double *U[2];
+    double *ustar;                // VL half-step state (null for MUSCL-Hancock)
     const int32_t *nbr;           // [n_groups][64]
     unsigned long long *scal;     // the box's 8 scalar slots (ring of speeds, counts)
     double dh;
@@ -685,7 +730,10 @@ struct BoxLaunch {
 // constants, so the scheme branches fold away; MODE 1: the limiter of B
 // and its HLLC, HLLE or Roe solver; MODE 2: the limiter of B and the exact
 // solver (kept out of the other instances: its Newton iteration is a call).
-template <typename real, int MODE>
+// STAGE: ST_MH, or one of the two VL launches of a step (the predictor
+// writes each box's U*, logs and reduces nothing; both take the box's dt
+// from the same speed slot).
+template <typename real, int MODE, int STAGE>
 __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydro_step_boxes(BoxLaunch B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<real> &S = *reinterpret_cast<StepSmem<real> *>(smem_raw);
@@ -721,7 +769,7 @@ __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydr
             double dt = B.dt_override;
             if (dt < 0.0) dt = B.cfl * d.dh / __longlong_as_double((long long)d.scal[r_in]);
             S.dt = dt;
-            if (it.y == 0 && B.dt_override < 0.0) {
+            if (STAGE != ST_VL_PRED && it.y == 0 && B.dt_override < 0.0) {
                 d.scal[r_clr] = 0ull;
                 d.scal[3 + r_clr] = 0ull;
                 if (B.dt_log) B.dt_log[(int64_t)B.step * B.n_boxes + d.log_index] = dt;
@@ -729,8 +777,10 @@ __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydr
         }
         __syncthreads();
         StepParams P;
-        P.U_old = d.U[cur];
-        P.U_new = d.U[1 - cur];
+        P.U_old = STAGE == ST_VL_CORR ? d.ustar : d.U[cur];
+        P.U_new = STAGE == ST_VL_PRED ? d.ustar : d.U[1 - cur];
+        P.U_base = d.U[cur];
+        P.stage = STAGE;
         P.nbr = d.nbr;
         P.ghost = nullptr;
         P.work = nullptr;
@@ -750,7 +800,8 @@ __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydr
         P.cf.coarse_buf = nullptr;
         real smax_r = real(0);
         unsigned nbad = 0;
-        step_run(S, P, (const int32_t *)nullptr, 0, it.y, 1, S.dt, g, smax_r, nbad);
+        step_run<real, STAGE>(S, P, (const int32_t *)nullptr, 0, it.y, 1, S.dt, g, smax_r, nbad);
+        if constexpr (STAGE == ST_VL_PRED) continue;  // step_run ends with a CTA barrier
         // this group's largest signal speed and unphysical count into its box
         double smax = (double)smax_r;
 #pragma unroll

@@ -14,7 +14,7 @@ class UniformGrid:
 
     def __init__(self, shape, gamma=5.0 / 3.0, cfl=0.5, prec=A.AMR_FP64, box_x=1.0, stream=None,
                  device="cuda", scheme=None):
-        """scheme: optional dict of make_params' limiter / riemann / minmod_coeff."""
+        """scheme: optional dict of make_params' limiter / riemann / minmod_coeff / scheme."""
         nx, ny, nz = shape
         self.shape = (nx, ny, nz)
         self.device = torch.device(device)

@@ -35,10 +35,19 @@ def test_strerror():
 
 @pytest.mark.parametrize("field,value", [("gamma", 1.0), ("cfl", 0.0), ("lmax", 9), ("max_patches", 12),
                                          ("prec", 7), ("limiter", 4), ("limiter", -1), ("riemann", 4),
-                                         ("minmod_coeff", 0.5), ("minmod_coeff", 2.5)])
+                                         ("minmod_coeff", 0.5), ("minmod_coeff", 2.5), ("scheme", 2),
+                                         ("scheme", -1)])
 def test_init_rejects_bad_params(field, value):
     p = A.make_params(root_n=(32, 32, 32))
     setattr(p, field, value)
+    ctx = ctypes.c_void_p()
+    assert A.lib().amr_hydro_init(ctypes.byref(p), None, ctypes.byref(ctx)) == A.AMR_E_INVAL
+    assert not ctx.value
+
+
+def test_init_rejects_vl_on_refined_hierarchies():
+    # the VL half step is built for single-level grids only
+    p = A.make_params(root_n=(32, 32, 32), lmax=1, scheme=A.AMR_SCHEME_VL)
     ctx = ctypes.c_void_p()
     assert A.lib().amr_hydro_init(ctypes.byref(p), None, ctypes.byref(ctx)) == A.AMR_E_INVAL
     assert not ctx.value

@@ -1,9 +1,9 @@
 """GPU parity of the other slope limiters and Riemann solvers (section 2.2:
-HLLE, Roe, the exact solver)
-against the oracle with the same scheme selected: uniform periodic steps in
-FP64 (relative L1 <= 1e-12) and the FP32 mode (1e-5), the AMR W-cycle with
-fix-up and regrid, and the batched-box launch; the adjoint refuses schemes
-its hand-written reverse does not cover."""
+HLLE, Roe, the exact solver) and of the VL scheme against the oracle with
+the same scheme selected: uniform periodic steps in FP64 (relative L1 <=
+1e-12) and the FP32 mode (1e-5), the AMR W-cycle with fix-up and regrid,
+the batched-box launch and the host-buffer step; the adjoint refuses
+schemes its hand-written reverse does not cover."""
 import numpy as np
 import pytest
 
@@ -102,13 +102,149 @@ def test_boxes_parity(prec, tol, lim, rs):
     B.close()
 
 
-def test_adjoint_refuses_other_schemes():
+@pytest.mark.parametrize("scheme", [sch(A.AMR_LIM_GMINMOD, A.AMR_RS_HLLC, 1.5),
+                                    dict(sch(A.AMR_LIM_VANLEER, A.AMR_RS_HLLC, 1.5), scheme=A.AMR_SCHEME_VL)])
+def test_adjoint_refuses_other_schemes(scheme):
     import torch
     from paper_1712_07070_b300.uniform import UniformGrid
-    g = UniformGrid((16, 16, 16), scheme=sch(A.AMR_LIM_GMINMOD, A.AMR_RS_HLLC, 1.5))
+    g = UniformGrid((16, 16, 16), scheme=scheme)
     U = g.state()
     lam = torch.zeros_like(U)
     with pytest.raises(A.AmrHydroError) as e:
         A.amr_hydro_step_adjoint(g.ctx, 0, 1e-3, U, lam, torch.empty_like(U))
     assert e.value.status == A.AMR_E_INVAL
     g.close()
+
+
+# ---- the VL scheme (section 2.2): a Riemann-solver half step, then the
+# limited piecewise-linear states of U* without the Hancock increment
+VL_SCHEMES = [
+    (A.AMR_LIM_VANLEER, A.AMR_RS_HLLC, 1.5),
+    (A.AMR_LIM_GMINMOD, A.AMR_RS_HLLE, 1.5),
+    (A.AMR_LIM_ALBADA, A.AMR_RS_ROE, 1.5),
+    (A.AMR_LIM_VL_GMINMOD, A.AMR_RS_EXACT, 1.2),
+]
+
+
+def vl(lim, rs, theta):
+    return dict(sch(lim, rs, theta), scheme=A.AMR_SCHEME_VL)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("lim,rs,theta", VL_SCHEMES)
+def test_vl_uniform_parity(prec, lim, rs, theta):
+    from paper_1712_07070_b300.uniform import UniformGrid
+    U0 = ics.sod_noise(32, seed=12, ny=48, nz=16)  # one group along z: the run wraps onto itself
+    nz, ny, nx = U0.shape[1:]
+    g = UniformGrid((nx, ny, nz), prec=prec, scheme=vl(lim, rs, theta))
+    g.upload(U0)
+    dts = []
+    for _ in range(4):
+        dt = g.min_dt()
+        dts.append(dt)
+        g.step(dt)
+    out = g.download()
+    g.close()
+    with oracle.scheme(lim, rs, theta, vl=True):
+        ref = U0
+        for dt in dts:
+            ref, nbad = oracle.step_periodic(ref, 1.0 / nx, dt, G53)
+            assert nbad == 0
+    err = rel_l1(out, ref)
+    assert (err <= TOL[prec]).all(), err
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_vl_turbulence_runs_parity(prec):
+    """The VL launches on a level with z-runs of stacked groups (64^3: 4
+    groups per z column) on the decaying-turbulence state."""
+    from paper_1712_07070_b300.uniform import UniformGrid
+    n = 64
+    U0 = ics.turbulence(n, seed=5)
+    g = UniformGrid((n, n, n), prec=prec, scheme=vl(A.AMR_LIM_VANLEER, A.AMR_RS_HLLC, 1.5))
+    g.upload(U0)
+    dt = g.min_dt()
+    g.step(dt)
+    g.step(dt)
+    out = g.download()
+    g.close()
+    with oracle.scheme(vl=True):
+        ref = U0
+        for _ in range(2):
+            ref, _ = oracle.step_periodic(ref, 1.0 / n, dt, G53)
+    err = rel_l1(out, ref)
+    assert (err <= TOL[prec]).all(), err
+
+
+@pytest.mark.parametrize("prec,tol", [(A.AMR_FP64, 1e-12), (A.AMR_FP32_ACC64, 1e-5)])
+@pytest.mark.parametrize("lim,rs", [(A.AMR_LIM_VANLEER, A.AMR_RS_HLLC), (A.AMR_LIM_GMINMOD, A.AMR_RS_ROE)])
+def test_vl_boxes_parity(prec, tol, lim, rs):
+    from paper_1712_07070_b300.boxes import BoxBatch
+    g14 = 1.4
+    B = BoxBatch(gamma=g14, prec=prec, scheme=vl(lim, rs, 1.5))
+    sizes = [32, 16, 48]
+    U0 = [ics.kh_box(n, seed=50 + i, gamma=g14) for i, n in enumerate(sizes)]
+    for U in U0:
+        B.add_box(U)
+    B.advance(3)
+    with oracle.scheme(lim, rs, 1.5, vl=True):
+        for i, n in enumerate(sizes):
+            ref, _ = oracle.run_periodic(U0[i], 1.0 / n, g14, 0.5, 3)
+            err = rel_l1(B.download(i), ref)
+            assert (err <= tol).all(), (n, err)
+    B.close()
+
+
+def pinned(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("nz", [16, 32, 80])
+def test_vl_host_stream_bitwise(prec, nz):
+    """The host-buffer step with the VL launches ordered by z-slab gives
+    bitwise the device path's result (1, 2 and 5 slabs; CFL dt chained)."""
+    from paper_1712_07070_b300.uniform import UniformGrid
+    nx, ny = 32, 48
+    U0 = ics.sod_noise(nx, seed=4, ny=ny, nz=nz)
+    s = vl(A.AMR_LIM_VANLEER, A.AMR_RS_HLLC, 1.5)
+    d = UniformGrid((nx, ny, nz), prec=prec, scheme=s)
+    d.upload(U0)
+    ref = []
+    for _ in range(2):
+        d.step(-1.0)
+        ref.append(d.download())
+    d.close()
+    h = UniformGrid((nx, ny, nz), prec=prec, scheme=s)
+    a, b = pinned(U0), pinned(np.zeros_like(U0))
+    dt = -1.0
+    for k in range(2):
+        dt = h.step_host(a, b, dt)
+        assert np.array_equal(b.numpy(), ref[k]), k
+        a, b = b, a
+    h.close()
+
+
+def test_vl_full_size_512_sampled_cells():
+    """One VL step of the 512^3 decaying-turbulence state on the device path:
+    sampled cells recomputed by the oracle on their periodic 9^3
+    neighbourhood (the VL step's domain of dependence is +-3 cells)."""
+    from paper_1712_07070_b300.uniform import UniformGrid
+    from test_gpu_uniform import subcube
+    n = 512
+    U0 = ics.turbulence(n, seed=1)
+    g = UniformGrid((n, n, n), scheme=vl(A.AMR_LIM_VANLEER, A.AMR_RS_HLLC, 1.5))
+    g.upload(U0)
+    dt = g.min_dt()
+    g.step(dt)
+    out = g.download()
+    g.close()
+    rng = np.random.default_rng(8)
+    cells = rng.integers(0, n, size=(24, 3))
+    cells[:3] = [[0, 0, 0], [n - 1, n - 1, n - 1], [15, 16, 31]]
+    with oracle.scheme(vl=True):
+        for c in cells:
+            r, _ = oracle.step_periodic(subcube(U0, c, 4), 1.0 / n, dt, G53)
+            scale = np.abs(U0[:, c[2], c[1], c[0]]).max()
+            assert np.abs(out[:, c[2], c[1], c[0]] - r[:, 4, 4, 4]).max() <= 1e-12 * scale, c
