@@ -39,6 +39,13 @@ def lib():
         L.or_exact_flux.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_double, _dp]
         L.or_set_scheme.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double]
         L.or_set_vl.argtypes = [ctypes.c_int]
+        L.or_set_ctu.argtypes = [ctypes.c_int]
+        L.or_set_ppm.argtypes = [ctypes.c_int]
+        L.or_ppm_faces.argtypes = [_dp, _dp, _dp]
+        L.or_max_speed1.argtypes = [_dp, ctypes.c_int64, ctypes.c_double]
+        L.or_max_speed1.restype = ctypes.c_double
+        L.or_dt_cfl1.argtypes = [_dp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.or_dt_cfl1.restype = ctypes.c_double
         for name in ("or_gminmod", "or_vl_gminmod"):
             getattr(L, name).argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
             getattr(L, name).restype = ctypes.c_double
@@ -110,19 +117,27 @@ LIM_VANLEER, LIM_GMINMOD, LIM_ALBADA, LIM_VL_GMINMOD = 0, 1, 2, 3
 RS_HLLC, RS_HLLE, RS_ROE, RS_EXACT = 0, 1, 2, 3
 
 
-def set_scheme(limiter=LIM_VANLEER, riemann=RS_HLLC, theta=1.5, vl=False):
+_ctu = [False]  # the CTU scheme takes its dt from Eq. CFL1
+
+
+def set_scheme(limiter=LIM_VANLEER, riemann=RS_HLLC, theta=1.5, vl=False, ctu=False, ppm=False):
     """Select the slope limiter, the Riemann solver, the generalized minmod
-    coefficient and the VL half step (else MUSCL-Hancock's) of every later
-    oracle step (process-wide)."""
+    coefficient, the integration scheme (VL half step, CTU, else
+    MUSCL-Hancock) and PPM reconstruction (else PLM) of every later oracle
+    step (process-wide)."""
+    assert not (vl and ctu)
     lib().or_set_scheme(limiter, riemann, theta)
     lib().or_set_vl(1 if vl else 0)
+    lib().or_set_ctu(1 if ctu else 0)
+    lib().or_set_ppm(1 if ppm else 0)
+    _ctu[0] = bool(ctu)
 
 
 class scheme:
     """Context manager: a scheme for the steps inside, the default after."""
 
-    def __init__(self, limiter=LIM_VANLEER, riemann=RS_HLLC, theta=1.5, vl=False):
-        self.args = (limiter, riemann, theta, vl)
+    def __init__(self, limiter=LIM_VANLEER, riemann=RS_HLLC, theta=1.5, vl=False, ctu=False, ppm=False):
+        self.args = (limiter, riemann, theta, vl, ctu, ppm)
 
     def __enter__(self):
         set_scheme(*self.args)
@@ -151,6 +166,14 @@ def vl_gminmod(a, b, theta):
 def slope(a, b):
     """The slope of the selected limiter."""
     return lib().or_slope(a, b)
+
+
+def ppm_faces(w5):
+    """PPM face values (W_L, W_R) of the middle cell of five cell values."""
+    w5 = np.ascontiguousarray(w5, dtype=np.float64)
+    a, b = np.empty(1), np.empty(1)
+    lib().or_ppm_faces(_ptr(w5), _ptr(a), _ptr(b))
+    return float(a[0]), float(b[0])
 
 
 def hlle(UL, UR, d, gamma):
@@ -199,6 +222,28 @@ def dt_cfl2(U, gamma, cfl, dh):
     return lib().or_dt_cfl2(_ptr(U), U[0].size, gamma, cfl, dh)
 
 
+def max_speed1(U, gamma):
+    """max over cells of max(|vx|,|vy|,|vz|)+c_s (denominator of Eq. CFL1)."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    return lib().or_max_speed1(_ptr(U), U[0].size, gamma)
+
+
+def dt_cfl1(U, gamma, cfl, dh):
+    """Eq. CFL1: dt = C_CFL dh / max(max(|vx|,|vy|,|vz|)+c_s)."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    return lib().or_dt_cfl1(_ptr(U), U[0].size, gamma, cfl, dh)
+
+
+def scheme_max_speed(U, gamma):
+    """The CFL denominator of the selected scheme (CFL1 for CTU, else CFL2)."""
+    return max_speed1(U, gamma) if _ctu[0] else max_speed(U, gamma)
+
+
+def dt_cfl(U, gamma, cfl, dh):
+    """The time step of the selected scheme: Eq. CFL1 for CTU, else CFL2."""
+    return dt_cfl1(U, gamma, cfl, dh) if _ctu[0] else dt_cfl2(U, gamma, cfl, dh)
+
+
 def step_periodic(U, dh, dt, gamma):
     """One MUSCL-Hancock + PLM + HLLC step on a periodic uniform grid.
 
@@ -211,12 +256,13 @@ def step_periodic(U, dh, dt, gamma):
 
 
 def run_periodic(U, dh, gamma, cfl, n_steps):
-    """n_steps steps, each with dt from Eq. CFL2 on the state at the step's start.
+    """n_steps steps, each with dt from the scheme's CFL condition (Eq. CFL1
+    for CTU, else CFL2) on the state at the step's start.
 
     Returns (U, list of dt)."""
     dts = []
     for _ in range(n_steps):
-        dt = dt_cfl2(U, gamma, cfl, dh)
+        dt = dt_cfl(U, gamma, cfl, dh)
         if not dt > 0:
             raise FloatingPointError("unphysical state (rho<=0 or P<=0)")
         U, nbad = step_periodic(U, dh, dt, gamma)

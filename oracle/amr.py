@@ -136,10 +136,11 @@ class OracleHierarchy:
         amr_lib().or_amr_fill_ghost(_ptr(f.U), _u8(f.mask), _dims(f.N), _ptr(c.U_prev), _ptr(c.U), w)
 
     def min_dt(self, l):
-        """Eq. (CFL2) over the cells of the level's patches."""
-        from . import max_speed
+        """The scheme's CFL condition (Eq. CFL2, CFL1 for CTU) over the cells of
+        the level's patches."""
+        from . import scheme_max_speed
         cells = self.lv[l].U[:, self.present(l)]
-        s = max_speed(np.ascontiguousarray(cells).reshape(5, -1, 1, 1), self.gamma)
+        s = scheme_max_speed(np.ascontiguousarray(cells).reshape(5, -1, 1, 1), self.gamma)
         if not s > 0:
             raise FloatingPointError("unphysical state")
         return self.cfl_c * self.dh(l) / s

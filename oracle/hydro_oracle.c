@@ -51,6 +51,26 @@
  * W* -/+ (1/2) dW* (no further evolution); the full step with the Riemann fluxes
  * of those face states.  or_set_vl(1) selects it for every later step.
  *
+ * Scheme (section 2.2 lists the CTU scheme of Colella 1990 in the variant with
+ * six Riemann solves per cell, as in Athena, Stone et al. 2008); reading:
+ *   - normal predictor: the face states along d of a cell evolve by d's own
+ *     flux difference only, U_{d,-/+} + (dt/2dh) [F_d(U_{d,-}) - F_d(U_{d,+})];
+ *   - first fluxes F1 of those states at every face (three solves per cell);
+ *   - transverse correction: the face states along d of a cell take
+ *     - (dt/2dh) sum_{e != d} [F1_e(i+1/2) - F1_e(i-1/2)] of that cell;
+ *   - final fluxes of the corrected states (three more solves) update U^n.
+ *   Time step: Eq. (CFL1), dt = C_CFL dh / max(max(|vx|,|vy|,|vz|) + c_s).
+ * or_set_ctu(1) selects it for every later step.
+ *
+ * Reconstruction (section 2.2 lists PPM, Colella & Woodward 1984): face values
+ * of a primitive component from the cells i-2..i+2,
+ *   W_{i+1/2} = (W_i + W_{i+1})/2 - (dW_{i+1} - dW_i)/6
+ * with dW the selected limiter's slope, then the CW84 monotonicity
+ * constraints: both faces take W_i at an extremum ((W_R - W_i)(W_i - W_L) <= 0);
+ * otherwise with d = W_R - W_L and m = 6 (W_i - (W_L + W_R)/2), d m > d^2 sets
+ * W_L = 3 W_i - 2 W_R and d m < -d^2 sets W_R = 3 W_i - 2 W_L.  The face
+ * values replace W -/+ dW/2 in every scheme above.  or_set_ppm(1) selects it.
+ *
  * Every per-cell loop is independent, so the OpenMP static split changes no
  * result: the oracle is bitwise reproducible for any thread count (the
  * paper's section 2.7.1 property).
@@ -124,10 +144,12 @@ double or_vanleer(double a, double b) {
 /* limiter: 0 van Leer-type, 1 generalized minmod, 2 van Albada-type,
  * 3 hybrid generalized minmod / van Leer-type; riemann: 0 HLLC, 1 HLLE;
  * theta: the generalized minmod coefficient. */
-static int or_limiter_id = 0, or_riemann_id = 0, or_vl = 0;
+static int or_limiter_id = 0, or_riemann_id = 0, or_vl = 0, or_ctu = 0, or_ppm = 0;
 static double or_theta = 1.5;
 
 void or_set_vl(int on) { or_vl = on; }
+void or_set_ctu(int on) { or_ctu = on; }
+void or_set_ppm(int on) { or_ppm = on; }
 
 void or_set_scheme(int limiter, int riemann, double theta) {
     or_limiter_id = limiter;
@@ -169,6 +191,30 @@ double or_slope(double a, double b) {
         case 3: return or_vl_gminmod(a, b, or_theta);
         default: return or_vanleer(a, b);
     }
+}
+
+/* PPM face values (W_L at i-1/2, W_R at i+1/2) of cell i from w[0..4] =
+ * W_{i-2..i+2} of one primitive component (Colella & Woodward 1984,
+ * interpolation with the selected limiter's slopes, then monotonicity). */
+void or_ppm_faces(const double *w, double *wl, double *wr) {
+    double dm = or_slope(w[1] - w[0], w[2] - w[1]);
+    double d0 = or_slope(w[2] - w[1], w[3] - w[2]);
+    double dp = or_slope(w[3] - w[2], w[4] - w[3]);
+    double l = 0.5 * (w[1] + w[2]) - (d0 - dm) / 6.0;
+    double r = 0.5 * (w[2] + w[3]) - (dp - d0) / 6.0;
+    double c = w[2];
+    if ((r - c) * (c - l) <= 0.0) {
+        l = c;
+        r = c;
+    } else {
+        double d = r - l, m = 6.0 * (c - 0.5 * (l + r));
+        if (d * m > d * d)
+            l = 3.0 * c - 2.0 * r;
+        else if (d * m < -d * d)
+            r = 3.0 * c - 2.0 * l;
+    }
+    *wl = l;
+    *wr = r;
 }
 
 /* ---- HLLC Riemann solver (section 2.2; Toro 2009 ch. 10 form) ---------- */
@@ -377,6 +423,35 @@ double or_max_speed(const double *U, int64_t ncell, double gamma) {
     return bad ? -1.0 : smax;
 }
 
+/* Eq. (CFL1): max over cells of max(|vx|,|vy|,|vz|) + c_s; -1 if a cell is
+ * unphysical. */
+double or_max_speed1(const double *U, int64_t ncell, double gamma) {
+    double smax = 0.0;
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(max : smax) reduction(| : bad)
+    for (int64_t i = 0; i < ncell; i++) {
+        double u[NV], W[NV];
+        for (int v = 0; v < NV; v++) u[v] = U[v * ncell + i];
+        or_prim(u, W, gamma);
+        if (!(W[0] > 0.0) || !(W[4] > 0.0)) {
+            bad = 1;
+            continue;
+        }
+        double m = fabs(W[1]);
+        if (fabs(W[2]) > m) m = fabs(W[2]);
+        if (fabs(W[3]) > m) m = fabs(W[3]);
+        double s = m + sound_speed(W, gamma);
+        if (s > smax) smax = s;
+    }
+    return bad ? -1.0 : smax;
+}
+
+double or_dt_cfl1(const double *U, int64_t ncell, double gamma, double cfl, double dh) {
+    double s = or_max_speed1(U, ncell, gamma);
+    if (s <= 0.0) return -1.0;
+    return cfl * dh / s;
+}
+
 double or_dt_cfl2(const double *U, int64_t ncell, double gamma, double cfl, double dh) {
     double s = or_max_speed(U, ncell, gamma);
     if (s <= 0.0) return -1.0;
@@ -395,6 +470,33 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
 int64_t or_step_periodic(const double *U, double *Unew, int nx, int ny, int nz,
                          double dh, double dt, double gamma) {
     return or_step_periodic_fx(U, Unew, nx, ny, nz, dh, dt, gamma, NULL);
+}
+
+/* Riemann fluxes FX[d][var][cell] through the high face of every cell along d
+ * from the face states FS[face][var][cell] (face 2d+1 of cell i against face
+ * 2d of cell i+1). */
+static void or_face_fluxes(const double *FS, double *FX, int nx, int ny, int nz, double gamma) {
+    const int64_t n = (int64_t)nx * ny * nz;
+    const int dims[3] = {nx, ny, nz};
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                int c[3] = {x, y, z};
+                int64_t i = cell_index(x, y, z, nx, ny);
+                for (int d = 0; d < 3; d++) {
+                    int cp[3] = {c[0], c[1], c[2]};
+                    cp[d] = wrap(c[d] + 1, dims[d]);
+                    int64_t ip = cell_index(cp[0], cp[1], cp[2], nx, ny);
+                    double UL[NV], UR[NV], F[NV];
+                    for (int v = 0; v < NV; v++) {
+                        UL[v] = FS[((int64_t)(2 * d + 1) * NV + v) * n + i];
+                        UR[v] = FS[((int64_t)(2 * d) * NV + v) * n + ip];
+                    }
+                    or_riemann(UL, UR, d, gamma, F);
+                    for (int v = 0; v < NV; v++) FX[((int64_t)d * NV + v) * n + i] = F[v];
+                }
+            }
 }
 
 /* Same step; if FX_out is not NULL it receives the interface fluxes
@@ -461,21 +563,40 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
                 double w[NV], Wf[6][NV], Uf[6][NV];
                 for (int v = 0; v < NV; v++) w[v] = W[v * n + i];
                 for (int d = 0; d < 3; d++) {
-                    int cm[3] = {c[0], c[1], c[2]}, cp[3] = {c[0], c[1], c[2]};
-                    cm[d] = wrap(c[d] - 1, dims[d]);
-                    cp[d] = wrap(c[d] + 1, dims[d]);
-                    int64_t im = cell_index(cm[0], cm[1], cm[2], nx, ny);
-                    int64_t ip = cell_index(cp[0], cp[1], cp[2], nx, ny);
+                    int64_t is[5]; /* cells i-2 .. i+2 along d */
+                    for (int k = 0; k < 5; k++) {
+                        int ck[3] = {c[0], c[1], c[2]};
+                        ck[d] = wrap(c[d] + k - 2, dims[d]);
+                        is[k] = cell_index(ck[0], ck[1], ck[2], nx, ny);
+                    }
                     for (int v = 0; v < NV; v++) {
-                        double slope = or_slope(w[v] - W[v * n + im], W[v * n + ip] - w[v]);
-                        Wf[2 * d][v] = w[v] - 0.5 * slope;
-                        Wf[2 * d + 1][v] = w[v] + 0.5 * slope;
+                        if (or_ppm) {
+                            double w5[5];
+                            for (int k = 0; k < 5; k++) w5[k] = W[v * n + is[k]];
+                            or_ppm_faces(w5, &Wf[2 * d][v], &Wf[2 * d + 1][v]);
+                        } else {
+                            double slope = or_slope(w[v] - W[v * n + is[1]], W[v * n + is[3]] - w[v]);
+                            Wf[2 * d][v] = w[v] - 0.5 * slope;
+                            Wf[2 * d + 1][v] = w[v] + 0.5 * slope;
+                        }
                     }
                 }
                 for (int f = 0; f < 6; f++) or_cons(Wf[f], Uf[f], gamma);
                 if (or_vl) { /* the face states are already at the half step */
                     for (int f = 0; f < 6; f++)
                         for (int v = 0; v < NV; v++) FS[((int64_t)f * NV + v) * n + i] = Uf[f][v];
+                    continue;
+                }
+                if (or_ctu) { /* CTU normal predictor: each direction's own flux difference */
+                    for (int d = 0; d < 3; d++) {
+                        double Fm[NV], Fp[NV];
+                        or_flux(Uf[2 * d], d, gamma, Fm);
+                        or_flux(Uf[2 * d + 1], d, gamma, Fp);
+                        for (int s2 = 0; s2 < 2; s2++)
+                            for (int v = 0; v < NV; v++)
+                                FS[((int64_t)(2 * d + s2) * NV + v) * n + i] =
+                                    Uf[2 * d + s2][v] + 0.5 * dt / dh * (Fm[v] - Fp[v]);
+                    }
                     continue;
                 }
                 double inc[NV] = {0, 0, 0, 0, 0};
@@ -490,27 +611,36 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
                         FS[((int64_t)f * NV + v) * n + i] = Uf[f][v] + 0.5 * dt / dh * inc[v];
             }
 
-    /* 4. Riemann solver (HLLC or HLLE) at every face i+1/2: left = high face state of cell i,
+    /* 4. Riemann solver at every face i+1/2: left = high face state of cell i,
      *    right = low face state of cell i+1 */
+    or_face_fluxes(FS, FX, nx, ny, nz, gamma);
+    if (or_ctu) {
+        /* CTU: transverse correction of the face states by the first fluxes,
+         * then the final fluxes */
 #pragma omp parallel for schedule(static)
-    for (int z = 0; z < nz; z++)
-        for (int y = 0; y < ny; y++)
-            for (int x = 0; x < nx; x++) {
-                int c[3] = {x, y, z};
-                int64_t i = cell_index(x, y, z, nx, ny);
-                for (int d = 0; d < 3; d++) {
-                    int cp[3] = {c[0], c[1], c[2]};
-                    cp[d] = wrap(c[d] + 1, dims[d]);
-                    int64_t ip = cell_index(cp[0], cp[1], cp[2], nx, ny);
-                    double UL[NV], UR[NV], F[NV];
-                    for (int v = 0; v < NV; v++) {
-                        UL[v] = FS[((int64_t)(2 * d + 1) * NV + v) * n + i];
-                        UR[v] = FS[((int64_t)(2 * d) * NV + v) * n + ip];
+        for (int z = 0; z < nz; z++)
+            for (int y = 0; y < ny; y++)
+                for (int x = 0; x < nx; x++) {
+                    int c[3] = {x, y, z};
+                    int64_t i = cell_index(x, y, z, nx, ny);
+                    double div[3][NV]; /* F1_e(i+1/2) - F1_e(i-1/2) of this cell along e */
+                    for (int e = 0; e < 3; e++) {
+                        int cm[3] = {c[0], c[1], c[2]};
+                        cm[e] = wrap(c[e] - 1, dims[e]);
+                        int64_t im = cell_index(cm[0], cm[1], cm[2], nx, ny);
+                        for (int v = 0; v < NV; v++)
+                            div[e][v] = FX[((int64_t)e * NV + v) * n + i] - FX[((int64_t)e * NV + v) * n + im];
                     }
-                    or_riemann(UL, UR, d, gamma, F);
-                    for (int v = 0; v < NV; v++) FX[((int64_t)d * NV + v) * n + i] = F[v];
+                    for (int d = 0; d < 3; d++) {
+                        int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
+                        for (int s2 = 0; s2 < 2; s2++)
+                            for (int v = 0; v < NV; v++)
+                                FS[((int64_t)(2 * d + s2) * NV + v) * n + i] -=
+                                    0.5 * dt / dh * (div[e1][v] + div[e2][v]);
+                    }
                 }
-            }
+        or_face_fluxes(FS, FX, nx, ny, nz, gamma);
+    }
 
     /* 5. conservative update */
     int64_t nbad = 0;
