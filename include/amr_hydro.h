@@ -77,10 +77,15 @@ typedef enum {
 /* Integration scheme of the hydro step (section 2.2). */
 typedef enum {
     AMR_SCHEME_MH = 0, /* MUSCL-Hancock: data-reconstructed half step (the default) */
-    AMR_SCHEME_VL = 1  /* VL: half step U* = U^n - dt/(2 dh) sum_d (F_{d,+} - F_{d,-}) from the
+    AMR_SCHEME_VL = 1, /* VL: half step U* = U^n - dt/(2 dh) sum_d (F_{d,+} - F_{d,-}) from the
                           Riemann fluxes of the cell averages, then the Riemann fluxes of the
                           limited piecewise-linear face states of U* update U^n.  Single-level
                           grids only: uniform levels (lmax = 0) and the batched boxes. */
+    AMR_SCHEME_CTU = 2 /* CTU (Colella 1990), six Riemann solves per cell: face states along d
+                          advanced by dt/2 with d's own flux difference, first fluxes, a
+                          transverse correction -(dt/2dh) of the cell's first-flux differences
+                          along the other two directions, final fluxes.  Time step of
+                          Eq. (CFL1), C_CFL <= 0.5. */
 } amr_scheme;
 
 /* Run parameters (section 2.1 and 2.6 symbols). */
@@ -99,7 +104,8 @@ typedef struct {
     int limiter;         /* amr_limiter (0: van Leer-type) */
     int riemann;         /* amr_riemann (0: HLLC) */
     double minmod_coeff; /* generalized minmod coefficient in [1, 2]; 0 means 1.5 */
-    int scheme;          /* amr_scheme (0: MUSCL-Hancock); AMR_SCHEME_VL needs lmax = 0 */
+    int scheme;          /* amr_scheme (0: MUSCL-Hancock); AMR_SCHEME_VL needs lmax = 0; the
+                            dt of AMR_SCHEME_CTU follows Eq. (CFL1), of the others Eq. (CFL2) */
 } amr_hydro_params;
 
 typedef struct amr_hydro_ctx amr_hydro_ctx; /* opaque, library-owned */

@@ -17,7 +17,7 @@ AMR_OK, AMR_E_INVAL, AMR_E_NOMEM, AMR_E_CUDA, AMR_E_UNPHYSICAL, AMR_E_TIMEOUT, A
 AMR_FP64, AMR_FP32_ACC64 = 0, 1
 AMR_LIM_VANLEER, AMR_LIM_GMINMOD, AMR_LIM_ALBADA, AMR_LIM_VL_GMINMOD = 0, 1, 2, 3
 AMR_RS_HLLC, AMR_RS_HLLE, AMR_RS_ROE, AMR_RS_EXACT = 0, 1, 2, 3
-AMR_SCHEME_MH, AMR_SCHEME_VL = 0, 1
+AMR_SCHEME_MH, AMR_SCHEME_VL, AMR_SCHEME_CTU = 0, 1, 2
 
 # every symbol include/amr_hydro.h declares
 SYMBOLS = (

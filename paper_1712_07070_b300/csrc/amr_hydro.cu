@@ -68,13 +68,13 @@ size_t step_smem_bytes(int prec) {
 }
 
 // Kernel instances: key K = MODE + 3 STAGE (scheme_mode of the limiter and
-// solver; ST_MH, ST_VL_PRED or ST_VL_CORR).
-using StepKeys = std::make_integer_sequence<int, 9>;
+// solver; ST_MH, ST_VL_PRED, ST_VL_CORR or ST_CTU).
+using StepKeys = std::make_integer_sequence<int, 12>;
 
 template <typename real, int K>
 static amr_status set_step_smem() {
     return cuda_fail(cudaFuncSetAttribute(k_hydro_step<real, K % 3, K / 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)sizeof(StepSmem<real>)),
+                                          (int)sizeof(StageSmem<real, K / 3>)),
                      "step kernel smem attribute");
 }
 template <typename real, int... K>
@@ -97,24 +97,33 @@ template <typename real, int K>
 static int step_occupancy_k() {
     int n = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hydro_step<real, K % 3, K / 3>, StepCfg<real>::NT,
-                                                  sizeof(StepSmem<real>));
+                                                  sizeof(StageSmem<real, K / 3>));
     return n;
 }
 template <typename real, int... K>
-static int step_occupancy(std::integer_sequence<int, K...>) {
+static int step_occupancy(int stage_lo, int stage_hi, std::integer_sequence<int, K...>) {
     int n = 1 << 20;
-    ((n = std::min(n, step_occupancy_k<real, K>())), ...);
+    ((n = (K / 3 >= stage_lo && K / 3 <= stage_hi) ? std::min(n, step_occupancy_k<real, K>()) : n), ...);
     return n > 0 ? n : 1;
 }
 
-// Number of resident step CTAs per SM, for sizing a persistent grid.
-int step_blocks_per_sm(int prec) {
-    return prec == AMR_FP64 ? step_occupancy<double>(StepKeys{}) : step_occupancy<float>(StepKeys{});
+// The march stages a scheme launches: MUSCL-Hancock, the two VL launches, CTU.
+void scheme_stages(int scheme, int &lo, int &hi) {
+    lo = scheme == AMR_SCHEME_VL ? ST_VL_PRED : (scheme == AMR_SCHEME_CTU ? ST_CTU : ST_MH);
+    hi = scheme == AMR_SCHEME_VL ? ST_VL_CORR : lo;
+}
+
+// Number of resident step CTAs per SM of a scheme's instances, for sizing a
+// persistent grid.
+int step_blocks_per_sm(int prec, int scheme) {
+    int lo, hi;
+    scheme_stages(scheme, lo, hi);
+    return prec == AMR_FP64 ? step_occupancy<double>(lo, hi, StepKeys{}) : step_occupancy<float>(lo, hi, StepKeys{});
 }
 
 template <typename real, int K>
 static void launch_step_one(const StepParams &P, int grid, cudaStream_t s) {
-    k_hydro_step<real, K % 3, K / 3><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(P);
+    k_hydro_step<real, K % 3, K / 3><<<grid, StepCfg<real>::NT, sizeof(StageSmem<real, K / 3>), s>>>(P);
 }
 template <typename real, int... K>
 static void launch_step_key(int key, const StepParams &P, int grid, cudaStream_t s, std::integer_sequence<int, K...>) {
@@ -144,7 +153,7 @@ amr_status launch_step_raw(int prec, const StepParams &P, cudaStream_t stream) {
     if ((st = cuda_fail(cudaGetDevice(&dev), "cudaGetDevice"))) return st;
     if ((st = cuda_fail(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev), "sm count")))
         return st;
-    const int cap = n_sm * step_blocks_per_sm(prec);
+    const int cap = n_sm * step_blocks_per_sm(prec, AMR_SCHEME_MH);
     const int grid = P.n_work < cap ? P.n_work : cap;
     if (prec == AMR_FP64)
         launch_step_k<double>(P, grid, stream);
@@ -161,7 +170,7 @@ amr_status launch_step_raw(int prec, const StepParams &P, cudaStream_t stream) {
 namespace {
 
 template <typename real>
-__global__ void k_max_speed(const double *__restrict__ U, int64_t n_slots, double gamma,
+__global__ void k_max_speed(const double *__restrict__ U, int64_t n_slots, double gamma, int cfl1,
                             unsigned long long *smax, unsigned long long *n_bad) {
     Gas<real> g;
     g.gamma = (real)gamma;
@@ -177,7 +186,7 @@ __global__ void k_max_speed(const double *__restrict__ U, int64_t n_slots, doubl
 #pragma unroll
         for (int v = 0; v < NV; v++) u[v] = to_real<real>(U[s * PSLOT + v * PV + c]);
         bool ok;
-        const real sp = cfl_speed(u, g, ok);
+        const real sp = cfl_speed(u, g, ok, cfl1 != 0);
         if (!ok) bad++;
         else if ((double)sp > m) m = (double)sp;
     }
@@ -234,7 +243,7 @@ amr_status amr_hydro_init(const amr_hydro_params *p, void *stream, amr_hydro_ctx
     if (p->limiter < AMR_LIM_VANLEER || p->limiter > AMR_LIM_VL_GMINMOD) return AMR_E_INVAL;
     if (p->riemann < AMR_RS_HLLC || p->riemann > AMR_RS_EXACT) return AMR_E_INVAL;
     if (p->minmod_coeff != 0.0 && !(p->minmod_coeff >= 1.0 && p->minmod_coeff <= 2.0)) return AMR_E_INVAL;
-    if (p->scheme != AMR_SCHEME_MH && p->scheme != AMR_SCHEME_VL) return AMR_E_INVAL;
+    if (p->scheme < AMR_SCHEME_MH || p->scheme > AMR_SCHEME_CTU) return AMR_E_INVAL;
     // VL on refined levels would need the half-step state in a 3-cell ring of
     // the coarse-fine ghost patches: single-level grids only
     if (p->scheme == AMR_SCHEME_VL && p->lmax > 0) return AMR_E_INVAL;
@@ -256,7 +265,7 @@ amr_status amr_hydro_init(const amr_hydro_params *p, void *stream, amr_hydro_ctx
     c->stream = (cudaStream_t)stream;
     cudaGetDevice(&c->device);
     cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
-    c->step_bps = step_blocks_per_sm(p->prec);
+    c->step_bps = step_blocks_per_sm(p->prec, p->scheme);
     if ((st = c->scal.reserve(SCAL_N))) { amr_hydro_destroy(c); return st; }
     if ((st = c->dtbuf.reserve(3 * (MAX_LEVELS + MAX_BOXES)))) { amr_hydro_destroy(c); return st; }
     if ((st = cuda_fail(cudaMemsetAsync(c->scal.p, 0, sizeof(unsigned long long) * SCAL_N, c->stream),
@@ -361,12 +370,12 @@ namespace amrh {
 
 // Max signal speed and unphysical count of n_slots patches into (smax, nbad),
 // which the caller has zeroed.
-amr_status launch_max_speed(int prec, const double *U, int64_t n_slots, double gamma, unsigned long long *smax,
-                            unsigned long long *nbad, int n_sm, cudaStream_t stream) {
+amr_status launch_max_speed(int prec, const double *U, int64_t n_slots, double gamma, int cfl1,
+                            unsigned long long *smax, unsigned long long *nbad, int n_sm, cudaStream_t stream) {
     if (prec == AMR_FP64)
-        k_max_speed<double><<<n_sm * 8, 256, 0, stream>>>(U, n_slots, gamma, smax, nbad);
+        k_max_speed<double><<<n_sm * 8, 256, 0, stream>>>(U, n_slots, gamma, cfl1, smax, nbad);
     else
-        k_max_speed<float><<<n_sm * 8, 256, 0, stream>>>(U, n_slots, gamma, smax, nbad);
+        k_max_speed<float><<<n_sm * 8, 256, 0, stream>>>(U, n_slots, gamma, cfl1, smax, nbad);
     return cuda_fail(cudaGetLastError(), "k_max_speed");
 }
 
@@ -384,10 +393,11 @@ amr_status level_speed(amr_hydro_ctx *c, int level) {
     if (st) return st;
     if ((st = cuda_fail(cudaMemsetAsync(nb, 0, 8, c->stream), "memset"))) return st;
     const int grid = c->n_sm * 8;
+    const int cfl1 = c->prm.scheme == AMR_SCHEME_CTU;
     if (c->prm.prec == AMR_FP64)
-        k_max_speed<double><<<grid, 256, 0, c->stream>>>(L.U[L.cur], L.n_patches, c->prm.gamma, sm, nb);
+        k_max_speed<double><<<grid, 256, 0, c->stream>>>(L.U[L.cur], L.n_patches, c->prm.gamma, cfl1, sm, nb);
     else
-        k_max_speed<float><<<grid, 256, 0, c->stream>>>(L.U[L.cur], L.n_patches, c->prm.gamma, sm, nb);
+        k_max_speed<float><<<grid, 256, 0, c->stream>>>(L.U[L.cur], L.n_patches, c->prm.gamma, cfl1, sm, nb);
     if ((st = cuda_fail(cudaGetLastError(), "k_max_speed"))) return st;
     L.speed_valid = true;
     return AMR_OK;

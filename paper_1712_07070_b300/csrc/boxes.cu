@@ -27,12 +27,13 @@ namespace {
 bool configured = false;
 
 // Kernel instances: key K = MODE + 3 STAGE, as for the level step kernel.
-using BoxKeys = std::make_integer_sequence<int, 9>;
+using BoxKeys = std::make_integer_sequence<int, 12>;
 
 template <typename real, int K>
 amr_status set_box_smem() {
     return cuda_fail(cudaFuncSetAttribute(k_hydro_step_boxes<real, K % 3, K / 3>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(StepSmem<real>)),
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sizeof(StageSmem<real, K / 3>)),
                      "box kernel smem attribute");
 }
 template <typename real, int... K>
@@ -54,35 +55,39 @@ template <typename real, int K>
 int box_occupancy_k() {
     int n = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hydro_step_boxes<real, K % 3, K / 3>, StepCfg<real>::NT,
-                                                  sizeof(StepSmem<real>));
+                                                  sizeof(StageSmem<real, K / 3>));
     return n;
 }
 template <typename real, int... K>
-int box_occupancy(std::integer_sequence<int, K...>) {
+int box_occupancy(int lo, int hi, std::integer_sequence<int, K...>) {
     int n = 1 << 20;
-    ((n = std::min(n, box_occupancy_k<real, K>())), ...);
+    ((n = (K / 3 >= lo && K / 3 <= hi) ? std::min(n, box_occupancy_k<real, K>()) : n), ...);
     return n > 0 ? n : 1;
 }
 
-int resident_per_sm(int prec) {
-    return prec == AMR_FP64 ? box_occupancy<double>(BoxKeys{}) : box_occupancy<float>(BoxKeys{});
+// Resident CTAs per SM of the instances the context's scheme launches.
+int resident_per_sm(int prec, int scheme) {
+    int lo, hi;
+    scheme_stages(scheme, lo, hi);
+    return prec == AMR_FP64 ? box_occupancy<double>(lo, hi, BoxKeys{}) : box_occupancy<float>(lo, hi, BoxKeys{});
 }
 
 template <typename real, int K>
 void launch_boxes_one(const BoxLaunch &B, int grid, cudaStream_t s) {
-    k_hydro_step_boxes<real, K % 3, K / 3><<<grid, StepCfg<real>::NT, sizeof(StepSmem<real>), s>>>(B);
+    k_hydro_step_boxes<real, K % 3, K / 3><<<grid, StepCfg<real>::NT, sizeof(StageSmem<real, K / 3>), s>>>(B);
 }
 template <typename real, int... K>
 void launch_boxes_key(int key, const BoxLaunch &B, int grid, cudaStream_t s, std::integer_sequence<int, K...>) {
     ((key == K ? launch_boxes_one<real, K>(B, grid, s) : void()), ...);
 }
 
-// One step of the batch: one launch (MUSCL-Hancock) or the VL predictor and
-// corrector launches.
+// One step of the batch: one launch (MUSCL-Hancock, CTU) or the VL predictor
+// and corrector launches.
 amr_status launch_boxes(amr_hydro_ctx *c, const BoxLaunch &B, int grid, cudaStream_t s) {
     const int mode = scheme_mode(B.limiter, B.riemann);
-    const bool vl = c->prm.scheme == AMR_SCHEME_VL;
-    for (int stage : vl ? std::vector<int>{ST_VL_PRED, ST_VL_CORR} : std::vector<int>{ST_MH}) {
+    int lo, hi;
+    scheme_stages(c->prm.scheme, lo, hi);
+    for (int stage = lo; stage <= hi; stage++) {
         if (c->prm.prec == AMR_FP64)
             launch_boxes_key<double>(mode + 3 * stage, B, grid, s, BoxKeys{});
         else
@@ -201,7 +206,8 @@ amr_status amr_hydro_advance_boxes(amr_hydro_ctx *c, int n_boxes, const int *box
         if (B.speed_valid) continue;
         unsigned long long *sc = c->scal.p + SCAL_BOX0 + SCAL_PER * id;
         if ((st = cuda_fail(cudaMemsetAsync(sc, 0, 8 * SCAL_PER, s), "memset"))) return st;
-        if ((st = launch_max_speed(c->prm.prec, B.U[B.cur], (int64_t)B.n_groups * 8, c->prm.gamma, sc + B.ring,
+        if ((st = launch_max_speed(c->prm.prec, B.U[B.cur], (int64_t)B.n_groups * 8, c->prm.gamma,
+                                   c->prm.scheme == AMR_SCHEME_CTU, sc + B.ring,
                                    sc + 3 + B.ring, c->n_sm, s)))
             return st;
         B.speed_valid = true;
@@ -241,7 +247,7 @@ amr_status amr_hydro_advance_boxes(amr_hydro_ctx *c, int n_boxes, const int *box
     if (c->tune_key != ids) {
         const char *env = std::getenv("AMR_HYDRO_AUTOTUNE");
         const bool tune = !(env && env[0] == '0');
-        const int res = resident_per_sm(c->prm.prec);
+        const int res = resident_per_sm(c->prm.prec, c->prm.scheme);
         std::vector<BoxTune> cands;
         for (int mult : {1, res, 2 * res, 4 * res})
             for (int chunked : {0, 1})

@@ -148,11 +148,12 @@ amr_status cuda_fail(cudaError_t e, const char *where);
 double level_dh(const amr_hydro_ctx *c, int level);
 amr_status level_speed(amr_hydro_ctx *c, int level);
 size_t step_smem_bytes(int prec);
+void scheme_stages(int scheme, int &lo, int &hi);
 struct StepParams;
 amr_status launch_step(amr_hydro_ctx *c, const StepParams &P, int grid);
 amr_status launch_step_raw(int prec, const StepParams &P, cudaStream_t stream);
-amr_status launch_max_speed(int prec, const double *U, int64_t n_slots, double gamma, unsigned long long *smax,
-                            unsigned long long *nbad, int n_sm, cudaStream_t stream);
+amr_status launch_max_speed(int prec, const double *U, int64_t n_slots, double gamma, int cfl1,
+                            unsigned long long *smax, unsigned long long *nbad, int n_sm, cudaStream_t stream);
 // AMR (amr_ops.cu, regrid.cpp)
 amr_status fill_ghost_impl(amr_hydro_ctx *c, int level, double t);
 amr_status interp_new_patches(amr_hydro_ctx *c, int coarse, double *out, const int32_t *out_slot,

@@ -423,14 +423,17 @@ __device__ __forceinline__ void face_flux(const real uL[NV], const real uR[NV], 
     for (int v = 0; v < NV; v++) F[v] = fK[v] + SK * (us[v] - uK[v]);
 }
 
-// Signal speed of Eq. (CFL2) of one conserved state, and whether the state is
+// Signal speed of Eq. (CFL2), |vx|+|vy|+|vz|+3c_s, or with cfl1 of Eq. (CFL1),
+// max(|vx|,|vy|,|vz|)+c_s, of one conserved state, and whether the state is
 // physical (rho>0 and P>0).
 template <typename real>
-__device__ __forceinline__ real cfl_speed(const real u[NV], const Gas<real> &g, bool &ok) {
+__device__ __forceinline__ real cfl_speed(const real u[NV], const Gas<real> &g, bool &ok, bool cfl1 = false) {
     real w[NV];
     const real ri = u2w(u, w, g);
     ok = gt0(w[0]) && gt0(w[4]);
-    return fabs(w[1]) + fabs(w[2]) + fabs(w[3]) + real(3) * sqrt_(g.gamma * w[4] * ri);
+    const real cs = sqrt_(g.gamma * w[4] * ri);
+    if (cfl1) return max_(max_(fabs(w[1]), fabs(w[2])), fabs(w[3])) + cs;
+    return fabs(w[1]) + fabs(w[2]) + fabs(w[3]) + real(3) * cs;
 }
 
 }  // namespace amrh

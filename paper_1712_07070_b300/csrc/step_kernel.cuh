@@ -25,6 +25,8 @@
 // (ST_VL_CORR) reconstructs the limited piecewise-linear face states of U*
 // (no Hancock increment) and updates U^n with their Riemann fluxes.
 #pragma once
+#include <type_traits>
+
 #include "hydro_math.cuh"
 
 namespace amrh {
@@ -41,6 +43,7 @@ constexpr int MAX_WARPS = 8;
 constexpr int ST_MH = 0;       // MUSCL-Hancock step
 constexpr int ST_VL_PRED = 1;  // VL half step U* from first-order fluxes of U^n
 constexpr int ST_VL_CORR = 2;  // VL update of U^n with the fluxes of the PLM states of U*
+constexpr int ST_CTU = 3;      // CTU step (ctu_kernel.cuh)
 
 // Threads per CTA: one per (x,y) column of the group.  The FP32 kernel is
 // register-bounded for two resident CTAs per SM, the FP64 kernel for one (its
@@ -114,8 +117,8 @@ struct StepSmem {
 // 0..15 within the group; pa / pb: local patch indices (0..7) of the two
 // cells in the groups of table slots sa / sb when they belong to the run
 // (-1 otherwise); fo: the fine register block of the face (-1: none).
-template <typename real>
-__device__ __forceinline__ void cf_register(const StepSmem<real> &S, const StepParams &P, double dt,
+template <typename real, typename SM>
+__device__ __forceinline__ void cf_register(const SM &S, const StepParams &P, double dt,
                                             const real F[NV], int D, int t1, int t2, int sa, int pa, int sb,
                                             int pb, long long fo) {
     double Fd[NV];
@@ -180,8 +183,8 @@ __device__ __forceinline__ const double *patch_src(const StepParams &P, int s) {
 
 // Load tile plane tl (-2..17 within the group of table slot ts) into the
 // ring slot of run plane tr and convert to primitives.
-template <typename real, int STAGE>
-__device__ __forceinline__ void load_plane(StepSmem<real> &S, const StepParams &P, int ts, int tl, int tr,
+template <typename real, int STAGE, typename SM>
+__device__ __forceinline__ void load_plane(SM &S, const StepParams &P, int ts, int tl, int tr,
                                            const Gas<real> &g) {
     const int slot = (tr + 3) % 3;
     const int qz = (tl + PS) >> 3, lz = (tl + PS) & 7;
@@ -222,8 +225,8 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-template <typename real>
-__device__ __forceinline__ void issue_plane(StepSmem<real> &S, const StepParams &P, int ts, int tl) {
+template <typename real, typename SM>
+__device__ __forceinline__ void issue_plane(SM &S, const StepParams &P, int ts, int tl) {
     const int qz = (tl + PS) >> 3, lz = (tl + PS) & 7;
     for (int j = threadIdx.x; j < TPAIRS; j += StepCfg<real>::NT) {
         const int ty = j / (TW / 2) - 2, tx = 2 * (j % (TW / 2)) - 2;
@@ -243,8 +246,8 @@ __device__ __forceinline__ void issue_plane(StepSmem<real> &S, const StepParams 
 // run plane tr) and convert them to primitives into the ring (the CTA
 // barrier before stage B publishes them); the VL predictor keeps them
 // conserved.
-template <typename real, int STAGE>
-__device__ __forceinline__ void finish_plane(StepSmem<real> &S, int ts, int tl, int tr, const Gas<real> &g) {
+template <typename real, int STAGE, typename SM>
+__device__ __forceinline__ void finish_plane(SM &S, int ts, int tl, int tr, const Gas<real> &g) {
     cp_async_wait_all();
     const int slot = (tr + 3) % 3;
     const int qz = (tl + PS) >> 3;
@@ -294,39 +297,41 @@ __device__ __forceinline__ void hancock_cell(const StepSmem<real> &S, int x, int
         for (int f = 0; f < 6; f++)
 #pragma unroll
             for (int v = 0; v < NV; v++) uf[f][v] = S.W[s0][v][Y][X];
-        return;
-    }
-    real w[NV], hs[3][NV];
-#pragma unroll
-    for (int v = 0; v < NV; v++) {
-        w[v] = S.W[s0][v][Y][X];
-        hs[0][v] = half_slope(w[v] - S.W[s0][v][Y][X - 1], S.W[s0][v][Y][X + 1] - w[v], g);
-        hs[1][v] = half_slope(w[v] - S.W[s0][v][Y - 1][X], S.W[s0][v][Y + 1][X] - w[v], g);
-        hs[2][v] = half_slope(w[v] - S.W[sm][v][Y][X], S.W[sp][v][Y][X] - w[v], g);
-    }
-    real inc[NV] = {real(0), real(0), real(0), real(0), real(0)};
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        real wm[NV], wp[NV], fm[NV], fp[NV];
+    } else {
+        real w[NV], hs[3][NV];
 #pragma unroll
         for (int v = 0; v < NV; v++) {
-            wm[v] = w[v] - hs[d][v];
-            wp[v] = w[v] + hs[d][v];
+            w[v] = S.W[s0][v][Y][X];
+            hs[0][v] = half_slope(w[v] - S.W[s0][v][Y][X - 1], S.W[s0][v][Y][X + 1] - w[v], g);
+            hs[1][v] = half_slope(w[v] - S.W[s0][v][Y - 1][X], S.W[s0][v][Y + 1][X] - w[v], g);
+            hs[2][v] = half_slope(w[v] - S.W[sm][v][Y][X], S.W[sp][v][Y][X] - w[v], g);
         }
-        w2u(wm, uf[2 * d], g);
-        w2u(wp, uf[2 * d + 1], g);
-        if constexpr (STAGE == ST_VL_CORR) continue;
-        if (d == 0) { phys_flux<0>(wm, uf[0], fm); phys_flux<0>(wp, uf[1], fp); }
-        if (d == 1) { phys_flux<1>(wm, uf[2], fm); phys_flux<1>(wp, uf[3], fp); }
-        if (d == 2) { phys_flux<2>(wm, uf[4], fm); phys_flux<2>(wp, uf[5], fp); }
+        real inc[NV] = {real(0), real(0), real(0), real(0), real(0)};
 #pragma unroll
-        for (int v = 0; v < NV; v++) inc[v] += fm[v] - fp[v];
+        for (int d = 0; d < 3; d++) {
+            real wm[NV], wp[NV], fm[NV], fp[NV];
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+                wm[v] = w[v] - hs[d][v];
+                wp[v] = w[v] + hs[d][v];
+            }
+            w2u(wm, uf[2 * d], g);
+            w2u(wp, uf[2 * d + 1], g);
+            if constexpr (STAGE == ST_MH) {
+                if (d == 0) { phys_flux<0>(wm, uf[0], fm); phys_flux<0>(wp, uf[1], fp); }
+                if (d == 1) { phys_flux<1>(wm, uf[2], fm); phys_flux<1>(wp, uf[3], fp); }
+                if (d == 2) { phys_flux<2>(wm, uf[4], fm); phys_flux<2>(wp, uf[5], fp); }
+#pragma unroll
+                for (int v = 0; v < NV; v++) inc[v] += fm[v] - fp[v];
+            }
+        }
+        if constexpr (STAGE == ST_MH) {
+#pragma unroll
+            for (int f = 0; f < 6; f++)
+#pragma unroll
+                for (int v = 0; v < NV; v++) uf[f][v] += dtdh_half * inc[v];
+        }
     }
-    if constexpr (STAGE == ST_VL_CORR) return;
-#pragma unroll
-    for (int f = 0; f < 6; f++)
-#pragma unroll
-        for (int v = 0; v < NV; v++) uf[f][v] += dtdh_half * inc[v];
 }
 
 // Stage C face evaluations of plane z (local plane zl of the group in table
@@ -396,8 +401,8 @@ __device__ __forceinline__ void high_faces(StepSmem<real> &S, const StepParams &
 // same group except at a group boundary, where ka = kb - 1: two same-level
 // groups, so no fine register, but each side's coarse registers);
 // cfm: bit s set when the group in table slot s touches a register.
-template <typename real>
-__device__ __forceinline__ void z_face(const StepSmem<real> &S, const StepParams &P, double dt, const real zp_prev[NV],
+template <typename real, typename SM>
+__device__ __forceinline__ void z_face(const SM &S, const StepParams &P, double dt, const real zp_prev[NV],
                                        const real zm[NV], int cx, int cy, int z, int len, unsigned cfm, real fz[NV],
                                        const Gas<real> &g) {
     face_flux<2>(zp_prev, zm, fz, g);
@@ -421,8 +426,8 @@ __host__ __device__ inline int scheme_mode(int limiter, int riemann) {
 
 // The tables of group grp into table slot ts; returns (per thread) whether
 // an entry this thread loaded names a coarse-fine register.
-template <typename real>
-__device__ __forceinline__ bool load_tables(StepSmem<real> &S, const StepParams &P, int ts, int grp) {
+template <typename SM>
+__device__ __forceinline__ bool load_tables(SM &S, const StepParams &P, int ts, int grp) {
     const int tid = threadIdx.x;
     bool has = false;
     if (tid < 64) S.nbr[ts][tid] = P.nbr[(int64_t)grp * 64 + tid];
@@ -472,7 +477,7 @@ __device__ __forceinline__ void step_run(StepSmem<real> &S, const StepParams &P,
     if (__syncthreads_or(load_tables(S, P, 0, gcur))) cfm = 1u;
     load_plane<real, STAGE>(S, P, 0, -2, -2, g);
     load_plane<real, STAGE>(S, P, 0, -1, -1, g);
-    issue_plane(S, P, 0, 0);
+    issue_plane<real>(S, P, 0, 0);
 
     real zp_prev[NV];   // high z face state of this column's cell at z-1
     real acc[NV];       // flux divergence of this column's cell at z-1 (minus its top z flux)
@@ -486,7 +491,7 @@ __device__ __forceinline__ void step_run(StepSmem<real> &S, const StepParams &P,
             const int t2 = z + 2;
             if (t2 <= Z + 1) {
                 const int k2 = min(t2 >> 4, len - 1);
-                issue_plane(S, P, k2 & 1, t2 - GE * k2);
+                issue_plane<real>(S, P, k2 & 1, t2 - GE * k2);
             }
         }
         __syncthreads();
@@ -625,16 +630,35 @@ __device__ __forceinline__ void step_run(StepSmem<real> &S, const StepParams &P,
     __syncthreads();  // the next run overwrites the tables and the ring
 }
 
+}  // namespace amrh
+
+#include "ctu_kernel.cuh"
+
+namespace amrh {
+
+// Shared memory of a kernel instance's march.
+template <typename real, int STAGE>
+using StageSmem = std::conditional_t<STAGE == ST_CTU, CtuSmem<real>, StepSmem<real>>;
+
+// One run (or group) of the instance's march.
+template <typename real, int STAGE>
+__device__ __forceinline__ void stage_run(StageSmem<real, STAGE> &S, const StepParams &P, const int32_t *runs,
+                                          int off, int first, int len, double dt, const Gas<real> &g, real &smax_r,
+                                          unsigned &nbad) {
+    if constexpr (STAGE == ST_CTU) ctu_run(S, P, runs, off, first, len, dt, g, smax_r, nbad);
+    else step_run<real, STAGE>(S, P, runs, off, first, len, dt, g, smax_r, nbad);
+}
+
 // MODE 0: the default scheme (van Leer-type limiter, HLLC) as compile-time
 // constants, so the scheme branches fold away; MODE 1: the limiter of P
 // and its HLLC, HLLE or Roe solver; MODE 2: the limiter of P and the exact
 // solver (kept out of the other instances: its Newton iteration is a call).
-// STAGE: ST_MH, or one of the two VL launches (the predictor reduces
-// nothing: the corrector reduces the new state's signal speed).
+// STAGE: ST_MH, one of the two VL launches (the predictor reduces nothing:
+// the corrector reduces the new state's signal speed), or ST_CTU.
 template <typename real, int MODE, int STAGE>
 __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydro_step(StepParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    StepSmem<real> &S = *reinterpret_cast<StepSmem<real> *>(smem_raw);
+    StageSmem<real, STAGE> &S = *reinterpret_cast<StageSmem<real, STAGE> *>(smem_raw);
     const int tid = threadIdx.x;
 
     Gas<real> g;
@@ -674,10 +698,10 @@ __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydr
     for (int wi = blockIdx.x; wi < P.n_work; wi += gridDim.x) {
         if (P.run_off) {
             const int o = __ldg(P.run_off + wi);
-            step_run<real, STAGE>(S, P, P.runs, o, 0, __ldg(P.run_off + wi + 1) - o, dt, g, smax_r, nbad);
+            stage_run<real, STAGE>(S, P, P.runs, o, 0, __ldg(P.run_off + wi + 1) - o, dt, g, smax_r, nbad);
         } else {
-            step_run<real, STAGE>(S, P, (const int32_t *)nullptr, 0, P.work ? P.work[wi] : P.work0 + wi, 1, dt, g,
-                                  smax_r, nbad);
+            stage_run<real, STAGE>(S, P, (const int32_t *)nullptr, 0, P.work ? P.work[wi] : P.work0 + wi, 1, dt, g,
+                                   smax_r, nbad);
         }
     }
     if constexpr (STAGE == ST_VL_PRED) return;
@@ -736,7 +760,7 @@ struct BoxLaunch {
 template <typename real, int MODE, int STAGE>
 __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydro_step_boxes(BoxLaunch B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    StepSmem<real> &S = *reinterpret_cast<StepSmem<real> *>(smem_raw);
+    StageSmem<real, STAGE> &S = *reinterpret_cast<StageSmem<real, STAGE> *>(smem_raw);
     const int tid = threadIdx.x;
     Gas<real> g;
     g.gamma = (real)B.gamma;
@@ -800,7 +824,7 @@ __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydr
         P.cf.coarse_buf = nullptr;
         real smax_r = real(0);
         unsigned nbad = 0;
-        step_run<real, STAGE>(S, P, (const int32_t *)nullptr, 0, it.y, 1, S.dt, g, smax_r, nbad);
+        stage_run<real, STAGE>(S, P, (const int32_t *)nullptr, 0, it.y, 1, S.dt, g, smax_r, nbad);
         if constexpr (STAGE == ST_VL_PRED) continue;  // step_run ends with a CTA barrier
         // this group's largest signal speed and unphysical count into its box
         double smax = (double)smax_r;

@@ -1,0 +1,169 @@
+"""GPU parity of the CTU scheme (section 2.2; six Riemann solves per cell,
+time step of Eq. CFL1) against the oracle's CTU branch: uniform periodic
+steps in FP64 (relative L1 <= 1e-12) and the FP32 mode (5e-5) for several
+limiter / solver pairs, a level with z-runs, the AMR W-cycle with fix-up and
+regrid, the batched boxes, the host-buffer step (bitwise against the device
+path), and sampled cells of a 512^3 step."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.amr import OracleHierarchy
+from paper_1712_07070_b300 import amr_hydro as A
+from paper_1712_07070_b300 import ics
+from test_gpu_amr import compare
+from test_gpu_uniform import PRECS, rel_l1
+
+pytestmark = pytest.mark.gpu
+G53 = 5.0 / 3.0
+# FP32 mode: every first and final flux, predictor and transverse term in
+# FP32 (relative rounding up to ~1e-6 per flux after tens of operations).
+# The error of a variable scales with the pressure part of its fluxes,
+# (dt/dh) * 6 faces * P * 1e-6 per step, so on the small transverse momenta
+# of the Sod-noise state (|rho v| ~ 1% of P) four steps allow up to ~5e-4;
+# measured 1.6e-5 (MUSCL-Hancock, with half the solves, stays below 1e-5).
+# Bound 5e-5.
+TOL = {A.AMR_FP64: 1e-12, A.AMR_FP32_ACC64: 5e-5}
+
+PAIRS = [
+    (A.AMR_LIM_VANLEER, A.AMR_RS_HLLC, 1.5),
+    (A.AMR_LIM_GMINMOD, A.AMR_RS_ROE, 1.5),
+    (A.AMR_LIM_ALBADA, A.AMR_RS_HLLE, 1.5),
+    (A.AMR_LIM_VL_GMINMOD, A.AMR_RS_EXACT, 1.2),
+]
+
+
+def ctu(lim=A.AMR_LIM_VANLEER, rs=A.AMR_RS_HLLC, theta=1.5):
+    return {"limiter": lim, "riemann": rs, "minmod_coeff": theta, "scheme": A.AMR_SCHEME_CTU}
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("lim,rs,theta", PAIRS)
+def test_uniform_parity(prec, lim, rs, theta):
+    from paper_1712_07070_b300.uniform import UniformGrid
+    U0 = ics.sod_noise(32, seed=21, ny=16, nz=48)
+    nz, ny, nx = U0.shape[1:]
+    g = UniformGrid((nx, ny, nz), prec=prec, scheme=ctu(lim, rs, theta))
+    g.upload(U0)
+    dts = []
+    for _ in range(4):
+        dt = g.min_dt()
+        dts.append(dt)
+        g.step(dt)
+    out = g.download()
+    g.close()
+    with oracle.scheme(lim, rs, theta, ctu=True):
+        odt = oracle.dt_cfl(U0, G53, 0.5, 1.0 / nx)
+        ref = U0
+        for dt in dts:
+            ref, nbad = oracle.step_periodic(ref, 1.0 / nx, dt, G53)
+            assert nbad == 0
+    assert abs(dts[0] - odt) <= (1e-14 if prec == A.AMR_FP64 else 1e-6) * odt  # Eq. CFL1
+    err = rel_l1(out, ref)
+    assert (err <= TOL[prec]).all(), err
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_turbulence_runs_parity(prec):
+    """A 64^3 level (z-runs of 4 stacked groups) on the turbulence state, the
+    device taking its own Eq. CFL1 dt each step."""
+    from paper_1712_07070_b300.uniform import UniformGrid
+    n = 64
+    U0 = ics.turbulence(n, seed=6)
+    g = UniformGrid((n, n, n), prec=prec, scheme=ctu())
+    g.upload(U0)
+    for _ in range(2):
+        g.step(-1.0)
+    out = g.download()
+    t = g.time()
+    g.close()
+    with oracle.scheme(ctu=True):
+        ref, dts = oracle.run_periodic(U0, 1.0 / n, G53, 0.5, 2)
+    assert abs(t - sum(dts)) <= (1e-14 if prec == A.AMR_FP64 else 1e-6) * t
+    err = rel_l1(out, ref)
+    assert (err <= TOL[prec]).all(), err
+
+
+@pytest.mark.parametrize("prec,tol", list(TOL.items()))
+def test_amr_w_cycle_parity(prec, tol):
+    from paper_1712_07070_b300.amr import AmrHierarchy
+    # CTU at Courant number 0.5 of Eq. CFL1 drives the Mach-2, contrast-100
+    # blobs to negative pressure in the oracle too: contrast 30 at Mach 1.5
+    U0 = ics.blobs(32, seed=3, contrast=30.0, mach=1.5)
+    with oracle.scheme(ctu=True):
+        H = AmrHierarchy(U0, lmax=2, theta=0.05, nbuf=(8, 4), prec=prec, max_patches=6000, scheme=ctu())
+        O = OracleHierarchy(U0, lmax=2, gamma=G53, cfl=0.5, theta=0.05, nbuf=[8, 4])
+        for _ in range(2):
+            H.advance_root()
+            O.advance(0)
+        compare(H, O, tol)
+    H.close()
+
+
+@pytest.mark.parametrize("prec,tol", list(TOL.items()))
+def test_boxes_parity(prec, tol):
+    from paper_1712_07070_b300.boxes import BoxBatch
+    g14 = 1.4
+    B = BoxBatch(gamma=g14, prec=prec, scheme=ctu(A.AMR_LIM_VANLEER, A.AMR_RS_ROE))
+    sizes = [32, 16, 48]
+    U0 = [ics.kh_box(n, seed=60 + i, gamma=g14) for i, n in enumerate(sizes)]
+    for U in U0:
+        B.add_box(U)
+    B.advance(3)
+    with oracle.scheme(A.AMR_LIM_VANLEER, A.AMR_RS_ROE, 1.5, ctu=True):
+        for i, n in enumerate(sizes):
+            ref, _ = oracle.run_periodic(U0[i], 1.0 / n, g14, 0.5, 3)
+            err = rel_l1(B.download(i), ref)
+            assert (err <= tol).all(), (n, err)
+    B.close()
+
+
+def pinned(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_host_stream_bitwise(prec):
+    from paper_1712_07070_b300.uniform import UniformGrid
+    nx, ny, nz = 32, 48, 64
+    U0 = ics.sod_noise(nx, seed=9, ny=ny, nz=nz)
+    d = UniformGrid((nx, ny, nz), prec=prec, scheme=ctu())
+    d.upload(U0)
+    ref = []
+    for _ in range(2):
+        d.step(-1.0)
+        ref.append(d.download())
+    d.close()
+    h = UniformGrid((nx, ny, nz), prec=prec, scheme=ctu())
+    a, b = pinned(U0), pinned(np.zeros_like(U0))
+    dt = -1.0
+    for k in range(2):
+        dt = h.step_host(a, b, dt)
+        assert np.array_equal(b.numpy(), ref[k]), k
+        a, b = b, a
+    h.close()
+
+
+def test_full_size_512_sampled_cells():
+    """One CTU step of the 512^3 decaying-turbulence state: sampled cells
+    recomputed by the oracle on their periodic 9^3 neighbourhood (the CTU
+    step's domain of dependence is +-2 cells)."""
+    from paper_1712_07070_b300.uniform import UniformGrid
+    from test_gpu_uniform import subcube
+    n = 512
+    U0 = ics.turbulence(n, seed=1)
+    g = UniformGrid((n, n, n), scheme=ctu())
+    g.upload(U0)
+    dt = g.min_dt()
+    g.step(dt)
+    out = g.download()
+    g.close()
+    rng = np.random.default_rng(9)
+    cells = rng.integers(0, n, size=(24, 3))
+    cells[:3] = [[0, 0, 0], [n - 1, n - 1, n - 1], [16, 15, 32]]
+    with oracle.scheme(ctu=True):
+        for c in cells:
+            r, _ = oracle.step_periodic(subcube(U0, c, 4), 1.0 / n, dt, G53)
+            scale = np.abs(U0[:, c[2], c[1], c[0]]).max()
+            assert np.abs(out[:, c[2], c[1], c[0]] - r[:, 4, 4, 4]).max() <= 1e-12 * scale, c
