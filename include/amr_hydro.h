@@ -88,6 +88,15 @@ typedef enum {
                           Eq. (CFL1), C_CFL <= 0.5. */
 } amr_scheme;
 
+/* Reconstruction of the face states (section 2.2), on primitive variables. */
+typedef enum {
+    AMR_RECON_PLM = 0, /* piecewise linear with the selected limiter (the default) */
+    AMR_RECON_PPM = 1  /* piecewise parabolic (Colella & Woodward 1984): face values
+                          (W_i + W_{i+1})/2 - (dW_{i+1} - dW_i)/6 from the limiter's slopes,
+                          then the CW84 monotonicity constraints; three ghost cells.
+                          With AMR_SCHEME_MH and AMR_SCHEME_CTU. */
+} amr_recon;
+
 /* Run parameters (section 2.1 and 2.6 symbols). */
 typedef struct {
     double gamma;        /* adiabatic index */
@@ -106,6 +115,7 @@ typedef struct {
     double minmod_coeff; /* generalized minmod coefficient in [1, 2]; 0 means 1.5 */
     int scheme;          /* amr_scheme (0: MUSCL-Hancock); AMR_SCHEME_VL needs lmax = 0; the
                             dt of AMR_SCHEME_CTU follows Eq. (CFL1), of the others Eq. (CFL2) */
+    int recon;           /* amr_recon (0: PLM); PPM not with AMR_SCHEME_VL */
 } amr_hydro_params;
 
 typedef struct amr_hydro_ctx amr_hydro_ctx; /* opaque, library-owned */
@@ -115,7 +125,8 @@ typedef struct amr_hydro_ctx amr_hydro_ctx; /* opaque, library-owned */
  * cfl<=0, lmax outside 0..7, root_n not a positive multiple of 16,
  * max_patches not a positive multiple of 8, non-periodic boundaries, a
  * limiter, riemann or scheme value outside its enum, minmod_coeff neither 0
- * nor in [1, 2], and AMR_SCHEME_VL with lmax > 0. */
+ * nor in [1, 2], AMR_SCHEME_VL with lmax > 0 or with AMR_RECON_PPM, and a
+ * recon value outside its enum. */
 amr_status amr_hydro_init(const amr_hydro_params *params, void *cuda_stream,
                           amr_hydro_ctx **out);
 

@@ -88,8 +88,9 @@ static void interp_cell(const double *Uo, const double *Un, double w, const int 
 
 /*
  * Ghost cells of level l from level l-1 (coarse-fine interpolation).
- * Every fine cell outside the level's patches but within Chebyshev distance 2
- * of a patch cell gets, per conserved variable,
+ * Every fine cell outside the level's patches but within Chebyshev distance 3
+ * of a patch cell (the ghost cells of PPM; PLM reads two) gets, per conserved
+ * variable,
  *     U_f = U_c + sum_d (+-1/4) s_d,   s_d = minmod(U_{c+d} - U_c, U_c - U_{c-d}),
  * with U_c the time-interpolated coarse value of its parent cell and the sign
  * that of the child's offset from the parent centre (interp_cell, with its
@@ -108,12 +109,12 @@ void or_amr_fill_ghost(double *Uf, const uint8_t *pmask_f, const int Nf[3], cons
             for (int x = 0; x < Nf[0]; x++) {
                 if (patch_present(pmask_f, Nf, x, y, z)) continue;
                 int near = 0;
-                for (int dz = -2; dz <= 2 && !near; dz += 2)
-                    for (int dy = -2; dy <= 2 && !near; dy += 2)
-                        for (int dx = -2; dx <= 2 && !near; dx += 2)
+                for (int dz = -3; dz <= 3 && !near; dz += 3)
+                    for (int dy = -3; dy <= 3 && !near; dy += 3)
+                        for (int dx = -3; dx <= 3 && !near; dx += 3)
                             near = patch_present(pmask_f, Nf, x + dx, y + dy, z + dz);
-                /* (the box [x-2,x+2] spans at most two patches per dimension,
-                 * both reached by the offsets -2, 0, +2) */
+                /* (the box [x-3,x+3] spans at most two patches per dimension,
+                 * both reached by the offsets -3, 0, +3) */
                 const int64_t i = cidx(x, y, z, Nf);
                 if (!near) {
                     Uf[0 * nf + i] = 1.0;

@@ -68,8 +68,8 @@ size_t step_smem_bytes(int prec) {
 }
 
 // Kernel instances: key K = MODE + 3 STAGE (scheme_mode of the limiter and
-// solver; ST_MH, ST_VL_PRED, ST_VL_CORR or ST_CTU).
-using StepKeys = std::make_integer_sequence<int, 12>;
+// solver; the stages ST_MH .. ST_CTU_PPM).
+using StepKeys = std::make_integer_sequence<int, 3 * N_STAGES>;
 
 template <typename real, int K>
 static amr_status set_step_smem() {
@@ -107,17 +107,25 @@ static int step_occupancy(int stage_lo, int stage_hi, std::integer_sequence<int,
     return n > 0 ? n : 1;
 }
 
-// The march stages a scheme launches: MUSCL-Hancock, the two VL launches, CTU.
-void scheme_stages(int scheme, int &lo, int &hi) {
-    lo = scheme == AMR_SCHEME_VL ? ST_VL_PRED : (scheme == AMR_SCHEME_CTU ? ST_CTU : ST_MH);
-    hi = scheme == AMR_SCHEME_VL ? ST_VL_CORR : lo;
+// The march stages a scheme launches, lo .. hi: MUSCL-Hancock or CTU (PLM or
+// PPM), or the two VL launches.
+void scheme_stages(int scheme, int recon, int &lo, int &hi) {
+    const bool ppm = recon == AMR_RECON_PPM;
+    if (scheme == AMR_SCHEME_VL) {
+        lo = ST_VL_PRED;
+        hi = ST_VL_CORR;
+    } else if (scheme == AMR_SCHEME_CTU) {
+        lo = hi = ppm ? ST_CTU_PPM : ST_CTU;
+    } else {
+        lo = hi = ppm ? ST_MH_PPM : ST_MH;
+    }
 }
 
 // Number of resident step CTAs per SM of a scheme's instances, for sizing a
 // persistent grid.
-int step_blocks_per_sm(int prec, int scheme) {
+int step_blocks_per_sm(int prec, int scheme, int recon) {
     int lo, hi;
-    scheme_stages(scheme, lo, hi);
+    scheme_stages(scheme, recon, lo, hi);
     return prec == AMR_FP64 ? step_occupancy<double>(lo, hi, StepKeys{}) : step_occupancy<float>(lo, hi, StepKeys{});
 }
 
@@ -153,7 +161,7 @@ amr_status launch_step_raw(int prec, const StepParams &P, cudaStream_t stream) {
     if ((st = cuda_fail(cudaGetDevice(&dev), "cudaGetDevice"))) return st;
     if ((st = cuda_fail(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev), "sm count")))
         return st;
-    const int cap = n_sm * step_blocks_per_sm(prec, AMR_SCHEME_MH);
+    const int cap = n_sm * step_blocks_per_sm(prec, AMR_SCHEME_MH, AMR_RECON_PLM);
     const int grid = P.n_work < cap ? P.n_work : cap;
     if (prec == AMR_FP64)
         launch_step_k<double>(P, grid, stream);
@@ -244,6 +252,8 @@ amr_status amr_hydro_init(const amr_hydro_params *p, void *stream, amr_hydro_ctx
     if (p->riemann < AMR_RS_HLLC || p->riemann > AMR_RS_EXACT) return AMR_E_INVAL;
     if (p->minmod_coeff != 0.0 && !(p->minmod_coeff >= 1.0 && p->minmod_coeff <= 2.0)) return AMR_E_INVAL;
     if (p->scheme < AMR_SCHEME_MH || p->scheme > AMR_SCHEME_CTU) return AMR_E_INVAL;
+    if (p->recon != AMR_RECON_PLM && p->recon != AMR_RECON_PPM) return AMR_E_INVAL;
+    if (p->scheme == AMR_SCHEME_VL && p->recon != AMR_RECON_PLM) return AMR_E_INVAL;
     // VL on refined levels would need the half-step state in a 3-cell ring of
     // the coarse-fine ghost patches: single-level grids only
     if (p->scheme == AMR_SCHEME_VL && p->lmax > 0) return AMR_E_INVAL;
@@ -265,7 +275,7 @@ amr_status amr_hydro_init(const amr_hydro_params *p, void *stream, amr_hydro_ctx
     c->stream = (cudaStream_t)stream;
     cudaGetDevice(&c->device);
     cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
-    c->step_bps = step_blocks_per_sm(p->prec, p->scheme);
+    c->step_bps = step_blocks_per_sm(p->prec, p->scheme, p->recon);
     if ((st = c->scal.reserve(SCAL_N))) { amr_hydro_destroy(c); return st; }
     if ((st = c->dtbuf.reserve(3 * (MAX_LEVELS + MAX_BOXES)))) { amr_hydro_destroy(c); return st; }
     if ((st = cuda_fail(cudaMemsetAsync(c->scal.p, 0, sizeof(unsigned long long) * SCAL_N, c->stream),

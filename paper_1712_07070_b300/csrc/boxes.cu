@@ -27,7 +27,7 @@ namespace {
 bool configured = false;
 
 // Kernel instances: key K = MODE + 3 STAGE, as for the level step kernel.
-using BoxKeys = std::make_integer_sequence<int, 12>;
+using BoxKeys = std::make_integer_sequence<int, 3 * N_STAGES>;
 
 template <typename real, int K>
 amr_status set_box_smem() {
@@ -66,9 +66,9 @@ int box_occupancy(int lo, int hi, std::integer_sequence<int, K...>) {
 }
 
 // Resident CTAs per SM of the instances the context's scheme launches.
-int resident_per_sm(int prec, int scheme) {
+int resident_per_sm(int prec, int scheme, int recon) {
     int lo, hi;
-    scheme_stages(scheme, lo, hi);
+    scheme_stages(scheme, recon, lo, hi);
     return prec == AMR_FP64 ? box_occupancy<double>(lo, hi, BoxKeys{}) : box_occupancy<float>(lo, hi, BoxKeys{});
 }
 
@@ -86,7 +86,7 @@ void launch_boxes_key(int key, const BoxLaunch &B, int grid, cudaStream_t s, std
 amr_status launch_boxes(amr_hydro_ctx *c, const BoxLaunch &B, int grid, cudaStream_t s) {
     const int mode = scheme_mode(B.limiter, B.riemann);
     int lo, hi;
-    scheme_stages(c->prm.scheme, lo, hi);
+    scheme_stages(c->prm.scheme, c->prm.recon, lo, hi);
     for (int stage = lo; stage <= hi; stage++) {
         if (c->prm.prec == AMR_FP64)
             launch_boxes_key<double>(mode + 3 * stage, B, grid, s, BoxKeys{});
@@ -247,7 +247,7 @@ amr_status amr_hydro_advance_boxes(amr_hydro_ctx *c, int n_boxes, const int *box
     if (c->tune_key != ids) {
         const char *env = std::getenv("AMR_HYDRO_AUTOTUNE");
         const bool tune = !(env && env[0] == '0');
-        const int res = resident_per_sm(c->prm.prec, c->prm.scheme);
+        const int res = resident_per_sm(c->prm.prec, c->prm.scheme, c->prm.recon);
         std::vector<BoxTune> cands;
         for (int mult : {1, res, 2 * res, 4 * res})
             for (int chunked : {0, 1})

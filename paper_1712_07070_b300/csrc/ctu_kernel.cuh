@@ -24,21 +24,24 @@
 //   F  update of cell z-1 from U^n (staged one plane ahead), its Eq. (CFL1)
 //      signal speed.
 // The march starts at z = -2 (the predicted z states of cell -1) and needs the
-// tile planes -2 .. 16 len + 1, like the MUSCL-Hancock march.
+// tile planes -NG .. 16 len - 1 + NG, like the MUSCL-Hancock march.  With PPM
+// (three ghost cells) the face values of a cell reach two cells instead of
+// one; the ring then holds planes z-1 .. z+3 instead of z .. z+2.
 #pragma once
 
 namespace amrh {
 
 constexpr int CE = GE + 2;  // predicted-state region: cells -1..16 along x and y
 
-template <typename real>
+template <typename real, int NG = 2>
 struct CtuSmem {
-    real W[3][NV][TW][TW];      // primitive ring, planes z, z+1, z+2
+    using Geo = Tile<NG>;
+    real W[Geo::NR][NV][Geo::TY][Geo::TX];  // primitive ring, planes z+1-S .. z+1+S (and z)
     real XS[2][NV][CE][CE];     // x face states (low, high) of cells x, y = -1..16: [.][v][y+1][x+1]
     real YS[2][NV][CE][CE];     // y face states, same layout
     real FX[NV][CE][GE + 1];    // x flux at face x-1/2 (x = 0..16) of rows y = -1..16: [v][y+1][x]
     real FY[NV][GE + 1][CE];    // y flux at face y-1/2 (y = 0..16) of columns x = -1..16: [v][y][x+1]
-    alignas(16) double raw[NV][TW * TW];  // next tile plane in flight (cp.async)
+    alignas(16) double raw[NV][Geo::TY * Geo::TX];  // next tile plane in flight (cp.async)
     alignas(16) double uo[2][NV][COLS];   // each column's U^n one plane ahead of its update
     int nbr[2][64];
     long long cfo[2][6];
@@ -47,24 +50,15 @@ struct CtuSmem {
     double dt;
 };
 
-// Normal predictor along D of tile cell (x, y) of the ring plane in slot s0
-// (sm / sp: the slots of the planes below / above it, read for D = 2): the
-// limited PLM face states W -/+ dW/2 as conserved states, each advanced by
+// Normal predictor along D of tile cell (x, y) on plane zc: the reconstructed
+// (PLM or PPM) face states as conserved states, each advanced by
 // (dt/2dh) [F_D(U_-) - F_D(U_+)].
-template <typename real, int D>
-__device__ __forceinline__ void ctu_predict(const CtuSmem<real> &S, int x, int y, int sm, int s0, int sp,
-                                            real dtdh_half, const Gas<real> &g, real um[NV], real up[NV]) {
-    const int X = x + 2, Y = y + 2;
+template <typename real, int D, typename SM>
+__device__ __forceinline__ void ctu_predict(const SM &S, int x, int y, int zc, real dtdh_half, const Gas<real> &g,
+                                            real um[NV], real up[NV]) {
+    using G = typename SM::Geo;
     real wm[NV], wp[NV], fm[NV], fp[NV];
-#pragma unroll
-    for (int v = 0; v < NV; v++) {
-        const real w = S.W[s0][v][Y][X];
-        const real lo = D == 0 ? S.W[s0][v][Y][X - 1] : (D == 1 ? S.W[s0][v][Y - 1][X] : S.W[sm][v][Y][X]);
-        const real hi = D == 0 ? S.W[s0][v][Y][X + 1] : (D == 1 ? S.W[s0][v][Y + 1][X] : S.W[sp][v][Y][X]);
-        const real hs = half_slope(w - lo, hi - w, g);
-        wm[v] = w - hs;
-        wp[v] = w + hs;
-    }
+    face_values<real, D, (G::S == 2)>(S, x + G::OX, y + G::OY, zc, g, wm, wp);
     w2u(wm, um, g);
     w2u(wp, up, g);
     phys_flux<D>(wm, um, fm);
@@ -82,8 +76,8 @@ __device__ __forceinline__ void ctu_predict(const CtuSmem<real> &S, int x, int y
 // and the group's high faces on one warp, with the coarse-fine registers of
 // patch faces (the face coordinates of the MUSCL-Hancock kernel's x_face,
 // y_face and high_faces).
-template <typename real>
-__device__ __forceinline__ void ctu_x_face(CtuSmem<real> &S, const StepParams &P, double dt, int row, int col,
+template <typename real, typename SM>
+__device__ __forceinline__ void ctu_x_face(SM &S, const StepParams &P, double dt, int row, int col,
                                            int zl, int ts, bool cf, const Gas<real> &g) {
     real uL[NV], uR[NV], F[NV];
 #pragma unroll
@@ -98,8 +92,8 @@ __device__ __forceinline__ void ctu_x_face(CtuSmem<real> &S, const StepParams &P
     }
 }
 
-template <typename real>
-__device__ __forceinline__ void ctu_y_face(CtuSmem<real> &S, const StepParams &P, double dt, int r, int col,
+template <typename real, typename SM>
+__device__ __forceinline__ void ctu_y_face(SM &S, const StepParams &P, double dt, int r, int col,
                                            int zl, int ts, bool cf, const Gas<real> &g) {
     real uL[NV], uR[NV], F[NV];
 #pragma unroll
@@ -114,8 +108,8 @@ __device__ __forceinline__ void ctu_y_face(CtuSmem<real> &S, const StepParams &P
     }
 }
 
-template <typename real>
-__device__ __forceinline__ void ctu_high_faces(CtuSmem<real> &S, const StepParams &P, double dt, int lane, int zl,
+template <typename real, typename SM>
+__device__ __forceinline__ void ctu_high_faces(SM &S, const StepParams &P, double dt, int lane, int zl,
                                                int ts, bool cf, const Gas<real> &g) {
     const int k = lane & 15, D = lane >> 4;
     real uL[NV], uR[NV], F[NV];
@@ -138,8 +132,8 @@ __device__ __forceinline__ void ctu_high_faces(CtuSmem<real> &S, const StepParam
 
 // The CTU step of a run of len patch groups stacked in z (len = 1: one
 // group); arguments as for step_run.
-template <typename real>
-__device__ __forceinline__ void ctu_run(CtuSmem<real> &S, const StepParams &P, const int32_t *runs, int off,
+template <typename real, typename SM>
+__device__ __forceinline__ void ctu_run(SM &S, const StepParams &P, const int32_t *runs, int off,
                                         int first, int len, double dt, const Gas<real> &g, real &smax_r,
                                         unsigned &nbad) {
     constexpr int NT = StepCfg<real>::NT;
@@ -157,9 +151,13 @@ __device__ __forceinline__ void ctu_run(CtuSmem<real> &S, const StepParams &P, c
     int gcur = run_group(runs, off, first, 0), gprev = gcur, gnext = gcur;
     unsigned cfm = 0;  // bit s: the group in table slot s touches a coarse-fine register
     if (__syncthreads_or(load_tables(S, P, 0, gcur))) cfm = 1u;
-    load_plane<real, ST_MH>(S, P, 0, -2, -2, g);
-    load_plane<real, ST_MH>(S, P, 0, -1, -1, g);
-    issue_plane<real>(S, P, 0, 0);
+    // iteration z (from -2) reads ring planes z and z+1-S .. z+1+S (S = 1 for
+    // PLM, 2 for PPM): planes -1 - S .. S - 2 are gathered now, plane S - 1
+    // is staged, and the top of iteration z converts plane z + S + 1 and
+    // stages plane z + S + 2
+    constexpr int SZ = SM::Geo::S;
+    for (int t = -1 - SZ; t <= SZ - 2; t++) load_plane<real, ST_MH>(S, P, 0, t, t, g);
+    issue_plane<real>(S, P, 0, SZ - 1);
 
     // interior column: predicted z states of cell z (low, high), first z flux
     // at z-1/2, corrected high z state of cell z-1, flux divergence of cell
@@ -172,14 +170,14 @@ __device__ __forceinline__ void ctu_run(CtuSmem<real> &S, const StepParams &P, c
     }
 
     for (int z = -2; z <= Z; z++) {
-        {  // plane z+2 is ready to convert, plane z+3 to stage
-            const int t1 = z + 2;
-            if (t1 <= Z + 1) {
+        {  // plane z+S+1 is ready to convert, plane z+S+2 to stage
+            const int t1 = z + SZ + 1;
+            if (t1 <= Z + SZ) {
                 const int k1 = t1 < 0 ? 0 : min(t1 >> 4, len - 1);
                 finish_plane<real, ST_MH>(S, k1 & 1, t1 - GE * k1, t1, g);
             }
-            const int t2 = z + 3;
-            if (t2 <= Z + 1) {
+            const int t2 = z + SZ + 2;
+            if (t2 <= Z + SZ) {
                 const int k2 = min(t2 >> 4, len - 1);
                 issue_plane<real>(S, P, k2 & 1, t2 - GE * k2);
             }
@@ -202,14 +200,14 @@ __device__ __forceinline__ void ctu_run(CtuSmem<real> &S, const StepParams &P, c
             cp_async_commit();
         }
         // the next run group's tables into the slot group kz - 1 used last;
-        // first read when plane 16 (kz + 1) is staged, at z = 16 kz + 13
-        const bool load_next = zl == 12 && kz + 1 < len;
+        // first read when plane 16 (kz + 1) is staged, at z = 16 kz + 12
+        // with PPM (the stage runs S + 2 planes ahead)
+        const bool load_next = zl == TABLE_ZL && kz + 1 < len;
         bool has_next = false;
         if (load_next) {
             gnext = run_group(runs, off, first, kz + 1);
             has_next = load_tables(S, P, (kz + 1) & 1, gnext);
         }
-        const int s0 = (z + 3) % 3, s1 = (z + 4) % 3, s2 = (z + 5) % 3;  // ring slots of planes z, z+1, z+2
         const bool xy = z >= -1;          // plane z's first x / y fluxes are needed
         const bool inner = z >= 0 && z < Z;
 
@@ -218,7 +216,7 @@ __device__ __forceinline__ void ctu_run(CtuSmem<real> &S, const StepParams &P, c
 #pragma unroll
         for (int v = 0; v < NV; v++) nlo[v] = nhi[v] = dz[v] = rdz[v] = real(0);
         if (z < Z) {
-            ctu_predict<real, 2>(S, cx, cy, s0, s1, s2, dtdh_half, g, nlo, nhi);
+            ctu_predict<real, 2>(S, cx, cy, z + 1, dtdh_half, g, nlo, nhi);
             if (z >= -1) {
                 real f[NV];
                 face_flux<2>(pz_hi, nlo, f, g);
@@ -230,7 +228,7 @@ __device__ __forceinline__ void ctu_run(CtuSmem<real> &S, const StepParams &P, c
             }
             if (has_ring) {
                 real rlo[NV], rhi[NV];
-                ctu_predict<real, 2>(S, rx, ry, s0, s1, s2, dtdh_half, g, rlo, rhi);
+                ctu_predict<real, 2>(S, rx, ry, z + 1, dtdh_half, g, rlo, rhi);
                 if (z >= -1) {
                     real f[NV];
                     face_flux<2>(rz_hi, rlo, f, g);
@@ -252,14 +250,14 @@ __device__ __forceinline__ void ctu_run(CtuSmem<real> &S, const StepParams &P, c
                 const int x = j % CE - 1, y = j / CE - 1;
                 real um[NV], up[NV];
                 if (D == 0) {
-                    ctu_predict<real, 0>(S, x, y, s0, s0, s0, dtdh_half, g, um, up);
+                    ctu_predict<real, 0>(S, x, y, z, dtdh_half, g, um, up);
 #pragma unroll
                     for (int v = 0; v < NV; v++) {
                         S.XS[0][v][y + 1][x + 1] = um[v];
                         S.XS[1][v][y + 1][x + 1] = up[v];
                     }
                 } else {
-                    ctu_predict<real, 1>(S, x, y, s0, s0, s0, dtdh_half, g, um, up);
+                    ctu_predict<real, 1>(S, x, y, z, dtdh_half, g, um, up);
 #pragma unroll
                     for (int v = 0; v < NV; v++) {
                         S.YS[0][v][y + 1][x + 1] = um[v];

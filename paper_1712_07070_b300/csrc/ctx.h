@@ -148,7 +148,7 @@ amr_status cuda_fail(cudaError_t e, const char *where);
 double level_dh(const amr_hydro_ctx *c, int level);
 amr_status level_speed(amr_hydro_ctx *c, int level);
 size_t step_smem_bytes(int prec);
-void scheme_stages(int scheme, int &lo, int &hi);
+void scheme_stages(int scheme, int recon, int &lo, int &hi);
 struct StepParams;
 amr_status launch_step(amr_hydro_ctx *c, const StepParams &P, int grid);
 amr_status launch_step_raw(int prec, const StepParams &P, cudaStream_t stream);
@@ -168,7 +168,7 @@ amr_status build_uniform_tables(const int np[3], int32_t *corner, int32_t *sib, 
                                 int32_t *child);
 amr_status build_nbr_plan(int level, int n_patches, const int32_t *corner, const int32_t *sib,
                           const int32_t *parent, const int level_cells[3],
-                          std::vector<int32_t> &nbr, std::vector<GhostInfo> &ghosts);
+                          std::vector<int32_t> &nbr, std::vector<GhostInfo> &ghosts, int ghost_depth = 2);
 // z-chains of a level's groups (same-level groups stacked in z), their
 // runs of at most max_len groups, and the run length for a grid (host_plan.cpp).
 void z_chains(int n_groups, const int32_t *nbr, std::vector<int32_t> &chains, std::vector<int32_t> &chain_off);

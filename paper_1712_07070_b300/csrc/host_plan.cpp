@@ -55,18 +55,20 @@ amr_status build_uniform_tables(const int np[3], int32_t *corner, int32_t *sib, 
 //   <= -2  coarse-fine ghost patch number (-2 - value), to be interpolated,
 //   -1     a corner position, which no stencil of the step reads.
 // Fails with AMR_E_NESTING when a face or edge neighbour is missing on the
-// root level (nothing to interpolate from).
+// root level (nothing to interpolate from).  ghost_depth (even: 2 for PLM, 4
+// for PPM's three ghost cells) is how deep the interpolated box of a ghost
+// patch reaches along an outer direction.
 amr_status build_nbr_plan(int level, int n_patches, const int32_t *corner, const int32_t *sib,
                           const int32_t *parent, const int level_cells[3],
-                          std::vector<int32_t> &nbr, std::vector<GhostInfo> &ghosts) {
+                          std::vector<int32_t> &nbr, std::vector<GhostInfo> &ghosts, int ghost_depth) {
     const int n_groups = n_patches / 8;
     nbr.assign((size_t)n_groups * 64, -1);
     ghosts.clear();
     // per position (qx+1) + 4(qy+1) + 16(qz+1): the group's own patch it is
     // reached from, the sibling index of the step to it, its offset in cells,
     // whether it is a corner (never read) and the box of its cells the
-    // group's stencils reach (2 deep along an outer direction, all 8 along an
-    // inner one)
+    // group's stencils reach (ghost_depth deep along an outer direction, all 8
+    // along an inner one)
     struct PosInfo {
         int own, sk, off[3], corner, box;
     };
@@ -77,7 +79,7 @@ amr_status build_nbr_plan(int level, int n_patches, const int32_t *corner, const
         for (int d = 0; d < 3; d++) {
             p3[d] = q3[d] < 0 ? 0 : (q3[d] > 1 ? 1 : q3[d]);
             d3[d] = q3[d] - p3[d];
-            box |= (q3[d] < 0 ? 6 : 0) << (4 * d) | (q3[d] > 1 ? 2 : 8) << (12 + 4 * d);
+            box |= (q3[d] < 0 ? 8 - ghost_depth : 0) << (4 * d) | (q3[d] > 1 ? ghost_depth : 8) << (12 + 4 * d);
         }
         PosInfo &e = pi[pos];
         e.own = p3[0] + 2 * p3[1] + 4 * p3[2];

@@ -146,7 +146,11 @@ extern "C" amr_status amr_hydro_advance_host(amr_hydro_ctx *c, const double *U_i
         H.work0 = j * G;
         return launch_step(c, H, grid);
     };
-    if (c->prm.scheme == AMR_SCHEME_CTU) P.stage = ST_CTU;
+    {
+        int lo, hi;
+        scheme_stages(c->prm.scheme, c->prm.recon, lo, hi);
+        P.stage = lo;
+    }
     if (vl) {
         P.stage = ST_VL_CORR;
         P.U_base = Uold;

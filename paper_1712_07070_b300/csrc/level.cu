@@ -164,7 +164,11 @@ amr_status amr_hydro_advance_level(amr_hydro_ctx *c, int level, double dt, int64
     }
     const int cap = c->n_sm * c->step_bps;
     const int grid = P.n_work < cap ? P.n_work : cap;
-    if (c->prm.scheme == AMR_SCHEME_CTU) P.stage = ST_CTU;
+    {
+        int lo, hi;
+        scheme_stages(c->prm.scheme, c->prm.recon, lo, hi);
+        P.stage = lo;  // MUSCL-Hancock or CTU (PLM or PPM): the one launch
+    }
     if (c->prm.scheme == AMR_SCHEME_VL) {  // predictor into U*, then the corrector
         StepParams H = P;
         H.stage = ST_VL_PRED;

@@ -35,7 +35,7 @@ constexpr int PS = 8;                 // patch edge
 constexpr int PV = PS * PS * PS;      // cells per patch
 constexpr int PSLOT = NV * PV;        // doubles per patch slot
 constexpr int GE = 16;                // group edge
-constexpr int TW = GE + 4;            // tile edge with 2 ghost cells per side
+constexpr int TW = GE + 4;            // tile edge with 2 ghost cells per side (PLM)
 constexpr int COLS = GE * GE;         // (x,y) columns of a group: one owner thread each
 constexpr int MAX_WARPS = 8;
 
@@ -44,6 +44,26 @@ constexpr int ST_MH = 0;       // MUSCL-Hancock step
 constexpr int ST_VL_PRED = 1;  // VL half step U* from first-order fluxes of U^n
 constexpr int ST_VL_CORR = 2;  // VL update of U^n with the fluxes of the PLM states of U*
 constexpr int ST_CTU = 3;      // CTU step (ctu_kernel.cuh)
+constexpr int ST_MH_PPM = 4;   // MUSCL-Hancock step with PPM reconstruction
+constexpr int ST_CTU_PPM = 5;  // CTU step with PPM reconstruction
+constexpr int N_STAGES = 6;
+__host__ __device__ constexpr bool stage_ppm(int st) { return st == ST_MH_PPM || st == ST_CTU_PPM; }
+__host__ __device__ constexpr bool stage_ctu(int st) { return st == ST_CTU || st == ST_CTU_PPM; }
+
+// Tile geometry for NG ghost cells per side (2: PLM, 3: PPM, whose face
+// values reach two cells).  Rows y = -NG .. 15+NG; columns are staged in
+// 16-byte x-pairs starting on even x, so the stored row runs from x = -OX
+// (NG rounded up to even) to 15 + OX.  The ring keeps NR = 2 S + 1 planes for
+// a stencil of half-width S = NG - 1 along z.
+template <int NG>
+struct Tile {
+    static constexpr int S = NG - 1;
+    static constexpr int NR = 2 * S + 1;
+    static constexpr int OY = NG, OX = NG + (NG & 1);
+    static constexpr int TY = GE + 2 * OY, TX = GE + 2 * OX;
+    static constexpr int PAIRS = TY * TX / 2;
+    __host__ __device__ static constexpr int slot(int t) { return (t + 4 * NR) % NR; }  // ring slot of plane t >= -NG
+};
 
 // Threads per CTA: one per (x,y) column of the group.  The FP32 kernel is
 // register-bounded for two resident CTAs per SM, the FP64 kernel for one (its
@@ -95,14 +115,15 @@ struct StepParams {
     CFRegs cf;
 };
 
-template <typename real>
+template <typename real, int NG = 2>
 struct StepSmem {
-    real W[3][NV][TW][TW];       // primitive ring, planes z-1, z, z+1
+    using Geo = Tile<NG>;
+    real W[Geo::NR][NV][Geo::TY][Geo::TX];  // primitive ring, planes z-S .. z+S
     real XS[2][NV][GE][GE + 2];  // x-/x+ face states, cells x=-1..16, rows y=0..15
     real YS[2][NV][GE + 2][GE];  // y-/y+ face states, cells y=-1..16, columns x=0..15
     real FX[NV][GE][GE + 1];     // x flux at face x-1/2, x=0..16
     real FY[NV][GE + 1][GE];     // y flux at face y-1/2, y=0..16
-    alignas(16) double raw[NV][TW * TW];  // next tile plane in flight (cp.async), x-pairs owned per thread
+    alignas(16) double raw[NV][Geo::TY * Geo::TX];  // next tile plane in flight (cp.async), x-pairs owned per thread
     alignas(16) double uo[2][NV][COLS];   // each column's U^n one plane ahead of its update (cp.async)
     // per-group tables, two slots (group k of a run uses slot k & 1)
     int nbr[2][64];
@@ -186,10 +207,11 @@ __device__ __forceinline__ const double *patch_src(const StepParams &P, int s) {
 template <typename real, int STAGE, typename SM>
 __device__ __forceinline__ void load_plane(SM &S, const StepParams &P, int ts, int tl, int tr,
                                            const Gas<real> &g) {
-    const int slot = (tr + 3) % 3;
+    using G = typename SM::Geo;
+    const int slot = G::slot(tr);
     const int qz = (tl + PS) >> 3, lz = (tl + PS) & 7;
-    for (int i = threadIdx.x; i < TW * TW; i += StepCfg<real>::NT) {
-        const int ty = i / TW - 2, tx = i % TW - 2;
+    for (int i = threadIdx.x; i < G::TY * G::TX; i += StepCfg<real>::NT) {
+        const int ty = i / G::TX - G::OY, tx = i % G::TX - G::OX;
         const int qy = (ty + PS) >> 3, ly = (ty + PS) & 7;
         const int qx = (tx + PS) >> 3, lx = (tx + PS) & 7;
         const double *src = patch_src(P, S.nbr[ts][qx + 4 * qy + 16 * qz]);
@@ -208,16 +230,15 @@ __device__ __forceinline__ void load_plane(SM &S, const StepParams &P, int ts, i
             w[0] = real(1); w[1] = w[2] = w[3] = real(0); w[4] = real(1);
         }
 #pragma unroll
-        for (int v = 0; v < NV; v++) S.W[slot][v][ty + 2][tx + 2] = w[v];
+        for (int v = 0; v < NV; v++) S.W[slot][v][ty + G::OY][tx + G::OX] = w[v];
     }
 }
 
 // Asynchronous copy of tile plane tz into S.raw in 16-byte pieces: tile
 // columns are taken in x-pairs (tx, tx+1) with tx even, which never straddle a
 // patch and start on a 16-byte boundary in both the patch slot and S.raw.
-// Thread j copies and later converts pair j (< 200), so the copy needs no CTA
-// barrier, only the thread's own cp.async wait.
-constexpr int TPAIRS = TW * TW / 2;
+// Thread j copies and later converts pair j (and j + 256), so the copy needs
+// no CTA barrier, only the thread's own cp.async wait.
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
@@ -227,9 +248,10 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 template <typename real, typename SM>
 __device__ __forceinline__ void issue_plane(SM &S, const StepParams &P, int ts, int tl) {
+    using G = typename SM::Geo;
     const int qz = (tl + PS) >> 3, lz = (tl + PS) & 7;
-    for (int j = threadIdx.x; j < TPAIRS; j += StepCfg<real>::NT) {
-        const int ty = j / (TW / 2) - 2, tx = 2 * (j % (TW / 2)) - 2;
+    for (int j = threadIdx.x; j < G::PAIRS; j += StepCfg<real>::NT) {
+        const int ty = j / (G::TX / 2) - G::OY, tx = 2 * (j % (G::TX / 2)) - G::OX;
         const int qy = (ty + PS) >> 3, ly = (ty + PS) & 7;
         const int qx = (tx + PS) >> 3, lx = (tx + PS) & 7;
         const double *src = patch_src(P, S.nbr[ts][qx + 4 * qy + 16 * qz]);
@@ -248,11 +270,12 @@ __device__ __forceinline__ void issue_plane(SM &S, const StepParams &P, int ts, 
 // conserved.
 template <typename real, int STAGE, typename SM>
 __device__ __forceinline__ void finish_plane(SM &S, int ts, int tl, int tr, const Gas<real> &g) {
+    using G = typename SM::Geo;
     cp_async_wait_all();
-    const int slot = (tr + 3) % 3;
+    const int slot = G::slot(tr);
     const int qz = (tl + PS) >> 3;
-    for (int j = threadIdx.x; j < TPAIRS; j += StepCfg<real>::NT) {
-        const int ty = j / (TW / 2) - 2, tx = 2 * (j % (TW / 2)) - 2;
+    for (int j = threadIdx.x; j < G::PAIRS; j += StepCfg<real>::NT) {
+        const int ty = j / (G::TX / 2) - G::OY, tx = 2 * (j % (G::TX / 2)) - G::OX;
         const int qy = (ty + PS) >> 3, qx = (tx + PS) >> 3;
         real w[2][NV];
         if (S.nbr[ts][qx + 4 * qy + 16 * qz] != -1) {
@@ -276,48 +299,93 @@ __device__ __forceinline__ void finish_plane(SM &S, int ts, int tl, int tr, cons
         }
 #pragma unroll
         for (int v = 0; v < NV; v++) {
-            S.W[slot][v][ty + 2][tx + 2] = w[0][v];
-            S.W[slot][v][ty + 2][tx + 3] = w[1][v];
+            S.W[slot][v][ty + G::OY][tx + G::OX] = w[0][v];
+            S.W[slot][v][ty + G::OY][tx + G::OX + 1] = w[1][v];
         }
     }
 }
 
-// Face states of tile cell (x,y) on plane z: limited slopes and the Hancock
-// half step (ST_MH), the limited slopes alone (ST_VL_CORR), or the cell's
-// conserved average on every face (ST_VL_PRED).
-// uf[2d] / uf[2d+1]: conserved state on the low / high face along d.
-template <typename real, int STAGE>
-__device__ __forceinline__ void hancock_cell(const StepSmem<real> &S, int x, int y, int z,
-                                             real dtdh_half, const Gas<real> &g,
+// PPM face values (lo at i-1/2, hi at i+1/2) of cell i from the values q[0..4]
+// of one primitive component at cells i-2 .. i+2 along a direction
+// (Colella & Woodward 1984): interpolation with the selected limiter's
+// slopes, then the monotonicity constraints (an extremum flattens the cell,
+// a face that would overshoot moves to 3 W_i - 2 W_other).
+template <typename real>
+__device__ __forceinline__ void ppm_faces(const real q[5], const Gas<real> &g, real &lo, real &hi) {
+    const real dm = real(2) * half_slope(q[1] - q[0], q[2] - q[1], g);
+    const real d0 = real(2) * half_slope(q[2] - q[1], q[3] - q[2], g);
+    const real dp = real(2) * half_slope(q[3] - q[2], q[4] - q[3], g);
+    const real sixth = real(1.0 / 6.0);
+    real l = real(0.5) * (q[1] + q[2]) - (d0 - dm) * sixth;
+    real r = real(0.5) * (q[2] + q[3]) - (dp - d0) * sixth;
+    const real c = q[2];
+    if (le0((r - c) * (c - l))) {
+        l = c;
+        r = c;
+    } else {
+        const real d = r - l, m = real(6) * (c - real(0.5) * (l + r));
+        const real dmv = d * m, dd = d * d;
+        if (gt0(dmv - dd)) l = real(3) * c - real(2) * r;
+        else if (gt0(-dd - dmv)) r = real(3) * c - real(2) * l;
+    }
+    lo = l;
+    hi = r;
+}
+
+// Primitive face values (low, high) along D of tile cell (X, Y) (ring
+// indices) on plane z: W -/+ dW/2 with the limiter's slope (PLM), or the PPM
+// face values.
+template <typename real, int D, bool PPM, typename SM>
+__device__ __forceinline__ void face_values(const SM &S, int X, int Y, int z, const Gas<real> &g, real wm[NV],
+                                            real wp[NV]) {
+    using G = typename SM::Geo;
+    constexpr int R = PPM ? 2 : 1;
+    int sl[2 * R + 1];
+#pragma unroll
+    for (int k = -R; k <= R; k++) sl[k + R] = G::slot(z + (D == 2 ? k : 0));
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+        real q[2 * R + 1];
+#pragma unroll
+        for (int k = -R; k <= R; k++)
+            q[k + R] = D == 0 ? S.W[sl[R]][v][Y][X + k] : (D == 1 ? S.W[sl[R]][v][Y + k][X] : S.W[sl[k + R]][v][Y][X]);
+        if constexpr (PPM) {
+            ppm_faces(q, g, wm[v], wp[v]);
+        } else {
+            const real hs = half_slope(q[1] - q[0], q[2] - q[1], g);
+            wm[v] = q[1] - hs;
+            wp[v] = q[1] + hs;
+        }
+    }
+}
+
+// Face states of tile cell (x,y) on plane z: reconstructed (PLM or PPM) face
+// states and the Hancock half step (ST_MH, ST_MH_PPM), the reconstructed
+// states alone (ST_VL_CORR), or the cell's conserved average on every face
+// (ST_VL_PRED).  uf[2d] / uf[2d+1]: conserved state on the low / high face along d.
+template <typename real, int STAGE, typename SM>
+__device__ __forceinline__ void hancock_cell(const SM &S, int x, int y, int z, real dtdh_half, const Gas<real> &g,
                                              real uf[6][NV]) {
-    const int s0 = (z + 3) % 3, sm = (z + 2) % 3, sp = (z + 4) % 3;
-    const int X = x + 2, Y = y + 2;
+    using G = typename SM::Geo;
+    const int X = x + G::OX, Y = y + G::OY;
     if constexpr (STAGE == ST_VL_PRED) {
+        const int s0 = G::slot(z);
 #pragma unroll
         for (int f = 0; f < 6; f++)
 #pragma unroll
             for (int v = 0; v < NV; v++) uf[f][v] = S.W[s0][v][Y][X];
     } else {
-        real w[NV], hs[3][NV];
-#pragma unroll
-        for (int v = 0; v < NV; v++) {
-            w[v] = S.W[s0][v][Y][X];
-            hs[0][v] = half_slope(w[v] - S.W[s0][v][Y][X - 1], S.W[s0][v][Y][X + 1] - w[v], g);
-            hs[1][v] = half_slope(w[v] - S.W[s0][v][Y - 1][X], S.W[s0][v][Y + 1][X] - w[v], g);
-            hs[2][v] = half_slope(w[v] - S.W[sm][v][Y][X], S.W[sp][v][Y][X] - w[v], g);
-        }
+        constexpr bool ppm = stage_ppm(STAGE), hancock = STAGE != ST_VL_CORR;
         real inc[NV] = {real(0), real(0), real(0), real(0), real(0)};
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             real wm[NV], wp[NV], fm[NV], fp[NV];
-#pragma unroll
-            for (int v = 0; v < NV; v++) {
-                wm[v] = w[v] - hs[d][v];
-                wp[v] = w[v] + hs[d][v];
-            }
+            if (d == 0) face_values<real, 0, ppm>(S, X, Y, z, g, wm, wp);
+            if (d == 1) face_values<real, 1, ppm>(S, X, Y, z, g, wm, wp);
+            if (d == 2) face_values<real, 2, ppm>(S, X, Y, z, g, wm, wp);
             w2u(wm, uf[2 * d], g);
             w2u(wp, uf[2 * d + 1], g);
-            if constexpr (STAGE == ST_MH) {
+            if constexpr (hancock) {
                 if (d == 0) { phys_flux<0>(wm, uf[0], fm); phys_flux<0>(wp, uf[1], fp); }
                 if (d == 1) { phys_flux<1>(wm, uf[2], fm); phys_flux<1>(wp, uf[3], fp); }
                 if (d == 2) { phys_flux<2>(wm, uf[4], fm); phys_flux<2>(wp, uf[5], fp); }
@@ -325,7 +393,7 @@ __device__ __forceinline__ void hancock_cell(const StepSmem<real> &S, int x, int
                 for (int v = 0; v < NV; v++) inc[v] += fm[v] - fp[v];
             }
         }
-        if constexpr (STAGE == ST_MH) {
+        if constexpr (hancock) {
 #pragma unroll
             for (int f = 0; f < 6; f++)
 #pragma unroll
@@ -342,8 +410,8 @@ __device__ __forceinline__ void hancock_cell(const StepSmem<real> &S, int x, int
 // columns (lanes 16..31), in one divergence-free pass through hllc_dir.  The
 // FP64 pipe charges a whole warp instruction however few lanes are active,
 // so that pass costs one solver evaluation instead of two.
-template <typename real>
-__device__ __forceinline__ void x_face(StepSmem<real> &S, const StepParams &P, double dt, int row, int col, int zl,
+template <typename real, typename SM>
+__device__ __forceinline__ void x_face(SM &S, const StepParams &P, double dt, int row, int col, int zl,
                                        int ts, bool cf, const Gas<real> &g) {
     real uL[NV], uR[NV], F[NV];
 #pragma unroll
@@ -358,8 +426,8 @@ __device__ __forceinline__ void x_face(StepSmem<real> &S, const StepParams &P, d
     }
 }
 
-template <typename real>
-__device__ __forceinline__ void y_face(StepSmem<real> &S, const StepParams &P, double dt, int r, int col, int zl,
+template <typename real, typename SM>
+__device__ __forceinline__ void y_face(SM &S, const StepParams &P, double dt, int r, int col, int zl,
                                        int ts, bool cf, const Gas<real> &g) {
     real uL[NV], uR[NV], F[NV];
 #pragma unroll
@@ -373,8 +441,8 @@ __device__ __forceinline__ void y_face(StepSmem<real> &S, const StepParams &P, d
     }
 }
 
-template <typename real>
-__device__ __forceinline__ void high_faces(StepSmem<real> &S, const StepParams &P, double dt, int lane, int zl,
+template <typename real, typename SM>
+__device__ __forceinline__ void high_faces(SM &S, const StepParams &P, double dt, int lane, int zl,
                                            int ts, bool cf, const Gas<real> &g) {
     const int k = lane & 15, D = lane >> 4;
     real uL[NV], uR[NV], F[NV];
@@ -445,6 +513,13 @@ __device__ __forceinline__ bool load_tables(SM &S, const StepParams &P, int ts, 
     return has;
 }
 
+// Local plane of a run group at whose iteration the marches load the next
+// group's tables: after the group's bottom face (plane 0) used the previous
+// group's, and at least one barrier before the first staging of the next
+// group's bottom plane (plane 12 for the CTU march with PPM, which stages
+// four planes ahead).
+constexpr int TABLE_ZL = 8;
+
 // Group k of a run: runs[off + k], or the single group `first`.
 __device__ __forceinline__ int run_group(const int32_t *runs, int off, int first, int k) {
     return runs ? __ldg(runs + off + k) : first;
@@ -457,8 +532,8 @@ __device__ __forceinline__ int run_group(const int32_t *runs, int off, int first
 // Plane z of the run is local plane z - 16k of run group k.  The caller has
 // set S.dt; smax_r / nbad accumulate the new state's largest signal speed and
 // its unphysical cells.
-template <typename real, int STAGE>
-__device__ __forceinline__ void step_run(StepSmem<real> &S, const StepParams &P, const int32_t *runs, int off,
+template <typename real, int STAGE, typename SM>
+__device__ __forceinline__ void step_run(SM &S, const StepParams &P, const int32_t *runs, int off,
                                          int first, int len, double dt, const Gas<real> &g, real &smax_r,
                                          unsigned &nbad) {
     static_assert(StepCfg<real>::NT == COLS, "one thread per (x,y) column");
@@ -475,9 +550,13 @@ __device__ __forceinline__ void step_run(StepSmem<real> &S, const StepParams &P,
     int gcur = run_group(runs, off, first, 0), gprev = gcur, gnext = gcur;
     unsigned cfm = 0;  // bit s: the group in table slot s touches a coarse-fine register
     if (__syncthreads_or(load_tables(S, P, 0, gcur))) cfm = 1u;
-    load_plane<real, STAGE>(S, P, 0, -2, -2, g);
-    load_plane<real, STAGE>(S, P, 0, -1, -1, g);
-    issue_plane<real>(S, P, 0, 0);
+    // iteration z (from -1) reads ring planes z - S .. z + S (S = 1 for PLM,
+    // 2 for PPM): planes -1 - S .. S - 2 are gathered now, plane S - 1 is
+    // staged, and the top of iteration z converts plane z + S and stages
+    // plane z + S + 1
+    constexpr int SZ = SM::Geo::S;
+    for (int t = -1 - SZ; t <= SZ - 2; t++) load_plane<real, STAGE>(S, P, 0, t, t, g);
+    issue_plane<real>(S, P, 0, SZ - 1);
 
     real zp_prev[NV];   // high z face state of this column's cell at z-1
     real acc[NV];       // flux divergence of this column's cell at z-1 (minus its top z flux)
@@ -485,11 +564,11 @@ __device__ __forceinline__ void step_run(StepSmem<real> &S, const StepParams &P,
     for (int v = 0; v < NV; v++) { zp_prev[v] = real(0); acc[v] = real(0); }
 
     for (int z = -1; z <= Z; z++) {
-        {  // plane z+1 is ready to convert, plane z+2 to stage
-            const int t1 = z + 1, k1 = t1 < 0 ? 0 : min(t1 >> 4, len - 1);
+        {  // plane z+S is ready to convert, plane z+S+1 to stage
+            const int t1 = z + SZ, k1 = t1 < 0 ? 0 : min(t1 >> 4, len - 1);
             finish_plane<real, STAGE>(S, k1 & 1, t1 - GE * k1, t1, g);
-            const int t2 = z + 2;
-            if (t2 <= Z + 1) {
+            const int t2 = z + SZ + 1;
+            if (t2 <= Z + SZ) {
                 const int k2 = min(t2 >> 4, len - 1);
                 issue_plane<real>(S, P, k2 & 1, t2 - GE * k2);
             }
@@ -514,8 +593,9 @@ __device__ __forceinline__ void step_run(StepSmem<real> &S, const StepParams &P,
             cp_async_commit();
         }
         // the next run group's tables, into the slot group kz - 1 used last
-        // at run plane 16 kz (its top face); first read at plane 16 kz + 14
-        const bool load_next = zl == 12 && kz + 1 < len;
+        // at run plane 16 kz (its top face); first read when plane
+        // 16 (kz + 1) is staged, at iteration 16 kz + 13 (PPM) or later
+        const bool load_next = zl == TABLE_ZL && kz + 1 < len;
         bool has_next = false;
         if (load_next) {
             gnext = run_group(runs, off, first, kz + 1);
@@ -638,14 +718,15 @@ namespace amrh {
 
 // Shared memory of a kernel instance's march.
 template <typename real, int STAGE>
-using StageSmem = std::conditional_t<STAGE == ST_CTU, CtuSmem<real>, StepSmem<real>>;
+using StageSmem = std::conditional_t<stage_ctu(STAGE), CtuSmem<real, stage_ppm(STAGE) ? 3 : 2>,
+                                     StepSmem<real, stage_ppm(STAGE) ? 3 : 2>>;
 
 // One run (or group) of the instance's march.
 template <typename real, int STAGE>
 __device__ __forceinline__ void stage_run(StageSmem<real, STAGE> &S, const StepParams &P, const int32_t *runs,
                                           int off, int first, int len, double dt, const Gas<real> &g, real &smax_r,
                                           unsigned &nbad) {
-    if constexpr (STAGE == ST_CTU) ctu_run(S, P, runs, off, first, len, dt, g, smax_r, nbad);
+    if constexpr (stage_ctu(STAGE)) ctu_run<real>(S, P, runs, off, first, len, dt, g, smax_r, nbad);
     else step_run<real, STAGE>(S, P, runs, off, first, len, dt, g, smax_r, nbad);
 }
 

@@ -36,7 +36,7 @@ def test_strerror():
 @pytest.mark.parametrize("field,value", [("gamma", 1.0), ("cfl", 0.0), ("lmax", 9), ("max_patches", 12),
                                          ("prec", 7), ("limiter", 4), ("limiter", -1), ("riemann", 4),
                                          ("minmod_coeff", 0.5), ("minmod_coeff", 2.5), ("scheme", 3),
-                                         ("scheme", -1)])
+                                         ("scheme", -1), ("recon", 2), ("recon", -1)])
 def test_init_rejects_bad_params(field, value):
     p = A.make_params(root_n=(32, 32, 32))
     setattr(p, field, value)
@@ -45,12 +45,13 @@ def test_init_rejects_bad_params(field, value):
     assert not ctx.value
 
 
-def test_init_rejects_vl_on_refined_hierarchies():
-    # the VL half step is built for single-level grids only
-    p = A.make_params(root_n=(32, 32, 32), lmax=1, scheme=A.AMR_SCHEME_VL)
+def test_init_rejects_vl_on_refined_hierarchies_and_with_ppm():
+    # the VL half step is built for single-level grids and PLM only
     ctx = ctypes.c_void_p()
-    assert A.lib().amr_hydro_init(ctypes.byref(p), None, ctypes.byref(ctx)) == A.AMR_E_INVAL
-    assert not ctx.value
+    for kw in (dict(lmax=1), dict(recon=A.AMR_RECON_PPM)):
+        p = A.make_params(root_n=(32, 32, 32), scheme=A.AMR_SCHEME_VL, **kw)
+        assert A.lib().amr_hydro_init(ctypes.byref(p), None, ctypes.byref(ctx)) == A.AMR_E_INVAL
+        assert not ctx.value
 
 
 def test_init_rejects_non_multiple_of_16_and_non_cubic_cells():
