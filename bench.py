@@ -312,9 +312,10 @@ def bench_schemes(torch, A, UniformGrid, stream, K, W, world):
     """The other slope limiters and Riemann solvers of section 2.2 (HLLE for
     every limiter; Roe and the exact solver with the van Leer-type limiter)
     the VL scheme (van Leer-type with HLLC and with HLLE) and the CTU scheme
-    (van Leer-type with HLLC and with Roe) on the 256^3 turbulence level, the
-    default MUSCL-Hancock van Leer-type + HLLC for reference: cells/s per
-    precision."""
+    (van Leer-type with HLLC and with Roe), PPM with MUSCL-Hancock + HLLC and
+    with CTU + Roe (the scheme of the paper's Kelvin-Helmholtz runs), on the
+    256^3 turbulence level, the default MUSCL-Hancock + PLM van Leer-type +
+    HLLC for reference: cells/s per precision."""
     from paper_1712_07070_b300 import ics
     U1 = ics.turbulence(256, seed=1)
     names = {A.AMR_LIM_VANLEER: "van Leer", A.AMR_LIM_GMINMOD: "generalized minmod 1.5",
@@ -326,11 +327,14 @@ def bench_schemes(torch, A, UniformGrid, stream, K, W, world):
     combos += [(A.AMR_LIM_VANLEER, A.AMR_RS_HLLC, VL), (A.AMR_LIM_VANLEER, A.AMR_RS_HLLE, VL)]
     CTU = A.AMR_SCHEME_CTU
     combos += [(A.AMR_LIM_VANLEER, A.AMR_RS_HLLC, CTU), (A.AMR_LIM_VANLEER, A.AMR_RS_ROE, CTU)]
+    PPM = 100  # PPM reconstruction of the same scheme (added to the scheme code here)
+    combos += [(A.AMR_LIM_VANLEER, A.AMR_RS_HLLC, MH + PPM), (A.AMR_LIM_VANLEER, A.AMR_RS_ROE, CTU + PPM)]
     rnames = {A.AMR_RS_HLLC: "HLLC", A.AMR_RS_HLLE: "HLLE", A.AMR_RS_ROE: "Roe", A.AMR_RS_EXACT: "exact"}
-    for lim, rs, scheme in combos:
-        sch = {"limiter": lim, "riemann": rs, "minmod_coeff": 1.5, "scheme": scheme}
+    for lim, rs, code in combos:
+        scheme, recon = code % PPM, (A.AMR_RECON_PPM if code >= PPM else A.AMR_RECON_PLM)
+        sch = {"limiter": lim, "riemann": rs, "minmod_coeff": 1.5, "scheme": scheme, "recon": recon}
         sname = {MH: "MUSCL-Hancock", VL: "VL", CTU: "CTU (6 solves/cell, Eq. CFL1)"}[scheme]
-        row = {"workload": "turbulence 256^3", "scheme": sname,
+        row = {"workload": "turbulence 256^3", "scheme": sname, "recon": "PPM" if code >= PPM else "PLM",
                "limiter": names[lim], "riemann": rnames[rs]}
         for prec, key in ((A.AMR_FP64, "f64"), (A.AMR_FP32_ACC64, "fp32_acc64")):
             r = run_case(torch, A, UniformGrid, U1, 256, prec, K, W, stream, want_e2e=False, scheme=sch)
