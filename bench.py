@@ -321,20 +321,19 @@ def bench_schemes(torch, A, UniformGrid, stream, K, W, world):
     names = {A.AMR_LIM_VANLEER: "van Leer", A.AMR_LIM_GMINMOD: "generalized minmod 1.5",
              A.AMR_LIM_ALBADA: "van Albada", A.AMR_LIM_VL_GMINMOD: "hybrid van Leer/minmod 1.5"}
     out = []
-    MH, VL = A.AMR_SCHEME_MH, A.AMR_SCHEME_VL
-    combos = [(lim, rs, MH) for lim in names for rs in (A.AMR_RS_HLLC, A.AMR_RS_HLLE)]
-    combos += [(A.AMR_LIM_VANLEER, A.AMR_RS_ROE, MH), (A.AMR_LIM_VANLEER, A.AMR_RS_EXACT, MH)]
-    combos += [(A.AMR_LIM_VANLEER, A.AMR_RS_HLLC, VL), (A.AMR_LIM_VANLEER, A.AMR_RS_HLLE, VL)]
-    CTU = A.AMR_SCHEME_CTU
-    combos += [(A.AMR_LIM_VANLEER, A.AMR_RS_HLLC, CTU), (A.AMR_LIM_VANLEER, A.AMR_RS_ROE, CTU)]
-    PPM = 100  # PPM reconstruction of the same scheme (added to the scheme code here)
-    combos += [(A.AMR_LIM_VANLEER, A.AMR_RS_HLLC, MH + PPM), (A.AMR_LIM_VANLEER, A.AMR_RS_ROE, CTU + PPM)]
+    MH, VL, CTU = A.AMR_SCHEME_MH, A.AMR_SCHEME_VL, A.AMR_SCHEME_CTU
+    PLM, PPM = A.AMR_RECON_PLM, A.AMR_RECON_PPM
+    VLR = A.AMR_LIM_VANLEER
+    combos = [(lim, rs, MH, PLM) for lim in names for rs in (A.AMR_RS_HLLC, A.AMR_RS_HLLE)]
+    combos += [(VLR, A.AMR_RS_ROE, MH, PLM), (VLR, A.AMR_RS_EXACT, MH, PLM)]
+    combos += [(VLR, A.AMR_RS_HLLC, VL, PLM), (VLR, A.AMR_RS_HLLE, VL, PLM)]
+    combos += [(VLR, A.AMR_RS_HLLC, CTU, PLM), (VLR, A.AMR_RS_ROE, CTU, PLM)]
+    combos += [(VLR, A.AMR_RS_HLLC, MH, PPM), (VLR, A.AMR_RS_ROE, CTU, PPM)]
     rnames = {A.AMR_RS_HLLC: "HLLC", A.AMR_RS_HLLE: "HLLE", A.AMR_RS_ROE: "Roe", A.AMR_RS_EXACT: "exact"}
-    for lim, rs, code in combos:
-        scheme, recon = code % PPM, (A.AMR_RECON_PPM if code >= PPM else A.AMR_RECON_PLM)
+    snames = {MH: "MUSCL-Hancock", VL: "VL", CTU: "CTU (6 solves/cell, Eq. CFL1)"}
+    for lim, rs, scheme, recon in combos:
         sch = {"limiter": lim, "riemann": rs, "minmod_coeff": 1.5, "scheme": scheme, "recon": recon}
-        sname = {MH: "MUSCL-Hancock", VL: "VL", CTU: "CTU (6 solves/cell, Eq. CFL1)"}[scheme]
-        row = {"workload": "turbulence 256^3", "scheme": sname, "recon": "PPM" if code >= PPM else "PLM",
+        row = {"workload": "turbulence 256^3", "scheme": snames[scheme], "recon": "PPM" if recon == PPM else "PLM",
                "limiter": names[lim], "riemann": rnames[rs]}
         for prec, key in ((A.AMR_FP64, "f64"), (A.AMR_FP32_ACC64, "fp32_acc64")):
             r = run_case(torch, A, UniformGrid, U1, 256, prec, K, W, stream, want_e2e=False, scheme=sch)
