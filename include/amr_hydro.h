@@ -116,6 +116,13 @@ typedef struct {
     int scheme;          /* amr_scheme (0: MUSCL-Hancock); AMR_SCHEME_VL needs lmax = 0; the
                             dt of AMR_SCHEME_CTU follows Eq. (CFL1), of the others Eq. (CFL2) */
     int recon;           /* amr_recon (0: PLM); PPM not with AMR_SCHEME_VL */
+    int fallback;        /* 1: remedies for unphysical results (section 2.2): the Roe solver
+                            falls back to HLLE where an intermediate state has rho <= 0 or
+                            P <= 0; an unphysical updated cell is recomputed first order
+                            unsplit from U^n, then first order dimensionally split */
+    double dt_min;       /* > 0: a level step that leaves unphysical cells is recomputed with
+                            dt x 0.8 until it succeeds or dt < dt_min (AMR_E_UNPHYSICAL);
+                            0: no retry */
 } amr_hydro_params;
 
 typedef struct amr_hydro_ctx amr_hydro_ctx; /* opaque, library-owned */
@@ -125,8 +132,8 @@ typedef struct amr_hydro_ctx amr_hydro_ctx; /* opaque, library-owned */
  * cfl<=0, lmax outside 0..7, root_n not a positive multiple of 16,
  * max_patches not a positive multiple of 8, non-periodic boundaries, a
  * limiter, riemann or scheme value outside its enum, minmod_coeff neither 0
- * nor in [1, 2], AMR_SCHEME_VL with lmax > 0 or with AMR_RECON_PPM, and a
- * recon value outside its enum. */
+ * nor in [1, 2], AMR_SCHEME_VL with lmax > 0 or with AMR_RECON_PPM, a
+ * recon value outside its enum, fallback not 0 or 1, and dt_min < 0. */
 amr_status amr_hydro_init(const amr_hydro_params *params, void *cuda_stream,
                           amr_hydro_ctx **out);
 
@@ -221,14 +228,20 @@ amr_status amr_hydro_touch_level(amr_hydro_ctx *ctx, int level);
 amr_status amr_hydro_fill_ghost(amr_hydro_ctx *ctx, int level, double t);
 
 /*
- * Advance every patch group of `level` by one MUSCL-Hancock step of size dt
- * (section 2.2): gather the 20^3 ghosted tile, PLM + van Leer limiter,
- * Hancock half step, HLLC at every face, conservative update into the other
- * buffer, coarse-fine flux registers, and the CFL reduction of the new
- * state (fused).  dt < 0 means: use the device-side dt of Eq. (CFL2) from the
+ * Advance every patch group of `level` by one step of size dt with the
+ * context's scheme (section 2.2; default MUSCL-Hancock): gather the ghosted
+ * tile, reconstruction + limiter, the scheme's predictor, the Riemann solver
+ * at every face, conservative update into the other buffer, coarse-fine
+ * flux registers, and the CFL reduction of the new state (fused).  dt < 0
+ * means: use the device-side dt of the scheme's CFL condition from the
  * latest reduction (no host synchronisation).  If n_unphysical_out is not
  * NULL the call synchronises and stores the number of updated cells with
- * rho<=0 or P<=0, returning AMR_E_UNPHYSICAL when it is not zero.
+ * rho<=0 or P<=0 (after the per-cell remedies when params.fallback is set),
+ * returning AMR_E_UNPHYSICAL when it is not zero.  With params.dt_min > 0
+ * the call synchronises after every attempt and retries the step from the
+ * same state with dt x 0.8 while cells stay unphysical, returning
+ * AMR_E_UNPHYSICAL once dt < dt_min; the level's time then advances by the
+ * dt actually taken.
  */
 amr_status amr_hydro_advance_level(amr_hydro_ctx *ctx, int level, double dt,
                                    int64_t *n_unphysical_out);

@@ -41,6 +41,8 @@ def lib():
         L.or_set_vl.argtypes = [ctypes.c_int]
         L.or_set_ctu.argtypes = [ctypes.c_int]
         L.or_set_ppm.argtypes = [ctypes.c_int]
+        L.or_set_fallback.argtypes = [ctypes.c_int]
+        L.or_fallback_counts.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
         L.or_ppm_faces.argtypes = [_dp, _dp, _dp]
         L.or_max_speed1.argtypes = [_dp, ctypes.c_int64, ctypes.c_double]
         L.or_max_speed1.restype = ctypes.c_double
@@ -120,24 +122,26 @@ RS_HLLC, RS_HLLE, RS_ROE, RS_EXACT = 0, 1, 2, 3
 _ctu = [False]  # the CTU scheme takes its dt from Eq. CFL1
 
 
-def set_scheme(limiter=LIM_VANLEER, riemann=RS_HLLC, theta=1.5, vl=False, ctu=False, ppm=False):
+def set_scheme(limiter=LIM_VANLEER, riemann=RS_HLLC, theta=1.5, vl=False, ctu=False, ppm=False, fallback=False):
     """Select the slope limiter, the Riemann solver, the generalized minmod
     coefficient, the integration scheme (VL half step, CTU, else
-    MUSCL-Hancock) and PPM reconstruction (else PLM) of every later oracle
-    step (process-wide)."""
+    MUSCL-Hancock), PPM reconstruction (else PLM) and the per-cell remedies
+    for unphysical results of every later oracle step (process-wide)."""
     assert not (vl and ctu)
     lib().or_set_scheme(limiter, riemann, theta)
     lib().or_set_vl(1 if vl else 0)
     lib().or_set_ctu(1 if ctu else 0)
     lib().or_set_ppm(1 if ppm else 0)
+    lib().or_set_fallback(1 if fallback else 0)
     _ctu[0] = bool(ctu)
 
 
 class scheme:
     """Context manager: a scheme for the steps inside, the default after."""
 
-    def __init__(self, limiter=LIM_VANLEER, riemann=RS_HLLC, theta=1.5, vl=False, ctu=False, ppm=False):
-        self.args = (limiter, riemann, theta, vl, ctu, ppm)
+    def __init__(self, limiter=LIM_VANLEER, riemann=RS_HLLC, theta=1.5, vl=False, ctu=False, ppm=False,
+                 fallback=False):
+        self.args = (limiter, riemann, theta, vl, ctu, ppm, fallback)
 
     def __enter__(self):
         set_scheme(*self.args)
@@ -270,6 +274,27 @@ def run_periodic(U, dh, gamma, cfl, n_steps):
             raise FloatingPointError(f"{nbad} unphysical cells")
         dts.append(dt)
     return U, dts
+
+
+def fallback_counts(reset=True):
+    """Cells the per-cell remedies handled since the last reset: (fixed by the
+    first-order unsplit update, fixed by the split one, still unphysical)."""
+    out = (ctypes.c_int64 * 3)()
+    lib().or_fallback_counts(out, 1 if reset else 0)
+    return tuple(out)
+
+
+def step_retry(U, dh, dt, gamma, dt_min, factor=0.8):
+    """One step with the level remedies (iv)-(v): while cells stay unphysical
+    after the per-cell remedies, retry from U with dt * factor; give up below
+    dt_min.  Returns (U_new, dt taken) or raises FloatingPointError."""
+    while True:
+        Un, nbad = step_periodic(U, dh, dt, gamma)
+        if nbad == 0:
+            return Un, dt
+        dt *= factor
+        if dt < dt_min:
+            raise FloatingPointError(f"{nbad} unphysical cells at the minimum dt")
 
 
 def conserved_sum(U, dV):

@@ -71,6 +71,24 @@
  * W_L = 3 W_i - 2 W_R and d m < -d^2 sets W_R = 3 W_i - 2 W_L.  The face
  * values replace W -/+ dW/2 in every scheme above.  or_set_ppm(1) selects it.
  *
+ * Unphysical results (section 2.2 lists GAMER's remedies; or_set_fallback(1)
+ * enables the per-cell ones):
+ *   (0)   a face whose left or right state has rho <= 0 or P <= 0 has no
+ *         flux (NaN), so the cells on both sides count as unphysical;
+ *   (i)   the Roe solver checks its two intermediate states U_L + alpha_1 K_1
+ *         and U_R - alpha_5 K_5 (and the Roe sound speed); if either has
+ *         rho <= 0 or P <= 0 the face takes the HLLE flux instead;
+ *   (ii)  a cell whose updated state has rho <= 0 or P <= 0 is recomputed
+ *         first order in space and time, unsplit:
+ *         U^n - (dt/dh) sum_d [F_d(U_i, U_i+1) - F_d(U_i-1, U_i)] with the
+ *         selected solver on cell averages;
+ *   (iii) if that is still unphysical, first order dimensionally split: an
+ *         x sweep of U^n, a y sweep of its result, a z sweep of that (each
+ *         sweep V - (dt/dh)[F(V_i, V_i+1) - F(V_i-1, V_i)] along its axis);
+ *   cells still unphysical after (iii) are counted, and the driver retries
+ *   the whole step with dt x 0.8 (iv) down to a minimum dt (v).
+ * The fluxes returned for the flux registers stay those of the scheme.
+ *
  * Every per-cell loop is independent, so the OpenMP static split changes no
  * result: the oracle is bitwise reproducible for any thread count (the
  * paper's section 2.7.1 property).
@@ -144,12 +162,23 @@ double or_vanleer(double a, double b) {
 /* limiter: 0 van Leer-type, 1 generalized minmod, 2 van Albada-type,
  * 3 hybrid generalized minmod / van Leer-type; riemann: 0 HLLC, 1 HLLE;
  * theta: the generalized minmod coefficient. */
-static int or_limiter_id = 0, or_riemann_id = 0, or_vl = 0, or_ctu = 0, or_ppm = 0;
+static int or_limiter_id = 0, or_riemann_id = 0, or_vl = 0, or_ctu = 0, or_ppm = 0, or_fallback = 0;
 static double or_theta = 1.5;
 
 void or_set_vl(int on) { or_vl = on; }
 void or_set_ctu(int on) { or_ctu = on; }
 void or_set_ppm(int on) { or_ppm = on; }
+void or_set_fallback(int on) { or_fallback = on; }
+
+/* Cells the per-cell remedies handled since the last reset: fixed by (ii),
+ * fixed by (iii), still unphysical (test instrumentation). */
+static int64_t or_fb_count[3];
+void or_fallback_counts(int64_t *out, int reset) {
+    for (int k = 0; k < 3; k++) {
+        out[k] = or_fb_count[k];
+        if (reset) or_fb_count[k] = 0;
+    }
+}
 
 void or_set_scheme(int limiter, int riemann, double theta) {
     or_limiter_id = limiter;
@@ -217,6 +246,15 @@ void or_ppm_faces(const double *w, double *wl, double *wr) {
     *wr = r;
 }
 
+/* With the remedies on, every solver gives a face whose left or right state
+ * has rho <= 0 or P <= 0 no flux (every component NaN), so the cells on both
+ * sides of it count as unphysical and take the cell remedies.  Compares only. */
+static int or_no_flux(const double *WL, const double *WR, double *F) {
+    if (!or_fallback || (WL[0] > 0.0 && WL[4] > 0.0 && WR[0] > 0.0 && WR[4] > 0.0)) return 0;
+    for (int v = 0; v < NV; v++) F[v] = NAN;
+    return 1;
+}
+
 /* ---- HLLC Riemann solver (section 2.2; Toro 2009 ch. 10 form) ---------- */
 
 /* Flux across a face normal to direction d, left state UL, right state UR. */
@@ -224,6 +262,7 @@ void or_hllc(const double *UL, const double *UR, int d, double gamma, double *F)
     double WL[NV], WR[NV], FL[NV], FR[NV];
     or_prim(UL, WL, gamma);
     or_prim(UR, WR, gamma);
+    if (or_no_flux(WL, WR, F)) return;
     or_flux(UL, d, gamma, FL);
     or_flux(UR, d, gamma, FR);
 
@@ -283,6 +322,7 @@ void or_hlle(const double *UL, const double *UR, int d, double gamma, double *F)
     double WL[NV], WR[NV], FL[NV], FR[NV];
     or_prim(UL, WL, gamma);
     or_prim(UR, WR, gamma);
+    if (or_no_flux(WL, WR, F)) return;
     or_flux(UL, d, gamma, FL);
     or_flux(UR, d, gamma, FR);
     double rl = WL[0], pl = WL[4], ul = WL[1 + d];
@@ -321,6 +361,7 @@ void or_roe(const double *UL, const double *UR, int d, double gamma, double *F) 
     double WL[NV], WR[NV], FL[NV], FR[NV];
     or_prim(UL, WL, gamma);
     or_prim(UR, WR, gamma);
+    if (or_no_flux(WL, WR, F)) return;
     or_flux(UL, d, gamma, FL);
     or_flux(UR, d, gamma, FR);
     double sl = sqrt(WL[0]), sr = sqrt(WR[0]);
@@ -365,6 +406,25 @@ void or_roe(const double *UL, const double *UR, int d, double gamma, double *F) 
         D[4] += sh * u[k];
     }
     for (int v = 0; v < NV; v++) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * D[v];
+    if (or_fallback) {
+        /* (i): the intermediate states U_L + a1 K1 and U_R - a5 K5 */
+        double Us[2][NV];
+        for (int s2 = 0; s2 < 2; s2++) {
+            const double al = s2 == 0 ? a1 : -a5, sg = s2 == 0 ? -1.0 : 1.0;
+            const double *U0 = s2 == 0 ? UL : UR;
+            Us[s2][0] = U0[0] + al;
+            for (int k = 0; k < 3; k++) Us[s2][1 + k] = U0[1 + k] + al * u[k];
+            Us[s2][1 + d] += al * sg * a;
+            Us[s2][4] = U0[4] + al * (H + sg * un * a);
+        }
+        int bad = !(a > 0.0);
+        for (int s2 = 0; s2 < 2 && !bad; s2++) {
+            double Wt[NV];
+            or_prim(Us[s2], Wt, gamma);
+            bad = !(Wt[0] > 0.0) || !(Wt[4] > 0.0);
+        }
+        if (bad) or_hlle(UL, UR, d, gamma, F);
+    }
 }
 
 /* ---- exact Riemann solver flux (section 2.2; Toro 2009 ch. 4) ----------- */
@@ -377,6 +437,7 @@ void or_exact_flux(const double *UL, const double *UR, int d, double gamma, doub
     double WL[NV], WR[NV], W[NV], U[NV];
     or_prim(UL, WL, gamma);
     or_prim(UR, WR, gamma);
+    if (or_no_flux(WL, WR, F)) return;
     double ps, us, xi = 0.0, r, v, q;
     or_exact_star(WL[0], WL[1 + d], WL[4], WR[0], WR[1 + d], WR[4], gamma, &ps, &us);
     or_exact_sample(WL[0], WL[1 + d], WL[4], WR[0], WR[1 + d], WR[4], gamma, &xi, 1, &r, &v, &q);
@@ -470,6 +531,66 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
 int64_t or_step_periodic(const double *U, double *Unew, int nx, int ny, int nz,
                          double dh, double dt, double gamma) {
     return or_step_periodic_fx(U, Unew, nx, ny, nz, dh, dt, gamma, NULL);
+}
+
+/* Whether a conserved state has rho > 0 and P > 0. */
+static int or_physical(const double *u, double gamma) {
+    double w[NV];
+    or_prim(u, w, gamma);
+    return w[0] > 0.0 && w[4] > 0.0;
+}
+
+/* The first-order update of one cell along d from V_m, V_0, V_p (cells i-1,
+ * i, i+1 along d): V_0 - r [F(V_0, V_p) - F(V_m, V_0)]. */
+static void or_sweep(const double *Vm, const double *V0, const double *Vp, int d, double r, double gamma,
+                     double *out) {
+    double Fp[NV], Fm[NV];
+    or_riemann(V0, Vp, d, gamma, Fp);
+    or_riemann(Vm, V0, d, gamma, Fm);
+    for (int v = 0; v < NV; v++) out[v] = V0[v] - r * (Fp[v] - Fm[v]);
+}
+
+/* Remedies (ii) and (iii) for cell (x, y, z) of U^n: the first-order unsplit
+ * update, and if that is unphysical the first-order split one (x, then y,
+ * then z sweeps over the cell's 3x3x3 neighbourhood).  Writes the state to
+ * out and returns whether it is physical. */
+static int or_fallback_cell(const double *U, int nx, int ny, int nz, int x, int y, int z, double dh, double dt,
+                            double gamma, double *out) {
+    const int64_t n = (int64_t)nx * ny * nz;
+    double B[3][3][3][NV]; /* B[k][j][i] = U^n at (x+i-1, y+j-1, z+k-1) */
+    for (int k = 0; k < 3; k++)
+        for (int j = 0; j < 3; j++)
+            for (int i = 0; i < 3; i++) {
+                int64_t c = cell_index(wrap(x + i - 1, nx), wrap(y + j - 1, ny), wrap(z + k - 1, nz), nx, ny);
+                for (int v = 0; v < NV; v++) B[k][j][i][v] = U[v * n + c];
+            }
+    const double r = dt / dh;
+    /* (ii) */
+    double div[NV] = {0, 0, 0, 0, 0};
+    for (int d = 0; d < 3; d++) {
+        const double *um = d == 0 ? B[1][1][0] : (d == 1 ? B[1][0][1] : B[0][1][1]);
+        const double *up = d == 0 ? B[1][1][2] : (d == 1 ? B[1][2][1] : B[2][1][1]);
+        double Fp[NV], Fm[NV];
+        or_riemann(B[1][1][1], up, d, gamma, Fp);
+        or_riemann(um, B[1][1][1], d, gamma, Fm);
+        for (int v = 0; v < NV; v++) div[v] += Fp[v] - Fm[v];
+    }
+    for (int v = 0; v < NV; v++) out[v] = B[1][1][1][v] - r * div[v];
+    if (or_physical(out, gamma)) {
+#pragma omp atomic
+        or_fb_count[0]++;
+        return 1;
+    }
+    /* (iii) */
+    double X[3][3][NV], Y[3][NV];
+    for (int k = 0; k < 3; k++)
+        for (int j = 0; j < 3; j++) or_sweep(B[k][j][0], B[k][j][1], B[k][j][2], 0, r, gamma, X[k][j]);
+    for (int k = 0; k < 3; k++) or_sweep(X[k][0], X[k][1], X[k][2], 1, r, gamma, Y[k]);
+    or_sweep(Y[0], Y[1], Y[2], 2, r, gamma, out);
+    const int ok = or_physical(out, gamma);
+#pragma omp atomic
+    or_fb_count[ok ? 1 : 2]++;
+    return ok;
 }
 
 /* Riemann fluxes FX[d][var][cell] through the high face of every cell along d
@@ -662,9 +783,14 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
                     un[v] = U[v * n + i] - dt / dh * div;
                     Unew[v * n + i] = un[v];
                 }
-                double w[NV];
-                or_prim(un, w, gamma);
-                if (!(w[0] > 0.0) || !(w[4] > 0.0)) nbad++;
+                if (!or_physical(un, gamma)) {
+                    int ok = 0;
+                    if (or_fallback) { /* (ii), (iii) */
+                        ok = or_fallback_cell(U, nx, ny, nz, x, y, z, dh, dt, gamma, un);
+                        for (int v = 0; v < NV; v++) Unew[v * n + i] = un[v];
+                    }
+                    if (!ok) nbad++;
+                }
             }
 
     if (FX_out) memcpy(FX_out, FX, sizeof(double) * 3 * NV * n);

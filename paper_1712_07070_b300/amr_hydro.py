@@ -41,7 +41,7 @@ class amr_hydro_params(ctypes.Structure):
         ("nbuf", ctypes.c_int * 8), ("prec", ctypes.c_int), ("periodic", ctypes.c_int * 3),
         ("box", ctypes.c_double * 3), ("root_n", ctypes.c_int * 3), ("max_patches", ctypes.c_int),
         ("limiter", ctypes.c_int), ("riemann", ctypes.c_int), ("minmod_coeff", ctypes.c_double),
-        ("scheme", ctypes.c_int), ("recon", ctypes.c_int),
+        ("scheme", ctypes.c_int), ("recon", ctypes.c_int), ("fallback", ctypes.c_int), ("dt_min", ctypes.c_double),
     ]
 
 
@@ -287,9 +287,10 @@ def amr_hydro_level_info(ctx, level):
 def make_params(gamma=5.0 / 3.0, cfl=0.5, root_n=(64, 64, 64), box=None, lmax=0,
                 prec=AMR_FP64, max_patches=None, theta=0.05, c_inc=0.1, c_dec=0.1, nbuf=None,
                 limiter=AMR_LIM_VANLEER, riemann=AMR_RS_HLLC, minmod_coeff=1.5, scheme=AMR_SCHEME_MH,
-                recon=AMR_RECON_PLM):
+                recon=AMR_RECON_PLM, fallback=0, dt_min=0.0):
     p = amr_hydro_params()
     p.limiter, p.riemann, p.minmod_coeff, p.scheme, p.recon = limiter, riemann, minmod_coeff, scheme, recon
+    p.fallback, p.dt_min = fallback, dt_min
     p.gamma, p.cfl, p.c_inc, p.c_dec, p.theta = gamma, cfl, c_inc, c_dec, theta
     p.lmax = lmax
     nb = nbuf if nbuf is not None else [8] * 8

@@ -254,6 +254,8 @@ amr_status amr_hydro_init(const amr_hydro_params *p, void *stream, amr_hydro_ctx
     if (p->scheme < AMR_SCHEME_MH || p->scheme > AMR_SCHEME_CTU) return AMR_E_INVAL;
     if (p->recon != AMR_RECON_PLM && p->recon != AMR_RECON_PPM) return AMR_E_INVAL;
     if (p->scheme == AMR_SCHEME_VL && p->recon != AMR_RECON_PLM) return AMR_E_INVAL;
+    if (p->fallback != 0 && p->fallback != 1) return AMR_E_INVAL;
+    if (!(p->dt_min >= 0.0)) return AMR_E_INVAL;
     // VL on refined levels would need the half-step state in a 3-cell ring of
     // the coarse-fine ghost patches: single-level grids only
     if (p->scheme == AMR_SCHEME_VL && p->lmax > 0) return AMR_E_INVAL;
@@ -278,6 +280,13 @@ amr_status amr_hydro_init(const amr_hydro_params *p, void *stream, amr_hydro_ctx
     c->step_bps = step_blocks_per_sm(p->prec, p->scheme, p->recon);
     if ((st = c->scal.reserve(SCAL_N))) { amr_hydro_destroy(c); return st; }
     if ((st = c->dtbuf.reserve(3 * (MAX_LEVELS + MAX_BOXES)))) { amr_hydro_destroy(c); return st; }
+    if (p->fallback) {
+        if ((st = c->fb_list.reserve(FB_CAP)) || (st = c->fb_count.reserve(1)) ||
+            (st = cuda_fail(cudaMemsetAsync(c->fb_count.p, 0, 8, c->stream), "memset"))) {
+            amr_hydro_destroy(c);
+            return st;
+        }
+    }
     if ((st = cuda_fail(cudaMemsetAsync(c->scal.p, 0, sizeof(unsigned long long) * SCAL_N, c->stream),
                         "memset"))) {
         amr_hydro_destroy(c);
@@ -309,6 +318,8 @@ amr_status amr_hydro_destroy(amr_hydro_ctx *c) {
     for (cudaEvent_t e : c->slab_ev) cudaEventDestroy(e);
     c->hstage[0].release();
     c->hstage[1].release();
+    c->fb_list.release();
+    c->fb_count.release();
     delete c;
     return AMR_OK;
 }

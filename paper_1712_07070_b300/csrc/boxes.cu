@@ -241,6 +241,7 @@ amr_status amr_hydro_advance_boxes(amr_hydro_ctx *c, int n_boxes, const int *box
     L.limiter = c->prm.limiter;
     L.riemann = c->prm.riemann;
     L.theta = c->prm.minmod_coeff;
+    L.fallback = c->prm.fallback;
     L.n_boxes = n_boxes;
 
     // autotune the launch shape once per box set

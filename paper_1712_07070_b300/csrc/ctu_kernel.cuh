@@ -373,7 +373,7 @@ __device__ __forceinline__ void ctu_run(SM &S, const StepParams &P, const int32_
             }
             bool ok;
             const real s = cfl_speed(ur, g, ok, true);
-            if (!ok) nbad++;
+            if (!ok && !fb_append(P, base)) nbad++;
             if (s > smax_r) smax_r = s;
         }
         if (inner) {

@@ -68,6 +68,8 @@ struct Level {
     bool bound = false;          // capacity arrays registered (levels >= 1)
     int32_t *w_corner = nullptr, *w_sib = nullptr, *w_parent = nullptr, *w_child = nullptr;
     double dt_prev = -1.0;       // last step size (W-cycle)
+    double dt_last = 0.0;        // dt argument of the level's last step (< 0: the device's CFL dt)
+    DevBuf<double> freg_save;    // fine registers before a step that may be retried
     int scal0 = 0;  // first of this level's 8 scalar slots
     int ring = 0;   // ring position of the newest state
     bool speed_valid = false;
@@ -84,6 +86,7 @@ struct Level {
         freg.release();
         coarse_off.release();
         creg.release();
+        freg_save.release();
         fix_list.release();
         restrict_list.release();
         n_patches = n_groups = 0;
@@ -140,6 +143,9 @@ struct amr_hydro_ctx {
     cudaStream_t xfer[2] = {nullptr, nullptr};
     std::vector<cudaEvent_t> slab_ev;
     amrh::DevBuf<double> hstage[2];
+    // cells the step left unphysical, for the cell remedies (params.fallback)
+    amrh::DevBuf<int64_t> fb_list;
+    amrh::DevBuf<unsigned long long> fb_count;
 };
 
 namespace amrh {
@@ -152,6 +158,9 @@ void scheme_stages(int scheme, int recon, int &lo, int &hi);
 struct StepParams;
 amr_status launch_step(amr_hydro_ctx *c, const StepParams &P, int grid);
 amr_status launch_step_raw(int prec, const StepParams &P, cudaStream_t stream);
+amr_status launch_cell_remedies(amr_hydro_ctx *c, const StepParams &P, const double *base, int cfl1,
+                                cudaStream_t s);
+constexpr int64_t FB_CAP = 1 << 20;  // listed cells per step launch (more are counted unphysical)
 amr_status launch_max_speed(int prec, const double *U, int64_t n_slots, double gamma, int cfl1,
                             unsigned long long *smax, unsigned long long *nbad, int n_sm, cudaStream_t stream);
 // AMR (amr_ops.cu, regrid.cpp)
@@ -168,7 +177,8 @@ amr_status build_uniform_tables(const int np[3], int32_t *corner, int32_t *sib, 
                                 int32_t *child);
 amr_status build_nbr_plan(int level, int n_patches, const int32_t *corner, const int32_t *sib,
                           const int32_t *parent, const int level_cells[3],
-                          std::vector<int32_t> &nbr, std::vector<GhostInfo> &ghosts, int ghost_depth = 2);
+                          std::vector<int32_t> &nbr, std::vector<GhostInfo> &ghosts, int ghost_depth = 2,
+                          bool corners = false);
 // z-chains of a level's groups (same-level groups stacked in z), their
 // runs of at most max_len groups, and the run length for a grid (host_plan.cpp).
 void z_chains(int n_groups, const int32_t *nbr, std::vector<int32_t> &chains, std::vector<int32_t> &chain_off);

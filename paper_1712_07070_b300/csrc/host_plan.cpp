@@ -57,10 +57,12 @@ amr_status build_uniform_tables(const int np[3], int32_t *corner, int32_t *sib, 
 // Fails with AMR_E_NESTING when a face or edge neighbour is missing on the
 // root level (nothing to interpolate from).  ghost_depth (even: 2 for PLM, 4
 // for PPM's three ghost cells) is how deep the interpolated box of a ghost
-// patch reaches along an outer direction.
+// patch reaches along an outer direction; with corners, corner positions get
+// ghost patches too (the per-cell remedies read a cell's 3x3x3 block).
 amr_status build_nbr_plan(int level, int n_patches, const int32_t *corner, const int32_t *sib,
                           const int32_t *parent, const int level_cells[3],
-                          std::vector<int32_t> &nbr, std::vector<GhostInfo> &ghosts, int ghost_depth) {
+                          std::vector<int32_t> &nbr, std::vector<GhostInfo> &ghosts, int ghost_depth,
+                          bool corners) {
     const int n_groups = n_patches / 8;
     nbr.assign((size_t)n_groups * 64, -1);
     ghosts.clear();
@@ -108,7 +110,7 @@ amr_status build_nbr_plan(int level, int n_patches, const int32_t *corner, const
                 out[pos] = s;
                 continue;
             }
-            if (e.corner) continue;  // never read
+            if (e.corner && !corners) continue;  // read only by the cell remedies
             if (level == 0 || !parent) return AMR_E_NESTING;
             const int cx = wrapc(corner[3 * own + 0] + e.off[0], level_cells[0]);
             const int cy = wrapc(corner[3 * own + 1] + e.off[1], level_cells[1]);

@@ -123,6 +123,12 @@ extern "C" amr_status amr_hydro_advance_host(amr_hydro_ctx *c, const double *U_i
     P.limiter = c->prm.limiter;
     P.riemann = c->prm.riemann;
     P.theta = c->prm.minmod_coeff;
+    P.fallback = c->prm.fallback;
+    if (c->prm.fallback) {
+        P.fb_count = c->fb_count.p;
+        P.fb_list = c->fb_list.p;
+        P.fb_cap = FB_CAP;
+    }
     P.smax_out = sc + r_out;
     P.n_bad = sc + 3 + r_out;
     P.clear2 = sc + r_clr;  // idempotent: every slab launch zeroes the same two slots
@@ -138,6 +144,8 @@ extern "C" amr_status amr_hydro_advance_host(amr_hydro_ctx *c, const double *U_i
     H.smax_out = H.n_bad = H.clear2 = nullptr;
     H.time_rec = nullptr;
     H.cf = CFRegs{nullptr, nullptr, nullptr, nullptr};
+    H.fb_count = nullptr;
+    H.fb_list = nullptr;
     auto predict = [&](int j) -> amr_status {  // VL half step of slab j
         if (predicted[j]) return AMR_OK;
         predicted[j] = 1;
@@ -166,6 +174,7 @@ extern "C" amr_status amr_hydro_advance_host(amr_hydro_ctx *c, const double *U_i
         P.work0 = k * G;
         P.time_rec = i == 0 ? c->dtbuf.p : nullptr;  // the level's time advances once
         if ((st = launch_step(c, P, grid))) return st;
+        if ((st = launch_cell_remedies(c, P, vl ? P.U_base : P.U_old, stage_ctu(P.stage), cs))) return st;
         k_pack_slab<<<c->n_sm * 4, 256, 0, cs>>>(c->hstage[1].p, nx, ny, nz, k * GE, Unew, 0);
         if ((st = cuda_fail(cudaGetLastError(), "k_unpack_slab"))) return st;
         if ((st = cuda_fail(cudaEventRecord(ev_out[k], cs), "event"))) return st;

@@ -134,7 +134,26 @@ struct Gas {
     real gamma, gm1, inv_gm1;
     int lim = LIM_VANLEER, rs = RS_HLLC;  // uniform over a launch: the branches on them never diverge
     real htheta = real(0.75);             // half the generalized minmod coefficient
+    int fb = 0;                           // remedies for unphysical results: no flux for an unphysical
+                                          // face state, and Roe falls back to HLLE
 };
+
+template <typename real>
+__device__ __forceinline__ real qnan();
+template <>
+__device__ __forceinline__ double qnan<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
+template <>
+__device__ __forceinline__ float qnan<float>() { return __int_as_float(0x7fc00000); }
+
+// x > 0 and finite, on the bit pattern (a NaN or +inf fails)
+__device__ __forceinline__ bool pos_finite(double x) {
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b < 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool pos_finite(float x) {
+    const int b = __float_as_int(x);
+    return b > 0 && b < 0x7f800000;
+}
 
 // |x| and sign transfer on the bit pattern (integer units)
 __device__ __forceinline__ double fabs_(double x) {
@@ -235,6 +254,11 @@ __device__ __noinline__ void exact_flux(const real uL[NV], const real uR[NV], re
     u2w(uR, wR, g);
     const real rl = wL[0], ul = wL[1 + D], pl = wL[4];
     const real rr = wR[0], ur = wR[1 + D], pr = wR[4];
+    if (g.fb && !(pos_finite(rl) && pos_finite(pl) && pos_finite(rr) && pos_finite(pr))) {
+#pragma unroll
+        for (int v = 0; v < NV; v++) F[v] = qnan<real>();  // no flux (as face_flux)
+        return;
+    }
     const real cl = sqrt_(g.gamma * pl / rl), cr = sqrt_(g.gamma * pr / rr);
     const real tol = sizeof(real) == sizeof(double) ? real(1e-15) : real(1e-7);
     real p = real(0.5) * (pl + pr), fl, dfl, fr, dfr;
@@ -304,7 +328,8 @@ __device__ __noinline__ void exact_flux(const real uL[NV], const real uR[NV], re
 //         S_R<=0 -> F_R, S*>=0 -> F*_L;
 //   HLLE: the same outer speeds and ties, one intermediate state;
 //   Roe:  (F_L + F_R)/2 - (1/2) sum_k |lambda_k| alpha_k K_k with Roe
-//         averages, Harten-Hyman entropy fix on the acoustic waves;
+//         averages, Harten-Hyman entropy fix on the acoustic waves; with
+//         g.fb, the HLLE flux when an intermediate state is unphysical;
 //   exact: exact_flux above.
 // Reciprocals are shared: 1/rho from one reciprocal square root per side,
 // which also gives the Roe weight sqrt(rho).
@@ -331,6 +356,13 @@ __device__ __forceinline__ void face_flux(const real uL[NV], const real uR[NV], 
     wR[4] = g.gm1 * (uR[4] - real(0.5) * uR[0] * (wR[1] * wR[1] + wR[2] * wR[2] + wR[3] * wR[3]));
     const real rl = wL[0], pl = wL[4], ul = wL[1 + D];
     const real rr = wR[0], pr = wR[4], ur = wR[1 + D];
+    if (g.fb && !(pos_finite(rl) && pos_finite(pl) && pos_finite(rr) && pos_finite(pr))) {
+        // with the remedies on, an unphysical face state has no flux: NaN marks
+        // both cells unphysical
+#pragma unroll
+        for (int v = 0; v < NV; v++) F[v] = qnan<real>();
+        return;
+    }
     const real cl = sqrt_(g.gamma * pl * ril);
     const real cr = sqrt_(g.gamma * pr * rir);
     const real iw = rcp_(sl + sr);
@@ -377,7 +409,23 @@ __device__ __forceinline__ void face_flux(const real uL[NV], const real uR[NV], 
         }
 #pragma unroll
         for (int v = 0; v < NV; v++) F[v] = real(0.5) * (fl[v] + fr[v]) - real(0.5) * Dv[v];
-        return;
+        if (!g.fb) return;
+        // Remedy (i): the intermediate states U_L + a1 K1 and U_R - a5 K5
+        // (K_1,5 = (1, v -/+ a n, H -/+ v_n a)) must have rho > 0 and P > 0,
+        // that is 2 rho E > |m|^2; otherwise the face takes the HLLE flux.
+        bool ok = pos_finite(a);
+#pragma unroll
+        for (int s2 = 0; s2 < 2; s2++) {
+            const real al = s2 == 0 ? a1 : -a5, sg = s2 == 0 ? real(-1) : real(1);
+            const real *u0 = s2 == 0 ? uL : uR;
+            real m[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++) m[k] = u0[1 + k] + al * vt[k];
+            m[D] += al * sg * a;
+            const real rs2 = u0[0] + al, es = u0[4] + al * (ht + sg * vtn * a);
+            ok = ok && pos_finite(rs2) && pos_finite(real(2) * rs2 * es - (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]));
+        }
+        if (ok) return;
     }
 
     const real SL = min_(ul - cl, vtn - ct);
@@ -391,7 +439,7 @@ __device__ __forceinline__ void face_flux(const real uL[NV], const real uR[NV], 
         phys_flux<D>(wR, uR, F);
         return;
     }
-    if (g.rs == RS_HLLE) {  // one intermediate state: (S_R F_L - S_L F_R + S_L S_R (U_R - U_L))/(S_R - S_L)
+    if (g.rs == RS_HLLE || g.rs == RS_ROE) {  // one intermediate state: (S_R F_L - S_L F_R + S_L S_R (U_R - U_L))/(S_R - S_L)
         real fl[NV], fr[NV];
         phys_flux<D>(wL, uL, fl);
         phys_flux<D>(wR, uR, fr);
@@ -425,12 +473,13 @@ __device__ __forceinline__ void face_flux(const real uL[NV], const real uR[NV], 
 
 // Signal speed of Eq. (CFL2), |vx|+|vy|+|vz|+3c_s, or with cfl1 of Eq. (CFL1),
 // max(|vx|,|vy|,|vz|)+c_s, of one conserved state, and whether the state is
-// physical (rho>0 and P>0).
+// physical (rho>0 and P>0, both finite: a NaN from a face state with negative
+// pressure counts as unphysical).
 template <typename real>
 __device__ __forceinline__ real cfl_speed(const real u[NV], const Gas<real> &g, bool &ok, bool cfl1 = false) {
     real w[NV];
     const real ri = u2w(u, w, g);
-    ok = gt0(w[0]) && gt0(w[4]);
+    ok = pos_finite(w[0]) && pos_finite(w[4]);
     const real cs = sqrt_(g.gamma * w[4] * ri);
     if (cfl1) return max_(max_(fabs(w[1]), fabs(w[2])), fabs(w[3])) + cs;
     return fabs(w[1]) + fabs(w[2]) + fabs(w[3]) + real(3) * cs;

@@ -112,11 +112,14 @@ amr_status amr_hydro_touch_level(amr_hydro_ctx *c, int level) {
     return AMR_OK;
 }
 
-amr_status amr_hydro_advance_level(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphysical_out) {
-    if (!c || level < 0 || level > c->prm.lmax) return AMR_E_INVAL;
+}  // extern "C"
+
+namespace {
+
+// One step of a level (the body of amr_hydro_advance_level without the
+// retry of remedy (iv)).
+amr_status advance_once(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphysical_out) {
     Level &L = c->lv[level];
-    if (!L.n_patches) return AMR_E_INVAL;
-    if (!(dt >= 0.0) && !(dt < 0.0)) return AMR_E_INVAL;  // NaN
     amr_status st;
     if (L.n_ghost) {  // coarse-fine ghosts need the level's time on the host
         if ((st = sync_level_time(c, L, level))) return st;
@@ -142,6 +145,12 @@ amr_status amr_hydro_advance_level(amr_hydro_ctx *c, int level, double dt, int64
     P.limiter = c->prm.limiter;
     P.riemann = c->prm.riemann;
     P.theta = c->prm.minmod_coeff;
+    P.fallback = c->prm.fallback;
+    if (c->prm.fallback) {
+        P.fb_count = c->fb_count.p;
+        P.fb_list = c->fb_list.p;
+        P.fb_cap = FB_CAP;
+    }
     P.smax_out = sc + r_out;
     P.n_bad = sc + 3 + r_out;
     P.clear2 = sc + r_clr;
@@ -176,12 +185,17 @@ amr_status amr_hydro_advance_level(amr_hydro_ctx *c, int level, double dt, int64
         H.smax_out = H.n_bad = H.clear2 = nullptr;
         H.time_rec = nullptr;
         H.cf = CFRegs{nullptr, nullptr, nullptr, nullptr};
+        H.fb_count = nullptr;
+        H.fb_list = nullptr;
         if ((st = launch_step(c, H, grid))) return st;
         P.stage = ST_VL_CORR;
         P.U_base = P.U_old;
         P.U_old = L.ustar.p;
     }
     if ((st = launch_step(c, P, grid))) return st;
+    if ((st = launch_cell_remedies(c, P, P.stage == ST_VL_CORR ? P.U_base : P.U_old, stage_ctu(P.stage),
+                                   c->stream)))
+        return st;
 
     L.cur = 1 - L.cur;
     if (dt >= 0.0 && !L.t_pending) {
@@ -192,6 +206,7 @@ amr_status amr_hydro_advance_level(amr_hydro_ctx *c, int level, double dt, int64
     }
     L.ring = r_out;
     L.speed_valid = true;
+    L.dt_last = dt;
 
     if (n_unphysical_out) {
         unsigned long long nb = 0;
@@ -202,6 +217,76 @@ amr_status amr_hydro_advance_level(amr_hydro_ctx *c, int level, double dt, int64
         if (nb) return AMR_E_UNPHYSICAL;
     }
     return AMR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+amr_status amr_hydro_advance_level(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphysical_out) {
+    if (!c || level < 0 || level > c->prm.lmax) return AMR_E_INVAL;
+    Level &L = c->lv[level];
+    if (!L.n_patches) return AMR_E_INVAL;
+    if (!(dt >= 0.0) && !(dt < 0.0)) return AMR_E_INVAL;  // NaN
+    if (!(c->prm.dt_min > 0.0)) return advance_once(c, level, dt, n_unphysical_out);
+
+    // Remedies (iv)-(v) (section 2.2): while cells stay unphysical after the
+    // per-cell remedies, recompute the whole level from U^n with dt x 0.8,
+    // down to dt_min.  U^n is untouched by a step (it writes the other
+    // buffer); the level's host time, ring position and device time record,
+    // the reduction slots the step accumulated into and the fine flux
+    // registers the step added to are put back before each retry.
+    amr_status st;
+    if ((st = sync_level_time(c, L, level))) return st;
+    const int cur = L.cur, ring = L.ring;
+    const bool valid = L.speed_valid;
+    const double t = L.t, t_prev = L.t_prev;
+    double rec[3];
+    if ((st = cuda_fail(cudaMemcpy(rec, c->dtbuf.p + 3 * level, 24, cudaMemcpyDeviceToHost), "d2h time"))) return st;
+    const size_t nfr = (size_t)1280 * L.n_freg;
+    if (level > 0 && nfr) {
+        if ((st = L.freg_save.reserve(nfr))) return st;
+        if ((st = cuda_fail(cudaMemcpyAsync(L.freg_save.p, L.freg.p, 8 * nfr, cudaMemcpyDeviceToDevice, c->stream),
+                            "save registers")))
+            return st;
+    }
+    double step = dt;
+    for (;;) {
+        int64_t nb = 0;
+        st = advance_once(c, level, step, &nb);
+        if (st != AMR_E_UNPHYSICAL) {
+            if (n_unphysical_out) *n_unphysical_out = st == AMR_OK ? 0 : nb;
+            return st;
+        }
+        if (step < 0.0) {  // the device took its own CFL dt
+            double used[3];
+            if ((st = cuda_fail(cudaMemcpy(used, c->dtbuf.p + 3 * level, 24, cudaMemcpyDeviceToHost), "d2h time")))
+                return st;
+            step = used[0];
+        }
+        L.cur = cur;
+        L.ring = ring;
+        L.speed_valid = valid;
+        L.t = t;
+        L.t_prev = t_prev;
+        L.t_pending = false;
+        unsigned long long *sc = c->scal.p + L.scal0;
+        const int r_out = (ring + 1) % 3;
+        if ((st = cuda_fail(cudaMemsetAsync(sc + r_out, 0, 8, c->stream), "memset")) ||
+            (st = cuda_fail(cudaMemsetAsync(sc + 3 + r_out, 0, 8, c->stream), "memset")) ||
+            (st = cuda_fail(cudaMemcpyAsync(c->dtbuf.p + 3 * level, rec, 24, cudaMemcpyHostToDevice, c->stream),
+                            "h2d time")))
+            return st;
+        if (level > 0 && nfr &&
+            (st = cuda_fail(cudaMemcpyAsync(L.freg.p, L.freg_save.p, 8 * nfr, cudaMemcpyDeviceToDevice, c->stream),
+                            "restore registers")))
+            return st;
+        step *= 0.8;
+        if (step < c->prm.dt_min) {
+            if (n_unphysical_out) *n_unphysical_out = nb;
+            return AMR_E_UNPHYSICAL;
+        }
+    }
 }
 
 }  // extern "C"

@@ -55,7 +55,7 @@ amr_status plan_level(amr_hydro_ctx *c, int level) {
     std::vector<GhostInfo> ghosts;
     amr_status st = build_nbr_plan(level, L.n_patches, L.corner.data(), L.sib.data(),
                                    level > 0 ? L.parent.data() : nullptr, cells, nbr, ghosts,
-                                   c->prm.recon == AMR_RECON_PPM ? 4 : 2);
+                                   c->prm.recon == AMR_RECON_PPM ? 4 : 2, c->prm.fallback != 0);
     if (st) return st;
     if ((st = upload(L.nbr, nbr, c->stream))) return st;
     {  // z-runs of the length the round-robin cost estimate prefers
@@ -424,6 +424,11 @@ amr_status advance_rec(amr_hydro_ctx *c, int l, double dt0, int64_t *updates) {
             }
         }
         if ((st = amr_hydro_advance_level(c, l, step, nullptr))) return st;
+        if (L.dt_last != step) {  // the level retried with a smaller dt (remedy iv)
+            step = L.dt_last;
+            last = false;
+            if (l == 0) target = L.t;
+        }
         if (last || l == 0) L.t = target;
         L.dt_prev = step;
         if (updates) *updates += (int64_t)L.n_patches * 512;

@@ -108,6 +108,12 @@ struct StepParams {
     double cfl, dh, gamma;
     int limiter, riemann;                    // amr_limiter / amr_riemann
     double theta;                            // generalized minmod coefficient
+    int fallback;                            // remedy (i): the Roe solver checks its intermediate states
+    // remedies (ii)-(iii): unphysical updated cells are appended (as their
+    // offset of variable 0 in U_new) for the cell-remedy kernel; null: counted
+    unsigned long long *fb_count;
+    int64_t *fb_list;
+    int64_t fb_cap;
     unsigned long long *smax_out;            // max signal speed of the new state (bits)
     unsigned long long *n_bad;               // count of unphysical new cells
     unsigned long long *clear2;              // two scalars the kernel zeroes for the next step
@@ -200,6 +206,16 @@ __device__ __forceinline__ const double *patch_src(const StepParams &P, int s) {
     if (s >= 0) return P.U_old + (int64_t)s * PSLOT;
     if (s <= -2) return P.ghost + (int64_t)(-2 - s) * PSLOT;
     return nullptr;
+}
+
+// An unphysical updated cell (offset base of its variable 0 in U_new): into
+// the list of the cell-remedy kernel when there is one and it has room.
+__device__ __forceinline__ bool fb_append(const StepParams &P, int64_t base) {
+    if (!P.fb_list) return false;
+    const unsigned long long k = atomicAdd(P.fb_count, 1ull);
+    if ((int64_t)k >= P.fb_cap) return false;
+    P.fb_list[k] = base;
+    return true;
 }
 
 // Load tile plane tl (-2..17 within the group of table slot ts) into the
@@ -692,7 +708,7 @@ __device__ __forceinline__ void step_run(SM &S, const StepParams &P, const int32
             if constexpr (STAGE != ST_VL_PRED) {
                 bool ok;
                 const real s = cfl_speed(ur, g, ok);
-                if (!ok) nbad++;
+                if (!ok && !fb_append(P, base)) nbad++;
                 if (s > smax_r) smax_r = s;
             }
         }
@@ -752,6 +768,7 @@ __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydr
     }
     if constexpr (MODE == 1)  // a value the compiler can see is never RS_EXACT
         g.rs = P.riemann == RS_HLLE ? RS_HLLE : (P.riemann == RS_ROE ? RS_ROE : RS_HLLC);
+    g.fb = P.fallback;
     if constexpr (MODE == 2) g.rs = RS_EXACT;
 
     if (tid == 0) {
@@ -826,6 +843,7 @@ struct BoxLaunch {
     double cfl, gamma;
     int limiter, riemann;  // amr_limiter / amr_riemann
     double theta;          // generalized minmod coefficient
+    int fallback;          // remedies for unphysical results
     double dt_override; // >= 0 (autotuning): fixed dt, no logging
     double *dt_log;     // [steps][n_boxes] or null
     int n_boxes;
@@ -853,6 +871,7 @@ __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydr
     }
     if constexpr (MODE == 1)  // a value the compiler can see is never RS_EXACT
         g.rs = B.riemann == RS_HLLE ? RS_HLLE : (B.riemann == RS_ROE ? RS_ROE : RS_HLLC);
+    g.fb = B.fallback;
     if constexpr (MODE == 2) g.rs = RS_EXACT;
     int first, last, stride;
     if (B.chunked) {
@@ -886,6 +905,7 @@ __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydr
         P.U_new = STAGE == ST_VL_PRED ? d.ustar : d.U[1 - cur];
         P.U_base = d.U[cur];
         P.stage = STAGE;
+        P.fallback = B.fallback;
         P.nbr = d.nbr;
         P.ghost = nullptr;
         P.work = nullptr;
@@ -899,6 +919,9 @@ __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydr
         P.n_bad = d.scal + 3 + r_out;
         P.clear2 = nullptr;
         P.time_rec = nullptr;
+        P.fb_count = nullptr;  // the box batch counts unphysical cells (no cell remedies)
+        P.fb_list = nullptr;
+        P.fb_cap = 0;
         P.cf.fine_off = nullptr;
         P.cf.fine_buf = nullptr;
         P.cf.coarse_off = nullptr;

@@ -14,7 +14,8 @@ class UniformGrid:
 
     def __init__(self, shape, gamma=5.0 / 3.0, cfl=0.5, prec=A.AMR_FP64, box_x=1.0, stream=None,
                  device="cuda", scheme=None):
-        """scheme: optional dict of make_params' limiter / riemann / minmod_coeff / scheme."""
+        """scheme: optional dict of make_params' scheme options (limiter, riemann, minmod_coeff,
+        scheme, recon, fallback, dt_min)."""
         nx, ny, nz = shape
         self.shape = (nx, ny, nz)
         self.device = torch.device(device)
