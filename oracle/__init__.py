@@ -43,6 +43,9 @@ def lib():
         L.or_set_ppm.argtypes = [ctypes.c_int]
         L.or_set_fallback.argtypes = [ctypes.c_int]
         L.or_fallback_counts.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
+        L.or_step_dual.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.or_step_dual.restype = ctypes.c_int64
         L.or_ppm_faces.argtypes = [_dp, _dp, _dp]
         L.or_max_speed1.argtypes = [_dp, ctypes.c_int64, ctypes.c_double]
         L.or_max_speed1.restype = ctypes.c_double
@@ -274,6 +277,27 @@ def run_periodic(U, dh, gamma, cfl, n_steps):
             raise FloatingPointError(f"{nbad} unphysical cells")
         dts.append(dt)
     return U, dts
+
+
+def entropy(U, gamma):
+    """The dual-energy variable s = P / rho^(gamma-1) of a state [5][...]."""
+    U = np.asarray(U, dtype=np.float64)
+    P = (gamma - 1.0) * (U[4] - 0.5 * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / U[0])
+    return P / U[0] ** (gamma - 1.0)
+
+
+def step_dual(U, S, dh, dt, gamma, xi=1e-2):
+    """One MUSCL-Hancock step with the dual-energy formalism (entropy S per
+    unit volume carried as a passive scalar; E corrected from S where
+    E_the / E_kin < xi, S reset from E elsewhere).  Returns (U, S, nbad)."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    nz, ny, nx = U.shape[1:]
+    Un, Sn = np.empty_like(U), np.empty_like(S)
+    nbad = lib().or_step_dual(_ptr(U), _ptr(S), _ptr(Un), _ptr(Sn), nx, ny, nz, dh, dt, gamma, xi)
+    if nbad < 0:
+        raise ValueError("dual energy is built for MUSCL-Hancock only")
+    return Un, Sn, nbad
 
 
 def fallback_counts(reset=True):

@@ -89,6 +89,19 @@
  *   the whole step with dt x 0.8 (iv) down to a minimum dt (v).
  * The fluxes returned for the flux registers stay those of the scheme.
  *
+ * Dual energy (section 2.2: the entropy per unit volume s = P / rho^(gamma-1)
+ * carried as a passive scalar; or_step_dual, MUSCL-Hancock only).  Reading:
+ *   - reconstruction of q = s / rho like a primitive component (the selected
+ *     limiter, PLM or PPM), face values s = rho_face q_face, the Hancock
+ *     increment (dt/2dh) sum_d [F_s(U_d,-) - F_s(U_d,+)] with F_s = s v_n;
+ *   - the scalar flux of a face: the mass flux F_rho times q of its upwind
+ *     side (q = s / rho of the left face state if F_rho >= 0, else of the
+ *     right one); conservative update of s;
+ *   - after the update, with E_kin = |m|^2 / (2 rho) and E_the = E - E_kin:
+ *     if E_the < xi E_kin the total energy becomes
+ *     E_kin + s rho^(gamma-1) / (gamma-1); otherwise the entropy is reset
+ *     from the total energy, s = (gamma-1) E_the / rho^(gamma-1).
+ *
  * Every per-cell loop is independent, so the OpenMP static split changes no
  * result: the oracle is bitwise reproducible for any thread count (the
  * paper's section 2.7.1 property).
@@ -163,6 +176,9 @@ double or_vanleer(double a, double b) {
  * 3 hybrid generalized minmod / van Leer-type; riemann: 0 HLLC, 1 HLLE;
  * theta: the generalized minmod coefficient. */
 static int or_limiter_id = 0, or_riemann_id = 0, or_vl = 0, or_ctu = 0, or_ppm = 0, or_fallback = 0;
+/* dual energy: the entropy fields of the step in progress (or_step_dual) */
+static const double *or_de_S = NULL;
+static double *or_de_Snew = NULL, or_de_xi = 0.0;
 static double or_theta = 1.5;
 
 void or_set_vl(int on) { or_vl = on; }
@@ -673,6 +689,15 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
         or_prim(u, w, gamma);
         for (int v = 0; v < NV; v++) W[v * n + i] = w[v];
     }
+    /* dual energy: q = s / rho, the scalar's face values after the Hancock
+     * step and its face fluxes */
+    double *Q = NULL, *FSs = NULL, *FXs = NULL;
+    if (or_de_S) {
+        Q = (double *)malloc(sizeof(double) * n);
+        FSs = (double *)malloc(sizeof(double) * 6 * n);
+        FXs = (double *)malloc(sizeof(double) * 3 * n);
+        for (int64_t i = 0; i < n; i++) Q[i] = or_de_S[i] / W[i];
+    }
 
     /* 2.-3. limited slopes, face states, Hancock half step */
 #pragma omp parallel for schedule(static)
@@ -730,11 +755,54 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
                 for (int f = 0; f < 6; f++)
                     for (int v = 0; v < NV; v++)
                         FS[((int64_t)f * NV + v) * n + i] = Uf[f][v] + 0.5 * dt / dh * inc[v];
+                if (or_de_S) { /* the entropy scalar: face values s = rho_f q_f, Hancock step */
+                    double sf[6], incs = 0.0;
+                    for (int d = 0; d < 3; d++) {
+                        double qm, qp;
+                        int64_t is[5];
+                        for (int k = 0; k < 5; k++) {
+                            int ck[3] = {c[0], c[1], c[2]};
+                            ck[d] = wrap(c[d] + k - 2, dims[d]);
+                            is[k] = cell_index(ck[0], ck[1], ck[2], nx, ny);
+                        }
+                        if (or_ppm) {
+                            double q5[5];
+                            for (int k = 0; k < 5; k++) q5[k] = Q[is[k]];
+                            or_ppm_faces(q5, &qm, &qp);
+                        } else {
+                            double slope = or_slope(Q[i] - Q[is[1]], Q[is[3]] - Q[i]);
+                            qm = Q[i] - 0.5 * slope;
+                            qp = Q[i] + 0.5 * slope;
+                        }
+                        sf[2 * d] = Wf[2 * d][0] * qm;
+                        sf[2 * d + 1] = Wf[2 * d + 1][0] * qp;
+                        incs += sf[2 * d] * Wf[2 * d][1 + d] - sf[2 * d + 1] * Wf[2 * d + 1][1 + d];
+                    }
+                    for (int f = 0; f < 6; f++) FSs[(int64_t)f * n + i] = sf[f] + 0.5 * dt / dh * incs;
+                }
             }
 
     /* 4. Riemann solver at every face i+1/2: left = high face state of cell i,
      *    right = low face state of cell i+1 */
     or_face_fluxes(FS, FX, nx, ny, nz, gamma);
+    if (or_de_S) { /* scalar flux: mass flux times q of the upwind face state */
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < nz; z++)
+            for (int y = 0; y < ny; y++)
+                for (int x = 0; x < nx; x++) {
+                    int c[3] = {x, y, z};
+                    int64_t i = cell_index(x, y, z, nx, ny);
+                    for (int d = 0; d < 3; d++) {
+                        int cp[3] = {c[0], c[1], c[2]};
+                        cp[d] = wrap(c[d] + 1, dims[d]);
+                        int64_t ip = cell_index(cp[0], cp[1], cp[2], nx, ny);
+                        double fr = FX[((int64_t)d * NV + 0) * n + i];
+                        double q = fr >= 0.0 ? FSs[(int64_t)(2 * d + 1) * n + i] / FS[((int64_t)(2 * d + 1) * NV) * n + i]
+                                             : FSs[(int64_t)(2 * d) * n + ip] / FS[((int64_t)(2 * d) * NV) * n + ip];
+                        FXs[(int64_t)d * n + i] = fr * q;
+                    }
+                }
+    }
     if (or_ctu) {
         /* CTU: transverse correction of the face states by the first fluxes,
          * then the final fluxes */
@@ -783,6 +851,26 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
                     un[v] = U[v * n + i] - dt / dh * div;
                     Unew[v * n + i] = un[v];
                 }
+                if (or_de_S) { /* entropy update and the dual-energy choice */
+                    double div = 0.0;
+                    for (int d = 0; d < 3; d++) {
+                        int cm[3] = {c[0], c[1], c[2]};
+                        cm[d] = wrap(c[d] - 1, dims[d]);
+                        int64_t im = cell_index(cm[0], cm[1], cm[2], nx, ny);
+                        div += FXs[(int64_t)d * n + i] - FXs[(int64_t)d * n + im];
+                    }
+                    double sn = or_de_S[i] - dt / dh * div;
+                    double ekin = 0.5 * (un[1] * un[1] + un[2] * un[2] + un[3] * un[3]) / un[0];
+                    double eth = un[4] - ekin;
+                    double rg = pow(un[0], gamma - 1.0);
+                    if (eth < or_de_xi * ekin) {
+                        un[4] = ekin + sn * rg / (gamma - 1.0);
+                        Unew[4 * n + i] = un[4];
+                    } else {
+                        sn = (gamma - 1.0) * eth / rg;
+                    }
+                    or_de_Snew[i] = sn;
+                }
                 if (!or_physical(un, gamma)) {
                     int ok = 0;
                     if (or_fallback) { /* (ii), (iii) */
@@ -794,10 +882,29 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
             }
 
     if (FX_out) memcpy(FX_out, FX, sizeof(double) * 3 * NV * n);
+    free(Q);
+    free(FSs);
+    free(FXs);
     free(Uh);
     free(W);
     free(FS);
     free(FX);
+    return nbad;
+}
+
+/* One MUSCL-Hancock step with the dual-energy formalism: S, Snew the entropy
+ * per unit volume [nz][ny][nx] before and after, xi the threshold on
+ * E_the / E_kin.  Returns the unphysical count, or -1 for a scheme other
+ * than MUSCL-Hancock. */
+int64_t or_step_dual(const double *U, const double *S, double *Unew, double *Snew, int nx, int ny, int nz,
+                     double dh, double dt, double gamma, double xi) {
+    if (or_vl || or_ctu) return -1;
+    or_de_S = S;
+    or_de_Snew = Snew;
+    or_de_xi = xi;
+    int64_t nbad = or_step_periodic_fx(U, Unew, nx, ny, nz, dh, dt, gamma, NULL);
+    or_de_S = NULL;
+    or_de_Snew = NULL;
     return nbad;
 }
 
