@@ -123,6 +123,13 @@ typedef struct {
     double dt_min;       /* > 0: a level step that leaves unphysical cells is recomputed with
                             dt x 0.8 until it succeeds or dt < dt_min (AMR_E_UNPHYSICAL);
                             0: no retry */
+    int dual_energy;     /* 1: the dual-energy formalism (section 2.2) on single-level grids
+                            with MUSCL-Hancock + PLM: the entropy per unit volume
+                            s = P / rho^(gamma-1) (arrays of amr_hydro_set_entropy) is carried
+                            as a passive scalar (PLM q = s / rho, F_s = mass flux x upwind q);
+                            after the update E = E_kin + s rho^(gamma-1)/(gamma-1) where
+                            E_the < dual_xi E_kin, else s is reset from E */
+    double dual_xi;      /* the threshold on E_the / E_kin; 0 means 1e-2 */
 } amr_hydro_params;
 
 typedef struct amr_hydro_ctx amr_hydro_ctx; /* opaque, library-owned */
@@ -133,7 +140,9 @@ typedef struct amr_hydro_ctx amr_hydro_ctx; /* opaque, library-owned */
  * max_patches not a positive multiple of 8, non-periodic boundaries, a
  * limiter, riemann or scheme value outside its enum, minmod_coeff neither 0
  * nor in [1, 2], AMR_SCHEME_VL with lmax > 0 or with AMR_RECON_PPM, a
- * recon value outside its enum, fallback not 0 or 1, and dt_min < 0. */
+ * recon value outside its enum, fallback not 0 or 1, dt_min < 0, and
+ * dual_energy not 0 or 1, dual_xi < 0, or dual_energy with another scheme,
+ * PPM, lmax > 0 or the cell remedies. */
 amr_status amr_hydro_init(const amr_hydro_params *params, void *cuda_stream,
                           amr_hydro_ctx **out);
 
@@ -216,6 +225,14 @@ amr_status amr_hydro_get_state(amr_hydro_ctx *ctx, int level, int *cur_buffer,
  * initial condition, a restart, an in-place edit): reductions cached from the
  * last step are dropped.  Asynchronous; no device work. */
 amr_status amr_hydro_touch_level(amr_hydro_ctx *ctx, int level);
+
+/* Register the dual-energy entropy fields of `level` (params.dual_energy):
+ * two FP64 buffers [n_patches][8][8][8] in the slot order of the level's
+ * state, S_a holding s = P / rho^(gamma-1) of the current state, S_b
+ * receiving the next; they swap with U_a / U_b at every step (the newest
+ * is S_a after an even number of steps).  Caller-owned.  AMR_E_INVAL for a
+ * context without dual energy, a level without patches, or equal buffers. */
+amr_status amr_hydro_set_entropy(amr_hydro_ctx *ctx, int level, double *S_a, double *S_b);
 
 /*
  * Fill the coarse-fine ghost patches of `level` (>0) at time t by linear

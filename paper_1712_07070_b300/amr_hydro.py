@@ -30,7 +30,7 @@ SYMBOLS = (
     "amr_hydro_strerror", "amr_hydro_uniform_tables", "amr_hydro_pack_uniform",
     "amr_hydro_unpack_uniform", "amr_hydro_step_uniform_noalloc", "amr_hydro_bind_level",
     "amr_hydro_regrid", "amr_hydro_advance_root", "amr_hydro_level_info", "amr_hydro_box_tuning",
-    "amr_hydro_advance_host",
+    "amr_hydro_advance_host", "amr_hydro_set_entropy",
 )
 
 
@@ -42,6 +42,7 @@ class amr_hydro_params(ctypes.Structure):
         ("box", ctypes.c_double * 3), ("root_n", ctypes.c_int * 3), ("max_patches", ctypes.c_int),
         ("limiter", ctypes.c_int), ("riemann", ctypes.c_int), ("minmod_coeff", ctypes.c_double),
         ("scheme", ctypes.c_int), ("recon", ctypes.c_int), ("fallback", ctypes.c_int), ("dt_min", ctypes.c_double),
+        ("dual_energy", ctypes.c_int), ("dual_xi", ctypes.c_double),
     ]
 
 
@@ -70,6 +71,7 @@ def lib():
         "amr_hydro_set_level": [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_double],
         "amr_hydro_get_state": [_vp, ctypes.c_int, _ip, _dp, _dp],
         "amr_hydro_touch_level": [_vp, ctypes.c_int],
+        "amr_hydro_set_entropy": [_vp, ctypes.c_int, _vp, _vp],
         "amr_hydro_fill_ghost": [_vp, ctypes.c_int, ctypes.c_double],
         "amr_hydro_advance_level": [_vp, ctypes.c_int, ctypes.c_double, _i64p],
         "amr_hydro_advance_host": [_vp, _vp, _vp, ctypes.c_double, _dp],
@@ -166,6 +168,10 @@ def amr_hydro_advance_level(ctx, level, dt, count_unphysical=False):
         return n.value
     check(lib().amr_hydro_advance_level(ctx, level, dt, None), "amr_hydro_advance_level")
     return None
+
+
+def amr_hydro_set_entropy(ctx, level, S_a, S_b):
+    check(lib().amr_hydro_set_entropy(ctx, level, _p(S_a), _p(S_b)), "amr_hydro_set_entropy")
 
 
 def amr_hydro_flux_fixup(ctx, coarse_level):
@@ -287,10 +293,10 @@ def amr_hydro_level_info(ctx, level):
 def make_params(gamma=5.0 / 3.0, cfl=0.5, root_n=(64, 64, 64), box=None, lmax=0,
                 prec=AMR_FP64, max_patches=None, theta=0.05, c_inc=0.1, c_dec=0.1, nbuf=None,
                 limiter=AMR_LIM_VANLEER, riemann=AMR_RS_HLLC, minmod_coeff=1.5, scheme=AMR_SCHEME_MH,
-                recon=AMR_RECON_PLM, fallback=0, dt_min=0.0):
+                recon=AMR_RECON_PLM, fallback=0, dt_min=0.0, dual_energy=0, dual_xi=0.0):
     p = amr_hydro_params()
     p.limiter, p.riemann, p.minmod_coeff, p.scheme, p.recon = limiter, riemann, minmod_coeff, scheme, recon
-    p.fallback, p.dt_min = fallback, dt_min
+    p.fallback, p.dt_min, p.dual_energy, p.dual_xi = fallback, dt_min, dual_energy, dual_xi
     p.gamma, p.cfl, p.c_inc, p.c_dec, p.theta = gamma, cfl, c_inc, c_dec, theta
     p.lmax = lmax
     nb = nbuf if nbuf is not None else [8] * 8

@@ -109,9 +109,11 @@ static int step_occupancy(int stage_lo, int stage_hi, std::integer_sequence<int,
 
 // The march stages a scheme launches, lo .. hi: MUSCL-Hancock or CTU (PLM or
 // PPM), or the two VL launches.
-void scheme_stages(int scheme, int recon, int &lo, int &hi) {
+void scheme_stages(int scheme, int recon, int dual_energy, int &lo, int &hi) {
     const bool ppm = recon == AMR_RECON_PPM;
-    if (scheme == AMR_SCHEME_VL) {
+    if (dual_energy) {
+        lo = hi = ST_MH_DE;
+    } else if (scheme == AMR_SCHEME_VL) {
         lo = ST_VL_PRED;
         hi = ST_VL_CORR;
     } else if (scheme == AMR_SCHEME_CTU) {
@@ -123,9 +125,9 @@ void scheme_stages(int scheme, int recon, int &lo, int &hi) {
 
 // Number of resident step CTAs per SM of a scheme's instances, for sizing a
 // persistent grid.
-int step_blocks_per_sm(int prec, int scheme, int recon) {
+int step_blocks_per_sm(int prec, int scheme, int recon, int dual_energy) {
     int lo, hi;
-    scheme_stages(scheme, recon, lo, hi);
+    scheme_stages(scheme, recon, dual_energy, lo, hi);
     return prec == AMR_FP64 ? step_occupancy<double>(lo, hi, StepKeys{}) : step_occupancy<float>(lo, hi, StepKeys{});
 }
 
@@ -161,7 +163,7 @@ amr_status launch_step_raw(int prec, const StepParams &P, cudaStream_t stream) {
     if ((st = cuda_fail(cudaGetDevice(&dev), "cudaGetDevice"))) return st;
     if ((st = cuda_fail(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev), "sm count")))
         return st;
-    const int cap = n_sm * step_blocks_per_sm(prec, AMR_SCHEME_MH, AMR_RECON_PLM);
+    const int cap = n_sm * step_blocks_per_sm(prec, AMR_SCHEME_MH, AMR_RECON_PLM, 0);
     const int grid = P.n_work < cap ? P.n_work : cap;
     if (prec == AMR_FP64)
         launch_step_k<double>(P, grid, stream);
@@ -256,6 +258,10 @@ amr_status amr_hydro_init(const amr_hydro_params *p, void *stream, amr_hydro_ctx
     if (p->scheme == AMR_SCHEME_VL && p->recon != AMR_RECON_PLM) return AMR_E_INVAL;
     if (p->fallback != 0 && p->fallback != 1) return AMR_E_INVAL;
     if (!(p->dt_min >= 0.0)) return AMR_E_INVAL;
+    if (p->dual_energy != 0 && p->dual_energy != 1) return AMR_E_INVAL;
+    if (!(p->dual_xi >= 0.0)) return AMR_E_INVAL;
+    if (p->dual_energy && (p->scheme != AMR_SCHEME_MH || p->recon != AMR_RECON_PLM || p->lmax > 0 || p->fallback))
+        return AMR_E_INVAL;
     // VL on refined levels would need the half-step state in a 3-cell ring of
     // the coarse-fine ghost patches: single-level grids only
     if (p->scheme == AMR_SCHEME_VL && p->lmax > 0) return AMR_E_INVAL;
@@ -274,10 +280,11 @@ amr_status amr_hydro_init(const amr_hydro_params *p, void *stream, amr_hydro_ctx
     if (!c) return AMR_E_NOMEM;
     c->prm = *p;
     if (c->prm.minmod_coeff == 0.0) c->prm.minmod_coeff = 1.5;
+    if (c->prm.dual_xi == 0.0) c->prm.dual_xi = 1e-2;
     c->stream = (cudaStream_t)stream;
     cudaGetDevice(&c->device);
     cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
-    c->step_bps = step_blocks_per_sm(p->prec, p->scheme, p->recon);
+    c->step_bps = step_blocks_per_sm(p->prec, p->scheme, p->recon, p->dual_energy);
     if ((st = c->scal.reserve(SCAL_N))) { amr_hydro_destroy(c); return st; }
     if ((st = c->dtbuf.reserve(3 * (MAX_LEVELS + MAX_BOXES)))) { amr_hydro_destroy(c); return st; }
     if (p->fallback) {

@@ -68,7 +68,7 @@ int box_occupancy(int lo, int hi, std::integer_sequence<int, K...>) {
 // Resident CTAs per SM of the instances the context's scheme launches.
 int resident_per_sm(int prec, int scheme, int recon) {
     int lo, hi;
-    scheme_stages(scheme, recon, lo, hi);
+    scheme_stages(scheme, recon, 0, lo, hi);
     return prec == AMR_FP64 ? box_occupancy<double>(lo, hi, BoxKeys{}) : box_occupancy<float>(lo, hi, BoxKeys{});
 }
 
@@ -86,7 +86,7 @@ void launch_boxes_key(int key, const BoxLaunch &B, int grid, cudaStream_t s, std
 amr_status launch_boxes(amr_hydro_ctx *c, const BoxLaunch &B, int grid, cudaStream_t s) {
     const int mode = scheme_mode(B.limiter, B.riemann);
     int lo, hi;
-    scheme_stages(c->prm.scheme, c->prm.recon, lo, hi);
+    scheme_stages(c->prm.scheme, c->prm.recon, 0, lo, hi);
     for (int stage = lo; stage <= hi; stage++) {
         if (c->prm.prec == AMR_FP64)
             launch_boxes_key<double>(mode + 3 * stage, B, grid, s, BoxKeys{});
@@ -143,6 +143,7 @@ extern "C" {
 amr_status amr_hydro_set_box(amr_hydro_ctx *c, int box_id, int n, double *U_a, double *U_b) {
     if (!c || box_id < 0 || box_id >= MAX_BOXES || n <= 0 || n % 16 || !U_a || !U_b || U_a == U_b)
         return AMR_E_INVAL;
+    if (c->prm.dual_energy) return AMR_E_INVAL;  // the box batch carries no entropy fields
     Box &B = c->boxes[box_id];
     const int np[3] = {n / 8, n / 8, n / 8};
     const int64_t npatch = (int64_t)np[0] * np[1] * np[2];

@@ -36,6 +36,7 @@ constexpr int CE = GE + 2;  // predicted-state region: cells -1..16 along x and 
 template <typename real, int NG = 2>
 struct CtuSmem {
     using Geo = Tile<NG>;
+    static constexpr bool DE = false;
     real W[Geo::NR][NV][Geo::TY][Geo::TX];  // primitive ring, planes z+1-S .. z+1+S (and z)
     real XS[2][NV][CE][CE];     // x face states (low, high) of cells x, y = -1..16: [.][v][y+1][x+1]
     real YS[2][NV][CE][CE];     // y face states, same layout

@@ -42,6 +42,7 @@ constexpr int GHOST_INFO = 8;  // int32 per ghost-patch job on the device
 struct Level {
     int n_patches = 0, n_groups = 0;
     double *U[2] = {nullptr, nullptr};
+    double *S[2] = {nullptr, nullptr};  // dual-energy entropy fields (amr_hydro_set_entropy)
     int cur = 0;
     double t = 0.0, t_prev = 0.0;
     bool t_pending = false;  // t awaits a device-side dt
@@ -154,7 +155,7 @@ amr_status cuda_fail(cudaError_t e, const char *where);
 double level_dh(const amr_hydro_ctx *c, int level);
 amr_status level_speed(amr_hydro_ctx *c, int level);
 size_t step_smem_bytes(int prec);
-void scheme_stages(int scheme, int recon, int &lo, int &hi);
+void scheme_stages(int scheme, int recon, int dual_energy, int &lo, int &hi);
 struct StepParams;
 amr_status launch_step(amr_hydro_ctx *c, const StepParams &P, int grid);
 amr_status launch_step_raw(int prec, const StepParams &P, cudaStream_t stream);

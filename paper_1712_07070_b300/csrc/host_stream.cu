@@ -64,6 +64,7 @@ extern "C" amr_status amr_hydro_advance_host(amr_hydro_ctx *c, const double *U_i
     Level &L = c->lv[0];
     if (!L.n_patches || !L.uniform || L.n_ghost) return AMR_E_INVAL;
     if (c->prm.lmax > 0 && c->lv[1].n_patches) return AMR_E_INVAL;  // refined levels: use the W-cycle
+    if (c->prm.dual_energy) return AMR_E_INVAL;  // no host copies of the entropy fields
     const int nx = c->prm.root_n[0], ny = c->prm.root_n[1], nz = c->prm.root_n[2];
     if ((int64_t)nx * ny * GE >= (1LL << 31)) return AMR_E_INVAL;
     const int ns = nz / GE, G = (nx / 16) * (ny / 16);  // slabs, groups per slab
@@ -156,7 +157,7 @@ extern "C" amr_status amr_hydro_advance_host(amr_hydro_ctx *c, const double *U_i
     };
     {
         int lo, hi;
-        scheme_stages(c->prm.scheme, c->prm.recon, lo, hi);
+        scheme_stages(c->prm.scheme, c->prm.recon, 0, lo, hi);
         P.stage = lo;
     }
     if (vl) {

@@ -46,6 +46,7 @@ amr_status amr_hydro_set_level(amr_hydro_ctx *c, int level, int n_patches, doubl
     L.n_groups = n_patches / 8;
     L.U[0] = U_a;
     L.U[1] = U_b;
+    L.S[0] = L.S[1] = nullptr;  // entropy fields: registered again after set_level
     L.cur = 0;
     L.t = L.t_prev = t;
     L.t_pending = false;
@@ -104,6 +105,15 @@ amr_status amr_hydro_set_level(amr_hydro_ctx *c, int level, int n_patches, doubl
     return AMR_OK;
 }
 
+amr_status amr_hydro_set_entropy(amr_hydro_ctx *c, int level, double *S_a, double *S_b) {
+    if (!c || level < 0 || level > c->prm.lmax || !c->prm.dual_energy) return AMR_E_INVAL;
+    Level &L = c->lv[level];
+    if (!L.n_patches || !S_a || !S_b || S_a == S_b) return AMR_E_INVAL;
+    L.S[L.cur] = S_a;
+    L.S[1 - L.cur] = S_b;
+    return AMR_OK;
+}
+
 amr_status amr_hydro_touch_level(amr_hydro_ctx *c, int level) {
     if (!c || level < 0 || level > c->prm.lmax) return AMR_E_INVAL;
     Level &L = c->lv[level];
@@ -146,6 +156,12 @@ amr_status advance_once(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphy
     P.riemann = c->prm.riemann;
     P.theta = c->prm.minmod_coeff;
     P.fallback = c->prm.fallback;
+    if (c->prm.dual_energy) {
+        if (!L.S[0] || !L.S[1]) return AMR_E_INVAL;  // amr_hydro_set_entropy first
+        P.S_old = L.S[L.cur];
+        P.S_new = L.S[1 - L.cur];
+        P.de_xi = c->prm.dual_xi;
+    }
     if (c->prm.fallback) {
         P.fb_count = c->fb_count.p;
         P.fb_list = c->fb_list.p;
@@ -175,8 +191,8 @@ amr_status advance_once(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphy
     const int grid = P.n_work < cap ? P.n_work : cap;
     {
         int lo, hi;
-        scheme_stages(c->prm.scheme, c->prm.recon, lo, hi);
-        P.stage = lo;  // MUSCL-Hancock or CTU (PLM or PPM): the one launch
+        scheme_stages(c->prm.scheme, c->prm.recon, c->prm.dual_energy, lo, hi);
+        P.stage = lo;  // MUSCL-Hancock (PLM, PPM, dual energy) or CTU: the one launch
     }
     if (c->prm.scheme == AMR_SCHEME_VL) {  // predictor into U*, then the corrector
         StepParams H = P;

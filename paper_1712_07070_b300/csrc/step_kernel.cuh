@@ -46,7 +46,8 @@ constexpr int ST_VL_CORR = 2;  // VL update of U^n with the fluxes of the PLM st
 constexpr int ST_CTU = 3;      // CTU step (ctu_kernel.cuh)
 constexpr int ST_MH_PPM = 4;   // MUSCL-Hancock step with PPM reconstruction
 constexpr int ST_CTU_PPM = 5;  // CTU step with PPM reconstruction
-constexpr int N_STAGES = 6;
+constexpr int ST_MH_DE = 6;    // MUSCL-Hancock step with the dual-energy formalism
+constexpr int N_STAGES = 7;
 __host__ __device__ constexpr bool stage_ppm(int st) { return st == ST_MH_PPM || st == ST_CTU_PPM; }
 __host__ __device__ constexpr bool stage_ctu(int st) { return st == ST_CTU || st == ST_CTU_PPM; }
 
@@ -114,6 +115,11 @@ struct StepParams {
     unsigned long long *fb_count;
     int64_t *fb_list;
     int64_t fb_cap;
+    // dual energy (ST_MH_DE): the entropy per unit volume [slot][8^3] before
+    // and after the step, and the threshold on E_the / E_kin
+    const double *__restrict__ S_old;
+    double *__restrict__ S_new;
+    double de_xi;
     unsigned long long *smax_out;            // max signal speed of the new state (bits)
     unsigned long long *n_bad;               // count of unphysical new cells
     unsigned long long *clear2;              // two scalars the kernel zeroes for the next step
@@ -124,6 +130,7 @@ struct StepParams {
 template <typename real, int NG = 2>
 struct StepSmem {
     using Geo = Tile<NG>;
+    static constexpr bool DE = false;
     real W[Geo::NR][NV][Geo::TY][Geo::TX];  // primitive ring, planes z-S .. z+S
     real XS[2][NV][GE][GE + 2];  // x-/x+ face states, cells x=-1..16, rows y=0..15
     real YS[2][NV][GE + 2][GE];  // y-/y+ face states, cells y=-1..16, columns x=0..15
@@ -137,6 +144,22 @@ struct StepSmem {
     long long cco[2][48];  // coarse register blocks of its 8 patches' faces (-1: none)
     double red[MAX_WARPS];
     double dt;
+};
+
+// The MUSCL-Hancock march with the entropy scalar s = P / rho^(gamma-1) of the
+// dual-energy formalism: q = s / rho rides along in its own ring, face
+// values, fluxes and staging (the same layouts as the hydro variables'
+// with one component).
+template <typename real>
+struct StepSmemDE : StepSmem<real, 2> {
+    static constexpr bool DE = true;
+    real Q[3][TW][TW];       // q ring
+    real QX[2][GE][GE + 2];  // s on the x-/x+ faces after the Hancock step
+    real QY[2][GE + 2][GE];
+    real FQX[GE][GE + 1];    // scalar x flux at face x-1/2
+    real FQY[GE + 1][GE];
+    alignas(16) double raws[TW * TW];  // next tile plane of s in flight
+    alignas(16) double uos[2][COLS];   // each column's s^n one plane ahead of its update
 };
 
 // dt * F into the registers of the face between cells a (low) and b (high)
@@ -247,6 +270,11 @@ __device__ __forceinline__ void load_plane(SM &S, const StepParams &P, int ts, i
         }
 #pragma unroll
         for (int v = 0; v < NV; v++) S.W[slot][v][ty + G::OY][tx + G::OX] = w[v];
+        if constexpr (SM::DE) {  // q = s / rho
+            const int sl = S.nbr[ts][qx + 4 * qy + 16 * qz];
+            S.Q[slot][ty + G::OY][tx + G::OX] =
+                sl >= 0 ? to_real<real>(__ldg(P.S_old + (int64_t)sl * PV + lz * 64 + ly * 8 + lx)) / w[0] : real(1);
+        }
     }
 }
 
@@ -270,11 +298,13 @@ __device__ __forceinline__ void issue_plane(SM &S, const StepParams &P, int ts, 
         const int ty = j / (G::TX / 2) - G::OY, tx = 2 * (j % (G::TX / 2)) - G::OX;
         const int qy = (ty + PS) >> 3, ly = (ty + PS) & 7;
         const int qx = (tx + PS) >> 3, lx = (tx + PS) & 7;
-        const double *src = patch_src(P, S.nbr[ts][qx + 4 * qy + 16 * qz]);
+        const int sl = S.nbr[ts][qx + 4 * qy + 16 * qz];
+        const double *src = patch_src(P, sl);
         if (src) {
             const int off = lz * 64 + ly * 8 + lx;
 #pragma unroll
             for (int v = 0; v < NV; v++) cp_async16(&S.raw[v][2 * j], src + v * PV + off);
+            if constexpr (SM::DE) cp_async16(&S.raws[2 * j], P.S_old + (int64_t)sl * PV + off);
         }
     }
     cp_async_commit();
@@ -293,7 +323,7 @@ __device__ __forceinline__ void finish_plane(SM &S, int ts, int tl, int tr, cons
     for (int j = threadIdx.x; j < G::PAIRS; j += StepCfg<real>::NT) {
         const int ty = j / (G::TX / 2) - G::OY, tx = 2 * (j % (G::TX / 2)) - G::OX;
         const int qy = (ty + PS) >> 3, qx = (tx + PS) >> 3;
-        real w[2][NV];
+        real w[2][NV], q[2] = {real(1), real(1)};
         if (S.nbr[ts][qx + 4 * qy + 16 * qz] != -1) {
 #pragma unroll
             for (int h = 0; h < 2; h++) {
@@ -304,7 +334,8 @@ __device__ __forceinline__ void finish_plane(SM &S, int ts, int tl, int tr, cons
 #pragma unroll
                     for (int v = 0; v < NV; v++) w[h][v] = u[v];
                 } else {
-                    u2w(u, w[h], g);
+                    const real ri = u2w(u, w[h], g);
+                    if constexpr (SM::DE) q[h] = to_real<real>(S.raws[2 * j + h]) * ri;  // q = s / rho
                 }
             }
         } else {  // a position no stencil reads (a tile corner): benign state
@@ -317,6 +348,10 @@ __device__ __forceinline__ void finish_plane(SM &S, int ts, int tl, int tr, cons
         for (int v = 0; v < NV; v++) {
             S.W[slot][v][ty + G::OY][tx + G::OX] = w[0][v];
             S.W[slot][v][ty + G::OY][tx + G::OX + 1] = w[1][v];
+        }
+        if constexpr (SM::DE) {
+            S.Q[slot][ty + G::OY][tx + G::OX] = q[0];
+            S.Q[slot][ty + G::OY][tx + G::OX + 1] = q[1];
         }
     }
 }
@@ -379,9 +414,11 @@ __device__ __forceinline__ void face_values(const SM &S, int X, int Y, int z, co
 // states and the Hancock half step (ST_MH, ST_MH_PPM), the reconstructed
 // states alone (ST_VL_CORR), or the cell's conserved average on every face
 // (ST_VL_PRED).  uf[2d] / uf[2d+1]: conserved state on the low / high face along d.
+// With the dual-energy scalar (SM::DE), us[f]: s on face f, rho_f q_f with
+// PLM q, after the Hancock step with F_s = s v_n.
 template <typename real, int STAGE, typename SM>
 __device__ __forceinline__ void hancock_cell(const SM &S, int x, int y, int z, real dtdh_half, const Gas<real> &g,
-                                             real uf[6][NV]) {
+                                             real uf[6][NV], real us[6]) {
     using G = typename SM::Geo;
     const int X = x + G::OX, Y = y + G::OY;
     if constexpr (STAGE == ST_VL_PRED) {
@@ -393,12 +430,23 @@ __device__ __forceinline__ void hancock_cell(const SM &S, int x, int y, int z, r
     } else {
         constexpr bool ppm = stage_ppm(STAGE), hancock = STAGE != ST_VL_CORR;
         real inc[NV] = {real(0), real(0), real(0), real(0), real(0)};
+        real incs = real(0);
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             real wm[NV], wp[NV], fm[NV], fp[NV];
             if (d == 0) face_values<real, 0, ppm>(S, X, Y, z, g, wm, wp);
             if (d == 1) face_values<real, 1, ppm>(S, X, Y, z, g, wm, wp);
             if (d == 2) face_values<real, 2, ppm>(S, X, Y, z, g, wm, wp);
+            if constexpr (SM::DE) {  // the entropy scalar: PLM q, s = rho_f q_f, F_s = s v_n
+                const int s0 = G::slot(z);
+                const real qc = S.Q[s0][Y][X];
+                const real ql = d == 0 ? S.Q[s0][Y][X - 1] : (d == 1 ? S.Q[s0][Y - 1][X] : S.Q[G::slot(z - 1)][Y][X]);
+                const real qh = d == 0 ? S.Q[s0][Y][X + 1] : (d == 1 ? S.Q[s0][Y + 1][X] : S.Q[G::slot(z + 1)][Y][X]);
+                const real hq = half_slope(qc - ql, qh - qc, g);
+                us[2 * d] = wm[0] * (qc - hq);
+                us[2 * d + 1] = wp[0] * (qc + hq);
+                incs += us[2 * d] * wm[1 + d] - us[2 * d + 1] * wp[1 + d];
+            }
             w2u(wm, uf[2 * d], g);
             w2u(wp, uf[2 * d + 1], g);
             if constexpr (hancock) {
@@ -415,7 +463,18 @@ __device__ __forceinline__ void hancock_cell(const SM &S, int x, int y, int z, r
 #pragma unroll
                 for (int v = 0; v < NV; v++) uf[f][v] += dtdh_half * inc[v];
         }
+        if constexpr (SM::DE) {
+#pragma unroll
+            for (int f = 0; f < 6; f++) us[f] += dtdh_half * incs;
+        }
     }
+}
+
+// Flux of the dual-energy scalar through a face: the mass flux F_rho times
+// q = s / rho of the upwind face state.
+template <typename real>
+__device__ __forceinline__ real scalar_flux(real frho, real sL, real rL, real sR, real rR) {
+    return frho * (ge0(frho) ? sL * rcp_(rL) : sR * rcp_(rR));
 }
 
 // Stage C face evaluations of plane z (local plane zl of the group in table
@@ -435,6 +494,7 @@ __device__ __forceinline__ void x_face(SM &S, const StepParams &P, double dt, in
     face_flux<0>(uL, uR, F, g);
 #pragma unroll
     for (int v = 0; v < NV; v++) S.FX[v][row][col] = F[v];
+    if constexpr (SM::DE) S.FQX[row][col] = scalar_flux(F[0], S.QX[1][row][col], uL[0], S.QX[0][row][col + 1], uR[0]);
     if (cf && (col & 7) == 0) {  // a patch face: x = 0 (group boundary) or x = 8
         const int pr = (row >> 3) * 2 + (zl >> 3) * 4;
         cf_register(S, P, dt, F, 0, row, zl, ts, col == 0 ? -1 : pr, ts, pr + (col >> 3),
@@ -451,6 +511,7 @@ __device__ __forceinline__ void y_face(SM &S, const StepParams &P, double dt, in
     face_flux<1>(uL, uR, F, g);
 #pragma unroll
     for (int v = 0; v < NV; v++) S.FY[v][r][col] = F[v];
+    if constexpr (SM::DE) S.FQY[r][col] = scalar_flux(F[0], S.QY[1][r][col], uL[0], S.QY[0][r + 1][col], uR[0]);
     if (cf && (r & 7) == 0) {  // a patch face: y = 0 (group boundary) or y = 8
         const int pr = (col >> 3) + (zl >> 3) * 4;
         cf_register(S, P, dt, F, 1, col, zl, ts, r == 0 ? -1 : pr, ts, pr + 2 * (r >> 3), r == 0 ? S.cfo[ts][2] : -1LL);
@@ -472,6 +533,10 @@ __device__ __forceinline__ void high_faces(SM &S, const StepParams &P, double dt
     for (int v = 0; v < NV; v++) {
         if (D == 0) S.FX[v][k][GE] = F[v];
         else S.FY[v][GE][k] = F[v];
+    }
+    if constexpr (SM::DE) {
+        if (D == 0) S.FQX[k][GE] = scalar_flux(F[0], S.QX[1][k][GE], uL[0], S.QX[0][k][GE + 1], uR[0]);
+        else S.FQY[GE][k] = scalar_flux(F[0], S.QY[1][GE][k], uL[0], S.QY[0][GE + 1][k], uR[0]);
     }
     if (cf) {
         const int pa = D == 0 ? 1 + (k >> 3) * 2 + (zl >> 3) * 4 : (k >> 3) + 2 + (zl >> 3) * 4;
@@ -578,6 +643,8 @@ __device__ __forceinline__ void step_run(SM &S, const StepParams &P, const int32
     real acc[NV];       // flux divergence of this column's cell at z-1 (minus its top z flux)
 #pragma unroll
     for (int v = 0; v < NV; v++) { zp_prev[v] = real(0); acc[v] = real(0); }
+    // the dual-energy scalar's counterparts (SM::DE)
+    real zps_prev = real(0), accs = real(0), fzs = real(0);
 
     for (int z = -1; z <= Z; z++) {
         {  // plane z+S is ready to convert, plane z+S+1 to stage
@@ -606,6 +673,9 @@ __device__ __forceinline__ void step_run(SM &S, const StepParams &P, const int32
                                 (zl & 7) * 64 + (py & 7) * 8 + (px & 7);
 #pragma unroll
             for (int v = 0; v < NV; v++) cp_async16(&S.uo[z & 1][v][2 * tid], src + v * PV);
+            if constexpr (SM::DE)
+                cp_async16(&S.uos[z & 1][2 * tid], P.S_old + (own + (px >> 3) + 2 * (py >> 3) + 4 * (zl >> 3)) * PV +
+                                                       (zl & 7) * 64 + (py & 7) * 8 + (px & 7));
             cp_async_commit();
         }
         // the next run group's tables, into the slot group kz - 1 used last
@@ -620,14 +690,22 @@ __device__ __forceinline__ void step_run(SM &S, const StepParams &P, const int32
 
         // ---- B: Hancock states of plane z
         real zm[NV], zp[NV], fz[NV];
+        real zms = real(0), zps = real(0);  // the scalar on the column cell's z faces
         {
-            real uf[6][NV];
-            hancock_cell<real, STAGE>(S, cx, cy, z, dtdh_half, g, uf);
+            real uf[6][NV], us[6];
+            hancock_cell<real, STAGE>(S, cx, cy, z, dtdh_half, g, uf, us);
 #pragma unroll
             for (int v = 0; v < NV; v++) { zm[v] = uf[4][v]; zp[v] = uf[5][v]; }
+            if constexpr (SM::DE) {
+                zms = us[4];
+                zps = us[5];
+            }
             // Sub-partitions 2 and 3 (warp & 2) have no ghost-ring cells in this
             // stage: they take their z face here rather than in stage C.
-            if ((warp & 2) && z >= 0) z_face(S, P, dt, zp_prev, zm, cx, cy, z, len, cfm, fz, g);
+            if ((warp & 2) && z >= 0) {
+                z_face(S, P, dt, zp_prev, zm, cx, cy, z, len, cfm, fz, g);
+                if constexpr (SM::DE) fzs = scalar_flux(fz[0], zps_prev, zp_prev[0], zms, zm[0]);
+            }
             if (z >= 0 && z < Z) {
 #pragma unroll
                 for (int v = 0; v < NV; v++) {
@@ -635,6 +713,12 @@ __device__ __forceinline__ void step_run(SM &S, const StepParams &P, const int32
                     S.XS[1][v][cy][cx + 1] = uf[1][v];
                     S.YS[0][v][cy + 1][cx] = uf[2][v];
                     S.YS[1][v][cy + 1][cx] = uf[3][v];
+                }
+                if constexpr (SM::DE) {
+                    S.QX[0][cy][cx + 1] = us[0];
+                    S.QX[1][cy][cx + 1] = us[1];
+                    S.QY[0][cy + 1][cx] = us[2];
+                    S.QY[1][cy + 1][cx] = us[3];
                 }
             }
         }
@@ -645,19 +729,27 @@ __device__ __forceinline__ void step_run(SM &S, const StepParams &P, const int32
             const int side = (tid >> 4) & 1;
             const int x = xring ? (side ? GE : -1) : r;
             const int y = xring ? r : (side ? GE : -1);
-            real uf[6][NV];
-            hancock_cell<real, STAGE>(S, x, y, z, dtdh_half, g, uf);
+            real uf[6][NV], us[6];
+            hancock_cell<real, STAGE>(S, x, y, z, dtdh_half, g, uf, us);
             if (xring) {
 #pragma unroll
                 for (int v = 0; v < NV; v++) {
                     S.XS[0][v][y][x + 1] = uf[0][v];
                     S.XS[1][v][y][x + 1] = uf[1][v];
                 }
+                if constexpr (SM::DE) {
+                    S.QX[0][y][x + 1] = us[0];
+                    S.QX[1][y][x + 1] = us[1];
+                }
             } else {
 #pragma unroll
                 for (int v = 0; v < NV; v++) {
                     S.YS[0][v][y + 1][x] = uf[2][v];
                     S.YS[1][v][y + 1][x] = uf[3][v];
+                }
+                if constexpr (SM::DE) {
+                    S.QY[0][y + 1][x] = us[2];
+                    S.QY[1][y + 1][x] = us[3];
                 }
             }
         }
@@ -672,7 +764,10 @@ __device__ __forceinline__ void step_run(SM &S, const StepParams &P, const int32
         // y faces, and the group's high faces on warp 2 (sub-partition 2), so
         // every sub-partition's FP64 share carries 5 or 6 face evaluations
         // here after 3 or 2 Hancock cells (+2 z faces) in stage B
-        if (!(warp & 2) && z >= 0) z_face(S, P, dt, zp_prev, zm, cx, cy, z, len, cfm, fz, g);
+        if (!(warp & 2) && z >= 0) {
+            z_face(S, P, dt, zp_prev, zm, cx, cy, z, len, cfm, fz, g);
+            if constexpr (SM::DE) fzs = scalar_flux(fz[0], zps_prev, zp_prev[0], zms, zm[0]);
+        }
         if (z >= 0 && z < Z) {
             const int ts = kz & 1;
             const bool cf = (cfm >> ts) & 1u;
@@ -689,6 +784,7 @@ __device__ __forceinline__ void step_run(SM &S, const StepParams &P, const int32
                                   4 * (zcl >> 3)) * PSLOT +
                                  (zcl & 7) * 64 + (cy & 7) * 8 + (cx & 7);
             real ur[NV];  // the new state in the compute type, for its signal speed
+            double una[NV];
 #pragma unroll
             for (int v = 0; v < NV; v++) {
                 const real tot = acc[v] + fz[v];
@@ -703,7 +799,28 @@ __device__ __forceinline__ void step_run(SM &S, const StepParams &P, const int32
                     un = uo - f2d_bits(inc);
                     ur[v] = d2f_bits(uo) - inc;
                 }
-                P.U_new[base + v * PV] = un;
+                if constexpr (SM::DE) una[v] = un;
+                else P.U_new[base + v * PV] = un;
+            }
+            if constexpr (SM::DE) {
+                // the scalar's update, then the dual-energy choice (FP64): E from
+                // s where E_the < xi E_kin, else s from E
+                const real tots = accs + fzs;
+                const double so = S.uos[zc & 1][tid];
+                double sn;
+                if constexpr (sizeof(real) == sizeof(double)) sn = so - dtdh * tots;
+                else sn = so - f2d_bits(dtdh_r * tots);
+                const double ekin = 0.5 * (una[1] * una[1] + una[2] * una[2] + una[3] * una[3]) / una[0];
+                const double eth = una[4] - ekin;
+                const double rg = pow(una[0], P.gamma - 1.0);
+                if (eth < P.de_xi * ekin) una[4] = ekin + sn * rg / (P.gamma - 1.0);
+                else sn = (P.gamma - 1.0) * eth / rg;
+                P.S_new[base / PSLOT * PV + base % PSLOT] = sn;
+#pragma unroll
+                for (int v = 0; v < NV; v++) {
+                    P.U_new[base + v * PV] = una[v];
+                    ur[v] = to_real<real>(una[v]);
+                }
             }
             if constexpr (STAGE != ST_VL_PRED) {
                 bool ok;
@@ -719,9 +836,12 @@ __device__ __forceinline__ void step_run(SM &S, const StepParams &P, const int32
                                  (S.FY[v][cy + 1][cx] - S.FY[v][cy][cx]);
                 acc[v] = dxy - fz[v];
             }
+            if constexpr (SM::DE)
+                accs = ((S.FQX[cy][cx + 1] - S.FQX[cy][cx]) + (S.FQY[cy + 1][cx] - S.FQY[cy][cx])) - fzs;
         }
 #pragma unroll
         for (int v = 0; v < NV; v++) zp_prev[v] = zp[v];
+        zps_prev = zps;
     }
     __syncthreads();  // the next run overwrites the tables and the ring
 }
@@ -734,8 +854,10 @@ namespace amrh {
 
 // Shared memory of a kernel instance's march.
 template <typename real, int STAGE>
-using StageSmem = std::conditional_t<stage_ctu(STAGE), CtuSmem<real, stage_ppm(STAGE) ? 3 : 2>,
-                                     StepSmem<real, stage_ppm(STAGE) ? 3 : 2>>;
+using StageSmem = std::conditional_t<
+    STAGE == ST_MH_DE, StepSmemDE<real>,
+    std::conditional_t<stage_ctu(STAGE), CtuSmem<real, stage_ppm(STAGE) ? 3 : 2>,
+                       StepSmem<real, stage_ppm(STAGE) ? 3 : 2>>>;
 
 // One run (or group) of the instance's march.
 template <typename real, int STAGE>

@@ -87,6 +87,35 @@ class UniformGrid:
             out.copy_(st, non_blocking=out.device.type == "cpu" and out.is_pinned())
             return out
 
+    def set_entropy(self, S_dense):
+        """Dual energy: the entropy per unit volume s = P / rho^(gamma-1) of the
+        current state, [nz][ny][nx] float64; allocates the two entropy slot
+        buffers and registers them (params.dual_energy)."""
+        cur, _, _ = A.amr_hydro_get_state(self.ctx, 0)
+        self.S = [torch.zeros((self.n_patches, 8, 8, 8), dtype=torch.float64, device=self.device)
+                  for _ in range(2)]
+        A.amr_hydro_set_entropy(self.ctx, 0, self.S[cur], self.S[1 - cur])
+        tmp = torch.zeros_like(self.U[0])
+        st = self._staging()
+        nx, ny, nz = self.shape
+        with torch.cuda.stream(self._torch_stream()):
+            st.zero_()
+            st[0].copy_(torch.as_tensor(np.ascontiguousarray(S_dense)))
+            A.amr_hydro_pack_uniform(st, nx, ny, nz, tmp, self.stream)
+            self.S[cur].copy_(tmp[:, 0])
+        torch.cuda.synchronize(self.device)
+
+    def entropy(self):
+        """The current entropy field as [nz][ny][nx] (numpy)."""
+        cur, _, _ = A.amr_hydro_get_state(self.ctx, 0)
+        tmp = torch.zeros_like(self.U[0])
+        st = self._staging()
+        nx, ny, nz = self.shape
+        with torch.cuda.stream(self._torch_stream()):
+            tmp[:, 0].copy_(self.S[cur])
+            A.amr_hydro_unpack_uniform(tmp, nx, ny, nz, st, self.stream)
+            return st[0].cpu().numpy()
+
     def min_dt(self):
         return A.amr_hydro_min_dt(self.ctx, 0)
 

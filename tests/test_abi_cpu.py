@@ -28,6 +28,13 @@ def test_library_exports_every_declared_symbol():
     assert sorted(A.SYMBOLS) == decl
 
 
+def test_every_symbol_has_declared_argument_types():
+    # an undeclared signature would pass 64-bit pointers as C ints
+    L = A.lib()
+    for name in A.SYMBOLS:
+        assert getattr(L, name).argtypes is not None, name
+
+
 def test_strerror():
     assert A.strerror(A.AMR_OK) == "ok"
     assert "unphysical" in A.strerror(A.AMR_E_UNPHYSICAL)
@@ -37,7 +44,7 @@ def test_strerror():
                                          ("prec", 7), ("limiter", 4), ("limiter", -1), ("riemann", 4),
                                          ("minmod_coeff", 0.5), ("minmod_coeff", 2.5), ("scheme", 3),
                                          ("scheme", -1), ("recon", 2), ("recon", -1), ("fallback", 2),
-                                         ("dt_min", -1.0)])
+                                         ("dt_min", -1.0), ("dual_energy", 2), ("dual_xi", -1.0)])
 def test_init_rejects_bad_params(field, value):
     p = A.make_params(root_n=(32, 32, 32))
     setattr(p, field, value)
@@ -52,6 +59,16 @@ def test_init_rejects_vl_on_refined_hierarchies_and_with_ppm():
     for kw in (dict(lmax=1), dict(recon=A.AMR_RECON_PPM)):
         p = A.make_params(root_n=(32, 32, 32), scheme=A.AMR_SCHEME_VL, **kw)
         assert A.lib().amr_hydro_init(ctypes.byref(p), None, ctypes.byref(ctx)) == A.AMR_E_INVAL
+        assert not ctx.value
+
+
+def test_init_rejects_dual_energy_outside_its_scope():
+    # built for single-level MUSCL-Hancock + PLM without the cell remedies
+    ctx = ctypes.c_void_p()
+    for kw in (dict(scheme=A.AMR_SCHEME_CTU), dict(scheme=A.AMR_SCHEME_VL), dict(recon=A.AMR_RECON_PPM),
+               dict(lmax=1), dict(fallback=1)):
+        p = A.make_params(root_n=(32, 32, 32), dual_energy=1, **kw)
+        assert A.lib().amr_hydro_init(ctypes.byref(p), None, ctypes.byref(ctx)) == A.AMR_E_INVAL, kw
         assert not ctx.value
 
 
