@@ -179,9 +179,17 @@ def e2e_steps(torch, grid, stream, host_a, host_b, K, dt):
     return t0.elapsed_time(t1), dt
 
 
+def entropy(U, gamma=5.0 / 3.0):
+    """s = P / rho^(gamma-1) of a dense state (the dual-energy variable)."""
+    P = (gamma - 1.0) * (U[4] - 0.5 * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / U[0])
+    return P / U[0] ** (gamma - 1.0)
+
+
 def run_case(torch, A, UniformGrid, U0, n, prec, K, W, stream, want_e2e, scheme=None):
     g = UniformGrid((n, n, n), prec=prec, stream=stream.cuda_stream, scheme=scheme)
     g.upload(torch.from_numpy(U0))
+    if scheme and scheme.get("dual_energy"):
+        g.set_entropy(entropy(U0))
     torch.cuda.synchronize()
     for _ in range(W):
         g.step(-1.0)
@@ -313,7 +321,8 @@ def bench_schemes(torch, A, UniformGrid, stream, K, W, world):
     every limiter; Roe and the exact solver with the van Leer-type limiter)
     the VL scheme (van Leer-type with HLLC and with HLLE) and the CTU scheme
     (van Leer-type with HLLC and with Roe), PPM with MUSCL-Hancock + HLLC and
-    with CTU + Roe (the scheme of the paper's Kelvin-Helmholtz runs), on the
+    with CTU + Roe (the scheme of the paper's Kelvin-Helmholtz runs), the
+    remedies for unphysical results and the dual-energy formalism, on the
     256^3 turbulence level, the default MUSCL-Hancock + PLM van Leer-type +
     HLLC for reference: cells/s per precision."""
     from paper_1712_07070_b300 import ics
@@ -329,12 +338,15 @@ def bench_schemes(torch, A, UniformGrid, stream, K, W, world):
     combos += [(VLR, A.AMR_RS_HLLC, VL, PLM), (VLR, A.AMR_RS_HLLE, VL, PLM)]
     combos += [(VLR, A.AMR_RS_HLLC, CTU, PLM), (VLR, A.AMR_RS_ROE, CTU, PLM)]
     combos += [(VLR, A.AMR_RS_HLLC, MH, PPM), (VLR, A.AMR_RS_ROE, CTU, PPM)]
+    # the remedies for unphysical results and the dual-energy formalism (options)
+    combos += [(VLR, A.AMR_RS_HLLC, MH, PLM, {"fallback": 1}), (VLR, A.AMR_RS_HLLC, MH, PLM, {"dual_energy": 1})]
     rnames = {A.AMR_RS_HLLC: "HLLC", A.AMR_RS_HLLE: "HLLE", A.AMR_RS_ROE: "Roe", A.AMR_RS_EXACT: "exact"}
     snames = {MH: "MUSCL-Hancock", VL: "VL", CTU: "CTU (6 solves/cell, Eq. CFL1)"}
-    for lim, rs, scheme, recon in combos:
-        sch = {"limiter": lim, "riemann": rs, "minmod_coeff": 1.5, "scheme": scheme, "recon": recon}
-        row = {"workload": "turbulence 256^3", "scheme": snames[scheme], "recon": "PPM" if recon == PPM else "PLM",
-               "limiter": names[lim], "riemann": rnames[rs]}
+    for lim, rs, scheme, recon, *extra in combos:
+        opts = extra[0] if extra else {}
+        sch = dict({"limiter": lim, "riemann": rs, "minmod_coeff": 1.5, "scheme": scheme, "recon": recon}, **opts)
+        row = dict({"workload": "turbulence 256^3", "scheme": snames[scheme], "recon": "PPM" if recon == PPM else "PLM",
+                    "limiter": names[lim], "riemann": rnames[rs]}, **opts)
         for prec, key in ((A.AMR_FP64, "f64"), (A.AMR_FP32_ACC64, "fp32_acc64")):
             r = run_case(torch, A, UniformGrid, U1, 256, prec, K, W, stream, want_e2e=False, scheme=sch)
             ms = max_over_ranks(r["region_ms"], "cuda") / K
