@@ -342,6 +342,36 @@ amr_status amr_hydro_box_tuning(amr_hydro_ctx *ctx, int *grid, int *chunked, int
                                 float *ms_per_step);
 
 /*
+ * Gravity (section 2.3; Appendix A).  Root level, periodic: the potential of
+ * the 7-point discrete Poisson equation
+ *   sum_d (phi_{i+e_d} - 2 phi_i + phi_{i-e_d}) / dh^2 = 4 pi G (rho_i - <rho>)
+ * by FFT (phi_k = 4 pi G dh^2 rho_k / lambda_k, lambda_k = -2 sum_d
+ * (1 - cos(2 pi k_d / N_d)), phi_0 = 0), from the density of level 0's
+ * current state (which must hold the whole root grid).  phi: FP64
+ * [n_patches][8][8][8] in level 0's slot order; acc: NULL or
+ * [n_patches][3][8][8][8] receiving g = -grad phi (x, y, z) by acc_order = 2
+ * or 4 point central differences.  Caller-owned, device; asynchronous on
+ * the context's stream.  Uses cuFFT (plans kept in the context).
+ */
+amr_status amr_hydro_poisson_root(amr_hydro_ctx *ctx, double G, double *phi, double *acc, int acc_order);
+
+/*
+ * Refined level (>= 1): every patch solved on its own (8 + 2*5)^3 grid
+ * (section 2.3): density from the level's patches, else injected from the
+ * parent level's cells; the grid's outermost layer (fixed) and initial guess
+ * by quadratic interpolation in space of phi_coarse (the parent level's
+ * potential, [n_coarse_patches][8][8][8]; the tensor product of the 1-D
+ * quadratic through coarse cells c-1, c, c+1 at the child's offset -1/4 or
+ * +1/4, along x, y, z); then `iters` red-black SOR iterations with
+ * relaxation factor omega; the active cells' potential into phi
+ * ([n_patches][8][8][8]) and, if acc is not NULL, -grad phi into acc
+ * ([n_patches][3][8][8][8]) by acc_order = 2 or 4 point central differences.
+ * Asynchronous on the context's stream.
+ */
+amr_status amr_hydro_poisson_level(amr_hydro_ctx *ctx, int level, double G, double omega, int iters,
+                                   const double *phi_coarse, double *phi, double *acc, int acc_order);
+
+/*
  * Discrete adjoint of one uniform periodic MUSCL-Hancock step of size dt (no
  * counterpart in the paper; the reverse of section 2.2's update with dt held
  * fixed): lam_n = (dU^{n+1}/dU^n)^T lam_np1.  U_n, lam_np1, lam_n: device FP64

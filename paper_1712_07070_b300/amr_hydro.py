@@ -30,7 +30,7 @@ SYMBOLS = (
     "amr_hydro_strerror", "amr_hydro_uniform_tables", "amr_hydro_pack_uniform",
     "amr_hydro_unpack_uniform", "amr_hydro_step_uniform_noalloc", "amr_hydro_bind_level",
     "amr_hydro_regrid", "amr_hydro_advance_root", "amr_hydro_level_info", "amr_hydro_box_tuning",
-    "amr_hydro_advance_host", "amr_hydro_set_entropy",
+    "amr_hydro_advance_host", "amr_hydro_set_entropy", "amr_hydro_poisson_root", "amr_hydro_poisson_level",
 )
 
 
@@ -72,6 +72,9 @@ def lib():
         "amr_hydro_get_state": [_vp, ctypes.c_int, _ip, _dp, _dp],
         "amr_hydro_touch_level": [_vp, ctypes.c_int],
         "amr_hydro_set_entropy": [_vp, ctypes.c_int, _vp, _vp],
+        "amr_hydro_poisson_root": [_vp, ctypes.c_double, _vp, _vp, ctypes.c_int],
+        "amr_hydro_poisson_level": [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp, _vp,
+                                    _vp, ctypes.c_int],
         "amr_hydro_fill_ghost": [_vp, ctypes.c_int, ctypes.c_double],
         "amr_hydro_advance_level": [_vp, ctypes.c_int, ctypes.c_double, _i64p],
         "amr_hydro_advance_host": [_vp, _vp, _vp, ctypes.c_double, _dp],
@@ -172,6 +175,15 @@ def amr_hydro_advance_level(ctx, level, dt, count_unphysical=False):
 
 def amr_hydro_set_entropy(ctx, level, S_a, S_b):
     check(lib().amr_hydro_set_entropy(ctx, level, _p(S_a), _p(S_b)), "amr_hydro_set_entropy")
+
+
+def amr_hydro_poisson_root(ctx, G, phi, acc=None, acc_order=2):
+    check(lib().amr_hydro_poisson_root(ctx, G, _p(phi), _p(acc), acc_order), "amr_hydro_poisson_root")
+
+
+def amr_hydro_poisson_level(ctx, level, G, omega, iters, phi_coarse, phi, acc=None, acc_order=2):
+    check(lib().amr_hydro_poisson_level(ctx, level, G, omega, iters, _p(phi_coarse), _p(phi), _p(acc), acc_order),
+          "amr_hydro_poisson_level")
 
 
 def amr_hydro_flux_fixup(ctx, coarse_level):

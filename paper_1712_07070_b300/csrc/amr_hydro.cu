@@ -327,6 +327,7 @@ amr_status amr_hydro_destroy(amr_hydro_ctx *c) {
     c->hstage[1].release();
     c->fb_list.release();
     c->fb_count.release();
+    release_poisson(c);
     delete c;
     return AMR_OK;
 }

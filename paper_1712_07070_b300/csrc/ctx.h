@@ -147,6 +147,9 @@ struct amr_hydro_ctx {
     // cells the step left unphysical, for the cell remedies (params.fallback)
     amrh::DevBuf<int64_t> fb_list;
     amrh::DevBuf<unsigned long long> fb_count;
+    // root-level Poisson solver: cuFFT plans (forward, inverse) and work arrays
+    long long fft_plan[2] = {0, 0};
+    amrh::DevBuf<double> fft_real, fft_cplx;
 };
 
 namespace amrh {
@@ -156,6 +159,7 @@ double level_dh(const amr_hydro_ctx *c, int level);
 amr_status level_speed(amr_hydro_ctx *c, int level);
 size_t step_smem_bytes(int prec);
 void scheme_stages(int scheme, int recon, int dual_energy, int &lo, int &hi);
+void release_poisson(amr_hydro_ctx *c);
 struct StepParams;
 amr_status launch_step(amr_hydro_ctx *c, const StepParams &P, int grid);
 amr_status launch_step_raw(int prec, const StepParams &P, cudaStream_t stream);

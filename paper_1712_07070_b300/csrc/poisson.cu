@@ -1,0 +1,291 @@
+// poisson.cu -- GAMER-2 gravity solvers (section 2.3; section 3.1 and
+// Appendix A for the refined levels): the root level's periodic potential by
+// FFT, the refined levels' potential by SOR on an 18^3 grid per patch, and
+// the cell-centred accelerations.
+//
+// Root level: the 7-point discrete Poisson equation
+//     sum_d (phi_{i+e_d} - 2 phi_i + phi_{i-e_d}) / dh^2 = 4 pi G (rho_i - <rho>)
+// is diagonal in Fourier space: phi_k = 4 pi G dh^2 rho_k / lambda_k with
+// lambda_k = -2 sum_d (1 - cos(2 pi k_d / N_d)) and phi_0 = 0 (cuFFT D2Z,
+// one scaling kernel, Z2D).
+//
+// Refined levels: one CTA per patch holds the potential and the density of
+// the patch's (8 + 2*5)^3 grid in shared memory (93 KB: two CTAs per SM).
+// The density is the level's where a same-level patch holds the cell, else
+// the parent level's cell (injection); the potential's outermost layer (held
+// fixed) and initial guess come from the parent level's potential by
+// quadratic interpolation in space (the tensor product of the 1-D quadratic
+// through coarse cells c-1, c, c+1 at the child's offset -1/4 or +1/4, along
+// x, then y, then z).  Then a fixed number of red-black SOR iterations
+//     phi += omega (sum of the 6 neighbours - 6 phi - dh^2 4 pi G rho) / 6
+// (red: i+j+k even in grid indices), the active 8^3 cells' potential and
+// -grad phi by two- or four-point central differences.  The parent level
+// holds every coarse cell read: a patch is refined only when all 26 of its
+// sibling positions hold patches, and the grid reaches at most 4 coarse cells
+// beyond the parent.
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstdio>
+
+#include "amr_hydro.h"
+#include "ctx.h"
+#include "step_kernel.cuh"
+
+namespace amrh {
+
+namespace {
+
+constexpr int PN = 18, PB = 5;  // SOR grid edge, buffer cells per side
+constexpr int PN3 = PN * PN * PN;
+constexpr double PI = 3.14159265358979323846;
+constexpr double FOUR_PI = 4.0 * PI;
+constexpr int SOR_NT = 256;
+
+// ---- root level ------------------------------------------------------------------
+
+// rho (variable 0 of the level's current state) into a dense [nz][ny][nx] array
+__global__ void k_rho_dense(const double *__restrict__ U, const int32_t *__restrict__ corner, int n_patches, int nx,
+                            int ny, double *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)n_patches * PV;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = i / PV;
+        const int c = (int)(i % PV);
+        const int x = corner[3 * s] + (c & 7), y = corner[3 * s + 1] + ((c >> 3) & 7),
+                  z = corner[3 * s + 2] + (c >> 6);
+        out[((int64_t)z * ny + y) * nx + x] = U[s * PSLOT + c];
+    }
+}
+
+// phi_k = 4 pi G dh^2 rho_k / (lambda_k N) (the inverse transform is unnormalised)
+__global__ void k_green(cufftDoubleComplex *F, int nx, int ny, int nz, double scale) {
+    const int nxh = nx / 2 + 1;
+    const int64_t n = (int64_t)nz * ny * nxh;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int kx = (int)(i % nxh), ky = (int)((i / nxh) % ny), kz = (int)(i / ((int64_t)nxh * ny));
+        const double lam = -2.0 * ((1.0 - cos(2.0 * PI * kx / nx)) + (1.0 - cos(2.0 * PI * ky / ny)) +
+                                   (1.0 - cos(2.0 * PI * kz / nz)));
+        if (i == 0) {
+            F[i].x = 0.0;
+            F[i].y = 0.0;
+        } else {
+            F[i].x = F[i].x / lam * scale;
+            F[i].y = F[i].y / lam * scale;
+        }
+    }
+}
+
+// phi and -grad phi (periodic central differences) of the dense root potential into the slots
+__global__ void k_root_out(const double *__restrict__ phi, const int32_t *__restrict__ corner, int n_patches, int nx,
+                           int ny, int nz, double dh, int order, double *__restrict__ phi_out,
+                           double *__restrict__ acc_out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)n_patches * PV;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = i / PV;
+        const int c = (int)(i % PV);
+        const int x = corner[3 * s] + (c & 7), y = corner[3 * s + 1] + ((c >> 3) & 7),
+                  z = corner[3 * s + 2] + (c >> 6);
+        auto at = [&](int a, int b, int d) {
+            a = (a + nx) % nx;
+            b = (b + ny) % ny;
+            d = (d + nz) % nz;
+            return phi[((int64_t)d * ny + b) * nx + a];
+        };
+        phi_out[s * PV + c] = at(x, y, z);
+        if (!acc_out) continue;
+        for (int d = 0; d < 3; d++) {
+            const int ex = d == 0, ey = d == 1, ez = d == 2;
+            double g;
+            if (order == 2) {
+                g = (at(x + ex, y + ey, z + ez) - at(x - ex, y - ey, z - ez)) / (2.0 * dh);
+            } else {
+                g = (-at(x + 2 * ex, y + 2 * ey, z + 2 * ez) + 8.0 * at(x + ex, y + ey, z + ez) -
+                     8.0 * at(x - ex, y - ey, z - ez) + at(x - 2 * ex, y - 2 * ey, z - 2 * ez)) /
+                    (12.0 * dh);
+            }
+            acc_out[(s * 3 + d) * PV + c] = -g;
+        }
+    }
+}
+
+// ---- refined levels -------------------------------------------------------------
+
+struct SorSmem {
+    double phi[PN][PN][PN];
+    double rho[PN][PN][PN];
+    int nb[27], cnb[27];  // same-level patches around the patch, parent-level patches around its parent
+    int off[3];           // the patch's lower corner relative to its parent's, in coarse cells (0 or 4)
+};
+
+__device__ __forceinline__ double quad1(double pm, double p0, double pp, double x) {
+    return p0 + x * (pp - pm) / 2.0 + x * x * (pp - 2.0 * p0 + pm) / 2.0;
+}
+
+// a value of a parent-level field at coarse cell c relative to the parent's
+// lower corner (each coordinate in -8..15)
+__device__ __forceinline__ double coarse_at(const double *__restrict__ F, int64_t stride, const int *cnb, int cx,
+                                            int cy, int cz) {
+    const int k = ((cx >> 3) + 1) + 3 * ((cy >> 3) + 1) + 9 * ((cz >> 3) + 1);
+    return F[(int64_t)cnb[k] * stride + (cz & 7) * 64 + (cy & 7) * 8 + (cx & 7)];
+}
+
+__global__ void __launch_bounds__(SOR_NT) k_sor_patches(
+    const double *__restrict__ U, const int32_t *__restrict__ sib, const int32_t *__restrict__ parent,
+    const int32_t *__restrict__ corner, const double *__restrict__ Uc, const int32_t *__restrict__ csib,
+    const int32_t *__restrict__ ccorner, const double *__restrict__ phic, int n_patches, double dh, double G,
+    double omega, int iters, int order, double *__restrict__ phi_out, double *__restrict__ acc_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SorSmem &S = *reinterpret_cast<SorSmem *>(smem_raw);
+    double *rho_flat = &S.rho[0][0][0], *phi_flat = &S.phi[0][0][0];
+    const int tid = threadIdx.x;
+    const double src_scale = dh * dh * FOUR_PI * G;
+    for (int p = blockIdx.x; p < n_patches; p += gridDim.x) {
+        if (tid < 27) {
+            const int P = parent[p];
+            S.nb[tid] = tid == 13 ? p : sib[(int64_t)p * 26 + tid - (tid > 13)];
+            const int cs = tid == 13 ? P : csib[(int64_t)P * 26 + tid - (tid > 13)];
+            S.cnb[tid] = cs >= 0 ? cs : P;  // present on a properly nested hierarchy
+            if (tid < 3) S.off[tid] = corner[3 * p + tid] / 2 - ccorner[3 * P + tid];
+        }
+        __syncthreads();
+        // density and initial guess on the 18^3 grid
+        for (int i = tid; i < PN3; i += SOR_NT) {
+            const int gx = i % PN - PB, gy = (i / PN) % PN - PB, gz = i / (PN * PN) - PB;  // fine, relative
+            const int k = ((gx >> 3) + 1) + 3 * ((gy >> 3) + 1) + 9 * ((gz >> 3) + 1);
+            const int cx = S.off[0] + (gx >> 1), cy = S.off[1] + (gy >> 1), cz = S.off[2] + (gz >> 1);
+            const int s = S.nb[k];
+            rho_flat[i] = s >= 0 ? U[(int64_t)s * PSLOT + (gz & 7) * 64 + (gy & 7) * 8 + (gx & 7)]
+                                 : coarse_at(Uc, PSLOT, S.cnb, cx, cy, cz);
+            const double ox = (gx & 1) ? 0.25 : -0.25, oy = (gy & 1) ? 0.25 : -0.25, oz = (gz & 1) ? 0.25 : -0.25;
+            double Y[3];
+            for (int dz = -1; dz <= 1; dz++) {
+                double X[3];
+                for (int dy = -1; dy <= 1; dy++)
+                    X[dy + 1] = quad1(coarse_at(phic, PV, S.cnb, cx - 1, cy + dy, cz + dz),
+                                      coarse_at(phic, PV, S.cnb, cx, cy + dy, cz + dz),
+                                      coarse_at(phic, PV, S.cnb, cx + 1, cy + dy, cz + dz), ox);
+                Y[dz + 1] = quad1(X[0], X[1], X[2], oy);
+            }
+            phi_flat[i] = quad1(Y[0], Y[1], Y[2], oz);
+        }
+        __syncthreads();
+        // red-black SOR on the interior 16^3 cells
+        for (int it = 0; it < iters; it++) {
+            for (int colour = 0; colour < 2; colour++) {
+                for (int t = tid; t < 2048; t += SOR_NT) {
+                    const int row = t >> 3, k = row / 16 + 1, j = row % 16 + 1;
+                    const int i = 1 + ((1 + j + k + colour) & 1) + 2 * (t & 7);
+                    const double ph = S.phi[k][j][i];
+                    const double nbs = S.phi[k - 1][j][i] + S.phi[k + 1][j][i] + S.phi[k][j - 1][i] +
+                                       S.phi[k][j + 1][i] + S.phi[k][j][i - 1] + S.phi[k][j][i + 1];
+                    S.phi[k][j][i] = ph + omega * (nbs - 6.0 * ph - src_scale * S.rho[k][j][i]) / 6.0;
+                }
+                __syncthreads();
+            }
+        }
+        // the active cells' potential and acceleration
+        for (int c = tid; c < PV; c += SOR_NT) {
+            const int x = (c & 7) + PB, y = ((c >> 3) & 7) + PB, z = (c >> 6) + PB;
+            phi_out[(int64_t)p * PV + c] = S.phi[z][y][x];
+            if (!acc_out) continue;
+            for (int d = 0; d < 3; d++) {
+                const int ex = d == 0, ey = d == 1, ez = d == 2;
+                double g;
+                if (order == 2) {
+                    g = (S.phi[z + ez][y + ey][x + ex] - S.phi[z - ez][y - ey][x - ex]) / (2.0 * dh);
+                } else {
+                    g = (-S.phi[z + 2 * ez][y + 2 * ey][x + 2 * ex] + 8.0 * S.phi[z + ez][y + ey][x + ex] -
+                         8.0 * S.phi[z - ez][y - ey][x - ex] + S.phi[z - 2 * ez][y - 2 * ey][x - 2 * ex]) /
+                        (12.0 * dh);
+                }
+                acc_out[((int64_t)p * 3 + d) * PV + c] = -g;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+amr_status cufft_fail(cufftResult r, const char *where) {
+    if (r == CUFFT_SUCCESS) return AMR_OK;
+    std::fprintf(stderr, "amr_hydro: %s: cuFFT error %d\n", where, (int)r);
+    return AMR_E_CUDA;
+}
+
+}  // namespace
+
+void release_poisson(amr_hydro_ctx *c) {
+    if (c->fft_plan[0]) cufftDestroy((cufftHandle)c->fft_plan[0]);
+    if (c->fft_plan[1]) cufftDestroy((cufftHandle)c->fft_plan[1]);
+    c->fft_plan[0] = c->fft_plan[1] = 0;
+    c->fft_real.release();
+    c->fft_cplx.release();
+}
+
+}  // namespace amrh
+
+using namespace amrh;
+
+extern "C" {
+
+amr_status amr_hydro_poisson_root(amr_hydro_ctx *c, double G, double *phi, double *acc, int acc_order) {
+    if (!c || !phi || (acc && acc_order != 2 && acc_order != 4)) return AMR_E_INVAL;
+    Level &L = c->lv[0];
+    const int nx = c->prm.root_n[0], ny = c->prm.root_n[1], nz = c->prm.root_n[2];
+    if ((int64_t)L.n_patches * PV != (int64_t)nx * ny * nz) return AMR_E_INVAL;  // the whole root grid
+    const int64_t n = (int64_t)nx * ny * nz, nc = (int64_t)nz * ny * (nx / 2 + 1);
+    amr_status st;
+    if ((st = c->fft_real.reserve(n)) || (st = c->fft_cplx.reserve(2 * nc))) return st;
+    if (!c->fft_plan[0]) {
+        cufftHandle f, b;
+        if ((st = cufft_fail(cufftPlan3d(&f, nz, ny, nx, CUFFT_D2Z), "plan"))) return st;
+        if ((st = cufft_fail(cufftPlan3d(&b, nz, ny, nx, CUFFT_Z2D), "plan"))) {
+            cufftDestroy(f);
+            return st;
+        }
+        c->fft_plan[0] = (long long)f;
+        c->fft_plan[1] = (long long)b;
+    }
+    cufftHandle f = (cufftHandle)c->fft_plan[0], b = (cufftHandle)c->fft_plan[1];
+    cudaStream_t s = c->stream;
+    if ((st = cufft_fail(cufftSetStream(f, s), "stream")) || (st = cufft_fail(cufftSetStream(b, s), "stream")))
+        return st;
+    const int grid = c->n_sm * 8;
+    const double dh = level_dh(c, 0);
+    k_rho_dense<<<grid, 256, 0, s>>>(L.U[L.cur], L.d_corner, L.n_patches, nx, ny, c->fft_real.p);
+    if ((st = cuda_fail(cudaGetLastError(), "k_rho_dense"))) return st;
+    cufftDoubleComplex *F = (cufftDoubleComplex *)c->fft_cplx.p;
+    if ((st = cufft_fail(cufftExecD2Z(f, c->fft_real.p, F), "D2Z"))) return st;
+    k_green<<<grid, 256, 0, s>>>(F, nx, ny, nz, FOUR_PI * G * dh * dh / (double)n);
+    if ((st = cuda_fail(cudaGetLastError(), "k_green"))) return st;
+    if ((st = cufft_fail(cufftExecZ2D(b, F, c->fft_real.p), "Z2D"))) return st;
+    k_root_out<<<grid, 256, 0, s>>>(c->fft_real.p, L.d_corner, L.n_patches, nx, ny, nz, dh, acc_order, phi, acc);
+    return cuda_fail(cudaGetLastError(), "k_root_out");
+}
+
+amr_status amr_hydro_poisson_level(amr_hydro_ctx *c, int level, double G, double omega, int iters,
+                                   const double *phi_coarse, double *phi, double *acc, int acc_order) {
+    if (!c || level < 1 || level > c->prm.lmax || !phi_coarse || !phi || iters < 0) return AMR_E_INVAL;
+    if (acc && acc_order != 2 && acc_order != 4) return AMR_E_INVAL;
+    Level &L = c->lv[level], &C = c->lv[level - 1];
+    if (!L.n_patches) return AMR_OK;
+    if (!L.d_parent || !C.n_patches) return AMR_E_INVAL;
+    static bool configured = false;
+    amr_status st;
+    if (!configured) {
+        if ((st = cuda_fail(cudaFuncSetAttribute(k_sor_patches, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)sizeof(SorSmem)),
+                            "sor smem attribute")))
+            return st;
+        configured = true;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sor_patches, SOR_NT, sizeof(SorSmem));
+    const int cap = c->n_sm * (per_sm > 0 ? per_sm : 1);
+    const int grid = L.n_patches < cap ? L.n_patches : cap;
+    k_sor_patches<<<grid, SOR_NT, sizeof(SorSmem), c->stream>>>(
+        L.U[L.cur], L.d_sib, L.d_parent, L.d_corner, C.U[C.cur], C.d_sib, C.d_corner, phi_coarse, L.n_patches,
+        level_dh(c, level), G, omega, iters, acc_order, phi, acc);
+    return cuda_fail(cudaGetLastError(), "k_sor_patches");
+}
+
+}  // extern "C"

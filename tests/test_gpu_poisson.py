@@ -1,0 +1,93 @@
+"""GPU parity of the gravity solvers (section 2.3; Appendix A) against the
+numpy oracle (oracle/poisson.py): the root level's periodic FFT potential
+and its accelerations (two- and four-point), and the refined levels' SOR
+potential on 18^3 grids per patch (density from the level or injected from
+its parent, boundary and initial guess by quadratic interpolation of the
+parent's potential) on a three-level hierarchy, each level's oracle input
+being the oracle's own potential of the level above."""
+import numpy as np
+import pytest
+
+from oracle import poisson as PS
+from oracle.amr import OracleHierarchy, cell_mask
+from paper_1712_07070_b300 import amr_hydro as A
+from paper_1712_07070_b300 import ics
+from test_gpu_amr import compare
+
+pytestmark = pytest.mark.gpu
+G53 = 5.0 / 3.0
+
+
+def dense_of(slots, corners, shape):
+    out = np.zeros(shape)
+    for s, (x, y, z) in enumerate(corners):
+        out[..., z:z + 8, y:y + 8, x:x + 8] = slots[s]
+    return out
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_root_periodic_fft(order):
+    import torch
+    from paper_1712_07070_b300.uniform import UniformGrid
+    nx, ny, nz = 32, 48, 64
+    U0 = ics.sod_noise(nx, seed=17, ny=ny, nz=nz)
+    g = UniformGrid((nx, ny, nz))
+    g.upload(U0)
+    n = g.n_patches
+    phi = torch.zeros((n, 8, 8, 8), dtype=torch.float64, device="cuda")
+    acc = torch.zeros((n, 3, 8, 8, 8), dtype=torch.float64, device="cuda")
+    A.amr_hydro_poisson_root(g.ctx, 0.9, phi, acc, order)
+    corners = g.tables[0].cpu().numpy()
+    ph = dense_of(phi.cpu().numpy(), corners, (nz, ny, nx))
+    ac = dense_of(acc.cpu().numpy(), corners, (3, nz, ny, nx))
+    g.close()
+    dh = 1.0 / nx
+    ref = PS.poisson_root_periodic(U0[0], dh, 0.9)
+    assert np.abs(ph - ref).max() <= 1e-12 * np.abs(ref).max()
+    h = order // 2
+    gref = PS.accel(np.pad(ref, h, mode="wrap"), dh, order)
+    assert np.abs(ac - gref).max() <= 1e-11 * np.abs(gref).max()
+
+
+def test_refined_levels_sor():
+    import torch
+    from paper_1712_07070_b300.amr import AmrHierarchy
+    U0 = ics.blobs(32, seed=3)
+    H = AmrHierarchy(U0, lmax=2, theta=0.05, nbuf=(8, 4), max_patches=6000)
+    O = OracleHierarchy(U0, lmax=2, gamma=G53, cfl=0.5, theta=0.05, nbuf=[8, 4])
+    compare(H, O, 1e-12)  # the same patches and states on every level
+    G, omega, iters = 1.0, 1.7, 40
+    phis = []
+    n0 = H.n_patches(0)
+    phi = torch.zeros((n0, 8, 8, 8), dtype=torch.float64, device="cuda")
+    A.amr_hydro_poisson_root(H.ctx, G, phi)
+    phis.append(phi)
+    accs = [None]
+    for l in (1, 2):
+        n = H.n_patches(l)
+        phi = torch.zeros((max(n, 1), 8, 8, 8), dtype=torch.float64, device="cuda")
+        acc = torch.zeros((max(n, 1), 3, 8, 8, 8), dtype=torch.float64, device="cuda")
+        A.amr_hydro_poisson_level(H.ctx, l, G, omega, iters, phis[-1], phi, acc, 4)
+        phis.append(phi)
+        accs.append(acc)
+    torch.cuda.synchronize()
+    # the oracle, each level from its own potential of the level above
+    phic = PS.poisson_root_periodic(O.lv[0].U[0], 1.0 / 32, G)
+    checked = 0
+    for l in (1, 2):
+        Lo, Lc = O.lv[l], O.lv[l - 1]
+        fmask = cell_mask(Lo.mask)
+        dh = 1.0 / (32 << l)
+        phi_l = np.zeros(Lo.U[0].shape)
+        gp, ga = phis[l].cpu().numpy(), accs[l].cpu().numpy()
+        for s, (x, y, z) in enumerate(H.corners(l)):
+            grid = PS.refined_patch_potential(phic, Lo.U[0], fmask, Lc.U[0], (x, y, z), dh, G, omega, iters)
+            act = grid[5:13, 5:13, 5:13]
+            assert np.abs(gp[s] - act).max() <= 1e-12 * np.abs(act).max(), (l, s)
+            gref = PS.accel(grid, dh, 4)[:, 3:11, 3:11, 3:11]
+            assert np.abs(ga[s] - gref).max() <= 1e-10 * np.abs(gref).max(), (l, s)
+            phi_l[z:z + 8, y:y + 8, x:x + 8] = act
+            checked += 1
+        phic = phi_l
+    assert checked > 100
+    H.close()
