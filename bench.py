@@ -306,6 +306,7 @@ def run_ours(args):
         line["amr"] = bench_amr(torch, args)
         line["boxes"] = bench_boxes(torch, args)
         line["adjoint"] = bench_adjoint(torch, args)
+        line["gravity"] = bench_gravity(torch, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n)
     if rank == 0:
@@ -383,6 +384,52 @@ def bench_amr(torch, args):
                      "patches": [H.n_patches(l) for l in range(3)]}
         H.close()
     out["value"] = out["f64"]["value"]
+    return out
+
+
+def bench_gravity(torch, args):
+    """Gravity solvers (section 2.3): the root level's periodic FFT Poisson
+    solve with accelerations on the 256^3 turbulence density, and the
+    per-patch SOR solve (18^3 grid per patch, 60 red-black iterations,
+    omega 1.7) with accelerations on the first refined level of the 3-level
+    blob hierarchy of the AMR workload."""
+    from paper_1712_07070_b300 import amr_hydro as A
+    from paper_1712_07070_b300 import ics
+    from paper_1712_07070_b300.amr import AmrHierarchy
+    from paper_1712_07070_b300.uniform import UniformGrid
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {"unit": UNIT}
+    n = 256
+    g = UniformGrid((n, n, n))
+    g.upload(torch.from_numpy(ics.turbulence(n, seed=1)))
+    phi = torch.zeros((g.n_patches, 8, 8, 8), dtype=torch.float64, device="cuda")
+    acc = torch.zeros((g.n_patches, 3, 8, 8, 8), dtype=torch.float64, device="cuda")
+    ms = timed(lambda: A.amr_hydro_poisson_root(g.ctx, 1.0, phi, acc, 2), 5)
+    out["root_fft"] = {"workload": "periodic FFT Poisson + 2-point accelerations, 256^3 root level (cuFFT)",
+                       "ms": ms, "value": n ** 3 / (ms * 1e-3)}
+    g.close()
+    H = AmrHierarchy(ics.blobs(128, seed=3), lmax=2, theta=0.1, nbuf=(8, 4), max_patches=120000)
+    phi0 = torch.zeros((H.n_patches(0), 8, 8, 8), dtype=torch.float64, device="cuda")
+    A.amr_hydro_poisson_root(H.ctx, 1.0, phi0)
+    n1 = H.n_patches(1)
+    phi1 = torch.zeros((n1, 8, 8, 8), dtype=torch.float64, device="cuda")
+    acc1 = torch.zeros((n1, 3, 8, 8, 8), dtype=torch.float64, device="cuda")
+    ms = timed(lambda: A.amr_hydro_poisson_level(H.ctx, 1, 1.0, 1.7, 60, phi0, phi1, acc1, 2), 3)
+    out["sor"] = {"workload": f"SOR on 18^3 per patch, 60 red-black iterations, {n1} level-1 patches of the "
+                              "blob hierarchy, FP64", "ms": ms, "value": n1 * 512 / (ms * 1e-3),
+                  "point_updates_per_s": n1 * 60 * 4096 / (ms * 1e-3)}
+    H.close()
     return out
 
 
