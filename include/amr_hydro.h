@@ -372,6 +372,22 @@ amr_status amr_hydro_poisson_level(amr_hydro_ctx *ctx, int level, double G, doub
                                    const double *phi_coarse, double *phi, double *acc, int acc_order);
 
 /*
+ * One hydro step of a single-level periodic grid coupled to self-gravity
+ * (section 2.3, the operator-unsplit predictor-corrector after Muller &
+ * Steinmetz 1995): the MUSCL-Hancock step whose half step also adds
+ * (dt/2) (0, rho g, m.g) of each face state (g = acc_n, the acceleration at
+ * t^n, [n_patches][3][8][8][8]); the FFT potential phi_new and acceleration
+ * acc_new of the predicted density (as amr_hydro_poisson_root); then
+ * m^{n+1} = m* + (dt/2)(rho^n g^n + rho^{n+1} g^{n+1}) and
+ * E^{n+1} = E* + (dt/2)(m^n.g^n + m^{n+1}.g^{n+1}).  acc_new is the next
+ * step's acc_n.  dt < 0: the device's Eq. (CFL2) dt.  MUSCL-Hancock + PLM
+ * without dual energy, the remedies or the level retry; AMR_E_INVAL otherwise or with
+ * refined levels.  Asynchronous on the context's stream.
+ */
+amr_status amr_hydro_advance_gravity(amr_hydro_ctx *ctx, double dt, double G, const double *acc_n, double *phi_new,
+                                     double *acc_new, int acc_order);
+
+/*
  * Discrete adjoint of one uniform periodic MUSCL-Hancock step of size dt (no
  * counterpart in the paper; the reverse of section 2.2's update with dt held
  * fixed): lam_n = (dU^{n+1}/dU^n)^T lam_np1.  U_n, lam_np1, lam_n: device FP64

@@ -46,6 +46,9 @@ def lib():
         L.or_step_dual.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.or_step_dual.restype = ctypes.c_int64
+        L.or_step_gravity_predictor.argtypes = [_dp, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.or_step_gravity_predictor.restype = ctypes.c_int64
         L.or_ppm_faces.argtypes = [_dp, _dp, _dp]
         L.or_max_speed1.argtypes = [_dp, ctypes.c_int64, ctypes.c_double]
         L.or_max_speed1.restype = ctypes.c_double
@@ -298,6 +301,20 @@ def step_dual(U, S, dh, dt, gamma, xi=1e-2):
     if nbad < 0:
         raise ValueError("dual energy is built for MUSCL-Hancock only")
     return Un, Sn, nbad
+
+
+def step_gravity_predictor(U, g, dh, dt, gamma):
+    """The gravity coupling's predictor: the MUSCL-Hancock step with
+    (dt/2)(0, rho g, m.g) of each face state in the half step; g [3][...]
+    the acceleration at t^n.  Returns (U*, nbad)."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    nz, ny, nx = U.shape[1:]
+    Un = np.empty_like(U)
+    nbad = lib().or_step_gravity_predictor(_ptr(U), _ptr(g), _ptr(Un), nx, ny, nz, dh, dt, gamma)
+    if nbad < 0:
+        raise ValueError("the gravity coupling is built for MUSCL-Hancock only")
+    return Un, nbad
 
 
 def fallback_counts(reset=True):

@@ -89,6 +89,14 @@
  *   the whole step with dt x 0.8 (iv) down to a minimum dt (v).
  * The fluxes returned for the flux registers stay those of the scheme.
  *
+ * Gravity (section 2.3: operator-unsplit predictor-corrector after Muller &
+ * Steinmetz 1995); reading: the predictor is the MUSCL-Hancock step whose
+ * half step also adds (dt/2) (0, rho g, m.g) of each reconstructed face
+ * state, g the cell's acceleration at t^n; the corrector (in oracle/poisson.py)
+ * takes g^{n+1} of the predicted density and sets
+ * m^{n+1} = m* + (dt/2)(rho^n g^n + rho^{n+1} g^{n+1}), then
+ * E^{n+1} = E* + (dt/2)(m^n.g^n + m^{n+1}.g^{n+1}) with the corrected m.
+ *
  * Dual energy (section 2.2: the entropy per unit volume s = P / rho^(gamma-1)
  * carried as a passive scalar; or_step_dual, MUSCL-Hancock only).  Reading:
  *   - reconstruction of q = s / rho like a primitive component (the selected
@@ -176,6 +184,9 @@ double or_vanleer(double a, double b) {
  * 3 hybrid generalized minmod / van Leer-type; riemann: 0 HLLC, 1 HLLE;
  * theta: the generalized minmod coefficient. */
 static int or_limiter_id = 0, or_riemann_id = 0, or_vl = 0, or_ctu = 0, or_ppm = 0, or_fallback = 0;
+/* gravity predictor: the cell-centred acceleration g^n [3][cell] of the
+ * step in progress (or_step_gravity_predictor) */
+static const double *or_grav_g = NULL;
 /* dual energy: the entropy fields of the step in progress (or_step_dual) */
 static const double *or_de_S = NULL;
 static double *or_de_Snew = NULL, or_de_xi = 0.0;
@@ -755,6 +766,16 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
                 for (int f = 0; f < 6; f++)
                     for (int v = 0; v < NV; v++)
                         FS[((int64_t)f * NV + v) * n + i] = Uf[f][v] + 0.5 * dt / dh * inc[v];
+                if (or_grav_g) { /* gravity in the half step: + (dt/2) (0, rho g, m.g) of each face state */
+                    double g[3];
+                    for (int d = 0; d < 3; d++) g[d] = or_grav_g[(int64_t)d * n + i];
+                    for (int f = 0; f < 6; f++) {
+                        for (int d = 0; d < 3; d++)
+                            FS[((int64_t)f * NV + 1 + d) * n + i] += 0.5 * dt * (Uf[f][0] * g[d]);
+                        FS[((int64_t)f * NV + 4) * n + i] +=
+                            0.5 * dt * (Uf[f][1] * g[0] + Uf[f][2] * g[1] + Uf[f][3] * g[2]);
+                    }
+                }
                 if (or_de_S) { /* the entropy scalar: face values s = rho_f q_f, Hancock step */
                     double sf[6], incs = 0.0;
                     for (int d = 0; d < 3; d++) {
@@ -889,6 +910,19 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
     free(W);
     free(FS);
     free(FX);
+    return nbad;
+}
+
+/* The predictor of the gravity coupling: one MUSCL-Hancock step whose half
+ * step adds (dt/2) (0, rho g, m.g) of each reconstructed face state, g the
+ * cell's acceleration at t^n, [3][nz][ny][nx].  Returns the unphysical
+ * count, or -1 for a scheme other than MUSCL-Hancock. */
+int64_t or_step_gravity_predictor(const double *U, const double *g, double *Unew, int nx, int ny, int nz, double dh,
+                                  double dt, double gamma) {
+    if (or_vl || or_ctu) return -1;
+    or_grav_g = g;
+    int64_t nbad = or_step_periodic_fx(U, Unew, nx, ny, nz, dh, dt, gamma, NULL);
+    or_grav_g = NULL;
     return nbad;
 }
 

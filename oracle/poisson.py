@@ -150,3 +150,35 @@ def refined_patch_potential(phi_c, rho_f_dense, fmask_dense, rho_c, corner, dh_f
                          (gx % nxf)[None, None, :] // 2])
     phi0 = interp_quadratic(phi_c, gx, gy, gz)
     return sor(phi0, rho, dh_f, G, omega, iters)
+
+
+def accel_periodic(phi, dh, order=2):
+    """-grad phi of a periodic field, on every cell."""
+    h = order // 2
+    return accel(np.pad(phi, h, mode="wrap"), dh, order)
+
+
+def step_gravity(U, g_n, dh, dt, gamma, G, order=2):
+    """One coupled hydro + self-gravity step on a periodic root grid
+    (section 2.3, after Muller & Steinmetz 1995): the predictor (the
+    MUSCL-Hancock step with gravity in its half step, hydro_oracle.c), the
+    FFT potential and acceleration g^{n+1} of the predicted density, then
+    m^{n+1} = m* + (dt/2)(rho^n g^n + rho^{n+1} g^{n+1}) and
+    E^{n+1} = E* + (dt/2)(m^n.g^n + m^{n+1}.g^{n+1}).
+    Returns (U^{n+1}, phi^{n+1}, g^{n+1}, nbad of the predictor)."""
+    import oracle
+    Us, nbad = oracle.step_gravity_predictor(U, g_n, dh, dt, gamma)
+    phi = poisson_root_periodic(Us[0], dh, G)
+    g1 = accel_periodic(phi, dh, order)
+    return gravity_correct(U, g_n, Us, g1, dt), phi, g1, nbad
+
+
+def gravity_correct(U, g_n, Us, g1, dt):
+    """The corrector: momentum from the accelerations at both ends of the
+    step, then energy with the corrected momentum."""
+    out = Us.copy()
+    for d in range(3):
+        out[1 + d] = Us[1 + d] + 0.5 * dt * (U[0] * g_n[d] + Us[0] * g1[d])
+    out[4] = Us[4] + 0.5 * dt * ((U[1] * g_n[0] + U[2] * g_n[1] + U[3] * g_n[2]) +
+                                 (out[1] * g1[0] + out[2] * g1[1] + out[3] * g1[2]))
+    return out

@@ -160,6 +160,7 @@ amr_status level_speed(amr_hydro_ctx *c, int level);
 size_t step_smem_bytes(int prec);
 void scheme_stages(int scheme, int recon, int dual_energy, int &lo, int &hi);
 void release_poisson(amr_hydro_ctx *c);
+amr_status advance_once(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphysical_out, const double *acc_n);
 struct StepParams;
 amr_status launch_step(amr_hydro_ctx *c, const StepParams &P, int grid);
 amr_status launch_step_raw(int prec, const StepParams &P, cudaStream_t stream);

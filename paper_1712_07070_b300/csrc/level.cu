@@ -124,11 +124,12 @@ amr_status amr_hydro_touch_level(amr_hydro_ctx *c, int level) {
 
 }  // extern "C"
 
-namespace {
+namespace amrh {
 
 // One step of a level (the body of amr_hydro_advance_level without the
-// retry of remedy (iv)).
-amr_status advance_once(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphysical_out) {
+// retry of remedy (iv)); acc_n: the gravity predictor's acceleration at t^n
+// (null: no gravity).
+amr_status advance_once(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphysical_out, const double *acc_n) {
     Level &L = c->lv[level];
     amr_status st;
     if (L.n_ghost) {  // coarse-fine ghosts need the level's time on the host
@@ -193,6 +194,10 @@ amr_status advance_once(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphy
         int lo, hi;
         scheme_stages(c->prm.scheme, c->prm.recon, c->prm.dual_energy, lo, hi);
         P.stage = lo;  // MUSCL-Hancock (PLM, PPM, dual energy) or CTU: the one launch
+        if (acc_n) {
+            P.stage = ST_MH_GRAV;
+            P.acc_n = acc_n;
+        }
     }
     if (c->prm.scheme == AMR_SCHEME_VL) {  // predictor into U*, then the corrector
         StepParams H = P;
@@ -235,7 +240,7 @@ amr_status advance_once(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphy
     return AMR_OK;
 }
 
-}  // namespace
+}  // namespace amrh
 
 extern "C" {
 
@@ -244,7 +249,7 @@ amr_status amr_hydro_advance_level(amr_hydro_ctx *c, int level, double dt, int64
     Level &L = c->lv[level];
     if (!L.n_patches) return AMR_E_INVAL;
     if (!(dt >= 0.0) && !(dt < 0.0)) return AMR_E_INVAL;  // NaN
-    if (!(c->prm.dt_min > 0.0)) return advance_once(c, level, dt, n_unphysical_out);
+    if (!(c->prm.dt_min > 0.0)) return advance_once(c, level, dt, n_unphysical_out, nullptr);
 
     // Remedies (iv)-(v) (section 2.2): while cells stay unphysical after the
     // per-cell remedies, recompute the whole level from U^n with dt x 0.8,
@@ -269,7 +274,7 @@ amr_status amr_hydro_advance_level(amr_hydro_ctx *c, int level, double dt, int64
     double step = dt;
     for (;;) {
         int64_t nb = 0;
-        st = advance_once(c, level, step, &nb);
+        st = advance_once(c, level, step, &nb, nullptr);
         if (st != AMR_E_UNPHYSICAL) {
             if (n_unphysical_out) *n_unphysical_out = st == AMR_OK ? 0 : nb;
             return st;

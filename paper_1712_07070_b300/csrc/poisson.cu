@@ -205,6 +205,38 @@ __global__ void __launch_bounds__(SOR_NT) k_sor_patches(
     }
 }
 
+// The corrector of the gravity coupling on every cell: momentum from the
+// accelerations at both ends of the step, then energy with the corrected
+// momentum.  U1: the predicted state (corrected in place), U0: U^n; dt from
+// the host or, when negative, the step's device time record.
+__global__ void k_grav_correct(double *__restrict__ U1, const double *__restrict__ U0,
+                               const double *__restrict__ g0, const double *__restrict__ g1, int64_t n_cells,
+                               double dt_in, const double *__restrict__ time_rec) {
+    const double dt = dt_in >= 0.0 ? dt_in : time_rec[0];
+    const double h = 0.5 * dt;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_cells;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = i / PV;
+        const int c = (int)(i % PV);
+        const double *u0 = U0 + s * PSLOT + c;
+        double *u1 = U1 + s * PSLOT + c;
+        double a0[3], a1[3], m1[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            a0[d] = g0[(s * 3 + d) * PV + c];
+            a1[d] = g1[(s * 3 + d) * PV + c];
+        }
+        const double r0 = u0[0], r1 = u1[0];
+#pragma unroll
+        for (int d = 0; d < 3; d++) m1[d] = u1[(1 + d) * PV] + h * (r0 * a0[d] + r1 * a1[d]);
+        const double e0 = u0[PV] * a0[0] + u0[2 * PV] * a0[1] + u0[3 * PV] * a0[2];
+        const double e1 = m1[0] * a1[0] + m1[1] * a1[1] + m1[2] * a1[2];
+        u1[4 * PV] = u1[4 * PV] + h * (e0 + e1);
+#pragma unroll
+        for (int d = 0; d < 3; d++) u1[(1 + d) * PV] = m1[d];
+    }
+}
+
 amr_status cufft_fail(cufftResult r, const char *where) {
     if (r == CUFFT_SUCCESS) return AMR_OK;
     std::fprintf(stderr, "amr_hydro: %s: cuFFT error %d\n", where, (int)r);
@@ -260,6 +292,30 @@ amr_status amr_hydro_poisson_root(amr_hydro_ctx *c, double G, double *phi, doubl
     if ((st = cufft_fail(cufftExecZ2D(b, F, c->fft_real.p), "Z2D"))) return st;
     k_root_out<<<grid, 256, 0, s>>>(c->fft_real.p, L.d_corner, L.n_patches, nx, ny, nz, dh, acc_order, phi, acc);
     return cuda_fail(cudaGetLastError(), "k_root_out");
+}
+
+amr_status amr_hydro_advance_gravity(amr_hydro_ctx *c, double dt, double G, const double *acc_n, double *phi_new,
+                                     double *acc_new, int acc_order) {
+    if (!c || !acc_n || !phi_new || !acc_new || (acc_order != 2 && acc_order != 4)) return AMR_E_INVAL;
+    if (!(dt >= 0.0) && !(dt < 0.0)) return AMR_E_INVAL;
+    if (c->prm.lmax > 0 && c->lv[1].n_patches) return AMR_E_INVAL;  // single-level grids
+    if (c->prm.scheme != AMR_SCHEME_MH || c->prm.recon != AMR_RECON_PLM || c->prm.dual_energy || c->prm.fallback ||
+        c->prm.dt_min > 0.0)
+        return AMR_E_INVAL;
+    Level &L = c->lv[0];
+    if (!L.n_patches || L.n_ghost) return AMR_E_INVAL;
+    amr_status st;
+    // predictor: the hydro step with gravity in the half step
+    if ((st = advance_once(c, 0, dt, nullptr, acc_n))) return st;
+    // the potential and acceleration of the predicted density
+    if ((st = amr_hydro_poisson_root(c, G, phi_new, acc_new, acc_order))) return st;
+    // corrector (the step flipped the buffers: U[cur] is the predicted state)
+    const int64_t n_cells = (int64_t)L.n_patches * PV;
+    k_grav_correct<<<c->n_sm * 8, 256, 0, c->stream>>>(L.U[L.cur], L.U[1 - L.cur], acc_n, acc_new, n_cells, dt,
+                                                        c->dtbuf.p);
+    if ((st = cuda_fail(cudaGetLastError(), "k_grav_correct"))) return st;
+    L.speed_valid = false;  // the step's fused signal speed was of the predicted state
+    return AMR_OK;
 }
 
 amr_status amr_hydro_poisson_level(amr_hydro_ctx *c, int level, double G, double omega, int iters,

@@ -47,7 +47,8 @@ constexpr int ST_CTU = 3;      // CTU step (ctu_kernel.cuh)
 constexpr int ST_MH_PPM = 4;   // MUSCL-Hancock step with PPM reconstruction
 constexpr int ST_CTU_PPM = 5;  // CTU step with PPM reconstruction
 constexpr int ST_MH_DE = 6;    // MUSCL-Hancock step with the dual-energy formalism
-constexpr int N_STAGES = 7;
+constexpr int ST_MH_GRAV = 7;  // MUSCL-Hancock predictor of the gravity coupling
+constexpr int N_STAGES = 8;
 __host__ __device__ constexpr bool stage_ppm(int st) { return st == ST_MH_PPM || st == ST_CTU_PPM; }
 __host__ __device__ constexpr bool stage_ctu(int st) { return st == ST_CTU || st == ST_CTU_PPM; }
 
@@ -120,6 +121,8 @@ struct StepParams {
     const double *__restrict__ S_old;
     double *__restrict__ S_new;
     double de_xi;
+    // gravity predictor (ST_MH_GRAV): the acceleration at t^n, [slot][3][8^3]
+    const double *__restrict__ acc_n;
     unsigned long long *smax_out;            // max signal speed of the new state (bits)
     unsigned long long *n_bad;               // count of unphysical new cells
     unsigned long long *clear2;              // two scalars the kernel zeroes for the next step
@@ -415,10 +418,13 @@ __device__ __forceinline__ void face_values(const SM &S, int X, int Y, int z, co
 // states alone (ST_VL_CORR), or the cell's conserved average on every face
 // (ST_VL_PRED).  uf[2d] / uf[2d+1]: conserved state on the low / high face along d.
 // With the dual-energy scalar (SM::DE), us[f]: s on face f, rho_f q_f with
-// PLM q, after the Hancock step with F_s = s v_n.
+// PLM q, after the Hancock step with F_s = s v_n.  The gravity predictor
+// (ST_MH_GRAV) adds (dt/2) (0, rho_f ga, m_f . ga) of each reconstructed face
+// state, ga the cell's acceleration at t^n (dt_half = dt/2).
 template <typename real, int STAGE, typename SM>
 __device__ __forceinline__ void hancock_cell(const SM &S, int x, int y, int z, real dtdh_half, const Gas<real> &g,
-                                             real uf[6][NV], real us[6]) {
+                                             real uf[6][NV], real us[6], const real ga[3] = nullptr,
+                                             real dt_half = real(0)) {
     using G = typename SM::Geo;
     const int X = x + G::OX, Y = y + G::OY;
     if constexpr (STAGE == ST_VL_PRED) {
@@ -457,7 +463,19 @@ __device__ __forceinline__ void hancock_cell(const SM &S, int x, int y, int z, r
                 for (int v = 0; v < NV; v++) inc[v] += fm[v] - fp[v];
             }
         }
-        if constexpr (hancock) {
+        if constexpr (STAGE == ST_MH_GRAV) {
+#pragma unroll
+            for (int f = 0; f < 6; f++) {
+                real src[NV];
+                src[0] = real(0);
+                src[1] = uf[f][0] * ga[0];
+                src[2] = uf[f][0] * ga[1];
+                src[3] = uf[f][0] * ga[2];
+                src[4] = uf[f][1] * ga[0] + uf[f][2] * ga[1] + uf[f][3] * ga[2];
+#pragma unroll
+                for (int v = 0; v < NV; v++) uf[f][v] = (uf[f][v] + dtdh_half * inc[v]) + dt_half * src[v];
+            }
+        } else if constexpr (hancock) {
 #pragma unroll
             for (int f = 0; f < 6; f++)
 #pragma unroll
@@ -468,6 +486,17 @@ __device__ __forceinline__ void hancock_cell(const SM &S, int x, int y, int z, r
             for (int f = 0; f < 6; f++) us[f] += dtdh_half * incs;
         }
     }
+}
+
+// The acceleration at t^n of tile cell (x, y, zl) of the group in table slot
+// ts (gravity predictor; single-level grids, so every position is a slot).
+template <typename real, typename SM>
+__device__ __forceinline__ void grav_at(const SM &S, const StepParams &P, int ts, int x, int y, int zl, real ga[3]) {
+    const int q = ((x + PS) >> 3) + 4 * ((y + PS) >> 3) + 16 * ((zl + PS) >> 3);
+    const int sl = S.nbr[ts][q];
+    const int off = ((zl + PS) & 7) * 64 + ((y + PS) & 7) * 8 + ((x + PS) & 7);
+#pragma unroll
+    for (int d = 0; d < 3; d++) ga[d] = sl >= 0 ? to_real<real>(__ldg(P.acc_n + ((int64_t)sl * 3 + d) * PV + off)) : real(0);
 }
 
 // Flux of the dual-energy scalar through a face: the mass flux F_rho times
@@ -691,9 +720,11 @@ __device__ __forceinline__ void step_run(SM &S, const StepParams &P, const int32
         // ---- B: Hancock states of plane z
         real zm[NV], zp[NV], fz[NV];
         real zms = real(0), zps = real(0);  // the scalar on the column cell's z faces
+        const real dt_half = (real)(0.5 * dt);
         {
-            real uf[6][NV], us[6];
-            hancock_cell<real, STAGE>(S, cx, cy, z, dtdh_half, g, uf, us);
+            real uf[6][NV], us[6], ga[3];
+            if constexpr (STAGE == ST_MH_GRAV) grav_at(S, P, kz & 1, cx, cy, zl, ga);
+            hancock_cell<real, STAGE>(S, cx, cy, z, dtdh_half, g, uf, us, ga, dt_half);
 #pragma unroll
             for (int v = 0; v < NV; v++) { zm[v] = uf[4][v]; zp[v] = uf[5][v]; }
             if constexpr (SM::DE) {
@@ -729,8 +760,9 @@ __device__ __forceinline__ void step_run(SM &S, const StepParams &P, const int32
             const int side = (tid >> 4) & 1;
             const int x = xring ? (side ? GE : -1) : r;
             const int y = xring ? r : (side ? GE : -1);
-            real uf[6][NV], us[6];
-            hancock_cell<real, STAGE>(S, x, y, z, dtdh_half, g, uf, us);
+            real uf[6][NV], us[6], ga[3];
+            if constexpr (STAGE == ST_MH_GRAV) grav_at(S, P, kz & 1, x, y, zl, ga);
+            hancock_cell<real, STAGE>(S, x, y, z, dtdh_half, g, uf, us, ga, dt_half);
             if (xring) {
 #pragma unroll
                 for (int v = 0; v < NV; v++) {

@@ -116,6 +116,32 @@ class UniformGrid:
             A.amr_hydro_unpack_uniform(tmp, nx, ny, nz, st, self.stream)
             return st[0].cpu().numpy()
 
+    def gravity(self, G, order=2):
+        """The FFT potential and acceleration of the current density:
+        ([n_patches][8][8][8], [n_patches][3][8][8][8]) device tensors."""
+        phi = torch.zeros((self.n_patches, 8, 8, 8), dtype=torch.float64, device=self.device)
+        acc = torch.zeros((self.n_patches, 3, 8, 8, 8), dtype=torch.float64, device=self.device)
+        A.amr_hydro_poisson_root(self.ctx, G, phi, acc, order)
+        return phi, acc
+
+    def step_gravity(self, G, acc_n, dt=-1.0, order=2):
+        """One hydro step coupled to self-gravity (predictor with acc_n, the
+        acceleration of the current state; the potential of the predicted
+        density; the corrector).  Returns (phi, acc) of the new state."""
+        phi = torch.zeros((self.n_patches, 8, 8, 8), dtype=torch.float64, device=self.device)
+        acc = torch.zeros((self.n_patches, 3, 8, 8, 8), dtype=torch.float64, device=self.device)
+        A.amr_hydro_advance_gravity(self.ctx, dt, G, acc_n, phi, acc, order)
+        return phi, acc
+
+    def to_dense(self, slots):
+        """Patch-slot arrays [n_patches][...][8][8][8] -> [...][nz][ny][nx] (numpy)."""
+        a = slots.cpu().numpy() if isinstance(slots, torch.Tensor) else slots
+        nx, ny, nz = self.shape
+        out = np.zeros(a.shape[1:-3] + (nz, ny, nx))
+        for s, (x, y, z) in enumerate(self.tables[0].cpu().numpy()):
+            out[..., z:z + 8, y:y + 8, x:x + 8] = a[s]
+        return out
+
     def min_dt(self):
         return A.amr_hydro_min_dt(self.ctx, 0)
 

@@ -91,3 +91,61 @@ def test_refined_levels_sor():
         phic = phi_l
     assert checked > 100
     H.close()
+
+
+def gravity_ics(n, seed):
+    """A self-gravitating box: the density blobs of the hydro tests (contrast
+    30, Mach 1.5) whose potential wells drive them inwards."""
+    return ics.blobs(n, seed=seed, contrast=30.0, mach=1.5)
+
+
+@pytest.mark.parametrize("prec,tol", [(A.AMR_FP64, 1e-12), (A.AMR_FP32, 1e-5)])
+@pytest.mark.parametrize("order", [2, 4])
+def test_coupled_gravity_step(prec, tol, order):
+    """Hydro + self-gravity steps (the gravity predictor in the MUSCL-Hancock
+    half step, the FFT potential of the predicted density, the corrector)
+    against the oracle's, state, potential and acceleration, with the CFL dt
+    taken on the device."""
+    from paper_1712_07070_b300.uniform import UniformGrid
+    n, G = 32, 2.0
+    U = gravity_ics(n, 5)
+    g = UniformGrid((n, n, n), prec=prec)
+    g.upload(U)
+    _, acc = g.gravity(G, order)
+    dh = 1.0 / n
+    gref = PS.accel_periodic(PS.poisson_root_periodic(U[0], dh, G), dh, order)
+    assert np.abs(g.to_dense(acc) - gref).max() <= 1e-11 * np.abs(gref).max()
+    import oracle
+    t = 0.0
+    for _ in range(3):
+        dt = oracle.dt_cfl2(U, G53, 0.5, dh)
+        # FP64: the device's own CFL dt; FP32: the oracle's (the FP32 speed differs in the last bits)
+        phi, acc = g.step_gravity(G, acc, -1.0 if prec == A.AMR_FP64 else dt, order)
+        U, phir, gref, nbad = PS.step_gravity(U, gref, dh, dt, G53, G, order)
+        assert nbad == 0
+        t += dt
+        assert g.time() == pytest.approx(t, rel=1e-12)
+        V = g.download()
+        scale = np.abs(U).reshape(5, -1).max(axis=1)
+        err = (np.abs(V - U).reshape(5, -1).max(axis=1) / scale).max()
+        assert err <= tol, err
+        if prec == A.AMR_FP32:  # continue from the GPU's own state
+            U = V
+            gref = PS.accel_periodic(PS.poisson_root_periodic(U[0], dh, G), dh, order)
+            g.upload(U)
+            _, acc = g.gravity(G, order)
+        else:
+            assert np.abs(g.to_dense(phi) - phir).max() <= 1e-12 * np.abs(phir).max()
+            assert np.abs(g.to_dense(acc) - gref).max() <= 1e-11 * np.abs(gref).max()
+    g.close()
+
+
+def test_coupled_gravity_rejects_other_schemes():
+    import torch
+    from paper_1712_07070_b300.uniform import UniformGrid
+    g = UniformGrid((16, 16, 16), scheme={"scheme": A.AMR_SCHEME_CTU})
+    g.upload(ics.blobs(16, seed=1))
+    acc = torch.zeros((g.n_patches, 3, 8, 8, 8), dtype=torch.float64, device="cuda")
+    with pytest.raises(A.AmrHydroError):
+        g.step_gravity(1.0, acc)
+    g.close()
