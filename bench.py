@@ -419,6 +419,20 @@ def bench_gravity(torch, args):
     out["root_fft"] = {"workload": "periodic FFT Poisson + 2-point accelerations, 256^3 root level (cuFFT)",
                        "ms": ms, "value": n ** 3 / (ms * 1e-3)}
     g.close()
+    for prec, tag in ((A.AMR_FP64, "fp64"), (A.AMR_FP32_ACC64, "fp32")):
+        g = UniformGrid((n, n, n), prec=prec)
+        g.upload(torch.from_numpy(ics.turbulence(n, seed=1)))
+        state = {"acc": g.gravity(1.0, 2)[1]}
+
+        def coupled():
+            state["acc"] = g.step_gravity(1.0, state["acc"], -1.0, 2)[1]
+
+        ms = timed(coupled, 5)
+        out[f"coupled_{tag}"] = {"workload": "hydro + self-gravity step (MUSCL-Hancock + PLM + HLLC with the "
+                                             "gravity predictor, FFT potential of the predicted density, "
+                                             f"corrector), 256^3 turbulence, {tag}", "ms": ms,
+                                 "value": n ** 3 / (ms * 1e-3)}
+        g.close()
     H = AmrHierarchy(ics.blobs(128, seed=3), lmax=2, theta=0.1, nbuf=(8, 4), max_patches=120000)
     phi0 = torch.zeros((H.n_patches(0), 8, 8, 8), dtype=torch.float64, device="cuda")
     A.amr_hydro_poisson_root(H.ctx, 1.0, phi0)

@@ -57,20 +57,50 @@ __global__ void k_rho_dense(const double *__restrict__ U, const int32_t *__restr
     }
 }
 
-// phi_k = 4 pi G dh^2 rho_k / (lambda_k N) (the inverse transform is unnormalised)
-__global__ void k_green(cufftDoubleComplex *F, int nx, int ny, int nz, double scale) {
+// The per-axis parts of the eigenvalues, lam1[k] = -2 (1 - cos(2 pi k / N)),
+// for x (nx/2+1 entries), then y (ny), then z (nz).
+__global__ void k_green_axes(double *__restrict__ lam1, int nx, int ny, int nz) {
     const int nxh = nx / 2 + 1;
-    const int64_t n = (int64_t)nz * ny * nxh;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int kx = (int)(i % nxh), ky = (int)((i / nxh) % ny), kz = (int)(i / ((int64_t)nxh * ny));
-        const double lam = -2.0 * ((1.0 - cos(2.0 * PI * kx / nx)) + (1.0 - cos(2.0 * PI * ky / ny)) +
-                                   (1.0 - cos(2.0 * PI * kz / nz)));
-        if (i == 0) {
-            F[i].x = 0.0;
-            F[i].y = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nxh + ny + nz; i += gridDim.x * blockDim.x) {
+        int k, n;
+        if (i < nxh) {
+            k = i;
+            n = nx;
+        } else if (i < nxh + ny) {
+            k = i - nxh;
+            n = ny;
         } else {
-            F[i].x = F[i].x / lam * scale;
-            F[i].y = F[i].y / lam * scale;
+            k = i - nxh - ny;
+            n = nz;
+        }
+        lam1[i] = -2.0 * (1.0 - cos(2.0 * PI * k / n));
+    }
+}
+
+// phi_k = 4 pi G dh^2 rho_k / (lambda_k N) (the inverse transform is
+// unnormalised), lambda_k = lam1x + lam1y + lam1z; one warp per (ky, kz) row.
+__global__ void k_green(cufftDoubleComplex *__restrict__ F, const double *__restrict__ lam1, int nx, int ny, int nz,
+                        double scale) {
+    const int nxh = nx / 2 + 1;
+    const int lane = threadIdx.x & 31;
+    const int64_t n_rows = (int64_t)ny * nz;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t row = warp0; row < n_rows; row += n_warps) {
+        const int ky = (int)(row % ny), kz = (int)(row / ny);
+        const double lyz = lam1[nxh + ky] + lam1[nxh + ny + kz];
+        cufftDoubleComplex *Fr = F + row * nxh;
+        for (int kx = lane; kx < nxh; kx += 32) {
+            cufftDoubleComplex v = Fr[kx];
+            if (row == 0 && kx == 0) {
+                v.x = 0.0;
+                v.y = 0.0;
+            } else {
+                const double f = scale / (lam1[kx] + lyz);
+                v.x *= f;
+                v.y *= f;
+            }
+            Fr[kx] = v;
         }
     }
 }
@@ -79,17 +109,16 @@ __global__ void k_green(cufftDoubleComplex *F, int nx, int ny, int nz, double sc
 __global__ void k_root_out(const double *__restrict__ phi, const int32_t *__restrict__ corner, int n_patches, int nx,
                            int ny, int nz, double dh, int order, double *__restrict__ phi_out,
                            double *__restrict__ acc_out) {
+    const double inv2 = 0.5 / dh, inv12 = 1.0 / (12.0 * dh);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)n_patches * PV;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = i / PV;
         const int c = (int)(i % PV);
         const int x = corner[3 * s] + (c & 7), y = corner[3 * s + 1] + ((c >> 3) & 7),
                   z = corner[3 * s + 2] + (c >> 6);
+        auto wrap = [](int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); };  // |offset| <= 2 < n
         auto at = [&](int a, int b, int d) {
-            a = (a + nx) % nx;
-            b = (b + ny) % ny;
-            d = (d + nz) % nz;
-            return phi[((int64_t)d * ny + b) * nx + a];
+            return phi[((int64_t)wrap(d, nz) * ny + wrap(b, ny)) * nx + wrap(a, nx)];
         };
         phi_out[s * PV + c] = at(x, y, z);
         if (!acc_out) continue;
@@ -97,11 +126,11 @@ __global__ void k_root_out(const double *__restrict__ phi, const int32_t *__rest
             const int ex = d == 0, ey = d == 1, ez = d == 2;
             double g;
             if (order == 2) {
-                g = (at(x + ex, y + ey, z + ez) - at(x - ex, y - ey, z - ez)) / (2.0 * dh);
+                g = (at(x + ex, y + ey, z + ez) - at(x - ex, y - ey, z - ez)) * inv2;
             } else {
                 g = (-at(x + 2 * ex, y + 2 * ey, z + 2 * ez) + 8.0 * at(x + ex, y + ey, z + ez) -
-                     8.0 * at(x - ex, y - ey, z - ez) + at(x - 2 * ex, y - 2 * ey, z - 2 * ez)) /
-                    (12.0 * dh);
+                     8.0 * at(x - ex, y - ey, z - ez) + at(x - 2 * ex, y - 2 * ey, z - 2 * ez)) *
+                    inv12;
             }
             acc_out[(s * 3 + d) * PV + c] = -g;
         }
@@ -139,6 +168,8 @@ __global__ void __launch_bounds__(SOR_NT) k_sor_patches(
     double *rho_flat = &S.rho[0][0][0], *phi_flat = &S.phi[0][0][0];
     const int tid = threadIdx.x;
     const double src_scale = dh * dh * FOUR_PI * G;
+    const double w6 = omega / 6.0;  // a multiply instead of an FP64 division per point update
+    const double inv2 = 0.5 / dh, inv12 = 1.0 / (12.0 * dh);
     for (int p = blockIdx.x; p < n_patches; p += gridDim.x) {
         if (tid < 27) {
             const int P = parent[p];
@@ -148,25 +179,40 @@ __global__ void __launch_bounds__(SOR_NT) k_sor_patches(
             if (tid < 3) S.off[tid] = corner[3 * p + tid] / 2 - ccorner[3 * P + tid];
         }
         __syncthreads();
-        // density and initial guess on the 18^3 grid
+        // initial guess on the 18^3 grid: quadratic interpolation along x, then
+        // y, then z, each pass once per distinct value (coarse rows -4..7
+        // around the patch in y and z: 12 x 12 x 18 along x into the phi
+        // array, 12 x 18 x 18 along y into the rho array, then all cells)
+        constexpr int NC = 12;
+        for (int i = tid; i < NC * NC * PN; i += SOR_NT) {
+            const int fx = i % PN, b = (i / PN) % NC, a = i / (PN * NC);
+            const int gx = fx - PB, cx = S.off[0] + (gx >> 1);
+            const int cy = S.off[1] + b - 4, cz = S.off[2] + a - 4;
+            phi_flat[i] = quad1(coarse_at(phic, PV, S.cnb, cx - 1, cy, cz), coarse_at(phic, PV, S.cnb, cx, cy, cz),
+                                coarse_at(phic, PV, S.cnb, cx + 1, cy, cz), (gx & 1) ? 0.25 : -0.25);
+        }
+        __syncthreads();
+        for (int i = tid; i < NC * PN * PN; i += SOR_NT) {
+            const int fx = i % PN, fy = (i / PN) % PN, a = i / (PN * PN);
+            const int gy = fy - PB, b = (gy >> 1) + 4;
+            const double *X = phi_flat + (a * NC + b) * PN + fx;
+            rho_flat[i] = quad1(X[-PN], X[0], X[PN], (gy & 1) ? 0.25 : -0.25);
+        }
+        __syncthreads();
+        for (int i = tid; i < PN3; i += SOR_NT) {
+            const int gz = i / (PN * PN) - PB, a = (gz >> 1) + 4;
+            const double *Y = rho_flat + a * PN * PN + i % (PN * PN);
+            phi_flat[i] = quad1(Y[-PN * PN], Y[0], Y[PN * PN], (gz & 1) ? 0.25 : -0.25);
+        }
+        __syncthreads();
+        // the source term dh^2 4 pi G rho on the grid, formed once per cell
         for (int i = tid; i < PN3; i += SOR_NT) {
             const int gx = i % PN - PB, gy = (i / PN) % PN - PB, gz = i / (PN * PN) - PB;  // fine, relative
             const int k = ((gx >> 3) + 1) + 3 * ((gy >> 3) + 1) + 9 * ((gz >> 3) + 1);
-            const int cx = S.off[0] + (gx >> 1), cy = S.off[1] + (gy >> 1), cz = S.off[2] + (gz >> 1);
             const int s = S.nb[k];
-            rho_flat[i] = s >= 0 ? U[(int64_t)s * PSLOT + (gz & 7) * 64 + (gy & 7) * 8 + (gx & 7)]
-                                 : coarse_at(Uc, PSLOT, S.cnb, cx, cy, cz);
-            const double ox = (gx & 1) ? 0.25 : -0.25, oy = (gy & 1) ? 0.25 : -0.25, oz = (gz & 1) ? 0.25 : -0.25;
-            double Y[3];
-            for (int dz = -1; dz <= 1; dz++) {
-                double X[3];
-                for (int dy = -1; dy <= 1; dy++)
-                    X[dy + 1] = quad1(coarse_at(phic, PV, S.cnb, cx - 1, cy + dy, cz + dz),
-                                      coarse_at(phic, PV, S.cnb, cx, cy + dy, cz + dz),
-                                      coarse_at(phic, PV, S.cnb, cx + 1, cy + dy, cz + dz), ox);
-                Y[dz + 1] = quad1(X[0], X[1], X[2], oy);
-            }
-            phi_flat[i] = quad1(Y[0], Y[1], Y[2], oz);
+            rho_flat[i] = src_scale * (s >= 0 ? U[(int64_t)s * PSLOT + (gz & 7) * 64 + (gy & 7) * 8 + (gx & 7)]
+                                              : coarse_at(Uc, PSLOT, S.cnb, S.off[0] + (gx >> 1),
+                                                          S.off[1] + (gy >> 1), S.off[2] + (gz >> 1)));
         }
         __syncthreads();
         // red-black SOR on the interior 16^3 cells
@@ -178,7 +224,7 @@ __global__ void __launch_bounds__(SOR_NT) k_sor_patches(
                     const double ph = S.phi[k][j][i];
                     const double nbs = S.phi[k - 1][j][i] + S.phi[k + 1][j][i] + S.phi[k][j - 1][i] +
                                        S.phi[k][j + 1][i] + S.phi[k][j][i - 1] + S.phi[k][j][i + 1];
-                    S.phi[k][j][i] = ph + omega * (nbs - 6.0 * ph - src_scale * S.rho[k][j][i]) / 6.0;
+                    S.phi[k][j][i] = ph + w6 * (nbs - 6.0 * ph - S.rho[k][j][i]);
                 }
                 __syncthreads();
             }
@@ -192,11 +238,11 @@ __global__ void __launch_bounds__(SOR_NT) k_sor_patches(
                 const int ex = d == 0, ey = d == 1, ez = d == 2;
                 double g;
                 if (order == 2) {
-                    g = (S.phi[z + ez][y + ey][x + ex] - S.phi[z - ez][y - ey][x - ex]) / (2.0 * dh);
+                    g = (S.phi[z + ez][y + ey][x + ex] - S.phi[z - ez][y - ey][x - ex]) * inv2;
                 } else {
                     g = (-S.phi[z + 2 * ez][y + 2 * ey][x + 2 * ex] + 8.0 * S.phi[z + ez][y + ey][x + ex] -
-                         8.0 * S.phi[z - ez][y - ey][x - ex] + S.phi[z - 2 * ez][y - 2 * ey][x - 2 * ex]) /
-                        (12.0 * dh);
+                         8.0 * S.phi[z - ez][y - ey][x - ex] + S.phi[z - 2 * ez][y - 2 * ey][x - 2 * ex]) *
+                        inv12;
                 }
                 acc_out[((int64_t)p * 3 + d) * PV + c] = -g;
             }
@@ -208,12 +254,22 @@ __global__ void __launch_bounds__(SOR_NT) k_sor_patches(
 // The corrector of the gravity coupling on every cell: momentum from the
 // accelerations at both ends of the step, then energy with the corrected
 // momentum.  U1: the predicted state (corrected in place), U0: U^n; dt from
-// the host or, when negative, the step's device time record.
+// the host or, when negative, the step's device time record.  Fused: the CFL
+// signal speed of the corrected state (as the max-speed pass, in the step's
+// precision) into smax / n_bad.
+template <typename real>
 __global__ void k_grav_correct(double *__restrict__ U1, const double *__restrict__ U0,
                                const double *__restrict__ g0, const double *__restrict__ g1, int64_t n_cells,
-                               double dt_in, const double *__restrict__ time_rec) {
+                               double dt_in, const double *__restrict__ time_rec, double gamma,
+                               unsigned long long *smax, unsigned long long *n_bad) {
     const double dt = dt_in >= 0.0 ? dt_in : time_rec[0];
     const double h = 0.5 * dt;
+    Gas<real> gas;
+    gas.gamma = (real)gamma;
+    gas.gm1 = (real)(gamma - 1.0);
+    gas.inv_gm1 = (real)(1.0 / (gamma - 1.0));
+    double m = 0.0;
+    unsigned bad = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_cells;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = i / PV;
@@ -231,9 +287,25 @@ __global__ void k_grav_correct(double *__restrict__ U1, const double *__restrict
         for (int d = 0; d < 3; d++) m1[d] = u1[(1 + d) * PV] + h * (r0 * a0[d] + r1 * a1[d]);
         const double e0 = u0[PV] * a0[0] + u0[2 * PV] * a0[1] + u0[3 * PV] * a0[2];
         const double e1 = m1[0] * a1[0] + m1[1] * a1[1] + m1[2] * a1[2];
-        u1[4 * PV] = u1[4 * PV] + h * (e0 + e1);
+        const double E1 = u1[4 * PV] + h * (e0 + e1);
+        u1[4 * PV] = E1;
 #pragma unroll
         for (int d = 0; d < 3; d++) u1[(1 + d) * PV] = m1[d];
+        real u[NV] = {to_real<real>(r1), to_real<real>(m1[0]), to_real<real>(m1[1]), to_real<real>(m1[2]),
+                      to_real<real>(E1)};
+        bool ok;
+        const real sp = cfl_speed(u, gas, ok, false);
+        if (!ok) bad++;
+        else if ((double)sp > m) m = (double)sp;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(smax, (unsigned long long)__double_as_longlong(m));
+        if (bad) atomicAdd(n_bad, (unsigned long long)bad);
     }
 }
 
@@ -266,7 +338,8 @@ amr_status amr_hydro_poisson_root(amr_hydro_ctx *c, double G, double *phi, doubl
     if ((int64_t)L.n_patches * PV != (int64_t)nx * ny * nz) return AMR_E_INVAL;  // the whole root grid
     const int64_t n = (int64_t)nx * ny * nz, nc = (int64_t)nz * ny * (nx / 2 + 1);
     amr_status st;
-    if ((st = c->fft_real.reserve(n)) || (st = c->fft_cplx.reserve(2 * nc))) return st;
+    // the complex spectrum, then the per-axis eigenvalue tables
+    if ((st = c->fft_real.reserve(n)) || (st = c->fft_cplx.reserve(2 * nc + nx / 2 + 1 + ny + nz))) return st;
     if (!c->fft_plan[0]) {
         cufftHandle f, b;
         if ((st = cufft_fail(cufftPlan3d(&f, nz, ny, nx, CUFFT_D2Z), "plan"))) return st;
@@ -287,7 +360,10 @@ amr_status amr_hydro_poisson_root(amr_hydro_ctx *c, double G, double *phi, doubl
     if ((st = cuda_fail(cudaGetLastError(), "k_rho_dense"))) return st;
     cufftDoubleComplex *F = (cufftDoubleComplex *)c->fft_cplx.p;
     if ((st = cufft_fail(cufftExecD2Z(f, c->fft_real.p, F), "D2Z"))) return st;
-    k_green<<<grid, 256, 0, s>>>(F, nx, ny, nz, FOUR_PI * G * dh * dh / (double)n);
+    double *lam1 = c->fft_cplx.p + 2 * nc;
+    k_green_axes<<<(nx / 2 + 1 + ny + nz + 255) / 256, 256, 0, s>>>(lam1, nx, ny, nz);
+    if ((st = cuda_fail(cudaGetLastError(), "k_green_axes"))) return st;
+    k_green<<<grid, 256, 0, s>>>(F, lam1, nx, ny, nz, FOUR_PI * G * dh * dh / (double)n);
     if ((st = cuda_fail(cudaGetLastError(), "k_green"))) return st;
     if ((st = cufft_fail(cufftExecZ2D(b, F, c->fft_real.p), "Z2D"))) return st;
     k_root_out<<<grid, 256, 0, s>>>(c->fft_real.p, L.d_corner, L.n_patches, nx, ny, nz, dh, acc_order, phi, acc);
@@ -309,12 +385,21 @@ amr_status amr_hydro_advance_gravity(amr_hydro_ctx *c, double dt, double G, cons
     if ((st = advance_once(c, 0, dt, nullptr, acc_n))) return st;
     // the potential and acceleration of the predicted density
     if ((st = amr_hydro_poisson_root(c, G, phi_new, acc_new, acc_order))) return st;
-    // corrector (the step flipped the buffers: U[cur] is the predicted state)
+    // corrector (the step flipped the buffers: U[cur] is the predicted state);
+    // its fused signal speed replaces the step's, which was of the predicted state
+    unsigned long long *sm = c->scal.p + L.scal0 + L.ring, *nb = c->scal.p + L.scal0 + 3 + L.ring;
+    if ((st = cuda_fail(cudaMemsetAsync(sm, 0, 8, c->stream), "memset")) ||
+        (st = cuda_fail(cudaMemsetAsync(nb, 0, 8, c->stream), "memset")))
+        return st;
     const int64_t n_cells = (int64_t)L.n_patches * PV;
-    k_grav_correct<<<c->n_sm * 8, 256, 0, c->stream>>>(L.U[L.cur], L.U[1 - L.cur], acc_n, acc_new, n_cells, dt,
-                                                        c->dtbuf.p);
+    if (c->prm.prec == AMR_FP64)
+        k_grav_correct<double><<<c->n_sm * 8, 256, 0, c->stream>>>(L.U[L.cur], L.U[1 - L.cur], acc_n, acc_new,
+                                                                    n_cells, dt, c->dtbuf.p, c->prm.gamma, sm, nb);
+    else
+        k_grav_correct<float><<<c->n_sm * 8, 256, 0, c->stream>>>(L.U[L.cur], L.U[1 - L.cur], acc_n, acc_new,
+                                                                   n_cells, dt, c->dtbuf.p, c->prm.gamma, sm, nb);
     if ((st = cuda_fail(cudaGetLastError(), "k_grav_correct"))) return st;
-    L.speed_valid = false;  // the step's fused signal speed was of the predicted state
+    L.speed_valid = true;
     return AMR_OK;
 }
 

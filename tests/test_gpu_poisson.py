@@ -99,7 +99,7 @@ def gravity_ics(n, seed):
     return ics.blobs(n, seed=seed, contrast=30.0, mach=1.5)
 
 
-@pytest.mark.parametrize("prec,tol", [(A.AMR_FP64, 1e-12), (A.AMR_FP32, 1e-5)])
+@pytest.mark.parametrize("prec,tol", [(A.AMR_FP64, 1e-12), (A.AMR_FP32_ACC64, 1e-5)])
 @pytest.mark.parametrize("order", [2, 4])
 def test_coupled_gravity_step(prec, tol, order):
     """Hydro + self-gravity steps (the gravity predictor in the MUSCL-Hancock
@@ -129,7 +129,7 @@ def test_coupled_gravity_step(prec, tol, order):
         scale = np.abs(U).reshape(5, -1).max(axis=1)
         err = (np.abs(V - U).reshape(5, -1).max(axis=1) / scale).max()
         assert err <= tol, err
-        if prec == A.AMR_FP32:  # continue from the GPU's own state
+        if prec == A.AMR_FP32_ACC64:  # continue from the GPU's own state
             U = V
             gref = PS.accel_periodic(PS.poisson_root_periodic(U[0], dh, G), dh, order)
             g.upload(U)
