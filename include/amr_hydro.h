@@ -380,12 +380,15 @@ amr_status amr_hydro_poisson_level(amr_hydro_ctx *ctx, int level, double G, doub
  * acc_new of the predicted density (as amr_hydro_poisson_root); then
  * m^{n+1} = m* + (dt/2)(rho^n g^n + rho^{n+1} g^{n+1}) and
  * E^{n+1} = E* + (dt/2)(m^n.g^n + m^{n+1}.g^{n+1}).  acc_new is the next
- * step's acc_n.  dt < 0: the device's Eq. (CFL2) dt.  MUSCL-Hancock + PLM
+ * step's acc_n.  dt < 0: the device's Eq. (CFL2) dt, and with c_acc > 0 the
+ * smaller of it and Eq. (acc), c_acc (dh / max|a|)^(1/2) over acc_n's values
+ * (c_acc = 0: Eq. (CFL2) alone; negative or non-finite: AMR_E_INVAL).
+ * MUSCL-Hancock + PLM
  * without dual energy, the remedies or the level retry; AMR_E_INVAL otherwise or with
  * refined levels.  Asynchronous on the context's stream.
  */
 amr_status amr_hydro_advance_gravity(amr_hydro_ctx *ctx, double dt, double G, const double *acc_n, double *phi_new,
-                                     double *acc_new, int acc_order);
+                                     double *acc_new, int acc_order, double c_acc);
 
 /*
  * Discrete adjoint of one uniform periodic MUSCL-Hancock step of size dt (no

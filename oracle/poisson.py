@@ -158,6 +158,11 @@ def accel_periodic(phi, dh, order=2):
     return accel(np.pad(phi, h, mode="wrap"), dh, order)
 
 
+def dt_acc(g, dh, c_acc):
+    """Eq. (acc): C_acc (dh / max over cells of max(|a_x|, |a_y|, |a_z|))^(1/2)."""
+    return c_acc * np.sqrt(dh / np.abs(g).max())
+
+
 def step_gravity(U, g_n, dh, dt, gamma, G, order=2):
     """One coupled hydro + self-gravity step on a periodic root grid
     (section 2.3, after Muller & Steinmetz 1995): the predictor (the

@@ -74,7 +74,8 @@ def lib():
         "amr_hydro_touch_level": [_vp, ctypes.c_int],
         "amr_hydro_set_entropy": [_vp, ctypes.c_int, _vp, _vp],
         "amr_hydro_poisson_root": [_vp, ctypes.c_double, _vp, _vp, ctypes.c_int],
-        "amr_hydro_advance_gravity": [_vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp, ctypes.c_int],
+        "amr_hydro_advance_gravity": [_vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp, ctypes.c_int,
+                                      ctypes.c_double],
         "amr_hydro_poisson_level": [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp, _vp,
                                     _vp, ctypes.c_int],
         "amr_hydro_fill_ghost": [_vp, ctypes.c_int, ctypes.c_double],
@@ -183,8 +184,8 @@ def amr_hydro_poisson_root(ctx, G, phi, acc=None, acc_order=2):
     check(lib().amr_hydro_poisson_root(ctx, G, _p(phi), _p(acc), acc_order), "amr_hydro_poisson_root")
 
 
-def amr_hydro_advance_gravity(ctx, dt, G, acc_n, phi_new, acc_new, acc_order=2):
-    check(lib().amr_hydro_advance_gravity(ctx, dt, G, _p(acc_n), _p(phi_new), _p(acc_new), acc_order),
+def amr_hydro_advance_gravity(ctx, dt, G, acc_n, phi_new, acc_new, acc_order=2, c_acc=0.0):
+    check(lib().amr_hydro_advance_gravity(ctx, dt, G, _p(acc_n), _p(phi_new), _p(acc_new), acc_order, c_acc),
           "amr_hydro_advance_gravity")
 
 

@@ -160,7 +160,12 @@ amr_status level_speed(amr_hydro_ctx *c, int level);
 size_t step_smem_bytes(int prec);
 void scheme_stages(int scheme, int recon, int dual_energy, int &lo, int &hi);
 void release_poisson(amr_hydro_ctx *c);
-amr_status advance_once(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphysical_out, const double *acc_n);
+amr_status advance_once(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphysical_out, const double *acc_n,
+                        double c_acc = 0.0);
+// Eq. (acc) as a signal speed: max over acc's values of (cfl / c_acc) sqrt(dh |a|)
+// into *smax, so that cfl dh / *smax is the smaller of the two time steps.
+amr_status launch_acc_speed(amr_hydro_ctx *c, const double *acc, int64_t n_values, double dh, double c_acc,
+                            unsigned long long *smax);
 struct StepParams;
 amr_status launch_step(amr_hydro_ctx *c, const StepParams &P, int grid);
 amr_status launch_step_raw(int prec, const StepParams &P, cudaStream_t stream);

@@ -128,8 +128,9 @@ namespace amrh {
 
 // One step of a level (the body of amr_hydro_advance_level without the
 // retry of remedy (iv)); acc_n: the gravity predictor's acceleration at t^n
-// (null: no gravity).
-amr_status advance_once(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphysical_out, const double *acc_n) {
+// (null: no gravity); c_acc > 0 with dt < 0: dt also obeys Eq. (acc) on acc_n.
+amr_status advance_once(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphysical_out, const double *acc_n,
+                        double c_acc) {
     Level &L = c->lv[level];
     amr_status st;
     if (L.n_ghost) {  // coarse-fine ghosts need the level's time on the host
@@ -137,6 +138,10 @@ amr_status advance_once(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphy
         if ((st = fill_ghost_impl(c, level, L.t))) return st;
     }
     if (dt < 0.0 && (st = level_speed(c, level))) return st;
+    if (dt < 0.0 && acc_n && c_acc > 0.0 &&  // Eq. (acc) joins Eq. (CFL2)
+        (st = launch_acc_speed(c, acc_n, (int64_t)L.n_patches * 3 * PV, level_dh(c, level), c_acc,
+                               c->scal.p + L.scal0 + L.ring)))
+        return st;
     unsigned long long *sc = c->scal.p + L.scal0;
     const int r_in = L.ring, r_out = (L.ring + 1) % 3, r_clr = (L.ring + 2) % 3;
 

@@ -309,6 +309,18 @@ __global__ void k_grav_correct(double *__restrict__ U1, const double *__restrict
     }
 }
 
+// max over the values of (cfl / c_acc) sqrt(dh |a|): warp maxima, one atomic each
+__global__ void k_acc_speed(const double *__restrict__ acc, int64_t n, double dh, double scale,
+                            unsigned long long *smax) {
+    double m = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(acc[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0)
+        atomicMax(smax, (unsigned long long)__double_as_longlong(scale * sqrt(dh * m)));
+}
+
 amr_status cufft_fail(cufftResult r, const char *where) {
     if (r == CUFFT_SUCCESS) return AMR_OK;
     std::fprintf(stderr, "amr_hydro: %s: cuFFT error %d\n", where, (int)r);
@@ -316,6 +328,12 @@ amr_status cufft_fail(cufftResult r, const char *where) {
 }
 
 }  // namespace
+
+amr_status launch_acc_speed(amr_hydro_ctx *c, const double *acc, int64_t n_values, double dh, double c_acc,
+                            unsigned long long *smax) {
+    k_acc_speed<<<c->n_sm * 8, 256, 0, c->stream>>>(acc, n_values, dh, c->prm.cfl / c_acc, smax);
+    return cuda_fail(cudaGetLastError(), "k_acc_speed");
+}
 
 void release_poisson(amr_hydro_ctx *c) {
     if (c->fft_plan[0]) cufftDestroy((cufftHandle)c->fft_plan[0]);
@@ -371,8 +389,9 @@ amr_status amr_hydro_poisson_root(amr_hydro_ctx *c, double G, double *phi, doubl
 }
 
 amr_status amr_hydro_advance_gravity(amr_hydro_ctx *c, double dt, double G, const double *acc_n, double *phi_new,
-                                     double *acc_new, int acc_order) {
+                                     double *acc_new, int acc_order, double c_acc) {
     if (!c || !acc_n || !phi_new || !acc_new || (acc_order != 2 && acc_order != 4)) return AMR_E_INVAL;
+    if (!(c_acc >= 0.0) || c_acc > 1e300) return AMR_E_INVAL;
     if (!(dt >= 0.0) && !(dt < 0.0)) return AMR_E_INVAL;
     if (c->prm.lmax > 0 && c->lv[1].n_patches) return AMR_E_INVAL;  // single-level grids
     if (c->prm.scheme != AMR_SCHEME_MH || c->prm.recon != AMR_RECON_PLM || c->prm.dual_energy || c->prm.fallback ||
@@ -382,7 +401,7 @@ amr_status amr_hydro_advance_gravity(amr_hydro_ctx *c, double dt, double G, cons
     if (!L.n_patches || L.n_ghost) return AMR_E_INVAL;
     amr_status st;
     // predictor: the hydro step with gravity in the half step
-    if ((st = advance_once(c, 0, dt, nullptr, acc_n))) return st;
+    if ((st = advance_once(c, 0, dt, nullptr, acc_n, c_acc))) return st;
     // the potential and acceleration of the predicted density
     if ((st = amr_hydro_poisson_root(c, G, phi_new, acc_new, acc_order))) return st;
     // corrector (the step flipped the buffers: U[cur] is the predicted state);

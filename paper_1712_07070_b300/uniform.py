@@ -124,13 +124,14 @@ class UniformGrid:
         A.amr_hydro_poisson_root(self.ctx, G, phi, acc, order)
         return phi, acc
 
-    def step_gravity(self, G, acc_n, dt=-1.0, order=2):
+    def step_gravity(self, G, acc_n, dt=-1.0, order=2, c_acc=0.0):
         """One hydro step coupled to self-gravity (predictor with acc_n, the
         acceleration of the current state; the potential of the predicted
-        density; the corrector).  Returns (phi, acc) of the new state."""
+        density; the corrector); dt < 0 with c_acc > 0 also obeys Eq. (acc).
+        Returns (phi, acc) of the new state."""
         phi = torch.zeros((self.n_patches, 8, 8, 8), dtype=torch.float64, device=self.device)
         acc = torch.zeros((self.n_patches, 3, 8, 8, 8), dtype=torch.float64, device=self.device)
-        A.amr_hydro_advance_gravity(self.ctx, dt, G, acc_n, phi, acc, order)
+        A.amr_hydro_advance_gravity(self.ctx, dt, G, acc_n, phi, acc, order, c_acc)
         return phi, acc
 
     def to_dense(self, slots):

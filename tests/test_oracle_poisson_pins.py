@@ -182,3 +182,18 @@ def test_jeans_oscillation_converges():
     e = [jeans_amplitude_error(n) for n in (16, 32, 64)]
     assert e[1] < e[0] and np.log2(e[1] / e[2]) >= 1.7, e
     assert e[2] < 2.5e-3, e  # measured 2.0e-3
+
+
+def test_acceleration_time_step_closed_form():
+    """Eq. (acc) on the two-point acceleration of phi = A cos(k y): the
+    discrete g_y = A sin(k dh) sin(k y_j) / dh peaks at the cell centres
+    nearest the quarter period, |sin| = cos(pi / n) for n a multiple of 4;
+    the other components vanish."""
+    n, A, c = 32, -0.7, 0.4
+    dh = 1.0 / n
+    y = (np.arange(n) + 0.5) * dh
+    phi = np.broadcast_to((A * np.cos(2 * np.pi * y))[None, :, None], (8, n, 16)).copy()
+    g = PS.accel_periodic(phi, dh, 2)
+    gmax = abs(A) * np.sin(2 * np.pi * dh) * np.cos(np.pi / n) / dh
+    assert np.abs(g[0]).max() == 0 and np.abs(g[2]).max() == 0
+    assert PS.dt_acc(g, dh, c) == pytest.approx(c * np.sqrt(dh / gmax), rel=1e-14)
