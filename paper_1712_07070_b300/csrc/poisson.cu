@@ -44,16 +44,49 @@ constexpr int SOR_NT = 256;
 
 // ---- root level ------------------------------------------------------------------
 
-// rho (variable 0 of the level's current state) into a dense [nz][ny][nx] array
-__global__ void k_rho_dense(const double *__restrict__ U, const int32_t *__restrict__ corner, int n_patches, int nx,
-                            int ny, double *__restrict__ out) {
+// Deterministic sum of a block's values (256 threads): fixed shuffle pattern,
+// then the 8 warp sums in order.
+__device__ __forceinline__ double block_sum(double v, double *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+    return t;
+}
+
+// per-block partial sums of rho over the level (the mean of the source term)
+__global__ void __launch_bounds__(256) k_rho_partial(const double *__restrict__ U, int n_patches,
+                                                     double *__restrict__ partial) {
+    __shared__ double red[8];
+    double m = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)n_patches * PV;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m += U[(i / PV) * PSLOT + i % PV];
+    m = block_sum(m, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = m;
+}
+
+// rho - <rho> (variable 0 of the level's current state) into a dense
+// [nz][ny][nx] array of the transform's precision T; every block forms the
+// same mean from the partial sums
+template <typename T>
+__global__ void __launch_bounds__(256) k_rho_dense(const double *__restrict__ U, const int32_t *__restrict__ corner,
+                                                   int n_patches, int nx, int ny, const double *__restrict__ partial,
+                                                   int n_partial, T *__restrict__ out) {
+    __shared__ double red[8];
+    double m = 0.0;
+    for (int k = threadIdx.x; k < n_partial; k += blockDim.x) m += partial[k];
+    const double mean = block_sum(m, red) / ((double)n_patches * PV);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)n_patches * PV;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = i / PV;
         const int c = (int)(i % PV);
         const int x = corner[3 * s] + (c & 7), y = corner[3 * s + 1] + ((c >> 3) & 7),
                   z = corner[3 * s + 2] + (c >> 6);
-        out[((int64_t)z * ny + y) * nx + x] = U[s * PSLOT + c];
+        out[((int64_t)z * ny + y) * nx + x] = (T)(U[s * PSLOT + c] - mean);
     }
 }
 
@@ -79,8 +112,8 @@ __global__ void k_green_axes(double *__restrict__ lam1, int nx, int ny, int nz) 
 
 // phi_k = 4 pi G dh^2 rho_k / (lambda_k N) (the inverse transform is
 // unnormalised), lambda_k = lam1x + lam1y + lam1z; one warp per (ky, kz) row.
-__global__ void k_green(cufftDoubleComplex *__restrict__ F, const double *__restrict__ lam1, int nx, int ny, int nz,
-                        double scale) {
+template <typename C>  // cufftDoubleComplex or cufftComplex
+__global__ void k_green(C *__restrict__ F, const double *__restrict__ lam1, int nx, int ny, int nz, double scale) {
     const int nxh = nx / 2 + 1;
     const int lane = threadIdx.x & 31;
     const int64_t n_rows = (int64_t)ny * nz;
@@ -89,16 +122,16 @@ __global__ void k_green(cufftDoubleComplex *__restrict__ F, const double *__rest
     for (int64_t row = warp0; row < n_rows; row += n_warps) {
         const int ky = (int)(row % ny), kz = (int)(row / ny);
         const double lyz = lam1[nxh + ky] + lam1[nxh + ny + kz];
-        cufftDoubleComplex *Fr = F + row * nxh;
+        C *Fr = F + row * nxh;
         for (int kx = lane; kx < nxh; kx += 32) {
-            cufftDoubleComplex v = Fr[kx];
+            C v = Fr[kx];
             if (row == 0 && kx == 0) {
-                v.x = 0.0;
-                v.y = 0.0;
+                v.x = 0;
+                v.y = 0;
             } else {
                 const double f = scale / (lam1[kx] + lyz);
-                v.x *= f;
-                v.y *= f;
+                v.x = (decltype(v.x))(v.x * f);
+                v.y = (decltype(v.y))(v.y * f);
             }
             Fr[kx] = v;
         }
@@ -106,7 +139,8 @@ __global__ void k_green(cufftDoubleComplex *__restrict__ F, const double *__rest
 }
 
 // phi and -grad phi (periodic central differences) of the dense root potential into the slots
-__global__ void k_root_out(const double *__restrict__ phi, const int32_t *__restrict__ corner, int n_patches, int nx,
+template <typename T>  // the transform's precision; differences in FP64
+__global__ void k_root_out(const T *__restrict__ phi, const int32_t *__restrict__ corner, int n_patches, int nx,
                            int ny, int nz, double dh, int order, double *__restrict__ phi_out,
                            double *__restrict__ acc_out) {
     const double inv2 = 0.5 / dh, inv12 = 1.0 / (12.0 * dh);
@@ -118,7 +152,7 @@ __global__ void k_root_out(const double *__restrict__ phi, const int32_t *__rest
                   z = corner[3 * s + 2] + (c >> 6);
         auto wrap = [](int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); };  // |offset| <= 2 < n
         auto at = [&](int a, int b, int d) {
-            return phi[((int64_t)wrap(d, nz) * ny + wrap(b, ny)) * nx + wrap(a, nx)];
+            return (double)phi[((int64_t)wrap(d, nz) * ny + wrap(b, ny)) * nx + wrap(a, nx)];
         };
         phi_out[s * PV + c] = at(x, y, z);
         if (!acc_out) continue;
@@ -356,12 +390,16 @@ amr_status amr_hydro_poisson_root(amr_hydro_ctx *c, double G, double *phi, doubl
     if ((int64_t)L.n_patches * PV != (int64_t)nx * ny * nz) return AMR_E_INVAL;  // the whole root grid
     const int64_t n = (int64_t)nx * ny * nz, nc = (int64_t)nz * ny * (nx / 2 + 1);
     amr_status st;
-    // the complex spectrum, then the per-axis eigenvalue tables
-    if ((st = c->fft_real.reserve(n)) || (st = c->fft_cplx.reserve(2 * nc + nx / 2 + 1 + ny + nz))) return st;
+    // FP64 transforms, or FP32 ones in the FP32-compute mode (potential and
+    // accelerations still written in FP64)
+    const bool f32 = c->prm.prec != AMR_FP64;
+    const int grid = c->n_sm * 8;
+    // the complex spectrum, the per-axis eigenvalue tables, the partial sums of rho
+    if ((st = c->fft_real.reserve(n)) || (st = c->fft_cplx.reserve(2 * nc + nx / 2 + 1 + ny + nz + grid))) return st;
     if (!c->fft_plan[0]) {
         cufftHandle f, b;
-        if ((st = cufft_fail(cufftPlan3d(&f, nz, ny, nx, CUFFT_D2Z), "plan"))) return st;
-        if ((st = cufft_fail(cufftPlan3d(&b, nz, ny, nx, CUFFT_Z2D), "plan"))) {
+        if ((st = cufft_fail(cufftPlan3d(&f, nz, ny, nx, f32 ? CUFFT_R2C : CUFFT_D2Z), "plan"))) return st;
+        if ((st = cufft_fail(cufftPlan3d(&b, nz, ny, nx, f32 ? CUFFT_C2R : CUFFT_Z2D), "plan"))) {
             cufftDestroy(f);
             return st;
         }
@@ -372,19 +410,34 @@ amr_status amr_hydro_poisson_root(amr_hydro_ctx *c, double G, double *phi, doubl
     cudaStream_t s = c->stream;
     if ((st = cufft_fail(cufftSetStream(f, s), "stream")) || (st = cufft_fail(cufftSetStream(b, s), "stream")))
         return st;
-    const int grid = c->n_sm * 8;
     const double dh = level_dh(c, 0);
-    k_rho_dense<<<grid, 256, 0, s>>>(L.U[L.cur], L.d_corner, L.n_patches, nx, ny, c->fft_real.p);
-    if ((st = cuda_fail(cudaGetLastError(), "k_rho_dense"))) return st;
-    cufftDoubleComplex *F = (cufftDoubleComplex *)c->fft_cplx.p;
-    if ((st = cufft_fail(cufftExecD2Z(f, c->fft_real.p, F), "D2Z"))) return st;
-    double *lam1 = c->fft_cplx.p + 2 * nc;
+    double *lam1 = c->fft_cplx.p + 2 * nc, *partial = lam1 + nx / 2 + 1 + ny + nz;
+    k_rho_partial<<<grid, 256, 0, s>>>(L.U[L.cur], L.n_patches, partial);
+    if ((st = cuda_fail(cudaGetLastError(), "k_rho_partial"))) return st;
     k_green_axes<<<(nx / 2 + 1 + ny + nz + 255) / 256, 256, 0, s>>>(lam1, nx, ny, nz);
     if ((st = cuda_fail(cudaGetLastError(), "k_green_axes"))) return st;
-    k_green<<<grid, 256, 0, s>>>(F, lam1, nx, ny, nz, FOUR_PI * G * dh * dh / (double)n);
-    if ((st = cuda_fail(cudaGetLastError(), "k_green"))) return st;
-    if ((st = cufft_fail(cufftExecZ2D(b, F, c->fft_real.p), "Z2D"))) return st;
-    k_root_out<<<grid, 256, 0, s>>>(c->fft_real.p, L.d_corner, L.n_patches, nx, ny, nz, dh, acc_order, phi, acc);
+    const double scale = FOUR_PI * G * dh * dh / (double)n;
+    if (f32) {
+        float *R = reinterpret_cast<float *>(c->fft_real.p);
+        cufftComplex *F = reinterpret_cast<cufftComplex *>(c->fft_cplx.p);
+        k_rho_dense<float><<<grid, 256, 0, s>>>(L.U[L.cur], L.d_corner, L.n_patches, nx, ny, partial, grid, R);
+        if ((st = cuda_fail(cudaGetLastError(), "k_rho_dense"))) return st;
+        if ((st = cufft_fail(cufftExecR2C(f, R, F), "R2C"))) return st;
+        k_green<cufftComplex><<<grid, 256, 0, s>>>(F, lam1, nx, ny, nz, scale);
+        if ((st = cuda_fail(cudaGetLastError(), "k_green"))) return st;
+        if ((st = cufft_fail(cufftExecC2R(b, F, R), "C2R"))) return st;
+        k_root_out<float><<<grid, 256, 0, s>>>(R, L.d_corner, L.n_patches, nx, ny, nz, dh, acc_order, phi, acc);
+    } else {
+        double *R = c->fft_real.p;
+        cufftDoubleComplex *F = reinterpret_cast<cufftDoubleComplex *>(c->fft_cplx.p);
+        k_rho_dense<double><<<grid, 256, 0, s>>>(L.U[L.cur], L.d_corner, L.n_patches, nx, ny, partial, grid, R);
+        if ((st = cuda_fail(cudaGetLastError(), "k_rho_dense"))) return st;
+        if ((st = cufft_fail(cufftExecD2Z(f, R, F), "D2Z"))) return st;
+        k_green<cufftDoubleComplex><<<grid, 256, 0, s>>>(F, lam1, nx, ny, nz, scale);
+        if ((st = cuda_fail(cudaGetLastError(), "k_green"))) return st;
+        if ((st = cufft_fail(cufftExecZ2D(b, F, R), "Z2D"))) return st;
+        k_root_out<double><<<grid, 256, 0, s>>>(R, L.d_corner, L.n_patches, nx, ny, nz, dh, acc_order, phi, acc);
+    }
     return cuda_fail(cudaGetLastError(), "k_root_out");
 }
 

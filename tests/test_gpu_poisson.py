@@ -25,13 +25,22 @@ def dense_of(slots, corners, shape):
     return out
 
 
+# FP32 transforms (the FP32-compute mode): an FFT of N values in precision
+# eps carries a round-off of about eps log2(N) of the transformed vector's
+# norm (eps 6e-8, log2(N) 17 here: 1e-6); the inverse Laplacian damps it,
+# and a difference over 2 dh raises it against the smooth part of g by at
+# most N_x / (2 pi) (5 at 32 cells): bounds 1e-5 of max|phi|, 1e-4 of max|g|.
+ROOT_TOL = {A.AMR_FP64: (1e-12, 1e-11), A.AMR_FP32_ACC64: (1e-5, 1e-4)}
+
+
+@pytest.mark.parametrize("prec", [A.AMR_FP64, A.AMR_FP32_ACC64])
 @pytest.mark.parametrize("order", [2, 4])
-def test_root_periodic_fft(order):
+def test_root_periodic_fft(order, prec):
     import torch
     from paper_1712_07070_b300.uniform import UniformGrid
     nx, ny, nz = 32, 48, 64
     U0 = ics.sod_noise(nx, seed=17, ny=ny, nz=nz)
-    g = UniformGrid((nx, ny, nz))
+    g = UniformGrid((nx, ny, nz), prec=prec)
     g.upload(U0)
     n = g.n_patches
     phi = torch.zeros((n, 8, 8, 8), dtype=torch.float64, device="cuda")
@@ -43,10 +52,11 @@ def test_root_periodic_fft(order):
     g.close()
     dh = 1.0 / nx
     ref = PS.poisson_root_periodic(U0[0], dh, 0.9)
-    assert np.abs(ph - ref).max() <= 1e-12 * np.abs(ref).max()
+    tp, tg = ROOT_TOL[prec]
+    assert np.abs(ph - ref).max() <= tp * np.abs(ref).max()
     h = order // 2
     gref = PS.accel(np.pad(ref, h, mode="wrap"), dh, order)
-    assert np.abs(ac - gref).max() <= 1e-11 * np.abs(gref).max()
+    assert np.abs(ac - gref).max() <= tg * np.abs(gref).max()
 
 
 def test_refined_levels_sor():
@@ -116,7 +126,7 @@ def test_coupled_gravity_step(prec, tol, c_acc, order):
     _, acc = g.gravity(G, order)
     dh = 1.0 / n
     gref = PS.accel_periodic(PS.poisson_root_periodic(U[0], dh, G), dh, order)
-    assert np.abs(g.to_dense(acc) - gref).max() <= 1e-11 * np.abs(gref).max()
+    assert np.abs(g.to_dense(acc) - gref).max() <= ROOT_TOL[prec][1] * np.abs(gref).max()
     import oracle
     t = 0.0
     for _ in range(3):
