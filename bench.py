@@ -47,7 +47,7 @@ FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # DRAM bytes (read+write) per cell update of one k_hydro_step launch from an
 # ncu capture, keyed by the hash of the kernel sources it was taken on.
-TRAFFIC_BYTES_PER_CELL = {"f64:fee62d4c11598550": 86.8, "f32:fee62d4c11598550": 92.6}
+TRAFFIC_BYTES_PER_CELL = {"f64:26f3ae6aea665331": 86.8, "f32:26f3ae6aea665331": 92.5}
 KERNEL_SOURCES = ("paper_1712_07070_b300/csrc/step_kernel.cuh", "paper_1712_07070_b300/csrc/hydro_math.cuh")
 
 
@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--n", type=int, default=512, help="box edge (cells), multiple of 16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--sor-case", action="store_true",
+                    help="only the refined-level SOR solve on the blob hierarchy with an n^3 root (profiling case)")
     return ap.parse_args()
 
 
@@ -555,8 +557,46 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def sor_case(args):
+    """The refined-level Poisson solve alone: SOR (60 red-black iterations,
+    omega 1.7, two-point accelerations) on level 1 of the blob hierarchy
+    with an n^3 root (3 blobs, seed 3, theta 0.1, N_buf 8), after the root
+    FFT solve; ``--warmup`` untimed and ``--steps`` timed solves, one JSON line."""
+    import torch
+    from paper_1712_07070_b300 import amr_hydro as A
+    from paper_1712_07070_b300 import ics
+    from paper_1712_07070_b300.amr import AmrHierarchy
+    H = AmrHierarchy(ics.blobs(args.n, seed=3), lmax=1, theta=0.1, nbuf=(8,), max_patches=120000)
+    phi0 = torch.zeros((H.n_patches(0), 8, 8, 8), dtype=torch.float64, device="cuda")
+    A.amr_hydro_poisson_root(H.ctx, 1.0, phi0)
+    n1 = H.n_patches(1)
+    phi1 = torch.zeros((n1, 8, 8, 8), dtype=torch.float64, device="cuda")
+    acc1 = torch.zeros((n1, 3, 8, 8, 8), dtype=torch.float64, device="cuda")
+
+    def solve():
+        A.amr_hydro_poisson_level(H.ctx, 1, 1.0, 1.7, 60, phi0, phi1, acc1, 2)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch)
+    e0.record()
+    for _ in range(args.steps):
+        solve()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    print(json.dumps({"metric": "SOR point updates per second", "value": n1 * 60 * 4096 / (ms * 1e-3),
+                      "unit": "point updates/s", "ms_per_solve": ms, "patches": n1,
+                      "config": {"workload": f"SOR, 60 iterations, level 1 of the {args.n}^3-root blob hierarchy"}}))
+    H.close()
+
+
 def main():
     args = parse()
+    if args.sor_case:
+        sor_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
