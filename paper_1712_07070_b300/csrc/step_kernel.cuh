@@ -844,9 +844,17 @@ __device__ __forceinline__ void step_run(SM &S, const StepParams &P, const int32
                 else sn = so - f2d_bits(dtdh_r * tots);
                 const double ekin = 0.5 * (una[1] * una[1] + una[2] * una[2] + una[3] * una[3]) / una[0];
                 const double eth = una[4] - ekin;
-                const double rg = pow(una[0], P.gamma - 1.0);
-                if (eth < P.de_xi * ekin) una[4] = ekin + sn * rg / (P.gamma - 1.0);
-                else sn = (P.gamma - 1.0) * eth / rg;
+                // rho^(gamma-1) at the flux precision: an FP64 pow costs about as much
+                // FP64 pipe time as the FP32 mode's whole cell update
+                if constexpr (sizeof(real) == sizeof(double)) {
+                    const double rg = pow(una[0], P.gamma - 1.0);
+                    if (eth < P.de_xi * ekin) una[4] = ekin + sn * rg / (P.gamma - 1.0);
+                    else sn = (P.gamma - 1.0) * eth / rg;
+                } else {  // the choice itself stays in FP64
+                    const float rg = powf((float)una[0], (float)(P.gamma - 1.0));
+                    if (eth < P.de_xi * ekin) una[4] = ekin + sn * (double)(rg / (float)(P.gamma - 1.0));
+                    else sn = eth * (double)((float)(P.gamma - 1.0) / rg);
+                }
                 P.S_new[base / PSLOT * PV + base % PSLOT] = sn;
 #pragma unroll
                 for (int v = 0; v < NV; v++) {
