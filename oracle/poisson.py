@@ -29,6 +29,13 @@ Readings taken (the paper names the methods; their details are ours):
     (phi_{i+1} - phi_{i-1}) / (2 dh) or four-point
     (-phi_{i+2} + 8 phi_{i+1} - 8 phi_{i-1} + phi_{i-2}) / (12 dh)
     central differences.
+  * root level, isolated: every cell is a point mass m = rho dh^3 at its
+    centre and the potential is the pairwise sum over the other cells,
+        phi_i = -G sum_{j != i} m_j / |r_i - r_j|,
+    evaluated by a cyclic FFT convolution on a zero-padded grid of at
+    least 2 N + 4 cells per axis (a multiple of 2, 3, 5, 7 only), which is
+    exact for offsets up to N + 1 and so also gives phi on the two layers
+    outside the box that the accelerations of the edge cells need.
 Arrays are [z][y][x] (x fastest) like the hydro oracle's.
 """
 import numpy as np
@@ -187,3 +194,64 @@ def gravity_correct(U, g_n, Us, g1, dt):
     out[4] = Us[4] + 0.5 * dt * ((U[1] * g_n[0] + U[2] * g_n[1] + U[3] * g_n[2]) +
                                  (out[1] * g1[0] + out[2] * g1[1] + out[3] * g1[2]))
     return out
+
+
+def pairwise_potential(rho, dh, G=1.0, points=None):
+    """Isolated potential by direct summation over all cell pairs (small
+    grids): at the cell centres, or at the given (z, y, x) cell-index
+    points (any integers, inside or outside the box)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    nz, ny, nx = rho.shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    src = np.stack([z.ravel(), y.ravel(), x.ravel()], axis=1).astype(np.float64)
+    m = rho.ravel() * dh ** 3
+    pts = src if points is None else np.asarray(points, dtype=np.float64)
+    out = np.empty(len(pts))
+    for i, p in enumerate(pts):
+        r = np.sqrt(((src - p) ** 2).sum(axis=1)) * dh
+        nz_ = r > 0
+        out[i] = -G * (m[nz_] / r[nz_]).sum()
+    return out.reshape(rho.shape) if points is None else out
+
+
+def smooth7(n):
+    """The smallest integer >= n whose prime factors are 2, 3, 5 or 7."""
+    while True:
+        k = n
+        for p in (2, 3, 5, 7):
+            while k % p == 0:
+                k //= p
+        if k == 1:
+            return n
+        n += 1
+
+
+def isolated_sizes(shape):
+    """The padded grid of the isolated solve, per axis (z, y, x)."""
+    return tuple(smooth7(2 * n + 4) for n in shape)
+
+
+def poisson_root_isolated(rho, dh, G=1.0, halo=0):
+    """Isolated potential of the root grid by zero-padded FFT convolution
+    with the point-mass kernel -G dh^2 / |offset in cells| (0 at offset 0).
+    halo > 0 (at most 2): also the layers outside the box, returned as an
+    array of shape N + 2 halo per axis."""
+    rho = np.asarray(rho, dtype=np.float64)
+    n = rho.shape
+    M = isolated_sizes(n)
+    pad = np.zeros(M)
+    pad[:n[0], :n[1], :n[2]] = rho
+    offs = [np.where(np.arange(m) <= m // 2, np.arange(m), np.arange(m) - m) for m in M]
+    dz, dy, dx = np.meshgrid(*offs, indexing="ij")
+    d = np.sqrt(dx * dx + dy * dy + dz * dz)
+    g = np.zeros(M)
+    g[d > 0] = -G * dh * dh / d[d > 0]
+    phi = np.fft.irfftn(np.fft.rfftn(pad) * np.fft.rfftn(g), s=M, axes=(0, 1, 2))
+    idx = [np.arange(-halo, k + halo) % m for k, m in zip(n, M)]
+    return phi[np.ix_(*idx)]
+
+
+def accel_isolated(rho, dh, G=1.0, order=2):
+    """-grad phi of the isolated potential on every cell of the box."""
+    h = order // 2
+    return accel(poisson_root_isolated(rho, dh, G, halo=h), dh, order)
