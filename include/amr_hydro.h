@@ -97,6 +97,14 @@ typedef enum {
                           With AMR_SCHEME_MH and AMR_SCHEME_CTU. */
 } amr_recon;
 
+/* Boundary condition of the root-level gravity solve (section 2.3). */
+typedef enum {
+    AMR_GRAVITY_PERIODIC = 0, /* the 7-point Laplacian's Green's function on the periodic box */
+    AMR_GRAVITY_ISOLATED = 1  /* every cell a point mass rho dh^3 at its centre, the potential the
+                                 pairwise sum -G sum_{j != i} m_j / |r_i - r_j| (zero-padded FFT
+                                 convolution on a grid of at least 2 N + 4 cells per axis) */
+} amr_gravity_bc;
+
 /* Run parameters (section 2.1 and 2.6 symbols). */
 typedef struct {
     double gamma;        /* adiabatic index */
@@ -130,6 +138,7 @@ typedef struct {
                             after the update E = E_kin + s rho^(gamma-1)/(gamma-1) where
                             E_the < dual_xi E_kin, else s is reset from E */
     double dual_xi;      /* the threshold on E_the / E_kin; 0 means 1e-2 */
+    int gravity_bc;      /* amr_gravity_bc of amr_hydro_poisson_root (0: periodic) */
 } amr_hydro_params;
 
 typedef struct amr_hydro_ctx amr_hydro_ctx; /* opaque, library-owned */
@@ -142,7 +151,7 @@ typedef struct amr_hydro_ctx amr_hydro_ctx; /* opaque, library-owned */
  * nor in [1, 2], AMR_SCHEME_VL with lmax > 0 or with AMR_RECON_PPM, a
  * recon value outside its enum, fallback not 0 or 1, dt_min < 0, and
  * dual_energy not 0 or 1, dual_xi < 0, or dual_energy with another scheme,
- * PPM, lmax > 0 or the cell remedies. */
+ * PPM, lmax > 0 or the cell remedies, and a gravity_bc outside its enum. */
 amr_status amr_hydro_init(const amr_hydro_params *params, void *cuda_stream,
                           amr_hydro_ctx **out);
 

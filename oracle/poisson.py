@@ -170,18 +170,23 @@ def dt_acc(g, dh, c_acc):
     return c_acc * np.sqrt(dh / np.abs(g).max())
 
 
-def step_gravity(U, g_n, dh, dt, gamma, G, order=2):
+def step_gravity(U, g_n, dh, dt, gamma, G, order=2, isolated=False):
     """One coupled hydro + self-gravity step on a periodic root grid
     (section 2.3, after Muller & Steinmetz 1995): the predictor (the
     MUSCL-Hancock step with gravity in its half step, hydro_oracle.c), the
     FFT potential and acceleration g^{n+1} of the predicted density, then
     m^{n+1} = m* + (dt/2)(rho^n g^n + rho^{n+1} g^{n+1}) and
     E^{n+1} = E* + (dt/2)(m^n.g^n + m^{n+1}.g^{n+1}).
-    Returns (U^{n+1}, phi^{n+1}, g^{n+1}, nbad of the predictor)."""
+    isolated: the root potential with isolated boundaries (the hydro stays
+    periodic).  Returns (U^{n+1}, phi^{n+1}, g^{n+1}, nbad of the predictor)."""
     import oracle
     Us, nbad = oracle.step_gravity_predictor(U, g_n, dh, dt, gamma)
-    phi = poisson_root_periodic(Us[0], dh, G)
-    g1 = accel_periodic(phi, dh, order)
+    if isolated:
+        phi = poisson_root_isolated(Us[0], dh, G)
+        g1 = accel_isolated(Us[0], dh, G, order)
+    else:
+        phi = poisson_root_periodic(Us[0], dh, G)
+        g1 = accel_periodic(phi, dh, order)
     return gravity_correct(U, g_n, Us, g1, dt), phi, g1, nbad
 
 

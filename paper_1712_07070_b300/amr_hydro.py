@@ -19,6 +19,7 @@ AMR_LIM_VANLEER, AMR_LIM_GMINMOD, AMR_LIM_ALBADA, AMR_LIM_VL_GMINMOD = 0, 1, 2, 
 AMR_RS_HLLC, AMR_RS_HLLE, AMR_RS_ROE, AMR_RS_EXACT = 0, 1, 2, 3
 AMR_SCHEME_MH, AMR_SCHEME_VL, AMR_SCHEME_CTU = 0, 1, 2
 AMR_RECON_PLM, AMR_RECON_PPM = 0, 1
+AMR_GRAVITY_PERIODIC, AMR_GRAVITY_ISOLATED = 0, 1
 
 # every symbol include/amr_hydro.h declares
 SYMBOLS = (
@@ -43,7 +44,7 @@ class amr_hydro_params(ctypes.Structure):
         ("box", ctypes.c_double * 3), ("root_n", ctypes.c_int * 3), ("max_patches", ctypes.c_int),
         ("limiter", ctypes.c_int), ("riemann", ctypes.c_int), ("minmod_coeff", ctypes.c_double),
         ("scheme", ctypes.c_int), ("recon", ctypes.c_int), ("fallback", ctypes.c_int), ("dt_min", ctypes.c_double),
-        ("dual_energy", ctypes.c_int), ("dual_xi", ctypes.c_double),
+        ("dual_energy", ctypes.c_int), ("dual_xi", ctypes.c_double), ("gravity_bc", ctypes.c_int),
     ]
 
 
@@ -313,10 +314,12 @@ def amr_hydro_level_info(ctx, level):
 def make_params(gamma=5.0 / 3.0, cfl=0.5, root_n=(64, 64, 64), box=None, lmax=0,
                 prec=AMR_FP64, max_patches=None, theta=0.05, c_inc=0.1, c_dec=0.1, nbuf=None,
                 limiter=AMR_LIM_VANLEER, riemann=AMR_RS_HLLC, minmod_coeff=1.5, scheme=AMR_SCHEME_MH,
-                recon=AMR_RECON_PLM, fallback=0, dt_min=0.0, dual_energy=0, dual_xi=0.0):
+                recon=AMR_RECON_PLM, fallback=0, dt_min=0.0, dual_energy=0, dual_xi=0.0,
+                gravity_bc=AMR_GRAVITY_PERIODIC):
     p = amr_hydro_params()
     p.limiter, p.riemann, p.minmod_coeff, p.scheme, p.recon = limiter, riemann, minmod_coeff, scheme, recon
     p.fallback, p.dt_min, p.dual_energy, p.dual_xi = fallback, dt_min, dual_energy, dual_xi
+    p.gravity_bc = gravity_bc
     p.gamma, p.cfl, p.c_inc, p.c_dec, p.theta = gamma, cfl, c_inc, c_dec, theta
     p.lmax = lmax
     nb = nbuf if nbuf is not None else [8] * 8

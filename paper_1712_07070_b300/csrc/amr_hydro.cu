@@ -260,6 +260,7 @@ amr_status amr_hydro_init(const amr_hydro_params *p, void *stream, amr_hydro_ctx
     if (!(p->dt_min >= 0.0)) return AMR_E_INVAL;
     if (p->dual_energy != 0 && p->dual_energy != 1) return AMR_E_INVAL;
     if (!(p->dual_xi >= 0.0)) return AMR_E_INVAL;
+    if (p->gravity_bc != AMR_GRAVITY_PERIODIC && p->gravity_bc != AMR_GRAVITY_ISOLATED) return AMR_E_INVAL;
     if (p->dual_energy && (p->scheme != AMR_SCHEME_MH || p->recon != AMR_RECON_PLM || p->lmax > 0 || p->fallback))
         return AMR_E_INVAL;
     // VL on refined levels would need the half-step state in a 3-cell ring of

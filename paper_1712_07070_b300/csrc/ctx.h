@@ -147,9 +147,12 @@ struct amr_hydro_ctx {
     // cells the step left unphysical, for the cell remedies (params.fallback)
     amrh::DevBuf<int64_t> fb_list;
     amrh::DevBuf<unsigned long long> fb_count;
-    // root-level Poisson solver: cuFFT plans (forward, inverse) and work arrays
+    // root-level Poisson solver: cuFFT plans (forward, inverse) and work arrays;
+    // isolated gravity: the padded grid's sizes and the transformed kernel
     long long fft_plan[2] = {0, 0};
-    amrh::DevBuf<double> fft_real, fft_cplx;
+    amrh::DevBuf<double> fft_real, fft_cplx, fft_green;
+    int fft_m[3] = {0, 0, 0};
+    bool fft_green_ready = false;
 };
 
 namespace amrh {

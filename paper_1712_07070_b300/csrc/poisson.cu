@@ -138,7 +138,63 @@ __global__ void k_green(C *__restrict__ F, const double *__restrict__ lam1, int 
     }
 }
 
-// phi and -grad phi (periodic central differences) of the dense root potential into the slots
+// ---- isolated boundaries: zero-padded convolution with the point-mass kernel ------
+
+// The smallest integer >= n whose prime factors are 2, 3, 5 or 7 (a fast cuFFT size).
+int smooth7(int n) {
+    for (;; n++) {
+        int k = n;
+        for (int p : {2, 3, 5, 7})
+            while (k % p == 0) k /= p;
+        if (k == 1) return n;
+    }
+}
+
+// The kernel -dh^2 / |offset in cells| (G = 1, cell mass rho dh^3) on the padded
+// [mz][my][mx] grid, offsets wrapped to (-m/2, m/2], 0 at offset 0.
+template <typename T>
+__global__ void k_iso_kernel(T *__restrict__ g, int mx, int my, int mz, double dh) {
+    const int64_t n = (int64_t)mx * my * mz;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int x = (int)(i % mx), y = (int)((i / mx) % my), z = (int)(i / ((int64_t)mx * my));
+        if (x > mx / 2) x -= mx;
+        if (y > my / 2) y -= my;
+        if (z > mz / 2) z -= mz;
+        const double d = sqrt((double)x * x + (double)y * y + (double)z * z);
+        g[i] = (T)(d > 0.0 ? -dh * dh / d : 0.0);
+    }
+}
+
+// rho (variable 0 of the level's current state) into the first octant of the
+// zeroed padded [mz][my][mx] array
+template <typename T>
+__global__ void k_rho_scatter(const double *__restrict__ U, const int32_t *__restrict__ corner, int n_patches,
+                              int mx, int my, T *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)n_patches * PV;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = i / PV;
+        const int c = (int)(i % PV);
+        const int x = corner[3 * s] + (c & 7), y = corner[3 * s + 1] + ((c >> 3) & 7),
+                  z = corner[3 * s + 2] + (c >> 6);
+        out[((int64_t)z * my + y) * mx + x] = (T)U[s * PSLOT + c];
+    }
+}
+
+// F *= G_hat * scale (the transforms of the density and of the kernel)
+template <typename C>
+__global__ void k_iso_mul(C *__restrict__ F, const C *__restrict__ Gk, int64_t n, double scale) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const C a = F[i], b = Gk[i];
+        const double re = (double)a.x * b.x - (double)a.y * b.y, im = (double)a.x * b.y + (double)a.y * b.x;
+        F[i].x = (decltype(a.x))(re * scale);
+        F[i].y = (decltype(a.y))(im * scale);
+    }
+}
+
+// phi and -grad phi (central differences) of the dense root potential into
+// the slots; the dense array is [mz][my][mx] and indices wrap modulo those
+// extents (the box itself when periodic; the padded grid, whose layers just
+// outside the box hold the potential there, when isolated)
 template <typename T>  // the transform's precision; differences in FP64
 __global__ void k_root_out(const T *__restrict__ phi, const int32_t *__restrict__ corner, int n_patches, int nx,
                            int ny, int nz, double dh, int order, double *__restrict__ phi_out,
@@ -375,6 +431,8 @@ void release_poisson(amr_hydro_ctx *c) {
     c->fft_plan[0] = c->fft_plan[1] = 0;
     c->fft_real.release();
     c->fft_cplx.release();
+    c->fft_green.release();
+    c->fft_green_ready = false;
 }
 
 }  // namespace amrh
@@ -388,29 +446,82 @@ amr_status amr_hydro_poisson_root(amr_hydro_ctx *c, double G, double *phi, doubl
     Level &L = c->lv[0];
     const int nx = c->prm.root_n[0], ny = c->prm.root_n[1], nz = c->prm.root_n[2];
     if ((int64_t)L.n_patches * PV != (int64_t)nx * ny * nz) return AMR_E_INVAL;  // the whole root grid
-    const int64_t n = (int64_t)nx * ny * nz, nc = (int64_t)nz * ny * (nx / 2 + 1);
+    const bool iso = c->prm.gravity_bc == AMR_GRAVITY_ISOLATED;
+    // the transformed grid: the box (periodic) or the zero-padded one (isolated)
+    const int mx = iso ? smooth7(2 * nx + 4) : nx, my = iso ? smooth7(2 * ny + 4) : ny,
+              mz = iso ? smooth7(2 * nz + 4) : nz;
+    const int64_t n = (int64_t)mx * my * mz, nc = (int64_t)mz * my * (mx / 2 + 1);
     amr_status st;
     // FP64 transforms, or FP32 ones in the FP32-compute mode (potential and
     // accelerations still written in FP64)
     const bool f32 = c->prm.prec != AMR_FP64;
     const int grid = c->n_sm * 8;
-    // the complex spectrum, the per-axis eigenvalue tables, the partial sums of rho
-    if ((st = c->fft_real.reserve(n)) || (st = c->fft_cplx.reserve(2 * nc + nx / 2 + 1 + ny + nz + grid))) return st;
+    // periodic: the complex spectrum, the per-axis eigenvalue tables, the
+    // partial sums of rho; isolated: the spectrum and the kernel's transform
+    if ((st = c->fft_real.reserve(n)) || (st = c->fft_cplx.reserve(2 * nc + (iso ? 0 : mx / 2 + 1 + my + mz + grid))) ||
+        (iso && (st = c->fft_green.reserve(2 * nc))))
+        return st;
     if (!c->fft_plan[0]) {
         cufftHandle f, b;
-        if ((st = cufft_fail(cufftPlan3d(&f, nz, ny, nx, f32 ? CUFFT_R2C : CUFFT_D2Z), "plan"))) return st;
-        if ((st = cufft_fail(cufftPlan3d(&b, nz, ny, nx, f32 ? CUFFT_C2R : CUFFT_Z2D), "plan"))) {
+        if ((st = cufft_fail(cufftPlan3d(&f, mz, my, mx, f32 ? CUFFT_R2C : CUFFT_D2Z), "plan"))) return st;
+        if ((st = cufft_fail(cufftPlan3d(&b, mz, my, mx, f32 ? CUFFT_C2R : CUFFT_Z2D), "plan"))) {
             cufftDestroy(f);
             return st;
         }
         c->fft_plan[0] = (long long)f;
         c->fft_plan[1] = (long long)b;
+        c->fft_m[0] = mx;
+        c->fft_m[1] = my;
+        c->fft_m[2] = mz;
     }
     cufftHandle f = (cufftHandle)c->fft_plan[0], b = (cufftHandle)c->fft_plan[1];
     cudaStream_t s = c->stream;
     if ((st = cufft_fail(cufftSetStream(f, s), "stream")) || (st = cufft_fail(cufftSetStream(b, s), "stream")))
         return st;
     const double dh = level_dh(c, 0);
+    if (iso) {
+        // the kernel's transform once per context (G = 1), then per call:
+        // scatter rho into the zeroed padded grid, transform, multiply, back
+        const double scale = G / (double)n;
+        if (f32) {
+            float *R = reinterpret_cast<float *>(c->fft_real.p);
+            cufftComplex *F = reinterpret_cast<cufftComplex *>(c->fft_cplx.p);
+            cufftComplex *Gk = reinterpret_cast<cufftComplex *>(c->fft_green.p);
+            if (!c->fft_green_ready) {
+                k_iso_kernel<float><<<grid, 256, 0, s>>>(R, mx, my, mz, dh);
+                if ((st = cuda_fail(cudaGetLastError(), "k_iso_kernel"))) return st;
+                if ((st = cufft_fail(cufftExecR2C(f, R, Gk), "R2C kernel"))) return st;
+                c->fft_green_ready = true;
+            }
+            if ((st = cuda_fail(cudaMemsetAsync(R, 0, sizeof(float) * n, s), "memset padded"))) return st;
+            k_rho_scatter<float><<<grid, 256, 0, s>>>(L.U[L.cur], L.d_corner, L.n_patches, mx, my, R);
+            if ((st = cuda_fail(cudaGetLastError(), "k_rho_scatter"))) return st;
+            if ((st = cufft_fail(cufftExecR2C(f, R, F), "R2C"))) return st;
+            k_iso_mul<cufftComplex><<<grid, 256, 0, s>>>(F, Gk, nc, scale);
+            if ((st = cuda_fail(cudaGetLastError(), "k_iso_mul"))) return st;
+            if ((st = cufft_fail(cufftExecC2R(b, F, R), "C2R"))) return st;
+            k_root_out<float><<<grid, 256, 0, s>>>(R, L.d_corner, L.n_patches, mx, my, mz, dh, acc_order, phi, acc);
+        } else {
+            double *R = c->fft_real.p;
+            cufftDoubleComplex *F = reinterpret_cast<cufftDoubleComplex *>(c->fft_cplx.p);
+            cufftDoubleComplex *Gk = reinterpret_cast<cufftDoubleComplex *>(c->fft_green.p);
+            if (!c->fft_green_ready) {
+                k_iso_kernel<double><<<grid, 256, 0, s>>>(R, mx, my, mz, dh);
+                if ((st = cuda_fail(cudaGetLastError(), "k_iso_kernel"))) return st;
+                if ((st = cufft_fail(cufftExecD2Z(f, R, Gk), "D2Z kernel"))) return st;
+                c->fft_green_ready = true;
+            }
+            if ((st = cuda_fail(cudaMemsetAsync(R, 0, sizeof(double) * n, s), "memset padded"))) return st;
+            k_rho_scatter<double><<<grid, 256, 0, s>>>(L.U[L.cur], L.d_corner, L.n_patches, mx, my, R);
+            if ((st = cuda_fail(cudaGetLastError(), "k_rho_scatter"))) return st;
+            if ((st = cufft_fail(cufftExecD2Z(f, R, F), "D2Z"))) return st;
+            k_iso_mul<cufftDoubleComplex><<<grid, 256, 0, s>>>(F, Gk, nc, scale);
+            if ((st = cuda_fail(cudaGetLastError(), "k_iso_mul"))) return st;
+            if ((st = cufft_fail(cufftExecZ2D(b, F, R), "Z2D"))) return st;
+            k_root_out<double><<<grid, 256, 0, s>>>(R, L.d_corner, L.n_patches, mx, my, mz, dh, acc_order, phi, acc);
+        }
+        return cuda_fail(cudaGetLastError(), "k_root_out");
+    }
     double *lam1 = c->fft_cplx.p + 2 * nc, *partial = lam1 + nx / 2 + 1 + ny + nz;
     k_rho_partial<<<grid, 256, 0, s>>>(L.U[L.cur], L.n_patches, partial);
     if ((st = cuda_fail(cudaGetLastError(), "k_rho_partial"))) return st;

@@ -44,7 +44,8 @@ def test_strerror():
                                          ("prec", 7), ("limiter", 4), ("limiter", -1), ("riemann", 4),
                                          ("minmod_coeff", 0.5), ("minmod_coeff", 2.5), ("scheme", 3),
                                          ("scheme", -1), ("recon", 2), ("recon", -1), ("fallback", 2),
-                                         ("dt_min", -1.0), ("dual_energy", 2), ("dual_xi", -1.0)])
+                                         ("dt_min", -1.0), ("dual_energy", 2), ("dual_xi", -1.0),
+                                         ("gravity_bc", 2), ("gravity_bc", -1)])
 def test_init_rejects_bad_params(field, value):
     p = A.make_params(root_n=(32, 32, 32))
     setattr(p, field, value)

@@ -164,3 +164,61 @@ def test_coupled_gravity_rejects_other_schemes():
     with pytest.raises(A.AmrHydroError):
         g.step_gravity(1.0, acc)
     g.close()
+
+
+# Isolated boundaries in FP32: the same eps log2(N) round-off, now of a
+# potential dominated by its smooth -GM/r part; a difference over 2 dh
+# raises it against max|g| ~ GM/L^2 by about N (64 here): 1e-5 of max|phi|,
+# 5e-4 of max|g|.
+ISO_TOL = {A.AMR_FP64: (1e-12, 1e-11), A.AMR_FP32_ACC64: (1e-5, 5e-4)}
+
+
+@pytest.mark.parametrize("prec", [A.AMR_FP64, A.AMR_FP32_ACC64])
+@pytest.mark.parametrize("order", [2, 4])
+def test_root_isolated(order, prec):
+    """Isolated root potential (every cell a point mass, the pairwise sum by
+    zero-padded FFT) and its accelerations, the edge cells' differences
+    reaching the two layers outside the box, on a 32 x 48 x 64 grid (padded
+    to 70 x 100 x 135), twice on one context (the kernel's transform is
+    made once)."""
+    import torch
+    from paper_1712_07070_b300.uniform import UniformGrid
+    nx, ny, nz = 32, 48, 64
+    U0 = ics.sod_noise(nx, seed=19, ny=ny, nz=nz)
+    g = UniformGrid((nx, ny, nz), prec=prec, scheme={"gravity_bc": A.AMR_GRAVITY_ISOLATED})
+    g.upload(U0)
+    dh = 1.0 / nx
+    ref = PS.poisson_root_isolated(U0[0], dh, 0.7)
+    gref = PS.accel_isolated(U0[0], dh, 0.7, order)
+    tp, tg = ISO_TOL[prec]
+    for _ in range(2):
+        phi, acc = g.gravity(0.7, order)
+        ph, ac = g.to_dense(phi), g.to_dense(acc)
+        assert np.abs(ph - ref).max() <= tp * np.abs(ref).max()
+        assert np.abs(ac - gref).max() <= tg * np.abs(gref).max()
+    g.close()
+
+
+def test_coupled_gravity_step_isolated():
+    """Two coupled steps with the isolated root potential, FP64, against the
+    oracle at 1e-12."""
+    from paper_1712_07070_b300.uniform import UniformGrid
+    import oracle
+    n, G = 32, 2.0
+    U = gravity_ics(n, 7)
+    g = UniformGrid((n, n, n), scheme={"gravity_bc": A.AMR_GRAVITY_ISOLATED})
+    g.upload(U)
+    dh = 1.0 / n
+    _, acc = g.gravity(G, 2)
+    gref = PS.accel_isolated(U[0], dh, G, 2)
+    for _ in range(2):
+        dt = oracle.dt_cfl2(U, G53, 0.5, dh)
+        phi, acc = g.step_gravity(G, acc, dt, 2)
+        U, phir, gref, nbad = PS.step_gravity(U, gref, dh, dt, G53, G, 2, isolated=True)
+        assert nbad == 0
+        V = g.download()
+        scale = np.abs(U).reshape(5, -1).max(axis=1)
+        assert (np.abs(V - U).reshape(5, -1).max(axis=1) / scale).max() <= 1e-12
+        assert np.abs(g.to_dense(phi) - phir).max() <= 1e-12 * np.abs(phir).max()
+        assert np.abs(g.to_dense(acc) - gref).max() <= 1e-11 * np.abs(gref).max()
+    g.close()
