@@ -441,17 +441,19 @@ def bench_gravity(torch, args):
                                              f"corrector), 256^3 turbulence, {tag}", "ms": ms,
                                  "value": n ** 3 / (ms * 1e-3)}
         g.close()
-    H = AmrHierarchy(ics.blobs(128, seed=3), lmax=2, theta=0.1, nbuf=(8, 4), max_patches=120000)
-    phi0 = torch.zeros((H.n_patches(0), 8, 8, 8), dtype=torch.float64, device="cuda")
-    A.amr_hydro_poisson_root(H.ctx, 1.0, phi0)
-    n1 = H.n_patches(1)
-    phi1 = torch.zeros((n1, 8, 8, 8), dtype=torch.float64, device="cuda")
-    acc1 = torch.zeros((n1, 3, 8, 8, 8), dtype=torch.float64, device="cuda")
-    ms = timed(lambda: A.amr_hydro_poisson_level(H.ctx, 1, 1.0, 1.7, 60, phi0, phi1, acc1, 2), 3)
-    out["sor"] = {"workload": f"SOR on 18^3 per patch, 60 red-black iterations, {n1} level-1 patches of the "
-                              "blob hierarchy, FP64", "ms": ms, "value": n1 * 512 / (ms * 1e-3),
-                  "point_updates_per_s": n1 * 60 * 4096 / (ms * 1e-3)}
-    H.close()
+    for prec, tag in ((A.AMR_FP64, ""), (A.AMR_FP32_ACC64, "_fp32")):
+        H = AmrHierarchy(ics.blobs(128, seed=3), lmax=2, theta=0.1, nbuf=(8, 4), max_patches=120000, prec=prec)
+        phi0 = torch.zeros((H.n_patches(0), 8, 8, 8), dtype=torch.float64, device="cuda")
+        A.amr_hydro_poisson_root(H.ctx, 1.0, phi0)
+        n1 = H.n_patches(1)
+        phi1 = torch.zeros((n1, 8, 8, 8), dtype=torch.float64, device="cuda")
+        acc1 = torch.zeros((n1, 3, 8, 8, 8), dtype=torch.float64, device="cuda")
+        ms = timed(lambda: A.amr_hydro_poisson_level(H.ctx, 1, 1.0, 1.7, 60, phi0, phi1, acc1, 2), 3)
+        out["sor" + tag] = {"workload": f"SOR on 18^3 per patch, 60 red-black iterations, {n1} level-1 patches "
+                                        f"of the blob hierarchy, {'FP64' if not tag else 'FP32 compute'}",
+                            "ms": ms, "value": n1 * 512 / (ms * 1e-3),
+                            "point_updates_per_s": n1 * 60 * 4096 / (ms * 1e-3)}
+        H.close()
     return out
 
 

@@ -229,15 +229,20 @@ __global__ void k_root_out(const T *__restrict__ phi, const int32_t *__restrict_
 
 // ---- refined levels -------------------------------------------------------------
 
+// real: the solve's precision (double, or float in the FP32-compute mode);
+// the parent level's potential and the states are read in FP64, the
+// potential and accelerations written in FP64
+template <typename real>
 struct SorSmem {
-    double phi[PN][PN][PN];
-    double rho[PN][PN][PN];
+    real phi[PN][PN][PN];
+    real rho[PN][PN][PN];
     int nb[27], cnb[27];  // same-level patches around the patch, parent-level patches around its parent
     int off[3];           // the patch's lower corner relative to its parent's, in coarse cells (0 or 4)
 };
 
-__device__ __forceinline__ double quad1(double pm, double p0, double pp, double x) {
-    return p0 + x * (pp - pm) / 2.0 + x * x * (pp - 2.0 * p0 + pm) / 2.0;
+template <typename real>
+__device__ __forceinline__ real quad1(real pm, real p0, real pp, real x) {
+    return p0 + x * (pp - pm) / real(2) + x * x * (pp - real(2) * p0 + pm) / real(2);
 }
 
 // a value of a parent-level field at coarse cell c relative to the parent's
@@ -248,18 +253,20 @@ __device__ __forceinline__ double coarse_at(const double *__restrict__ F, int64_
     return F[(int64_t)cnb[k] * stride + (cz & 7) * 64 + (cy & 7) * 8 + (cx & 7)];
 }
 
+template <typename real>
 __global__ void __launch_bounds__(SOR_NT) k_sor_patches(
     const double *__restrict__ U, const int32_t *__restrict__ sib, const int32_t *__restrict__ parent,
     const int32_t *__restrict__ corner, const double *__restrict__ Uc, const int32_t *__restrict__ csib,
     const int32_t *__restrict__ ccorner, const double *__restrict__ phic, int n_patches, double dh, double G,
     double omega, int iters, int order, double *__restrict__ phi_out, double *__restrict__ acc_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SorSmem &S = *reinterpret_cast<SorSmem *>(smem_raw);
-    double *rho_flat = &S.rho[0][0][0], *phi_flat = &S.phi[0][0][0];
+    SorSmem<real> &S = *reinterpret_cast<SorSmem<real> *>(smem_raw);
+    real *rho_flat = &S.rho[0][0][0], *phi_flat = &S.phi[0][0][0];
     const int tid = threadIdx.x;
     const double src_scale = dh * dh * FOUR_PI * G;
-    const double w6 = omega / 6.0;  // a multiply instead of an FP64 division per point update
+    const real w6 = (real)(omega / 6.0);  // a multiply instead of a division per point update
     const double inv2 = 0.5 / dh, inv12 = 1.0 / (12.0 * dh);
+    const real qm = real(-0.25), qp = real(0.25);
     for (int p = blockIdx.x; p < n_patches; p += gridDim.x) {
         if (tid < 27) {
             const int P = parent[p];
@@ -278,21 +285,22 @@ __global__ void __launch_bounds__(SOR_NT) k_sor_patches(
             const int fx = i % PN, b = (i / PN) % NC, a = i / (PN * NC);
             const int gx = fx - PB, cx = S.off[0] + (gx >> 1);
             const int cy = S.off[1] + b - 4, cz = S.off[2] + a - 4;
-            phi_flat[i] = quad1(coarse_at(phic, PV, S.cnb, cx - 1, cy, cz), coarse_at(phic, PV, S.cnb, cx, cy, cz),
-                                coarse_at(phic, PV, S.cnb, cx + 1, cy, cz), (gx & 1) ? 0.25 : -0.25);
+            phi_flat[i] = quad1<real>((real)coarse_at(phic, PV, S.cnb, cx - 1, cy, cz),
+                                      (real)coarse_at(phic, PV, S.cnb, cx, cy, cz),
+                                      (real)coarse_at(phic, PV, S.cnb, cx + 1, cy, cz), (gx & 1) ? qp : qm);
         }
         __syncthreads();
         for (int i = tid; i < NC * PN * PN; i += SOR_NT) {
             const int fx = i % PN, fy = (i / PN) % PN, a = i / (PN * PN);
             const int gy = fy - PB, b = (gy >> 1) + 4;
-            const double *X = phi_flat + (a * NC + b) * PN + fx;
-            rho_flat[i] = quad1(X[-PN], X[0], X[PN], (gy & 1) ? 0.25 : -0.25);
+            const real *X = phi_flat + (a * NC + b) * PN + fx;
+            rho_flat[i] = quad1<real>(X[-PN], X[0], X[PN], (gy & 1) ? qp : qm);
         }
         __syncthreads();
         for (int i = tid; i < PN3; i += SOR_NT) {
             const int gz = i / (PN * PN) - PB, a = (gz >> 1) + 4;
-            const double *Y = rho_flat + a * PN * PN + i % (PN * PN);
-            phi_flat[i] = quad1(Y[-PN * PN], Y[0], Y[PN * PN], (gz & 1) ? 0.25 : -0.25);
+            const real *Y = rho_flat + a * PN * PN + i % (PN * PN);
+            phi_flat[i] = quad1<real>(Y[-PN * PN], Y[0], Y[PN * PN], (gz & 1) ? qp : qm);
         }
         __syncthreads();
         // the source term dh^2 4 pi G rho on the grid, formed once per cell
@@ -300,9 +308,9 @@ __global__ void __launch_bounds__(SOR_NT) k_sor_patches(
             const int gx = i % PN - PB, gy = (i / PN) % PN - PB, gz = i / (PN * PN) - PB;  // fine, relative
             const int k = ((gx >> 3) + 1) + 3 * ((gy >> 3) + 1) + 9 * ((gz >> 3) + 1);
             const int s = S.nb[k];
-            rho_flat[i] = src_scale * (s >= 0 ? U[(int64_t)s * PSLOT + (gz & 7) * 64 + (gy & 7) * 8 + (gx & 7)]
-                                              : coarse_at(Uc, PSLOT, S.cnb, S.off[0] + (gx >> 1),
-                                                          S.off[1] + (gy >> 1), S.off[2] + (gz >> 1)));
+            rho_flat[i] = (real)(src_scale * (s >= 0 ? U[(int64_t)s * PSLOT + (gz & 7) * 64 + (gy & 7) * 8 + (gx & 7)]
+                                                      : coarse_at(Uc, PSLOT, S.cnb, S.off[0] + (gx >> 1),
+                                                                  S.off[1] + (gy >> 1), S.off[2] + (gz >> 1))));
         }
         __syncthreads();
         // red-black SOR on the interior 16^3 cells
@@ -311,28 +319,29 @@ __global__ void __launch_bounds__(SOR_NT) k_sor_patches(
                 for (int t = tid; t < 2048; t += SOR_NT) {
                     const int row = t >> 3, k = row / 16 + 1, j = row % 16 + 1;
                     const int i = 1 + ((1 + j + k + colour) & 1) + 2 * (t & 7);
-                    const double ph = S.phi[k][j][i];
-                    const double nbs = S.phi[k - 1][j][i] + S.phi[k + 1][j][i] + S.phi[k][j - 1][i] +
-                                       S.phi[k][j + 1][i] + S.phi[k][j][i - 1] + S.phi[k][j][i + 1];
-                    S.phi[k][j][i] = ph + w6 * (nbs - 6.0 * ph - S.rho[k][j][i]);
+                    const real ph = S.phi[k][j][i];
+                    const real nbs = S.phi[k - 1][j][i] + S.phi[k + 1][j][i] + S.phi[k][j - 1][i] +
+                                     S.phi[k][j + 1][i] + S.phi[k][j][i - 1] + S.phi[k][j][i + 1];
+                    S.phi[k][j][i] = ph + w6 * (nbs - real(6) * ph - S.rho[k][j][i]);
                 }
                 __syncthreads();
             }
         }
-        // the active cells' potential and acceleration
+        // the active cells' potential and acceleration (differences in FP64)
         for (int c = tid; c < PV; c += SOR_NT) {
             const int x = (c & 7) + PB, y = ((c >> 3) & 7) + PB, z = (c >> 6) + PB;
-            phi_out[(int64_t)p * PV + c] = S.phi[z][y][x];
+            phi_out[(int64_t)p * PV + c] = (double)S.phi[z][y][x];
             if (!acc_out) continue;
             for (int d = 0; d < 3; d++) {
                 const int ex = d == 0, ey = d == 1, ez = d == 2;
+                const double p1 = S.phi[z + ez][y + ey][x + ex], m1 = S.phi[z - ez][y - ey][x - ex];
                 double g;
                 if (order == 2) {
-                    g = (S.phi[z + ez][y + ey][x + ex] - S.phi[z - ez][y - ey][x - ex]) * inv2;
+                    g = (p1 - m1) * inv2;
                 } else {
-                    g = (-S.phi[z + 2 * ez][y + 2 * ey][x + 2 * ex] + 8.0 * S.phi[z + ez][y + ey][x + ex] -
-                         8.0 * S.phi[z - ez][y - ey][x - ex] + S.phi[z - 2 * ez][y - 2 * ey][x - 2 * ex]) *
-                        inv12;
+                    const double p2 = S.phi[z + 2 * ez][y + 2 * ey][x + 2 * ex],
+                                 m2 = S.phi[z - 2 * ez][y - 2 * ey][x - 2 * ex];
+                    g = (-p2 + 8.0 * p1 - 8.0 * m1 + m2) * inv12;
                 }
                 acc_out[((int64_t)p * 3 + d) * PV + c] = -g;
             }
@@ -423,6 +432,28 @@ amr_status launch_acc_speed(amr_hydro_ctx *c, const double *acc, int64_t n_value
                             unsigned long long *smax) {
     k_acc_speed<<<c->n_sm * 8, 256, 0, c->stream>>>(acc, n_values, dh, c->prm.cfl / c_acc, smax);
     return cuda_fail(cudaGetLastError(), "k_acc_speed");
+}
+
+template <typename real>
+amr_status launch_sor(amr_hydro_ctx *c, Level &L, Level &C, int level, double G, double omega, int iters,
+                      const double *phi_coarse, double *phi, double *acc, int acc_order) {
+    static bool configured = false;
+    amr_status st;
+    if (!configured) {
+        if ((st = cuda_fail(cudaFuncSetAttribute(k_sor_patches<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)sizeof(SorSmem<real>)),
+                            "sor smem attribute")))
+            return st;
+        configured = true;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sor_patches<real>, SOR_NT, sizeof(SorSmem<real>));
+    const int cap = c->n_sm * (per_sm > 0 ? per_sm : 1);
+    const int grid = L.n_patches < cap ? L.n_patches : cap;
+    k_sor_patches<real><<<grid, SOR_NT, sizeof(SorSmem<real>), c->stream>>>(
+        L.U[L.cur], L.d_sib, L.d_parent, L.d_corner, C.U[C.cur], C.d_sib, C.d_corner, phi_coarse, L.n_patches,
+        level_dh(c, level), G, omega, iters, acc_order, phi, acc);
+    return cuda_fail(cudaGetLastError(), "k_sor_patches");
 }
 
 void release_poisson(amr_hydro_ctx *c) {
@@ -593,23 +624,9 @@ amr_status amr_hydro_poisson_level(amr_hydro_ctx *c, int level, double G, double
     Level &L = c->lv[level], &C = c->lv[level - 1];
     if (!L.n_patches) return AMR_OK;
     if (!L.d_parent || !C.n_patches) return AMR_E_INVAL;
-    static bool configured = false;
-    amr_status st;
-    if (!configured) {
-        if ((st = cuda_fail(cudaFuncSetAttribute(k_sor_patches, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)sizeof(SorSmem)),
-                            "sor smem attribute")))
-            return st;
-        configured = true;
-    }
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sor_patches, SOR_NT, sizeof(SorSmem));
-    const int cap = c->n_sm * (per_sm > 0 ? per_sm : 1);
-    const int grid = L.n_patches < cap ? L.n_patches : cap;
-    k_sor_patches<<<grid, SOR_NT, sizeof(SorSmem), c->stream>>>(
-        L.U[L.cur], L.d_sib, L.d_parent, L.d_corner, C.U[C.cur], C.d_sib, C.d_corner, phi_coarse, L.n_patches,
-        level_dh(c, level), G, omega, iters, acc_order, phi, acc);
-    return cuda_fail(cudaGetLastError(), "k_sor_patches");
+    // FP64, or FP32 in the FP32-compute mode (half the shared memory: 4 CTAs per SM)
+    return c->prm.prec == AMR_FP64 ? launch_sor<double>(c, L, C, level, G, omega, iters, phi_coarse, phi, acc, acc_order)
+                                   : launch_sor<float>(c, L, C, level, G, omega, iters, phi_coarse, phi, acc, acc_order);
 }
 
 }  // extern "C"

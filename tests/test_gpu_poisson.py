@@ -59,11 +59,21 @@ def test_root_periodic_fft(order, prec):
     assert np.abs(ac - gref).max() <= tg * np.abs(gref).max()
 
 
-def test_refined_levels_sor():
+# FP32 SOR (the FP32-compute mode): every sweep rounds phi to eps_32 = 6e-8
+# of its size and the error iteration contracts, so the iterate stays
+# within a few eps / (1 - rho_SOR) of the FP64 one (rho_SOR < 0.9 here):
+# 1e-5 of max|phi|; the four-point difference (weights summing to 18/12)
+# over dh raises that against max|g| by |phi| / (|g| dh), about 20 for these
+# blobs: 3e-4 of max|g|.
+SOR_TOL = {A.AMR_FP64: (1e-12, 1e-10), A.AMR_FP32_ACC64: (1e-5, 3e-4)}
+
+
+@pytest.mark.parametrize("prec", [A.AMR_FP64, A.AMR_FP32_ACC64])
+def test_refined_levels_sor(prec):
     import torch
     from paper_1712_07070_b300.amr import AmrHierarchy
     U0 = ics.blobs(32, seed=3)
-    H = AmrHierarchy(U0, lmax=2, theta=0.05, nbuf=(8, 4), max_patches=6000)
+    H = AmrHierarchy(U0, lmax=2, theta=0.05, nbuf=(8, 4), max_patches=6000, prec=prec)
     O = OracleHierarchy(U0, lmax=2, gamma=G53, cfl=0.5, theta=0.05, nbuf=[8, 4])
     compare(H, O, 1e-12)  # the same patches and states on every level
     G, omega, iters = 1.0, 1.7, 40
@@ -93,9 +103,10 @@ def test_refined_levels_sor():
         for s, (x, y, z) in enumerate(H.corners(l)):
             grid = PS.refined_patch_potential(phic, Lo.U[0], fmask, Lc.U[0], (x, y, z), dh, G, omega, iters)
             act = grid[5:13, 5:13, 5:13]
-            assert np.abs(gp[s] - act).max() <= 1e-12 * np.abs(act).max(), (l, s)
+            tp, tg = SOR_TOL[prec]
+            assert np.abs(gp[s] - act).max() <= tp * np.abs(act).max(), (l, s)
             gref = PS.accel(grid, dh, 4)[:, 3:11, 3:11, 3:11]
-            assert np.abs(ga[s] - gref).max() <= 1e-10 * np.abs(gref).max(), (l, s)
+            assert np.abs(ga[s] - gref).max() <= tg * np.abs(gref).max(), (l, s)
             phi_l[z:z + 8, y:y + 8, x:x + 8] = act
             checked += 1
         phic = phi_l
