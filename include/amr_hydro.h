@@ -360,7 +360,11 @@ amr_status amr_hydro_box_tuning(amr_hydro_ctx *ctx, int *grid, int *chunked, int
  * [n_patches][8][8][8] in level 0's slot order; acc: NULL or
  * [n_patches][3][8][8][8] receiving g = -grad phi (x, y, z) by acc_order = 2
  * or 4 point central differences.  Caller-owned, device; asynchronous on
- * the context's stream.  Uses cuFFT (plans kept in the context).
+ * the context's stream.  Uses cuFFT (plans kept in the context).  With
+ * params.gravity_bc = AMR_GRAVITY_ISOLATED: the pairwise point-mass
+ * potential (no mean subtracted) by zero-padded FFT convolution, the edge
+ * cells' differences reading the potential just outside the box.  In the
+ * FP32-compute mode the transforms run in FP32 (outputs still FP64).
  */
 amr_status amr_hydro_poisson_root(amr_hydro_ctx *ctx, double G, double *phi, double *acc, int acc_order);
 
@@ -375,10 +379,22 @@ amr_status amr_hydro_poisson_root(amr_hydro_ctx *ctx, double G, double *phi, dou
  * relaxation factor omega; the active cells' potential into phi
  * ([n_patches][8][8][8]) and, if acc is not NULL, -grad phi into acc
  * ([n_patches][3][8][8][8]) by acc_order = 2 or 4 point central differences.
- * Asynchronous on the context's stream.
+ * Asynchronous on the context's stream.  FP64, or FP32 in the FP32-compute
+ * mode (inputs and outputs FP64).
  */
 amr_status amr_hydro_poisson_level(amr_hydro_ctx *ctx, int level, double G, double omega, int iters,
                                    const double *phi_coarse, double *phi, double *acc, int acc_order);
+
+/*
+ * The same with the parent's potential interpolated linearly in time
+ * (section 2.3, adaptive time steps): every parent cell's value is
+ * (1 - w) phi_coarse_old + w phi_coarse_new before the spatial
+ * interpolation, w = (t - t_old) / (t_new - t_old) of the parent's two
+ * potentials (w in [0, 1], else AMR_E_INVAL).
+ */
+amr_status amr_hydro_poisson_level_t(amr_hydro_ctx *ctx, int level, double G, double omega, int iters,
+                                     const double *phi_coarse_old, const double *phi_coarse_new, double w,
+                                     double *phi, double *acc, int acc_order);
 
 /*
  * One hydro step of a single-level periodic grid coupled to self-gravity

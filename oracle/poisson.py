@@ -25,6 +25,9 @@ Readings taken (the paper names the methods; their details are ours):
     iteration, each interior cell
         phi += omega (sum of 6 neighbours - 6 phi - dh^2 4 pi G rho) / 6,
     a fixed number of iterations;
+  * with adaptive time steps the parent's potential at the child's time is
+    linear in time between its two potentials, taken per coarse cell
+    before the spatial interpolation: (1 - w) phi_old + w phi_new;
   * acceleration g = -grad phi at cell centres by two-point
     (phi_{i+1} - phi_{i-1}) / (2 dh) or four-point
     (-phi_{i+2} + 8 phi_{i+1} - 8 phi_{i-1} + phi_{i-2}) / (12 dh)
@@ -97,6 +100,11 @@ def interp_quadratic(phi_c, fx, fy, fz):
     Y = quad1d(X[:, :, :, 0], X[:, :, :, 1], X[:, :, :, 2], oy[None, None, :, None])  # [nfz][3][nfy][nfx]
     Z = quad1d(Y[:, 0], Y[:, 1], Y[:, 2], oz[:, None, None])                         # [nfz][nfy][nfx]
     return Z
+
+
+def time_interp(phi_old, phi_new, w):
+    """The parent's potential at w = (t - t_old) / (t_new - t_old)."""
+    return (1.0 - w) * np.asarray(phi_old) + w * np.asarray(phi_new)
 
 
 def sor(phi0, rho, dh, G, omega, iters):

@@ -32,7 +32,7 @@ SYMBOLS = (
     "amr_hydro_unpack_uniform", "amr_hydro_step_uniform_noalloc", "amr_hydro_bind_level",
     "amr_hydro_regrid", "amr_hydro_advance_root", "amr_hydro_level_info", "amr_hydro_box_tuning",
     "amr_hydro_advance_host", "amr_hydro_set_entropy", "amr_hydro_poisson_root", "amr_hydro_poisson_level",
-    "amr_hydro_advance_gravity",
+    "amr_hydro_advance_gravity", "amr_hydro_poisson_level_t",
 )
 
 
@@ -75,6 +75,8 @@ def lib():
         "amr_hydro_touch_level": [_vp, ctypes.c_int],
         "amr_hydro_set_entropy": [_vp, ctypes.c_int, _vp, _vp],
         "amr_hydro_poisson_root": [_vp, ctypes.c_double, _vp, _vp, ctypes.c_int],
+        "amr_hydro_poisson_level_t": [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp, _vp,
+                                      ctypes.c_double, _vp, _vp, ctypes.c_int],
         "amr_hydro_advance_gravity": [_vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp, ctypes.c_int,
                                       ctypes.c_double],
         "amr_hydro_poisson_level": [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp, _vp,
@@ -188,6 +190,12 @@ def amr_hydro_poisson_root(ctx, G, phi, acc=None, acc_order=2):
 def amr_hydro_advance_gravity(ctx, dt, G, acc_n, phi_new, acc_new, acc_order=2, c_acc=0.0):
     check(lib().amr_hydro_advance_gravity(ctx, dt, G, _p(acc_n), _p(phi_new), _p(acc_new), acc_order, c_acc),
           "amr_hydro_advance_gravity")
+
+
+def amr_hydro_poisson_level_t(ctx, level, G, omega, iters, phi_coarse_old, phi_coarse_new, w, phi, acc=None,
+                              acc_order=2):
+    check(lib().amr_hydro_poisson_level_t(ctx, level, G, omega, iters, _p(phi_coarse_old), _p(phi_coarse_new), w,
+                                          _p(phi), _p(acc), acc_order), "amr_hydro_poisson_level_t")
 
 
 def amr_hydro_poisson_level(ctx, level, G, omega, iters, phi_coarse, phi, acc=None, acc_order=2):

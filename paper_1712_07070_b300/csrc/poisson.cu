@@ -253,12 +253,22 @@ __device__ __forceinline__ double coarse_at(const double *__restrict__ F, int64_
     return F[(int64_t)cnb[k] * stride + (cz & 7) * 64 + (cy & 7) * 8 + (cx & 7)];
 }
 
+// the parent's potential at coarse cell c, linear in time between two
+// potentials when F1 is given: (1 - w) F0 + w F1
+__device__ __forceinline__ double coarse_phi(const double *__restrict__ F0, const double *__restrict__ F1, double w,
+                                             const int *cnb, int cx, int cy, int cz) {
+    const double a = coarse_at(F0, PV, cnb, cx, cy, cz);
+    if (!F1) return a;
+    return (1.0 - w) * a + w * coarse_at(F1, PV, cnb, cx, cy, cz);
+}
+
 template <typename real>
 __global__ void __launch_bounds__(SOR_NT) k_sor_patches(
     const double *__restrict__ U, const int32_t *__restrict__ sib, const int32_t *__restrict__ parent,
     const int32_t *__restrict__ corner, const double *__restrict__ Uc, const int32_t *__restrict__ csib,
-    const int32_t *__restrict__ ccorner, const double *__restrict__ phic, int n_patches, double dh, double G,
-    double omega, int iters, int order, double *__restrict__ phi_out, double *__restrict__ acc_out) {
+    const int32_t *__restrict__ ccorner, const double *__restrict__ phic, const double *__restrict__ phic1,
+    double w, int n_patches, double dh, double G, double omega, int iters, int order, double *__restrict__ phi_out,
+    double *__restrict__ acc_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SorSmem<real> &S = *reinterpret_cast<SorSmem<real> *>(smem_raw);
     real *rho_flat = &S.rho[0][0][0], *phi_flat = &S.phi[0][0][0];
@@ -285,9 +295,9 @@ __global__ void __launch_bounds__(SOR_NT) k_sor_patches(
             const int fx = i % PN, b = (i / PN) % NC, a = i / (PN * NC);
             const int gx = fx - PB, cx = S.off[0] + (gx >> 1);
             const int cy = S.off[1] + b - 4, cz = S.off[2] + a - 4;
-            phi_flat[i] = quad1<real>((real)coarse_at(phic, PV, S.cnb, cx - 1, cy, cz),
-                                      (real)coarse_at(phic, PV, S.cnb, cx, cy, cz),
-                                      (real)coarse_at(phic, PV, S.cnb, cx + 1, cy, cz), (gx & 1) ? qp : qm);
+            phi_flat[i] = quad1<real>((real)coarse_phi(phic, phic1, w, S.cnb, cx - 1, cy, cz),
+                                      (real)coarse_phi(phic, phic1, w, S.cnb, cx, cy, cz),
+                                      (real)coarse_phi(phic, phic1, w, S.cnb, cx + 1, cy, cz), (gx & 1) ? qp : qm);
         }
         __syncthreads();
         for (int i = tid; i < NC * PN * PN; i += SOR_NT) {
@@ -436,7 +446,8 @@ amr_status launch_acc_speed(amr_hydro_ctx *c, const double *acc, int64_t n_value
 
 template <typename real>
 amr_status launch_sor(amr_hydro_ctx *c, Level &L, Level &C, int level, double G, double omega, int iters,
-                      const double *phi_coarse, double *phi, double *acc, int acc_order) {
+                      const double *phi_coarse, const double *phi_coarse1, double w, double *phi, double *acc,
+                      int acc_order) {
     static bool configured = false;
     amr_status st;
     if (!configured) {
@@ -451,8 +462,8 @@ amr_status launch_sor(amr_hydro_ctx *c, Level &L, Level &C, int level, double G,
     const int cap = c->n_sm * (per_sm > 0 ? per_sm : 1);
     const int grid = L.n_patches < cap ? L.n_patches : cap;
     k_sor_patches<real><<<grid, SOR_NT, sizeof(SorSmem<real>), c->stream>>>(
-        L.U[L.cur], L.d_sib, L.d_parent, L.d_corner, C.U[C.cur], C.d_sib, C.d_corner, phi_coarse, L.n_patches,
-        level_dh(c, level), G, omega, iters, acc_order, phi, acc);
+        L.U[L.cur], L.d_sib, L.d_parent, L.d_corner, C.U[C.cur], C.d_sib, C.d_corner, phi_coarse, phi_coarse1, w,
+        L.n_patches, level_dh(c, level), G, omega, iters, acc_order, phi, acc);
     return cuda_fail(cudaGetLastError(), "k_sor_patches");
 }
 
@@ -617,16 +628,31 @@ amr_status amr_hydro_advance_gravity(amr_hydro_ctx *c, double dt, double G, cons
     return AMR_OK;
 }
 
-amr_status amr_hydro_poisson_level(amr_hydro_ctx *c, int level, double G, double omega, int iters,
-                                   const double *phi_coarse, double *phi, double *acc, int acc_order) {
-    if (!c || level < 1 || level > c->prm.lmax || !phi_coarse || !phi || iters < 0) return AMR_E_INVAL;
+static amr_status poisson_level(amr_hydro_ctx *c, int level, double G, double omega, int iters,
+                                const double *phi_c0, const double *phi_c1, double w, double *phi, double *acc,
+                                int acc_order) {
+    if (!c || level < 1 || level > c->prm.lmax || !phi_c0 || !phi || iters < 0) return AMR_E_INVAL;
     if (acc && acc_order != 2 && acc_order != 4) return AMR_E_INVAL;
+    if (!(w >= 0.0 && w <= 1.0)) return AMR_E_INVAL;
     Level &L = c->lv[level], &C = c->lv[level - 1];
     if (!L.n_patches) return AMR_OK;
     if (!L.d_parent || !C.n_patches) return AMR_E_INVAL;
     // FP64, or FP32 in the FP32-compute mode (half the shared memory: 4 CTAs per SM)
-    return c->prm.prec == AMR_FP64 ? launch_sor<double>(c, L, C, level, G, omega, iters, phi_coarse, phi, acc, acc_order)
-                                   : launch_sor<float>(c, L, C, level, G, omega, iters, phi_coarse, phi, acc, acc_order);
+    return c->prm.prec == AMR_FP64
+               ? launch_sor<double>(c, L, C, level, G, omega, iters, phi_c0, phi_c1, w, phi, acc, acc_order)
+               : launch_sor<float>(c, L, C, level, G, omega, iters, phi_c0, phi_c1, w, phi, acc, acc_order);
+}
+
+amr_status amr_hydro_poisson_level(amr_hydro_ctx *c, int level, double G, double omega, int iters,
+                                   const double *phi_coarse, double *phi, double *acc, int acc_order) {
+    return poisson_level(c, level, G, omega, iters, phi_coarse, nullptr, 0.0, phi, acc, acc_order);
+}
+
+amr_status amr_hydro_poisson_level_t(amr_hydro_ctx *c, int level, double G, double omega, int iters,
+                                     const double *phi_coarse_old, const double *phi_coarse_new, double w,
+                                     double *phi, double *acc, int acc_order) {
+    if (!phi_coarse_new) return AMR_E_INVAL;
+    return poisson_level(c, level, G, omega, iters, phi_coarse_old, phi_coarse_new, w, phi, acc, acc_order);
 }
 
 }  // extern "C"

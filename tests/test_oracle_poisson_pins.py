@@ -239,3 +239,26 @@ def test_isolated_polytrope_converges_at_second_order():
     e = [polytrope_error(n) for n in (16, 32, 64)]
     assert e[0][0] / e[1][0] > 3.5 and e[1][0] / e[2][0] > 3.5, e  # measured 4.0, 3.9
     assert e[2][0] < 2.5e-3 and e[2][1] < 1e-4, e  # measured 2.2e-3, 4.3e-5
+
+
+def test_time_interpolated_boundary_is_affine():
+    """A refined patch's potential after a fixed number of SOR iterations
+    is an affine function of the parent potential (boundary and initial
+    guess are linear in it, the density term fixed), so the solve from the
+    time-interpolated parent potential equals the same weights applied to
+    the two solves."""
+    rng = np.random.default_rng(8)
+    n = 16
+    A_ = rng.random((n, n, n))
+    B_ = rng.random((n, n, n))
+    rho_c = 1.0 + rng.random((n, n, n))
+    rho_f = np.repeat(np.repeat(np.repeat(rho_c, 2, 0), 2, 1), 2, 2) * (1 + 0.1 * rng.random((2 * n,) * 3))
+    fmask = np.zeros((2 * n,) * 3, dtype=bool)
+    fmask[8:24, 8:24, 8:24] = True
+    args = (rho_f, fmask, rho_c, (8, 16, 8), 1.0 / (2 * n), 1.0, 1.6, 10)
+    w = 0.3
+    mid = PS.refined_patch_potential(PS.time_interp(A_, B_, w), *args)
+    a = PS.refined_patch_potential(A_, *args)
+    b = PS.refined_patch_potential(B_, *args)
+    assert np.abs(mid - ((1 - w) * a + w * b)).max() <= 1e-13 * np.abs(mid).max()
+    assert np.array_equal(PS.time_interp(A_, B_, 0.0), A_) and np.array_equal(PS.time_interp(A_, B_, 1.0), B_)
