@@ -271,3 +271,41 @@ def test_refined_level_sor_time_interpolated():
     with pytest.raises(A.AmrHydroError):
         A.amr_hydro_poisson_level_t(H.ctx, 1, G, omega, iters, slots(old), slots(new), 1.5, phi, acc, 2)
     H.close()
+
+
+def test_gravity_edge_cases():
+    """Zero SOR iterations give the interpolated initial guess; no
+    acceleration array; invalid arguments are rejected without a launch."""
+    import torch
+    from paper_1712_07070_b300.amr import AmrHierarchy
+    from paper_1712_07070_b300.uniform import UniformGrid
+    U0 = ics.blobs(32, seed=3)
+    H = AmrHierarchy(U0, lmax=1, theta=0.05, nbuf=(8,), max_patches=6000)
+    O = OracleHierarchy(U0, lmax=1, gamma=G53, cfl=0.5, theta=0.05, nbuf=[8])
+    compare(H, O, 1e-12)
+    phi0 = torch.zeros((H.n_patches(0), 8, 8, 8), dtype=torch.float64, device="cuda")
+    A.amr_hydro_poisson_root(H.ctx, 1.0, phi0)  # no acceleration array
+    n1 = H.n_patches(1)
+    phi1 = torch.zeros((n1, 8, 8, 8), dtype=torch.float64, device="cuda")
+    A.amr_hydro_poisson_level(H.ctx, 1, 1.0, 1.7, 0, phi0, phi1)
+    phic = PS.poisson_root_periodic(O.lv[0].U[0], 1.0 / 32, 1.0)
+    fmask = cell_mask(O.lv[1].mask)
+    got = phi1.cpu().numpy()
+    for s, (x, y, z) in enumerate(H.corners(1)):
+        grid = PS.refined_patch_potential(phic, O.lv[1].U[0], fmask, O.lv[0].U[0], (x, y, z), 1.0 / 64, 1.0, 1.7, 0)
+        assert np.abs(got[s] - grid[5:13, 5:13, 5:13]).max() <= 1e-12 * np.abs(grid).max(), s
+    for bad in (dict(iters=-1), dict(acc_order=3), dict(level=2)):
+        kw = dict(level=1, iters=10, acc_order=2)
+        kw.update(bad)
+        with pytest.raises(A.AmrHydroError):
+            A.amr_hydro_poisson_level(H.ctx, kw["level"], 1.0, 1.7, kw["iters"], phi0, phi1, phi1, kw["acc_order"])
+    H.close()
+    g = UniformGrid((16, 16, 16))
+    g.upload(ics.blobs(16, seed=1))
+    _, acc = g.gravity(1.0, 2)
+    for kw in (dict(c_acc=-1.0), dict(order=3), dict(dt=float("nan"))):
+        args = dict(dt=-1.0, order=2, c_acc=0.0)
+        args.update(kw)
+        with pytest.raises(A.AmrHydroError):
+            g.step_gravity(1.0, acc, args["dt"], args["order"], args["c_acc"])
+    g.close()
