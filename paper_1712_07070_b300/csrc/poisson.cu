@@ -232,10 +232,20 @@ __global__ void k_root_out(const T *__restrict__ phi, const int32_t *__restrict_
 // real: the solve's precision (double, or float in the FP32-compute mode);
 // the parent level's potential and the states are read in FP64, the
 // potential and accelerations written in FP64
+// Rows of the grid padded to 24 values in FP32: the 8 same-colour cells of
+// a row sit 2 apart, a warp covers 4 rows, and with a row stride of 24
+// words rows j and j+2 (same colour parity) fall on disjoint banks, so a
+// sweep's loads are free of bank conflicts (a stride of 18 makes them
+// 2-way).  FP64 values take two banks each and keep the dense layout.
+template <typename real>
+struct SorGeo {
+    static constexpr int PX = sizeof(real) == 4 ? 24 : PN;
+};
+
 template <typename real>
 struct SorSmem {
-    real phi[PN][PN][PN];
-    real rho[PN][PN][PN];
+    real phi[PN][PN][SorGeo<real>::PX];
+    real rho[PN][PN][SorGeo<real>::PX];
     int nb[27], cnb[27];  // same-level patches around the patch, parent-level patches around its parent
     int off[3];           // the patch's lower corner relative to its parent's, in coarse cells (0 or 4)
 };
@@ -310,7 +320,8 @@ __global__ void __launch_bounds__(SOR_NT) k_sor_patches(
         for (int i = tid; i < PN3; i += SOR_NT) {
             const int gz = i / (PN * PN) - PB, a = (gz >> 1) + 4;
             const real *Y = rho_flat + a * PN * PN + i % (PN * PN);
-            phi_flat[i] = quad1<real>(Y[-PN * PN], Y[0], Y[PN * PN], (gz & 1) ? qp : qm);
+            S.phi[i / (PN * PN)][(i / PN) % PN][i % PN] =
+                quad1<real>(Y[-PN * PN], Y[0], Y[PN * PN], (gz & 1) ? qp : qm);
         }
         __syncthreads();
         // the source term dh^2 4 pi G rho on the grid, formed once per cell
@@ -318,7 +329,8 @@ __global__ void __launch_bounds__(SOR_NT) k_sor_patches(
             const int gx = i % PN - PB, gy = (i / PN) % PN - PB, gz = i / (PN * PN) - PB;  // fine, relative
             const int k = ((gx >> 3) + 1) + 3 * ((gy >> 3) + 1) + 9 * ((gz >> 3) + 1);
             const int s = S.nb[k];
-            rho_flat[i] = (real)(src_scale * (s >= 0 ? U[(int64_t)s * PSLOT + (gz & 7) * 64 + (gy & 7) * 8 + (gx & 7)]
+            S.rho[i / (PN * PN)][(i / PN) % PN][i % PN] =
+                (real)(src_scale * (s >= 0 ? U[(int64_t)s * PSLOT + (gz & 7) * 64 + (gy & 7) * 8 + (gx & 7)]
                                                       : coarse_at(Uc, PSLOT, S.cnb, S.off[0] + (gx >> 1),
                                                                   S.off[1] + (gy >> 1), S.off[2] + (gz >> 1))));
         }
