@@ -424,7 +424,7 @@ def bench_gravity(torch, args):
     g = UniformGrid((n, n, n), scheme={"gravity_bc": A.AMR_GRAVITY_ISOLATED})
     g.upload(torch.from_numpy(ics.turbulence(n, seed=1)))
     ms = timed(lambda: A.amr_hydro_poisson_root(g.ctx, 1.0, phi, acc, 2), 5)
-    out["root_fft_isolated"] = {"workload": "isolated FFT Poisson (zero-padded to 525^3) + 2-point accelerations, "
+    out["root_fft_isolated"] = {"workload": "isolated FFT Poisson (zero-padded to 540x525x525, pruned transforms) + 2-point accelerations, "
                                             "256^3 root level (cuFFT), FP64", "ms": ms, "value": n ** 3 / (ms * 1e-3)}
     g.close()
     for prec, tag in ((A.AMR_FP64, "fp64"), (A.AMR_FP32_ACC64, "fp32")):

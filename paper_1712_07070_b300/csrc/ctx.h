@@ -149,7 +149,7 @@ struct amr_hydro_ctx {
     amrh::DevBuf<unsigned long long> fb_count;
     // root-level Poisson solver: cuFFT plans (forward, inverse) and work arrays;
     // isolated gravity: the padded grid's sizes and the transformed kernel
-    long long fft_plan[2] = {0, 0};
+    long long fft_plan[4] = {0, 0, 0, 0};
     amrh::DevBuf<double> fft_real, fft_cplx, fft_green;
     int fft_m[3] = {0, 0, 0};
     bool fft_green_ready = false;
