@@ -85,7 +85,7 @@
  *   (iii) if that is still unphysical, first order dimensionally split: an
  *         x sweep of U^n, a y sweep of its result, a z sweep of that (each
  *         sweep V - (dt/dh)[F(V_i, V_i+1) - F(V_i-1, V_i)] along its axis);
- *   cells still unphysical after (iii) are counted, and the driver retries
+ *   cells still unphysical after (iii) are counted, and the step loop retries
  *   the whole step with dt x 0.8 (iv) down to a minimum dt (v).
  * The fluxes returned for the flux registers stay those of the scheme.
  *

@@ -12,7 +12,7 @@ them; the readings are in the oracle's header):
     Riemann solvers; every other cell is bitwise the plain step's;
   * (iii) where (ii) is unphysical too, the first-order split update (x, y,
     then z sweeps over the cell's 3x3x3 neighbourhood), written out here;
-  * (iv)-(v) the retry driver takes dt x 0.8^k and its result is the plain
+  * (iv)-(v) the retry loop takes dt x 0.8^k and its result is the plain
     step at that dt;
   * the Mach-2, contrast-100 blobs, which drive every scheme to negative
     pressure within a few steps, stay physical with the remedies.
