@@ -427,8 +427,9 @@ def bench_gravity(torch, args):
     out["root_fft_isolated"] = {"workload": "isolated FFT Poisson (zero-padded to 540x525x525, pruned transforms) + 2-point accelerations, "
                                             "256^3 root level (cuFFT), FP64", "ms": ms, "value": n ** 3 / (ms * 1e-3)}
     g.close()
-    for prec, tag in ((A.AMR_FP64, "fp64"), (A.AMR_FP32_ACC64, "fp32")):
-        g = UniformGrid((n, n, n), prec=prec)
+    for prec, tag, sch in ((A.AMR_FP64, "fp64", None), (A.AMR_FP32_ACC64, "fp32", None),
+                           (A.AMR_FP64, "ctu_fp64", {"scheme": A.AMR_SCHEME_CTU})):
+        g = UniformGrid((n, n, n), prec=prec, scheme=sch)
         g.upload(torch.from_numpy(ics.turbulence(n, seed=1)))
         state = {"acc": g.gravity(1.0, 2)[1]}
 
@@ -436,9 +437,9 @@ def bench_gravity(torch, args):
             state["acc"] = g.step_gravity(1.0, state["acc"], -1.0, 2)[1]
 
         ms = timed(coupled, 5)
-        out[f"coupled_{tag}"] = {"workload": "hydro + self-gravity step (MUSCL-Hancock + PLM + HLLC with the "
-                                             "gravity predictor, FFT potential of the predicted density, "
-                                             f"corrector), 256^3 turbulence, {tag}", "ms": ms,
+        out[f"coupled_{tag}"] = {"workload": f"hydro + self-gravity step ({'CTU' if sch else 'MUSCL-Hancock'} "
+                                             "+ PLM + HLLC with the gravity predictor, FFT potential of the "
+                                             f"predicted density, corrector), 256^3 turbulence, {tag}", "ms": ms,
                                  "value": n ** 3 / (ms * 1e-3)}
         g.close()
     for prec, tag in ((A.AMR_FP64, ""), (A.AMR_FP32_ACC64, "_fp32")):

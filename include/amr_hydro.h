@@ -399,8 +399,9 @@ amr_status amr_hydro_poisson_level_t(amr_hydro_ctx *ctx, int level, double G, do
 /*
  * One hydro step of a single-level periodic grid coupled to self-gravity
  * (section 2.3, the operator-unsplit predictor-corrector after Muller &
- * Steinmetz 1995): the MUSCL-Hancock step whose half step also adds
- * (dt/2) (0, rho g, m.g) of each face state (g = acc_n, the acceleration at
+ * Steinmetz 1995): the MUSCL-Hancock (or CTU) step whose half step also adds
+ * (dt/2) (0, rho g, m.g) of each reconstructed face state (CTU: after the
+ * normal predictor, before the transverse correction; g = acc_n, the acceleration at
  * t^n, [n_patches][3][8][8][8]); the FFT potential phi_new and acceleration
  * acc_new of the predicted density (as amr_hydro_poisson_root); then
  * m^{n+1} = m* + (dt/2)(rho^n g^n + rho^{n+1} g^{n+1}) and
@@ -408,7 +409,7 @@ amr_status amr_hydro_poisson_level_t(amr_hydro_ctx *ctx, int level, double G, do
  * step's acc_n.  dt < 0: the device's Eq. (CFL2) dt, and with c_acc > 0 the
  * smaller of it and Eq. (acc), c_acc (dh / max|a|)^(1/2) over acc_n's values
  * (c_acc = 0: Eq. (CFL2) alone; negative or non-finite: AMR_E_INVAL).
- * MUSCL-Hancock + PLM
+ * MUSCL-Hancock or CTU with PLM
  * without dual energy, the remedies or the level retry; AMR_E_INVAL otherwise or with
  * refined levels.  Asynchronous on the context's stream.
  */

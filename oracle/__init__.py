@@ -304,16 +304,18 @@ def step_dual(U, S, dh, dt, gamma, xi=1e-2):
 
 
 def step_gravity_predictor(U, g, dh, dt, gamma):
-    """The gravity coupling's predictor: the MUSCL-Hancock step with
-    (dt/2)(0, rho g, m.g) of each face state in the half step; g [3][...]
-    the acceleration at t^n.  Returns (U*, nbad)."""
+    """The gravity coupling's predictor: the MUSCL-Hancock (or, with the CTU
+    scheme selected, the CTU) step with (dt/2)(0, rho g, m.g) of each
+    reconstructed face state added to its predicted state (CTU: after the
+    normal predictor, before the transverse correction); g [3][...] the
+    acceleration at t^n.  Returns (U*, nbad)."""
     U = np.ascontiguousarray(U, dtype=np.float64)
     g = np.ascontiguousarray(g, dtype=np.float64)
     nz, ny, nx = U.shape[1:]
     Un = np.empty_like(U)
     nbad = lib().or_step_gravity_predictor(_ptr(U), _ptr(g), _ptr(Un), nx, ny, nz, dh, dt, gamma)
     if nbad < 0:
-        raise ValueError("the gravity coupling is built for MUSCL-Hancock only")
+        raise ValueError("the gravity coupling is built for MUSCL-Hancock and CTU")
     return Un, nbad
 
 

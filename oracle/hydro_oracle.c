@@ -187,6 +187,19 @@ static int or_limiter_id = 0, or_riemann_id = 0, or_vl = 0, or_ctu = 0, or_ppm =
 /* gravity predictor: the cell-centred acceleration g^n [3][cell] of the
  * step in progress (or_step_gravity_predictor) */
 static const double *or_grav_g = NULL;
+
+/* Gravity in the half step of cell i: + (dt/2) (0, rho g, m.g) of each of
+ * its six reconstructed face states Uf, added to the predicted states FS
+ * (MUSCL-Hancock after the Hancock increment; CTU after the normal
+ * predictor, before the transverse correction). */
+static void or_grav_faces(double *FS, double Uf[6][NV], const double *gfield, int64_t i, int64_t n, double dt) {
+    double g[3];
+    for (int d = 0; d < 3; d++) g[d] = gfield[(int64_t)d * n + i];
+    for (int f = 0; f < 6; f++) {
+        for (int d = 0; d < 3; d++) FS[((int64_t)f * NV + 1 + d) * n + i] += 0.5 * dt * (Uf[f][0] * g[d]);
+        FS[((int64_t)f * NV + 4) * n + i] += 0.5 * dt * (Uf[f][1] * g[0] + Uf[f][2] * g[1] + Uf[f][3] * g[2]);
+    }
+}
 /* dual energy: the entropy fields of the step in progress (or_step_dual) */
 static const double *or_de_S = NULL;
 static double *or_de_Snew = NULL, or_de_xi = 0.0;
@@ -754,6 +767,7 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
                                 FS[((int64_t)(2 * d + s2) * NV + v) * n + i] =
                                     Uf[2 * d + s2][v] + 0.5 * dt / dh * (Fm[v] - Fp[v]);
                     }
+                    if (or_grav_g) or_grav_faces(FS, Uf, or_grav_g, i, n, dt);
                     continue;
                 }
                 double inc[NV] = {0, 0, 0, 0, 0};
@@ -766,16 +780,7 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
                 for (int f = 0; f < 6; f++)
                     for (int v = 0; v < NV; v++)
                         FS[((int64_t)f * NV + v) * n + i] = Uf[f][v] + 0.5 * dt / dh * inc[v];
-                if (or_grav_g) { /* gravity in the half step: + (dt/2) (0, rho g, m.g) of each face state */
-                    double g[3];
-                    for (int d = 0; d < 3; d++) g[d] = or_grav_g[(int64_t)d * n + i];
-                    for (int f = 0; f < 6; f++) {
-                        for (int d = 0; d < 3; d++)
-                            FS[((int64_t)f * NV + 1 + d) * n + i] += 0.5 * dt * (Uf[f][0] * g[d]);
-                        FS[((int64_t)f * NV + 4) * n + i] +=
-                            0.5 * dt * (Uf[f][1] * g[0] + Uf[f][2] * g[1] + Uf[f][3] * g[2]);
-                    }
-                }
+                if (or_grav_g) or_grav_faces(FS, Uf, or_grav_g, i, n, dt);
                 if (or_de_S) { /* the entropy scalar: face values s = rho_f q_f, Hancock step */
                     double sf[6], incs = 0.0;
                     for (int d = 0; d < 3; d++) {
@@ -919,7 +924,7 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
  * count, or -1 for a scheme other than MUSCL-Hancock. */
 int64_t or_step_gravity_predictor(const double *U, const double *g, double *Unew, int nx, int ny, int nz, double dh,
                                   double dt, double gamma) {
-    if (or_vl || or_ctu) return -1;
+    if (or_vl) return -1;
     or_grav_g = g;
     int64_t nbad = or_step_periodic_fx(U, Unew, nx, ny, nz, dh, dt, gamma, NULL);
     or_grav_g = NULL;

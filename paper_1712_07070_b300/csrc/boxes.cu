@@ -27,7 +27,8 @@ namespace {
 bool configured = false;
 
 // Kernel instances: key K = MODE + 3 STAGE, as for the level step kernel.
-using BoxKeys = std::make_integer_sequence<int, 3 * N_STAGES>;
+// the box batch runs the plain stages only (no dual energy, no gravity)
+using BoxKeys = std::make_integer_sequence<int, 3 * ST_MH_DE>;
 
 template <typename real, int K>
 amr_status set_box_smem() {

@@ -53,10 +53,13 @@ struct CtuSmem {
 
 // Normal predictor along D of tile cell (x, y) on plane zc: the reconstructed
 // (PLM or PPM) face states as conserved states, each advanced by
-// (dt/2dh) [F_D(U_-) - F_D(U_+)].
-template <typename real, int D, typename SM>
+// (dt/2dh) [F_D(U_-) - F_D(U_+)]; with GRAV (the gravity coupling's
+// predictor) each also gains (dt/2) (0, rho_f ga, m_f . ga) of its
+// reconstructed state, ga the cell's acceleration at t^n.
+template <typename real, int D, bool GRAV = false, typename SM>
 __device__ __forceinline__ void ctu_predict(const SM &S, int x, int y, int zc, real dtdh_half, const Gas<real> &g,
-                                            real um[NV], real up[NV]) {
+                                            real um[NV], real up[NV], const real *ga = nullptr,
+                                            real dt_half = real(0)) {
     using G = typename SM::Geo;
     real wm[NV], wp[NV], fm[NV], fp[NV];
     face_values<real, D, (G::S == 2)>(S, x + G::OX, y + G::OY, zc, g, wm, wp);
@@ -64,11 +67,29 @@ __device__ __forceinline__ void ctu_predict(const SM &S, int x, int y, int zc, r
     w2u(wp, up, g);
     phys_flux<D>(wm, um, fm);
     phys_flux<D>(wp, up, fp);
+    if constexpr (GRAV) {
+        real sm[NV], sp[NV];
+        sm[0] = sp[0] = real(0);
 #pragma unroll
-    for (int v = 0; v < NV; v++) {
-        const real inc = dtdh_half * (fm[v] - fp[v]);
-        um[v] += inc;
-        up[v] += inc;
+        for (int d = 0; d < 3; d++) {
+            sm[1 + d] = um[0] * ga[d];
+            sp[1 + d] = up[0] * ga[d];
+        }
+        sm[4] = um[1] * ga[0] + um[2] * ga[1] + um[3] * ga[2];
+        sp[4] = up[1] * ga[0] + up[2] * ga[1] + up[3] * ga[2];
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            const real inc = dtdh_half * (fm[v] - fp[v]);
+            um[v] = (um[v] + inc) + dt_half * sm[v];
+            up[v] = (up[v] + inc) + dt_half * sp[v];
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            const real inc = dtdh_half * (fm[v] - fp[v]);
+            um[v] += inc;
+            up[v] += inc;
+        }
     }
 }
 
@@ -133,7 +154,7 @@ __device__ __forceinline__ void ctu_high_faces(SM &S, const StepParams &P, doubl
 
 // The CTU step of a run of len patch groups stacked in z (len = 1: one
 // group); arguments as for step_run.
-template <typename real, typename SM>
+template <typename real, bool GRAV, typename SM>
 __device__ __forceinline__ void ctu_run(SM &S, const StepParams &P, const int32_t *runs, int off,
                                         int first, int len, double dt, const Gas<real> &g, real &smax_r,
                                         unsigned &nbad) {
@@ -148,6 +169,7 @@ __device__ __forceinline__ void ctu_run(SM &S, const StepParams &P, const int32_
     const double dtdh = dt / P.dh;
     const real dtdh_r = (real)dtdh;
     const real dtdh_half = (real)(0.5 * dt / P.dh);
+    const real dt_half = (real)(0.5 * dt);  // the gravity predictor's source factor
     const int Z = GE * len;
     int gcur = run_group(runs, off, first, 0), gprev = gcur, gnext = gcur;
     unsigned cfm = 0;  // bit s: the group in table slot s touches a coarse-fine register
@@ -217,7 +239,9 @@ __device__ __forceinline__ void ctu_run(SM &S, const StepParams &P, const int32_
 #pragma unroll
         for (int v = 0; v < NV; v++) nlo[v] = nhi[v] = dz[v] = rdz[v] = real(0);
         if (z < Z) {
-            ctu_predict<real, 2>(S, cx, cy, z + 1, dtdh_half, g, nlo, nhi);
+            real ga[3];
+            if constexpr (GRAV) grav_at(S, P, kz & 1, cx, cy, zl + 1, ga);
+            ctu_predict<real, 2, GRAV>(S, cx, cy, z + 1, dtdh_half, g, nlo, nhi, ga, dt_half);
             if (z >= -1) {
                 real f[NV];
                 face_flux<2>(pz_hi, nlo, f, g);
@@ -229,7 +253,8 @@ __device__ __forceinline__ void ctu_run(SM &S, const StepParams &P, const int32_
             }
             if (has_ring) {
                 real rlo[NV], rhi[NV];
-                ctu_predict<real, 2>(S, rx, ry, z + 1, dtdh_half, g, rlo, rhi);
+                if constexpr (GRAV) grav_at(S, P, kz & 1, rx, ry, zl + 1, ga);
+                ctu_predict<real, 2, GRAV>(S, rx, ry, z + 1, dtdh_half, g, rlo, rhi, ga, dt_half);
                 if (z >= -1) {
                     real f[NV];
                     face_flux<2>(rz_hi, rlo, f, g);
@@ -249,16 +274,17 @@ __device__ __forceinline__ void ctu_run(SM &S, const StepParams &P, const int32_
             for (int i = tid; i < 2 * CE * CE; i += NT) {
                 const int D = i >= CE * CE ? 1 : 0, j = i - D * CE * CE;
                 const int x = j % CE - 1, y = j / CE - 1;
-                real um[NV], up[NV];
+                real um[NV], up[NV], ga[3];
+                if constexpr (GRAV) grav_at(S, P, kz & 1, x, y, zl, ga);
                 if (D == 0) {
-                    ctu_predict<real, 0>(S, x, y, z, dtdh_half, g, um, up);
+                    ctu_predict<real, 0, GRAV>(S, x, y, z, dtdh_half, g, um, up, ga, dt_half);
 #pragma unroll
                     for (int v = 0; v < NV; v++) {
                         S.XS[0][v][y + 1][x + 1] = um[v];
                         S.XS[1][v][y + 1][x + 1] = up[v];
                     }
                 } else {
-                    ctu_predict<real, 1>(S, x, y, z, dtdh_half, g, um, up);
+                    ctu_predict<real, 1, GRAV>(S, x, y, z, dtdh_half, g, um, up, ga, dt_half);
 #pragma unroll
                     for (int v = 0; v < NV; v++) {
                         S.YS[0][v][y + 1][x + 1] = um[v];

@@ -199,8 +199,8 @@ amr_status advance_once(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphy
         int lo, hi;
         scheme_stages(c->prm.scheme, c->prm.recon, c->prm.dual_energy, lo, hi);
         P.stage = lo;  // MUSCL-Hancock (PLM, PPM, dual energy) or CTU: the one launch
-        if (acc_n) {
-            P.stage = ST_MH_GRAV;
+        if (acc_n) {  // the gravity coupling's predictor
+            P.stage = c->prm.scheme == AMR_SCHEME_CTU ? ST_CTU_GRAV : ST_MH_GRAV;
             P.acc_n = acc_n;
         }
     }

@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(SOR_NT) k_sor_patches(
 template <typename real>
 __global__ void k_grav_correct(double *__restrict__ U1, const double *__restrict__ U0,
                                const double *__restrict__ g0, const double *__restrict__ g1, int64_t n_cells,
-                               double dt_in, const double *__restrict__ time_rec, double gamma,
+                               double dt_in, const double *__restrict__ time_rec, double gamma, int cfl1,
                                unsigned long long *smax, unsigned long long *n_bad) {
     const double dt = dt_in >= 0.0 ? dt_in : time_rec[0];
     const double h = 0.5 * dt;
@@ -421,7 +421,7 @@ __global__ void k_grav_correct(double *__restrict__ U1, const double *__restrict
         real u[NV] = {to_real<real>(r1), to_real<real>(m1[0]), to_real<real>(m1[1]), to_real<real>(m1[2]),
                       to_real<real>(E1)};
         bool ok;
-        const real sp = cfl_speed(u, gas, ok, false);
+        const real sp = cfl_speed(u, gas, ok, cfl1 != 0);
         if (!ok) bad++;
         else if ((double)sp > m) m = (double)sp;
     }
@@ -682,8 +682,8 @@ amr_status amr_hydro_advance_gravity(amr_hydro_ctx *c, double dt, double G, cons
     if (!(c_acc >= 0.0) || c_acc > 1e300) return AMR_E_INVAL;
     if (!(dt >= 0.0) && !(dt < 0.0)) return AMR_E_INVAL;
     if (c->prm.lmax > 0 && c->lv[1].n_patches) return AMR_E_INVAL;  // single-level grids
-    if (c->prm.scheme != AMR_SCHEME_MH || c->prm.recon != AMR_RECON_PLM || c->prm.dual_energy || c->prm.fallback ||
-        c->prm.dt_min > 0.0)
+    if ((c->prm.scheme != AMR_SCHEME_MH && c->prm.scheme != AMR_SCHEME_CTU) || c->prm.recon != AMR_RECON_PLM ||
+        c->prm.dual_energy || c->prm.fallback || c->prm.dt_min > 0.0)
         return AMR_E_INVAL;
     Level &L = c->lv[0];
     if (!L.n_patches || L.n_ghost) return AMR_E_INVAL;
@@ -699,12 +699,13 @@ amr_status amr_hydro_advance_gravity(amr_hydro_ctx *c, double dt, double G, cons
         (st = cuda_fail(cudaMemsetAsync(nb, 0, 8, c->stream), "memset")))
         return st;
     const int64_t n_cells = (int64_t)L.n_patches * PV;
+    const int cfl1 = c->prm.scheme == AMR_SCHEME_CTU;  // Eq. (CFL1) for CTU, else Eq. (CFL2)
     if (c->prm.prec == AMR_FP64)
         k_grav_correct<double><<<c->n_sm * 8, 256, 0, c->stream>>>(L.U[L.cur], L.U[1 - L.cur], acc_n, acc_new,
-                                                                    n_cells, dt, c->dtbuf.p, c->prm.gamma, sm, nb);
+                                                                    n_cells, dt, c->dtbuf.p, c->prm.gamma, cfl1, sm, nb);
     else
         k_grav_correct<float><<<c->n_sm * 8, 256, 0, c->stream>>>(L.U[L.cur], L.U[1 - L.cur], acc_n, acc_new,
-                                                                   n_cells, dt, c->dtbuf.p, c->prm.gamma, sm, nb);
+                                                                   n_cells, dt, c->dtbuf.p, c->prm.gamma, cfl1, sm, nb);
     if ((st = cuda_fail(cudaGetLastError(), "k_grav_correct"))) return st;
     L.speed_valid = true;
     return AMR_OK;

@@ -48,9 +48,12 @@ constexpr int ST_MH_PPM = 4;   // MUSCL-Hancock step with PPM reconstruction
 constexpr int ST_CTU_PPM = 5;  // CTU step with PPM reconstruction
 constexpr int ST_MH_DE = 6;    // MUSCL-Hancock step with the dual-energy formalism
 constexpr int ST_MH_GRAV = 7;  // MUSCL-Hancock predictor of the gravity coupling
-constexpr int N_STAGES = 8;
+constexpr int ST_CTU_GRAV = 8;  // CTU (PLM) predictor of the gravity coupling
+constexpr int N_STAGES = 9;
 __host__ __device__ constexpr bool stage_ppm(int st) { return st == ST_MH_PPM || st == ST_CTU_PPM; }
-__host__ __device__ constexpr bool stage_ctu(int st) { return st == ST_CTU || st == ST_CTU_PPM; }
+__host__ __device__ constexpr bool stage_ctu(int st) {
+    return st == ST_CTU || st == ST_CTU_PPM || st == ST_CTU_GRAV;
+}
 
 // Tile geometry for NG ghost cells per side (2: PLM, 3: PPM, whose face
 // values reach two cells).  Rows y = -NG .. 15+NG; columns are staged in
@@ -904,7 +907,8 @@ template <typename real, int STAGE>
 __device__ __forceinline__ void stage_run(StageSmem<real, STAGE> &S, const StepParams &P, const int32_t *runs,
                                           int off, int first, int len, double dt, const Gas<real> &g, real &smax_r,
                                           unsigned &nbad) {
-    if constexpr (stage_ctu(STAGE)) ctu_run<real>(S, P, runs, off, first, len, dt, g, smax_r, nbad);
+    if constexpr (stage_ctu(STAGE))
+        ctu_run<real, STAGE == ST_CTU_GRAV>(S, P, runs, off, first, len, dt, g, smax_r, nbad);
     else step_run<real, STAGE>(S, P, runs, off, first, len, dt, g, smax_r, nbad);
 }
 

@@ -169,11 +169,48 @@ def test_coupled_gravity_step(prec, tol, c_acc, order):
 def test_coupled_gravity_rejects_other_schemes():
     import torch
     from paper_1712_07070_b300.uniform import UniformGrid
-    g = UniformGrid((16, 16, 16), scheme={"scheme": A.AMR_SCHEME_CTU})
-    g.upload(ics.blobs(16, seed=1))
-    acc = torch.zeros((g.n_patches, 3, 8, 8, 8), dtype=torch.float64, device="cuda")
-    with pytest.raises(A.AmrHydroError):
-        g.step_gravity(1.0, acc)
+    for sch in ({"scheme": A.AMR_SCHEME_VL}, {"recon": A.AMR_RECON_PPM}):
+        g = UniformGrid((16, 16, 16), scheme=sch)
+        g.upload(ics.blobs(16, seed=1))
+        acc = torch.zeros((g.n_patches, 3, 8, 8, 8), dtype=torch.float64, device="cuda")
+        with pytest.raises(A.AmrHydroError):
+            g.step_gravity(1.0, acc)
+        g.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(A.AMR_FP64, 1e-12), (A.AMR_FP32_ACC64, 5e-5)])
+def test_coupled_gravity_step_ctu(prec, tol):
+    """The coupling with the CTU scheme (the half-step source on the normal-
+    predicted face states; Eq. (CFL1) time step taken on the device in
+    FP64), three steps against the oracle; FP32 compute at the CTU scheme's
+    derived per-step bound."""
+    import oracle
+    from paper_1712_07070_b300.uniform import UniformGrid
+    n, G = 32, 2.0
+    U = gravity_ics(n, 5)
+    g = UniformGrid((n, n, n), prec=prec, scheme={"scheme": A.AMR_SCHEME_CTU})
+    g.upload(U)
+    dh = 1.0 / n
+    _, acc = g.gravity(G, 2)
+    gref = PS.accel_periodic(PS.poisson_root_periodic(U[0], dh, G), dh, 2)
+    t = 0.0
+    with oracle.scheme(ctu=True):
+        for _ in range(3):
+            dt = oracle.dt_cfl(U, G53, 0.5, dh)
+            phi, acc = g.step_gravity(G, acc, -1.0 if prec == A.AMR_FP64 else dt, 2)
+            U, phir, gref, nbad = PS.step_gravity(U, gref, dh, dt, G53, G, 2)
+            assert nbad == 0
+            t += dt
+            assert g.time() == pytest.approx(t, rel=1e-12)
+            V = g.download()
+            scale = np.abs(U).reshape(5, -1).max(axis=1)
+            err = (np.abs(V - U).reshape(5, -1).max(axis=1) / scale).max()
+            assert err <= tol, err
+            if prec == A.AMR_FP32_ACC64:  # continue from the GPU's own state
+                U = V
+                gref = PS.accel_periodic(PS.poisson_root_periodic(U[0], dh, G), dh, 2)
+                g.upload(U)
+                _, acc = g.gravity(G, 2)
     g.close()
 
 

@@ -262,3 +262,24 @@ def test_time_interpolated_boundary_is_affine():
     b = PS.refined_patch_potential(B_, *args)
     assert np.abs(mid - ((1 - w) * a + w * b)).max() <= 1e-13 * np.abs(mid).max()
     assert np.array_equal(PS.time_interp(A_, B_, 0.0), A_) and np.array_equal(PS.time_interp(A_, B_, 1.0), B_)
+
+
+def test_ctu_predictor_with_zero_field_is_the_plain_ctu_step():
+    """The CTU variant of the coupling's predictor (the half-step source on
+    the normal-predicted states) reduces to the plain CTU step for g = 0,
+    and for a uniform state in a constant field, as the MUSCL-Hancock one,
+    leaves the state unchanged (the source enters only through the fluxes
+    of equal face states)."""
+    import oracle
+    from paper_1712_07070_b300 import ics
+    U = ics.sod_noise(16, seed=6, gamma=G53)
+    with oracle.scheme(ctu=True):
+        dt = oracle.dt_cfl(U, G53, 0.5, 1 / 16)
+        a, _ = oracle.step_periodic(U, 1 / 16, dt, G53)
+        b, _ = oracle.step_gravity_predictor(U, np.zeros((3,) + U.shape[1:]), 1 / 16, dt, G53)
+        assert np.array_equal(a, b)
+        V = np.zeros((5, 4, 4, 4))
+        V[0], V[1], V[4] = 1.3, 0.2, 2.0
+        g = np.broadcast_to(np.array([0.3, 0.5, -0.2])[:, None, None, None], (3, 4, 4, 4)).copy()
+        c, _ = oracle.step_gravity_predictor(V, g, 1 / 4, 0.01, G53)
+        assert np.array_equal(c, V)
