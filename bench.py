@@ -47,7 +47,7 @@ FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # DRAM bytes (read+write) per cell update of one k_hydro_step launch from an
 # ncu capture, keyed by the hash of the kernel sources it was taken on.
-TRAFFIC_BYTES_PER_CELL = {"f64:c0be775159612700": 86.9, "f32:c0be775159612700": 92.3}
+TRAFFIC_BYTES_PER_CELL = {"f64:d834820ed8bea972": 86.7, "f32:d834820ed8bea972": 92.5}
 KERNEL_SOURCES = ("paper_1712_07070_b300/csrc/step_kernel.cuh", "paper_1712_07070_b300/csrc/hydro_math.cuh")
 
 
