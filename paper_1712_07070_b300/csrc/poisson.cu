@@ -1,7 +1,11 @@
 // poisson.cu -- GAMER-2 gravity solvers (section 2.3; section 3.1 and
-// Appendix A for the refined levels): the root level's periodic potential by
-// FFT, the refined levels' potential by SOR on an 18^3 grid per patch, and
-// the cell-centred accelerations.
+// Appendix A for the refined levels): the root level's periodic or isolated
+// potential by FFT, the refined levels' potential by SOR on an 18^3 grid per
+// patch (the parent potential interpolated in space and, optionally, in
+// time), the cell-centred accelerations, and the corrector of the
+// predictor-corrector coupling of gravity to the hydro step (the predictor
+// is the step kernel's ST_MH_GRAV / ST_CTU_GRAV instance).  FP64, or FP32
+// transforms and SOR in the FP32-compute mode.
 //
 // Root level: the 7-point discrete Poisson equation
 //     sum_d (phi_{i+e_d} - 2 phi_i + phi_{i-e_d}) / dh^2 = 4 pi G (rho_i - <rho>)
@@ -9,8 +13,13 @@
 // lambda_k = -2 sum_d (1 - cos(2 pi k_d / N_d)) and phi_0 = 0 (cuFFT D2Z,
 // one scaling kernel, Z2D).
 //
+// Isolated root level: every cell a point mass, the pairwise potential by a
+// zero-padded FFT convolution with the kernel -dh^2 / |offset| (details at
+// root_isolated).
+//
 // Refined levels: one CTA per patch holds the potential and the density of
-// the patch's (8 + 2*5)^3 grid in shared memory (93 KB: two CTAs per SM).
+// the patch's (8 + 2*5)^3 grid in shared memory (93 KB FP64: two CTAs per
+// SM; 62 KB FP32 with padded rows: three).
 // The density is the level's where a same-level patch holds the cell, else
 // the parent level's cell (injection); the potential's outermost layer (held
 // fixed) and initial guess come from the parent level's potential by
