@@ -384,3 +384,27 @@ def test_root_solves_at_the_benchmark_size():
     want = PS.pairwise_potential(U0[0], dh, G, points=pts)
     got = np.array([ph[p] for p in pts])
     assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("prec", [A.AMR_FP64, A.AMR_FP32_ACC64])
+def test_coupled_step_at_the_benchmark_size(prec):
+    """Two 256^3 hydro + self-gravity steps as the benchmark runs them (device
+    dt): mass is conserved to round-off (gravity changes no density and the
+    fluxes are conservative), the time record advances by the device's CFL
+    steps, and the new acceleration is the root solve of the new state."""
+    from paper_1712_07070_b300.uniform import UniformGrid
+    n, G = 256, 1.0
+    U0 = ics.turbulence(n, seed=1)
+    g = UniformGrid((n, n, n), prec=prec)
+    g.upload(U0)
+    m0 = U0[0].sum()
+    _, acc = g.gravity(G, 2)
+    for _ in range(2):
+        _, acc = g.step_gravity(G, acc, -1.0, 2)
+    V = g.download()
+    assert abs(V[0].sum() - m0) <= 1e-12 * m0
+    assert np.isfinite(V).all() and V[0].min() > 0
+    assert g.time() > 0
+    _, acc2 = g.gravity(G, 2)
+    assert np.array_equal(acc.cpu().numpy(), acc2.cpu().numpy())
+    g.close()
