@@ -406,7 +406,7 @@ amr_status amr_hydro_poisson_level_t(amr_hydro_ctx *ctx, int level, double G, do
  * acc_new of the predicted density (as amr_hydro_poisson_root); then
  * m^{n+1} = m* + (dt/2)(rho^n g^n + rho^{n+1} g^{n+1}) and
  * E^{n+1} = E* + (dt/2)(m^n.g^n + m^{n+1}.g^{n+1}).  acc_new is the next
- * step's acc_n.  dt < 0: the device's Eq. (CFL2) dt, and with c_acc > 0 the
+ * step's acc_n; the two arrays must not overlap (AMR_E_INVAL).  dt < 0: the device's Eq. (CFL2) dt, and with c_acc > 0 the
  * smaller of it and Eq. (acc), c_acc (dh / max|a|)^(1/2) over acc_n's values
  * (c_acc = 0: Eq. (CFL2) alone; negative or non-finite: AMR_E_INVAL).
  * MUSCL-Hancock or CTU with PLM

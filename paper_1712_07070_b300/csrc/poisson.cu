@@ -693,6 +693,11 @@ amr_status amr_hydro_advance_gravity(amr_hydro_ctx *c, double dt, double G, cons
                                      double *acc_new, int acc_order, double c_acc) {
     if (!c || !acc_n || !phi_new || !acc_new || (acc_order != 2 && acc_order != 4)) return AMR_E_INVAL;
     if (!(c_acc >= 0.0) || c_acc > 1e300) return AMR_E_INVAL;
+    {  // the corrector reads g^n after the root solve has written g^{n+1}: no overlap
+        const int64_t bytes = (int64_t)c->lv[0].n_patches * 3 * PV * (int64_t)sizeof(double);
+        const char *a = reinterpret_cast<const char *>(acc_n), *b = reinterpret_cast<const char *>(acc_new);
+        if (a < b + bytes && b < a + bytes) return AMR_E_INVAL;
+    }
     if (!(dt >= 0.0) && !(dt < 0.0)) return AMR_E_INVAL;
     if (c->prm.lmax > 0 && c->lv[1].n_patches) return AMR_E_INVAL;  // single-level grids
     if ((c->prm.scheme != AMR_SCHEME_MH && c->prm.scheme != AMR_SCHEME_CTU) || c->prm.recon != AMR_RECON_PLM ||

@@ -345,6 +345,9 @@ def test_gravity_edge_cases():
         args.update(kw)
         with pytest.raises(A.AmrHydroError):
             g.step_gravity(1.0, acc, args["dt"], args["order"], args["c_acc"])
+    phi = torch.zeros((g.n_patches, 8, 8, 8), dtype=torch.float64, device="cuda")
+    with pytest.raises(A.AmrHydroError):  # the new acceleration may not overwrite g^n
+        A.amr_hydro_advance_gravity(g.ctx, -1.0, 1.0, acc, phi, acc, 2)
     g.close()
 
 
