@@ -380,7 +380,8 @@ amr_status amr_hydro_poisson_root(amr_hydro_ctx *ctx, double G, double *phi, dou
  * ([n_patches][8][8][8]) and, if acc is not NULL, -grad phi into acc
  * ([n_patches][3][8][8][8]) by acc_order = 2 or 4 point central differences.
  * Asynchronous on the context's stream.  FP64, or FP32 in the FP32-compute
- * mode (inputs and outputs FP64).
+ * mode (inputs and outputs FP64).  phi and acc may not overlap each other or
+ * phi_coarse (AMR_E_INVAL).
  */
 amr_status amr_hydro_poisson_level(amr_hydro_ctx *ctx, int level, double G, double omega, int iters,
                                    const double *phi_coarse, double *phi, double *acc, int acc_order);

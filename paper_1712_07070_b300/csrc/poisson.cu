@@ -159,6 +159,11 @@ int smooth7(int n) {
     }
 }
 
+// [a, a + na) and [b, b + nb) (doubles) overlap
+bool overlaps(const double *a, int64_t na, const double *b, int64_t nb) {
+    return a && b && a < b + nb && b < a + na;
+}
+
 int smooth7_even(int n) {
     for (n = smooth7(n); n % 2; n = smooth7(n + 1)) {
     }
@@ -738,6 +743,11 @@ static amr_status poisson_level(amr_hydro_ctx *c, int level, double G, double om
     Level &L = c->lv[level], &C = c->lv[level - 1];
     if (!L.n_patches) return AMR_OK;
     if (!L.d_parent || !C.n_patches) return AMR_E_INVAL;
+    // the outputs are written while other CTAs still read the parent's potential
+    const int64_t nf = (int64_t)L.n_patches * PV, ncp = (int64_t)C.n_patches * PV;
+    if (overlaps(phi, nf, phi_c0, ncp) || overlaps(phi, nf, phi_c1, ncp) || overlaps(acc, 3 * nf, phi_c0, ncp) ||
+        overlaps(acc, 3 * nf, phi_c1, ncp) || overlaps(phi, nf, acc, 3 * nf))
+        return AMR_E_INVAL;
     // FP64, or FP32 in the FP32-compute mode (half the shared memory: 4 CTAs per SM)
     return c->prm.prec == AMR_FP64
                ? launch_sor<double>(c, L, C, level, G, omega, iters, phi_c0, phi_c1, w, phi, acc, acc_order)

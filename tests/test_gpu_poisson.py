@@ -331,6 +331,8 @@ def test_gravity_edge_cases():
     for s, (x, y, z) in enumerate(H.corners(1)):
         grid = PS.refined_patch_potential(phic, O.lv[1].U[0], fmask, O.lv[0].U[0], (x, y, z), 1.0 / 64, 1.0, 1.7, 0)
         assert np.abs(got[s] - grid[5:13, 5:13, 5:13]).max() <= 1e-12 * np.abs(grid).max(), s
+    with pytest.raises(A.AmrHydroError):  # the output may not overwrite the parent potential
+        A.amr_hydro_poisson_level(H.ctx, 1, 1.0, 1.7, 10, phi0, phi0)
     for bad in (dict(iters=-1), dict(acc_order=3), dict(level=2)):
         kw = dict(level=1, iters=10, acc_order=2)
         kw.update(bad)
