@@ -137,10 +137,14 @@ __global__ void k_green(C *__restrict__ F, const double *__restrict__ lam1, int 
             if (row == 0 && kx == 0) {
                 v.x = 0;
                 v.y = 0;
+            } else if constexpr (sizeof(v.x) == sizeof(float)) {  // FP32 transforms: an FP32 division
+                const float f = (float)scale / (float)(lam1[kx] + lyz);
+                v.x *= f;
+                v.y *= f;
             } else {
                 const double f = scale / (lam1[kx] + lyz);
-                v.x = (decltype(v.x))(v.x * f);
-                v.y = (decltype(v.y))(v.y * f);
+                v.x *= f;
+                v.y *= f;
             }
             Fr[kx] = v;
         }
