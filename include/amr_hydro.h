@@ -407,7 +407,8 @@ amr_status amr_hydro_poisson_level_t(amr_hydro_ctx *ctx, int level, double G, do
  * acc_new of the predicted density (as amr_hydro_poisson_root); then
  * m^{n+1} = m* + (dt/2)(rho^n g^n + rho^{n+1} g^{n+1}) and
  * E^{n+1} = E* + (dt/2)(m^n.g^n + m^{n+1}.g^{n+1}).  acc_new is the next
- * step's acc_n; the two arrays must not overlap (AMR_E_INVAL).  dt < 0: the device's Eq. (CFL2) dt, and with c_acc > 0 the
+ * step's acc_n; acc_n, phi_new, acc_new and the level's two state buffers
+ * must not overlap one another (AMR_E_INVAL).  dt < 0: the device's Eq. (CFL2) dt, and with c_acc > 0 the
  * smaller of it and Eq. (acc), c_acc (dh / max|a|)^(1/2) over acc_n's values
  * (c_acc = 0: Eq. (CFL2) alone; negative or non-finite: AMR_E_INVAL).
  * MUSCL-Hancock or CTU with PLM
@@ -454,7 +455,9 @@ const char *amr_hydro_strerror(amr_status s);
  *                  rho<=0 or P<=0
  * Asynchronous on cuda_stream.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) and configures the kernel;
- * make that first call before any stream capture.  Every call shares the
+ * make that first call before any stream capture.  The address is kept for
+ * the life of the process: calls after cudaDeviceReset (or any other
+ * teardown of the device's primary context) are not supported.  Every call shares the
  * array and it keeps the last call's contents (each call rebuilds what it
  * reads and zeroes what it accumulates into); calls that overlap on the GPU
  * race on it.

@@ -85,12 +85,12 @@ static amr_status set_step_smem_all(std::integer_sequence<int, K...>) {
 }
 
 amr_status configure_kernels() {
-    static bool done = false;
-    if (done) return AMR_OK;
-    amr_status st;
-    if ((st = set_step_smem_all<double>(StepKeys{})) || (st = set_step_smem_all<float>(StepKeys{}))) return st;
-    done = true;
-    return AMR_OK;
+    static DeviceOnce once;
+    return once_per_device(once, [] {
+        amr_status st;
+        if ((st = set_step_smem_all<double>(StepKeys{})) || (st = set_step_smem_all<float>(StepKeys{}))) return st;
+        return AMR_OK;
+    });
 }
 
 template <typename real, int K>

@@ -24,8 +24,6 @@ using namespace amrh;
 
 namespace {
 
-bool configured = false;
-
 // Kernel instances: key K = MODE + 3 STAGE, as for the level step kernel.
 // the box batch runs the plain stages only (no dual energy, no gravity)
 using BoxKeys = std::make_integer_sequence<int, 3 * ST_MH_DE>;
@@ -45,11 +43,12 @@ amr_status set_box_smem_all(std::integer_sequence<int, K...>) {
 }
 
 amr_status configure_box_kernels() {
-    if (configured) return AMR_OK;
-    amr_status st;
-    if ((st = set_box_smem_all<double>(BoxKeys{})) || (st = set_box_smem_all<float>(BoxKeys{}))) return st;
-    configured = true;
-    return AMR_OK;
+    static DeviceOnce once;
+    return once_per_device(once, [] {
+        amr_status st;
+        if ((st = set_box_smem_all<double>(BoxKeys{})) || (st = set_box_smem_all<float>(BoxKeys{}))) return st;
+        return AMR_OK;
+    });
 }
 
 template <typename real, int K>

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <vector>
 
 #include "amr_hydro.h"
@@ -201,4 +202,25 @@ void cut_runs(const std::vector<int32_t> &chains, const std::vector<int32_t> &ch
 void build_runs(int n_groups, const int32_t *nbr, int max_len, std::vector<int32_t> &runs,
                 std::vector<int32_t> &run_off);
 int choose_run_len(const std::vector<int32_t> &chain_off, int grid, double e);
+
+// Kernel attributes set by cudaFuncSetAttribute hold per device: fn() runs
+// once for each device it is first needed on (the current one), under a lock,
+// so concurrent first calls from several host threads wait for one setter.
+constexpr int MAX_DEVICES = 64;
+struct DeviceOnce {
+    std::mutex m;
+    bool done[MAX_DEVICES] = {};
+};
+template <typename F>
+amr_status once_per_device(DeviceOnce &o, F &&fn) {
+    int dev = 0;
+    amr_status st = cuda_fail(cudaGetDevice(&dev), "cudaGetDevice");
+    if (st) return st;
+    if (dev < 0 || dev >= MAX_DEVICES) return AMR_E_INVAL;
+    std::lock_guard<std::mutex> lock(o.m);
+    if (o.done[dev]) return AMR_OK;
+    if ((st = fn())) return st;
+    o.done[dev] = true;
+    return AMR_OK;
+}
 }  // namespace amrh

@@ -488,15 +488,13 @@ template <typename real>
 amr_status launch_sor(amr_hydro_ctx *c, Level &L, Level &C, int level, double G, double omega, int iters,
                       const double *phi_coarse, const double *phi_coarse1, double w, double *phi, double *acc,
                       int acc_order) {
-    static bool configured = false;
-    amr_status st;
-    if (!configured) {
-        if ((st = cuda_fail(cudaFuncSetAttribute(k_sor_patches<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)sizeof(SorSmem<real>)),
-                            "sor smem attribute")))
-            return st;
-        configured = true;
-    }
+    static DeviceOnce once;
+    amr_status st = once_per_device(once, [] {
+        return cuda_fail(cudaFuncSetAttribute(k_sor_patches<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)sizeof(SorSmem<real>)),
+                         "sor smem attribute");
+    });
+    if (st) return st;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sor_patches<real>, SOR_NT, sizeof(SorSmem<real>));
     const int cap = c->n_sm * (per_sm > 0 ? per_sm : 1);
@@ -702,10 +700,18 @@ amr_status amr_hydro_advance_gravity(amr_hydro_ctx *c, double dt, double G, cons
                                      double *acc_new, int acc_order, double c_acc) {
     if (!c || !acc_n || !phi_new || !acc_new || (acc_order != 2 && acc_order != 4)) return AMR_E_INVAL;
     if (!(c_acc >= 0.0) || c_acc > 1e300) return AMR_E_INVAL;
-    {  // the corrector reads g^n after the root solve has written g^{n+1}: no overlap
-        const int64_t bytes = (int64_t)c->lv[0].n_patches * 3 * PV * (int64_t)sizeof(double);
-        const char *a = reinterpret_cast<const char *>(acc_n), *b = reinterpret_cast<const char *>(acc_new);
-        if (a < b + bytes && b < a + bytes) return AMR_E_INVAL;
+    {  // the corrector reads g^n and the state after the root solve has written
+       // phi^{n+1} and g^{n+1}: none of the outputs may overlap g^n, each other
+       // or the level's two state buffers
+        const Level &L0 = c->lv[0];
+        const int64_t nf = (int64_t)L0.n_patches * PV, nu = (int64_t)L0.n_patches * PSLOT;
+        if (overlaps(acc_n, 3 * nf, acc_new, 3 * nf) || overlaps(acc_n, 3 * nf, phi_new, nf) ||
+            overlaps(phi_new, nf, acc_new, 3 * nf))
+            return AMR_E_INVAL;
+        for (int b = 0; b < 2; b++)
+            if (overlaps(L0.U[b], nu, phi_new, nf) || overlaps(L0.U[b], nu, acc_new, 3 * nf) ||
+                overlaps(L0.U[b], nu, acc_n, 3 * nf))
+                return AMR_E_INVAL;
     }
     if (!(dt >= 0.0) && !(dt < 0.0)) return AMR_E_INVAL;
     if (c->prm.lmax > 0 && c->lv[1].n_patches) return AMR_E_INVAL;  // single-level grids

@@ -350,6 +350,11 @@ def test_gravity_edge_cases():
     phi = torch.zeros((g.n_patches, 8, 8, 8), dtype=torch.float64, device="cuda")
     with pytest.raises(A.AmrHydroError):  # the new acceleration may not overwrite g^n
         A.amr_hydro_advance_gravity(g.ctx, -1.0, 1.0, acc, phi, acc, 2)
+    acc2 = torch.zeros_like(acc)
+    with pytest.raises(A.AmrHydroError):  # nor may the new potential (it is written before the corrector)
+        A.amr_hydro_advance_gravity(g.ctx, -1.0, 1.0, acc, acc.view(-1)[:phi.numel()].view_as(phi), acc2, 2)
+    with pytest.raises(A.AmrHydroError):  # nor the level's state
+        A.amr_hydro_advance_gravity(g.ctx, -1.0, 1.0, acc, g.state().view(-1)[:phi.numel()].view_as(phi), acc2, 2)
     g.close()
 
 
