@@ -288,6 +288,12 @@ amr_status amr_hydro_init(const amr_hydro_params *p, void *stream, amr_hydro_ctx
     c->step_bps = step_blocks_per_sm(p->prec, p->scheme, p->recon, p->dual_energy);
     if ((st = c->scal.reserve(SCAL_N))) { amr_hydro_destroy(c); return st; }
     if ((st = c->dtbuf.reserve(3 * (MAX_LEVELS + MAX_BOXES)))) { amr_hydro_destroy(c); return st; }
+    if (cudaMallocHost(&c->rg.hcnt, 32 * sizeof(int32_t)) != cudaSuccess ||
+        cudaMallocHost(&c->rg.htime, 3 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        amr_hydro_destroy(c);
+        return AMR_E_NOMEM;
+    }
     if (p->fallback) {
         if ((st = c->fb_list.reserve(FB_CAP)) || (st = c->fb_count.reserve(1)) ||
             (st = cuda_fail(cudaMemsetAsync(c->fb_count.p, 0, 8, c->stream), "memset"))) {
@@ -318,7 +324,7 @@ amr_status amr_hydro_destroy(amr_hydro_ctx *c) {
     c->cflag.release();
     c->pflag.release();
     c->psum.release();
-    c->regrid_tmp.release();
+    c->rg.release();
     c->adjbuf.release();
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     for (cudaStream_t x : c->xfer)
@@ -328,6 +334,11 @@ amr_status amr_hydro_destroy(amr_hydro_ctx *c) {
     c->hstage[1].release();
     c->fb_list.release();
     c->fb_count.release();
+    for (const auto &r : c->phase_recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : c->phase_spare) cudaEventDestroy(e);
     release_poisson(c);
     delete c;
     return AMR_OK;
@@ -434,3 +445,72 @@ amr_status level_speed(amr_hydro_ctx *c, int level) {
 }
 
 }  // namespace amrh
+
+// ---- phase timing ------------------------------------------------------------------------
+
+namespace amrh {
+
+static cudaEvent_t phase_event(amr_hydro_ctx *c) {
+    if (!c->phase_spare.empty()) {
+        cudaEvent_t e = c->phase_spare.back();
+        c->phase_spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+PhaseScope::PhaseScope(amr_hydro_ctx *ctx, int ph) : c(ctx), phase(ph) {
+    if (!c->timing || c->phase_depth++ > 0) return;
+    a = phase_event(c);
+    if (!a) return;
+    on = cudaEventRecord(a, c->stream) == cudaSuccess;
+    if (!on) c->phase_spare.push_back(a);
+}
+
+PhaseScope::~PhaseScope() {
+    if (!c->timing) return;
+    c->phase_depth--;
+    if (!on) return;
+    cudaEvent_t b = phase_event(c);
+    if (b && cudaEventRecord(b, c->stream) == cudaSuccess) {
+        c->phase_recs.push_back({phase, a, b});
+    } else {
+        c->phase_spare.push_back(a);
+        if (b) c->phase_spare.push_back(b);
+    }
+}
+
+}  // namespace amrh
+
+extern "C" amr_status amr_hydro_phase_timing(amr_hydro_ctx *c, int on) {
+    if (!c) return AMR_E_INVAL;
+    c->timing = on != 0;
+    return AMR_OK;
+}
+
+extern "C" amr_status amr_hydro_phase_times(amr_hydro_ctx *c, double *ms_out, int64_t *calls_out) {
+    if (!c || !ms_out) return AMR_E_INVAL;
+    amr_status st = cuda_fail(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize(), "sync");
+    if (st) return st;
+    for (int k = 0; k < AMR_N_PHASES; k++) {
+        ms_out[k] = 0.0;
+        if (calls_out) calls_out[k] = 0;
+    }
+    for (const auto &r : c->phase_recs) {
+        float ms = 0.f;
+        if (r.phase >= 0 && r.phase < AMR_N_PHASES && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            ms_out[r.phase] += ms;
+            if (calls_out) calls_out[r.phase]++;
+        }
+        c->phase_spare.push_back(r.a);
+        c->phase_spare.push_back(r.b);
+    }
+    cudaGetLastError();
+    c->phase_recs.clear();
+    return AMR_OK;
+}

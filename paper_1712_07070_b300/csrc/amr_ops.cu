@@ -43,8 +43,8 @@ struct CoarseView {
 };
 
 // Fine patches interpolated from the coarse level.  Job j (GHOST_INFO ints):
-// coarse parent P of the group the patch is placed around, patch position q
-// relative to that group (each -1..2), and the box of fine cells wanted
+// a coarse patch P and the patch position q relative to P's children (each
+// -1..2; P < 0: no job), and the box of fine cells wanted
 // (even bounds); output patch out_slot[j] (or j).  One warp per job (a box
 // has at most 4x4x4 coarse cells, a face ghost 16); one lane per coarse cell
 // of the box computes its value, slopes and positivity test once and writes
@@ -59,6 +59,7 @@ __global__ void k_interp_patches(double *__restrict__ out, const int32_t *__rest
     for (int j = blockIdx.x * INTERP_WARPS + warp; j < n_jobs; j += gridDim.x * INTERP_WARPS) {
         const int32_t *I = info + (int64_t)GHOST_INFO * j;
         const int P = I[0], qx = I[1], qy = I[2], qz = I[3], box = I[4];
+        if (P < 0) continue;  // a slot filled otherwise (a regrid's copied slots)
         const int lo[3] = {box & 15, (box >> 4) & 15, (box >> 8) & 15};
         const int hi[3] = {(box >> 12) & 15, (box >> 16) & 15, (box >> 20) & 15};
         const int n[3] = {(hi[0] - lo[0]) >> 1, (hi[1] - lo[1]) >> 1, (hi[2] - lo[2]) >> 1};
@@ -264,6 +265,9 @@ amr_status fill_ghost_impl(amr_hydro_ctx *c, int level, double t) {
     if (!L.n_ghost) return AMR_OK;
     if (level == 0) return AMR_E_NESTING;
     Level &C = c->lv[level - 1];
+    // the ghosts already hold this interpolation: same time, same coarse data, same plan
+    if (L.ghost_valid && L.ghost_t == t && L.ghost_cver == C.version && L.ghost_pver == L.plan_version)
+        return AMR_OK;
     amr_status st = level_time(c, level - 1);
     if (st) return st;
     const double w = coarse_weight(C, t);
@@ -271,7 +275,12 @@ amr_status fill_ghost_impl(amr_hydro_ctx *c, int level, double t) {
     const int grid = blocks < 8 * c->n_sm ? blocks : 8 * c->n_sm;
     k_interp_patches<<<grid, 256, 0, c->stream>>>(L.ghost.p, nullptr, L.ghost_info.p, L.n_ghost, C.U[1 - C.cur],
                                                    C.U[C.cur], w, C.d_sib);
-    return cuda_fail(cudaGetLastError(), "k_interp_patches");
+    if ((st = cuda_fail(cudaGetLastError(), "k_interp_patches"))) return st;
+    L.ghost_valid = true;
+    L.ghost_t = t;
+    L.ghost_cver = C.version;
+    L.ghost_pver = L.plan_version;
+    return AMR_OK;
 }
 
 amr_status interp_new_patches(amr_hydro_ctx *c, int coarse, double *out, const int32_t *out_slot,
@@ -334,6 +343,7 @@ amr_status amr_hydro_flux_fixup(amr_hydro_ctx *c, int l) {
         if ((st = cuda_fail(cudaGetLastError(), "k_restrict"))) return st;
     }
     C.speed_valid = false;
+    C.version++;
     return AMR_OK;
 }
 
@@ -349,6 +359,7 @@ amr_status amr_hydro_conserved_sum(amr_hydro_ctx *c, int level, double *out) {
     for (int v = 0; v < NV; v++) out[v] = 0.0;
     if (!L.n_patches) return AMR_OK;
     amr_status st;
+    if ((st = refresh_host_tables(c, level))) return st;  // leaf test on the host child table
     if ((st = c->psum.reserve((size_t)L.n_patches * NV))) return st;
     const int grid = L.n_patches < 8 * c->n_sm ? L.n_patches : 8 * c->n_sm;
     k_patch_sums<<<grid, 256, 0, c->stream>>>(L.U[L.cur], L.n_patches, c->psum.p);

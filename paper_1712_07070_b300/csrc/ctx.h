@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <initializer_list>
 #include <mutex>
 #include <vector>
 
@@ -76,6 +77,18 @@ struct Level {
     int ring = 0;   // ring position of the newest state
     bool speed_valid = false;
     bool uniform = false;  // level 0 holding the whole root grid in the order of amr_hydro_uniform_tables
+    // device-side bookkeeping (regrid_dev.cu): dense patch-position -> slot
+    // map, ghost-position bits and ranks of the neighbour plan
+    DevBuf<int32_t> posmap, gbits, grank;
+    bool posmap_valid = false;
+    bool host_stale = false;       // host table mirrors behind the device tables (refresh_host_tables)
+    unsigned long long version = 0;       // bumped whenever the level's cell data change
+    unsigned long long plan_version = 0;  // bumped whenever its neighbour plan changes
+    // the coarse-fine ghost patches hold the interpolation at ghost_t of the
+    // coarse level's data version ghost_cver under plan ghost_pver
+    bool ghost_valid = false;
+    double ghost_t = 0.0;
+    unsigned long long ghost_cver = 0, ghost_pver = 0;
     void release() {
         nbr.release();
         ustar.release();
@@ -91,6 +104,10 @@ struct Level {
         freg_save.release();
         fix_list.release();
         restrict_list.release();
+        posmap.release();
+        gbits.release();
+        grank.release();
+        posmap_valid = ghost_valid = false;
         n_patches = n_groups = 0;
     }
 };
@@ -120,6 +137,29 @@ struct BoxTune {
 
 }  // namespace amrh
 
+namespace amrh {
+// Scratch of the device-side regrid (regrid_dev.cu): counts and error word
+// (device, with a pinned host copy), prefix-sum block sums, selection and
+// numbering arrays, the new level's tables before they replace the old ones,
+// and the register-map flags and ranks.
+struct RegridScratch {
+    DevBuf<int32_t> cnt, bsum, keep, mark, rank, gnew, gpar;
+    DevBuf<int32_t> corner, sib, parent, child, old_of, info, new_of;
+    DevBuf<int32_t> cf_a, cf_b, cf_c, cf_d, cf_e, cf_f, cf_g, cf_h;
+    int32_t *hcnt = nullptr;  // pinned, 32 entries
+    double *htime = nullptr;  // pinned, 3 entries
+    void release() {
+        for (DevBuf<int32_t> *b : {&cnt, &bsum, &keep, &mark, &rank, &gnew, &gpar, &corner, &sib, &parent, &child,
+                                   &old_of, &info, &new_of, &cf_a, &cf_b, &cf_c, &cf_d, &cf_e, &cf_f, &cf_g, &cf_h})
+            b->release();
+        if (hcnt) cudaFreeHost(hcnt);
+        if (htime) cudaFreeHost(htime);
+        hcnt = nullptr;
+        htime = nullptr;
+    }
+};
+}  // namespace amrh
+
 struct amr_hydro_ctx {
     amr_hydro_params prm;
     cudaStream_t stream = nullptr;
@@ -130,7 +170,7 @@ struct amr_hydro_ctx {
     amrh::DevBuf<double> dtbuf;
     amrh::DevBuf<uint8_t> cflag, pflag;  // refinement flag scratch
     amrh::DevBuf<double> psum;           // per-patch conservation partials
-    amrh::DevBuf<int32_t> regrid_tmp;    // slot maps / interpolation jobs of a regrid
+    amrh::RegridScratch rg;              // the device-side regrid's scratch
     amrh::DevBuf<double> adjbuf;         // dense scratch of the adjoint step
     // batched-box launch plan, tuning and its captured graph
     amrh::DevBuf<int32_t> box_plan;   // (box, group) work items
@@ -148,6 +188,16 @@ struct amr_hydro_ctx {
     // cells the step left unphysical, for the cell remedies (params.fallback)
     amrh::DevBuf<int64_t> fb_list;
     amrh::DevBuf<unsigned long long> fb_count;
+    // phase timing (amr_hydro_phase_timing): event pairs of the recorded
+    // phases, spare events, and the nesting depth of the open phase scopes
+    bool timing = false;
+    int phase_depth = 0;
+    struct PhaseRec {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<PhaseRec> phase_recs;
+    std::vector<cudaEvent_t> phase_spare;
     // root-level Poisson solver: cuFFT plans (forward, inverse) and work arrays;
     // isolated gravity: the padded grid's sizes and the transformed kernel
     long long fft_plan[4] = {0, 0, 0, 0};
@@ -186,6 +236,10 @@ amr_status copy_slots(amr_hydro_ctx *c, double *dst, const double *src, const in
 amr_status patch_flags_dev(amr_hydro_ctx *c, int level, uint8_t *pflag);
 amr_status plan_level(amr_hydro_ctx *c, int level);
 amr_status rebuild_cf(amr_hydro_ctx *c, int fine_level);
+// device-side bookkeeping (regrid_dev.cu)
+amr_status regrid_dev(amr_hydro_ctx *c, int level);
+amr_status build_posmap(amr_hydro_ctx *c, int level);
+amr_status refresh_host_tables(amr_hydro_ctx *c, int level);
 amr_status level_time(amr_hydro_ctx *c, int level);
 // host planning (host_plan.cpp)
 amr_status build_uniform_tables(const int np[3], int32_t *corner, int32_t *sib, int32_t *parent,
@@ -202,6 +256,17 @@ void cut_runs(const std::vector<int32_t> &chains, const std::vector<int32_t> &ch
 void build_runs(int n_groups, const int32_t *nbr, int max_len, std::vector<int32_t> &runs,
                 std::vector<int32_t> &run_off);
 int choose_run_len(const std::vector<int32_t> &chain_off, int grid, double e);
+
+// A phase of the level path timed by an event pair on the context's stream
+// (outermost scope only); does nothing while timing is off.
+struct PhaseScope {
+    amr_hydro_ctx *c;
+    int phase;
+    bool on = false;
+    cudaEvent_t a = nullptr;
+    PhaseScope(amr_hydro_ctx *ctx, int ph);
+    ~PhaseScope();
+};
 
 // Kernel attributes set by cudaFuncSetAttribute hold per device: fn() runs
 // once for each device it is first needed on (the current one), under a lock,

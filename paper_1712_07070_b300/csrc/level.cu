@@ -58,6 +58,10 @@ amr_status amr_hydro_set_level(amr_hydro_ctx *c, int level, int n_patches, doubl
     L.scal0 = SCAL_LEVEL0 + SCAL_PER * level;
     L.ring = 0;
     L.speed_valid = false;
+    L.posmap_valid = false;
+    L.host_stale = false;
+    L.ghost_valid = false;
+    L.version++;
     if ((st = cuda_fail(cudaMemset(c->scal.p + L.scal0, 0, 8 * SCAL_PER), "memset"))) return st;
     L.n_ghost = 0;
     {
@@ -119,6 +123,7 @@ amr_status amr_hydro_touch_level(amr_hydro_ctx *c, int level) {
     Level &L = c->lv[level];
     if (!L.n_patches) return AMR_E_INVAL;
     L.speed_valid = false;
+    L.version++;
     return AMR_OK;
 }
 
@@ -134,9 +139,11 @@ amr_status advance_once(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphy
     Level &L = c->lv[level];
     amr_status st;
     if (L.n_ghost) {  // coarse-fine ghosts need the level's time on the host
+        PhaseScope ph(c, AMR_PH_GHOST);
         if ((st = sync_level_time(c, L, level))) return st;
         if ((st = fill_ghost_impl(c, level, L.t))) return st;
     }
+    PhaseScope ph_step(c, AMR_PH_STEP);
     if (dt < 0.0 && (st = level_speed(c, level))) return st;
     if (dt < 0.0 && acc_n && c_acc > 0.0 &&  // Eq. (acc) joins Eq. (CFL2)
         (st = launch_acc_speed(c, acc_n, (int64_t)L.n_patches * 3 * PV, level_dh(c, level), c_acc,
@@ -224,6 +231,7 @@ amr_status advance_once(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphy
         return st;
 
     L.cur = 1 - L.cur;
+    L.version++;
     if (dt >= 0.0 && !L.t_pending) {
         L.t_prev = L.t;
         L.t += dt;
