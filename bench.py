@@ -238,6 +238,59 @@ def cpu_baseline(n, steps=8, slab=64):
                       f"({cells} cell updates, {el:.1f} s)"}
 
 
+def cpu_baseline_single_core(n, slab=16):
+    """The same oracle step on one host core (a child process with
+    OMP_NUM_THREADS=1): one FP64 step of an n x n x slab slab."""
+    code = ("import time, oracle; from paper_1712_07070_b300 import ics; "
+            f"U = ics.turbulence({n}, seed=1)[:, :{slab}].copy(); g = 5.0 / 3.0; "
+            f"dt = oracle.dt_cfl2(U, g, 0.5, 1.0 / {n}); oracle.step_periodic(U, 1.0 / {n}, dt, g); "
+            f"t0 = time.perf_counter(); oracle.step_periodic(U, 1.0 / {n}, dt, g); "
+            "print(time.perf_counter() - t0)")
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], cwd=HERE, env=env, capture_output=True, text=True, timeout=600)
+    el = float(r.stdout.strip().splitlines()[-1])
+    cells = n * n * slab
+    return {"value": cells / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one FP64 step of a {n}x{n}x{slab} periodic slab of the same seeded turbulence field "
+                      f"({cells} cell updates, {el:.1f} s)"}
+
+
+def live_parity(torch, A, UniformGrid):
+    """The Sod + noise workload (64^3, 10 steps, device dt) in both
+    precisions against the FP64 oracle: relative L1 per conserved variable
+    (the full-length checks of the other workloads are GPU tests)."""
+    import numpy as np
+    import oracle
+    from paper_1712_07070_b300 import ics
+    U0 = ics.sod_noise(64, seed=1)
+    ref, _ = oracle.run_periodic(U0, 1.0 / 64, 5.0 / 3.0, 0.5, 10)
+    out = {"workload": "Sod + 8 density modes + N(0,0.01) velocities, 64^3, 10 steps, vs the FP64 oracle",
+           "metric": "relative L1 per conserved variable (max over the five)"}
+    for prec, name in ((A.AMR_FP64, "f64"), (A.AMR_FP32_ACC64, "fp32_acc64")):
+        g = UniformGrid((64, 64, 64), prec=prec)
+        g.upload(U0)
+        for _ in range(10):
+            g.step(-1.0)
+        u = g.download()
+        g.close()
+        out[name] = max(float(np.abs(u[v] - ref[v]).sum() / np.abs(ref[v]).sum()) for v in range(5))
+    out["tolerance"] = {"f64": 1e-12, "fp32_acc64": 1e-5}
+    return out
+
+
+def repeats(torch, grid_factory, stream, K, reps=5):
+    """Median (and spread) of the per-step time over `reps` further
+    repetitions of K steps (after the timed region)."""
+    g = grid_factory()
+    ms = []
+    for _ in range(reps):
+        r, _ = timed_steps(torch, g, stream, K)
+        ms.append(r / K)
+    g.close()
+    ms.sort()
+    return {"n": reps, "steps_each": K, "ms_per_step": ms, "median_ms_per_step": ms[len(ms) // 2]}
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -309,8 +362,26 @@ def run_ours(args):
         line["boxes"] = bench_boxes(torch, args)
         line["adjoint"] = bench_adjoint(torch, args)
         line["gravity"] = bench_gravity(torch, args)
+    if not args.no_variants:
+        def mk(prec):
+            def f():
+                g = UniformGrid((n, n, n), prec=prec, stream=stream.cuda_stream)
+                g.upload(torch.from_numpy(U0))
+                for _ in range(W):
+                    g.step(-1.0)
+                return g
+            return f
+        line["repeats"] = {"f64": repeats(torch, mk(A.AMR_FP64), stream, K),
+                           "fp32_acc64": repeats(torch, mk(A.AMR_FP32_ACC64), stream, K)}
+        line["parity"] = live_parity(torch, A, UniformGrid)
+        line["breakdown"] = {
+            "uniform level": "ghost gather, solve and the dt reduction of Eq. (CFL2) are fused in one "
+                             "k_hydro_step launch per step (no separate ghost-fill or reduce pass); the AMR "
+                             "workload's amr.*.phases_ms_per_root_step splits ghost fill / step / fix-up / "
+                             "regrid / dt"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n)
+        line["cpu_baseline"]["single_core"] = cpu_baseline_single_core(n)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -384,6 +455,17 @@ def bench_amr(torch, args):
         ms = e0.elapsed_time(e1)
         out[name] = {"value": n / (ms * 1e-3), "ms_per_root_step": ms / K, "cell_updates_per_root_step": n // K,
                      "patches": [H.n_patches(l) for l in range(3)]}
+        # where a root step's time goes: event pairs around each phase on the
+        # context's stream, over two further root steps (after the timed region)
+        A.amr_hydro_phase_timing(H.ctx, True)
+        A.amr_hydro_phase_times(H.ctx)
+        for _ in range(2):
+            H.advance_root()
+        ph = A.amr_hydro_phase_times(H.ctx)
+        A.amr_hydro_phase_timing(H.ctx, False)
+        tot = sum(v[0] for v in ph.values())
+        out[name]["phases_ms_per_root_step"] = {k: v[0] / 2 for k, v in ph.items()}
+        out[name]["phase_share"] = {k: (v[0] / tot if tot > 0 else None) for k, v in ph.items()}
         H.close()
     out["value"] = out["f64"]["value"]
     return out

@@ -327,6 +327,31 @@ amr_status amr_hydro_regrid_flags(amr_hydro_ctx *ctx, int level, uint8_t *patch_
 amr_status amr_hydro_conserved_sum(amr_hydro_ctx *ctx, int level, double *out);
 
 /*
+ * Where the time of the level path goes (the paper's performance analysis of
+ * section 4.1 splits a step the same way).  With timing on, the context
+ * records a CUDA event pair around each phase of its level steps on its
+ * stream; phases do not nest (a phase inside another counts for the outer
+ * one), so together they cover the stream's time between the first and last
+ * event, host gaps included:
+ *   AMR_PH_GHOST   coarse-fine ghost interpolation (section 3.2)
+ *   AMR_PH_STEP    the fused patch-group step and the cell remedies
+ *   AMR_PH_FIXUP   flux fix-up and restriction (section 2.2)
+ *   AMR_PH_REGRID  refinement flags, the device-side regrid, plans
+ *   AMR_PH_DT      time-step reductions read by the host (Eq. CFL2)
+ * amr_hydro_phase_times synchronises the stream, returns the milliseconds
+ * and calls per phase (host arrays of AMR_N_PHASES) since the last call, and
+ * clears them.  Timing off (the default) records nothing.
+ */
+#define AMR_PH_GHOST 0
+#define AMR_PH_STEP 1
+#define AMR_PH_FIXUP 2
+#define AMR_PH_REGRID 3
+#define AMR_PH_DT 4
+#define AMR_N_PHASES 5
+amr_status amr_hydro_phase_timing(amr_hydro_ctx *ctx, int on);
+amr_status amr_hydro_phase_times(amr_hydro_ctx *ctx, double *ms_out, int64_t *calls_out);
+
+/*
  * Independent periodic boxes advanced together (section 4.2 runs many
  * independent periodic domains, one per node; here they share one GPU).
  * set_box registers box `box_id` (< 256): a uniform periodic cube of n^3 cells

@@ -32,8 +32,11 @@ SYMBOLS = (
     "amr_hydro_unpack_uniform", "amr_hydro_step_uniform_noalloc", "amr_hydro_bind_level",
     "amr_hydro_regrid", "amr_hydro_advance_root", "amr_hydro_level_info", "amr_hydro_box_tuning",
     "amr_hydro_advance_host", "amr_hydro_set_entropy", "amr_hydro_poisson_root", "amr_hydro_poisson_level",
-    "amr_hydro_advance_gravity", "amr_hydro_poisson_level_t",
+    "amr_hydro_advance_gravity", "amr_hydro_poisson_level_t", "amr_hydro_phase_timing", "amr_hydro_phase_times",
 )
+AMR_PH_GHOST, AMR_PH_STEP, AMR_PH_FIXUP, AMR_PH_REGRID, AMR_PH_DT = range(5)
+AMR_N_PHASES = 5
+PHASE_NAMES = ("ghost fill", "step", "fix-up", "regrid", "dt")
 
 
 class amr_hydro_params(ctypes.Structure):
@@ -101,6 +104,8 @@ def lib():
         "amr_hydro_regrid": [_vp, ctypes.c_int],
         "amr_hydro_advance_root": [_vp, ctypes.c_double, _i64p],
         "amr_hydro_level_info": [_vp, ctypes.c_int, _ip, _ip],
+        "amr_hydro_phase_timing": [_vp, ctypes.c_int],
+        "amr_hydro_phase_times": [_vp, _dp, _i64p],
         "amr_hydro_step_uniform_noalloc": [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                            _vp, _vp, _vp],
@@ -342,3 +347,15 @@ def make_params(gamma=5.0 / 3.0, cfl=0.5, root_n=(64, 64, 64), box=None, lmax=0,
         max_patches = (root_n[0] // 8) * (root_n[1] // 8) * (root_n[2] // 8)
     p.max_patches = max_patches
     return p
+
+
+def amr_hydro_phase_timing(ctx, on=True):
+    check(lib().amr_hydro_phase_timing(ctx, 1 if on else 0), "amr_hydro_phase_timing")
+
+
+def amr_hydro_phase_times(ctx):
+    """{phase name: (ms, calls)} since the last call (synchronises the stream)."""
+    ms = (ctypes.c_double * AMR_N_PHASES)()
+    n = (ctypes.c_int64 * AMR_N_PHASES)()
+    check(lib().amr_hydro_phase_times(ctx, ms, n), "amr_hydro_phase_times")
+    return {PHASE_NAMES[k]: (ms[k], n[k]) for k in range(AMR_N_PHASES)}
