@@ -62,6 +62,7 @@ template struct DevBuf<int64_t>;
 template struct DevBuf<double>;
 template struct DevBuf<unsigned long long>;
 template struct DevBuf<uint8_t>;
+template struct DevBuf<uint32_t>;
 
 size_t step_smem_bytes(int prec) {
     return prec == AMR_FP64 ? sizeof(StepSmem<double>) : sizeof(StepSmem<float>);
@@ -321,7 +322,7 @@ amr_status amr_hydro_destroy(amr_hydro_ctx *c) {
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     c->scal.release();
     c->dtbuf.release();
-    c->cflag.release();
+    c->flag_summary.release();
     c->pflag.release();
     c->psum.release();
     c->rg.release();

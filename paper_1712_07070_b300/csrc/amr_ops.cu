@@ -44,32 +44,42 @@ struct CoarseView {
 
 // Fine patches interpolated from the coarse level.  Job j (GHOST_INFO ints):
 // a coarse patch P and the patch position q relative to P's children (each
-// -1..2; P < 0: no job), and the box of fine cells wanted
-// (even bounds); output patch out_slot[j] (or j).  One warp per job (a box
-// has at most 4x4x4 coarse cells, a face ghost 16); one lane per coarse cell
-// of the box computes its value, slopes and positivity test once and writes
-// its eight children.
-constexpr int INTERP_WARPS = 8;  // warps (jobs in flight) per 256-thread block
+// -1..2; P < 0: no job), and the box of fine cells wanted (even bounds);
+// output patch out_slot[j] (or j).  Each half warp takes one job (a box has
+// at most 4x4x4 coarse cells, a face ghost 4x4x1, so a whole warp per job
+// would leave half of it idle on the narrow FP64 pipe); one lane per coarse
+// cell of the box computes its value, slopes and positivity test once and
+// writes its eight children.
+constexpr int INTERP_WARPS = 8;  // warps per 256-thread block, two jobs in flight each
 __global__ void k_interp_patches(double *__restrict__ out, const int32_t *__restrict__ out_slot,
                                  const int32_t *__restrict__ info, int n_jobs, const double *Uo,
                                  const double *Un, double w, const int32_t *__restrict__ csib) {
-    __shared__ int nbs[INTERP_WARPS][27];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int *nb = nbs[warp];
-    for (int j = blockIdx.x * INTERP_WARPS + warp; j < n_jobs; j += gridDim.x * INTERP_WARPS) {
-        const int32_t *I = info + (int64_t)GHOST_INFO * j;
-        const int P = I[0], qx = I[1], qy = I[2], qz = I[3], box = I[4];
-        if (P < 0) continue;  // a slot filled otherwise (a regrid's copied slots)
+    __shared__ int nbs[2 * INTERP_WARPS][27];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+    int *nb = nbs[2 * warp + half];
+    for (int j0 = 2 * (blockIdx.x * INTERP_WARPS + warp); j0 < n_jobs; j0 += 2 * gridDim.x * INTERP_WARPS) {
+        const int j = j0 + half;
+        int P = -1, qx = 0, qy = 0, qz = 0, box = 0;
+        if (j < n_jobs) {
+            const int32_t *I = info + (int64_t)GHOST_INFO * j;
+            P = I[0];
+            qx = I[1];
+            qy = I[2];
+            qz = I[3];
+            box = I[4];
+        }
+        __syncwarp();  // the previous jobs' reads of nb are done
+        if (P >= 0)  // P < 0: a slot filled otherwise (a regrid's copied slots)
+            for (int k = hl; k < 27; k += 16) nb[k] = k == 13 ? P : csib[(int64_t)P * 26 + k - (k > 13)];
+        __syncwarp();
+        if (P < 0) continue;
         const int lo[3] = {box & 15, (box >> 4) & 15, (box >> 8) & 15};
         const int hi[3] = {(box >> 12) & 15, (box >> 16) & 15, (box >> 20) & 15};
         const int n[3] = {(hi[0] - lo[0]) >> 1, (hi[1] - lo[1]) >> 1, (hi[2] - lo[2]) >> 1};
-        __syncwarp();  // the previous job's reads of nb are done
-        if (lane < 27) nb[lane] = lane == 13 ? P : csib[(int64_t)P * 26 + lane - (lane > 13)];
-        __syncwarp();
         CoarseView C{Uo, Un, w, nb};
         double *o = out + (int64_t)(out_slot ? out_slot[j] : j) * PSLOT;
         const int total = n[0] * n[1] * n[2];
-        for (int i = lane; i < total; i += 32) {
+        for (int i = hl; i < total; i += 16) {
             // local fine cell of the child (0,0,0) of this coarse cell
             const int fx = lo[0] + 2 * (i % n[0]), fy = lo[1] + 2 * ((i / n[0]) % n[1]),
                       fz = lo[2] + 2 * (i / (n[0] * n[1]));
@@ -163,10 +173,17 @@ __global__ void k_restrict(double *__restrict__ Uc, const double *__restrict__ U
 // Cell flags (section 2.1 refinement criterion, FP64 in every mode):
 // sum_d ((rho_{+d} - rho_{-d})/2)^2 > theta^2 rho^2; neighbours through the
 // group's 4x4x4 source table (same-level or interpolated ghost patches).
-__global__ void k_flag_cells(const double *__restrict__ U, const double *__restrict__ ghost,
-                             const int32_t *__restrict__ nbr, int n_groups, double theta,
-                             uint8_t *__restrict__ cflag) {
+// The cell flags themselves are not stored: each patch keeps a 27-bit
+// summary of where its flagged cells lie for the flag buffer of width nbuf
+// (<= 8).  Per dimension a cell is in the low part (coordinate < nbuf), the
+// whole patch, and the high part (coordinate >= 8 - nbuf); bit
+// a + 3 b + 9 c (a, b, c = 0 low, 1 whole, 2 high along x, y, z) is set when
+// a flagged cell lies in that product of parts.  One warp per patch.
+__global__ void k_flag_summary(const double *__restrict__ U, const double *__restrict__ ghost,
+                               const int32_t *__restrict__ nbr, int n_groups, double theta, int nbuf,
+                               uint32_t *__restrict__ summary) {
     __shared__ int src[64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;  // warp = local patch 0..7
     for (int g = blockIdx.x; g < n_groups; g += gridDim.x) {
         __syncthreads();
         if (threadIdx.x < 64) src[threadIdx.x] = nbr[(int64_t)g * 64 + threadIdx.x];
@@ -179,8 +196,11 @@ __global__ void k_flag_cells(const double *__restrict__ U, const double *__restr
             if (s <= -2) return ghost[(int64_t)(-2 - s) * PSLOT + off];
             return 1.0;  // a corner position: the +-1 stencil never reaches it
         };
-        for (int i = threadIdx.x; i < 4096; i += blockDim.x) {
-            const int x = i & 15, y = (i >> 4) & 15, z = i >> 8;
+        const int ox = 8 * (warp & 1), oy = 8 * ((warp >> 1) & 1), oz = 8 * (warp >> 2);
+        uint32_t bits = 0;
+        for (int c = lane; c < PV; c += 32) {
+            const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+            const int x = ox + lx, y = oy + ly, z = oz + lz;
             const double r = rho_at(x, y, z);
             const double gx = (rho_at(x + 1, y, z) - rho_at(x - 1, y, z)) / 2.0;
             const double gy = (rho_at(x, y + 1, z) - rho_at(x, y - 1, z)) / 2.0;
@@ -188,33 +208,36 @@ __global__ void k_flag_cells(const double *__restrict__ U, const double *__restr
             double g2 = gx * gx;
             g2 += gy * gy;
             g2 += gz * gz;
-            const int64_t slot = 8 * (int64_t)g + (x >> 3) + 2 * (y >> 3) + 4 * (z >> 3);
-            cflag[slot * PV + (z & 7) * 64 + (y & 7) * 8 + (x & 7)] = (uint8_t)(g2 > theta * theta * (r * r));
+            if (!(g2 > theta * theta * (r * r))) continue;
+            // parts this cell is in, per dimension (bit 0 low, 1 whole, 2 high)
+            const int px = (lx < nbuf) | 2 | (lx >= 8 - nbuf) << 2;
+            const int py = (ly < nbuf) | 2 | (ly >= 8 - nbuf) << 2;
+            const int pz = (lz < nbuf) | 2 | (lz >= 8 - nbuf) << 2;
+            for (int k = 0; k < 27; k++)
+                if ((px >> (k % 3)) & (py >> ((k / 3) % 3)) & (pz >> (k / 9)) & 1) bits |= 1u << k;
         }
+        bits = __reduce_or_sync(0xffffffffu, bits);
+        if (lane == 0) summary[8 * (int64_t)g + warp] = bits;
     }
 }
 
 // Patch flags with the flag buffer: patch P is flagged when a flagged cell of
-// P or of a sibling lies within Chebyshev distance nbuf (<= 8) of P.
-__global__ void k_flag_patches(const uint8_t *__restrict__ cflag, const int32_t *__restrict__ sib, int n_patches,
-                               int nbuf, uint8_t *__restrict__ pflag) {
-    __shared__ int nb[27];
-    __shared__ int hit;
-    for (int P = blockIdx.x; P < n_patches; P += gridDim.x) {
-        __syncthreads();
-        load_block27(nb, P, sib);
-        if (threadIdx.x == 0) hit = 0;
-        __syncthreads();
-        const int W = 8 + 2 * nbuf;
-        int local = 0;
-        for (int i = threadIdx.x; i < W * W * W && !local; i += blockDim.x) {
-            const int x = i % W - nbuf, y = (i / W) % W - nbuf, z = i / (W * W) - nbuf;
-            const int s = nb[((x >> 3) + 1) + 3 * ((y >> 3) + 1) + 9 * ((z >> 3) + 1)];
-            if (s >= 0 && cflag[(int64_t)s * PV + (z & 7) * 64 + (y & 7) * 8 + (x & 7)]) local = 1;
+// P or of a sibling lies within Chebyshev distance nbuf (<= 8) of P, that is,
+// in the part of the sibling Q at offset d that faces P (along each
+// dimension: Q's high part when Q lies below P, all of it when level, its
+// low part when above).
+__global__ void k_flag_patches(const uint32_t *__restrict__ summary, const int32_t *__restrict__ sib,
+                               int n_patches, uint8_t *__restrict__ pflag) {
+    for (int P = blockIdx.x * blockDim.x + threadIdx.x; P < n_patches; P += gridDim.x * blockDim.x) {
+        int hit = 0;
+        for (int k = 0; k < 27 && !hit; k++) {
+            const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+            const int Q = k == 13 ? P : sib[(int64_t)P * 26 + k - (k > 13)];
+            if (Q < 0) continue;
+            const int bit = (1 - dx) + 3 * (1 - dy) + 9 * (1 - dz);
+            hit = (summary[Q] >> bit) & 1u;
         }
-        if (local) hit = 1;
-        __syncthreads();
-        if (threadIdx.x == 0) pflag[P] = (uint8_t)hit;
+        pflag[P] = (uint8_t)hit;
     }
 }
 
@@ -271,7 +294,7 @@ amr_status fill_ghost_impl(amr_hydro_ctx *c, int level, double t) {
     amr_status st = level_time(c, level - 1);
     if (st) return st;
     const double w = coarse_weight(C, t);
-    const int blocks = (L.n_ghost + INTERP_WARPS - 1) / INTERP_WARPS;
+    const int blocks = (L.n_ghost + 2 * INTERP_WARPS - 1) / (2 * INTERP_WARPS);
     const int grid = blocks < 8 * c->n_sm ? blocks : 8 * c->n_sm;
     k_interp_patches<<<grid, 256, 0, c->stream>>>(L.ghost.p, nullptr, L.ghost_info.p, L.n_ghost, C.U[1 - C.cur],
                                                    C.U[C.cur], w, C.d_sib);
@@ -287,7 +310,7 @@ amr_status interp_new_patches(amr_hydro_ctx *c, int coarse, double *out, const i
                               const int32_t *info, int n_jobs) {
     if (!n_jobs) return AMR_OK;
     Level &C = c->lv[coarse];
-    const int blocks = (n_jobs + INTERP_WARPS - 1) / INTERP_WARPS;
+    const int blocks = (n_jobs + 2 * INTERP_WARPS - 1) / (2 * INTERP_WARPS);
     const int grid = blocks < 8 * c->n_sm ? blocks : 8 * c->n_sm;
     k_interp_patches<<<grid, 256, 0, c->stream>>>(out, out_slot, info, n_jobs, C.U[C.cur], C.U[C.cur], 1.0,
                                                    C.d_sib);
@@ -305,15 +328,16 @@ amr_status patch_flags_dev(amr_hydro_ctx *c, int level, uint8_t *pflag) {
     Level &L = c->lv[level];
     amr_status st;
     if (L.n_ghost && (st = fill_ghost_impl(c, level, L.t))) return st;
-    if ((st = c->cflag.reserve((size_t)L.n_patches * PV))) return st;
-    const int g1 = L.n_groups < 4 * c->n_sm ? L.n_groups : 4 * c->n_sm;
-    k_flag_cells<<<g1, 256, 0, c->stream>>>(L.U[L.cur], L.ghost.p, L.nbr.p, L.n_groups, c->prm.theta, c->cflag.p);
-    if ((st = cuda_fail(cudaGetLastError(), "k_flag_cells"))) return st;
+    if ((st = c->flag_summary.reserve((size_t)L.n_patches))) return st;
     int nbuf = c->prm.nbuf[level];
     if (nbuf < 0) nbuf = 0;
     if (nbuf > 8) nbuf = 8;
-    const int g2 = L.n_patches < 8 * c->n_sm ? L.n_patches : 8 * c->n_sm;
-    k_flag_patches<<<g2, 256, 0, c->stream>>>(c->cflag.p, L.d_sib, L.n_patches, nbuf, pflag);
+    const int g1 = L.n_groups < 8 * c->n_sm ? L.n_groups : 8 * c->n_sm;
+    k_flag_summary<<<g1, 256, 0, c->stream>>>(L.U[L.cur], L.ghost.p, L.nbr.p, L.n_groups, c->prm.theta, nbuf,
+                                              c->flag_summary.p);
+    if ((st = cuda_fail(cudaGetLastError(), "k_flag_summary"))) return st;
+    const int g2 = (L.n_patches + 255) / 256 < 8 * c->n_sm ? (L.n_patches + 255) / 256 : 8 * c->n_sm;
+    k_flag_patches<<<g2 > 0 ? g2 : 1, 256, 0, c->stream>>>(c->flag_summary.p, L.d_sib, L.n_patches, pflag);
     return cuda_fail(cudaGetLastError(), "k_flag_patches");
 }
 

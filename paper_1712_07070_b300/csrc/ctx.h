@@ -168,7 +168,8 @@ struct amr_hydro_ctx {
     amrh::Box boxes[amrh::MAX_BOXES];
     amrh::DevBuf<unsigned long long> scal;
     amrh::DevBuf<double> dtbuf;
-    amrh::DevBuf<uint8_t> cflag, pflag;  // refinement flag scratch
+    amrh::DevBuf<uint8_t> pflag;         // refinement flag scratch
+    amrh::DevBuf<uint32_t> flag_summary;  // per-patch summary of where flagged cells lie
     amrh::DevBuf<double> psum;           // per-patch conservation partials
     amrh::RegridScratch rg;              // the device-side regrid's scratch
     amrh::DevBuf<double> adjbuf;         // dense scratch of the adjoint step
