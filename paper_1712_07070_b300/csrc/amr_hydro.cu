@@ -266,7 +266,6 @@ amr_status amr_hydro_init(const amr_hydro_params *p, void *stream, amr_hydro_ctx
         return AMR_E_INVAL;
     // VL on refined levels would need the half-step state in a 3-cell ring of
     // the coarse-fine ghost patches: single-level grids only
-    if (p->scheme == AMR_SCHEME_VL && p->lmax > 0) return AMR_E_INVAL;
     for (int d = 0; d < 3; d++) {
         if (p->root_n[d] <= 0 || p->root_n[d] % 16) return AMR_E_INVAL;
         if (!p->periodic[d]) return AMR_E_INVAL;

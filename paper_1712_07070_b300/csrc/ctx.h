@@ -56,6 +56,11 @@ struct Level {
     DevBuf<double> ustar;       // VL half-step state, [n_patches][5][512]
     DevBuf<double> ghost;       // [n_ghost][5][512]
     DevBuf<int32_t> ghost_info; // [n_ghost][GHOST_INFO]
+    // VL on refined levels: the half-step state U* of the ghost patches and
+    // each ghost patch's 27 neighbouring patch positions (slot >= 0, ghost
+    // -2 - id, none -1)
+    DevBuf<double> ghost_ustar;
+    DevBuf<int32_t> ghost_nbr;
     int n_ghost = 0;
     // coarse-fine flux registers (section 2.2 fix-up)
     DevBuf<int64_t> fine_off;    // [n_groups*6]: this level's group faces on coarse-fine interfaces
@@ -97,6 +102,8 @@ struct Level {
         n_runs = 0;
         ghost.release();
         ghost_info.release();
+        ghost_ustar.release();
+        ghost_nbr.release();
         fine_off.release();
         freg.release();
         coarse_off.release();
@@ -227,6 +234,8 @@ amr_status launch_step_raw(int prec, const StepParams &P, cudaStream_t stream);
 amr_status launch_cell_remedies(amr_hydro_ctx *c, const StepParams &P, const double *base, int cfl1,
                                 cudaStream_t s);
 constexpr int64_t FB_CAP = 1 << 20;  // listed cells per step launch (more are counted unphysical)
+// the VL predictor's half step on a level's coarse-fine ghost patches (vl_ghost.cu)
+amr_status launch_vl_ghost_pred(amr_hydro_ctx *c, int level, const StepParams &P);
 amr_status launch_max_speed(int prec, const double *U, int64_t n_slots, double gamma, int cfl1,
                             unsigned long long *smax, unsigned long long *nbad, int n_sm, cudaStream_t stream);
 // AMR (amr_ops.cu, regrid.cpp)

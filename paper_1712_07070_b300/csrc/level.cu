@@ -38,6 +38,9 @@ amr_status amr_hydro_set_level(amr_hydro_ctx *c, int level, int n_patches, doubl
     if (n_patches < 0 || n_patches % 8 || n_patches > c->prm.max_patches) return AMR_E_INVAL;
     if (n_patches > 0 && (!U_a || !U_b || !corner || !sib)) return AMR_E_INVAL;
     if (level > 0 && n_patches > 0 && !parent) return AMR_E_INVAL;
+    // VL on a refined level needs the ghost-patch neighbour tables the
+    // device-side regrid builds: refined levels come from amr_hydro_regrid
+    if (level > 0 && n_patches > 0 && c->prm.scheme == AMR_SCHEME_VL) return AMR_E_INVAL;
     Level &L = c->lv[level];
     amr_status st;
     if ((st = cuda_fail(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize(), "sync")))
@@ -221,14 +224,21 @@ amr_status advance_once(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphy
         H.fb_count = nullptr;
         H.fb_list = nullptr;
         if ((st = launch_step(c, H, grid))) return st;
+        // refined levels: the half step of the ghost cells the corrector reads
+        if (L.n_ghost && (st = launch_vl_ghost_pred(c, level, H))) return st;
         P.stage = ST_VL_CORR;
         P.U_base = P.U_old;
         P.U_old = L.ustar.p;
+        if (L.n_ghost) P.ghost = L.ghost_ustar.p;
     }
     if ((st = launch_step(c, P, grid))) return st;
-    if ((st = launch_cell_remedies(c, P, P.stage == ST_VL_CORR ? P.U_base : P.U_old, stage_ctu(P.stage),
-                                   c->stream)))
-        return st;
+    {
+        StepParams R = P;  // the cell remedies recompute from U^n: its ghosts
+        R.ghost = L.ghost.p;
+        if ((st = launch_cell_remedies(c, R, P.stage == ST_VL_CORR ? P.U_base : P.U_old, stage_ctu(P.stage),
+                                       c->stream)))
+            return st;
+    }
 
     L.cur = 1 - L.cur;
     L.version++;

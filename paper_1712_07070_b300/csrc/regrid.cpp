@@ -51,7 +51,8 @@ amr_status plan_level(amr_hydro_ctx *c, int level) {
     std::vector<GhostInfo> ghosts;
     amr_status st = build_nbr_plan(level, L.n_patches, L.corner.data(), L.sib.data(),
                                    level > 0 ? L.parent.data() : nullptr, cells, nbr, ghosts,
-                                   c->prm.recon == AMR_RECON_PPM ? 4 : 2, c->prm.fallback != 0);
+                                   (c->prm.recon == AMR_RECON_PPM || c->prm.scheme == AMR_SCHEME_VL) ? 4 : 2,
+                                   c->prm.fallback != 0);
     if (st) return st;
     if ((st = upload(L.nbr, nbr, c->stream))) return st;
     {  // z-runs of the length the round-robin cost estimate prefers

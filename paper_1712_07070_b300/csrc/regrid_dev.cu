@@ -322,6 +322,26 @@ __global__ void k_plan_ghosts(int64_t npos, const int32_t *__restrict__ gbits, c
     }
 }
 
+// VL on refined levels: the 27 patch positions around each ghost patch
+// (a slot of the level, another ghost patch as -2 - id, or -1)
+__global__ void k_plan_ghost_nbr(int64_t npos, const int32_t *__restrict__ gbits, const int32_t *__restrict__ grank,
+                                 const int32_t *__restrict__ posmap, int PX, int PY, int PZ, int cap,
+                                 int32_t *__restrict__ gnbr) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npos; p += (int64_t)gridDim.x * blockDim.x) {
+        if (!gbits[p]) continue;
+        const int id = grank[p];
+        if (id >= cap) continue;
+        const int px = (int)(p % PX), py = (int)((p / PX) % PY), pz = (int)(p / ((int64_t)PX * PY));
+        for (int k = 0; k < 27; k++) {
+            const int qx = wrapd(px + k % 3 - 1, PX), qy = wrapd(py + (k / 3) % 3 - 1, PY),
+                      qz = wrapd(pz + k / 9 - 1, PZ);
+            const int64_t q = pos_index(qx, qy, qz, PX, PY);
+            const int32_t s = posmap[q];
+            gnbr[(int64_t)id * 27 + k] = s >= 0 ? s : (gbits[q] ? -2 - grank[q] : -1);
+        }
+    }
+}
+
 __global__ void k_plan_fix(int64_t n, int32_t *__restrict__ nbr, const int32_t *__restrict__ grank) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = nbr[i];
@@ -460,7 +480,10 @@ static amr_status plan_level_dev(amr_hydro_ctx *c, int X, int32_t *n_ghost_dev, 
     int P[3];
     patch_grid(c, X, P);
     const int64_t np = (int64_t)P[0] * P[1] * P[2];
-    const int depth = c->prm.recon == AMR_RECON_PPM ? 4 : 2;
+    // ghost cells a step reads: two (PLM), three (PPM; the VL predictor's
+    // half step on the two the corrector reads), in boxes of even depth
+    const bool vl = c->prm.scheme == AMR_SCHEME_VL;
+    const int depth = (c->prm.recon == AMR_RECON_PPM || vl) ? 4 : 2;
     L.n_runs = 0;
     if ((st = L.nbr.reserve((size_t)L.n_groups * 64 + 64))) return st;
     if ((st = L.gbits.reserve(np)) || (st = L.grank.reserve(np))) return st;
@@ -478,6 +501,13 @@ static amr_status plan_level_dev(amr_hydro_ctx *c, int X, int32_t *n_ghost_dev, 
     k_plan_ghosts<<<grid_for(np, 256, 8 * c->n_sm), 256, 0, c->stream>>>(np, L.gbits.p, L.grank.p, C.posmap.p, P[0],
                                                                         P[1], depth, L.ghost_info.p, cap, err);
     if ((st = cuda_fail(cudaGetLastError(), "k_plan_ghosts"))) return st;
+    if (vl) {
+        if (!L.posmap_valid && (st = build_posmap(c, X))) return st;
+        if ((st = L.ghost_nbr.reserve((size_t)cap * 27))) return st;
+        k_plan_ghost_nbr<<<grid_for(np, 256, 8 * c->n_sm), 256, 0, c->stream>>>(np, L.gbits.p, L.grank.p, L.posmap.p,
+                                                                                P[0], P[1], P[2], cap, L.ghost_nbr.p);
+        if ((st = cuda_fail(cudaGetLastError(), "k_plan_ghost_nbr"))) return st;
+    }
     k_plan_fix<<<grid_for(ne, 256, 8 * c->n_sm), 256, 0, c->stream>>>(ne, L.nbr.p, L.grank.p);
     L.plan_version++;
     return cuda_fail(cudaGetLastError(), "k_plan_fix");
@@ -661,11 +691,16 @@ amr_status regrid_dev(amr_hydro_ctx *c, int l) {
     if (nn) {
         F.n_ghost = S.hcnt[4];
         if (F.n_ghost && (st = F.ghost.reserve((size_t)F.n_ghost * PSLOT))) return st;
+        if (F.n_ghost && c->prm.scheme == AMR_SCHEME_VL && (st = F.ghost_ustar.reserve((size_t)F.n_ghost * PSLOT)))
+            return st;
         if ((st = cf_finish(c, l + 1, S.hcnt + 5))) return st;
         F.ghost_valid = false;
         if (G2) {
             G2->n_ghost = S.hcnt[9];
             if (G2->n_ghost && (st = G2->ghost.reserve((size_t)G2->n_ghost * PSLOT))) return st;
+            if (G2->n_ghost && c->prm.scheme == AMR_SCHEME_VL &&
+                (st = G2->ghost_ustar.reserve((size_t)G2->n_ghost * PSLOT)))
+                return st;
             if ((st = cf_finish(c, l + 2, S.hcnt + 10))) return st;
             G2->ghost_valid = false;
         }

@@ -54,13 +54,12 @@ def test_init_rejects_bad_params(field, value):
     assert not ctx.value
 
 
-def test_init_rejects_vl_on_refined_hierarchies_and_with_ppm():
-    # the VL half step is built for single-level grids and PLM only
+def test_init_rejects_vl_with_ppm():
+    # the VL scheme reconstructs its half step with PLM only
     ctx = ctypes.c_void_p()
-    for kw in (dict(lmax=1), dict(recon=A.AMR_RECON_PPM)):
-        p = A.make_params(root_n=(32, 32, 32), scheme=A.AMR_SCHEME_VL, **kw)
-        assert A.lib().amr_hydro_init(ctypes.byref(p), None, ctypes.byref(ctx)) == A.AMR_E_INVAL
-        assert not ctx.value
+    p = A.make_params(root_n=(32, 32, 32), scheme=A.AMR_SCHEME_VL, recon=A.AMR_RECON_PPM)
+    assert A.lib().amr_hydro_init(ctypes.byref(p), None, ctypes.byref(ctx)) == A.AMR_E_INVAL
+    assert not ctx.value
 
 
 def test_init_rejects_dual_energy_outside_its_scope():

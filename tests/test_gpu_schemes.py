@@ -248,3 +248,52 @@ def test_vl_full_size_512_sampled_cells():
             r, _ = oracle.step_periodic(subcube(U0, c, 4), 1.0 / n, dt, G53)
             scale = np.abs(U0[:, c[2], c[1], c[0]]).max()
             assert np.abs(out[:, c[2], c[1], c[0]] - r[:, 4, 4, 4]).max() <= 1e-12 * scale, c
+
+
+# ---- the VL scheme on refined hierarchies ------------------------------------------------
+
+def vl_sch(lim, rs, theta=1.5):
+    return dict(sch(lim, rs, theta), scheme=A.AMR_SCHEME_VL)
+
+
+@pytest.mark.parametrize("prec,tol", [(A.AMR_FP64, 1e-12), (A.AMR_FP32_ACC64, 1e-5)])
+@pytest.mark.parametrize("lim,rs,mild", [(A.AMR_LIM_VANLEER, A.AMR_RS_HLLC, False),
+                                         (A.AMR_LIM_GMINMOD, A.AMR_RS_HLLE, True)])
+def test_vl_amr_w_cycle_parity(prec, tol, lim, rs, mild):
+    """VL on the three-level blob hierarchy: the corrector of groups next to
+    coarse-fine interfaces reads the half step of their ghost cells, made
+    from the interpolated U^n three cells deep; bit-exact patch lists and
+    every level's cells against the oracle hierarchy with VL selected."""
+    from paper_1712_07070_b300.amr import AmrHierarchy
+    U0 = ics.blobs(32, seed=3, contrast=10.0, mach=1.0) if mild else ics.blobs(32, seed=3)
+    with oracle.scheme(lim, rs, 1.5, vl=True):
+        H = AmrHierarchy(U0, lmax=2, theta=0.05, nbuf=(8, 4), prec=prec, max_patches=6000,
+                         scheme=vl_sch(lim, rs))
+        O = OracleHierarchy(U0, lmax=2, gamma=G53, cfl=0.5, theta=0.05, nbuf=[8, 4])
+        assert H.n_patches(2) > 0
+        for _ in range(2):
+            H.advance_root()
+            O.advance(0)
+        compare(H, O, tol)
+    H.close()
+
+
+def test_vl_amr_interfaces_and_conservation():
+    """Many coarse-fine interfaces (small flag buffer): parity with the oracle
+    and the composite conserved sums across fix-up and regrid."""
+    from paper_1712_07070_b300.amr import AmrHierarchy
+    U0 = ics.blobs(32, seed=5, contrast=10.0, mach=1.0)
+    with oracle.scheme(A.AMR_LIM_VANLEER, A.AMR_RS_HLLC, 1.5, vl=True):
+        H = AmrHierarchy(U0, lmax=2, theta=0.3, nbuf=(1, 1), max_patches=6000,
+                         scheme=vl_sch(A.AMR_LIM_VANLEER, A.AMR_RS_HLLC))
+        O = OracleHierarchy(U0, lmax=2, gamma=G53, cfl=0.5, theta=0.3, nbuf=[1, 1])
+        assert 0 < H.n_patches(1) < 8 * 64
+        s0 = H.conserved_total()
+        for _ in range(2):
+            H.advance_root()
+            O.advance(0)
+        compare(H, O, 1e-12)
+        s1 = H.conserved_total()
+    scale = np.abs(U0).reshape(5, -1).sum(1) / 32 ** 3
+    assert (np.abs(s1 - s0) <= 1e-13 * scale).all(), (s1 - s0) / scale
+    H.close()
