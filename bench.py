@@ -68,6 +68,10 @@ def parse():
     ap.add_argument("--n", type=int, default=512, help="box edge (cells), multiple of 16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--adjoint-case", action="store_true",
+                    help="only adjoint steps of an n^3 turbulence level (profiling case)")
+    ap.add_argument("--boxes-case", action="store_true",
+                    help="only the box batch restricted to the boxes of edge <= n (profiling case)")
     ap.add_argument("--sor-case", action="store_true",
                     help="only the refined-level SOR solve on the blob hierarchy with an n^3 root (profiling case)")
     return ap.parse_args()
@@ -683,10 +687,76 @@ def sor_case(args):
     H.close()
 
 
+def adjoint_case(args):
+    """The adjoint step alone: --warmup untimed and --steps timed
+    amr_hydro_step_adjoint calls on an n^3 turbulence level (two spin-up
+    steps, dt of Eq. CFL2); one JSON line."""
+    import torch
+    from paper_1712_07070_b300 import amr_hydro as A
+    from paper_1712_07070_b300 import ics
+    from paper_1712_07070_b300.uniform import UniformGrid
+    n = args.n
+    g = UniformGrid((n, n, n))
+    g.upload(torch.from_numpy(ics.turbulence(n, seed=5)))
+    for _ in range(2):
+        g.step(-1.0)
+    dt = g.min_dt()
+    U = g.state().clone()
+    lam = torch.zeros_like(U)
+    lam[:, 0] = 1.0 / n ** 3
+    out = torch.empty_like(U)
+    for _ in range(args.warmup):
+        A.amr_hydro_step_adjoint(g.ctx, 0, dt, U, lam, out)
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch)
+    e0.record()
+    for _ in range(args.steps):
+        A.amr_hydro_step_adjoint(g.ctx, 0, dt, U, lam, out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    print(json.dumps({"metric": "adjoint cell updates/s", "value": n ** 3 / (ms * 1e-3), "unit": "cells/s",
+                      "ms_per_step": ms, "config": {"workload": f"adjoint of one FP64 step, {n}^3 turbulence"}}))
+    g.close()
+
+
+def boxes_case(args):
+    """The box batch alone, on the boxes of edge <= n of the seeded 64-box
+    set (FP32 mode, autotuned launch): --warmup untimed and --steps timed
+    steps; one JSON line."""
+    import torch
+    from paper_1712_07070_b300 import amr_hydro as A
+    from paper_1712_07070_b300 import ics
+    from paper_1712_07070_b300.boxes import BoxBatch
+    sizes = [m for m in ics.kh_batch_sizes(64, seed=4) if m <= args.n]
+    B = BoxBatch(gamma=1.4, prec=A.AMR_FP32_ACC64)
+    for i, m in enumerate(sizes):
+        B.add_box(ics.kh_box(m, seed=100 + i, gamma=1.4))
+    B.advance(max(args.warmup, 1), log=False)
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch)
+    e0.record()
+    B.advance(args.steps, log=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    cells = sum(m ** 3 for m in sizes)
+    print(json.dumps({"metric": "cell updates/s", "value": cells / (ms * 1e-3), "unit": "cells/s",
+                      "ms_per_step": ms, "boxes": len(sizes), "cells": cells,
+                      "config": {"workload": f"KH box batch, the {len(sizes)} boxes of edge <= {args.n}"}}))
+    B.close()
+
+
 def main():
     args = parse()
     if args.sor_case:
         sor_case(args)
+        return
+    if args.adjoint_case:
+        adjoint_case(args)
+        return
+    if args.boxes_case:
+        boxes_case(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -80,6 +80,27 @@ def test_step_adjoint_matches_oracle(shape):
     assert err <= 1e-10, err
 
 
+@pytest.mark.parametrize("shape", [(16, 16, 16), (32, 16, 48), (64, 64, 64)])
+def test_dot_product_identity_gpu_adjoint_vs_oracle_tangent(shape):
+    """<J v, w> = <v, J^T w> for the one-step linearisation, with J v from the
+    oracle's dual-number tangent (itself pinned against its tape and central
+    differences) and J^T w from the GPU adjoint: equal to rounding (1e-12 of
+    the terms' scale), so the GPU adjoint's exactness does not rest on
+    finite differences."""
+    nx, ny, nz = shape
+    U = ics.sod_noise(nx, seed=7, ny=ny, nz=nz)
+    U, _ = oracle.run_periodic(U, 1.0 / nx, G53, 0.5, 2)
+    dt = oracle.dt_cfl2(U, G53, 0.5, 1.0 / nx)
+    rng = np.random.default_rng(3)
+    v = rng.normal(size=U.shape)
+    w = rng.normal(size=U.shape)
+    Jv = OD.jvp_step(U, v, 1.0 / nx, dt, G53)
+    JTw = gpu_adjoint_step(U, w, dt)
+    lhs, rhs = float((Jv * w).sum()), float((v * JTw).sum())
+    scale = float(np.abs(Jv * w).sum())
+    assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs, scale)
+
+
 def grad_and_fd(n, n_steps, n_dirs, seed=5, h=1e-6, with_oracle=False):
     import torch
     from paper_1712_07070_b300.adjoint import CheckpointedRun, HydroRun, density_loss
