@@ -131,8 +131,8 @@ typedef struct {
     double dt_min;       /* > 0: a level step that leaves unphysical cells is recomputed with
                             dt x 0.8 until it succeeds or dt < dt_min (AMR_E_UNPHYSICAL);
                             0: no retry */
-    int dual_energy;     /* 1: the dual-energy formalism (section 2.2) on single-level grids
-                            with MUSCL-Hancock + PLM: the entropy per unit volume
+    int dual_energy;     /* 1: the dual-energy formalism (section 2.2) on single-level grids and
+                            in the box batch, with MUSCL-Hancock + PLM: the entropy per unit volume
                             s = P / rho^(gamma-1) (arrays of amr_hydro_set_entropy) is carried
                             as a passive scalar (PLM q = s / rho, F_s = mass flux x upwind q);
                             after the update E = E_kin + s rho^(gamma-1)/(gamma-1) where
@@ -367,6 +367,14 @@ amr_status amr_hydro_set_box(amr_hydro_ctx *ctx, int box_id, int n, double *U_a,
 amr_status amr_hydro_advance_boxes(amr_hydro_ctx *ctx, int n_boxes, const int *box_ids,
                                    int n_steps, double *dt_log);
 amr_status amr_hydro_box_state(amr_hydro_ctx *ctx, int box_id, int *cur_buffer);
+/* Dual energy in the box batch (section 2.2 dual-energy formalism, as for a
+ * level with amr_hydro_set_entropy): the entropy per unit volume of box
+ * box_id, two caller-owned device FP64 buffers [n_patches][8][8][8] in the
+ * box's slot order; S_a holds the current field (it pairs with the box's
+ * current state buffer).  Every box of an advance_boxes call needs them when
+ * params.dual_energy is set (AMR_E_INVAL otherwise, and for a context
+ * without dual energy, an unregistered box or equal buffers). */
+amr_status amr_hydro_set_box_entropy(amr_hydro_ctx *ctx, int box_id, double *S_a, double *S_b);
 /* Launch shape the autotuner picked for the last box set: persistent grid
  * size, contiguous (1) or grid-stride (0) work runs per CTA, interleaved (1)
  * or box-major (0) work order, and its measured time per batch step.

@@ -25,7 +25,9 @@ class BoxBatch:
         except Exception:
             pass
 
-    def add_box(self, U_dense):
+    def add_box(self, U_dense, S_dense=None):
+        """Register a periodic n^3 box from its dense state [5][n][n][n]; with
+        dual energy also its entropy per unit volume S_dense [n][n][n]."""
         n = U_dense.shape[-1]
         npatch = (n // 8) ** 3
         U = [torch.empty((npatch, 5, 8, 8, 8), dtype=torch.float64, device=self.device) for _ in range(2)]
@@ -34,7 +36,17 @@ class BoxBatch:
         torch.cuda.synchronize()
         bid = len(self.boxes)
         A.amr_hydro_set_box(self.ctx, bid, n, U[0], U[1])
-        self.boxes.append((n, U))
+        S = None
+        if S_dense is not None:
+            S = [torch.zeros((npatch, 8, 8, 8), dtype=torch.float64, device=self.device) for _ in range(2)]
+            tmp = torch.zeros_like(U[0])
+            ds = torch.zeros((5, n, n, n), dtype=torch.float64, device=self.device)
+            ds[0].copy_(torch.from_numpy(np.ascontiguousarray(S_dense)))
+            A.amr_hydro_pack_uniform(ds, n, n, n, tmp, self.stream)
+            torch.cuda.synchronize()
+            S[0].copy_(tmp[:, 0])
+            A.amr_hydro_set_box_entropy(self.ctx, bid, S[0], S[1])
+        self.boxes.append((n, U, S))
         return bid
 
     def advance(self, n_steps, ids=None, log=True):
@@ -45,6 +57,16 @@ class BoxBatch:
 
     def state(self, i):
         return self.boxes[i][1][A.amr_hydro_box_state(self.ctx, i)]
+
+    def entropy(self, i):
+        """The dual-energy entropy field of box i as [n][n][n] (numpy)."""
+        n, _, S = self.boxes[i]
+        cur = A.amr_hydro_box_state(self.ctx, i)
+        tmp = torch.zeros((S[0].shape[0], 5, 8, 8, 8), dtype=torch.float64, device=self.device)
+        tmp[:, 0].copy_(S[cur])
+        d = torch.empty((5, n, n, n), dtype=torch.float64, device=self.device)
+        A.amr_hydro_unpack_uniform(tmp, n, n, n, d, self.stream)
+        return d[0].cpu().numpy()
 
     def download(self, i):
         n = self.boxes[i][0]

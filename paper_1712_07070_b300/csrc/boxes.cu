@@ -25,8 +25,8 @@ using namespace amrh;
 namespace {
 
 // Kernel instances: key K = MODE + 3 STAGE, as for the level step kernel.
-// the box batch runs the plain stages only (no dual energy, no gravity)
-using BoxKeys = std::make_integer_sequence<int, 3 * ST_MH_DE>;
+// the box batch runs the stages up to dual energy (no gravity)
+using BoxKeys = std::make_integer_sequence<int, 3 * (ST_MH_DE + 1)>;
 
 template <typename real, int K>
 amr_status set_box_smem() {
@@ -66,9 +66,9 @@ int box_occupancy(int lo, int hi, std::integer_sequence<int, K...>) {
 }
 
 // Resident CTAs per SM of the instances the context's scheme launches.
-int resident_per_sm(int prec, int scheme, int recon) {
+int resident_per_sm(int prec, int scheme, int recon, int dual_energy) {
     int lo, hi;
-    scheme_stages(scheme, recon, 0, lo, hi);
+    scheme_stages(scheme, recon, dual_energy, lo, hi);
     return prec == AMR_FP64 ? box_occupancy<double>(lo, hi, BoxKeys{}) : box_occupancy<float>(lo, hi, BoxKeys{});
 }
 
@@ -86,7 +86,7 @@ void launch_boxes_key(int key, const BoxLaunch &B, int grid, cudaStream_t s, std
 amr_status launch_boxes(amr_hydro_ctx *c, const BoxLaunch &B, int grid, cudaStream_t s) {
     const int mode = scheme_mode(B.limiter, B.riemann);
     int lo, hi;
-    scheme_stages(c->prm.scheme, c->prm.recon, 0, lo, hi);
+    scheme_stages(c->prm.scheme, c->prm.recon, c->prm.dual_energy, lo, hi);
     for (int stage = lo; stage <= hi; stage++) {
         if (c->prm.prec == AMR_FP64)
             launch_boxes_key<double>(mode + 3 * stage, B, grid, s, BoxKeys{});
@@ -143,7 +143,6 @@ extern "C" {
 amr_status amr_hydro_set_box(amr_hydro_ctx *c, int box_id, int n, double *U_a, double *U_b) {
     if (!c || box_id < 0 || box_id >= MAX_BOXES || n <= 0 || n % 16 || !U_a || !U_b || U_a == U_b)
         return AMR_E_INVAL;
-    if (c->prm.dual_energy) return AMR_E_INVAL;  // the box batch carries no entropy fields
     Box &B = c->boxes[box_id];
     const int np[3] = {n / 8, n / 8, n / 8};
     const int64_t npatch = (int64_t)np[0] * np[1] * np[2];
@@ -161,11 +160,23 @@ amr_status amr_hydro_set_box(amr_hydro_ctx *c, int box_id, int n, double *U_a, d
     B.n_groups = (int)(npatch / 8);
     B.U[0] = U_a;
     B.U[1] = U_b;
+    B.S[0] = B.S[1] = nullptr;  // dual energy: amr_hydro_set_box_entropy
     B.cur = 0;
     B.ring = 0;
     B.speed_valid = false;
     c->plan_key.clear();
     c->tune_key.clear();
+    c->graph_key.clear();
+    return AMR_OK;
+}
+
+amr_status amr_hydro_set_box_entropy(amr_hydro_ctx *c, int box_id, double *S_a, double *S_b) {
+    if (!c || box_id < 0 || box_id >= MAX_BOXES || !c->prm.dual_energy) return AMR_E_INVAL;
+    Box &B = c->boxes[box_id];
+    if (!B.n || !S_a || !S_b || S_a == S_b) return AMR_E_INVAL;
+    B.S[B.cur] = S_a;
+    B.S[1 - B.cur] = S_b;
+    B.speed_valid = false;
     c->graph_key.clear();
     return AMR_OK;
 }
@@ -195,6 +206,7 @@ amr_status amr_hydro_advance_boxes(amr_hydro_ctx *c, int n_boxes, const int *box
         for (int i = 0; i < n_boxes; i++) {
             if (sorted[i] < 0 || sorted[i] >= MAX_BOXES || !c->boxes[sorted[i]].n) return AMR_E_INVAL;
             if (i && sorted[i] == sorted[i - 1]) return AMR_E_INVAL;
+            if (c->prm.dual_energy && !c->boxes[sorted[i]].S[0]) return AMR_E_INVAL;  // no entropy fields
         }
     }
     if (!n_steps) return AMR_OK;
@@ -220,6 +232,8 @@ amr_status amr_hydro_advance_boxes(amr_hydro_ctx *c, int n_boxes, const int *box
         Box &B = c->boxes[ids[i]];
         desc[i].U[0] = B.U[0];
         desc[i].U[1] = B.U[1];
+        desc[i].S[0] = B.S[0];
+        desc[i].S[1] = B.S[1];
         desc[i].ustar = B.ustar.p;
         desc[i].nbr = B.nbr.p;
         desc[i].scal = c->scal.p + SCAL_BOX0 + SCAL_PER * ids[i];
@@ -244,12 +258,13 @@ amr_status amr_hydro_advance_boxes(amr_hydro_ctx *c, int n_boxes, const int *box
     L.theta = c->prm.minmod_coeff;
     L.fallback = c->prm.fallback;
     L.n_boxes = n_boxes;
+    L.de_xi = c->prm.dual_xi;
 
     // autotune the launch shape once per box set
     if (c->tune_key != ids) {
         const char *env = std::getenv("AMR_HYDRO_AUTOTUNE");
         const bool tune = !(env && env[0] == '0');
-        const int res = resident_per_sm(c->prm.prec, c->prm.scheme, c->prm.recon);
+        const int res = resident_per_sm(c->prm.prec, c->prm.scheme, c->prm.recon, c->prm.dual_energy);
         std::vector<BoxTune> cands;
         for (int mult : {1, res, 2 * res, 4 * res})
             for (int chunked : {0, 1})

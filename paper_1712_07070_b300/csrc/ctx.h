@@ -92,6 +92,7 @@ struct Level {
     // the coarse-fine ghost patches hold the interpolation at ghost_t of the
     // coarse level's data version ghost_cver under plan ghost_pver
     bool ghost_valid = false;
+    cudaGraphExec_t gexec = nullptr;  // the level step as a CUDA graph (refined hierarchies)
     double ghost_t = 0.0;
     unsigned long long ghost_cver = 0, ghost_pver = 0;
     void release() {
@@ -114,6 +115,8 @@ struct Level {
         posmap.release();
         gbits.release();
         grank.release();
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
         posmap_valid = ghost_valid = false;
         n_patches = n_groups = 0;
     }
@@ -122,6 +125,7 @@ struct Level {
 struct Box {
     int n = 0, n_groups = 0;
     double *U[2] = {nullptr, nullptr};
+    double *S[2] = {nullptr, nullptr};  // dual-energy entropy fields
     int cur = 0;
     int ring = 0;
     bool speed_valid = false;

@@ -369,8 +369,9 @@ __device__ __forceinline__ void face_flux(const real uL[NV], const real uR[NV], 
     const real vtx = (sl * wL[1] + sr * wR[1]) * iw;
     const real vty = (sl * wL[2] + sr * wR[2]) * iw;
     const real vtz = (sl * wL[3] + sr * wR[3]) * iw;
-    const real hl = (uL[4] + pl) * ril, hr = (uR[4] + pr) * rir;
-    const real ht = (sl * hl + sr * hr) * iw;
+    // Roe-averaged enthalpy (sqrt(rho_L) H_L + sqrt(rho_R) H_R) / (sqrt(rho_L) + sqrt(rho_R))
+    // with sqrt(rho) H = (E + P) / sqrt(rho)
+    const real ht = ((uL[4] + pl) * yl + (uR[4] + pr) * yr) * iw;
     const real ct = sqrt_(g.gm1 * (ht - real(0.5) * (vtx * vtx + vty * vty + vtz * vtz)));
     const real vtn = D == 0 ? vtx : (D == 1 ? vty : vtz);
 
@@ -459,14 +460,18 @@ __device__ __forceinline__ void face_flux(const real uL[NV], const real uR[NV], 
     const real uKn = wK[1 + D], pK = wK[4];
     real fK[NV];
     phys_flux<D>(wK, uK, fK);
-    const real fac = mK * rcp_(SK - Ss);
+    // Toro's star state U*_K = fac (1, ..., S*, ..., E_K/rho_K + (S* - u_K)(S* + P_K/m_K)),
+    // fac = m_K / (S_K - S*); the P_K / m_K term is (S* - u_K) P_K / (S_K - S*)
+    // after the factor, so one reciprocal serves both
+    const real rsk = rcp_(SK - Ss);
+    const real fac = mK * rsk, dS = Ss - uKn;
     real us[NV];
     us[0] = fac;
     us[1] = fac * wK[1];
     us[2] = fac * wK[2];
     us[3] = fac * wK[3];
     us[1 + D] = fac * Ss;
-    us[4] = fac * (uK[4] * riK + (Ss - uKn) * (Ss + pK * rcp_(mK)));
+    us[4] = fac * (uK[4] * riK + dS * Ss) + (rsk * dS) * pK;
 #pragma unroll
     for (int v = 0; v < NV; v++) F[v] = fK[v] + SK * (us[v] - uK[v]);
 }

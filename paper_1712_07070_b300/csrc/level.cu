@@ -134,6 +134,63 @@ amr_status amr_hydro_touch_level(amr_hydro_ctx *c, int level) {
 
 namespace amrh {
 
+// The launches of one level step on c->stream: the fine registers' reset,
+// the step launch(es) and the cell remedies (P: the step's parameters).
+static amr_status launch_level_step(amr_hydro_ctx *c, int level, StepParams &P, const double *acc_n) {
+    Level &L = c->lv[level];
+    amr_status st;
+    if (level < c->prm.lmax) {  // a coarse step restarts the fine level's flux sums
+        Level &F = c->lv[level + 1];
+        if (F.n_patches && F.n_freg &&
+            (st = cuda_fail(cudaMemsetAsync(F.freg.p, 0, sizeof(double) * 1280 * (size_t)F.n_freg, c->stream),
+                            "memset fine registers")))
+            return st;
+    }
+    if (L.n_runs > 0) {  // z-runs of groups as the work items
+        P.runs = L.runs.p;
+        P.run_off = L.run_off.p;
+        P.n_work = L.n_runs;
+    }
+    const int cap = c->n_sm * c->step_bps;
+    const int grid = P.n_work < cap ? P.n_work : cap;
+    {
+        int lo, hi;
+        scheme_stages(c->prm.scheme, c->prm.recon, c->prm.dual_energy, lo, hi);
+        P.stage = lo;  // MUSCL-Hancock (PLM, PPM, dual energy) or CTU: the one launch
+        if (acc_n) {  // the gravity coupling's predictor
+            P.stage = c->prm.scheme == AMR_SCHEME_CTU ? ST_CTU_GRAV : ST_MH_GRAV;
+            P.acc_n = acc_n;
+        }
+    }
+    if (c->prm.scheme == AMR_SCHEME_VL) {  // predictor into U*, then the corrector
+        StepParams H = P;
+        H.stage = ST_VL_PRED;
+        H.U_new = L.ustar.p;
+        H.smax_out = H.n_bad = H.clear2 = nullptr;
+        H.time_rec = nullptr;
+        H.cf = CFRegs{nullptr, nullptr, nullptr, nullptr};
+        H.fb_count = nullptr;
+        H.fb_list = nullptr;
+        if ((st = launch_step(c, H, grid))) return st;
+        // refined levels: the half step of the ghost cells the corrector reads
+        if (L.n_ghost && (st = launch_vl_ghost_pred(c, level, H))) return st;
+        P.stage = ST_VL_CORR;
+        P.U_base = P.U_old;
+        P.U_old = L.ustar.p;
+        if (L.n_ghost) P.ghost = L.ghost_ustar.p;
+    }
+    if ((st = launch_step(c, P, grid))) return st;
+    {
+        StepParams R = P;  // the cell remedies recompute from U^n: its ghosts
+        R.ghost = L.ghost.p;
+        if ((st = launch_cell_remedies(c, R, P.stage == ST_VL_CORR ? P.U_base : P.U_old, stage_ctu(P.stage),
+                                       c->stream)))
+            return st;
+    }
+
+    return AMR_OK;
+}
+
 // One step of a level (the body of amr_hydro_advance_level without the
 // retry of remedy (iv)); acc_n: the gravity predictor's acceleration at t^n
 // (null: no gravity); c_acc > 0 with dt < 0: dt also obeys Eq. (acc) on acc_n.
@@ -191,54 +248,42 @@ amr_status advance_once(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphy
     P.cf.fine_buf = L.freg.p;
     P.cf.coarse_off = L.n_creg ? L.coarse_off.p : nullptr;
     P.cf.coarse_buf = L.creg.p;
-    if (level < c->prm.lmax) {  // a coarse step restarts the fine level's flux sums
-        Level &F = c->lv[level + 1];
-        if (F.n_patches && F.n_freg &&
-            (st = cuda_fail(cudaMemsetAsync(F.freg.p, 0, sizeof(double) * 1280 * (size_t)F.n_freg, c->stream),
-                            "memset fine registers")))
+    // On a refined hierarchy the launches of the level step (the fine
+    // registers' reset, the persistent step launch over all the level's
+    // groups -- two with VL, plus the ghost half step -- and the cell
+    // remedies) are captured into one CUDA graph per level: each step's
+    // capture updates the level's instantiated graph in place
+    // (cudaGraphExecUpdate: same nodes, new parameters, also after a regrid)
+    // and the graph runs on the context's stream.
+    const bool as_graph = c->prm.lmax > 0;
+    cudaStream_t stream0 = c->stream;
+    if (as_graph) {
+        if (!c->capture_stream &&
+            (st = cuda_fail(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking), "stream")))
             return st;
+        if ((st = cuda_fail(cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal), "capture")))
+            return st;
+        c->stream = c->capture_stream;
     }
-    if (L.n_runs > 0) {  // z-runs of groups as the work items
-        P.runs = L.runs.p;
-        P.run_off = L.run_off.p;
-        P.n_work = L.n_runs;
-    }
-    const int cap = c->n_sm * c->step_bps;
-    const int grid = P.n_work < cap ? P.n_work : cap;
-    {
-        int lo, hi;
-        scheme_stages(c->prm.scheme, c->prm.recon, c->prm.dual_energy, lo, hi);
-        P.stage = lo;  // MUSCL-Hancock (PLM, PPM, dual energy) or CTU: the one launch
-        if (acc_n) {  // the gravity coupling's predictor
-            P.stage = c->prm.scheme == AMR_SCHEME_CTU ? ST_CTU_GRAV : ST_MH_GRAV;
-            P.acc_n = acc_n;
+    st = launch_level_step(c, level, P, acc_n);
+    if (as_graph) {
+        c->stream = stream0;
+        cudaGraph_t gr = nullptr;
+        const amr_status ce = cuda_fail(cudaStreamEndCapture(c->capture_stream, &gr), "end capture");
+        if (!st) st = ce;
+        if (!st && L.gexec) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(L.gexec, gr, &info) != cudaSuccess) {  // the nodes changed
+                cudaGetLastError();
+                cudaGraphExecDestroy(L.gexec);
+                L.gexec = nullptr;
+            }
         }
+        if (!st && !L.gexec) st = cuda_fail(cudaGraphInstantiate(&L.gexec, gr, 0), "instantiate");
+        if (gr) cudaGraphDestroy(gr);
+        if (!st) st = cuda_fail(cudaGraphLaunch(L.gexec, c->stream), "graph launch");
     }
-    if (c->prm.scheme == AMR_SCHEME_VL) {  // predictor into U*, then the corrector
-        StepParams H = P;
-        H.stage = ST_VL_PRED;
-        H.U_new = L.ustar.p;
-        H.smax_out = H.n_bad = H.clear2 = nullptr;
-        H.time_rec = nullptr;
-        H.cf = CFRegs{nullptr, nullptr, nullptr, nullptr};
-        H.fb_count = nullptr;
-        H.fb_list = nullptr;
-        if ((st = launch_step(c, H, grid))) return st;
-        // refined levels: the half step of the ghost cells the corrector reads
-        if (L.n_ghost && (st = launch_vl_ghost_pred(c, level, H))) return st;
-        P.stage = ST_VL_CORR;
-        P.U_base = P.U_old;
-        P.U_old = L.ustar.p;
-        if (L.n_ghost) P.ghost = L.ghost_ustar.p;
-    }
-    if ((st = launch_step(c, P, grid))) return st;
-    {
-        StepParams R = P;  // the cell remedies recompute from U^n: its ghosts
-        R.ghost = L.ghost.p;
-        if ((st = launch_cell_remedies(c, R, P.stage == ST_VL_CORR ? P.U_base : P.U_old, stage_ctu(P.stage),
-                                       c->stream)))
-            return st;
-    }
+    if (st) return st;
 
     L.cur = 1 - L.cur;
     L.version++;

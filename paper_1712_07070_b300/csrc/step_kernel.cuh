@@ -424,10 +424,12 @@ __device__ __forceinline__ void face_values(const SM &S, int X, int Y, int z, co
 // PLM q, after the Hancock step with F_s = s v_n.  The gravity predictor
 // (ST_MH_GRAV) adds (dt/2) (0, rho_f ga, m_f . ga) of each reconstructed face
 // state, ga the cell's acceleration at t^n (dt_half = dt/2).
+// only_dim >= 0: only the two face states along that dimension are wanted
+// (a ghost-ring cell of the group, whose other faces no face solve reads).
 template <typename real, int STAGE, typename SM>
 __device__ __forceinline__ void hancock_cell(const SM &S, int x, int y, int z, real dtdh_half, const Gas<real> &g,
                                              real uf[6][NV], real us[6], const real ga[3] = nullptr,
-                                             real dt_half = real(0)) {
+                                             real dt_half = real(0), int only_dim = -1) {
     using G = typename SM::Geo;
     const int X = x + G::OX, Y = y + G::OY;
     if constexpr (STAGE == ST_VL_PRED) {
@@ -469,6 +471,7 @@ __device__ __forceinline__ void hancock_cell(const SM &S, int x, int y, int z, r
         if constexpr (STAGE == ST_MH_GRAV) {
 #pragma unroll
             for (int f = 0; f < 6; f++) {
+                if (only_dim >= 0 && (f >> 1) != only_dim) continue;
                 real src[NV];
                 src[0] = real(0);
                 src[1] = uf[f][0] * ga[0];
@@ -480,13 +483,18 @@ __device__ __forceinline__ void hancock_cell(const SM &S, int x, int y, int z, r
             }
         } else if constexpr (hancock) {
 #pragma unroll
-            for (int f = 0; f < 6; f++)
+            for (int f = 0; f < 6; f++) {
+                if (only_dim >= 0 && (f >> 1) != only_dim) continue;
 #pragma unroll
                 for (int v = 0; v < NV; v++) uf[f][v] += dtdh_half * inc[v];
+            }
         }
         if constexpr (SM::DE) {
 #pragma unroll
-            for (int f = 0; f < 6; f++) us[f] += dtdh_half * incs;
+            for (int f = 0; f < 6; f++) {
+                if (only_dim >= 0 && (f >> 1) != only_dim) continue;
+                us[f] += dtdh_half * incs;
+            }
         }
     }
 }
@@ -765,7 +773,7 @@ __device__ __forceinline__ void step_run(SM &S, const StepParams &P, const int32
             const int y = xring ? r : (side ? GE : -1);
             real uf[6][NV], us[6], ga[3];
             if constexpr (STAGE == ST_MH_GRAV) grav_at(S, P, kz & 1, x, y, zl, ga);
-            hancock_cell<real, STAGE>(S, x, y, z, dtdh_half, g, uf, us, ga, dt_half);
+            hancock_cell<real, STAGE>(S, x, y, z, dtdh_half, g, uf, us, ga, dt_half, xring ? 0 : 1);
             if (xring) {
 #pragma unroll
                 for (int v = 0; v < NV; v++) {
@@ -993,6 +1001,7 @@ __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydr
 // A box registered with amr_hydro_set_box: a fully covered periodic level.
 struct BoxDesc {
     double *U[2];
+    double *S[2];                 // dual-energy entropy fields (null without dual energy)
     double *ustar;                // VL half-step state (null for MUSCL-Hancock)
     const int32_t *nbr;           // [n_groups][64]
     unsigned long long *scal;     // the box's 8 scalar slots (ring of speeds, counts)
@@ -1013,6 +1022,7 @@ struct BoxLaunch {
     double dt_override; // >= 0 (autotuning): fixed dt, no logging
     double *dt_log;     // [steps][n_boxes] or null
     int n_boxes;
+    double de_xi;       // dual energy (ST_MH_DE): the threshold on E_the / E_kin
 };
 
 // MODE 0: the default scheme (van Leer-type limiter, HLLC) as compile-time
@@ -1070,6 +1080,9 @@ __global__ void __launch_bounds__(StepCfg<real>::NT, StepCfg<real>::MINB) k_hydr
         P.U_old = STAGE == ST_VL_CORR ? d.ustar : d.U[cur];
         P.U_new = STAGE == ST_VL_PRED ? d.ustar : d.U[1 - cur];
         P.U_base = d.U[cur];
+        P.S_old = d.S[cur];
+        P.S_new = d.S[1 - cur];
+        P.de_xi = B.de_xi;
         P.stage = STAGE;
         P.fallback = B.fallback;
         P.nbr = d.nbr;

@@ -74,3 +74,41 @@ def test_cold_fast_shear_keeps_its_pressure():
     assert (rel_l1(out, ref) <= 1e-12).all()
     p = (G53 - 1) * (out[4] - 0.5 * (out[1] ** 2 + out[2] ** 2 + out[3] ** 2) / out[0])
     assert np.abs(p / P0 - 1).max() < 1e-4
+
+
+@pytest.mark.parametrize("prec", [A.AMR_FP64, A.AMR_FP32_ACC64])
+def test_box_batch_dual_energy(prec):
+    """Dual energy in the box batch (one persistent launch per step, graph,
+    per-box device dt): every box against the oracle's step_dual with the
+    box's own Eq. (CFL2) step, the correction active everywhere (xi huge)
+    and, on a cold fast shear box, at the default threshold."""
+    from paper_1712_07070_b300.boxes import BoxBatch
+    xi = 1e300
+    B = BoxBatch(gamma=G53, prec=prec, scheme={"dual_energy": 1, "dual_xi": xi})
+    sizes = [32, 16, 48]
+    U0 = [ics.sod_noise(n, seed=20 + i) for i, n in enumerate(sizes)]
+    S0 = [oracle.entropy(U, G53) * (1.0 + 0.05 * np.random.default_rng(i).random(U.shape[1:]))
+          for i, U in enumerate(U0)]
+    for U, S in zip(U0, S0):
+        B.add_box(U, S)
+    dts = B.advance(3).cpu().numpy()
+    for i, n in enumerate(sizes):
+        ref, Sr = U0[i], S0[i]
+        for k in range(3):
+            dt = oracle.dt_cfl2(ref, G53, 0.5, 1.0 / n)
+            assert abs(dts[k, i] - dt) <= (1e-14 if prec == A.AMR_FP64 else 1e-6) * dt
+            ref, Sr, nbad = oracle.step_dual(ref, Sr, 1.0 / n, dts[k, i], G53, xi)
+            assert nbad == 0
+        assert (rel_l1(B.download(i), ref) <= TOL[prec]).all(), n
+        S = B.entropy(i)
+        assert np.abs(S - Sr).sum() <= TOL[prec] * np.abs(Sr).sum(), n
+    B.close()
+
+
+def test_box_batch_dual_energy_requires_entropy_fields():
+    from paper_1712_07070_b300.boxes import BoxBatch
+    B = BoxBatch(gamma=G53, scheme={"dual_energy": 1})
+    B.add_box(ics.sod_noise(16, seed=1))  # no entropy registered
+    with pytest.raises(A.AmrHydroError):
+        B.advance(1)
+    B.close()
