@@ -12,6 +12,10 @@ Paper passages followed:
     the C_inc / C_dec synchronisation rule of the section's pseudo-code.
   * section 2.2: restriction and coarse-fine flux fix-up at synchronisation.
   * section 2.6: Eq. (CFL2) per level.
+  * section 2.2 dual-energy formalism (optional, S_root given): the entropy
+    per unit volume S of every level is a conserved density carried through
+    the same operations -- the step (or_step_dual_fx), ghost interpolation,
+    flux registers and fix-up, restriction, and the data of new patches.
 
 Each level is a dense whole-domain array with a patch mask (see amr_oracle.c).
 """
@@ -43,10 +47,19 @@ def amr_lib():
             "or_amr_prolong_patches": [_dp, _u8p, _i3, _dp],
             "or_step_periodic_fx": [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_double, _dp],
+            "or_step_dual_fx": [_dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _dp],
+            "or_amr_fill_ghost_s": [_dp, _u8p, _i3, _dp, _dp, _dp, _dp, ctypes.c_double],
+            "or_amr_cf_fine_accumulate_s": [_dp, _dp, _u8p, _u8p, _i3, ctypes.c_double],
+            "or_amr_cf_coarse_store_s": [_dp, _dp, _u8p, _u8p, _i3, ctypes.c_double],
+            "or_amr_fixup_s": [_dp, _dp, _dp, _u8p, _u8p, _i3, ctypes.c_double],
+            "or_amr_restrict_s": [_dp, _dp, _u8p, _i3],
+            "or_amr_prolong_patches_s": [_dp, _u8p, _i3, _dp, _dp],
         }.items():
             fn = getattr(L, name)
             fn.argtypes = args
         L.or_step_periodic_fx.restype = ctypes.c_int64
+        L.or_step_dual_fx.restype = ctypes.c_int64
         _amr = L
     return _amr
 
@@ -74,7 +87,7 @@ def cell_mask(mask):
 
 
 class Level:
-    def __init__(self, N):
+    def __init__(self, N, dual=False):
         self.N = list(N)  # cells per dimension (x, y, z)
         self.mask = np.zeros((N[2] // 8, N[1] // 8, N[0] // 8), np.uint8)
         self.U = np.zeros((5, N[2], N[1], N[0]))
@@ -84,6 +97,11 @@ class Level:
         self.acc = np.zeros((3, 5, N[2], N[1], N[0]))   # fine-flux sums on this (coarse) level's faces
         self.cfl = np.zeros((3, 5, N[2], N[1], N[0]))   # dt_c * F_c on this level's coarse-fine faces
         self.dt_prev = None
+        if dual:  # the entropy per unit volume and its flux registers
+            self.S = np.ones((N[2], N[1], N[0]))
+            self.S_prev = self.S.copy()
+            self.acc_s = np.zeros((3, N[2], N[1], N[0]))
+            self.cfl_s = np.zeros((3, N[2], N[1], N[0]))
 
     @property
     def empty(self):
@@ -92,17 +110,22 @@ class Level:
 
 class OracleHierarchy:
     def __init__(self, U_root, lmax, gamma, cfl, theta, nbuf, c_inc=0.1, c_dec=0.1, box=1.0,
-                 regrid_at_start=True):
+                 regrid_at_start=True, S_root=None, dual_xi=1e-2):
         _, nz, ny, nx = U_root.shape
         self.root_n = (nx, ny, nz)
         self.lmax, self.gamma, self.cfl_c, self.theta = lmax, gamma, cfl, theta
         self.nbuf = list(nbuf)
         self.c_inc, self.c_dec, self.box = c_inc, c_dec, box
-        self.lv = [Level([n << l for n in self.root_n]) for l in range(lmax + 1)]
+        self.dual = S_root is not None
+        self.dual_xi = dual_xi
+        self.lv = [Level([n << l for n in self.root_n], self.dual) for l in range(lmax + 1)]
         L0 = self.lv[0]
         L0.mask[:] = 1
         L0.U = np.ascontiguousarray(U_root, dtype=np.float64).copy()
         L0.U_prev = L0.U.copy()
+        if self.dual:
+            L0.S = np.ascontiguousarray(S_root, dtype=np.float64).copy()
+            L0.S_prev = L0.S.copy()
         self.n_updates = 0
         self.log = []  # (level, dt) of every level step, in order
         if regrid_at_start:
@@ -134,6 +157,9 @@ class OracleHierarchy:
         else:
             w = (t - c.t_prev) / (c.t - c.t_prev)
         amr_lib().or_amr_fill_ghost(_ptr(f.U), _u8(f.mask), _dims(f.N), _ptr(c.U_prev), _ptr(c.U), w)
+        if self.dual:
+            amr_lib().or_amr_fill_ghost_s(_ptr(f.S), _u8(f.mask), _dims(f.N), _ptr(c.S_prev), _ptr(c.S),
+                                          _ptr(c.U_prev), _ptr(c.U), w)
 
     def min_dt(self, l):
         """The scheme's CFL condition (Eq. CFL2, CFL1 for CTU) over the cells of
@@ -152,10 +178,23 @@ class OracleHierarchy:
         N = L.N
         Un = np.empty_like(L.U)
         FX = np.empty((3, 5, N[2], N[1], N[0]))
-        amr_lib().or_step_periodic_fx(_ptr(L.U), _ptr(Un), N[0], N[1], N[2], self.dh(l), dt, self.gamma, _ptr(FX))
+        if self.dual:
+            Sn = np.empty_like(L.S)
+            FXs = np.empty((3, N[2], N[1], N[0]))
+            nb = amr_lib().or_step_dual_fx(_ptr(L.U), _ptr(L.S), _ptr(Un), _ptr(Sn), N[0], N[1], N[2], self.dh(l),
+                                           dt, self.gamma, self.dual_xi, _ptr(FX), _ptr(FXs))
+            if nb < 0:
+                raise ValueError("dual energy is built for MUSCL-Hancock only")
+        else:
+            amr_lib().or_step_periodic_fx(_ptr(L.U), _ptr(Un), N[0], N[1], N[2], self.dh(l), dt, self.gamma,
+                                          _ptr(FX))
         pres = self.present(l)
         new = L.U.copy()
         new[:, pres] = Un[:, pres]
+        if self.dual:
+            news = L.S.copy()
+            news[pres] = Sn[pres]
+            L.S_prev, L.S = L.S, news
         rho = new[0][pres]
         v2 = (new[1][pres] ** 2 + new[2][pres] ** 2 + new[3][pres] ** 2) / rho
         if not ((rho > 0).all() and (new[4][pres] - 0.5 * v2 > 0).all()):
@@ -168,10 +207,16 @@ class OracleHierarchy:
             c = self.lv[l - 1]
             cov = covered(L.mask, N)
             amr_lib().or_amr_cf_fine_accumulate(_ptr(c.acc), _ptr(FX), _u8(cov), _u8(c.mask), _dims(c.N), dt)
+            if self.dual:
+                amr_lib().or_amr_cf_fine_accumulate_s(_ptr(c.acc_s), _ptr(FXs), _u8(cov), _u8(c.mask), _dims(c.N),
+                                                      dt)
         if l < self.lmax and not self.lv[l + 1].empty:
             cov = covered(self.lv[l + 1].mask, self.lv[l + 1].N)
             amr_lib().or_amr_cf_coarse_store(_ptr(L.cfl), _ptr(FX), _u8(cov), _u8(L.mask), _dims(N), dt)
             L.acc[:] = 0.0
+            if self.dual:
+                amr_lib().or_amr_cf_coarse_store_s(_ptr(L.cfl_s), _ptr(FXs), _u8(cov), _u8(L.mask), _dims(N), dt)
+                L.acc_s[:] = 0.0
 
     def flux_fixup(self, l):
         """Section 2.2 synchronisation of level l with level l+1."""
@@ -179,6 +224,10 @@ class OracleHierarchy:
         cov = covered(f.mask, f.N)
         amr_lib().or_amr_fixup(_ptr(c.U), _ptr(c.acc), _ptr(c.cfl), _u8(cov), _u8(c.mask), _dims(c.N), self.dh(l))
         amr_lib().or_amr_restrict(_ptr(c.U), _ptr(f.U), _u8(cov), _dims(c.N))
+        if self.dual:
+            amr_lib().or_amr_fixup_s(_ptr(c.S), _ptr(c.acc_s), _ptr(c.cfl_s), _u8(cov), _u8(c.mask), _dims(c.N),
+                                     self.dh(l))
+            amr_lib().or_amr_restrict_s(_ptr(c.S), _ptr(f.S), _u8(cov), _dims(c.N))
 
     # ---- W-cycle (section 2.1 pseudo-code) -------------------------------------------
 
@@ -265,6 +314,13 @@ class OracleHierarchy:
         F.U = Unew
         F.mask = newmask
         F.U_prev = F.U.copy()
+        if self.dual:
+            Snew = F.S.copy()
+            if created.any():
+                amr_lib().or_amr_prolong_patches_s(_ptr(Snew), _u8(created.astype(np.uint8)), _dims(F.N),
+                                                   _ptr(L.S), _ptr(L.U))
+            F.S = Snew
+            F.S_prev = F.S.copy()
         F.t = F.t_prev = L.t
         if F.empty:
             F.dt_prev = None

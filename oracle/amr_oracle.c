@@ -60,8 +60,8 @@ static double coarse_at(const double *Uo, const double *Un, double w, int v, int
  * cell would have rho <= 0 or P <= 0 (2 rho E <= |rho v|^2), all eight take
  * U_c (slopes zeroed), which stays conservative and positive.
  */
-static void interp_cell(const double *Uo, const double *Un, double w, const int Nc[3], int x, int y,
-                        int z, double out[NV]) {
+static int interp_cell(const double *Uo, const double *Un, double w, const int Nc[3], int x, int y,
+                       int z, double out[NV]) {
     const int cx = x / 2, cy = y / 2, cz = z / 2;
     double c[NV], sl[3][NV];
     for (int v = 0; v < NV; v++) {
@@ -84,6 +84,7 @@ static void interp_cell(const double *Uo, const double *Un, double w, const int 
     const double sx = (x & 1) ? 0.25 : -0.25, sy = (y & 1) ? 0.25 : -0.25, sz = (z & 1) ? 0.25 : -0.25;
     for (int v = 0; v < NV; v++)
         out[v] = ok ? c[v] + sx * sl[0][v] + sy * sl[1][v] + sz * sl[2][v] : c[v];
+    return ok;
 }
 
 /*
@@ -159,8 +160,8 @@ static int cf_face(const uint8_t *covered, const uint8_t *pmask_c, const int Nc[
  * summed in a fixed order.  FXf: fine-level interface fluxes of that step,
  * [3][5][Nf cells] at the high face of every fine cell.  acc: [3][5][Nc].
  */
-void or_amr_cf_fine_accumulate(double *acc, const double *FXf, const uint8_t *covered,
-                               const uint8_t *pmask_c, const int Nc[3], double dt_f) {
+static void cf_fine_accumulate_nv(double *acc, const double *FXf, const uint8_t *covered, const uint8_t *pmask_c,
+                                  const int Nc[3], double dt_f, int nv) {
     const int Nf[3] = {2 * Nc[0], 2 * Nc[1], 2 * Nc[2]};
     const int64_t nc = (int64_t)Nc[0] * Nc[1] * Nc[2], nf = 8 * nc;
     for (int d = 0; d < 3; d++)
@@ -172,22 +173,33 @@ void or_amr_cf_fine_accumulate(double *acc, const double *FXf, const uint8_t *co
                     const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
                     int f[3];
                     f[d] = 2 * c[d] + 1; /* fine cell whose high face is the interface */
-                    for (int v = 0; v < NV; v++) {
+                    for (int v = 0; v < nv; v++) {
                         double s = 0.0;
                         for (int j2 = 0; j2 < 2; j2++)
                             for (int j1 = 0; j1 < 2; j1++) {
                                 f[t1] = 2 * c[t1] + j1;
                                 f[t2] = 2 * c[t2] + j2;
-                                s += FXf[((int64_t)d * NV + v) * nf + cidx(f[0], f[1], f[2], Nf)];
+                                s += FXf[((int64_t)d * nv + v) * nf + cidx(f[0], f[1], f[2], Nf)];
                             }
-                        acc[((int64_t)d * NV + v) * nc + cidx(x, y, z, Nc)] += dt_f * (0.25 * s);
+                        acc[((int64_t)d * nv + v) * nc + cidx(x, y, z, Nc)] += dt_f * (0.25 * s);
                     }
                 }
 }
 
+void or_amr_cf_fine_accumulate(double *acc, const double *FXf, const uint8_t *covered,
+                               const uint8_t *pmask_c, const int Nc[3], double dt_f) {
+    cf_fine_accumulate_nv(acc, FXf, covered, pmask_c, Nc, dt_f, NV);
+}
+
+/* The same for the dual-energy entropy's flux (one variable: [3][Nf], [3][Nc]). */
+void or_amr_cf_fine_accumulate_s(double *acc, const double *FXf, const uint8_t *covered,
+                                 const uint8_t *pmask_c, const int Nc[3], double dt_f) {
+    cf_fine_accumulate_nv(acc, FXf, covered, pmask_c, Nc, dt_f, 1);
+}
+
 /* Coarse side: cfl = dt_c * F_c on every coarse-fine face (0 elsewhere). */
-void or_amr_cf_coarse_store(double *cfl, const double *FXc, const uint8_t *covered,
-                            const uint8_t *pmask_c, const int Nc[3], double dt_c) {
+static void cf_coarse_store_nv(double *cfl, const double *FXc, const uint8_t *covered, const uint8_t *pmask_c,
+                               const int Nc[3], double dt_c, int nv) {
     const int64_t nc = (int64_t)Nc[0] * Nc[1] * Nc[2];
     for (int d = 0; d < 3; d++)
         for (int z = 0; z < Nc[2]; z++)
@@ -195,11 +207,21 @@ void or_amr_cf_coarse_store(double *cfl, const double *FXc, const uint8_t *cover
                 for (int x = 0; x < Nc[0]; x++) {
                     const int64_t i = cidx(x, y, z, Nc);
                     const int on = cf_face(covered, pmask_c, Nc, x, y, z, d);
-                    for (int v = 0; v < NV; v++) {
-                        const int64_t k = ((int64_t)d * NV + v) * nc + i;
+                    for (int v = 0; v < nv; v++) {
+                        const int64_t k = ((int64_t)d * nv + v) * nc + i;
                         cfl[k] = on ? dt_c * FXc[k] : 0.0;
                     }
                 }
+}
+
+void or_amr_cf_coarse_store(double *cfl, const double *FXc, const uint8_t *covered,
+                            const uint8_t *pmask_c, const int Nc[3], double dt_c) {
+    cf_coarse_store_nv(cfl, FXc, covered, pmask_c, Nc, dt_c, NV);
+}
+
+void or_amr_cf_coarse_store_s(double *cfl, const double *FXc, const uint8_t *covered,
+                              const uint8_t *pmask_c, const int Nc[3], double dt_c) {
+    cf_coarse_store_nv(cfl, FXc, covered, pmask_c, Nc, dt_c, 1);
 }
 
 /*
@@ -208,8 +230,8 @@ void or_amr_cf_coarse_store(double *cfl, const double *FXc, const uint8_t *cover
  * face on its low side U_c += (acc - cfl)/dh_c; faces are applied in the
  * order -x, +x, -y, +y, -z, +z.
  */
-void or_amr_fixup(double *Uc, const double *acc, const double *cfl, const uint8_t *covered,
-                  const uint8_t *pmask_c, const int Nc[3], double dh_c) {
+static void fixup_nv(double *Uc, const double *acc, const double *cfl, const uint8_t *covered, const uint8_t *pmask_c,
+                     const int Nc[3], double dh_c, int nv) {
     const int64_t nc = (int64_t)Nc[0] * Nc[1] * Nc[2];
     for (int z = 0; z < Nc[2]; z++)
         for (int y = 0; y < Nc[1]; y++)
@@ -223,22 +245,32 @@ void or_amr_fixup(double *Uc, const double *acc, const double *cfl, const uint8_
                     p[d] = wrapi(c[d] + 1, Nc[d]);
                     const int64_t im = cidx(m[0], m[1], m[2], Nc), ip = cidx(p[0], p[1], p[2], Nc);
                     if (covered[im]) /* low face: the interface is the high face of m */
-                        for (int v = 0; v < NV; v++) {
-                            const int64_t k = ((int64_t)d * NV + v) * nc + im;
+                        for (int v = 0; v < nv; v++) {
+                            const int64_t k = ((int64_t)d * nv + v) * nc + im;
                             Uc[v * nc + i] += (acc[k] - cfl[k]) / dh_c;
                         }
                     if (covered[ip]) /* high face */
-                        for (int v = 0; v < NV; v++) {
-                            const int64_t k = ((int64_t)d * NV + v) * nc + i;
+                        for (int v = 0; v < nv; v++) {
+                            const int64_t k = ((int64_t)d * nv + v) * nc + i;
                             Uc[v * nc + i] -= (acc[k] - cfl[k]) / dh_c;
                         }
                 }
             }
 }
 
+void or_amr_fixup(double *Uc, const double *acc, const double *cfl, const uint8_t *covered,
+                  const uint8_t *pmask_c, const int Nc[3], double dh_c) {
+    fixup_nv(Uc, acc, cfl, covered, pmask_c, Nc, dh_c, NV);
+}
+
+void or_amr_fixup_s(double *Sc, const double *acc, const double *cfl, const uint8_t *covered,
+                    const uint8_t *pmask_c, const int Nc[3], double dh_c) {
+    fixup_nv(Sc, acc, cfl, covered, pmask_c, Nc, dh_c, 1);
+}
+
 /* Restriction (section 2.2): every covered coarse cell becomes the mean of
  * its 8 children, summed in the order x fastest, then y, then z. */
-void or_amr_restrict(double *Uc, const double *Uf, const uint8_t *covered, const int Nc[3]) {
+static void restrict_nv(double *Uc, const double *Uf, const uint8_t *covered, const int Nc[3], int nv) {
     const int Nf[3] = {2 * Nc[0], 2 * Nc[1], 2 * Nc[2]};
     const int64_t nc = (int64_t)Nc[0] * Nc[1] * Nc[2], nf = 8 * nc;
 #pragma omp parallel for schedule(static)
@@ -247,7 +279,7 @@ void or_amr_restrict(double *Uc, const double *Uf, const uint8_t *covered, const
             for (int x = 0; x < Nc[0]; x++) {
                 const int64_t i = cidx(x, y, z, Nc);
                 if (!covered[i]) continue;
-                for (int v = 0; v < NV; v++) {
+                for (int v = 0; v < nv; v++) {
                     double s = 0.0;
                     for (int dz = 0; dz < 2; dz++)
                         for (int dy = 0; dy < 2; dy++)
@@ -256,6 +288,14 @@ void or_amr_restrict(double *Uc, const double *Uf, const uint8_t *covered, const
                     Uc[v * nc + i] = s * 0.125;
                 }
             }
+}
+
+void or_amr_restrict(double *Uc, const double *Uf, const uint8_t *covered, const int Nc[3]) {
+    restrict_nv(Uc, Uf, covered, Nc, NV);
+}
+
+void or_amr_restrict_s(double *Sc, const double *Sf, const uint8_t *covered, const int Nc[3]) {
+    restrict_nv(Sc, Sf, covered, Nc, 1);
 }
 
 /*
@@ -327,4 +367,62 @@ void or_amr_prolong_patches(double *Uf, const uint8_t *newmask, const int Nf[3],
                 interp_cell(Uc, Uc, 1.0, Nc, x, y, z, u);
                 for (int v = 0; v < NV; v++) Uf[v * nf + i] = u[v];
             }
+}
+
+/*
+ * The dual-energy entropy per unit volume on refined levels (section 2.2
+ * dual-energy formalism on the section 2.1 hierarchy): a conserved density,
+ * interpolated like the conserved variables -- time first, then
+ * S_f = S_c + sum_d (+-1/4) s_d with s_d = minmod(S_{c+d} - S_c, S_c - S_{c-d})
+ * -- and sharing their positivity decision: where the conserved variables'
+ * children fall back to the parent value (ok == 0), so does the entropy.
+ */
+static double interp_scalar(const double *So, const double *Sn, double w, const int Nc[3], int x, int y, int z,
+                            int ok) {
+    const int cx = x / 2, cy = y / 2, cz = z / 2;
+    const double c = coarse_at(So, Sn, w, 0, cx, cy, cz, Nc);
+    const double s0 = minmod(coarse_at(So, Sn, w, 0, cx + 1, cy, cz, Nc) - c, c - coarse_at(So, Sn, w, 0, cx - 1, cy, cz, Nc));
+    const double s1 = minmod(coarse_at(So, Sn, w, 0, cx, cy + 1, cz, Nc) - c, c - coarse_at(So, Sn, w, 0, cx, cy - 1, cz, Nc));
+    const double s2 = minmod(coarse_at(So, Sn, w, 0, cx, cy, cz + 1, Nc) - c, c - coarse_at(So, Sn, w, 0, cx, cy, cz - 1, Nc));
+    const double sx = (x & 1) ? 0.25 : -0.25, sy = (y & 1) ? 0.25 : -0.25, sz = (z & 1) ? 0.25 : -0.25;
+    return ok ? c + sx * s0 + sy * s1 + sz * s2 : c;
+}
+
+/* Entropy ghosts of level l from level l-1 (the cells or_amr_fill_ghost fills). */
+void or_amr_fill_ghost_s(double *Sf, const uint8_t *pmask_f, const int Nf[3], const double *Sc_old,
+                         const double *Sc_new, const double *Uc_old, const double *Uc_new, double w) {
+    const int Nc[3] = {Nf[0] / 2, Nf[1] / 2, Nf[2] / 2};
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < Nf[2]; z++)
+        for (int y = 0; y < Nf[1]; y++)
+            for (int x = 0; x < Nf[0]; x++) {
+                if (patch_present(pmask_f, Nf, x, y, z)) continue;
+                int near = 0;
+                for (int dz = -3; dz <= 3 && !near; dz += 3)
+                    for (int dy = -3; dy <= 3 && !near; dy += 3)
+                        for (int dx = -3; dx <= 3 && !near; dx += 3)
+                            near = patch_present(pmask_f, Nf, x + dx, y + dy, z + dz);
+                if (!near) {
+                    Sf[cidx(x, y, z, Nf)] = 1.0;
+                    continue;
+                }
+                double u[NV];
+                const int ok = interp_cell(Uc_old, Uc_new, w, Nc, x, y, z, u);
+                Sf[cidx(x, y, z, Nf)] = interp_scalar(Sc_old, Sc_new, w, Nc, x, y, z, ok);
+            }
+}
+
+/* Entropy of newly created patches of the fine level, from the coarse S. */
+void or_amr_prolong_patches_s(double *Sf, const uint8_t *newmask, const int Nf[3], const double *Sc,
+                              const double *Uc) {
+    const int Nc[3] = {Nf[0] / 2, Nf[1] / 2, Nf[2] / 2};
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < Nf[2]; z++)
+        for (int y = 0; y < Nf[1]; y++)
+            for (int x = 0; x < Nf[0]; x++)
+                if (patch_present(newmask, Nf, x, y, z)) {
+                    double u[NV];
+                    const int ok = interp_cell(Uc, Uc, 1.0, Nc, x, y, z, u);
+                    Sf[cidx(x, y, z, Nf)] = interp_scalar(Sc, Sc, 1.0, Nc, x, y, z, ok);
+                }
 }

@@ -203,6 +203,7 @@ static void or_grav_faces(double *FS, double Uf[6][NV], const double *gfield, in
 /* dual energy: the entropy fields of the step in progress (or_step_dual) */
 static const double *or_de_S = NULL;
 static double *or_de_Snew = NULL, or_de_xi = 0.0;
+static double *or_de_FXs_out = NULL; /* the scalar's face fluxes [3][cells] (or_step_dual_fx) */
 static double or_theta = 1.5;
 
 void or_set_vl(int on) { or_vl = on; }
@@ -908,6 +909,7 @@ int64_t or_step_periodic_fx(const double *U, double *Unew, int nx, int ny, int n
             }
 
     if (FX_out) memcpy(FX_out, FX, sizeof(double) * 3 * NV * n);
+    if (or_de_FXs_out && FXs) memcpy(or_de_FXs_out, FXs, sizeof(double) * 3 * n);
     free(Q);
     free(FSs);
     free(FXs);
@@ -944,6 +946,23 @@ int64_t or_step_dual(const double *U, const double *S, double *Unew, double *Sne
     int64_t nbad = or_step_periodic_fx(U, Unew, nx, ny, nz, dh, dt, gamma, NULL);
     or_de_S = NULL;
     or_de_Snew = NULL;
+    return nbad;
+}
+
+/* or_step_dual that also returns the face fluxes through the high face of
+ * every cell: FX_out [3][5][cells] of the conserved variables, FXs_out
+ * [3][cells] of the entropy (for the refined levels' flux registers). */
+int64_t or_step_dual_fx(const double *U, const double *S, double *Unew, double *Snew, int nx, int ny, int nz,
+                        double dh, double dt, double gamma, double xi, double *FX_out, double *FXs_out) {
+    if (or_vl || or_ctu) return -1;
+    or_de_S = S;
+    or_de_Snew = Snew;
+    or_de_xi = xi;
+    or_de_FXs_out = FXs_out;
+    int64_t nbad = or_step_periodic_fx(U, Unew, nx, ny, nz, dh, dt, gamma, FX_out);
+    or_de_S = NULL;
+    or_de_Snew = NULL;
+    or_de_FXs_out = NULL;
     return nbad;
 }
 
