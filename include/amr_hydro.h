@@ -131,8 +131,10 @@ typedef struct {
     double dt_min;       /* > 0: a level step that leaves unphysical cells is recomputed with
                             dt x 0.8 until it succeeds or dt < dt_min (AMR_E_UNPHYSICAL);
                             0: no retry */
-    int dual_energy;     /* 1: the dual-energy formalism (section 2.2) on single-level grids and
-                            in the box batch, with MUSCL-Hancock + PLM: the entropy per unit volume
+    int dual_energy;     /* 1: the dual-energy formalism (section 2.2) on single-level grids,
+                            refined hierarchies (the entropy is interpolated, flux-registered,
+                            fixed up and restricted like the conserved variables) and in the
+                            box batch, with MUSCL-Hancock + PLM: the entropy per unit volume
                             s = P / rho^(gamma-1) (arrays of amr_hydro_set_entropy) is carried
                             as a passive scalar (PLM q = s / rho, F_s = mass flux x upwind q);
                             after the update E = E_kin + s rho^(gamma-1)/(gamma-1) where
@@ -239,8 +241,11 @@ amr_status amr_hydro_touch_level(amr_hydro_ctx *ctx, int level);
  * two FP64 buffers [n_patches][8][8][8] in the slot order of the level's
  * state, S_a holding s = P / rho^(gamma-1) of the current state, S_b
  * receiving the next; they swap with U_a / U_b at every step (the newest
- * is S_a after an even number of steps).  Caller-owned.  AMR_E_INVAL for a
- * context without dual energy, a level without patches, or equal buffers. */
+ * is S_a after an even number of steps).  Caller-owned.  For a refined level
+ * bound with amr_hydro_bind_level, register buffers of its capacity before
+ * the first regrid fills it: S_a pairs with U_a, S_b with U_b.  AMR_E_INVAL
+ * for a context without dual energy, a level without patches that is not
+ * bound, or equal buffers. */
 amr_status amr_hydro_set_entropy(amr_hydro_ctx *ctx, int level, double *S_a, double *S_b);
 
 /*

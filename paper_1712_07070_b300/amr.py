@@ -12,7 +12,8 @@ from . import amr_hydro as A
 
 class AmrHierarchy:
     def __init__(self, U_root, lmax, gamma=5.0 / 3.0, cfl=0.5, theta=0.05, nbuf=(8, 4), prec=A.AMR_FP64,
-                 max_patches=None, c_inc=0.1, c_dec=0.1, stream=None, device="cuda", regrid_at_start=True, scheme=None):
+                 max_patches=None, c_inc=0.1, c_dec=0.1, stream=None, device="cuda", regrid_at_start=True, scheme=None,
+                 S_root=None):
         _, nz, ny, nx = U_root.shape
         self.root = (nx, ny, nz)
         self.lmax = lmax
@@ -33,6 +34,17 @@ class AmrHierarchy:
         A.amr_hydro_pack_uniform(dense, nx, ny, nz, self.U[0][0], stream)
         torch.cuda.synchronize()
         A.amr_hydro_set_level(self.ctx, 0, n0, self.U[0][0], self.U[0][1], *self.tables[0], t=0.0)
+        # dual energy: the entropy per unit volume of every level, paired with U
+        self.S = None
+        if S_root is not None:
+            self.S = [[torch.zeros((n0, 8, 8, 8), dtype=torch.float64, device=dev) for _ in range(2)]]
+            tmp = torch.zeros_like(self.U[0][0])
+            ds = torch.zeros((5, nz, ny, nx), dtype=torch.float64, device=dev)
+            ds[0].copy_(torch.from_numpy(np.ascontiguousarray(S_root)))
+            A.amr_hydro_pack_uniform(ds, nx, ny, nz, tmp, stream)
+            torch.cuda.synchronize()
+            self.S[0][0].copy_(tmp[:, 0])
+            A.amr_hydro_set_entropy(self.ctx, 0, self.S[0][0], self.S[0][1])
         mp = p.max_patches
         for l in range(1, lmax + 1):
             U = [torch.zeros((mp, 5, 8, 8, 8), dtype=torch.float64, device=dev) for _ in range(2)]
@@ -43,6 +55,10 @@ class AmrHierarchy:
             self.U.append(U)
             self.tables.append(t)
             A.amr_hydro_bind_level(self.ctx, l, U[0], U[1], *t)
+            if self.S is not None:
+                S = [torch.zeros((mp, 8, 8, 8), dtype=torch.float64, device=dev) for _ in range(2)]
+                self.S.append(S)
+                A.amr_hydro_set_entropy(self.ctx, l, S[0], S[1])
         if regrid_at_start:
             for l in range(lmax):
                 A.amr_hydro_regrid(self.ctx, l)
@@ -65,6 +81,12 @@ class AmrHierarchy:
         n = self.n_patches(l)
         cur, _, _ = A.amr_hydro_get_state(self.ctx, l)
         return self.U[l][cur][:n]
+
+    def entropy(self, l):
+        """Dual energy: level l's current entropy per unit volume, [n_patches][8][8][8]."""
+        n = self.n_patches(l)
+        cur, _, _ = A.amr_hydro_get_state(self.ctx, l)
+        return self.S[l][cur][:n]
 
     def time(self, l):
         return A.amr_hydro_get_state(self.ctx, l)[1]

@@ -262,10 +262,8 @@ amr_status amr_hydro_init(const amr_hydro_params *p, void *stream, amr_hydro_ctx
     if (p->dual_energy != 0 && p->dual_energy != 1) return AMR_E_INVAL;
     if (!(p->dual_xi >= 0.0)) return AMR_E_INVAL;
     if (p->gravity_bc != AMR_GRAVITY_PERIODIC && p->gravity_bc != AMR_GRAVITY_ISOLATED) return AMR_E_INVAL;
-    if (p->dual_energy && (p->scheme != AMR_SCHEME_MH || p->recon != AMR_RECON_PLM || p->lmax > 0 || p->fallback))
+    if (p->dual_energy && (p->scheme != AMR_SCHEME_MH || p->recon != AMR_RECON_PLM || p->fallback))
         return AMR_E_INVAL;
-    // VL on refined levels would need the half-step state in a 3-cell ring of
-    // the coarse-fine ghost patches: single-level grids only
     for (int d = 0; d < 3; d++) {
         if (p->root_n[d] <= 0 || p->root_n[d] % 16) return AMR_E_INVAL;
         if (!p->periodic[d]) return AMR_E_INVAL;

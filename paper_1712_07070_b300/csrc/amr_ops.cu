@@ -29,13 +29,14 @@ struct CoarseView {
     const double *Uo, *Un;
     double w;
     const int *nb;  // 27 slots around the parent
+    int64_t stride = PSLOT;  // doubles per slot (PV for a one-variable field)
     // coarse value of variable v at coarse cell c (relative to the parent's
     // origin, each coordinate in -8..15), time-interpolated
     __device__ __forceinline__ double at(int v, int cx, int cy, int cz) const {
         const int px = cx >> 3, py = cy >> 3, pz = cz >> 3;
         int s = nb[(px + 1) + 3 * (py + 1) + 9 * (pz + 1)];
         if (s < 0) s = nb[13];  // cannot happen on a properly nested hierarchy
-        const int64_t i = (int64_t)s * PSLOT + v * PV + (cz & 7) * 64 + (cy & 7) * 8 + (cx & 7);
+        const int64_t i = (int64_t)s * stride + v * PV + (cz & 7) * 64 + (cy & 7) * 8 + (cx & 7);
         if (w == 0.0) return Uo[i];
         if (w == 1.0) return Un[i];
         return Uo[i] + w * (Un[i] - Uo[i]);
@@ -51,9 +52,13 @@ struct CoarseView {
 // cell of the box computes its value, slopes and positivity test once and
 // writes its eight children.
 constexpr int INTERP_WARPS = 8;  // warps per 256-thread block, two jobs in flight each
+// With So (dual energy) the entropy per unit volume is interpolated the same
+// way into outS ([slot][8^3]), sharing the conserved variables' positivity
+// decision.
 __global__ void k_interp_patches(double *__restrict__ out, const int32_t *__restrict__ out_slot,
                                  const int32_t *__restrict__ info, int n_jobs, const double *Uo,
-                                 const double *Un, double w, const int32_t *__restrict__ csib) {
+                                 const double *Un, double w, const int32_t *__restrict__ csib,
+                                 const double *So = nullptr, const double *Sn = nullptr, double *outS = nullptr) {
     __shared__ int nbs[2 * INTERP_WARPS][27];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
     int *nb = nbs[2 * warp + half];
@@ -77,7 +82,9 @@ __global__ void k_interp_patches(double *__restrict__ out, const int32_t *__rest
         const int hi[3] = {(box >> 12) & 15, (box >> 16) & 15, (box >> 20) & 15};
         const int n[3] = {(hi[0] - lo[0]) >> 1, (hi[1] - lo[1]) >> 1, (hi[2] - lo[2]) >> 1};
         CoarseView C{Uo, Un, w, nb};
-        double *o = out + (int64_t)(out_slot ? out_slot[j] : j) * PSLOT;
+        CoarseView CS{So, Sn, w, nb, PV};
+        const int64_t oslot = out_slot ? out_slot[j] : j;
+        double *o = out + oslot * PSLOT;
         const int total = n[0] * n[1] * n[2];
         for (int i = hl; i < total; i += 16) {
             // local fine cell of the child (0,0,0) of this coarse cell
@@ -109,6 +116,18 @@ __global__ void k_interp_patches(double *__restrict__ out, const int32_t *__rest
 #pragma unroll
                 for (int v = 0; v < NV; v++) o[v * PV + off] = ok ? u[k][v] : c[v];
             }
+            if (So) {
+                const double cs = CS.at(0, cx, cy, cz);
+                const double s0 = minmod(CS.at(0, cx + 1, cy, cz) - cs, cs - CS.at(0, cx - 1, cy, cz));
+                const double s1 = minmod(CS.at(0, cx, cy + 1, cz) - cs, cs - CS.at(0, cx, cy - 1, cz));
+                const double s2 = minmod(CS.at(0, cx, cy, cz + 1) - cs, cs - CS.at(0, cx, cy, cz - 1));
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    const double sx = (k & 1) ? 0.25 : -0.25, sy = (k & 2) ? 0.25 : -0.25, sz = (k & 4) ? 0.25 : -0.25;
+                    const int off = (fz + (k >> 2)) * 64 + (fy + ((k >> 1) & 1)) * 8 + fx + (k & 1);
+                    outS[oslot * PV + off] = ok ? cs + sx * s0 + sy * s1 + sz * s2 : cs;
+                }
+            }
         }
     }
 }
@@ -118,8 +137,10 @@ __global__ void k_interp_patches(double *__restrict__ out, const int32_t *__rest
 // fix[13e+7+f] = the fine register block (of the refined neighbour's child
 // group) of the same interface.  Faces in the order -x,+x,-y,+y,-z,+z: a
 // high face subtracts (dt_f-sum - dt_c F_c)/dh, a low face adds it.
+// nreg = 6 (dual energy): the registers' sixth variable fixes the entropy S.
 __global__ void k_cf_fixup(double *__restrict__ U, const int64_t *__restrict__ fix, int n_fix,
-                           const double *__restrict__ creg, const double *__restrict__ freg, double dh) {
+                           const double *__restrict__ creg, const double *__restrict__ freg, double dh,
+                           double *__restrict__ Sv = nullptr, int nreg = NV) {
     for (int e = blockIdx.x; e < n_fix; e += gridDim.x) {
         const int64_t *F = fix + 13 * (int64_t)e;
         const int64_t Q = F[0];
@@ -127,7 +148,7 @@ __global__ void k_cf_fixup(double *__restrict__ U, const int64_t *__restrict__ f
             const int64_t co = F[1 + f], fo = F[7 + f];
             if (co >= 0) {
                 const int d = f >> 1, hi = f & 1;
-                for (int i = threadIdx.x; i < 64 * NV; i += blockDim.x) {
+                for (int i = threadIdx.x; i < 64 * nreg; i += blockDim.x) {
                     const int v = i / 64, t2 = (i >> 3) & 7, t1 = i & 7;
                     const double *B = freg + fo + (int64_t)v * 256;
                     const double fsum = 0.25 * (((B[(2 * t2) * 16 + 2 * t1] + B[(2 * t2) * 16 + 2 * t1 + 1]) +
@@ -139,7 +160,7 @@ __global__ void k_cf_fixup(double *__restrict__ U, const int64_t *__restrict__ f
                     if (d == 0) { x = a; y = t1; z = t2; }
                     else if (d == 1) { x = t1; y = a; z = t2; }
                     else { x = t1; y = t2; z = a; }
-                    double &u = U[Q * PSLOT + v * PV + z * 64 + y * 8 + x];
+                    double &u = v < NV ? U[Q * PSLOT + v * PV + z * 64 + y * 8 + x] : Sv[Q * PV + z * 64 + y * 8 + x];
                     u = hi ? u - corr : u + corr;
                 }
             }
@@ -150,11 +171,13 @@ __global__ void k_cf_fixup(double *__restrict__ U, const int64_t *__restrict__ f
 
 // Restriction (section 2.2): entry e = (coarse patch P, its child group G);
 // each coarse cell becomes the mean of its 8 children (x fastest, then y, z).
+// With Sc (dual energy) the entropy per unit volume is restricted too.
 __global__ void k_restrict(double *__restrict__ Uc, const double *__restrict__ Uf, const int32_t *__restrict__ list,
-                           int n) {
+                           int n, double *__restrict__ Sc = nullptr, const double *__restrict__ Sf = nullptr) {
+    const int nv = Sc ? NV + 1 : NV;
     for (int e = blockIdx.x; e < n; e += gridDim.x) {
         const int64_t P = list[2 * e], G = list[2 * e + 1];
-        for (int i = threadIdx.x; i < PV * NV; i += blockDim.x) {
+        for (int i = threadIdx.x; i < PV * nv; i += blockDim.x) {
             const int v = i / PV, c = i % PV;
             const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
             double s = 0.0;
@@ -163,9 +186,11 @@ __global__ void k_restrict(double *__restrict__ Uc, const double *__restrict__ U
                     for (int dx = 0; dx < 2; dx++) {
                         const int fx = 2 * x + dx, fy = 2 * y + dy, fz = 2 * z + dz;
                         const int64_t slot = 8 * G + (fx >> 3) + 2 * (fy >> 3) + 4 * (fz >> 3);
-                        s += Uf[slot * PSLOT + v * PV + (fz & 7) * 64 + (fy & 7) * 8 + (fx & 7)];
+                        const int64_t o = (fz & 7) * 64 + (fy & 7) * 8 + (fx & 7);
+                        s += v < NV ? Uf[slot * PSLOT + v * PV + o] : Sf[slot * PV + o];
                     }
-            Uc[P * PSLOT + v * PV + c] = s * 0.125;
+            if (v < NV) Uc[P * PSLOT + v * PV + c] = s * 0.125;
+            else Sc[P * PV + c] = s * 0.125;
         }
     }
 }
@@ -263,13 +288,13 @@ __global__ void k_patch_sums(const double *__restrict__ U, int n_patches, double
     }
 }
 
-// dst[s] = src[map[s]] for every slot s with map[s] >= 0.
+// dst[s] = src[map[s]] for every slot s with map[s] >= 0 (width doubles per slot).
 __global__ void k_copy_slots(double *__restrict__ dst, const double *__restrict__ src,
-                             const int32_t *__restrict__ map, int n) {
+                             const int32_t *__restrict__ map, int n, int width) {
     for (int s = blockIdx.x; s < n; s += gridDim.x) {
         const int m = map[s];
         if (m < 0) continue;
-        for (int i = threadIdx.x; i < PSLOT; i += blockDim.x) dst[(int64_t)s * PSLOT + i] = src[(int64_t)m * PSLOT + i];
+        for (int i = threadIdx.x; i < width; i += blockDim.x) dst[(int64_t)s * width + i] = src[(int64_t)m * width + i];
     }
 }
 
@@ -296,8 +321,10 @@ amr_status fill_ghost_impl(amr_hydro_ctx *c, int level, double t) {
     const double w = coarse_weight(C, t);
     const int blocks = (L.n_ghost + 2 * INTERP_WARPS - 1) / (2 * INTERP_WARPS);
     const int grid = blocks < 8 * c->n_sm ? blocks : 8 * c->n_sm;
+    const bool de = c->prm.dual_energy && L.ghost_S.p;
     k_interp_patches<<<grid, 256, 0, c->stream>>>(L.ghost.p, nullptr, L.ghost_info.p, L.n_ghost, C.U[1 - C.cur],
-                                                   C.U[C.cur], w, C.d_sib);
+                                                   C.U[C.cur], w, C.d_sib, de ? C.S[1 - C.cur] : nullptr,
+                                                   de ? C.S[C.cur] : nullptr, de ? L.ghost_S.p : nullptr);
     if ((st = cuda_fail(cudaGetLastError(), "k_interp_patches"))) return st;
     L.ghost_valid = true;
     L.ghost_t = t;
@@ -307,20 +334,21 @@ amr_status fill_ghost_impl(amr_hydro_ctx *c, int level, double t) {
 }
 
 amr_status interp_new_patches(amr_hydro_ctx *c, int coarse, double *out, const int32_t *out_slot,
-                              const int32_t *info, int n_jobs) {
+                              const int32_t *info, int n_jobs, double *out_S) {
     if (!n_jobs) return AMR_OK;
     Level &C = c->lv[coarse];
     const int blocks = (n_jobs + 2 * INTERP_WARPS - 1) / (2 * INTERP_WARPS);
     const int grid = blocks < 8 * c->n_sm ? blocks : 8 * c->n_sm;
+    const double *cs = out_S ? C.S[C.cur] : nullptr;
     k_interp_patches<<<grid, 256, 0, c->stream>>>(out, out_slot, info, n_jobs, C.U[C.cur], C.U[C.cur], 1.0,
-                                                   C.d_sib);
+                                                   C.d_sib, cs, cs, out_S);
     return cuda_fail(cudaGetLastError(), "k_interp_patches (new patches)");
 }
 
-amr_status copy_slots(amr_hydro_ctx *c, double *dst, const double *src, const int32_t *map, int n) {
+amr_status copy_slots(amr_hydro_ctx *c, double *dst, const double *src, const int32_t *map, int n, int width) {
     if (!n) return AMR_OK;
     const int grid = n < 8 * c->n_sm ? n : 8 * c->n_sm;
-    k_copy_slots<<<grid, 256, 0, c->stream>>>(dst, src, map, n);
+    k_copy_slots<<<grid, 256, 0, c->stream>>>(dst, src, map, n, width);
     return cuda_fail(cudaGetLastError(), "k_copy_slots");
 }
 
@@ -358,12 +386,15 @@ amr_status amr_hydro_flux_fixup(amr_hydro_ctx *c, int l) {
     amr_status st;
     if (C.n_fix) {
         const int grid = C.n_fix < 4 * c->n_sm ? C.n_fix : 4 * c->n_sm;
-        k_cf_fixup<<<grid, 128, 0, c->stream>>>(C.U[C.cur], C.fix_list.p, C.n_fix, C.creg.p, F.freg.p, level_dh(c, l));
+        k_cf_fixup<<<grid, 128, 0, c->stream>>>(C.U[C.cur], C.fix_list.p, C.n_fix, C.creg.p, F.freg.p, level_dh(c, l),
+                                                 c->prm.dual_energy ? C.S[C.cur] : nullptr, reg_vars(c));
         if ((st = cuda_fail(cudaGetLastError(), "k_cf_fixup"))) return st;
     }
     if (C.n_restrict) {
         const int grid = C.n_restrict < 8 * c->n_sm ? C.n_restrict : 8 * c->n_sm;
-        k_restrict<<<grid, 256, 0, c->stream>>>(C.U[C.cur], F.U[F.cur], C.restrict_list.p, C.n_restrict);
+        k_restrict<<<grid, 256, 0, c->stream>>>(C.U[C.cur], F.U[F.cur], C.restrict_list.p, C.n_restrict,
+                                                 c->prm.dual_energy ? C.S[C.cur] : nullptr,
+                                                 c->prm.dual_energy ? F.S[F.cur] : nullptr);
         if ((st = cuda_fail(cudaGetLastError(), "k_restrict"))) return st;
     }
     C.speed_valid = false;

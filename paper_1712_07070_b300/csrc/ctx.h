@@ -40,6 +40,7 @@ struct GhostInfo {
                       // hi_x<<12 | hi_y<<16 | hi_z<<20), even bounds in 0..8
 };
 constexpr int GHOST_INFO = 8;  // int32 per ghost-patch job on the device
+constexpr int PSLOT_DOUBLES = 5 * 512;  // doubles of one patch slot of the conserved variables
 
 struct Level {
     int n_patches = 0, n_groups = 0;
@@ -61,6 +62,7 @@ struct Level {
     // -2 - id, none -1)
     DevBuf<double> ghost_ustar;
     DevBuf<int32_t> ghost_nbr;
+    DevBuf<double> ghost_S;  // dual energy: the entropy of the ghost patches [n_ghost][512]
     int n_ghost = 0;
     // coarse-fine flux registers (section 2.2 fix-up)
     DevBuf<int64_t> fine_off;    // [n_groups*6]: this level's group faces on coarse-fine interfaces
@@ -105,6 +107,7 @@ struct Level {
         ghost_info.release();
         ghost_ustar.release();
         ghost_nbr.release();
+        ghost_S.release();
         fine_off.release();
         freg.release();
         coarse_off.release();
@@ -245,8 +248,9 @@ amr_status launch_max_speed(int prec, const double *U, int64_t n_slots, double g
 // AMR (amr_ops.cu, regrid.cpp)
 amr_status fill_ghost_impl(amr_hydro_ctx *c, int level, double t);
 amr_status interp_new_patches(amr_hydro_ctx *c, int coarse, double *out, const int32_t *out_slot,
-                              const int32_t *info, int n_jobs);
-amr_status copy_slots(amr_hydro_ctx *c, double *dst, const double *src, const int32_t *map, int n);
+                              const int32_t *info, int n_jobs, double *out_S = nullptr);
+amr_status copy_slots(amr_hydro_ctx *c, double *dst, const double *src, const int32_t *map, int n,
+                      int width = PSLOT_DOUBLES);
 amr_status patch_flags_dev(amr_hydro_ctx *c, int level, uint8_t *pflag);
 amr_status plan_level(amr_hydro_ctx *c, int level);
 amr_status rebuild_cf(amr_hydro_ctx *c, int fine_level);
@@ -302,4 +306,13 @@ amr_status once_per_device(DeviceOnce &o, F &&fn) {
     o.done[dev] = true;
     return AMR_OK;
 }
+}  // namespace amrh
+
+namespace amrh {
+// Variables per coarse-fine flux register: the five conserved ones, and the
+// dual-energy entropy's flux as a sixth.  A fine register block holds
+// reg_vars x 16 x 16 doubles, a coarse one reg_vars x 8 x 8.
+inline int reg_vars(const amr_hydro_ctx *c) { return c->prm.dual_energy ? 6 : 5; }
+inline int64_t fine_block(const amr_hydro_ctx *c) { return 256 * (int64_t)reg_vars(c); }
+inline int64_t coarse_block(const amr_hydro_ctx *c) { return 64 * (int64_t)reg_vars(c); }
 }  // namespace amrh

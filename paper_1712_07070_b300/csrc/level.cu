@@ -115,7 +115,8 @@ amr_status amr_hydro_set_level(amr_hydro_ctx *c, int level, int n_patches, doubl
 amr_status amr_hydro_set_entropy(amr_hydro_ctx *c, int level, double *S_a, double *S_b) {
     if (!c || level < 0 || level > c->prm.lmax || !c->prm.dual_energy) return AMR_E_INVAL;
     Level &L = c->lv[level];
-    if (!L.n_patches || !S_a || !S_b || S_a == S_b) return AMR_E_INVAL;
+    // a level with patches, or a refined level's capacity arrays (bind_level)
+    if ((!L.n_patches && !L.bound) || !S_a || !S_b || S_a == S_b) return AMR_E_INVAL;
     L.S[L.cur] = S_a;
     L.S[1 - L.cur] = S_b;
     return AMR_OK;
@@ -142,7 +143,7 @@ static amr_status launch_level_step(amr_hydro_ctx *c, int level, StepParams &P, 
     if (level < c->prm.lmax) {  // a coarse step restarts the fine level's flux sums
         Level &F = c->lv[level + 1];
         if (F.n_patches && F.n_freg &&
-            (st = cuda_fail(cudaMemsetAsync(F.freg.p, 0, sizeof(double) * 1280 * (size_t)F.n_freg, c->stream),
+            (st = cuda_fail(cudaMemsetAsync(F.freg.p, 0, sizeof(double) * fine_block(c) * (size_t)F.n_freg, c->stream),
                             "memset fine registers")))
             return st;
     }
@@ -233,6 +234,7 @@ amr_status advance_once(amr_hydro_ctx *c, int level, double dt, int64_t *n_unphy
         if (!L.S[0] || !L.S[1]) return AMR_E_INVAL;  // amr_hydro_set_entropy first
         P.S_old = L.S[L.cur];
         P.S_new = L.S[1 - L.cur];
+        P.ghost_S = L.ghost_S.p;
         P.de_xi = c->prm.dual_xi;
     }
     if (c->prm.fallback) {
@@ -332,7 +334,7 @@ amr_status amr_hydro_advance_level(amr_hydro_ctx *c, int level, double dt, int64
     const double t = L.t, t_prev = L.t_prev;
     double rec[3];
     if ((st = cuda_fail(cudaMemcpy(rec, c->dtbuf.p + 3 * level, 24, cudaMemcpyDeviceToHost), "d2h time"))) return st;
-    const size_t nfr = (size_t)1280 * L.n_freg;
+    const size_t nfr = (size_t)fine_block(c) * L.n_freg;
     if (level > 0 && nfr) {
         if ((st = L.freg_save.reserve(nfr))) return st;
         if ((st = cuda_fail(cudaMemcpyAsync(L.freg_save.p, L.freg.p, 8 * nfr, cudaMemcpyDeviceToDevice, c->stream),

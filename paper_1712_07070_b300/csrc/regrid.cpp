@@ -109,7 +109,7 @@ amr_status rebuild_cf(amr_hydro_ctx *c, int l) {
         for (int f = 0; f < 6; f++) {
             const int Q = C.sib[(size_t)P * 26 + face_sib(f)];
             if (Q < 0) return AMR_E_NESTING;
-            if (C.child[Q] < 0) foff[(size_t)g * 6 + f] = (int64_t)(nf++) * 1280;
+            if (C.child[Q] < 0) foff[(size_t)g * 6 + f] = (int64_t)(nf++) * fine_block(c);
         }
     }
     // coarse side
@@ -129,7 +129,7 @@ amr_status rebuild_cf(amr_hydro_ctx *c, int l) {
             const int G = C.child[P];
             const int64_t fo = foff[(size_t)G * 6 + (f ^ 1)];
             if (fo < 0) return AMR_E_NESTING;
-            coff[(size_t)Q * 6 + f] = (int64_t)(nc++) * 320;
+            coff[(size_t)Q * 6 + f] = (int64_t)(nc++) * coarse_block(c);
             e[1 + f] = coff[(size_t)Q * 6 + f];
             e[7 + f] = fo;
             any = true;
@@ -141,9 +141,10 @@ amr_status rebuild_cf(amr_hydro_ctx *c, int l) {
     if ((st = upload(C.coarse_off, coff, c->stream))) return st;
     if ((st = upload(C.fix_list, fix, c->stream))) return st;
     if ((st = upload(C.restrict_list, rlist, c->stream))) return st;
-    if (nf && (st = F.freg.reserve((size_t)nf * 1280))) return st;
-    if (nc && (st = C.creg.reserve((size_t)nc * 320))) return st;
-    if (nf && (st = cuda_fail(cudaMemsetAsync(F.freg.p, 0, sizeof(double) * 1280 * (size_t)nf, c->stream), "memset")))
+    if (nf && (st = F.freg.reserve((size_t)nf * fine_block(c)))) return st;
+    if (nc && (st = C.creg.reserve((size_t)nc * coarse_block(c)))) return st;
+    if (nf && (st = cuda_fail(cudaMemsetAsync(F.freg.p, 0, sizeof(double) * fine_block(c) * (size_t)nf, c->stream),
+                              "memset")))
         return st;
     F.n_freg = nf;
     C.n_creg = nc;

@@ -371,9 +371,9 @@ __global__ void k_cf_fine_flags(int n_groups_f, const int32_t *__restrict__ fpar
 }
 
 __global__ void k_cf_fine_off(int n, const int32_t *__restrict__ flag, const int32_t *__restrict__ rank,
-                              int64_t *__restrict__ fine_off) {
+                              int64_t block, int64_t *__restrict__ fine_off) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        fine_off[i] = flag[i] ? (int64_t)rank[i] * 1280 : -1;
+        fine_off[i] = flag[i] ? (int64_t)rank[i] * block : -1;
 }
 
 // coarse side: per coarse patch Q, register flags of its faces (leaf Q next to
@@ -401,7 +401,7 @@ __global__ void k_cf_coarse_write(int n_c, const int32_t *__restrict__ csib, con
                                   const int32_t *__restrict__ fflag, const int32_t *__restrict__ frank,
                                   const int32_t *__restrict__ fix, const int32_t *__restrict__ fixrank,
                                   const int32_t *__restrict__ rst, const int32_t *__restrict__ rstrank,
-                                  const int64_t *__restrict__ fine_off, int64_t *__restrict__ coarse_off,
+                                  const int64_t *__restrict__ fine_off, int64_t cblock, int64_t *__restrict__ coarse_off,
                                   int64_t *__restrict__ fix_list, int32_t *__restrict__ restrict_list, int32_t *err) {
     for (int Q = blockIdx.x * blockDim.x + threadIdx.x; Q < n_c; Q += gridDim.x * blockDim.x) {
         if (rst[Q]) {
@@ -414,7 +414,7 @@ __global__ void k_cf_coarse_write(int n_c, const int32_t *__restrict__ csib, con
         for (int f = 0; f < 6; f++) {
             int64_t co = -1, fo = -1;
             if (fflag[Q * 6 + f]) {
-                co = (int64_t)frank[Q * 6 + f] * 320;
+                co = (int64_t)frank[Q * 6 + f] * cblock;
                 const int P = csib[(int64_t)Q * 26 + face_sib_d(f)];
                 fo = fine_off[(int64_t)cchild[P] * 6 + (f ^ 1)];
                 if (fo < 0) atomicOr(err, 1);
@@ -533,7 +533,8 @@ static amr_status cf_dev(amr_hydro_ctx *c, int F_, int32_t *cnt, int32_t *err) {
         k_cf_fine_flags<<<grid_for(nfg, 256, 8 * c->n_sm), 256, 0, c->stream>>>(F.n_groups, F.d_parent, C.d_sib,
                                                                                C.d_child, nc, S.cf_a.p, err);
         if ((st = scan_i32(c, S.cf_a.p, S.cf_b.p, nfg, cnt + 0, false))) return st;
-        k_cf_fine_off<<<grid_for(nfg, 256, 8 * c->n_sm), 256, 0, c->stream>>>(nfg, S.cf_a.p, S.cf_b.p, F.fine_off.p);
+        k_cf_fine_off<<<grid_for(nfg, 256, 8 * c->n_sm), 256, 0, c->stream>>>(nfg, S.cf_a.p, S.cf_b.p, fine_block(c),
+                                                                             F.fine_off.p);
     } else if ((st = cuda_fail(cudaMemsetAsync(cnt + 0, 0, 4, c->stream), "memset"))) {
         return st;
     }
@@ -546,7 +547,7 @@ static amr_status cf_dev(amr_hydro_ctx *c, int F_, int32_t *cnt, int32_t *err) {
             return st;
         k_cf_coarse_write<<<grid_for(nc, 256, 8 * c->n_sm), 256, 0, c->stream>>>(
             nc, C.d_sib, C.d_child, S.cf_c.p, S.cf_d.p, S.cf_e.p, S.cf_f.p, S.cf_g.p, S.cf_h.p, F.fine_off.p,
-            C.coarse_off.p, C.fix_list.p, C.restrict_list.p, err);
+            coarse_block(c), C.coarse_off.p, C.fix_list.p, C.restrict_list.p, err);
     }
     return cuda_fail(cudaGetLastError(), "cf maps");
 }
@@ -556,9 +557,10 @@ static amr_status cf_finish(amr_hydro_ctx *c, int F_, const int32_t *cnt) {
     Level &C = c->lv[F_ - 1], &F = c->lv[F_];
     amr_status st;
     const int nf = cnt[0], nc = cnt[1];
-    if (nf && (st = F.freg.reserve((size_t)nf * 1280))) return st;
-    if (nc && (st = C.creg.reserve((size_t)nc * 320))) return st;
-    if (nf && (st = cuda_fail(cudaMemsetAsync(F.freg.p, 0, sizeof(double) * 1280 * (size_t)nf, c->stream), "memset")))
+    if (nf && (st = F.freg.reserve((size_t)nf * fine_block(c)))) return st;
+    if (nc && (st = C.creg.reserve((size_t)nc * coarse_block(c)))) return st;
+    if (nf && (st = cuda_fail(cudaMemsetAsync(F.freg.p, 0, sizeof(double) * fine_block(c) * (size_t)nf, c->stream),
+                              "memset")))
         return st;
     F.n_freg = nf;
     C.n_creg = nc;
@@ -629,11 +631,15 @@ amr_status regrid_dev(amr_hydro_ctx *c, int l) {
             S.new_of.p);
         if ((st = cuda_fail(cudaGetLastError(), "k_rg_new_slots"))) return st;
     }
-    // cell data of the new level into its other buffer
+    // cell data of the new level into its other buffer (with dual energy also
+    // the entropy, which pairs with the same buffer index)
     const int dst = n_old ? 1 - F.cur : 0;
     double *Ud = F.U[dst];
+    const bool de = c->prm.dual_energy != 0;
+    if (de && (!F.S[0] || !F.S[1] || !L.S[0])) return AMR_E_INVAL;  // amr_hydro_set_entropy first
     if (n_old && nn && (st = copy_slots(c, Ud, F.U[F.cur], S.old_of.p, nn))) return st;
-    if ((st = interp_new_patches(c, l, Ud, nullptr, S.info.p, nn))) return st;
+    if (de && n_old && nn && (st = copy_slots(c, F.S[dst], F.S[F.cur], S.old_of.p, nn, PV))) return st;
+    if ((st = interp_new_patches(c, l, Ud, nullptr, S.info.p, nn, de ? F.S[dst] : nullptr))) return st;
     // commit: level l's child groups, grandchildren's parents, the new tables
     const int n_g2 = G2 ? G2->n_patches : 0;
     k_rg_commit<<<grid_for(n > n_g2 ? n : n_g2, 256, 8 * c->n_sm), 256, 0, c->stream>>>(
@@ -693,6 +699,7 @@ amr_status regrid_dev(amr_hydro_ctx *c, int l) {
         if (F.n_ghost && (st = F.ghost.reserve((size_t)F.n_ghost * PSLOT))) return st;
         if (F.n_ghost && c->prm.scheme == AMR_SCHEME_VL && (st = F.ghost_ustar.reserve((size_t)F.n_ghost * PSLOT)))
             return st;
+        if (F.n_ghost && c->prm.dual_energy && (st = F.ghost_S.reserve((size_t)F.n_ghost * PV))) return st;
         if ((st = cf_finish(c, l + 1, S.hcnt + 5))) return st;
         F.ghost_valid = false;
         if (G2) {
@@ -701,6 +708,7 @@ amr_status regrid_dev(amr_hydro_ctx *c, int l) {
             if (G2->n_ghost && c->prm.scheme == AMR_SCHEME_VL &&
                 (st = G2->ghost_ustar.reserve((size_t)G2->n_ghost * PSLOT)))
                 return st;
+            if (G2->n_ghost && c->prm.dual_energy && (st = G2->ghost_S.reserve((size_t)G2->n_ghost * PV))) return st;
             if ((st = cf_finish(c, l + 2, S.hcnt + 10))) return st;
             G2->ghost_valid = false;
         }

@@ -81,12 +81,13 @@ struct StepCfg {
 
 // Coarse-fine flux registers (section 2.2 fix-up).  Faces f = 0..5 are
 // -x, +x, -y, +y, -z, +z.  Fine side: fine_off[g*6+f] >= 0 is the offset (in
-// doubles) of a [5][16][16] block of this level's fine register buffer for
+// doubles) of a [NREG][16][16] block of this level's fine register buffer for
 // group face f lying on a coarse-fine interface; every step adds dt * F of
 // each fine boundary face into it.  Coarse side: coarse_off[slot*6+f] >= 0 is
-// the offset of a [5][8][8] block of this level's coarse register buffer for
+// the offset of a [NREG][8][8] block of this level's coarse register buffer for
 // a leaf patch face next to a refined patch; every step stores dt * F there.
-// Block index (v, t2, t1) with t1 < t2 the two transverse dimensions.
+// Block index (v, t2, t1) with t1 < t2 the two transverse dimensions.  NREG
+// is 5, or 6 with dual energy (the entropy's flux in the sixth).
 struct CFRegs {
     const int64_t *fine_off;    // [n_groups*6] or null
     double *fine_buf;
@@ -123,6 +124,7 @@ struct StepParams {
     // and after the step, and the threshold on E_the / E_kin
     const double *__restrict__ S_old;
     double *__restrict__ S_new;
+    const double *__restrict__ ghost_S;  // the entropy of the coarse-fine ghost patches [ghost][8^3]
     double de_xi;
     // gravity predictor (ST_MH_GRAV): the acceleration at t^n, [slot][3][8^3]
     const double *__restrict__ acc_n;
@@ -176,8 +178,13 @@ struct StepSmemDE : StepSmem<real, 2> {
 template <typename real, typename SM>
 __device__ __forceinline__ void cf_register(const SM &S, const StepParams &P, double dt,
                                             const real F[NV], int D, int t1, int t2, int sa, int pa, int sb,
-                                            int pb, long long fo) {
+                                            int pb, long long fo, real fs = real(0)) {
     double Fd[NV];
+    double fsd = 0.0;  // the dual-energy entropy's flux (SM::DE)
+    if constexpr (SM::DE) {
+        if constexpr (sizeof(real) == sizeof(double)) fsd = fs;
+        else fsd = f2d_bits(fs);
+    }
     const long long ca = pa >= 0 ? S.cco[sa][pa * 6 + 2 * D + 1] : -1;  // high face of the low cell's patch
     const long long cb = pb >= 0 ? S.cco[sb][pb * 6 + 2 * D] : -1;      // low face of the high cell's patch
     if (fo < 0 && ca < 0 && cb < 0) return;
@@ -190,17 +197,20 @@ __device__ __forceinline__ void cf_register(const SM &S, const StepParams &P, do
         double *b = P.cf.fine_buf + fo;
 #pragma unroll
         for (int v = 0; v < NV; v++) b[(v * 16 + t2) * 16 + t1] += dt * Fd[v];
+        if constexpr (SM::DE) b[(NV * 16 + t2) * 16 + t1] += dt * fsd;
     }
     const int c1 = t1 & 7, c2 = t2 & 7;
     if (ca >= 0) {
         double *b = P.cf.coarse_buf + ca;
 #pragma unroll
         for (int v = 0; v < NV; v++) b[(v * 8 + c2) * 8 + c1] = dt * Fd[v];
+        if constexpr (SM::DE) b[(NV * 8 + c2) * 8 + c1] = dt * fsd;
     }
     if (cb >= 0) {
         double *b = P.cf.coarse_buf + cb;
 #pragma unroll
         for (int v = 0; v < NV; v++) b[(v * 8 + c2) * 8 + c1] = dt * Fd[v];
+        if constexpr (SM::DE) b[(NV * 8 + c2) * 8 + c1] = dt * fsd;
     }
 }
 
@@ -276,10 +286,12 @@ __device__ __forceinline__ void load_plane(SM &S, const StepParams &P, int ts, i
         }
 #pragma unroll
         for (int v = 0; v < NV; v++) S.W[slot][v][ty + G::OY][tx + G::OX] = w[v];
-        if constexpr (SM::DE) {  // q = s / rho
+        if constexpr (SM::DE) {  // q = s / rho (coarse-fine ghost patches: their interpolated s)
             const int sl = S.nbr[ts][qx + 4 * qy + 16 * qz];
+            const double *ss = sl >= 0 ? P.S_old + (int64_t)sl * PV
+                                       : (sl <= -2 ? P.ghost_S + (int64_t)(-2 - sl) * PV : nullptr);
             S.Q[slot][ty + G::OY][tx + G::OX] =
-                sl >= 0 ? to_real<real>(__ldg(P.S_old + (int64_t)sl * PV + lz * 64 + ly * 8 + lx)) / w[0] : real(1);
+                ss ? to_real<real>(__ldg(ss + lz * 64 + ly * 8 + lx)) / w[0] : real(1);
         }
     }
 }
@@ -310,7 +322,8 @@ __device__ __forceinline__ void issue_plane(SM &S, const StepParams &P, int ts, 
             const int off = lz * 64 + ly * 8 + lx;
 #pragma unroll
             for (int v = 0; v < NV; v++) cp_async16(&S.raw[v][2 * j], src + v * PV + off);
-            if constexpr (SM::DE) cp_async16(&S.raws[2 * j], P.S_old + (int64_t)sl * PV + off);
+            if constexpr (SM::DE)
+                cp_async16(&S.raws[2 * j], (sl >= 0 ? P.S_old + (int64_t)sl * PV : P.ghost_S + (int64_t)(-2 - sl) * PV) + off);
         }
     }
     cp_async_commit();
@@ -534,11 +547,15 @@ __device__ __forceinline__ void x_face(SM &S, const StepParams &P, double dt, in
     face_flux<0>(uL, uR, F, g);
 #pragma unroll
     for (int v = 0; v < NV; v++) S.FX[v][row][col] = F[v];
-    if constexpr (SM::DE) S.FQX[row][col] = scalar_flux(F[0], S.QX[1][row][col], uL[0], S.QX[0][row][col + 1], uR[0]);
+    real fs = real(0);
+    if constexpr (SM::DE) {
+        fs = scalar_flux(F[0], S.QX[1][row][col], uL[0], S.QX[0][row][col + 1], uR[0]);
+        S.FQX[row][col] = fs;
+    }
     if (cf && (col & 7) == 0) {  // a patch face: x = 0 (group boundary) or x = 8
         const int pr = (row >> 3) * 2 + (zl >> 3) * 4;
         cf_register(S, P, dt, F, 0, row, zl, ts, col == 0 ? -1 : pr, ts, pr + (col >> 3),
-                    col == 0 ? S.cfo[ts][0] : -1LL);
+                    col == 0 ? S.cfo[ts][0] : -1LL, fs);
     }
 }
 
@@ -551,10 +568,15 @@ __device__ __forceinline__ void y_face(SM &S, const StepParams &P, double dt, in
     face_flux<1>(uL, uR, F, g);
 #pragma unroll
     for (int v = 0; v < NV; v++) S.FY[v][r][col] = F[v];
-    if constexpr (SM::DE) S.FQY[r][col] = scalar_flux(F[0], S.QY[1][r][col], uL[0], S.QY[0][r + 1][col], uR[0]);
+    real fs = real(0);
+    if constexpr (SM::DE) {
+        fs = scalar_flux(F[0], S.QY[1][r][col], uL[0], S.QY[0][r + 1][col], uR[0]);
+        S.FQY[r][col] = fs;
+    }
     if (cf && (r & 7) == 0) {  // a patch face: y = 0 (group boundary) or y = 8
         const int pr = (col >> 3) + (zl >> 3) * 4;
-        cf_register(S, P, dt, F, 1, col, zl, ts, r == 0 ? -1 : pr, ts, pr + 2 * (r >> 3), r == 0 ? S.cfo[ts][2] : -1LL);
+        cf_register(S, P, dt, F, 1, col, zl, ts, r == 0 ? -1 : pr, ts, pr + 2 * (r >> 3),
+                    r == 0 ? S.cfo[ts][2] : -1LL, fs);
     }
 }
 
@@ -574,13 +596,19 @@ __device__ __forceinline__ void high_faces(SM &S, const StepParams &P, double dt
         if (D == 0) S.FX[v][k][GE] = F[v];
         else S.FY[v][GE][k] = F[v];
     }
+    real fs = real(0);
     if constexpr (SM::DE) {
-        if (D == 0) S.FQX[k][GE] = scalar_flux(F[0], S.QX[1][k][GE], uL[0], S.QX[0][k][GE + 1], uR[0]);
-        else S.FQY[GE][k] = scalar_flux(F[0], S.QY[1][GE][k], uL[0], S.QY[0][GE + 1][k], uR[0]);
+        if (D == 0) {
+            fs = scalar_flux(F[0], S.QX[1][k][GE], uL[0], S.QX[0][k][GE + 1], uR[0]);
+            S.FQX[k][GE] = fs;
+        } else {
+            fs = scalar_flux(F[0], S.QY[1][GE][k], uL[0], S.QY[0][GE + 1][k], uR[0]);
+            S.FQY[GE][k] = fs;
+        }
     }
     if (cf) {
         const int pa = D == 0 ? 1 + (k >> 3) * 2 + (zl >> 3) * 4 : (k >> 3) + 2 + (zl >> 3) * 4;
-        cf_register(S, P, dt, F, D, k, zl, ts, pa, ts, -1, S.cfo[ts][2 * D + 1]);
+        cf_register(S, P, dt, F, D, k, zl, ts, pa, ts, -1, S.cfo[ts][2 * D + 1], fs);
     }
 }
 
@@ -590,11 +618,19 @@ __device__ __forceinline__ void high_faces(SM &S, const StepParams &P, double dt
 // same group except at a group boundary, where ka = kb - 1: two same-level
 // groups, so no fine register, but each side's coarse registers);
 // cfm: bit s set when the group in table slot s touches a register.
+// With dual energy (SM::DE) also the scalar's flux fzs from the entropy on
+// the face's two sides (zps_prev below, zms above).
 template <typename real, typename SM>
 __device__ __forceinline__ void z_face(const SM &S, const StepParams &P, double dt, const real zp_prev[NV],
                                        const real zm[NV], int cx, int cy, int z, int len, unsigned cfm, real fz[NV],
-                                       const Gas<real> &g) {
+                                       const Gas<real> &g, real zps_prev = real(0), real zms = real(0),
+                                       real *fzs = nullptr) {
     face_flux<2>(zp_prev, zm, fz, g);
+    real fs = real(0);
+    if constexpr (SM::DE) {
+        fs = scalar_flux(fz[0], zps_prev, zp_prev[0], zms, zm[0]);
+        *fzs = fs;
+    }
     if ((z & 7) == 0) {
         const bool bot = z == 0, top = z == GE * len;
         const int ka = bot ? 0 : (z - 1) >> 4, kb = top ? len - 1 : z >> 4;
@@ -602,7 +638,7 @@ __device__ __forceinline__ void z_face(const SM &S, const StepParams &P, double 
             const int pl = (cx >> 3) + 2 * (cy >> 3);
             const long long fo = bot ? S.cfo[0][4] : (top ? S.cfo[(len - 1) & 1][5] : -1LL);
             cf_register(S, P, dt, fz, 2, cx, cy, ka & 1, bot ? -1 : pl + 4 * (((z - 1) & 15) >> 3), kb & 1,
-                        top ? -1 : pl + 4 * ((z & 15) >> 3), fo);
+                        top ? -1 : pl + 4 * ((z & 15) >> 3), fo, fs);
         }
     }
 }
@@ -745,8 +781,7 @@ __device__ __forceinline__ void step_run(SM &S, const StepParams &P, const int32
             // Sub-partitions 2 and 3 (warp & 2) have no ghost-ring cells in this
             // stage: they take their z face here rather than in stage C.
             if ((warp & 2) && z >= 0) {
-                z_face(S, P, dt, zp_prev, zm, cx, cy, z, len, cfm, fz, g);
-                if constexpr (SM::DE) fzs = scalar_flux(fz[0], zps_prev, zp_prev[0], zms, zm[0]);
+                z_face(S, P, dt, zp_prev, zm, cx, cy, z, len, cfm, fz, g, zps_prev, zms, &fzs);
             }
             if (z >= 0 && z < Z) {
 #pragma unroll
@@ -808,8 +843,7 @@ __device__ __forceinline__ void step_run(SM &S, const StepParams &P, const int32
         // every sub-partition's FP64 share carries 5 or 6 face evaluations
         // here after 3 or 2 Hancock cells (+2 z faces) in stage B
         if (!(warp & 2) && z >= 0) {
-            z_face(S, P, dt, zp_prev, zm, cx, cy, z, len, cfm, fz, g);
-            if constexpr (SM::DE) fzs = scalar_flux(fz[0], zps_prev, zp_prev[0], zms, zm[0]);
+            z_face(S, P, dt, zp_prev, zm, cx, cy, z, len, cfm, fz, g, zps_prev, zms, &fzs);
         }
         if (z >= 0 && z < Z) {
             const int ts = kz & 1;

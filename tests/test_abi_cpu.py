@@ -63,10 +63,10 @@ def test_init_rejects_vl_with_ppm():
 
 
 def test_init_rejects_dual_energy_outside_its_scope():
-    # built for single-level MUSCL-Hancock + PLM without the cell remedies
+    # built for MUSCL-Hancock + PLM without the cell remedies
     ctx = ctypes.c_void_p()
     for kw in (dict(scheme=A.AMR_SCHEME_CTU), dict(scheme=A.AMR_SCHEME_VL), dict(recon=A.AMR_RECON_PPM),
-               dict(lmax=1), dict(fallback=1)):
+               dict(fallback=1)):
         p = A.make_params(root_n=(32, 32, 32), dual_energy=1, **kw)
         assert A.lib().amr_hydro_init(ctypes.byref(p), None, ctypes.byref(ctx)) == A.AMR_E_INVAL, kw
         assert not ctx.value

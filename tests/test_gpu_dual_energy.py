@@ -112,3 +112,49 @@ def test_box_batch_dual_energy_requires_entropy_fields():
     with pytest.raises(A.AmrHydroError):
         B.advance(1)
     B.close()
+
+
+# ---- dual energy on refined hierarchies ----------------------------------------------------
+
+def amr_compare_entropy(H, O, tol):
+    """Every level's entropy against the oracle hierarchy's (relative L1)."""
+    for l in range(H.lmax + 1):
+        cg = H.corners(l)
+        if not len(cg):
+            continue
+        S = H.entropy(l).cpu().numpy()
+        num = den = 0.0
+        for s, (x, y, z) in enumerate(cg.tolist()):
+            r = O.lv[l].S[z:z + 8, y:y + 8, x:x + 8]
+            num += np.abs(S[s] - r).sum()
+            den += np.abs(r).sum()
+        assert num <= tol * den, (l, num / den)
+
+
+@pytest.mark.parametrize("prec,tol", [(A.AMR_FP64, 1e-12), (A.AMR_FP32_ACC64, 1e-5)])
+@pytest.mark.parametrize("xi,strong", [(1e-2, False), (1e300, True)])
+def test_amr_dual_energy_matches_oracle(prec, tol, xi, strong):
+    """The three-level W-cycle with the dual-energy formalism: the entropy's
+    ghosts (interpolated with the conserved variables' positivity decision),
+    its flux registers, fix-up, restriction and new-patch data against the
+    oracle hierarchy; bit-exact patch lists, U and S of every level."""
+    from oracle.amr import OracleHierarchy
+    from paper_1712_07070_b300.amr import AmrHierarchy
+    from test_gpu_amr import compare
+    if strong:
+        U0 = ics.blobs(32, seed=3)
+        theta, nbuf = 0.05, (8, 4)
+    else:
+        U0 = ics.blobs(32, seed=5, contrast=10.0, mach=1.0)
+        theta, nbuf = 0.3, (1, 1)
+    S0 = oracle.entropy(U0, G53) * (1.0 + 0.05 * np.random.default_rng(4).random(U0.shape[1:]))
+    H = AmrHierarchy(U0, lmax=2, theta=theta, nbuf=nbuf, prec=prec, max_patches=6000,
+                     scheme={"dual_energy": 1, "dual_xi": xi}, S_root=S0)
+    O = OracleHierarchy(U0, lmax=2, gamma=G53, cfl=0.5, theta=theta, nbuf=list(nbuf), S_root=S0, dual_xi=xi)
+    assert H.n_patches(2) > 0
+    for _ in range(2):
+        H.advance_root()
+        O.advance(0)
+    compare(H, O, tol)
+    amr_compare_entropy(H, O, tol)
+    H.close()
