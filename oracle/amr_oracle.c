@@ -426,3 +426,26 @@ void or_amr_prolong_patches_s(double *Sf, const uint8_t *newmask, const int Nf[3
                     Sf[cidx(x, y, z, Nf)] = interp_scalar(Sc, Sc, 1.0, Nc, x, y, z, ok);
                 }
 }
+
+/*
+ * A cell-centred field (one component of the gravitational acceleration) on
+ * the ghost cells of level l from level l-1 (the cells or_amr_fill_ghost
+ * fills): time interpolation, then the minmod-limited linear prolongation,
+ * with no positivity decision (the field has no sign constraint).
+ */
+void or_amr_fill_ghost_field(double *Ff, const uint8_t *pmask_f, const int Nf[3], const double *Fc_old,
+                             const double *Fc_new, double w) {
+    const int Nc[3] = {Nf[0] / 2, Nf[1] / 2, Nf[2] / 2};
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < Nf[2]; z++)
+        for (int y = 0; y < Nf[1]; y++)
+            for (int x = 0; x < Nf[0]; x++) {
+                if (patch_present(pmask_f, Nf, x, y, z)) continue;
+                int near = 0;
+                for (int dz = -3; dz <= 3 && !near; dz += 3)
+                    for (int dy = -3; dy <= 3 && !near; dy += 3)
+                        for (int dx = -3; dx <= 3 && !near; dx += 3)
+                            near = patch_present(pmask_f, Nf, x + dx, y + dy, z + dz);
+                Ff[cidx(x, y, z, Nf)] = near ? interp_scalar(Fc_old, Fc_new, w, Nc, x, y, z, 1) : 0.0;
+            }
+}

@@ -933,6 +933,18 @@ int64_t or_step_gravity_predictor(const double *U, const double *g, double *Unew
     return nbad;
 }
 
+/* The same predictor, also returning the face fluxes FX_out [3][5][cells]
+ * through the high face of every cell (for the refined levels' flux
+ * registers). */
+int64_t or_step_gravity_predictor_fx(const double *U, const double *g, double *Unew, int nx, int ny, int nz,
+                                     double dh, double dt, double gamma, double *FX_out) {
+    if (or_vl) return -1;
+    or_grav_g = g;
+    int64_t nbad = or_step_periodic_fx(U, Unew, nx, ny, nz, dh, dt, gamma, FX_out);
+    or_grav_g = NULL;
+    return nbad;
+}
+
 /* One MUSCL-Hancock step with the dual-energy formalism: S, Snew the entropy
  * per unit volume [nz][ny][nx] before and after, xi the threshold on
  * E_the / E_kin.  Returns the unphysical count, or -1 for a scheme other
