@@ -457,6 +457,27 @@ amr_status amr_hydro_advance_gravity(amr_hydro_ctx *ctx, double dt, double G, co
                                      double *acc_new, int acc_order, double c_acc);
 
 /*
+ * Self-gravity inside the adaptive time-step W-cycle of amr_hydro_advance_root
+ * (section 2.3 on the section 2.1 hierarchy): after this call every level
+ * step is the coupled step -- the predictor with g^n in its half step (g^n
+ * of coarse-fine ghost cells interpolated from the coarse level), the
+ * potential of the predicted density at the step's end (root: periodic FFT;
+ * refined levels: the per-patch 18^3 SOR, iters red-black sweeps at
+ * omega, the parent's potential interpolated linearly in time), and the
+ * corrector with g^n and g^{n+1}; one Poisson solve per level step, and a
+ * level whose patches a regrid changed is solved again at its time.  The
+ * call solves every level's potential at its current time.  G >= 0,
+ * 0 < omega < 2, iters >= 0, acc_order 2 or 4.  MUSCL-Hancock + PLM on a
+ * periodic root, without dual energy, the remedies or the level retry;
+ * AMR_E_INVAL otherwise.  The library owns the potentials.
+ */
+amr_status amr_hydro_set_gravity(amr_hydro_ctx *ctx, double G, double omega, int iters, int acc_order);
+/* The newest potential [n_patches][8][8][8] and acceleration
+ * [n_patches][3][8][8][8] of `level` copied into caller-owned device arrays
+ * (either may be NULL), in the level's slot order.  Synchronises. */
+amr_status amr_hydro_level_gravity(amr_hydro_ctx *ctx, int level, double *phi_out, double *acc_out);
+
+/*
  * Discrete adjoint of one uniform periodic MUSCL-Hancock step of size dt (no
  * counterpart in the paper; the reverse of section 2.2's update with dt held
  * fixed): lam_n = (dU^{n+1}/dU^n)^T lam_np1.  U_n, lam_np1, lam_n: device FP64

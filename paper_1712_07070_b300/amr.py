@@ -82,6 +82,18 @@ class AmrHierarchy:
         cur, _, _ = A.amr_hydro_get_state(self.ctx, l)
         return self.U[l][cur][:n]
 
+    def set_gravity(self, G, omega=1.7, iters=60, acc_order=2):
+        """Self-gravity in the W-cycle from now on (solves every level's potential)."""
+        A.amr_hydro_set_gravity(self.ctx, G, omega, iters, acc_order)
+
+    def gravity(self, l):
+        """Level l's newest potential [n][8][8][8] and acceleration [n][3][8][8][8]."""
+        n = self.n_patches(l)
+        phi = torch.zeros((n, 8, 8, 8), dtype=torch.float64, device=self.device)
+        acc = torch.zeros((n, 3, 8, 8, 8), dtype=torch.float64, device=self.device)
+        A.amr_hydro_level_gravity(self.ctx, l, phi, acc)
+        return phi, acc
+
     def entropy(self, l):
         """Dual energy: level l's current entropy per unit volume, [n_patches][8][8][8]."""
         n = self.n_patches(l)

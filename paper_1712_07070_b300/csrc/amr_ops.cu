@@ -132,6 +132,58 @@ __global__ void k_interp_patches(double *__restrict__ out, const int32_t *__rest
     }
 }
 
+// A three-component cell field (the gravitational acceleration, [slot][3][8^3])
+// on the coarse-fine ghost patches: time interpolation, then the
+// minmod-limited prolongation of each component, with no positivity
+// decision.  Jobs as in k_interp_patches, half a warp each.
+__global__ void k_interp_vec3(double *__restrict__ out, const int32_t *__restrict__ info, int n_jobs,
+                              const double *Fo, const double *Fn, double w, const int32_t *__restrict__ csib) {
+    __shared__ int nbs[2 * INTERP_WARPS][27];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+    int *nb = nbs[2 * warp + half];
+    for (int j0 = 2 * (blockIdx.x * INTERP_WARPS + warp); j0 < n_jobs; j0 += 2 * gridDim.x * INTERP_WARPS) {
+        const int j = j0 + half;
+        int P = -1, qx = 0, qy = 0, qz = 0, box = 0;
+        if (j < n_jobs) {
+            const int32_t *I = info + (int64_t)GHOST_INFO * j;
+            P = I[0];
+            qx = I[1];
+            qy = I[2];
+            qz = I[3];
+            box = I[4];
+        }
+        __syncwarp();
+        if (P >= 0)
+            for (int k = hl; k < 27; k += 16) nb[k] = k == 13 ? P : csib[(int64_t)P * 26 + k - (k > 13)];
+        __syncwarp();
+        if (P < 0) continue;
+        const int lo[3] = {box & 15, (box >> 4) & 15, (box >> 8) & 15};
+        const int hi[3] = {(box >> 12) & 15, (box >> 16) & 15, (box >> 20) & 15};
+        const int n[3] = {(hi[0] - lo[0]) >> 1, (hi[1] - lo[1]) >> 1, (hi[2] - lo[2]) >> 1};
+        CoarseView C{Fo, Fn, w, nb, 3 * PV};
+        double *o = out + (int64_t)j * 3 * PV;
+        const int total = n[0] * n[1] * n[2];
+        for (int i = hl; i < total; i += 16) {
+            const int fx = lo[0] + 2 * (i % n[0]), fy = lo[1] + 2 * ((i / n[0]) % n[1]),
+                      fz = lo[2] + 2 * (i / (n[0] * n[1]));
+            const int cx = (qx * 8 + fx) >> 1, cy = (qy * 8 + fy) >> 1, cz = (qz * 8 + fz) >> 1;
+#pragma unroll
+            for (int v = 0; v < 3; v++) {
+                const double c = C.at(v, cx, cy, cz);
+                const double s0 = minmod(C.at(v, cx + 1, cy, cz) - c, c - C.at(v, cx - 1, cy, cz));
+                const double s1 = minmod(C.at(v, cx, cy + 1, cz) - c, c - C.at(v, cx, cy - 1, cz));
+                const double s2 = minmod(C.at(v, cx, cy, cz + 1) - c, c - C.at(v, cx, cy, cz - 1));
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    const double sx = (k & 1) ? 0.25 : -0.25, sy = (k & 2) ? 0.25 : -0.25, sz = (k & 4) ? 0.25 : -0.25;
+                    const int off = (fz + (k >> 2)) * 64 + (fy + ((k >> 1) & 1)) * 8 + fx + (k & 1);
+                    o[v * PV + off] = c + sx * s0 + sy * s1 + sz * s2;
+                }
+            }
+        }
+    }
+}
+
 // Coarse-fine flux fix-up (section 2.2).  Entry e: fix[13e] = coarse leaf
 // patch Q, fix[13e+1+f] = coarse register block of face f (-1: none),
 // fix[13e+7+f] = the fine register block (of the refined neighbour's child
@@ -331,6 +383,24 @@ amr_status fill_ghost_impl(amr_hydro_ctx *c, int level, double t) {
     L.ghost_cver = C.version;
     L.ghost_pver = L.plan_version;
     return AMR_OK;
+}
+
+// g^n of a refined level's coarse-fine ghost patches at time t from the coarse
+// level's accelerations at its two newest times (self-gravity in the W-cycle).
+amr_status fill_ghost_acc(amr_hydro_ctx *c, int level, double t) {
+    Level &L = c->lv[level];
+    if (!L.n_ghost) return AMR_OK;
+    if (level == 0) return AMR_E_NESTING;
+    Level &C = c->lv[level - 1];
+    amr_status st = level_time(c, level - 1);
+    if (st) return st;
+    if ((st = L.ghost_acc.reserve((size_t)L.n_ghost * 3 * PV))) return st;
+    const double w = coarse_weight(C, t);
+    const int blocks = (L.n_ghost + 2 * INTERP_WARPS - 1) / (2 * INTERP_WARPS);
+    const int grid = blocks < 8 * c->n_sm ? blocks : 8 * c->n_sm;
+    k_interp_vec3<<<grid, 256, 0, c->stream>>>(L.ghost_acc.p, L.ghost_info.p, L.n_ghost, C.gacc[1 - C.gc].p,
+                                               C.gacc[C.gc].p, w, C.d_sib);
+    return cuda_fail(cudaGetLastError(), "k_interp_vec3");
 }
 
 amr_status interp_new_patches(amr_hydro_ctx *c, int coarse, double *out, const int32_t *out_slot,

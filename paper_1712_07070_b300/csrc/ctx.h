@@ -63,6 +63,13 @@ struct Level {
     DevBuf<double> ghost_ustar;
     DevBuf<int32_t> ghost_nbr;
     DevBuf<double> ghost_S;  // dual energy: the entropy of the ghost patches [n_ghost][512]
+    // self-gravity in the W-cycle (grav_amr.cu): potential [slot][512] and
+    // acceleration [slot][3][512] at the level's newest (index gc) and
+    // previous times, and g^n of the coarse-fine ghost patches
+    DevBuf<double> phi[2], gacc[2];
+    DevBuf<double> ghost_acc;
+    int gc = 0;
+    unsigned long long structure = 0;  // bumped whenever a regrid changes the level's patches
     int n_ghost = 0;
     // coarse-fine flux registers (section 2.2 fix-up)
     DevBuf<int64_t> fine_off;    // [n_groups*6]: this level's group faces on coarse-fine interfaces
@@ -108,6 +115,12 @@ struct Level {
         ghost_ustar.release();
         ghost_nbr.release();
         ghost_S.release();
+        phi[0].release();
+        phi[1].release();
+        gacc[0].release();
+        gacc[1].release();
+        ghost_acc.release();
+        gc = 0;
         fine_off.release();
         freg.release();
         coarse_off.release();
@@ -203,6 +216,10 @@ struct amr_hydro_ctx {
     // cells the step left unphysical, for the cell remedies (params.fallback)
     amrh::DevBuf<int64_t> fb_list;
     amrh::DevBuf<unsigned long long> fb_count;
+    // self-gravity in the W-cycle (amr_hydro_set_gravity)
+    bool grav_on = false;
+    double grav_G = 0.0, grav_omega = 1.7;
+    int grav_iters = 60, grav_order = 2;
     // phase timing (amr_hydro_phase_timing): event pairs of the recorded
     // phases, spare events, and the nesting depth of the open phase scopes
     bool timing = false;
@@ -254,6 +271,11 @@ amr_status copy_slots(amr_hydro_ctx *c, double *dst, const double *src, const in
 amr_status patch_flags_dev(amr_hydro_ctx *c, int level, uint8_t *pflag);
 amr_status plan_level(amr_hydro_ctx *c, int level);
 amr_status rebuild_cf(amr_hydro_ctx *c, int fine_level);
+// self-gravity in the W-cycle (grav_amr.cu)
+amr_status gravity_level_step(amr_hydro_ctx *c, int level, double dt);
+amr_status gravity_solve_level(amr_hydro_ctx *c, int level);
+amr_status fill_ghost_acc(amr_hydro_ctx *c, int level, double t);
+amr_status launch_grav_correct(amr_hydro_ctx *c, int level, double dt, const double *acc_n, const double *acc_new);
 // device-side bookkeeping (regrid_dev.cu)
 amr_status regrid_dev(amr_hydro_ctx *c, int level);
 amr_status build_posmap(amr_hydro_ctx *c, int level);

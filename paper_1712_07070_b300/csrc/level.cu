@@ -161,6 +161,7 @@ static amr_status launch_level_step(amr_hydro_ctx *c, int level, StepParams &P, 
         if (acc_n) {  // the gravity coupling's predictor
             P.stage = c->prm.scheme == AMR_SCHEME_CTU ? ST_CTU_GRAV : ST_MH_GRAV;
             P.acc_n = acc_n;
+            P.ghost_acc = L.n_ghost ? L.ghost_acc.p : nullptr;
         }
     }
     if (c->prm.scheme == AMR_SCHEME_VL) {  // predictor into U*, then the corrector

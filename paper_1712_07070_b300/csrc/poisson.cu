@@ -618,6 +618,31 @@ void release_poisson(amr_hydro_ctx *c) {
     c->fft_green_ready = false;
 }
 
+// The gravity corrector of a level just advanced by its predictor (U[cur]
+// the predicted state, U[1 - cur] U^n); its fused signal speed replaces the
+// step's, which was of the predicted state.
+amr_status launch_grav_correct(amr_hydro_ctx *c, int level, double dt, const double *acc_n, const double *acc_new) {
+    Level &L = c->lv[level];
+    amr_status st;
+    unsigned long long *sm = c->scal.p + L.scal0 + L.ring, *nb = c->scal.p + L.scal0 + 3 + L.ring;
+    if ((st = cuda_fail(cudaMemsetAsync(sm, 0, 8, c->stream), "memset")) ||
+        (st = cuda_fail(cudaMemsetAsync(nb, 0, 8, c->stream), "memset")))
+        return st;
+    const int64_t n_cells = (int64_t)L.n_patches * PV;
+    const int cfl1 = c->prm.scheme == AMR_SCHEME_CTU;  // Eq. (CFL1) for CTU, else Eq. (CFL2)
+    const double *rec = c->dtbuf.p + 3 * level;
+    if (c->prm.prec == AMR_FP64)
+        k_grav_correct<double><<<c->n_sm * 8, 256, 0, c->stream>>>(L.U[L.cur], L.U[1 - L.cur], acc_n, acc_new,
+                                                                    n_cells, dt, rec, c->prm.gamma, cfl1, sm, nb);
+    else
+        k_grav_correct<float><<<c->n_sm * 8, 256, 0, c->stream>>>(L.U[L.cur], L.U[1 - L.cur], acc_n, acc_new,
+                                                                   n_cells, dt, rec, c->prm.gamma, cfl1, sm, nb);
+    if ((st = cuda_fail(cudaGetLastError(), "k_grav_correct"))) return st;
+    L.speed_valid = true;
+    L.version++;
+    return AMR_OK;
+}
+
 }  // namespace amrh
 
 using namespace amrh;
@@ -725,23 +750,8 @@ amr_status amr_hydro_advance_gravity(amr_hydro_ctx *c, double dt, double G, cons
     if ((st = advance_once(c, 0, dt, nullptr, acc_n, c_acc))) return st;
     // the potential and acceleration of the predicted density
     if ((st = amr_hydro_poisson_root(c, G, phi_new, acc_new, acc_order))) return st;
-    // corrector (the step flipped the buffers: U[cur] is the predicted state);
-    // its fused signal speed replaces the step's, which was of the predicted state
-    unsigned long long *sm = c->scal.p + L.scal0 + L.ring, *nb = c->scal.p + L.scal0 + 3 + L.ring;
-    if ((st = cuda_fail(cudaMemsetAsync(sm, 0, 8, c->stream), "memset")) ||
-        (st = cuda_fail(cudaMemsetAsync(nb, 0, 8, c->stream), "memset")))
-        return st;
-    const int64_t n_cells = (int64_t)L.n_patches * PV;
-    const int cfl1 = c->prm.scheme == AMR_SCHEME_CTU;  // Eq. (CFL1) for CTU, else Eq. (CFL2)
-    if (c->prm.prec == AMR_FP64)
-        k_grav_correct<double><<<c->n_sm * 8, 256, 0, c->stream>>>(L.U[L.cur], L.U[1 - L.cur], acc_n, acc_new,
-                                                                    n_cells, dt, c->dtbuf.p, c->prm.gamma, cfl1, sm, nb);
-    else
-        k_grav_correct<float><<<c->n_sm * 8, 256, 0, c->stream>>>(L.U[L.cur], L.U[1 - L.cur], acc_n, acc_new,
-                                                                   n_cells, dt, c->dtbuf.p, c->prm.gamma, cfl1, sm, nb);
-    if ((st = cuda_fail(cudaGetLastError(), "k_grav_correct"))) return st;
-    L.speed_valid = true;
-    return AMR_OK;
+    // corrector (the step flipped the buffers: U[cur] is the predicted state)
+    return launch_grav_correct(c, 0, dt, acc_n, acc_new);
 }
 
 static amr_status poisson_level(amr_hydro_ctx *c, int level, double G, double omega, int iters,

@@ -250,7 +250,10 @@ amr_status advance_rec(amr_hydro_ctx *c, int l, double dt0, int64_t *updates) {
                 step = dec_rule(c, l, step);
             }
         }
-        if ((st = amr_hydro_advance_level(c, l, step, nullptr))) return st;
+        // with self-gravity the coupled step (predictor, the level's Poisson
+        // solve at the step's end, corrector)
+        if ((st = c->grav_on ? gravity_level_step(c, l, step) : amr_hydro_advance_level(c, l, step, nullptr)))
+            return st;
         if (L.dt_last != step) {  // the level retried with a smaller dt (remedy iv)
             step = L.dt_last;
             last = false;
@@ -266,7 +269,10 @@ amr_status advance_rec(amr_hydro_ctx *c, int l, double dt0, int64_t *updates) {
         }
         if (l < c->prm.lmax && c->lv[l + 1].bound) {
             PhaseScope ph(c, AMR_PH_REGRID);
+            const unsigned long long before = c->lv[l + 1].structure;
             if ((st = amr_hydro_regrid(c, l))) return st;
+            // a changed level solves its potential again at its time
+            if (c->grav_on && c->lv[l + 1].structure != before && (st = gravity_solve_level(c, l + 1))) return st;
         }
     }
     return AMR_OK;

@@ -664,6 +664,7 @@ amr_status regrid_dev(amr_hydro_ctx *c, int l) {
     F.host_stale = L.host_stale = true;
     if (G2) G2->host_stale = true;
     F.version++;
+    F.structure++;
     if ((st = build_posmap(c, l + 1))) return st;
     if (nn) {
         k_rg_sib<<<grid_for((int64_t)nn * 26, 256, 8 * c->n_sm), 256, 0, c->stream>>>(nn, F.d_corner, F.posmap.p,

@@ -126,8 +126,10 @@ struct StepParams {
     double *__restrict__ S_new;
     const double *__restrict__ ghost_S;  // the entropy of the coarse-fine ghost patches [ghost][8^3]
     double de_xi;
-    // gravity predictor (ST_MH_GRAV): the acceleration at t^n, [slot][3][8^3]
+    // gravity predictor (ST_MH_GRAV): the acceleration at t^n, [slot][3][8^3],
+    // and on refined levels that of the coarse-fine ghost patches [ghost][3][8^3]
     const double *__restrict__ acc_n;
+    const double *__restrict__ ghost_acc;
     unsigned long long *smax_out;            // max signal speed of the new state (bits)
     unsigned long long *n_bad;               // count of unphysical new cells
     unsigned long long *clear2;              // two scalars the kernel zeroes for the next step
@@ -513,14 +515,18 @@ __device__ __forceinline__ void hancock_cell(const SM &S, int x, int y, int z, r
 }
 
 // The acceleration at t^n of tile cell (x, y, zl) of the group in table slot
-// ts (gravity predictor; single-level grids, so every position is a slot).
+// ts (gravity predictor).
 template <typename real, typename SM>
 __device__ __forceinline__ void grav_at(const SM &S, const StepParams &P, int ts, int x, int y, int zl, real ga[3]) {
     const int q = ((x + PS) >> 3) + 4 * ((y + PS) >> 3) + 16 * ((zl + PS) >> 3);
     const int sl = S.nbr[ts][q];
     const int off = ((zl + PS) & 7) * 64 + ((y + PS) & 7) * 8 + ((x + PS) & 7);
+    // a same-level slot, or a coarse-fine ghost patch (refined levels: g^n
+    // interpolated from the coarse level)
+    const double *src = sl >= 0 ? P.acc_n + (int64_t)sl * 3 * PV
+                                : (sl <= -2 && P.ghost_acc ? P.ghost_acc + (int64_t)(-2 - sl) * 3 * PV : nullptr);
 #pragma unroll
-    for (int d = 0; d < 3; d++) ga[d] = sl >= 0 ? to_real<real>(__ldg(P.acc_n + ((int64_t)sl * 3 + d) * PV + off)) : real(0);
+    for (int d = 0; d < 3; d++) ga[d] = src ? to_real<real>(__ldg(src + d * PV + off)) : real(0);
 }
 
 // Flux of the dual-energy scalar through a face: the mass flux F_rho times

@@ -418,3 +418,58 @@ def test_coupled_step_at_the_benchmark_size(prec):
     _, acc2 = g.gravity(G, 2)
     assert np.array_equal(acc.cpu().numpy(), acc2.cpu().numpy())
     g.close()
+
+
+# ---- self-gravity inside the AMR W-cycle ---------------------------------------------------
+
+@pytest.mark.parametrize("prec,tol", [(A.AMR_FP64, 1e-12), (A.AMR_FP32_ACC64, 1e-5)])
+def test_wcycle_with_gravity_matches_oracle(prec, tol):
+    """Two root steps of the three-level blob hierarchy with self-gravity in
+    every level step (section 2.3 coupling on the section 2.1 W-cycle): the
+    coupled predictor with ghost accelerations from the coarse level, each
+    level's Poisson solve at its step's end (root FFT, refined SOR with the
+    parent's potential interpolated in time), the corrector, and the
+    re-solve of levels a regrid changed; bit-exact patch lists, every
+    level's state, potential and acceleration against the oracle."""
+    from oracle.amr_gravity import GravityHierarchy
+    from paper_1712_07070_b300.amr import AmrHierarchy
+    U0 = ics.blobs(32, seed=5, contrast=10.0, mach=1.0)
+    G, omega, iters = 2.0, 1.7, 20
+    H = AmrHierarchy(U0, lmax=2, theta=0.3, nbuf=(1, 1), prec=prec, max_patches=6000)
+    H.set_gravity(G, omega, iters, 2)
+    O = GravityHierarchy(U0, lmax=2, gamma=G53, cfl=0.5, theta=0.3, nbuf=[1, 1], G=G, omega=omega, iters=iters)
+    assert 0 < H.n_patches(1) and H.n_patches(2) > 0
+    for _ in range(2):
+        H.advance_root()
+        O.advance(0)
+    compare(H, O, tol)
+    for l in range(3):
+        phi, acc = (t.cpu().numpy() for t in H.gravity(l))
+        num_p = den_p = num_g = den_g = 0.0
+        for s, (x, y, z) in enumerate(H.corners(l).tolist()):
+            rp = O.lv[l].phi[z:z + 8, y:y + 8, x:x + 8]
+            rg = O.lv[l].g[:, z:z + 8, y:y + 8, x:x + 8]
+            num_p += np.abs(phi[s] - rp).sum()
+            den_p += np.abs(rp).sum()
+            num_g += np.abs(acc[s] - rg).sum()
+            den_g += np.abs(rg).sum()
+        assert num_p <= tol * den_p, (l, num_p / den_p)
+        assert num_g <= 10 * tol * den_g, (l, num_g / den_g)
+    H.close()
+
+
+def test_set_gravity_rejects_other_schemes():
+    from paper_1712_07070_b300.amr import AmrHierarchy
+    U0 = ics.blobs(16, seed=1, contrast=10.0, mach=1.0)
+    H = AmrHierarchy(U0, lmax=1, theta=0.3, nbuf=(1,), max_patches=2000,
+                     scheme={"scheme": A.AMR_SCHEME_CTU})
+    with pytest.raises(A.AmrHydroError):
+        H.set_gravity(1.0)
+    H.close()
+    H = AmrHierarchy(U0, lmax=1, theta=0.3, nbuf=(1,), max_patches=2000)
+    for bad in (dict(G=-1.0), dict(omega=2.0), dict(iters=-1), dict(acc_order=3)):
+        kw = dict(G=1.0, omega=1.7, iters=10, acc_order=2)
+        kw.update(bad)
+        with pytest.raises(A.AmrHydroError):
+            H.set_gravity(kw["G"], kw["omega"], kw["iters"], kw["acc_order"])
+    H.close()
