@@ -234,6 +234,8 @@ struct amr_hydro_ctx {
     // isolated gravity: the padded grid's sizes and the transformed kernel
     long long fft_plan[4] = {0, 0, 0, 0};
     amrh::DevBuf<double> fft_real, fft_cplx, fft_green;
+    amrh::DevBuf<double> fft_tw;     // our transforms' twiddle tables (x, y, z), fft.cu
+    int fft_tw_n[3] = {0, 0, 0};
     int fft_m[3] = {0, 0, 0};
     bool fft_green_ready = false;
 };

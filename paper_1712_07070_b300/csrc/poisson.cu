@@ -10,8 +10,9 @@
 // Root level: the 7-point discrete Poisson equation
 //     sum_d (phi_{i+e_d} - 2 phi_i + phi_{i-e_d}) / dh^2 = 4 pi G (rho_i - <rho>)
 // is diagonal in Fourier space: phi_k = 4 pi G dh^2 rho_k / lambda_k with
-// lambda_k = -2 sum_d (1 - cos(2 pi k_d / N_d)) and phi_0 = 0 (cuFFT D2Z,
-// one scaling kernel, Z2D).
+// lambda_k = -2 sum_d (1 - cos(2 pi k_d / N_d)) and phi_0 = 0 (our own
+// transforms, fft.cu, with the Green's factor applied between the forward
+// and inverse z transforms).
 //
 // Isolated root level: every cell a point mass, the pairwise potential by a
 // zero-padded FFT convolution with the kernel -dh^2 / |offset| (details at
@@ -39,6 +40,7 @@
 
 #include "amr_hydro.h"
 #include "ctx.h"
+#include "fft.h"
 #include "step_kernel.cuh"
 
 namespace amrh {
@@ -116,38 +118,6 @@ __global__ void k_green_axes(double *__restrict__ lam1, int nx, int ny, int nz) 
             n = nz;
         }
         lam1[i] = -2.0 * (1.0 - cos(2.0 * PI * k / n));
-    }
-}
-
-// phi_k = 4 pi G dh^2 rho_k / (lambda_k N) (the inverse transform is
-// unnormalised), lambda_k = lam1x + lam1y + lam1z; one warp per (ky, kz) row.
-template <typename C>  // cufftDoubleComplex or cufftComplex
-__global__ void k_green(C *__restrict__ F, const double *__restrict__ lam1, int nx, int ny, int nz, double scale) {
-    const int nxh = nx / 2 + 1;
-    const int lane = threadIdx.x & 31;
-    const int64_t n_rows = (int64_t)ny * nz;
-    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t row = warp0; row < n_rows; row += n_warps) {
-        const int ky = (int)(row % ny), kz = (int)(row / ny);
-        const double lyz = lam1[nxh + ky] + lam1[nxh + ny + kz];
-        C *Fr = F + row * nxh;
-        for (int kx = lane; kx < nxh; kx += 32) {
-            C v = Fr[kx];
-            if (row == 0 && kx == 0) {
-                v.x = 0;
-                v.y = 0;
-            } else if constexpr (sizeof(v.x) == sizeof(float)) {  // FP32 transforms: an FP32 division
-                const float f = (float)scale / (float)(lam1[kx] + lyz);
-                v.x *= f;
-                v.y *= f;
-            } else {
-                const double f = scale / (lam1[kx] + lyz);
-                v.x *= f;
-                v.y *= f;
-            }
-            Fr[kx] = v;
-        }
     }
 }
 
@@ -616,6 +586,8 @@ void release_poisson(amr_hydro_ctx *c) {
     c->fft_cplx.release();
     c->fft_green.release();
     c->fft_green_ready = false;
+    c->fft_tw.release();
+    c->fft_tw_n[0] = c->fft_tw_n[1] = c->fft_tw_n[2] = 0;
 }
 
 // The gravity corrector of a level just advanced by its predictor (U[cur]
@@ -673,23 +645,7 @@ amr_status amr_hydro_poisson_root(amr_hydro_ctx *c, double G, double *phi, doubl
     if (iso)
         return f32 ? root_isolated<Fft32>(c, L, nx, ny, nz, mx, my, mz, G, phi, acc, acc_order)
                    : root_isolated<Fft64>(c, L, nx, ny, nz, mx, my, mz, G, phi, acc, acc_order);
-    if (!c->fft_plan[0]) {
-        cufftHandle f, b;
-        if ((st = cufft_fail(cufftPlan3d(&f, mz, my, mx, f32 ? CUFFT_R2C : CUFFT_D2Z), "plan"))) return st;
-        if ((st = cufft_fail(cufftPlan3d(&b, mz, my, mx, f32 ? CUFFT_C2R : CUFFT_Z2D), "plan"))) {
-            cufftDestroy(f);
-            return st;
-        }
-        c->fft_plan[0] = (long long)f;
-        c->fft_plan[1] = (long long)b;
-        c->fft_m[0] = mx;
-        c->fft_m[1] = my;
-        c->fft_m[2] = mz;
-    }
-    cufftHandle f = (cufftHandle)c->fft_plan[0], b = (cufftHandle)c->fft_plan[1];
     cudaStream_t s = c->stream;
-    if ((st = cufft_fail(cufftSetStream(f, s), "stream")) || (st = cufft_fail(cufftSetStream(b, s), "stream")))
-        return st;
     const double dh = level_dh(c, 0);
     double *lam1 = c->fft_cplx.p + 2 * nc, *partial = lam1 + nx / 2 + 1 + ny + nz;
     k_rho_partial<<<grid, 256, 0, s>>>(L.U[L.cur], L.n_patches, partial);
@@ -697,25 +653,19 @@ amr_status amr_hydro_poisson_root(amr_hydro_ctx *c, double G, double *phi, doubl
     k_green_axes<<<(nx / 2 + 1 + ny + nz + 255) / 256, 256, 0, s>>>(lam1, nx, ny, nz);
     if ((st = cuda_fail(cudaGetLastError(), "k_green_axes"))) return st;
     const double scale = FOUR_PI * G * dh * dh / (double)n;
+    // our transforms (fft.cu): the real field in place, the half spectrum in
+    // fft_cplx, the Green's factor applied between the z transforms
     if (f32) {
         float *R = reinterpret_cast<float *>(c->fft_real.p);
-        cufftComplex *F = reinterpret_cast<cufftComplex *>(c->fft_cplx.p);
         k_rho_dense<float><<<grid, 256, 0, s>>>(L.U[L.cur], L.d_corner, L.n_patches, nx, ny, partial, grid, R);
         if ((st = cuda_fail(cudaGetLastError(), "k_rho_dense"))) return st;
-        if ((st = cufft_fail(cufftExecR2C(f, R, F), "R2C"))) return st;
-        k_green<cufftComplex><<<grid, 256, 0, s>>>(F, lam1, nx, ny, nz, scale);
-        if ((st = cuda_fail(cudaGetLastError(), "k_green"))) return st;
-        if ((st = cufft_fail(cufftExecC2R(b, F, R), "C2R"))) return st;
+        if ((st = fft_poisson_periodic<float>(c, R, nx, ny, nz, lam1, scale, c->fft_cplx.p, nullptr, s))) return st;
         k_root_out<float><<<grid, 256, 0, s>>>(R, L.d_corner, L.n_patches, nx, ny, nz, dh, acc_order, phi, acc);
     } else {
         double *R = c->fft_real.p;
-        cufftDoubleComplex *F = reinterpret_cast<cufftDoubleComplex *>(c->fft_cplx.p);
         k_rho_dense<double><<<grid, 256, 0, s>>>(L.U[L.cur], L.d_corner, L.n_patches, nx, ny, partial, grid, R);
         if ((st = cuda_fail(cudaGetLastError(), "k_rho_dense"))) return st;
-        if ((st = cufft_fail(cufftExecD2Z(f, R, F), "D2Z"))) return st;
-        k_green<cufftDoubleComplex><<<grid, 256, 0, s>>>(F, lam1, nx, ny, nz, scale);
-        if ((st = cuda_fail(cudaGetLastError(), "k_green"))) return st;
-        if ((st = cufft_fail(cufftExecZ2D(b, F, R), "Z2D"))) return st;
+        if ((st = fft_poisson_periodic<double>(c, R, nx, ny, nz, lam1, scale, c->fft_cplx.p, nullptr, s))) return st;
         k_root_out<double><<<grid, 256, 0, s>>>(R, L.d_corner, L.n_patches, nx, ny, nz, dh, acc_order, phi, acc);
     }
     return cuda_fail(cudaGetLastError(), "k_root_out");
