@@ -14,8 +14,9 @@ using namespace amrh;
 
 namespace {
 
-__device__ __forceinline__ double minmod(double a, double b) {
-    if (!(a * b > 0.0)) return 0.0;
+template <typename real>
+__device__ __forceinline__ real minmod(real a, real b) {
+    if (!(a * b > real(0))) return real(0);
     return fabs(a) < fabs(b) ? a : b;
 }
 
@@ -30,18 +31,42 @@ struct CoarseView {
     double w;
     const int *nb;  // 27 slots around the parent
     int64_t stride = PSLOT;  // doubles per slot (PV for a one-variable field)
-    // coarse value of variable v at coarse cell c (relative to the parent's
-    // origin, each coordinate in -8..15), time-interpolated
-    __device__ __forceinline__ double at(int v, int cx, int cy, int cz) const {
+    // offset of variable v at coarse cell c (relative to the parent's
+    // origin, each coordinate in -8..15)
+    __device__ __forceinline__ int64_t index(int v, int cx, int cy, int cz) const {
         const int px = cx >> 3, py = cy >> 3, pz = cz >> 3;
         int s = nb[(px + 1) + 3 * (py + 1) + 9 * (pz + 1)];
         if (s < 0) s = nb[13];  // cannot happen on a properly nested hierarchy
-        const int64_t i = (int64_t)s * stride + v * PV + (cz & 7) * 64 + (cy & 7) * 8 + (cx & 7);
+        return (int64_t)s * stride + v * PV + (cz & 7) * 64 + (cy & 7) * 8 + (cx & 7);
+    }
+    // the coarse value there, time-interpolated
+    __device__ __forceinline__ double at(int v, int cx, int cy, int cz) const {
+        const int64_t i = index(v, cx, cy, cz);
         if (w == 0.0) return Uo[i];
         if (w == 1.0) return Un[i];
         return Uo[i] + w * (Un[i] - Uo[i]);
     }
 };
+
+// The coarse value in the compute type: FP64 as above; in the FP32-compute
+// mode both times' values are rounded to FP32 on the integer units and
+// interpolated in FP32 (wf: w rounded once).
+template <typename real>
+__device__ __forceinline__ real coarse_at(const CoarseView &C, float wf, int v, int cx, int cy, int cz);
+template <>
+__device__ __forceinline__ double coarse_at<double>(const CoarseView &C, float, int v, int cx, int cy, int cz) {
+    return C.at(v, cx, cy, cz);
+}
+template <>
+__device__ __forceinline__ float coarse_at<float>(const CoarseView &C, float wf, int v, int cx, int cy, int cz) {
+    const int64_t i = C.index(v, cx, cy, cz);
+    if (C.w == 0.0) return d2f_bits(C.Uo[i]);
+    if (C.w == 1.0) return d2f_bits(C.Un[i]);
+    const float a = d2f_bits(C.Uo[i]);
+    return a + wf * (d2f_bits(C.Un[i]) - a);
+}
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ double to_double(float x) { return f2d_bits(x); }
 
 // Fine patches interpolated from the coarse level.  Job j (GHOST_INFO ints):
 // a coarse patch P and the patch position q relative to P's children (each
@@ -54,7 +79,11 @@ struct CoarseView {
 constexpr int INTERP_WARPS = 8;  // warps per 256-thread block, two jobs in flight each
 // With So (dual energy) the entropy per unit volume is interpolated the same
 // way into outS ([slot][8^3]), sharing the conserved variables' positivity
-// decision.
+// decision.  real: the arithmetic type.  The coarse-fine ghost patches of the
+// FP32-compute mode are interpolated in FP32 (they only feed its FP32 step;
+// on the FP64 pipe this kernel took a sixth of an AMR root step); the state
+// of new fine patches (a regrid) is interpolated in FP64 in every mode.
+template <typename real>
 __global__ void k_interp_patches(double *__restrict__ out, const int32_t *__restrict__ out_slot,
                                  const int32_t *__restrict__ info, int n_jobs, const double *Uo,
                                  const double *Un, double w, const int32_t *__restrict__ csib,
@@ -83,6 +112,7 @@ __global__ void k_interp_patches(double *__restrict__ out, const int32_t *__rest
         const int n[3] = {(hi[0] - lo[0]) >> 1, (hi[1] - lo[1]) >> 1, (hi[2] - lo[2]) >> 1};
         CoarseView C{Uo, Un, w, nb};
         CoarseView CS{So, Sn, w, nb, PV};
+        const float wf = (float)w;
         const int64_t oslot = out_slot ? out_slot[j] : j;
         double *o = out + oslot * PSLOT;
         const int total = n[0] * n[1] * n[2];
@@ -92,40 +122,48 @@ __global__ void k_interp_patches(double *__restrict__ out, const int32_t *__rest
                       fz = lo[2] + 2 * (i / (n[0] * n[1]));
             // coarse cell relative to the parent's origin
             const int cx = (qx * 8 + fx) >> 1, cy = (qy * 8 + fy) >> 1, cz = (qz * 8 + fz) >> 1;
-            double c[NV], sl[3][NV];
+            real c[NV], sl[3][NV];
 #pragma unroll
             for (int v = 0; v < NV; v++) {
-                c[v] = C.at(v, cx, cy, cz);
-                sl[0][v] = minmod(C.at(v, cx + 1, cy, cz) - c[v], c[v] - C.at(v, cx - 1, cy, cz));
-                sl[1][v] = minmod(C.at(v, cx, cy + 1, cz) - c[v], c[v] - C.at(v, cx, cy - 1, cz));
-                sl[2][v] = minmod(C.at(v, cx, cy, cz + 1) - c[v], c[v] - C.at(v, cx, cy, cz - 1));
+                c[v] = coarse_at<real>(C, wf, v, cx, cy, cz);
+                sl[0][v] = minmod(coarse_at<real>(C, wf, v, cx + 1, cy, cz) - c[v],
+                                  c[v] - coarse_at<real>(C, wf, v, cx - 1, cy, cz));
+                sl[1][v] = minmod(coarse_at<real>(C, wf, v, cx, cy + 1, cz) - c[v],
+                                  c[v] - coarse_at<real>(C, wf, v, cx, cy - 1, cz));
+                sl[2][v] = minmod(coarse_at<real>(C, wf, v, cx, cy, cz + 1) - c[v],
+                                  c[v] - coarse_at<real>(C, wf, v, cx, cy, cz - 1));
             }
-            double u[8][NV];
+            real u[8][NV];
             bool ok = true;
 #pragma unroll
             for (int k = 0; k < 8; k++) {
-                const double sx = (k & 1) ? 0.25 : -0.25, sy = (k & 2) ? 0.25 : -0.25, sz = (k & 4) ? 0.25 : -0.25;
+                const real sx = (k & 1) ? real(0.25) : real(-0.25), sy = (k & 2) ? real(0.25) : real(-0.25),
+                           sz = (k & 4) ? real(0.25) : real(-0.25);
 #pragma unroll
                 for (int v = 0; v < NV; v++) u[k][v] = c[v] + sx * sl[0][v] + sy * sl[1][v] + sz * sl[2][v];
-                const double m2 = u[k][1] * u[k][1] + u[k][2] * u[k][2] + u[k][3] * u[k][3];
-                ok = ok && (u[k][0] > 0.0) && (2.0 * u[k][0] * u[k][4] > m2);
+                const real m2 = u[k][1] * u[k][1] + u[k][2] * u[k][2] + u[k][3] * u[k][3];
+                ok = ok && (u[k][0] > real(0)) && (real(2) * u[k][0] * u[k][4] > m2);
             }
 #pragma unroll
             for (int k = 0; k < 8; k++) {
                 const int off = (fz + (k >> 2)) * 64 + (fy + ((k >> 1) & 1)) * 8 + fx + (k & 1);
 #pragma unroll
-                for (int v = 0; v < NV; v++) o[v * PV + off] = ok ? u[k][v] : c[v];
+                for (int v = 0; v < NV; v++) o[v * PV + off] = to_double(ok ? u[k][v] : c[v]);
             }
             if (So) {
-                const double cs = CS.at(0, cx, cy, cz);
-                const double s0 = minmod(CS.at(0, cx + 1, cy, cz) - cs, cs - CS.at(0, cx - 1, cy, cz));
-                const double s1 = minmod(CS.at(0, cx, cy + 1, cz) - cs, cs - CS.at(0, cx, cy - 1, cz));
-                const double s2 = minmod(CS.at(0, cx, cy, cz + 1) - cs, cs - CS.at(0, cx, cy, cz - 1));
+                const real cs = coarse_at<real>(CS, wf, 0, cx, cy, cz);
+                const real s0 = minmod(coarse_at<real>(CS, wf, 0, cx + 1, cy, cz) - cs,
+                                       cs - coarse_at<real>(CS, wf, 0, cx - 1, cy, cz));
+                const real s1 = minmod(coarse_at<real>(CS, wf, 0, cx, cy + 1, cz) - cs,
+                                       cs - coarse_at<real>(CS, wf, 0, cx, cy - 1, cz));
+                const real s2 = minmod(coarse_at<real>(CS, wf, 0, cx, cy, cz + 1) - cs,
+                                       cs - coarse_at<real>(CS, wf, 0, cx, cy, cz - 1));
 #pragma unroll
                 for (int k = 0; k < 8; k++) {
-                    const double sx = (k & 1) ? 0.25 : -0.25, sy = (k & 2) ? 0.25 : -0.25, sz = (k & 4) ? 0.25 : -0.25;
+                    const real sx = (k & 1) ? real(0.25) : real(-0.25), sy = (k & 2) ? real(0.25) : real(-0.25),
+                               sz = (k & 4) ? real(0.25) : real(-0.25);
                     const int off = (fz + (k >> 2)) * 64 + (fy + ((k >> 1) & 1)) * 8 + fx + (k & 1);
-                    outS[oslot * PV + off] = ok ? cs + sx * s0 + sy * s1 + sz * s2 : cs;
+                    outS[oslot * PV + off] = to_double(ok ? cs + sx * s0 + sy * s1 + sz * s2 : cs);
                 }
             }
         }
@@ -232,15 +270,18 @@ __global__ void k_restrict(double *__restrict__ Uc, const double *__restrict__ U
         for (int i = threadIdx.x; i < PV * nv; i += blockDim.x) {
             const int v = i / PV, c = i % PV;
             const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
+            // the children in (z, y, x) order, summed from the first (the sum
+            // from 0 differs only in the sign of an all-negative-zero sum; on
+            // the narrow FP64 pipe the add saved is a ninth of the kernel)
             double s = 0.0;
-            for (int dz = 0; dz < 2; dz++)
-                for (int dy = 0; dy < 2; dy++)
-                    for (int dx = 0; dx < 2; dx++) {
-                        const int fx = 2 * x + dx, fy = 2 * y + dy, fz = 2 * z + dz;
-                        const int64_t slot = 8 * G + (fx >> 3) + 2 * (fy >> 3) + 4 * (fz >> 3);
-                        const int64_t o = (fz & 7) * 64 + (fy & 7) * 8 + (fx & 7);
-                        s += v < NV ? Uf[slot * PSLOT + v * PV + o] : Sf[slot * PV + o];
-                    }
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int fx = 2 * x + (k & 1), fy = 2 * y + ((k >> 1) & 1), fz = 2 * z + (k >> 2);
+                const int64_t slot = 8 * G + (fx >> 3) + 2 * (fy >> 3) + 4 * (fz >> 3);
+                const int64_t o = (fz & 7) * 64 + (fy & 7) * 8 + (fx & 7);
+                const double f = v < NV ? Uf[slot * PSLOT + v * PV + o] : Sf[slot * PV + o];
+                s = k ? s + f : f;
+            }
             if (v < NV) Uc[P * PSLOT + v * PV + c] = s * 0.125;
             else Sc[P * PV + c] = s * 0.125;
         }
@@ -261,6 +302,7 @@ __global__ void k_flag_summary(const double *__restrict__ U, const double *__res
                                uint32_t *__restrict__ summary) {
     __shared__ int src[64];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;  // warp = local patch 0..7
+    const double theta4 = 4.0 * (theta * theta);
     for (int g = blockIdx.x; g < n_groups; g += gridDim.x) {
         __syncthreads();
         if (threadIdx.x < 64) src[threadIdx.x] = nbr[(int64_t)g * 64 + threadIdx.x];
@@ -279,13 +321,20 @@ __global__ void k_flag_summary(const double *__restrict__ U, const double *__res
             const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
             const int x = ox + lx, y = oy + ly, z = oz + lz;
             const double r = rho_at(x, y, z);
-            const double gx = (rho_at(x + 1, y, z) - rho_at(x - 1, y, z)) / 2.0;
-            const double gy = (rho_at(x, y + 1, z) - rho_at(x, y - 1, z)) / 2.0;
-            const double gz = (rho_at(x, y, z + 1) - rho_at(x, y, z - 1)) / 2.0;
-            double g2 = gx * gx;
-            g2 += gy * gy;
-            g2 += gz * gz;
-            if (!(g2 > theta * theta * (r * r))) continue;
+            // with the undivided differences d = 2 g every term is 4 times
+            // the criterion's, and scaling by 4 is exact, so
+            // D2 = dx^2 + dy^2 + dz^2 > (4 theta^2) r^2 decides exactly as
+            // g^2 > theta^2 r^2 with three FP64 operations fewer; the test
+            // itself compares the bit patterns (both sides >= +0; a NaN
+            // D2 or threshold flags nothing)
+            const double dx = rho_at(x + 1, y, z) - rho_at(x - 1, y, z);
+            const double dy = rho_at(x, y + 1, z) - rho_at(x, y - 1, z);
+            const double dz = rho_at(x, y, z + 1) - rho_at(x, y, z - 1);
+            double d2 = dx * dx;
+            d2 += dy * dy;
+            d2 += dz * dz;
+            const long long bd = __double_as_longlong(d2), bt = __double_as_longlong(theta4 * (r * r));
+            if (!(bd > bt && bd <= 0x7ff0000000000000LL)) continue;
             // parts this cell is in, per dimension (bit 0 low, 1 whole, 2 high)
             const int px = (lx < nbuf) | 2 | (lx >= 8 - nbuf) << 2;
             const int py = (ly < nbuf) | 2 | (ly >= 8 - nbuf) << 2;
@@ -374,9 +423,14 @@ amr_status fill_ghost_impl(amr_hydro_ctx *c, int level, double t) {
     const int blocks = (L.n_ghost + 2 * INTERP_WARPS - 1) / (2 * INTERP_WARPS);
     const int grid = blocks < 8 * c->n_sm ? blocks : 8 * c->n_sm;
     const bool de = c->prm.dual_energy && L.ghost_S.p;
-    k_interp_patches<<<grid, 256, 0, c->stream>>>(L.ghost.p, nullptr, L.ghost_info.p, L.n_ghost, C.U[1 - C.cur],
-                                                   C.U[C.cur], w, C.d_sib, de ? C.S[1 - C.cur] : nullptr,
-                                                   de ? C.S[C.cur] : nullptr, de ? L.ghost_S.p : nullptr);
+    if (c->prm.prec == AMR_FP32_ACC64)
+        k_interp_patches<float><<<grid, 256, 0, c->stream>>>(
+            L.ghost.p, nullptr, L.ghost_info.p, L.n_ghost, C.U[1 - C.cur], C.U[C.cur], w, C.d_sib,
+            de ? C.S[1 - C.cur] : nullptr, de ? C.S[C.cur] : nullptr, de ? L.ghost_S.p : nullptr);
+    else
+        k_interp_patches<double><<<grid, 256, 0, c->stream>>>(
+            L.ghost.p, nullptr, L.ghost_info.p, L.n_ghost, C.U[1 - C.cur], C.U[C.cur], w, C.d_sib,
+            de ? C.S[1 - C.cur] : nullptr, de ? C.S[C.cur] : nullptr, de ? L.ghost_S.p : nullptr);
     if ((st = cuda_fail(cudaGetLastError(), "k_interp_patches"))) return st;
     L.ghost_valid = true;
     L.ghost_t = t;
@@ -410,7 +464,7 @@ amr_status interp_new_patches(amr_hydro_ctx *c, int coarse, double *out, const i
     const int blocks = (n_jobs + 2 * INTERP_WARPS - 1) / (2 * INTERP_WARPS);
     const int grid = blocks < 8 * c->n_sm ? blocks : 8 * c->n_sm;
     const double *cs = out_S ? C.S[C.cur] : nullptr;
-    k_interp_patches<<<grid, 256, 0, c->stream>>>(out, out_slot, info, n_jobs, C.U[C.cur], C.U[C.cur], 1.0,
+    k_interp_patches<double><<<grid, 256, 0, c->stream>>>(out, out_slot, info, n_jobs, C.U[C.cur], C.U[C.cur], 1.0,
                                                    C.d_sib, cs, cs, out_S);
     return cuda_fail(cudaGetLastError(), "k_interp_patches (new patches)");
 }
