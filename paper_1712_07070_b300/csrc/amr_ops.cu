@@ -390,6 +390,7 @@ __global__ void k_patch_sums(const double *__restrict__ U, int n_patches, double
 }
 
 // dst[s] = src[map[s]] for every slot s with map[s] >= 0 (width doubles per slot).
+// dst and src may be one buffer when no copied slot is also written.
 __global__ void k_copy_slots(double *__restrict__ dst, const double *__restrict__ src,
                              const int32_t *__restrict__ map, int n, int width) {
     for (int s = blockIdx.x; s < n; s += gridDim.x) {

@@ -54,6 +54,10 @@ struct Level {
     DevBuf<int32_t> nbr;        // [n_groups][64]
     DevBuf<int32_t> runs, run_off;  // z-runs of groups (step work items), see build_runs
     int n_runs = 0;
+    // the groups in (z, y, x) order of their positions (single-group work
+    // items of a device-regridded level, whose slots stay in place)
+    DevBuf<int32_t> work;
+    bool has_work = false;
     DevBuf<double> ustar;       // VL half-step state, [n_patches][5][512]
     DevBuf<double> ghost;       // [n_ghost][5][512]
     DevBuf<int32_t> ghost_info; // [n_ghost][GHOST_INFO]
@@ -110,6 +114,8 @@ struct Level {
         runs.release();
         run_off.release();
         n_runs = 0;
+        work.release();
+        has_work = false;
         ghost.release();
         ghost_info.release();
         ghost_ustar.release();
@@ -173,11 +179,15 @@ struct RegridScratch {
     DevBuf<int32_t> cnt, bsum, keep, mark, rank, gnew, gpar;
     DevBuf<int32_t> corner, sib, parent, child, old_of, info, new_of;
     DevBuf<int32_t> cf_a, cf_b, cf_c, cf_d, cf_e, cf_f, cf_g, cf_h;
+    DevBuf<int32_t> run_up, run_down, run_len, run_cnt, run_lpos, run_rpos, run_hist;  // z-chains of a plan
+    DevBuf<int32_t> taken, frank, flist, mflag, mrank, nflag;  // group numbering with slots kept in place
     int32_t *hcnt = nullptr;  // pinned, 32 entries
     double *htime = nullptr;  // pinned, 3 entries
     void release() {
         for (DevBuf<int32_t> *b : {&cnt, &bsum, &keep, &mark, &rank, &gnew, &gpar, &corner, &sib, &parent, &child,
-                                   &old_of, &info, &new_of, &cf_a, &cf_b, &cf_c, &cf_d, &cf_e, &cf_f, &cf_g, &cf_h})
+                                   &old_of, &info, &new_of, &cf_a, &cf_b, &cf_c, &cf_d, &cf_e, &cf_f, &cf_g, &cf_h,
+                                   &run_up, &run_down, &run_len, &run_cnt, &run_lpos, &run_rpos, &run_hist, &taken, &frank,
+                                   &flist, &mflag, &mrank, &nflag})
             b->release();
         if (hcnt) cudaFreeHost(hcnt);
         if (htime) cudaFreeHost(htime);

@@ -151,6 +151,8 @@ static amr_status launch_level_step(amr_hydro_ctx *c, int level, StepParams &P, 
         P.runs = L.runs.p;
         P.run_off = L.run_off.p;
         P.n_work = L.n_runs;
+    } else if (L.has_work) {  // single groups in position order (neighbours share ghost reads in L2)
+        P.work = L.work.p;
     }
     const int cap = c->n_sm * c->step_bps;
     const int grid = P.n_work < cap ? P.n_work : cap;

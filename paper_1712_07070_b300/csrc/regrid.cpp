@@ -42,6 +42,8 @@ amr_status plan_level(amr_hydro_ctx *c, int level) {
     L.n_ghost = 0;
     L.plan_version++;
     L.ghost_valid = false;
+    L.n_runs = 0;
+    L.has_work = false;  // the host tables' group order is the caller's
     if (!L.n_patches) return AMR_OK;
     amr_status st0 = refresh_host_tables(c, level);
     if (st0) return st0;
@@ -61,7 +63,6 @@ amr_status plan_level(amr_hydro_ctx *c, int level) {
         const int len = choose_run_len(coff, c->n_sm * c->step_bps, c->prm.prec == AMR_FP64 ? 0.05 : 0.13);
         // single-group runs: the plain group list (a run list would only add
         // the lookups of each work item's group ahead of its tables)
-        L.n_runs = 0;
         if (len > 1) {
             cut_runs(chains, coff, len, runs, off);
             L.n_runs = (int)off.size() - 1;
@@ -183,6 +184,8 @@ amr_status amr_hydro_bind_level(amr_hydro_ctx *c, int level, double *U_a, double
     L.speed_valid = false;
     L.dt_prev = -1.0;
     L.posmap_valid = L.ghost_valid = L.host_stale = false;
+    L.has_work = false;
+    L.n_runs = 0;
     L.version++;
     return AMR_OK;
 }

@@ -15,6 +15,8 @@
 // the same hierarchy, and the numbering never changes a computed value.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <cstring>
 
 #include "amr_hydro.h"
@@ -40,10 +42,14 @@ __device__ __forceinline__ int64_t pos_index(int px, int py, int pz, int PX, int
     return ((int64_t)pz * PY + py) * PX + px;
 }
 
-// ---- exclusive prefix sums of int32 counts (flags: nonzero counts as one) -----------
+// ---- exclusive prefix sums of int32 counts (flags 1: nonzero counts as one; 2: zero
+// counts as one, nonzero as none) ----
 
+// One block per SCAN_BLOCK values; its total into bsum (one block: into
+// *total, and the scan is complete).
 __global__ void __launch_bounds__(SCAN_NT) k_scan_block(const int32_t *__restrict__ in, int32_t *__restrict__ out,
-                                                        int32_t *__restrict__ bsum, int n, int flags) {
+                                                        int32_t *__restrict__ bsum, int n, int flags,
+                                                        int32_t *__restrict__ total) {
     __shared__ int32_t ws[SCAN_NT / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t base = (int64_t)blockIdx.x * SCAN_BLOCK + (int64_t)tid * SCAN_PER;
@@ -52,7 +58,8 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_block(const int32_t *__restric
     for (int k = 0; k < SCAN_PER; k++) {
         const int64_t i = base + k;
         int32_t x = i < n ? in[i] : 0;
-        if (flags) x = x != 0;
+        if (flags == 1) x = x != 0;
+        else if (flags == 2) x = i < n && x == 0;
         v[k] = s;
         s += x;
     }
@@ -72,7 +79,10 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_block(const int32_t *__restric
             if (lane >= o) wi += y;
         }
         if (lane < SCAN_NT / 32) ws[lane] = wi - w;  // exclusive warp offsets
-        if (lane == SCAN_NT / 32 - 1) bsum[blockIdx.x] = wi;
+        if (lane == SCAN_NT / 32 - 1) {
+            if (gridDim.x == 1) *total = wi;
+            else bsum[blockIdx.x] = wi;
+        }
     }
     __syncthreads();
     const int32_t off = ws[warp] + incl - s;
@@ -168,23 +178,85 @@ __global__ void k_rg_select(const uint8_t *__restrict__ pflag, const int32_t *__
     }
 }
 
-// group numbers of the chosen parents (their rank in (z, y, x) corner order)
-__global__ void k_rg_number(const int32_t *__restrict__ mark, const int32_t *__restrict__ rank,
-                            const int32_t *__restrict__ corner, const int32_t *__restrict__ child, int n, int PX,
-                            int PY, int32_t *__restrict__ gnew, int32_t *__restrict__ gpar, int32_t *changed) {
+// Whether the set of chosen parents differs from the current children's
+// parents (changed), and how many there are (count).
+__global__ void k_rg_classify(const int32_t *__restrict__ mark, const int32_t *__restrict__ corner,
+                              const int32_t *__restrict__ child, int n, int PX, int PY, int32_t *changed,
+                              int32_t *count) {
+    int cnt = 0, chg = 0;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const int chosen = mark[pos_index(corner[3 * s] >> 3, corner[3 * s + 1] >> 3, corner[3 * s + 2] >> 3, PX, PY)];
+        cnt += chosen;
+        chg |= chosen != (child[s] >= 0);
+    }
+    if (cnt) atomicAdd(count, cnt);
+    if (chg) atomicOr(changed, 1);
+}
+
+// Group numbers of the new level (ng groups), keeping slots in place: an
+// existing child group keeps its number when it is below ng (taken); the
+// others (moved: numbers >= ng, by number; new: parents without children, in
+// (z, y, x) position order through nflag) take the free numbers below ng in
+// increasing order, the moved ones first.  Pass 1 marks; pass 2 assigns.
+__global__ void k_rg_keepmark(const int32_t *__restrict__ mark, const int32_t *__restrict__ corner,
+                              const int32_t *__restrict__ child, int n, int PX, int PY, int ng,
+                              int32_t *__restrict__ gnew, int32_t *__restrict__ gpar, int32_t *__restrict__ taken,
+                              int32_t *__restrict__ mflag, int32_t *__restrict__ nflag) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
         const int64_t p = pos_index(corner[3 * s] >> 3, corner[3 * s + 1] >> 3, corner[3 * s + 2] >> 3, PX, PY);
-        const int g = mark[p] ? rank[p] : -1;
+        const int og = child[s];
+        gnew[s] = -1;
+        if (!mark[p]) continue;
+        if (og >= 0 && og < ng) {  // stays
+            taken[og] = 1;
+            gnew[s] = og;
+            gpar[og] = s;
+        } else if (og >= 0) {
+            mflag[og] = 1;
+        } else {
+            nflag[p] = 1;
+        }
+    }
+}
+
+// work[rank of the parent's position among the chosen] = group: the new
+// level's groups in (z, y, x) position order.
+__global__ void k_rg_order(const int32_t *__restrict__ mark, const int32_t *__restrict__ prank,
+                           const int32_t *__restrict__ corner, const int32_t *__restrict__ gnew, int n, int PX, int PY,
+                           int32_t *__restrict__ work) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const int64_t p = pos_index(corner[3 * s] >> 3, corner[3 * s + 1] >> 3, corner[3 * s + 2] >> 3, PX, PY);
+        if (mark[p]) work[prank[p]] = gnew[s];
+    }
+}
+
+__global__ void k_rg_freelist(int ng, const int32_t *__restrict__ taken, const int32_t *__restrict__ frank,
+                              int32_t *__restrict__ flist) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
+        if (!taken[g]) flist[frank[g]] = g;
+}
+
+__global__ void k_rg_assign(const int32_t *__restrict__ mark, const int32_t *__restrict__ corner,
+                            const int32_t *__restrict__ child, int n, int PX, int PY, int ng,
+                            const int32_t *__restrict__ flist, const int32_t *__restrict__ mrank,
+                            const int32_t *__restrict__ n_moved, const int32_t *__restrict__ nrank,
+                            int32_t *__restrict__ gnew, int32_t *__restrict__ gpar) {
+    const int M = *n_moved;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const int64_t p = pos_index(corner[3 * s] >> 3, corner[3 * s + 1] >> 3, corner[3 * s + 2] >> 3, PX, PY);
+        const int og = child[s];
+        if (!mark[p] || (og >= 0 && og < ng)) continue;
+        const int g = flist[og >= 0 ? mrank[og] : M + nrank[p]];
         gnew[s] = g;
-        if (g >= 0) gpar[g] = s;
-        if (g != child[s]) atomicOr(changed, 1);
+        gpar[g] = s;
     }
 }
 
 // The new level's tables, slot j = 8 g + k (k: x fastest): corner, parent,
-// the old slot holding its data (-1: interpolated from the parent; job info
-// in the GHOST_INFO layout of k_interp_patches, parent -1 for copied slots),
-// child (the grandchildren of an old slot keep their group), new_of[old] = j.
+// the old slot whose data moves here (-1: none -- the data is already in
+// place, or is interpolated from the parent: job info in the GHOST_INFO
+// layout of k_interp_patches, parent -1 for kept slots), child (the
+// grandchildren of an old slot keep their group), new_of[old] = j.
 __global__ void k_rg_new_slots(int nn, const int32_t *__restrict__ gpar, const int32_t *__restrict__ lcorner,
                                const int32_t *__restrict__ lchild_old, const int32_t *__restrict__ fchild_old,
                                int32_t *__restrict__ corner, int32_t *__restrict__ parent, int32_t *__restrict__ child,
@@ -200,7 +272,7 @@ __global__ void k_rg_new_slots(int nn, const int32_t *__restrict__ gpar, const i
         const int og = lchild_old[P];
         if (og >= 0) {
             const int o = 8 * og + k;
-            old_of[j] = o;
+            old_of[j] = o == j ? -1 : o;
             child[j] = fchild_old[o];
             new_of[o] = j;
             I[0] = -1;
@@ -430,6 +502,121 @@ __global__ void k_cf_coarse_write(int n_c, const int32_t *__restrict__ csib, con
     }
 }
 
+// ---- z-runs of a refined level (the counterpart of z_chains, choose_run_len
+// and cut_runs of the host plan: the same chains, length and runs, closed
+// cycles listed among the open chains by their head) ----
+//
+// Group u is g's upper neighbour when position (1,1,3) of g's 4x4x4 table
+// (index 53) holds u's first patch and position (1,1,0) of u (index 5) holds
+// g's patch (0,0,1): same-level groups stacked in z.  The relation is one to
+// one.
+__global__ void k_run_links(int ng, const int32_t *__restrict__ nbr, int32_t *__restrict__ up,
+                            int32_t *__restrict__ down) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        const int32_t s = nbr[(int64_t)g * 64 + 53];
+        int u = -1;
+        if (s >= 0 && s % 8 == 0) {
+            const int cand = s / 8;
+            if (cand != g && cand < ng && nbr[(int64_t)cand * 64 + 5] == 8 * g + 4) u = cand;
+        }
+        up[g] = u;
+        if (u >= 0) down[u] = g;
+    }
+}
+
+// Chain heads and their lengths (0 elsewhere), with a histogram of the
+// lengths (bins 1..hmax, longer ones in bin hmax): a group with no lower
+// neighbour heads the chain of upper neighbours above it; a closed cycle (a
+// periodic column) is headed by its lowest group id.  Walks are bounded by
+// the group count.
+__global__ void k_run_heads(int ng, const int32_t *__restrict__ up, const int32_t *__restrict__ down,
+                            int32_t *__restrict__ clen, int32_t *__restrict__ hist, int hmax) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        int L = 0;
+        if (down[g] < 0) {
+            L = 1;
+            for (int x = up[g]; x >= 0 && L < ng; x = up[x]) L++;
+        } else {
+            int x = up[g], m = g, n = 1;
+            while (x >= 0 && x != g && n < ng) {
+                m = x < m ? x : m;
+                x = up[x];
+                n++;
+            }
+            if (x == g && m == g) L = n;
+        }
+        clen[g] = L;
+        if (L) atomicAdd(hist + (L < hmax ? L : hmax), 1);
+    }
+}
+
+// The run length in 1..32 minimising the round-robin estimate
+// ceil(n_runs / grid) (min(len, longest) + e), from the length histogram
+// (one block; the first minimum, as on the host); out[0] = length.
+constexpr int RUN_NT = 256, RUN_MAXLEN = 32;
+__global__ void __launch_bounds__(RUN_NT) k_run_len(const int32_t *__restrict__ hist, int hmax, int grid, double e,
+                                                    int32_t *__restrict__ out) {
+    __shared__ unsigned long long cnt[RUN_MAXLEN];
+    __shared__ double cost[RUN_MAXLEN];
+    __shared__ int longest;
+    if (threadIdx.x < RUN_MAXLEN) cnt[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) longest = 0;
+    __syncthreads();
+    for (int L = 1 + threadIdx.x; L <= hmax; L += RUN_NT) {
+        const unsigned long long h = (unsigned)hist[L];
+        if (!h) continue;
+        atomicMax(&longest, L);
+#pragma unroll
+        for (int k = 0; k < RUN_MAXLEN; k++) atomicAdd(&cnt[k], h * (unsigned)((L + k) / (k + 1)));
+    }
+    __syncthreads();
+    if (threadIdx.x < RUN_MAXLEN) {
+        const int len = threadIdx.x + 1;
+        const long long rounds = ((long long)cnt[threadIdx.x] + grid - 1) / grid;
+        cost[threadIdx.x] = (double)rounds * ((len < longest ? len : longest) + e);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int best_len = 1;
+        double best = 1e300;
+        for (int k = 0; k < RUN_MAXLEN; k++)
+            if (cost[k] < best - 1e-9) {
+                best = cost[k];
+                best_len = k + 1;
+            }
+        out[0] = best_len;
+    }
+}
+
+// Runs per chain head for the chosen length.
+__global__ void k_run_count(int ng, const int32_t *__restrict__ clen, const int32_t *__restrict__ lenp,
+                            int32_t *__restrict__ rcnt) {
+    const int len = *lenp;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
+        rcnt[g] = (clen[g] + len - 1) / len;
+}
+
+// Each head writes its chain at lpos and its runs' offsets at rpos; the
+// head whose runs come last also closes run_off.
+__global__ void k_run_write(int ng, const int32_t *__restrict__ up, const int32_t *__restrict__ clen,
+                            const int32_t *__restrict__ lpos, const int32_t *__restrict__ rpos,
+                            const int32_t *__restrict__ lenp, const int32_t *__restrict__ n_runs,
+                            int32_t *__restrict__ runs, int32_t *__restrict__ run_off) {
+    const int len = *lenp, total = *n_runs;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        const int L = clen[g];
+        if (!L) continue;
+        const int a = lpos[g], r0 = rpos[g], R = (L + len - 1) / len;
+        int x = g;
+        for (int i = 0; i < L; i++) {
+            runs[a + i] = x;
+            x = up[x];
+        }
+        for (int r = 0; r < R; r++) run_off[r0 + r] = a + r * len;
+        if (r0 + R == total) run_off[total] = a + L;
+    }
+}
+
 inline int grid_for(int64_t n, int nt, int cap) {
     const int64_t b = (n + nt - 1) / nt;
     return (int)(b < 1 ? 1 : (b < cap ? b : cap));
@@ -438,12 +625,13 @@ inline int grid_for(int64_t n, int nt, int cap) {
 }  // namespace
 
 // Exclusive scan of n int32 values into out; the total goes to *total (device).
-static amr_status scan_i32(amr_hydro_ctx *c, const int32_t *in, int32_t *out, int64_t n, int32_t *total, bool flags) {
+static amr_status scan_i32(amr_hydro_ctx *c, const int32_t *in, int32_t *out, int64_t n, int32_t *total, int flags) {
     amr_status st;
     const int nb = (int)((n + SCAN_BLOCK - 1) / SCAN_BLOCK);
     if ((st = c->rg.bsum.reserve(nb > 0 ? nb : 1))) return st;
     if (n == 0) return cuda_fail(cudaMemsetAsync(total, 0, 4, c->stream), "memset");
-    k_scan_block<<<nb, SCAN_NT, 0, c->stream>>>(in, out, c->rg.bsum.p, (int)n, flags ? 1 : 0);
+    k_scan_block<<<nb, SCAN_NT, 0, c->stream>>>(in, out, c->rg.bsum.p, (int)n, flags, total);
+    if (nb == 1) return cuda_fail(cudaGetLastError(), "scan");
     k_scan_sums<<<1, SCAN_NT, 0, c->stream>>>(c->rg.bsum.p, nb, total);
     k_scan_add<<<(int)((n + 255) / 256), 256, 0, c->stream>>>(out, c->rg.bsum.p, (int)n);
     return cuda_fail(cudaGetLastError(), "scan");
@@ -472,8 +660,41 @@ amr_status build_posmap(amr_hydro_ctx *c, int level) {
 }
 
 // Neighbour plan of level X >= 1 on the device (the counterpart of
-// build_nbr_plan + plan_level on the host), without z-runs.  Queues the
+// build_nbr_plan + plan_level on the host; its z-runs: plan_runs_dev).  Queues the
 // kernels; the ghost count lands in *n_ghost_dev.
+// z-runs of level X from its neighbour plan, into L.runs / L.run_off;
+// run_cnt[0] = the number of runs, run_cnt[1] = their length (the host uses
+// the runs when the length exceeds 1, as the host plan does).
+static amr_status plan_runs_dev(amr_hydro_ctx *c, int X, int32_t *run_cnt) {
+    Level &L = c->lv[X];
+    auto &S = c->rg;
+    const int ng = L.n_groups;
+    amr_status st;
+    if ((st = S.run_up.reserve(ng + 1)) || (st = S.run_down.reserve(ng + 1)) || (st = S.run_len.reserve(ng + 1)) ||
+        (st = S.run_cnt.reserve(ng + 1)) || (st = S.run_lpos.reserve(ng + 1)) || (st = S.run_rpos.reserve(ng + 1)) ||
+        (st = L.runs.reserve(ng + 1)) || (st = L.run_off.reserve(ng + 2)))
+        return st;
+    // a chain holds at most the level's column of groups
+    const int hmax = ((c->prm.root_n[2] << X) + 15) / 16;
+    if ((st = S.run_hist.reserve(hmax + 1))) return st;
+    if ((st = cuda_fail(cudaMemsetAsync(S.run_down.p, 0xff, 4 * (size_t)ng, c->stream), "memset")) ||
+        (st = cuda_fail(cudaMemsetAsync(S.run_hist.p, 0, 4 * (size_t)(hmax + 1), c->stream), "memset")))
+        return st;
+    const int gb = grid_for(ng, 256, 8 * c->n_sm);
+    k_run_links<<<gb, 256, 0, c->stream>>>(ng, L.nbr.p, S.run_up.p, S.run_down.p);
+    k_run_heads<<<gb, 256, 0, c->stream>>>(ng, S.run_up.p, S.run_down.p, S.run_len.p, S.run_hist.p, hmax);
+    k_run_len<<<1, RUN_NT, 0, c->stream>>>(S.run_hist.p, hmax, c->n_sm * c->step_bps,
+                                           c->prm.prec == AMR_FP64 ? 0.05 : 0.13, run_cnt + 1);
+    k_run_count<<<gb, 256, 0, c->stream>>>(ng, S.run_len.p, run_cnt + 1, S.run_cnt.p);
+    if ((st = cuda_fail(cudaGetLastError(), "z-runs"))) return st;
+    if ((st = scan_i32(c, S.run_len.p, S.run_lpos.p, ng, run_cnt + 2, false)) ||
+        (st = scan_i32(c, S.run_cnt.p, S.run_rpos.p, ng, run_cnt, false)))
+        return st;
+    k_run_write<<<gb, 256, 0, c->stream>>>(ng, S.run_up.p, S.run_len.p, S.run_lpos.p, S.run_rpos.p, run_cnt + 1,
+                                           run_cnt, L.runs.p, L.run_off.p);
+    return cuda_fail(cudaGetLastError(), "k_run_write");
+}
+
 static amr_status plan_level_dev(amr_hydro_ctx *c, int X, int32_t *n_ghost_dev, int32_t *err) {
     Level &L = c->lv[X], &C = c->lv[X - 1];
     amr_status st;
@@ -608,15 +829,41 @@ amr_status regrid_dev(amr_hydro_ctx *c, int l) {
     k_rg_select<<<gl, 256, 0, c->stream>>>(c->pflag.p, L.d_sib, L.d_child, G2 ? S.keep.p : nullptr, L.d_corner, n,
                                            PL[0], PL[1], S.mark.p);
     if ((st = cuda_fail(cudaGetLastError(), "k_rg_select"))) return st;
-    if ((st = scan_i32(c, S.mark.p, S.rank.p, npl, cnt + 2, false))) return st;
-    k_rg_number<<<gl, 256, 0, c->stream>>>(S.mark.p, S.rank.p, L.d_corner, L.d_child, n, PL[0], PL[1], S.gnew.p,
-                                           S.gpar.p, cnt + 1);
-    if ((st = cuda_fail(cudaGetLastError(), "k_rg_number"))) return st;
+    k_rg_classify<<<gl, 256, 0, c->stream>>>(S.mark.p, L.d_corner, L.d_child, n, PL[0], PL[1], cnt + 1, cnt + 2);
+    if ((st = cuda_fail(cudaGetLastError(), "k_rg_classify"))) return st;
     if ((st = read_counts(c, 3))) return st;
     if (S.hcnt[0]) return AMR_E_NESTING;
     if (!S.hcnt[1]) return AMR_OK;  // the refined set is unchanged
     const int ng = S.hcnt[2], nn = 8 * ng;
     if (nn > c->prm.max_patches) return AMR_E_NOMEM;
+
+    // group numbers, slots kept in place (k_rg_keepmark); counts of free
+    // numbers, moved and new groups into cnt[21..23]
+    const int ng_old = F.n_groups;
+    if ((st = S.taken.reserve(ng + 1)) || (st = S.frank.reserve(ng + 1)) || (st = S.flist.reserve(ng + 1)) ||
+        (st = S.mflag.reserve(ng_old + 1)) || (st = S.mrank.reserve(ng_old + 1)) || (st = S.nflag.reserve(npl)))
+        return st;
+    if ((st = cuda_fail(cudaMemsetAsync(S.taken.p, 0, 4 * ((size_t)ng + 1), c->stream), "memset")) ||
+        (st = cuda_fail(cudaMemsetAsync(S.mflag.p, 0, 4 * ((size_t)ng_old + 1), c->stream), "memset")) ||
+        (st = cuda_fail(cudaMemsetAsync(S.nflag.p, 0, 4 * (size_t)npl, c->stream), "memset")))
+        return st;
+    k_rg_keepmark<<<gl, 256, 0, c->stream>>>(S.mark.p, L.d_corner, L.d_child, n, PL[0], PL[1], ng, S.gnew.p, S.gpar.p,
+                                             S.taken.p, S.mflag.p, S.nflag.p);
+    if ((st = cuda_fail(cudaGetLastError(), "k_rg_keepmark"))) return st;
+    if ((st = scan_i32(c, S.taken.p, S.frank.p, ng, cnt + 21, 2)) ||
+        (st = scan_i32(c, S.mflag.p, S.mrank.p, ng_old, cnt + 22, 0)) ||
+        (st = scan_i32(c, S.nflag.p, S.rank.p, npl, cnt + 23, 0)))
+        return st;
+    k_rg_freelist<<<grid_for(ng, 256, 8 * c->n_sm), 256, 0, c->stream>>>(ng, S.taken.p, S.frank.p, S.flist.p);
+    k_rg_assign<<<gl, 256, 0, c->stream>>>(S.mark.p, L.d_corner, L.d_child, n, PL[0], PL[1], ng, S.flist.p, S.mrank.p,
+                                           cnt + 22, S.rank.p, S.gnew.p, S.gpar.p);
+    // the step's work list: the groups in position order (nflag's buffer
+    // takes the chosen positions' ranks)
+    if ((st = F.work.reserve(ng + 1))) return st;
+    if ((st = scan_i32(c, S.mark.p, S.nflag.p, npl, cnt + 24, 0))) return st;
+    k_rg_order<<<gl, 256, 0, c->stream>>>(S.mark.p, S.nflag.p, L.d_corner, S.gnew.p, n, PL[0], PL[1], F.work.p);
+    F.has_work = true;
+    if ((st = cuda_fail(cudaGetLastError(), "k_rg_assign"))) return st;
 
     // the new level's tables (into scratch first: the old ones are still read)
     const int n_old = F.n_patches;
@@ -631,15 +878,16 @@ amr_status regrid_dev(amr_hydro_ctx *c, int l) {
             S.new_of.p);
         if ((st = cuda_fail(cudaGetLastError(), "k_rg_new_slots"))) return st;
     }
-    // cell data of the new level into its other buffer (with dual energy also
-    // the entropy, which pairs with the same buffer index)
-    const int dst = n_old ? 1 - F.cur : 0;
-    double *Ud = F.U[dst];
+    // cell data of the new level in place (with dual energy also the
+    // entropy): kept groups stay in their slots, moved ones are copied from
+    // slots >= nn into free slots < nn, new ones are interpolated into the
+    // remaining free slots
+    double *Ud = F.U[F.cur];
     const bool de = c->prm.dual_energy != 0;
     if (de && (!F.S[0] || !F.S[1] || !L.S[0])) return AMR_E_INVAL;  // amr_hydro_set_entropy first
-    if (n_old && nn && (st = copy_slots(c, Ud, F.U[F.cur], S.old_of.p, nn))) return st;
-    if (de && n_old && nn && (st = copy_slots(c, F.S[dst], F.S[F.cur], S.old_of.p, nn, PV))) return st;
-    if ((st = interp_new_patches(c, l, Ud, nullptr, S.info.p, nn, de ? F.S[dst] : nullptr))) return st;
+    if (n_old && nn && (st = copy_slots(c, Ud, Ud, S.old_of.p, nn))) return st;
+    if (de && n_old && nn && (st = copy_slots(c, F.S[F.cur], F.S[F.cur], S.old_of.p, nn, PV))) return st;
+    if ((st = interp_new_patches(c, l, Ud, nullptr, S.info.p, nn, de ? F.S[F.cur] : nullptr))) return st;
     // commit: level l's child groups, grandchildren's parents, the new tables
     const int n_g2 = G2 ? G2->n_patches : 0;
     k_rg_commit<<<grid_for(n > n_g2 ? n : n_g2, 256, 8 * c->n_sm), 256, 0, c->stream>>>(
@@ -656,7 +904,6 @@ amr_status regrid_dev(amr_hydro_ctx *c, int l) {
     }
     F.n_patches = nn;
     F.n_groups = ng;
-    F.cur = dst;
     F.t = F.t_prev = L.t;
     F.t_pending = false;
     F.speed_valid = false;
@@ -686,16 +933,19 @@ amr_status regrid_dev(amr_hydro_ctx *c, int l) {
     F.n_creg = F.n_fix = F.n_restrict = 0;
     if (nn) {
         if ((st = plan_level_dev(c, l + 1, cnt + 4, cnt + 0))) return st;
+        if ((st = plan_runs_dev(c, l + 1, cnt + 14))) return st;
         if ((st = cf_dev(c, l + 1, cnt + 5, cnt + 0))) return st;
         if (G2) {
             if ((st = plan_level_dev(c, l + 2, cnt + 9, cnt + 0))) return st;
+            if ((st = plan_runs_dev(c, l + 2, cnt + 17))) return st;
             if ((st = cf_dev(c, l + 2, cnt + 10, cnt + 0))) return st;
         }
     }
-    if ((st = read_counts(c, 14))) return st;
+    if ((st = read_counts(c, 20))) return st;
     if (S.hcnt[0] & 2) return AMR_E_NOMEM;
     if (S.hcnt[0]) return AMR_E_NESTING;
     if (nn) {
+        F.n_runs = S.hcnt[15] > 1 ? S.hcnt[14] : 0;
         F.n_ghost = S.hcnt[4];
         if (F.n_ghost && (st = F.ghost.reserve((size_t)F.n_ghost * PSLOT))) return st;
         if (F.n_ghost && c->prm.scheme == AMR_SCHEME_VL && (st = F.ghost_ustar.reserve((size_t)F.n_ghost * PSLOT)))
@@ -704,6 +954,7 @@ amr_status regrid_dev(amr_hydro_ctx *c, int l) {
         if ((st = cf_finish(c, l + 1, S.hcnt + 5))) return st;
         F.ghost_valid = false;
         if (G2) {
+            G2->n_runs = S.hcnt[18] > 1 ? S.hcnt[17] : 0;
             G2->n_ghost = S.hcnt[9];
             if (G2->n_ghost && (st = G2->ghost.reserve((size_t)G2->n_ghost * PSLOT))) return st;
             if (G2->n_ghost && c->prm.scheme == AMR_SCHEME_VL &&
@@ -748,3 +999,38 @@ amr_status refresh_host_tables(amr_hydro_ctx *c, int level) {
 }
 
 }  // namespace amrh
+
+// Test hook (not part of the C ABI): whether level `level`'s z-runs (the
+// device plan's, or single groups) equal what the host plan makes from the
+// same neighbour table (chains, run length for the same grid and estimate,
+// runs); *n_runs_out = the level's run count.  1: equal, 0: different,
+// -1: a CUDA error.
+extern "C" int amrh_selftest_level_runs(amr_hydro_ctx *c, int level, int *n_runs_out) {
+    using namespace amrh;
+    Level &L = c->lv[level];
+    const int ng = L.n_groups;
+    std::vector<int32_t> nbr((size_t)ng * 64);
+    if (ng && cudaMemcpy(nbr.data(), L.nbr.p, 4 * nbr.size(), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    std::vector<int32_t> chains, coff, runs, off;
+    z_chains(ng, nbr.data(), chains, coff);
+    const int len = choose_run_len(coff, c->n_sm * c->step_bps, c->prm.prec == AMR_FP64 ? 0.05 : 0.13);
+    *n_runs_out = L.n_runs;
+    if (len <= 1) return L.n_runs == 0 ? 1 : 0;
+    cut_runs(chains, coff, len, runs, off);
+    if (L.n_runs != (int)off.size() - 1) return 0;
+    std::vector<int32_t> dr(runs.size()), doff(off.size());
+    if (cudaMemcpy(dr.data(), L.runs.p, 4 * dr.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(doff.data(), L.run_off.p, 4 * doff.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return -1;
+    // the same runs; closed cycles may come in another order than the host's
+    // (which lists them after the open chains)
+    std::vector<std::vector<int32_t>> a, b;
+    for (size_t r = 0; r + 1 < off.size(); r++) {
+        a.emplace_back(runs.begin() + off[r], runs.begin() + off[r + 1]);
+        if (doff[r] < 0 || doff[r + 1] > (int)dr.size() || doff[r] > doff[r + 1]) return 0;
+        b.emplace_back(dr.begin() + doff[r], dr.begin() + doff[r + 1]);
+    }
+    std::sort(a.begin(), a.end());
+    std::sort(b.begin(), b.end());
+    return a == b ? 1 : 0;
+}
