@@ -287,7 +287,7 @@ amr_status amr_hydro_init(const amr_hydro_params *p, void *stream, amr_hydro_ctx
     if ((st = c->scal.reserve(SCAL_N))) { amr_hydro_destroy(c); return st; }
     if ((st = c->dtbuf.reserve(3 * (MAX_LEVELS + MAX_BOXES)))) { amr_hydro_destroy(c); return st; }
     if (cudaMallocHost(&c->rg.hcnt, 32 * sizeof(int32_t)) != cudaSuccess ||
-        cudaMallocHost(&c->rg.htime, 3 * sizeof(double)) != cudaSuccess) {
+        cudaMallocHost(&c->rg.htime, 8 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         amr_hydro_destroy(c);
         return AMR_E_NOMEM;
@@ -370,7 +370,8 @@ amr_status amr_hydro_min_dt(amr_hydro_ctx *c, int level, double *dt_out) {
         k_dt_from_speed<<<1, 1, 0, c->stream>>>(sm, nb, c->prm.cfl, dh, dt_out);
         return cuda_fail(cudaGetLastError(), "k_dt_from_speed");
     }
-    unsigned long long h[2];
+    // into pinned host memory (a pageable copy takes a staging detour)
+    unsigned long long *h = reinterpret_cast<unsigned long long *>(c->rg.htime + 4);
     if ((st = cuda_fail(cudaMemcpyAsync(&h[0], sm, 8, cudaMemcpyDeviceToHost, c->stream), "d2h")))
         return st;
     if ((st = cuda_fail(cudaMemcpyAsync(&h[1], nb, 8, cudaMemcpyDeviceToHost, c->stream), "d2h")))

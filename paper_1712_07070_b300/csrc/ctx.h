@@ -182,7 +182,7 @@ struct RegridScratch {
     DevBuf<int32_t> run_up, run_down, run_len, run_cnt, run_lpos, run_rpos, run_hist;  // z-chains of a plan
     DevBuf<int32_t> taken, frank, flist, mflag, mrank, nflag;  // group numbering with slots kept in place
     int32_t *hcnt = nullptr;  // pinned, 32 entries
-    double *htime = nullptr;  // pinned, 3 entries
+    double *htime = nullptr;  // pinned, 8 entries: a time record (0..2), min_dt's reads (4, 5)
     void release() {
         for (DevBuf<int32_t> *b : {&cnt, &bsum, &keep, &mark, &rank, &gnew, &gpar, &corner, &sib, &parent, &child,
                                    &old_of, &info, &new_of, &cf_a, &cf_b, &cf_c, &cf_d, &cf_e, &cf_f, &cf_g, &cf_h,
