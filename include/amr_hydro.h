@@ -398,7 +398,9 @@ amr_status amr_hydro_box_tuning(amr_hydro_ctx *ctx, int *grid, int *chunked, int
  * [n_patches][8][8][8] in level 0's slot order; acc: NULL or
  * [n_patches][3][8][8][8] receiving g = -grad phi (x, y, z) by acc_order = 2
  * or 4 point central differences.  Caller-owned, device; asynchronous on
- * the context's stream.  Uses cuFFT (plans kept in the context).  With
+ * the context's stream.  The library's own mixed-radix FFT (twiddle tables
+ * and work arrays kept in the context; every root extent's prime factors at
+ * most 64, x even).  With
  * params.gravity_bc = AMR_GRAVITY_ISOLATED: the pairwise point-mass
  * potential (no mean subtracted) by zero-padded FFT convolution, the edge
  * cells' differences reading the potential just outside the box.  In the

@@ -54,7 +54,7 @@ def build(force=False, verbose=False):
                 print(log)
     objs = [o for o, _ in results]
     tmp = LIB + ".tmp"
-    subprocess.run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcufft"], check=True)
+    subprocess.run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], check=True)
     os.replace(tmp, LIB)
     return LIB
 

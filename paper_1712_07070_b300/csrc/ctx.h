@@ -240,13 +240,12 @@ struct amr_hydro_ctx {
     };
     std::vector<PhaseRec> phase_recs;
     std::vector<cudaEvent_t> phase_spare;
-    // root-level Poisson solver: cuFFT plans (forward, inverse) and work arrays;
-    // isolated gravity: the padded grid's sizes and the transformed kernel
-    long long fft_plan[4] = {0, 0, 0, 0};
+    // root-level Poisson solver (fft.cu): the real grid, its half spectrum,
+    // the twiddle tables (x, y, z) and, with isolated boundaries, the
+    // transformed kernel
     amrh::DevBuf<double> fft_real, fft_cplx, fft_green;
-    amrh::DevBuf<double> fft_tw;     // our transforms' twiddle tables (x, y, z), fft.cu
+    amrh::DevBuf<double> fft_tw;
     int fft_tw_n[3] = {0, 0, 0};
-    int fft_m[3] = {0, 0, 0};
     bool fft_green_ready = false;
 };
 

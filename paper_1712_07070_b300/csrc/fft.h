@@ -1,5 +1,5 @@
-// fft.h -- the root level's periodic Poisson solve with our own transforms
-// (fft.cu).
+// fft.h -- the root level's Poisson solves (periodic, and the isolated
+// zero-padded convolution) with our own transforms (fft.cu).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -24,9 +24,25 @@ bool fft_factor(int n, FftAxis &ax);
 // [nz][ny][nx] (in place; the (0,0,0) mode set to zero), lambda_k the
 // second-order Laplacian's eigenvalues from the per-axis table lam1 (x: nx/2+1
 // entries, then y, then z).  T: double, or float in the FP32-compute mode.
-// Work arrays: spec (nz ny (nx/2+1) complex), tw (the twiddle tables).
+// spec: the half spectrum's storage, nz ny (nx/2+1) complex values of T.
 template <typename T>
 amr_status fft_poisson_periodic(amr_hydro_ctx *c, T *R, int nx, int ny, int nz, const double *lam1, double scale,
-                                void *spec, double2 *tw, cudaStream_t s);
+                                void *spec, cudaStream_t s);
+
+// The forward transform of the real field R [mz][my][mx] (mx even) into its
+// half spectrum spec [mz][my][mx/2+1] (R is overwritten by nothing).
+template <typename T>
+amr_status fft_forward_full(amr_hydro_ctx *c, T *R, int mx, int my, int mz, void *spec, cudaStream_t s);
+
+// The zero-padded convolution of the isolated root solve: R [mz][my][mx]
+// holds data on planes z < nz (zero elsewhere; those planes are not read);
+// R <- FFT^-1[ scale FFT[R] gk ] (gk: a half spectrum as fft_forward_full
+// makes, the product formed in FP64), written on the planes z < nz + 2 and
+// z >= mz - 2 only (the ones the potential's differences read).  The
+// transforms are pruned to those planes; the arithmetic is the full 3-D
+// transform's.  spec: the half spectrum's storage.
+template <typename T>
+amr_status fft_convolve_isolated(amr_hydro_ctx *c, T *R, int mx, int my, int mz, int nz, const void *gk,
+                                 double scale, void *spec, cudaStream_t s);
 
 }  // namespace amrh

@@ -34,7 +34,6 @@
 // sibling positions hold patches, and the grid reaches at most 4 coarse cells
 // beyond the parent.
 #include <cuda_runtime.h>
-#include <cufft.h>
 
 #include <cstdio>
 
@@ -123,7 +122,8 @@ __global__ void k_green_axes(double *__restrict__ lam1, int nx, int ny, int nz) 
 
 // ---- isolated boundaries: zero-padded convolution with the point-mass kernel ------
 
-// The smallest integer >= n whose prime factors are 2, 3, 5 or 7 (a fast cuFFT size).
+// The smallest integer >= n whose prime factors are 2, 3, 5 or 7 (a size our
+// transforms take with radix 2-7 stages).
 int smooth7(int n) {
     for (;; n++) {
         int k = n;
@@ -171,17 +171,6 @@ __global__ void k_rho_scatter(const double *__restrict__ U, const int32_t *__res
         const int x = corner[3 * s] + (c & 7), y = corner[3 * s + 1] + ((c >> 3) & 7),
                   z = corner[3 * s + 2] + (c >> 6);
         out[((int64_t)z * my + y) * mx + x] = (T)U[s * PSLOT + c];
-    }
-}
-
-// F *= G_hat * scale (the transforms of the density and of the kernel)
-template <typename C>
-__global__ void k_iso_mul(C *__restrict__ F, const C *__restrict__ Gk, int64_t n, double scale) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const C a = F[i], b = Gk[i];
-        const double re = (double)a.x * b.x - (double)a.y * b.y, im = (double)a.x * b.y + (double)a.y * b.x;
-        F[i].x = (decltype(a.x))(re * scale);
-        F[i].y = (decltype(a.y))(im * scale);
     }
 }
 
@@ -440,12 +429,6 @@ __global__ void k_acc_speed(const double *__restrict__ acc, int64_t n, double dh
         atomicMax(smax, (unsigned long long)__double_as_longlong(scale * sqrt(dh * m)));
 }
 
-amr_status cufft_fail(cufftResult r, const char *where) {
-    if (r == CUFFT_SUCCESS) return AMR_OK;
-    std::fprintf(stderr, "amr_hydro: %s: cuFFT error %d\n", where, (int)r);
-    return AMR_E_CUDA;
-}
-
 }  // namespace
 
 amr_status launch_acc_speed(amr_hydro_ctx *c, const double *acc, int64_t n_values, double dh, double c_acc,
@@ -475,113 +458,42 @@ amr_status launch_sor(amr_hydro_ctx *c, Level &L, Level &C, int level, double G,
     return cuda_fail(cudaGetLastError(), "k_sor_patches");
 }
 
-// cuFFT types and calls of one precision
-struct Fft64 {
-    using T = double;
-    using C = cufftDoubleComplex;
-    static constexpr cufftType R2C = CUFFT_D2Z, C2C = CUFFT_Z2Z, C2R = CUFFT_Z2D;
-    static cufftResult r2c(cufftHandle p, T *i, C *o) { return cufftExecD2Z(p, i, o); }
-    static cufftResult c2c(cufftHandle p, C *i, C *o, int dir) { return cufftExecZ2Z(p, i, o, dir); }
-    static cufftResult c2r(cufftHandle p, C *i, T *o) { return cufftExecZ2D(p, i, o); }
-};
-struct Fft32 {
-    using T = float;
-    using C = cufftComplex;
-    static constexpr cufftType R2C = CUFFT_R2C, C2C = CUFFT_C2C, C2R = CUFFT_C2R;
-    static cufftResult r2c(cufftHandle p, T *i, C *o) { return cufftExecR2C(p, i, o); }
-    static cufftResult c2c(cufftHandle p, C *i, C *o, int dir) { return cufftExecC2C(p, i, o, dir); }
-    static cufftResult c2r(cufftHandle p, C *i, T *o) { return cufftExecC2R(p, i, o); }
-};
-
-// 2-D (y, x) real transforms of `batch` consecutive [my][mx] planes
-template <typename F>
-amr_status plan_xy(cufftHandle *p, int mx, int my, int batch, bool forward) {
-    int n[2] = {my, mx}, re[2] = {my, mx}, ce[2] = {my, mx / 2 + 1};
-    const int rd = my * mx, cd = my * (mx / 2 + 1);
-    return forward ? cufft_fail(cufftPlanMany(p, 2, n, re, 1, rd, ce, 1, cd, F::R2C, batch), "plan xy")
-                   : cufft_fail(cufftPlanMany(p, 2, n, ce, 1, cd, re, 1, rd, F::C2R, batch), "plan xy");
-}
-
-// Isolated root potential with the transforms pruned to where the data is:
-// the density fills planes z < nz of the padded grid, so the forward (y, x)
-// transforms run on those planes only (the others are zero), then every
-// (ky, kx) column is transformed along z; after the product with the
-// kernel's transform, the inverse z pass runs on every column and the
-// inverse (y, x) transforms only on the planes the outputs read (z < nz + 2
-// and the two planes below z = 0).  Same arithmetic as the full 3-D
-// transform, about 0.6 of its work.
-template <typename F>
+// Isolated root potential: the kernel's transform once per context (a full
+// forward transform of k_iso_kernel's grid), then per solve the density
+// scattered into planes z < nz of the zeroed padded grid and the pruned
+// convolution of fft_convolve_isolated (fft.cu): the forward (y, x)
+// transforms on those planes only, every (ky, kx) column along z with the
+// product by the kernel's transform between its forward and inverse
+// transforms, the inverse (y, x) transforms only on the planes the outputs
+// read (z < nz + 2 and the two planes below z = 0).  Same arithmetic as the
+// full 3-D transform, about 0.6 of its work.
+template <typename T>
 amr_status root_isolated(amr_hydro_ctx *c, Level &L, int nx, int ny, int nz, int mx, int my, int mz, double G,
                          double *phi, double *acc, int acc_order) {
-    using T = typename F::T;
-    using C = typename F::C;
+    (void)nx;
+    (void)ny;
     amr_status st;
-    const int mxh = mx / 2 + 1, grid = c->n_sm * 8;
-    const int64_t n = (int64_t)mx * my * mz, nc = (int64_t)mz * my * mxh, plane_c = (int64_t)my * mxh;
+    const int grid = c->n_sm * 8;
+    const int64_t n = (int64_t)mx * my * mz;
     cudaStream_t s = c->stream;
-    if (!c->fft_plan[0]) {
-        cufftHandle h[4] = {0, 0, 0, 0};
-        int nzz[1] = {mz};
-        const int col = my * mxh;
-        if ((st = plan_xy<F>(&h[0], mx, my, nz, true)) ||
-            (st = cufft_fail(cufftPlanMany(&h[1], 1, nzz, nzz, col, 1, nzz, col, 1, F::C2C, col), "plan z")) ||
-            (st = plan_xy<F>(&h[2], mx, my, nz + 2, false)) || (st = plan_xy<F>(&h[3], mx, my, 2, false))) {
-            for (cufftHandle x : h)
-                if (x) cufftDestroy(x);
-            return st;
-        }
-        for (int k = 0; k < 4; k++) c->fft_plan[k] = (long long)h[k];
-        c->fft_m[0] = mx;
-        c->fft_m[1] = my;
-        c->fft_m[2] = mz;
-    }
-    cufftHandle h[4];
-    for (int k = 0; k < 4; k++) {
-        h[k] = (cufftHandle)c->fft_plan[k];
-        if ((st = cufft_fail(cufftSetStream(h[k], s), "stream"))) return st;
-    }
     T *R = reinterpret_cast<T *>(c->fft_real.p);
-    C *Fk = reinterpret_cast<C *>(c->fft_cplx.p), *Gk = reinterpret_cast<C *>(c->fft_green.p);
     const double dh = level_dh(c, 0);
-    if (!c->fft_green_ready) {  // the kernel fills every plane: a full (y, x) pass, then z
-        cufftHandle all = 0;
-        if ((st = plan_xy<F>(&all, mx, my, mz, true))) return st;
-        if ((st = cufft_fail(cufftSetStream(all, s), "stream"))) {
-            cufftDestroy(all);
-            return st;
-        }
+    if (!c->fft_green_ready) {
         k_iso_kernel<T><<<grid, 256, 0, s>>>(R, mx, my, mz, dh);
-        st = cuda_fail(cudaGetLastError(), "k_iso_kernel");
-        if (!st) st = cufft_fail(F::r2c(all, R, Gk), "kernel xy");
-        if (!st) st = cufft_fail(F::c2c(h[1], Gk, Gk, CUFFT_FORWARD), "kernel z");
-        if (!st) st = cuda_fail(cudaStreamSynchronize(s), "kernel transform");  // before the plan goes
-        cufftDestroy(all);
-        if (st) return st;
+        if ((st = cuda_fail(cudaGetLastError(), "k_iso_kernel"))) return st;
+        if ((st = fft_forward_full<T>(c, R, mx, my, mz, c->fft_green.p, s))) return st;
         c->fft_green_ready = true;
     }
-    if ((st = cuda_fail(cudaMemsetAsync(R, 0, sizeof(T) * (int64_t)nz * my * mx, s), "memset padded")) ||
-        (st = cuda_fail(cudaMemsetAsync(Fk + nz * plane_c, 0, sizeof(C) * (mz - nz) * plane_c, s), "memset spectrum")))
-        return st;
+    if ((st = cuda_fail(cudaMemsetAsync(R, 0, sizeof(T) * (int64_t)nz * my * mx, s), "memset padded"))) return st;
     k_rho_scatter<T><<<grid, 256, 0, s>>>(L.U[L.cur], L.d_corner, L.n_patches, mx, my, R);
     if ((st = cuda_fail(cudaGetLastError(), "k_rho_scatter"))) return st;
-    if ((st = cufft_fail(F::r2c(h[0], R, Fk), "forward xy")) ||
-        (st = cufft_fail(F::c2c(h[1], Fk, Fk, CUFFT_FORWARD), "forward z")))
-        return st;
-    k_iso_mul<C><<<grid, 256, 0, s>>>(Fk, Gk, nc, G / (double)n);
-    if ((st = cuda_fail(cudaGetLastError(), "k_iso_mul"))) return st;
-    if ((st = cufft_fail(F::c2c(h[1], Fk, Fk, CUFFT_INVERSE), "inverse z")) ||
-        (st = cufft_fail(F::c2r(h[2], Fk, R), "inverse xy")) ||
-        (st = cufft_fail(F::c2r(h[3], Fk + (mz - 2) * plane_c, R + (int64_t)(mz - 2) * my * mx), "inverse xy")))
+    if ((st = fft_convolve_isolated<T>(c, R, mx, my, mz, nz, c->fft_green.p, G / (double)n, c->fft_cplx.p, s)))
         return st;
     k_root_out<T><<<grid, 256, 0, s>>>(R, L.d_corner, L.n_patches, mx, my, mz, dh, acc_order, phi, acc);
     return cuda_fail(cudaGetLastError(), "k_root_out");
 }
 
 void release_poisson(amr_hydro_ctx *c) {
-    for (long long &h : c->fft_plan) {
-        if (h) cufftDestroy((cufftHandle)h);
-        h = 0;
-    }
     c->fft_real.release();
     c->fft_cplx.release();
     c->fft_green.release();
@@ -643,8 +555,8 @@ amr_status amr_hydro_poisson_root(amr_hydro_ctx *c, double G, double *phi, doubl
         (iso && (st = c->fft_green.reserve(2 * nc))))
         return st;
     if (iso)
-        return f32 ? root_isolated<Fft32>(c, L, nx, ny, nz, mx, my, mz, G, phi, acc, acc_order)
-                   : root_isolated<Fft64>(c, L, nx, ny, nz, mx, my, mz, G, phi, acc, acc_order);
+        return f32 ? root_isolated<float>(c, L, nx, ny, nz, mx, my, mz, G, phi, acc, acc_order)
+                   : root_isolated<double>(c, L, nx, ny, nz, mx, my, mz, G, phi, acc, acc_order);
     cudaStream_t s = c->stream;
     const double dh = level_dh(c, 0);
     double *lam1 = c->fft_cplx.p + 2 * nc, *partial = lam1 + nx / 2 + 1 + ny + nz;
@@ -659,13 +571,13 @@ amr_status amr_hydro_poisson_root(amr_hydro_ctx *c, double G, double *phi, doubl
         float *R = reinterpret_cast<float *>(c->fft_real.p);
         k_rho_dense<float><<<grid, 256, 0, s>>>(L.U[L.cur], L.d_corner, L.n_patches, nx, ny, partial, grid, R);
         if ((st = cuda_fail(cudaGetLastError(), "k_rho_dense"))) return st;
-        if ((st = fft_poisson_periodic<float>(c, R, nx, ny, nz, lam1, scale, c->fft_cplx.p, nullptr, s))) return st;
+        if ((st = fft_poisson_periodic<float>(c, R, nx, ny, nz, lam1, scale, c->fft_cplx.p, s))) return st;
         k_root_out<float><<<grid, 256, 0, s>>>(R, L.d_corner, L.n_patches, nx, ny, nz, dh, acc_order, phi, acc);
     } else {
         double *R = c->fft_real.p;
         k_rho_dense<double><<<grid, 256, 0, s>>>(L.U[L.cur], L.d_corner, L.n_patches, nx, ny, partial, grid, R);
         if ((st = cuda_fail(cudaGetLastError(), "k_rho_dense"))) return st;
-        if ((st = fft_poisson_periodic<double>(c, R, nx, ny, nz, lam1, scale, c->fft_cplx.p, nullptr, s))) return st;
+        if ((st = fft_poisson_periodic<double>(c, R, nx, ny, nz, lam1, scale, c->fft_cplx.p, s))) return st;
         k_root_out<double><<<grid, 256, 0, s>>>(R, L.d_corner, L.n_patches, nx, ny, nz, dh, acc_order, phi, acc);
     }
     return cuda_fail(cudaGetLastError(), "k_root_out");
