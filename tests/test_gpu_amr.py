@@ -20,6 +20,9 @@ def gpu_level_blocks(H, l):
 
 
 def compare(H, O, tol):
+    """Asserts the parity of every level; returns the per-level relative L1
+    errors (level, 5 variables)."""
+    errs = []
     for l in range(H.lmax + 1):
         cg, U = gpu_level_blocks(H, l)
         co = O.patch_corners(l)
@@ -37,6 +40,8 @@ def compare(H, O, tol):
         err = num / np.where(den > 0, den, den[0])
         assert (err <= tol).all(), (l, err)
         assert abs(H.time(l) - O.lv[l].t) <= max(1e-15, tol) * O.lv[l].t, (l, H.time(l), O.lv[l].t)
+        errs.append((l, err.tolist()))
+    return errs
 
 
 def make(U0, prec, lmax=2, theta=0.05, nbuf=(8, 4), max_patches=6000):
