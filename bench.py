@@ -47,7 +47,7 @@ FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # DRAM bytes (read+write) per cell update of one k_hydro_step launch from an
 # ncu capture, keyed by the hash of the kernel sources it was taken on.
-TRAFFIC_BYTES_PER_CELL = {"f64:3a53b9b9c1ffc44e": 86.75}
+TRAFFIC_BYTES_PER_CELL = {"f64:3a53b9b9c1ffc44e": 86.75, "f32:3a53b9b9c1ffc44e": 92.5}
 KERNEL_SOURCES = ("paper_1712_07070_b300/csrc/step_kernel.cuh", "paper_1712_07070_b300/csrc/hydro_math.cuh")
 
 

@@ -1,6 +1,6 @@
 """GPU parity of the CTU scheme (section 2.2; six Riemann solves per cell,
 time step of Eq. CFL1) against the oracle's CTU branch: uniform periodic
-steps in FP64 (relative L1 <= 1e-12) and the FP32 mode (5e-5) for several
+steps in FP64 (relative L1 <= 1e-12) and the FP32 mode (1e-5; one case 2e-5) for several
 limiter / solver pairs, a level with z-runs, the AMR W-cycle with fix-up and
 regrid, the batched boxes, the host-buffer step (bitwise against the device
 path), and sampled cells of a 512^3 step."""
@@ -20,10 +20,13 @@ G53 = 5.0 / 3.0
 # FP32 (relative rounding up to ~1e-6 per flux after tens of operations).
 # The error of a variable scales with the pressure part of its fluxes,
 # (dt/dh) * 6 faces * P * 1e-6 per step, so on the small transverse momenta
-# of the Sod-noise state (|rho v| ~ 1% of P) four steps allow up to ~5e-4;
-# measured 1.6e-5 (MUSCL-Hancock, with half the solves, stays below 1e-5).
-# Bound 5e-5.
-TOL = {A.AMR_FP64: 1e-12, A.AMR_FP32_ACC64: 5e-5}
+# of the Sod-noise state (|rho v| ~ 1% of P) four steps allow up to ~5e-4.
+# Measured (relative L1, max over the variables): 5.2e-6 ... 7.4e-6 on the
+# Sod-noise cases except van Albada + HLLE, 1.61e-5 (the transverse
+# momenta); 5.6e-8 turbulence, 5.7e-7 AMR, 1.2e-6 ... 2.9e-6 boxes.  Bound
+# 1e-5, and 2e-5 for that one case.
+TOL = {A.AMR_FP64: 1e-12, A.AMR_FP32_ACC64: 1e-5}
+TOL_CASE = {(A.AMR_LIM_ALBADA, A.AMR_RS_HLLE, A.AMR_FP32_ACC64): 2e-5}
 NAME = {A.AMR_FP64: "f64", A.AMR_FP32_ACC64: "fp32_acc64"}
 
 
@@ -72,7 +75,7 @@ def test_uniform_parity(prec, lim, rs, theta):
     assert abs(dts[0] - odt) <= (1e-14 if prec == A.AMR_FP64 else 1e-6) * odt  # Eq. CFL1
     err = rel_l1(out, ref)
     report(case=f"Sod noise 32x16x48, 4 steps, limiter {lim}, solver {rs}", prec=NAME[prec], rel_l1=list(map(float, err)))
-    assert (err <= TOL[prec]).all(), err
+    assert (err <= TOL_CASE.get((lim, rs, prec), TOL[prec])).all(), err
 
 
 @pytest.mark.parametrize("prec", PRECS)
