@@ -110,12 +110,16 @@ class Level:
 
 class OracleHierarchy:
     def __init__(self, U_root, lmax, gamma, cfl, theta, nbuf, c_inc=0.1, c_dec=0.1, box=1.0,
-                 regrid_at_start=True, S_root=None, dual_xi=1e-2):
+                 regrid_at_start=True, S_root=None, dual_xi=1e-2, shared_dt=False):
         _, nz, ny, nx = U_root.shape
         self.root_n = (nx, ny, nz)
         self.lmax, self.gamma, self.cfl_c, self.theta = lmax, gamma, cfl, theta
         self.nbuf = list(nbuf)
         self.c_inc, self.c_dec, self.box = c_inc, c_dec, box
+        # shared time-step integration (section 2.6): one dt for every level,
+        # the minimum of the levels' constraints
+        self.shared_dt = shared_dt
+        self._shared_step = None
         self.dual = S_root is not None
         self.dual_xi = dual_xi
         self.lv = [Level([n << l for n in self.root_n], self.dual) for l in range(lmax + 1)]
@@ -234,8 +238,16 @@ class OracleHierarchy:
     def advance(self, l, dt0=None):
         L = self.lv[l]
         if l == 0:
-            dt = self.min_dt(0) if dt0 is None else dt0
-            dt = self._dec_rule(l, dt)
+            if self.shared_dt:
+                # the time-step constraint evaluated on all levels, the minimum taken
+                if dt0 is None:
+                    dt = min(self.min_dt(k) for k in range(self.lmax + 1) if not self.lv[k].empty)
+                else:
+                    dt = dt0
+                self._shared_step = dt
+            else:
+                dt = self.min_dt(0) if dt0 is None else dt0
+                dt = self._dec_rule(l, dt)
             target = L.t + dt
         else:
             target = self.lv[l - 1].t
@@ -244,11 +256,12 @@ class OracleHierarchy:
             if l == 0:
                 step = dt  # the root level takes one step of exactly dt per call
             else:
-                step = self.min_dt(l)
+                # shared: the root's dt, which lands on the parent's time in one step
+                step = self._shared_step if self.shared_dt else self.min_dt(l)
                 if (1.0 + self.c_inc) * step > target - L.t:
                     step = target - L.t
                     last = True
-                else:
+                elif not self.shared_dt:
                     step = self._dec_rule(l, step)
             self.advance_level(l, step)
             L.t = target if (last or l == 0) else L.t + step

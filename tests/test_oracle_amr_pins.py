@@ -282,12 +282,12 @@ def test_refinement_criterion_sums_squares_over_dimensions():
 
 # ---- adaptive time-step W-cycle (section 2.1 pseudo-code: C_inc and C_dec rules) ----
 
-def _scripted_hierarchy(lmax, dts):
+def _scripted_hierarchy(lmax, dts, shared_dt=False):
     """A hierarchy whose per-level CFL step comes from the scripted lists dts[l]
     (the last entry repeats) and whose level updates, fix-ups and regrids are
     only recorded: what is left is the W-cycle's control flow."""
     H = OA.OracleHierarchy(ics.uniform_state(16), lmax=lmax, gamma=G53, cfl=0.5, theta=0.05,
-                           nbuf=[1] * lmax, regrid_at_start=False)
+                           nbuf=[1] * lmax, regrid_at_start=False, shared_dt=shared_dt)
     for l in range(1, lmax + 1):
         H.lv[l].mask[0:2, 0:2, 0:2] = 1
     log, calls = [], [0] * (lmax + 1)
@@ -347,3 +347,57 @@ def test_wcycle_c_inc_takes_priority_over_c_dec():
                    ("fix", 1), ("regrid", 1),
                    ("fix", 0), ("regrid", 0)]
     assert H.lv[0].t == H.lv[1].t == H.lv[2].t == 17 / 16
+
+
+# ---- shared time-step integration (section 2.6: the constraints of all levels, the minimum) ----
+
+def test_shared_dt_takes_the_minimum_over_levels_one_step_each():
+    # CFL steps: root 1 then 1/4; level 1 1/2; level 2 3/8 then 5/8.
+    # Root step 1: min(1, 1/2, 3/8) = 3/8 on every level, one step each (the
+    #   level's own step 1/2 or 5/8 is never taken).  Root step 2: the
+    #   constraints are evaluated again on all levels: min(1/4, 1/2, 5/8) = 1/4.
+    # No C_dec rule: in the adaptive cycle root step 2's 1/4 < 2*(3/8) keeps
+    # its value anyway, and step 1 checks the rule's absence below.
+    H, log = _scripted_hierarchy(2, [[1.0, 1 / 4], [1 / 2], [3 / 8, 5 / 8]], shared_dt=True)
+    for _ in range(2):
+        H.advance(0)
+    assert log == [("step", 0, 3 / 8), ("step", 1, 3 / 8), ("step", 2, 3 / 8), ("fix", 1), ("regrid", 1),
+                   ("fix", 0), ("regrid", 0),
+                   ("step", 0, 1 / 4), ("step", 1, 1 / 4), ("step", 2, 1 / 4), ("fix", 1), ("regrid", 1),
+                   ("fix", 0), ("regrid", 0)]
+    assert H.lv[0].t == H.lv[1].t == H.lv[2].t == 3 / 8 + 1 / 4
+
+
+def test_shared_dt_applies_no_c_dec_shrink():
+    # root CFL 17/16 with level 1's previous step 33/64: the adaptive cycle
+    # shrinks the root step to 2*(33/64) = 33/32 (C_dec; see the hand
+    # sequence above), the shared one keeps the minimum over levels, 17/16
+    # when level 1's own constraint (9/8) is larger
+    for shared, want in ((False, 33 / 32), (True, 17 / 16)):
+        H, log = _scripted_hierarchy(1, [[17 / 16], [9 / 8]], shared_dt=shared)
+        H.lv[1].dt_prev = 33 / 64
+        H.advance(0)
+        steps = [(e[1], e[2]) for e in log if e[0] == "step"]
+        assert steps[0] == (0, want), (shared, steps)
+        if shared:
+            assert steps == [(0, 17 / 16), (1, 17 / 16)]
+
+
+def test_shared_dt_hierarchy_keeps_levels_in_step_and_conserves():
+    U0 = ics.blobs(32, seed=5, contrast=10.0, mach=1.0)
+    H = OA.OracleHierarchy(U0, lmax=2, gamma=G53, cfl=0.5, theta=0.3, nbuf=[1, 1], shared_dt=True)
+    assert not H.lv[2].empty
+
+    def mass():
+        return sum(H.lv[l].U[0][H.leaf(l)].sum() * H.dh(l) ** 3 for l in range(3) if not H.lv[l].empty)
+
+    m0 = mass()
+    for _ in range(2):
+        own = [H.min_dt(l) for l in range(3) if not H.lv[l].empty]
+        n0 = len(H.log)
+        H.advance(0)
+        steps = H.log[n0:]
+        assert [l for l, _ in steps] == [0, 1, 2]
+        assert steps[0][1] == min(own) and min(own) < max(own)
+        assert H.lv[0].t == H.lv[1].t == H.lv[2].t
+    assert abs(mass() - m0) <= 1e-14 * m0
