@@ -206,9 +206,13 @@ amr_status amr_hydro_bind_level(amr_hydro_ctx *ctx, int level, double *U_a, doub
  * criterion).  Kept children keep their data; new children are interpolated
  * from the parent level (conservative minmod-limited linear interpolation of
  * the conserved variables, with all eight children of a coarse cell falling
- * back to the coarse value when any would have rho<=0 or P<=0).  Groups are
- * numbered in the order of their parents' corners (z, then y, then x).
- * Synchronises.  AMR_E_NOMEM if the new level exceeds max_patches.
+ * back to the coarse value when any would have rho<=0 or P<=0).  Existing
+ * groups keep their numbers (and their slots' data stays in place) where
+ * the new group count allows; the others take the free numbers in
+ * increasing order, moved groups (by number) before new ones (by their
+ * parents' corners, z, then y, then x), so the numbering depends only on the
+ * old and new refined sets.  Synchronises.  AMR_E_NOMEM if the new level
+ * exceeds max_patches.
  */
 amr_status amr_hydro_regrid(amr_hydro_ctx *ctx, int level);
 
@@ -220,9 +224,18 @@ amr_status amr_hydro_regrid(amr_hydro_ctx *ctx, int level);
  * level l its child level catches up, then flux fix-up + restriction and the
  * regrid of level l+1.  dt0 > 0 fixes the root step, else Eq. (CFL2).
  * cell_updates (may be NULL) receives the number of cell updates of all
- * levels.  Synchronises the host once per level step (for its dt).
+ * levels.  Synchronises the host once per level step (for its dt).  With
+ * the shared time step on (amr_hydro_set_shared_dt) every level takes one
+ * step per root step of the root step's dt: the minimum of Eq. (CFL2) over
+ * all levels (section 2.6), no C_dec shrink.
  */
 amr_status amr_hydro_advance_root(amr_hydro_ctx *ctx, double dt0, int64_t *cell_updates);
+
+/*
+ * Shared (on != 0) or adaptive (0, the default) time-step integration of
+ * amr_hydro_advance_root (section 2.6).  AMR_E_INVAL for a NULL context.
+ */
+amr_status amr_hydro_set_shared_dt(amr_hydro_ctx *ctx, int on);
 
 /* Patch and coarse-fine ghost-patch counts of a level. */
 amr_status amr_hydro_level_info(amr_hydro_ctx *ctx, int level, int *n_patches, int *n_ghost);

@@ -13,7 +13,7 @@ from . import amr_hydro as A
 class AmrHierarchy:
     def __init__(self, U_root, lmax, gamma=5.0 / 3.0, cfl=0.5, theta=0.05, nbuf=(8, 4), prec=A.AMR_FP64,
                  max_patches=None, c_inc=0.1, c_dec=0.1, stream=None, device="cuda", regrid_at_start=True, scheme=None,
-                 S_root=None):
+                 S_root=None, shared_dt=False):
         _, nz, ny, nx = U_root.shape
         self.root = (nx, ny, nz)
         self.lmax = lmax
@@ -26,6 +26,8 @@ class AmrHierarchy:
                           max_patches=max(max_patches, n0), theta=theta, c_inc=c_inc, c_dec=c_dec,
                           nbuf=list(nbuf))
         self.ctx = A.amr_hydro_init(p, stream)
+        if shared_dt:
+            A.amr_hydro_set_shared_dt(self.ctx, True)
         dev = self.device
         corner, sib, parent, child = A.amr_hydro_uniform_tables((nx // 8, ny // 8, nz // 8))
         self.tables = [[torch.from_numpy(a).to(dev) for a in (corner, sib, parent, child)]]

@@ -33,7 +33,7 @@ SYMBOLS = (
     "amr_hydro_regrid", "amr_hydro_advance_root", "amr_hydro_level_info", "amr_hydro_box_tuning",
     "amr_hydro_advance_host", "amr_hydro_set_entropy", "amr_hydro_poisson_root", "amr_hydro_poisson_level",
     "amr_hydro_advance_gravity", "amr_hydro_poisson_level_t", "amr_hydro_phase_timing", "amr_hydro_phase_times",
-    "amr_hydro_set_box_entropy", "amr_hydro_set_gravity", "amr_hydro_level_gravity",
+    "amr_hydro_set_box_entropy", "amr_hydro_set_gravity", "amr_hydro_level_gravity", "amr_hydro_set_shared_dt",
 )
 AMR_PH_GHOST, AMR_PH_STEP, AMR_PH_FIXUP, AMR_PH_REGRID, AMR_PH_DT = range(5)
 AMR_N_PHASES = 5
@@ -96,6 +96,7 @@ def lib():
         "amr_hydro_set_box_entropy": [_vp, ctypes.c_int, _vp, _vp],
         "amr_hydro_set_gravity": [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int],
         "amr_hydro_level_gravity": [_vp, ctypes.c_int, _vp, _vp],
+        "amr_hydro_set_shared_dt": [_vp, ctypes.c_int],
         "amr_hydro_advance_boxes": [_vp, ctypes.c_int, _ip, ctypes.c_int, _vp],
         "amr_hydro_box_state": [_vp, ctypes.c_int, _ip],
         "amr_hydro_step_adjoint": [_vp, ctypes.c_int, ctypes.c_double, _vp, _vp, _vp],
@@ -367,6 +368,10 @@ def amr_hydro_phase_times(ctx):
 
 def amr_hydro_set_box_entropy(ctx, box_id, S_a, S_b):
     check(lib().amr_hydro_set_box_entropy(ctx, box_id, _p(S_a), _p(S_b)), "amr_hydro_set_box_entropy")
+
+
+def amr_hydro_set_shared_dt(ctx, on):
+    check(lib().amr_hydro_set_shared_dt(ctx, 1 if on else 0), "amr_hydro_set_shared_dt")
 
 
 def amr_hydro_set_gravity(ctx, G, omega=1.7, iters=60, acc_order=2):

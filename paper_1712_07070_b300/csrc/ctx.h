@@ -227,6 +227,8 @@ struct amr_hydro_ctx {
     amrh::DevBuf<int64_t> fb_list;
     amrh::DevBuf<unsigned long long> fb_count;
     // self-gravity in the W-cycle (amr_hydro_set_gravity)
+    bool shared_dt = false;  // shared time-step integration of the W-cycle
+    double shared_step = 0.0;
     bool grav_on = false;
     double grav_G = 0.0, grav_omega = 1.7;
     int grav_iters = 60, grav_order = 2;

@@ -233,8 +233,21 @@ amr_status advance_rec(amr_hydro_ctx *c, int l, double dt0, int64_t *updates) {
     double target, dt = 0.0;
     if (l == 0) {
         dt = dt0;
-        if (!(dt > 0.0) && (st = min_dt_host(c, 0, &dt))) return st;
-        dt = dec_rule(c, 0, dt);
+        if (c->shared_dt) {  // the constraint of every level, the minimum
+            if (!(dt > 0.0)) {
+                if ((st = min_dt_host(c, 0, &dt))) return st;
+                for (int k = 1; k <= c->prm.lmax; k++) {
+                    if (!c->lv[k].n_patches) continue;
+                    double dk;
+                    if ((st = min_dt_host(c, k, &dk))) return st;
+                    dt = dk < dt ? dk : dt;
+                }
+            }
+            c->shared_step = dt;
+        } else {
+            if (!(dt > 0.0) && (st = min_dt_host(c, 0, &dt))) return st;
+            dt = dec_rule(c, 0, dt);
+        }
         target = L.t + dt;
     } else {
         target = c->lv[l - 1].t;
@@ -245,11 +258,13 @@ amr_status advance_rec(amr_hydro_ctx *c, int l, double dt0, int64_t *updates) {
         if (l == 0) {
             step = dt;
         } else {
-            if ((st = min_dt_host(c, l, &step))) return st;
+            // shared: the root step's dt, which lands on the parent's time
+            if (c->shared_dt) step = c->shared_step;
+            else if ((st = min_dt_host(c, l, &step))) return st;
             if ((1.0 + c->prm.c_inc) * step > target - L.t) {
                 step = target - L.t;
                 last = true;
-            } else {
+            } else if (!c->shared_dt) {
                 step = dec_rule(c, l, step);
             }
         }
@@ -282,6 +297,12 @@ amr_status advance_rec(amr_hydro_ctx *c, int l, double dt0, int64_t *updates) {
 }
 
 }  // namespace
+
+extern "C" amr_status amr_hydro_set_shared_dt(amr_hydro_ctx *c, int on) {
+    if (!c) return AMR_E_INVAL;
+    c->shared_dt = on != 0;
+    return AMR_OK;
+}
 
 extern "C" amr_status amr_hydro_advance_root(amr_hydro_ctx *c, double dt0, int64_t *cell_updates) {
     if (!c || !c->lv[0].n_patches) return AMR_E_INVAL;

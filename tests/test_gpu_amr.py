@@ -167,3 +167,26 @@ def test_refined_levels_march_z_runs():
             H.advance_root()
         assert used > 0  # some refined level marched runs of more than one group
         H.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(A.AMR_FP64, 1e-12), (A.AMR_FP32_ACC64, 1e-5)])
+def test_shared_time_step_matches_oracle(prec, tol):
+    """Shared time-step integration (section 2.6): every level one step per
+    root step of the minimum of the levels' Eq. (CFL2) steps; the hierarchy
+    and the level times against the oracle's shared cycle, and conservation."""
+    from paper_1712_07070_b300.amr import AmrHierarchy
+    U0 = ics.blobs(32, seed=5, contrast=10.0, mach=1.0)
+    H = AmrHierarchy(U0, lmax=2, theta=0.3, nbuf=(1, 1), prec=prec, max_patches=6000, shared_dt=True)
+    O = OracleHierarchy(U0, lmax=2, gamma=G53, cfl=0.5, theta=0.3, nbuf=[1, 1], shared_dt=True)
+    assert H.n_patches(2) > 0
+    s0 = H.conserved_total()
+    for _ in range(2):
+        n = H.advance_root()
+        O.advance(0)
+        assert n > 0
+        assert H.time(0) == H.time(1) == H.time(2)
+    compare(H, O, tol)
+    if prec == A.AMR_FP64:
+        scale = np.abs(U0).reshape(5, -1).sum(1) / 32 ** 3
+        assert (np.abs(H.conserved_total() - s0) <= 1e-13 * scale).all()
+    H.close()
