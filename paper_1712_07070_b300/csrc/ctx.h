@@ -54,6 +54,7 @@ struct Level {
     DevBuf<int32_t> nbr;        // [n_groups][64]
     DevBuf<int32_t> runs, run_off;  // z-runs of groups (step work items), see build_runs
     int n_runs = 0;
+    DevBuf<int32_t> chain_up, chain_len;  // the device plan's z-chains (upper neighbour, head lengths)
     // the groups in (z, y, x) order of their positions (single-group work
     // items of a device-regridded level, whose slots stay in place)
     DevBuf<int32_t> work;
@@ -114,6 +115,8 @@ struct Level {
         runs.release();
         run_off.release();
         n_runs = 0;
+        chain_up.release();
+        chain_len.release();
         work.release();
         has_work = false;
         ghost.release();
@@ -179,14 +182,14 @@ struct RegridScratch {
     DevBuf<int32_t> cnt, bsum, keep, mark, rank, gnew, gpar;
     DevBuf<int32_t> corner, sib, parent, child, old_of, info, new_of;
     DevBuf<int32_t> cf_a, cf_b, cf_c, cf_d, cf_e, cf_f, cf_g, cf_h;
-    DevBuf<int32_t> run_up, run_down, run_len, run_cnt, run_lpos, run_rpos, run_hist;  // z-chains of a plan
+    DevBuf<int32_t> run_down, run_cnt, run_lpos, run_rpos, run_hist;  // z-runs of a plan
     DevBuf<int32_t> taken, frank, flist, mflag, mrank, nflag;  // group numbering with slots kept in place
     int32_t *hcnt = nullptr;  // pinned, 32 entries
     double *htime = nullptr;  // pinned, 8 entries: a time record (0..2), min_dt's reads (4, 5)
     void release() {
         for (DevBuf<int32_t> *b : {&cnt, &bsum, &keep, &mark, &rank, &gnew, &gpar, &corner, &sib, &parent, &child,
                                    &old_of, &info, &new_of, &cf_a, &cf_b, &cf_c, &cf_d, &cf_e, &cf_f, &cf_g, &cf_h,
-                                   &run_up, &run_down, &run_len, &run_cnt, &run_lpos, &run_rpos, &run_hist, &taken, &frank,
+                                   &run_down, &run_cnt, &run_lpos, &run_rpos, &run_hist, &taken, &frank,
                                    &flist, &mflag, &mrank, &nflag})
             b->release();
         if (hcnt) cudaFreeHost(hcnt);

@@ -552,7 +552,8 @@ __global__ void k_run_heads(int ng, const int32_t *__restrict__ up, const int32_
 
 // The run length in 1..32 minimising the round-robin estimate
 // ceil(n_runs / grid) (min(len, longest) + e), from the length histogram
-// (one block; the first minimum, as on the host); out[0] = length.
+// (one block; the first minimum, as on the host); out[0] = the number of
+// runs of that length, out[1] = the length.
 constexpr int RUN_NT = 256, RUN_MAXLEN = 32;
 __global__ void __launch_bounds__(RUN_NT) k_run_len(const int32_t *__restrict__ hist, int hmax, int grid, double e,
                                                     int32_t *__restrict__ out) {
@@ -584,7 +585,8 @@ __global__ void __launch_bounds__(RUN_NT) k_run_len(const int32_t *__restrict__ 
                 best = cost[k];
                 best_len = k + 1;
             }
-        out[0] = best_len;
+        out[0] = (int32_t)cnt[best_len - 1];
+        out[1] = best_len;
     }
 }
 
@@ -662,17 +664,18 @@ amr_status build_posmap(amr_hydro_ctx *c, int level) {
 // Neighbour plan of level X >= 1 on the device (the counterpart of
 // build_nbr_plan + plan_level on the host; its z-runs: plan_runs_dev).  Queues the
 // kernels; the ghost count lands in *n_ghost_dev.
-// z-runs of level X from its neighbour plan, into L.runs / L.run_off;
-// run_cnt[0] = the number of runs, run_cnt[1] = their length (the host uses
-// the runs when the length exceeds 1, as the host plan does).
+// z-runs of level X from its neighbour plan: the chains and the run length
+// (run_cnt[0] = the number of runs, run_cnt[1] = their length); the runs
+// themselves (L.runs / L.run_off, plan_runs_write) only when the length
+// exceeds 1, as the host plan does.
 static amr_status plan_runs_dev(amr_hydro_ctx *c, int X, int32_t *run_cnt) {
     Level &L = c->lv[X];
     auto &S = c->rg;
     const int ng = L.n_groups;
     amr_status st;
-    if ((st = S.run_up.reserve(ng + 1)) || (st = S.run_down.reserve(ng + 1)) || (st = S.run_len.reserve(ng + 1)) ||
-        (st = S.run_cnt.reserve(ng + 1)) || (st = S.run_lpos.reserve(ng + 1)) || (st = S.run_rpos.reserve(ng + 1)) ||
-        (st = L.runs.reserve(ng + 1)) || (st = L.run_off.reserve(ng + 2)))
+    // the chains stay with the level until plan_runs_write (another level's
+    // plan may run in between)
+    if ((st = L.chain_up.reserve(ng + 1)) || (st = S.run_down.reserve(ng + 1)) || (st = L.chain_len.reserve(ng + 1)))
         return st;
     // a chain holds at most the level's column of groups
     const int hmax = ((c->prm.root_n[2] << X) + 15) / 16;
@@ -681,16 +684,30 @@ static amr_status plan_runs_dev(amr_hydro_ctx *c, int X, int32_t *run_cnt) {
         (st = cuda_fail(cudaMemsetAsync(S.run_hist.p, 0, 4 * (size_t)(hmax + 1), c->stream), "memset")))
         return st;
     const int gb = grid_for(ng, 256, 8 * c->n_sm);
-    k_run_links<<<gb, 256, 0, c->stream>>>(ng, L.nbr.p, S.run_up.p, S.run_down.p);
-    k_run_heads<<<gb, 256, 0, c->stream>>>(ng, S.run_up.p, S.run_down.p, S.run_len.p, S.run_hist.p, hmax);
+    k_run_links<<<gb, 256, 0, c->stream>>>(ng, L.nbr.p, L.chain_up.p, S.run_down.p);
+    k_run_heads<<<gb, 256, 0, c->stream>>>(ng, L.chain_up.p, S.run_down.p, L.chain_len.p, S.run_hist.p, hmax);
     k_run_len<<<1, RUN_NT, 0, c->stream>>>(S.run_hist.p, hmax, c->n_sm * c->step_bps,
-                                           c->prm.prec == AMR_FP64 ? 0.05 : 0.13, run_cnt + 1);
-    k_run_count<<<gb, 256, 0, c->stream>>>(ng, S.run_len.p, run_cnt + 1, S.run_cnt.p);
-    if ((st = cuda_fail(cudaGetLastError(), "z-runs"))) return st;
-    if ((st = scan_i32(c, S.run_len.p, S.run_lpos.p, ng, run_cnt + 2, false)) ||
-        (st = scan_i32(c, S.run_cnt.p, S.run_rpos.p, ng, run_cnt, false)))
+                                           c->prm.prec == AMR_FP64 ? 0.05 : 0.13, run_cnt);
+    return cuda_fail(cudaGetLastError(), "z-runs");
+}
+
+// The runs of plan_runs_dev's chains and length (after the host read the
+// counts: queued only when the length exceeds 1).
+static amr_status plan_runs_write(amr_hydro_ctx *c, int X, int32_t *run_cnt) {
+    Level &L = c->lv[X];
+    auto &S = c->rg;
+    const int ng = L.n_groups;
+    amr_status st;
+    if ((st = S.run_cnt.reserve(ng + 1)) || (st = S.run_lpos.reserve(ng + 1)) || (st = S.run_rpos.reserve(ng + 1)) ||
+        (st = L.runs.reserve(ng + 1)) || (st = L.run_off.reserve(ng + 2)))
         return st;
-    k_run_write<<<gb, 256, 0, c->stream>>>(ng, S.run_up.p, S.run_len.p, S.run_lpos.p, S.run_rpos.p, run_cnt + 1,
+    const int gb = grid_for(ng, 256, 8 * c->n_sm);
+    k_run_count<<<gb, 256, 0, c->stream>>>(ng, L.chain_len.p, run_cnt + 1, S.run_cnt.p);
+    if ((st = cuda_fail(cudaGetLastError(), "k_run_count"))) return st;
+    if ((st = scan_i32(c, L.chain_len.p, S.run_lpos.p, ng, run_cnt + 2, 0)) ||
+        (st = scan_i32(c, S.run_cnt.p, S.run_rpos.p, ng, run_cnt, 0)))
+        return st;
+    k_run_write<<<gb, 256, 0, c->stream>>>(ng, L.chain_up.p, L.chain_len.p, S.run_lpos.p, S.run_rpos.p, run_cnt + 1,
                                            run_cnt, L.runs.p, L.run_off.p);
     return cuda_fail(cudaGetLastError(), "k_run_write");
 }
@@ -946,6 +963,7 @@ amr_status regrid_dev(amr_hydro_ctx *c, int l) {
     if (S.hcnt[0]) return AMR_E_NESTING;
     if (nn) {
         F.n_runs = S.hcnt[15] > 1 ? S.hcnt[14] : 0;
+        if (F.n_runs && (st = plan_runs_write(c, l + 1, cnt + 14))) return st;
         F.n_ghost = S.hcnt[4];
         if (F.n_ghost && (st = F.ghost.reserve((size_t)F.n_ghost * PSLOT))) return st;
         if (F.n_ghost && c->prm.scheme == AMR_SCHEME_VL && (st = F.ghost_ustar.reserve((size_t)F.n_ghost * PSLOT)))
@@ -955,6 +973,7 @@ amr_status regrid_dev(amr_hydro_ctx *c, int l) {
         F.ghost_valid = false;
         if (G2) {
             G2->n_runs = S.hcnt[18] > 1 ? S.hcnt[17] : 0;
+            if (G2->n_runs && (st = plan_runs_write(c, l + 2, cnt + 17))) return st;
             G2->n_ghost = S.hcnt[9];
             if (G2->n_ghost && (st = G2->ghost.reserve((size_t)G2->n_ghost * PSLOT))) return st;
             if (G2->n_ghost && c->prm.scheme == AMR_SCHEME_VL &&
