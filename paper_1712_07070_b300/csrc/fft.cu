@@ -403,10 +403,19 @@ struct FftPasses {
         twy = twx + nx;
         twz = twy + ny;
         nxh = nx / 2 + 1;
-        ppb = nx >= 1024 ? 1 : 1024 / nx;
-        auto col_w = [](int n) {
+        // lines per CTA: about 2048 points of work for 256 threads; column
+        // tiles of at least 64-byte row segments (coalescing); two buffers of
+        // at most 160 KB of shared memory
+        constexpr size_t SMAX = 160 * 1024;
+        ppb = 2048 / nx;
+        ppb = ppb < 1 ? 1 : (ppb > 16 ? 16 : ppb);
+        while (ppb > 1 && 2 * (size_t)ppb * nx * sizeof(Cx<T>) > SMAX) ppb--;
+        auto col_w = [SMAX](int n) {
+            const int wmin = sizeof(T) == sizeof(double) ? 4 : 8;
             int w = 2048 / n;
-            return w < 1 ? 1 : (w > 16 ? 16 : w);
+            w = w < wmin ? wmin : (w > 16 ? 16 : w);
+            while (w > 1 && 2 * (size_t)w * n * sizeof(Cx<T>) > SMAX) w--;
+            return w;
         };
         wy = col_w(ny);
         wz = col_w(nz);

@@ -178,6 +178,9 @@ __global__ void k_rho_scatter(const double *__restrict__ U, const int32_t *__res
 // the slots; the dense array is [mz][my][mx] and indices wrap modulo those
 // extents (the box itself when periodic; the padded grid, whose layers just
 // outside the box hold the potential there, when isolated)
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f2d_bits(x); }
+
 template <typename T>  // the transform's precision; differences in FP64
 __global__ void k_root_out(const T *__restrict__ phi, const int32_t *__restrict__ corner, int n_patches, int nx,
                            int ny, int nz, double dh, int order, double *__restrict__ phi_out,
@@ -190,8 +193,8 @@ __global__ void k_root_out(const T *__restrict__ phi, const int32_t *__restrict_
         const int x = corner[3 * s] + (c & 7), y = corner[3 * s + 1] + ((c >> 3) & 7),
                   z = corner[3 * s + 2] + (c >> 6);
         auto wrap = [](int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); };  // |offset| <= 2 < n
-        auto at = [&](int a, int b, int d) {
-            return (double)phi[((int64_t)wrap(d, nz) * ny + wrap(b, ny)) * nx + wrap(a, nx)];
+        auto at = [&](int a, int b, int d) {  // an FP32 value widened exactly on the integer units
+            return to_f64(phi[((int64_t)wrap(d, nz) * ny + wrap(b, ny)) * nx + wrap(a, nx)]);
         };
         phi_out[s * PV + c] = at(x, y, z);
         if (!acc_out) continue;
