@@ -48,22 +48,36 @@ struct CoarseView {
     }
 };
 
-// The coarse value in the compute type: FP64 as above; in the FP32-compute
-// mode both times' values are rounded to FP32 on the integer units and
-// interpolated in FP32 (wf: w rounded once).
+// The coarse value in the compute type at a precomputed offset i of
+// variable 0 (plus v PV for variable v): FP64 as CoarseView::at; in the
+// FP32-compute mode both times' values are rounded to FP32 on the integer
+// units and interpolated in FP32 (wf: w rounded once).
 template <typename real>
-__device__ __forceinline__ real coarse_at(const CoarseView &C, float wf, int v, int cx, int cy, int cz);
+__device__ __forceinline__ real coarse_val(const CoarseView &C, float wf, int64_t i);
 template <>
-__device__ __forceinline__ double coarse_at<double>(const CoarseView &C, float, int v, int cx, int cy, int cz) {
-    return C.at(v, cx, cy, cz);
+__device__ __forceinline__ double coarse_val<double>(const CoarseView &C, float, int64_t i) {
+    if (C.w == 0.0) return C.Uo[i];
+    if (C.w == 1.0) return C.Un[i];
+    return C.Uo[i] + C.w * (C.Un[i] - C.Uo[i]);
 }
 template <>
-__device__ __forceinline__ float coarse_at<float>(const CoarseView &C, float wf, int v, int cx, int cy, int cz) {
-    const int64_t i = C.index(v, cx, cy, cz);
+__device__ __forceinline__ float coarse_val<float>(const CoarseView &C, float wf, int64_t i) {
     if (C.w == 0.0) return d2f_bits(C.Uo[i]);
     if (C.w == 1.0) return d2f_bits(C.Un[i]);
     const float a = d2f_bits(C.Uo[i]);
     return a + wf * (d2f_bits(C.Un[i]) - a);
+}
+// Offsets (variable 0) of coarse cell c and its six face neighbours
+// (centre, x+, x-, y+, y-, z+, z-): within the cell's coarse patch by
+// stepping 1, 8 or 64, across a patch boundary through the 27-patch table.
+__device__ __forceinline__ void stencil_index(const CoarseView &C, int cx, int cy, int cz, int64_t ic[7]) {
+    ic[0] = C.index(0, cx, cy, cz);
+    ic[1] = (cx & 7) != 7 ? ic[0] + 1 : C.index(0, cx + 1, cy, cz);
+    ic[2] = (cx & 7) != 0 ? ic[0] - 1 : C.index(0, cx - 1, cy, cz);
+    ic[3] = (cy & 7) != 7 ? ic[0] + 8 : C.index(0, cx, cy + 1, cz);
+    ic[4] = (cy & 7) != 0 ? ic[0] - 8 : C.index(0, cx, cy - 1, cz);
+    ic[5] = (cz & 7) != 7 ? ic[0] + 64 : C.index(0, cx, cy, cz + 1);
+    ic[6] = (cz & 7) != 0 ? ic[0] - 64 : C.index(0, cx, cy, cz - 1);
 }
 __device__ __forceinline__ double to_double(double x) { return x; }
 __device__ __forceinline__ double to_double(float x) { return f2d_bits(x); }
@@ -123,15 +137,15 @@ __global__ void k_interp_patches(double *__restrict__ out, const int32_t *__rest
             // coarse cell relative to the parent's origin
             const int cx = (qx * 8 + fx) >> 1, cy = (qy * 8 + fy) >> 1, cz = (qz * 8 + fz) >> 1;
             real c[NV], sl[3][NV];
+            int64_t ic[7];
+            stencil_index(C, cx, cy, cz, ic);
 #pragma unroll
             for (int v = 0; v < NV; v++) {
-                c[v] = coarse_at<real>(C, wf, v, cx, cy, cz);
-                sl[0][v] = minmod(coarse_at<real>(C, wf, v, cx + 1, cy, cz) - c[v],
-                                  c[v] - coarse_at<real>(C, wf, v, cx - 1, cy, cz));
-                sl[1][v] = minmod(coarse_at<real>(C, wf, v, cx, cy + 1, cz) - c[v],
-                                  c[v] - coarse_at<real>(C, wf, v, cx, cy - 1, cz));
-                sl[2][v] = minmod(coarse_at<real>(C, wf, v, cx, cy, cz + 1) - c[v],
-                                  c[v] - coarse_at<real>(C, wf, v, cx, cy, cz - 1));
+                const int64_t vo = (int64_t)v * PV;
+                c[v] = coarse_val<real>(C, wf, ic[0] + vo);
+                sl[0][v] = minmod(coarse_val<real>(C, wf, ic[1] + vo) - c[v], c[v] - coarse_val<real>(C, wf, ic[2] + vo));
+                sl[1][v] = minmod(coarse_val<real>(C, wf, ic[3] + vo) - c[v], c[v] - coarse_val<real>(C, wf, ic[4] + vo));
+                sl[2][v] = minmod(coarse_val<real>(C, wf, ic[5] + vo) - c[v], c[v] - coarse_val<real>(C, wf, ic[6] + vo));
             }
             real u[8][NV];
             bool ok = true;
@@ -151,13 +165,12 @@ __global__ void k_interp_patches(double *__restrict__ out, const int32_t *__rest
                 for (int v = 0; v < NV; v++) o[v * PV + off] = to_double(ok ? u[k][v] : c[v]);
             }
             if (So) {
-                const real cs = coarse_at<real>(CS, wf, 0, cx, cy, cz);
-                const real s0 = minmod(coarse_at<real>(CS, wf, 0, cx + 1, cy, cz) - cs,
-                                       cs - coarse_at<real>(CS, wf, 0, cx - 1, cy, cz));
-                const real s1 = minmod(coarse_at<real>(CS, wf, 0, cx, cy + 1, cz) - cs,
-                                       cs - coarse_at<real>(CS, wf, 0, cx, cy - 1, cz));
-                const real s2 = minmod(coarse_at<real>(CS, wf, 0, cx, cy, cz + 1) - cs,
-                                       cs - coarse_at<real>(CS, wf, 0, cx, cy, cz - 1));
+                int64_t is[7];
+                stencil_index(CS, cx, cy, cz, is);
+                const real cs = coarse_val<real>(CS, wf, is[0]);
+                const real s0 = minmod(coarse_val<real>(CS, wf, is[1]) - cs, cs - coarse_val<real>(CS, wf, is[2]));
+                const real s1 = minmod(coarse_val<real>(CS, wf, is[3]) - cs, cs - coarse_val<real>(CS, wf, is[4]));
+                const real s2 = minmod(coarse_val<real>(CS, wf, is[5]) - cs, cs - coarse_val<real>(CS, wf, is[6]));
 #pragma unroll
                 for (int k = 0; k < 8; k++) {
                     const real sx = (k & 1) ? real(0.25) : real(-0.25), sy = (k & 2) ? real(0.25) : real(-0.25),
@@ -205,12 +218,15 @@ __global__ void k_interp_vec3(double *__restrict__ out, const int32_t *__restric
             const int fx = lo[0] + 2 * (i % n[0]), fy = lo[1] + 2 * ((i / n[0]) % n[1]),
                       fz = lo[2] + 2 * (i / (n[0] * n[1]));
             const int cx = (qx * 8 + fx) >> 1, cy = (qy * 8 + fy) >> 1, cz = (qz * 8 + fz) >> 1;
+            int64_t ic[7];
+            stencil_index(C, cx, cy, cz, ic);
 #pragma unroll
             for (int v = 0; v < 3; v++) {
-                const double c = C.at(v, cx, cy, cz);
-                const double s0 = minmod(C.at(v, cx + 1, cy, cz) - c, c - C.at(v, cx - 1, cy, cz));
-                const double s1 = minmod(C.at(v, cx, cy + 1, cz) - c, c - C.at(v, cx, cy - 1, cz));
-                const double s2 = minmod(C.at(v, cx, cy, cz + 1) - c, c - C.at(v, cx, cy, cz - 1));
+                const int64_t vo = (int64_t)v * PV;
+                const double c = coarse_val<double>(C, 0.0f, ic[0] + vo);
+                const double s0 = minmod(coarse_val<double>(C, 0.0f, ic[1] + vo) - c, c - coarse_val<double>(C, 0.0f, ic[2] + vo));
+                const double s1 = minmod(coarse_val<double>(C, 0.0f, ic[3] + vo) - c, c - coarse_val<double>(C, 0.0f, ic[4] + vo));
+                const double s2 = minmod(coarse_val<double>(C, 0.0f, ic[5] + vo) - c, c - coarse_val<double>(C, 0.0f, ic[6] + vo));
 #pragma unroll
                 for (int k = 0; k < 8; k++) {
                     const double sx = (k & 1) ? 0.25 : -0.25, sy = (k & 2) ? 0.25 : -0.25, sz = (k & 4) ? 0.25 : -0.25;
