@@ -113,3 +113,11 @@ def test_uniform_tables_match_brute_force(np_):
 def test_uniform_tables_reject_odd_counts():
     with pytest.raises(A.AmrHydroError):
         A.amr_hydro_uniform_tables((3, 2, 2))
+
+
+def test_null_context_calls_are_rejected():
+    # entry points that take a context check it before any CUDA work
+    L = A.lib()
+    assert L.amr_hydro_set_shared_dt(None, 1) == A.AMR_E_INVAL
+    assert L.amr_hydro_regrid(None, 0) == A.AMR_E_INVAL
+    assert L.amr_hydro_set_gravity(None, 1.0, 1.7, 10, 2) == A.AMR_E_INVAL
