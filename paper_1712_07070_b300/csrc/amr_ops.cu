@@ -304,7 +304,47 @@ __global__ void k_restrict(double *__restrict__ Uc, const double *__restrict__ U
     }
 }
 
-// Cell flags (section 2.1 refinement criterion, FP64 in every mode):
+// The refinement criterion of one cell from its density r and the six face
+// neighbours' (p: +d, m: -d): with the undivided differences d = 2 g every
+// term is 4 times the criterion's, and scaling by 4 is exact, so
+// D2 = dx^2 + dy^2 + dz^2 > (4 theta^2) r^2 decides exactly as
+// g^2 > theta^2 r^2.  First in FP32 (values rounded on the integer units)
+// with a bound on its error: every rounded value is within 2^-24 of its own
+// size, each difference within delta = 2^-21 M of the exact one (M the
+// largest of the seven magnitudes), so |D2_32 - D2| <= 2^-21 D2_32
+// + 2 delta sum|d| + 3 delta^2 and |T_32 - T| <= 2^-20 T_32; beyond twice
+// those bounds (plus the rounding of the comparison itself) the FP32 result
+// is the FP64 one.  Otherwise, and for magnitudes outside [2^-40, 2^60] or
+// non-finite values, the decision is taken in FP64 (the test on the bit
+// patterns: both sides >= +0, a NaN flags nothing).  theta4 = 4 theta^2.
+__device__ __forceinline__ bool flag_cell(double r, double px, double mx, double py, double my, double pz, double mz,
+                                          double theta4, float theta4f) {
+    const float rf = d2f_bits(r), pxf = d2f_bits(px), mxf = d2f_bits(mx), pyf = d2f_bits(py), myf = d2f_bits(my),
+                pzf = d2f_bits(pz), mzf = d2f_bits(mz);
+    const float M = fmaxf(fmaxf(fmaxf(fabsf(rf), fabsf(pxf)), fmaxf(fabsf(mxf), fabsf(pyf))),
+                          fmaxf(fmaxf(fabsf(myf), fabsf(pzf)), fabsf(mzf)));
+    if (M >= 9.09494702e-13f && M <= 1.1529215e18f) {  // 2^-40 .. 2^60 (NaN fails both): no square underflows
+        const float dx = pxf - mxf, dy = pyf - myf, dz = pzf - mzf;
+        const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        const float t = theta4f * (rf * rf);
+        const float delta = 4.76837158e-7f * M;  // 2^-21 M
+        const float ed = 4.76837158e-7f * d2 + 2.0f * delta * (fabsf(dx) + fabsf(dy) + fabsf(dz)) + 3.0f * delta * delta;
+        // + 2^-20 T, + the comparison's rounding, + 2^-120 for any flushed tiny term
+        const float e = ed + 9.53674316e-7f * t + 9.53674316e-7f * (d2 + t) + 7.52316385e-37f;
+        const float diff = d2 - t;
+        if (diff > 2.0f * e) return true;
+        if (-diff > 2.0f * e) return false;
+    }
+    const double ddx = px - mx, ddy = py - my, ddz = pz - mz;
+    double d2 = ddx * ddx;
+    d2 += ddy * ddy;
+    d2 += ddz * ddz;
+    const long long bd = __double_as_longlong(d2), bt = __double_as_longlong(theta4 * (r * r));
+    return bd > bt && bd <= 0x7ff0000000000000LL;
+}
+
+// Cell flags (section 2.1 refinement criterion, decided as in FP64 in every
+// mode, flag_cell):
 // sum_d ((rho_{+d} - rho_{-d})/2)^2 > theta^2 rho^2; neighbours through the
 // group's 4x4x4 source table (same-level or interpolated ghost patches).
 // The cell flags themselves are not stored: each patch keeps a 27-bit
@@ -319,6 +359,7 @@ __global__ void k_flag_summary(const double *__restrict__ U, const double *__res
     __shared__ int src[64];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;  // warp = local patch 0..7
     const double theta4 = 4.0 * (theta * theta);
+    const float theta4f = d2f_bits(theta4);
     for (int g = blockIdx.x; g < n_groups; g += gridDim.x) {
         __syncthreads();
         if (threadIdx.x < 64) src[threadIdx.x] = nbr[(int64_t)g * 64 + threadIdx.x];
@@ -336,21 +377,9 @@ __global__ void k_flag_summary(const double *__restrict__ U, const double *__res
         for (int c = lane; c < PV; c += 32) {
             const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
             const int x = ox + lx, y = oy + ly, z = oz + lz;
-            const double r = rho_at(x, y, z);
-            // with the undivided differences d = 2 g every term is 4 times
-            // the criterion's, and scaling by 4 is exact, so
-            // D2 = dx^2 + dy^2 + dz^2 > (4 theta^2) r^2 decides exactly as
-            // g^2 > theta^2 r^2 with three FP64 operations fewer; the test
-            // itself compares the bit patterns (both sides >= +0; a NaN
-            // D2 or threshold flags nothing)
-            const double dx = rho_at(x + 1, y, z) - rho_at(x - 1, y, z);
-            const double dy = rho_at(x, y + 1, z) - rho_at(x, y - 1, z);
-            const double dz = rho_at(x, y, z + 1) - rho_at(x, y, z - 1);
-            double d2 = dx * dx;
-            d2 += dy * dy;
-            d2 += dz * dz;
-            const long long bd = __double_as_longlong(d2), bt = __double_as_longlong(theta4 * (r * r));
-            if (!(bd > bt && bd <= 0x7ff0000000000000LL)) continue;
+            if (!flag_cell(rho_at(x, y, z), rho_at(x + 1, y, z), rho_at(x - 1, y, z), rho_at(x, y + 1, z),
+                           rho_at(x, y - 1, z), rho_at(x, y, z + 1), rho_at(x, y, z - 1), theta4, theta4f))
+                continue;
             // parts this cell is in, per dimension (bit 0 low, 1 whole, 2 high)
             const int px = (lx < nbuf) | 2 | (lx >= 8 - nbuf) << 2;
             const int py = (ly < nbuf) | 2 | (ly >= 8 - nbuf) << 2;
@@ -360,6 +389,25 @@ __global__ void k_flag_summary(const double *__restrict__ U, const double *__res
         }
         bits = __reduce_or_sync(0xffffffffu, bits);
         if (lane == 0) summary[8 * (int64_t)g + warp] = bits;
+    }
+}
+
+// Test hook kernel: flag_cell and the plain FP64 decision of n stencils
+// (7 densities each: r, +x, -x, +y, -y, +z, -z).
+__global__ void k_flag_cells_test(const double *__restrict__ v, int n, double theta, int *__restrict__ out) {
+    const double theta4 = 4.0 * (theta * theta);
+    const float theta4f = d2f_bits(theta4);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double *q = v + 7 * (int64_t)i;
+        const bool f = flag_cell(q[0], q[1], q[2], q[3], q[4], q[5], q[6], theta4, theta4f);
+        const double dx = q[1] - q[2], dy = q[3] - q[4], dz = q[5] - q[6];
+        double d2 = dx * dx;
+        d2 += dy * dy;
+        d2 += dz * dz;
+        const long long bd = __double_as_longlong(d2), bt = __double_as_longlong(theta4 * (q[0] * q[0]));
+        const bool e = bd > bt && bd <= 0x7ff0000000000000LL;
+        out[2 * i] = f;
+        out[2 * i + 1] = e;
     }
 }
 
@@ -574,3 +622,27 @@ amr_status amr_hydro_conserved_sum(amr_hydro_ctx *c, int level, double *out) {
 }
 
 }  // extern "C"
+
+// Test hook (not part of the C ABI): flag_cell's decisions and the plain
+// FP64 ones for n host stencils (7 densities each) into out[2 i], out[2 i + 1].
+// 0 on success, -1 on a CUDA error.
+extern "C" int amrh_selftest_flag_cells(const double *vals, int n, double theta, int *out) {
+    double *dv = nullptr;
+    int *dout = nullptr;
+    if (cudaMalloc(&dv, 56 * (size_t)n) != cudaSuccess) return -1;
+    if (cudaMalloc(&dout, 8 * (size_t)n) != cudaSuccess) {
+        cudaFree(dv);
+        return -1;
+    }
+    int rc = 0;
+    if (cudaMemcpy(dv, vals, 56 * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess) rc = -1;
+    if (!rc) {
+        k_flag_cells_test<<<(n + 255) / 256, 256>>>(dv, n, theta, dout);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpy(out, dout, 8 * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = -1;
+    }
+    cudaFree(dv);
+    cudaFree(dout);
+    return rc;
+}

@@ -190,3 +190,31 @@ def test_shared_time_step_matches_oracle(prec, tol):
         scale = np.abs(U0).reshape(5, -1).sum(1) / 32 ** 3
         assert (np.abs(H.conserved_total() - s0) <= 1e-13 * scale).all()
     H.close()
+
+
+def test_flag_criterion_fp32_prefilter_decides_as_fp64():
+    """The refinement criterion's FP32 first pass with its error bound must
+    give the FP64 decision on every stencil, including those within 1e-8 ..
+    1e-1 of the threshold and flat, steep and strongly varying ones."""
+    import ctypes
+    fn = A.lib().amrh_selftest_flag_cells
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p]
+    rng = np.random.default_rng(11)
+    for theta in (0.05, 0.1, 0.3, 1.0):
+        n = 200000
+        r = rng.uniform(0.01, 100.0, n)
+        T = 4 * theta * theta * r * r
+        d = rng.standard_normal((n, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        rel = rng.choice([0.0, 1e-9, 1e-8, 1e-7, 1e-6, 1e-5, 1e-3, 0.1, 0.5], n) * rng.choice([-1.0, 1.0], n)
+        d *= (np.sqrt(T) * (1 + rel))[:, None]
+        base = r[:, None] * (1 + rng.standard_normal((n, 3)) * rng.choice([0.0, 1e-6, 0.1, 1.0], (n, 1)))
+        v = np.empty((n, 7))
+        v[:, 0] = r
+        v[:, 1::2] = base + d / 2
+        v[:, 2::2] = base - d / 2
+        out = np.zeros((n, 2), dtype=np.int32)
+        assert fn(v.ctypes.data, n, theta, out.ctypes.data) == 0
+        assert np.array_equal(out[:, 0], out[:, 1]), (theta, np.nonzero(out[:, 0] != out[:, 1])[0][:5])
+        assert 0 < out[:, 1].sum() < n
