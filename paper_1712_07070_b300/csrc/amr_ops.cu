@@ -283,23 +283,32 @@ __global__ void k_restrict(double *__restrict__ Uc, const double *__restrict__ U
     const int nv = Sc ? NV + 1 : NV;
     for (int e = blockIdx.x; e < n; e += gridDim.x) {
         const int64_t P = list[2 * e], G = list[2 * e + 1];
-        for (int i = threadIdx.x; i < PV * nv; i += blockDim.x) {
-            const int v = i / PV, c = i % PV;
+        for (int c = threadIdx.x; c < PV; c += blockDim.x) {
             const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
-            // the children in (z, y, x) order, summed from the first (the sum
-            // from 0 differs only in the sign of an all-negative-zero sum; on
-            // the narrow FP64 pipe the add saved is a ninth of the kernel)
-            double s = 0.0;
-#pragma unroll
-            for (int k = 0; k < 8; k++) {
-                const int fx = 2 * x + (k & 1), fy = 2 * y + ((k >> 1) & 1), fz = 2 * z + (k >> 2);
-                const int64_t slot = 8 * G + (fx >> 3) + 2 * (fy >> 3) + 4 * (fz >> 3);
-                const int64_t o = (fz & 7) * 64 + (fy & 7) * 8 + (fx & 7);
-                const double f = v < NV ? Uf[slot * PSLOT + v * PV + o] : Sf[slot * PV + o];
-                s = k ? s + f : f;
+            // the eight children lie in one fine patch of the group, at b + {0, 1,
+            // 8, 9, 64, 65, 72, 73}: four 16-byte pairs (b even)
+            const int64_t slot = 8 * G + (x >> 2) + 2 * (y >> 2) + 4 * (z >> 2);
+            const int b = ((2 * z) & 7) * 64 + ((2 * y) & 7) * 8 + ((2 * x) & 7);
+            for (int v = 0; v < nv; v++) {
+                const double *F = v < NV ? Uf + slot * PSLOT + v * PV + b : Sf + slot * PV + b;
+                const double2 a0 = __ldg(reinterpret_cast<const double2 *>(F)),
+                              a1 = __ldg(reinterpret_cast<const double2 *>(F + 8)),
+                              a2 = __ldg(reinterpret_cast<const double2 *>(F + 64)),
+                              a3 = __ldg(reinterpret_cast<const double2 *>(F + 72));
+                // the children in (z, y, x) order, summed from the first (the sum
+                // from 0 differs only in the sign of an all-negative-zero sum; on
+                // the narrow FP64 pipe the add saved is a ninth of the kernel)
+                double s = a0.x;
+                s = s + a0.y;
+                s = s + a1.x;
+                s = s + a1.y;
+                s = s + a2.x;
+                s = s + a2.y;
+                s = s + a3.x;
+                s = s + a3.y;
+                if (v < NV) Uc[P * PSLOT + v * PV + c] = s * 0.125;
+                else Sc[P * PV + c] = s * 0.125;
             }
-            if (v < NV) Uc[P * PSLOT + v * PV + c] = s * 0.125;
-            else Sc[P * PV + c] = s * 0.125;
         }
     }
 }
