@@ -74,6 +74,9 @@ def parse():
                     help="only the box batch restricted to the boxes of edge <= n (profiling case)")
     ap.add_argument("--sor-case", action="store_true",
                     help="only the refined-level SOR solve on the blob hierarchy with an n^3 root (profiling case)")
+    ap.add_argument("--amr-case", action="store_true",
+                    help="only root steps of the 3-level blob hierarchy with an n^3 root in the FP32-compute mode, "
+                         "the timed ones between cudaProfilerStart/Stop (profiling case)")
     return ap.parse_args()
 
 
@@ -747,8 +750,41 @@ def boxes_case(args):
     B.close()
 
 
+def amr_case(args):
+    """The AMR workload alone (3 blobs, seed 3, theta 0.1, N_buf 8/4, lmax 2,
+    n^3 root, FP32 compute): --warmup untimed root steps, then --steps timed
+    ones inside cudaProfilerStart/Stop (for a launch list with ncu's
+    --profile-from-start off); one JSON line."""
+    import torch
+    from paper_1712_07070_b300 import amr_hydro as A
+    from paper_1712_07070_b300 import ics
+    from paper_1712_07070_b300.amr import AmrHierarchy
+    H = AmrHierarchy(ics.blobs(args.n, seed=3), lmax=2, theta=0.1, nbuf=(8, 4), prec=A.AMR_FP32_ACC64,
+                     max_patches=120000)
+    for _ in range(args.warmup):
+        H.advance_root()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    e0, e1 = _events(torch)
+    e0.record()
+    n = 0
+    for _ in range(args.steps):
+        n += H.advance_root()
+    e1.record()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    print(json.dumps({"metric": "cell updates/s", "value": n / max(args.steps, 1) / (ms * 1e-3), "unit": "cells/s",
+                      "ms_per_root_step": ms, "patches": [H.n_patches(l) for l in range(3)],
+                      "config": {"workload": f"AMR blobs, {args.n}^3 root, lmax 2, FP32 compute"}}))
+    H.close()
+
+
 def main():
     args = parse()
+    if args.amr_case:
+        amr_case(args)
+        return
     if args.sor_case:
         sor_case(args)
         return
